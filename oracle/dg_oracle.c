@@ -1,0 +1,1149 @@
+/*
+ * dg_oracle.c -- plain, slow, FP64 CPU oracle for the colored DG right-hand side.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline load this file's library.  The product path (the CUDA library under
+ * paper_1601_07613_gb300/) never links, loads or calls it, and it shares no code,
+ * header, table or constant generator with that path.
+ *
+ * What it computes, and where the paper defines it (Giuliani & Krivodonova,
+ * "Edge coloring in unstructured CFD codes"):
+ *
+ *   - the modal DG semi-discretisation of the conservation law (Eq. 1) as in
+ *     Eq. 2: volume integral of F(U).grad(v_j) minus, over the element's faces,
+ *     the integral of v_j times the numerical flux F(U_i, U_nb).n  (Sec. 1);
+ *     written element by element, exactly as Eq. 2 is stated -- no edge loop,
+ *     no coloring, no scatter, so it is structurally independent of the
+ *     colored edge kernels it checks;
+ *   - the connectivity graph / edge table with left and right elements
+ *     (Sec. 2, Sec. 5 "an edge points to the two elements that share it");
+ *   - the modified greedy coloring, the conflict resolution by swaps and the
+ *     loop breaking of Sec. 3.1;
+ *   - the color-major edge order, the color-1 element renumbering and the
+ *     left-ascending order of the remaining colors of Sec. 5 (Tables 5, 6).
+ *
+ * The paper leaves the DG ingredients to its reference [giuliani]; the readings
+ * used here (orthonormal Dubiner basis, Gauss rules, local Lax-Friedrichs flux,
+ * the CFL rule, SSP-RK3, the RNG and tie-break protocol of the coloring) are
+ * stated beside each function.  Parity pins for each function live in tests/.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXP 8
+#define ORC_MAXNP 165 /* (p+1)(p+2)(p+3)/6 at p = 8 */
+#define ORC_MAXM 5
+
+static char orc_err[256];
+const char *orc_last_error(void) { return orc_err; }
+static int fail(const char *msg) {
+  snprintf(orc_err, sizeof orc_err, "%s", msg);
+  return -1;
+}
+
+/* ======================================================================= */
+/* 1-D Gauss rules                                                          */
+/* ======================================================================= */
+
+/* Jacobi polynomial P_n^{(a,0)}(x) and its derivative, by the classical
+ * three-term recurrence in n (beta = 0). */
+static void jacobi_a0(int n, double a, double x, double *P, double *dP) {
+  double p0 = 1.0, p1, d0 = 0.0, d1;
+  if (n == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  p1 = 0.5 * ((a + 2.0) * x + a);
+  d1 = 0.5 * (a + 2.0);
+  for (int k = 2; k <= n; ++k) {
+    double c = 2.0 * k + a; /* 2k + a + b with b = 0 */
+    double A = 2.0 * k * (k + a) * (c - 2.0);
+    double B = (c - 1.0) * (c * (c - 2.0) * x + a * a);
+    double C = 2.0 * (k + a - 1.0) * (k - 1.0) * c;
+    double p2 = (B * p1 - C * p0) / A;
+    double d2 = ((c - 1.0) * c * (c - 2.0) * p1 + B * d1 - C * d0) / A;
+    p0 = p1;
+    p1 = p2;
+    d0 = d1;
+    d1 = d2;
+  }
+  *P = p1;
+  *dP = d1;
+}
+
+/* n-point Gauss-Jacobi rule for the weight (1-x)^a on [-1, 1] (a = 0 is
+ * Gauss-Legendre).  Roots are bracketed by sign changes on a fine grid, then
+ * polished by Newton; weights from the classical formula
+ *   w_i = 2^(a+1) * G(n+a+1) G(n+1) / (G(n+a+1) n!) / ((1-x_i^2) P_n'(x_i)^2)
+ * which for integer a in {0,1,2} reduces to 2^(a+1) / ((1-x^2) P'^2). */
+int orc_gauss_jacobi(int n, double a, double *x, double *w) {
+  if (n < 1 || n > 64) return fail("gauss_jacobi: n out of range");
+  int found = 0;
+  const int grid = 200000;
+  double xa = -1.0, Pa, dPa;
+  jacobi_a0(n, a, xa, &Pa, &dPa);
+  for (int g = 1; g <= grid && found < n; ++g) {
+    double xb = -1.0 + 2.0 * g / grid, Pb, dPb;
+    jacobi_a0(n, a, xb, &Pb, &dPb);
+    if (Pa == 0.0) {
+      x[found++] = xa;
+    } else if (Pa * Pb < 0.0) {
+      double lo = xa, hi = xb, r = 0.5 * (xa + xb);
+      for (int it = 0; it < 200; ++it) { /* safeguarded Newton */
+        double P, dP;
+        jacobi_a0(n, a, r, &P, &dP);
+        if ((P < 0.0) == (Pa < 0.0)) lo = r; else hi = r;
+        double rn = r - P / dP;
+        if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
+        if (fabs(rn - r) < 1e-17) { r = rn; break; }
+        r = rn;
+      }
+      x[found++] = r;
+    }
+    xa = xb;
+    Pa = Pb;
+  }
+  if (found != n) return fail("gauss_jacobi: root count mismatch");
+  for (int i = 0; i < n; ++i) {
+    double P, dP;
+    jacobi_a0(n, a, x[i], &P, &dP);
+    w[i] = pow(2.0, a + 1.0) / ((1.0 - x[i] * x[i]) * dP * dP);
+  }
+  return 0;
+}
+
+int orc_gauss_legendre(int n, double *x, double *w) { return orc_gauss_jacobi(n, 0.0, x, w); }
+
+/* ======================================================================= */
+/* Reference-element rules (collapsed "Duffy" products)                    */
+/* ======================================================================= */
+
+/* Triangle {r,s >= 0, r+s <= 1}: n Gauss-Legendre points in xi times n
+ * Gauss-Jacobi(1,0) points in eta; r = (1+xi)(1-eta)/4, s = (1+eta)/2,
+ * w = w_xi w_eta / 8.  Exact for total degree 2n-1.  Point index = i*n + k
+ * (i over eta, k over xi). */
+int orc_tri_rule(int n, double *r, double *s, double *w) {
+  double xg[64], wg[64], xj[64], wj[64];
+  if (orc_gauss_jacobi(n, 0.0, xg, wg) || orc_gauss_jacobi(n, 1.0, xj, wj)) return -1;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      r[i * n + k] = 0.25 * (1.0 + xg[k]) * (1.0 - xj[i]);
+      s[i * n + k] = 0.5 * (1.0 + xj[i]);
+      w[i * n + k] = wg[k] * wj[i] / 8.0;
+    }
+  return 0;
+}
+
+/* Tetrahedron {r,s,t >= 0, r+s+t <= 1}: Gauss-Legendre x Gauss-Jacobi(1,0) x
+ * Gauss-Jacobi(2,0), n points each; exact for total degree 2n-1. */
+int orc_tet_rule(int n, double *r, double *s, double *t, double *w) {
+  double xa[64], wa[64], xb[64], wb[64], xc[64], wc[64];
+  if (orc_gauss_jacobi(n, 0.0, xa, wa) || orc_gauss_jacobi(n, 1.0, xb, wb) ||
+      orc_gauss_jacobi(n, 2.0, xc, wc))
+    return -1;
+  int q = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k, ++q) {
+        double a = xa[k], b = xb[j], c = xc[i];
+        t[q] = 0.5 * (1.0 + c);
+        s[q] = 0.25 * (1.0 + b) * (1.0 - c);
+        r[q] = 0.125 * (1.0 + a) * (1.0 - b) * (1.0 - c);
+        w[q] = wa[k] * wb[j] * wc[i] / 64.0;
+      }
+  return 0;
+}
+
+/* ======================================================================= */
+/* Orthonormal modal basis (the v_ij of Eq. 2)                              */
+/* ======================================================================= */
+/* Reading: Dubiner's orthogonal polynomials on the reference simplex,
+ * normalised to unit L2 norm on the reference element.  Ordering by total
+ * degree d = 0..p; within a degree the first index runs from d down to 0.
+ *
+ * Triangle: phi_{k,l}(r,s) = N_kl Q_k(r,s) P_l^{(2k+1,0)}(2s-1),
+ *   Q_k = (1-s)^k P_k(2r/(1-s) - 1), evaluated without division through
+ *   (n+1) Q_{n+1} = (2n+1)(2r-1+s) Q_n - n (1-s)^2 Q_{n-1}, Q_0 = 1,
+ *   Q_1 = 2r - 1 + s;  N_kl^2 = 2 (2k+1)(k+l+1) (closed form of the Jacobi
+ *   norms; pinned numerically by the orthonormality test). */
+
+static int npoly_tri(int p) { return (p + 1) * (p + 2) / 2; }
+static int npoly_tet(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+/* Q_n, dQ/dr, dQ/ds for n = 0..p of the homogeneous Legendre recurrence in
+ * the variable (2r - 1 + s) with "scale" (1 - s); used by both simplices. */
+static void hleg(int p, double u, double du_dr, double du_ds, double v, double dv_ds,
+                 double *Q, double *Qr, double *Qs) {
+  /* Q_n = v^n P_n(u / v); recurrence (n+1)Q_{n+1} = (2n+1) u Q_n - n v^2 Q_{n-1} */
+  Q[0] = 1.0;
+  Qr[0] = 0.0;
+  Qs[0] = 0.0;
+  if (p >= 1) {
+    Q[1] = u;
+    Qr[1] = du_dr;
+    Qs[1] = du_ds;
+  }
+  for (int n = 1; n < p; ++n) {
+    Q[n + 1] = ((2 * n + 1) * u * Q[n] - n * v * v * Q[n - 1]) / (n + 1);
+    Qr[n + 1] = ((2 * n + 1) * (du_dr * Q[n] + u * Qr[n]) - n * v * v * Qr[n - 1]) / (n + 1);
+    Qs[n + 1] = ((2 * n + 1) * (du_ds * Q[n] + u * Qs[n]) -
+                 n * (2.0 * v * dv_ds * Q[n - 1] + v * v * Qs[n - 1])) / (n + 1);
+  }
+}
+
+int orc_basis_tri(int p, double r, double s, double *phi, double *dr, double *ds) {
+  if (p < 0 || p > ORC_MAXP) return fail("basis_tri: p out of range");
+  double Q[ORC_MAXP + 1], Qr[ORC_MAXP + 1], Qs[ORC_MAXP + 1];
+  hleg(p, 2.0 * r - 1.0 + s, 2.0, 1.0, 1.0 - s, -1.0, Q, Qr, Qs);
+  int j = 0;
+  for (int d = 0; d <= p; ++d)
+    for (int k = d; k >= 0; --k) {
+      int l = d - k;
+      double J, dJ;
+      jacobi_a0(l, 2.0 * k + 1.0, 2.0 * s - 1.0, &J, &dJ);
+      double N = sqrt(2.0 * (2 * k + 1) * (k + l + 1));
+      phi[j] = N * Q[k] * J;
+      if (dr) dr[j] = N * Qr[k] * J;
+      if (ds) ds[j] = N * (Qs[k] * J + Q[k] * 2.0 * dJ);
+      ++j;
+    }
+  return j;
+}
+
+/* Tetrahedron: phi_{i,j,k} = N Q_i R_ij P_k^{(2i+2j+2,0)}(2t-1),
+ *   Q_i  = (1-s-t)^i P_i(2r/(1-s-t) - 1),
+ *   R_ij = (1-t)^j P_j^{(2i+1,0)}(2s/(1-t) - 1)   (homogeneous Jacobi, below),
+ *   N^2  = 2 (2i+1)(i+j+1)(2i+2j+2k+3)  (closed form of the three Jacobi norms
+ *          in collapsed coordinates; pinned numerically by orthonormality).
+ * Ordering: d = 0..p, i = d..0, j = d-i..0, k = d-i-j. */
+/* homogeneous Jacobi H_n = v^n P_n^{(a,0)}(u/v) with partial derivatives */
+static void hjac(int p, double a, double u, double ur, double us, double ut, double v, double vs,
+                 double vt, double *H, double *Hr, double *Hs, double *Ht) {
+  H[0] = 1.0;
+  Hr[0] = Hs[0] = Ht[0] = 0.0;
+  if (p >= 1) {
+    /* P_1 = ((a+2) x + a)/2  ->  H_1 = ((a+2) u + a v)/2 */
+    H[1] = 0.5 * ((a + 2.0) * u + a * v);
+    Hr[1] = 0.5 * ((a + 2.0) * ur);
+    Hs[1] = 0.5 * ((a + 2.0) * us + a * vs);
+    Ht[1] = 0.5 * ((a + 2.0) * ut + a * vt);
+  }
+  for (int n = 2; n <= p; ++n) {
+    double c = 2.0 * n + a;
+    double A = 2.0 * n * (n + a) * (c - 2.0);
+    double B1 = (c - 1.0) * c * (c - 2.0); /* multiplies x P_{n-1} -> u H_{n-1} */
+    double B0 = (c - 1.0) * a * a;         /* multiplies P_{n-1}   -> v H_{n-1} */
+    double C = 2.0 * (n + a - 1.0) * (n - 1.0) * c; /* multiplies P_{n-2} -> v^2 H_{n-2} */
+    H[n] = (B1 * u * H[n - 1] + B0 * v * H[n - 1] - C * v * v * H[n - 2]) / A;
+    Hr[n] = (B1 * (ur * H[n - 1] + u * Hr[n - 1]) + B0 * v * Hr[n - 1] - C * v * v * Hr[n - 2]) / A;
+    Hs[n] = (B1 * (us * H[n - 1] + u * Hs[n - 1]) + B0 * (vs * H[n - 1] + v * Hs[n - 1]) -
+             C * (2.0 * v * vs * H[n - 2] + v * v * Hs[n - 2])) / A;
+    Ht[n] = (B1 * (ut * H[n - 1] + u * Ht[n - 1]) + B0 * (vt * H[n - 1] + v * Ht[n - 1]) -
+             C * (2.0 * v * vt * H[n - 2] + v * v * Ht[n - 2])) / A;
+  }
+}
+
+int orc_basis_tet(int p, double r, double s, double t, double *phi, double *dr, double *ds,
+                  double *dt) {
+  if (p < 0 || p > ORC_MAXP) return fail("basis_tet: p out of range");
+  /* Q_i: homogeneous Legendre in u = 2r - 1 + s + t, v = 1 - s - t */
+  double Q[ORC_MAXP + 1], Qr[ORC_MAXP + 1], Qs[ORC_MAXP + 1], Qt[ORC_MAXP + 1];
+  hjac(p, 0.0, 2.0 * r - 1.0 + s + t, 2.0, 1.0, 1.0, 1.0 - s - t, -1.0, -1.0, Q, Qr, Qs, Qt);
+  int n = 0;
+  for (int d = 0; d <= p; ++d)
+    for (int i = d; i >= 0; --i) {
+      /* R_ij: homogeneous Jacobi(2i+1,0) in u = 2s - 1 + t, v = 1 - t */
+      double R[ORC_MAXP + 1], Rr[ORC_MAXP + 1], Rs[ORC_MAXP + 1], Rt[ORC_MAXP + 1];
+      hjac(d - i, 2.0 * i + 1.0, 2.0 * s - 1.0 + t, 0.0, 2.0, 1.0, 1.0 - t, 0.0, -1.0, R, Rr, Rs, Rt);
+      for (int j = d - i; j >= 0; --j) {
+        int k = d - i - j;
+        double J, dJ;
+        jacobi_a0(k, 2.0 * i + 2.0 * j + 2.0, 2.0 * t - 1.0, &J, &dJ);
+        double N = sqrt(2.0 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3));
+        double a = Q[i] * R[j];
+        phi[n] = N * a * J;
+        if (dr) dr[n] = N * (Qr[i] * R[j]) * J;
+        if (ds) ds[n] = N * (Qs[i] * R[j] + Q[i] * Rs[j]) * J;
+        if (dt) dt[n] = N * ((Qt[i] * R[j] + Q[i] * Rt[j]) * J + a * 2.0 * dJ);
+        ++n;
+      }
+    }
+  return n;
+}
+
+/* ======================================================================= */
+/* Mesh: edge/face table (Sec. 2 connectivity graph, Sec. 5 edge table)     */
+/* ======================================================================= */
+/* Reading of the edge table: a face key is the sorted tuple of its global
+ * vertex ids; faces are numbered in order of first appearance when elements
+ * 0..E-1 and their local faces 0..F-1 are scanned; the left element is the
+ * first to list the face, the right the second (-1 on a boundary).
+ * Local face q of a triangle (v0,v1,v2) is (v_q, v_{q+1 mod 3}); local face q
+ * of a tetrahedron is the face opposite vertex q.  Periodic meshes share
+ * vertex ids across the period; each element's coordinates are unwrapped to
+ * lie within half a period of its vertex 0. */
+
+typedef struct {
+  int dim, nvpe, nfpe;
+  int64_t nv, ne, ns;
+  double L[3];
+  int periodic;
+  double *X;      /* ne * nvpe * dim unwrapped vertex coordinates */
+  int32_t *ev;    /* ne * nvpe */
+  int32_t *sl, *sr;
+  int8_t *sql, *sqr;
+  int32_t *es;    /* ne * nfpe: side of each local face */
+  int32_t *enb;   /* ne * nfpe: neighbour element (-1 on boundary) */
+  /* geometry, FP64 */
+  double *detJ;   /* ne */
+  double *Jinv;   /* ne * dim * dim, row k = grad of reference coordinate k */
+} orc_mesh;
+
+static void face_verts(int dim, int q, int *fv) {
+  if (dim == 2) {
+    fv[0] = q;
+    fv[1] = (q + 1) % 3;
+  } else {
+    int n = 0;
+    for (int k = 0; k < 4; ++k)
+      if (k != q) fv[n++] = k;
+  }
+}
+
+typedef struct {
+  int32_t k[3];
+  int64_t idx;
+} fkey;
+
+static int fkey_cmp(const void *a, const void *b) {
+  const fkey *x = (const fkey *)a, *y = (const fkey *)b;
+  for (int i = 0; i < 3; ++i)
+    if (x->k[i] != y->k[i]) return x->k[i] < y->k[i] ? -1 : 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static void sort3(int32_t *k, int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (k[j] < k[i]) {
+        int32_t t = k[i];
+        k[i] = k[j];
+        k[j] = t;
+      }
+}
+
+static double det_and_inv(int dim, const double *J, double *Ji) {
+  /* J column-major by reference direction: J[a*dim + k] = d x_a / d r_k */
+  if (dim == 2) {
+    double a = J[0], b = J[1], c = J[2], d = J[3]; /* [[a b],[c d]] */
+    double det = a * d - b * c;
+    Ji[0] = d / det;
+    Ji[1] = -b / det;
+    Ji[2] = -c / det;
+    Ji[3] = a / det;
+    return det;
+  }
+  double a = J[0], b = J[1], c = J[2], d = J[3], e = J[4], f = J[5], g = J[6], h = J[7], i = J[8];
+  double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+  Ji[0] = (e * i - f * h) / det;
+  Ji[1] = (c * h - b * i) / det;
+  Ji[2] = (b * f - c * e) / det;
+  Ji[3] = (f * g - d * i) / det;
+  Ji[4] = (a * i - c * g) / det;
+  Ji[5] = (c * d - a * f) / det;
+  Ji[6] = (d * h - e * g) / det;
+  Ji[7] = (b * g - a * h) / det;
+  Ji[8] = (a * e - b * d) / det;
+  return det;
+}
+
+void orc_mesh_free(void *h);
+
+void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
+                   const double *L) {
+  if (dim != 2 && dim != 3) return fail("mesh: dim must be 2 or 3"), (void *)0;
+  if (ne <= 0 || nv <= 0 || ne > (1LL << 30) || nv > (1LL << 30))
+    return fail("mesh: element or vertex count out of range"), (void *)0;
+  orc_mesh *m = (orc_mesh *)calloc(1, sizeof *m);
+  m->dim = dim;
+  m->nvpe = dim + 1;
+  m->nfpe = dim + 1;
+  m->nv = nv;
+  m->ne = ne;
+  m->periodic = L != NULL;
+  for (int a = 0; a < dim; ++a) m->L[a] = L ? L[a] : 0.0;
+  int nvpe = m->nvpe, nfpe = m->nfpe;
+  m->ev = (int32_t *)malloc(sizeof(int32_t) * ne * nvpe);
+  memcpy(m->ev, ev, sizeof(int32_t) * ne * nvpe);
+  m->X = (double *)malloc(sizeof(double) * ne * nvpe * dim);
+  m->detJ = (double *)malloc(sizeof(double) * ne);
+  m->Jinv = (double *)malloc(sizeof(double) * ne * dim * dim);
+  for (int64_t e = 0; e < ne; ++e) {
+    for (int k = 0; k < nvpe; ++k) {
+      int32_t v = ev[e * nvpe + k];
+      if (v < 0 || v >= nv) {
+        orc_mesh_free(m);
+        return fail("mesh: vertex id out of range"), (void *)0;
+      }
+      for (int a = 0; a < dim; ++a) {
+        double x = xyz[(int64_t)v * dim + a];
+        if (m->periodic && k > 0) {
+          double x0 = m->X[(e * nvpe) * dim + a];
+          x += m->L[a] * round((x0 - x) / m->L[a]);
+        }
+        m->X[(e * nvpe + k) * dim + a] = x;
+      }
+    }
+    double J[9];
+    const double *X = m->X + e * nvpe * dim;
+    for (int a = 0; a < dim; ++a)
+      for (int k = 0; k < dim; ++k) J[a * dim + k] = X[(k + 1) * dim + a] - X[a];
+    double det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
+    if (!(det > 0.0)) {
+      orc_mesh_free(m);
+      return fail("mesh: element with non-positive Jacobian"), (void *)0;
+    }
+    m->detJ[e] = det;
+  }
+  /* face table by sorting keys */
+  int64_t nent = ne * nfpe;
+  fkey *keys = (fkey *)malloc(sizeof(fkey) * nent);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int q = 0; q < nfpe; ++q) {
+      int fv[3];
+      face_verts(dim, q, fv);
+      fkey *k = keys + e * nfpe + q;
+      k->k[2] = -1;
+      for (int i = 0; i < dim; ++i) k->k[i] = ev[e * nvpe + fv[i]];
+      sort3(k->k, dim);
+      k->idx = e * nfpe + q;
+    }
+  qsort(keys, nent, sizeof(fkey), fkey_cmp);
+  int64_t *partner = (int64_t *)malloc(sizeof(int64_t) * nent);
+  char *first = (char *)calloc(nent, 1);
+  int bad = 0;
+  for (int64_t i = 0; i < nent;) {
+    int64_t j = i + 1;
+    while (j < nent && memcmp(keys[j].k, keys[i].k, sizeof keys[i].k) == 0) ++j;
+    if (j - i > 2) bad = 1;
+    if (j - i == 2 && keys[i].idx / nfpe == keys[i + 1].idx / nfpe) bad = 1;
+    first[keys[i].idx] = 1;
+    partner[keys[i].idx] = (j - i == 2) ? keys[i + 1].idx : -1;
+    if (j - i == 2) partner[keys[i + 1].idx] = keys[i].idx;
+    i = j;
+  }
+  free(keys);
+  if (bad) {
+    free(partner);
+    free(first);
+    orc_mesh_free(m);
+    return fail("mesh: face shared by more than two elements"), (void *)0;
+  }
+  m->es = (int32_t *)malloc(sizeof(int32_t) * nent);
+  m->enb = (int32_t *)malloc(sizeof(int32_t) * nent);
+  m->sl = (int32_t *)malloc(sizeof(int32_t) * nent);
+  m->sr = (int32_t *)malloc(sizeof(int32_t) * nent);
+  m->sql = (int8_t *)malloc(nent);
+  m->sqr = (int8_t *)malloc(nent);
+  int64_t ns = 0;
+  for (int64_t i = 0; i < nent; ++i) {
+    if (!first[i]) continue;
+    int64_t s = ns++;
+    m->sl[s] = (int32_t)(i / nfpe);
+    m->sql[s] = (int8_t)(i % nfpe);
+    m->es[i] = (int32_t)s;
+    if (partner[i] >= 0) {
+      int64_t o = partner[i];
+      m->sr[s] = (int32_t)(o / nfpe);
+      m->sqr[s] = (int8_t)(o % nfpe);
+      m->es[o] = (int32_t)s;
+      m->enb[i] = (int32_t)(o / nfpe);
+      m->enb[o] = (int32_t)(i / nfpe);
+    } else {
+      m->sr[s] = -1;
+      m->sqr[s] = -1;
+      m->enb[i] = -1;
+    }
+  }
+  m->ns = ns;
+  free(partner);
+  free(first);
+  return m;
+}
+
+void orc_mesh_free(void *h) {
+  orc_mesh *m = (orc_mesh *)h;
+  if (!m) return;
+  free(m->X);
+  free(m->ev);
+  free(m->sl);
+  free(m->sr);
+  free(m->sql);
+  free(m->sqr);
+  free(m->es);
+  free(m->enb);
+  free(m->detJ);
+  free(m->Jinv);
+  free(m);
+}
+
+int64_t orc_mesh_nsides(void *h) { return ((orc_mesh *)h)->ns; }
+
+void orc_mesh_sides(void *h, int32_t *l, int32_t *r, int8_t *ql, int8_t *qr) {
+  orc_mesh *m = (orc_mesh *)h;
+  memcpy(l, m->sl, sizeof(int32_t) * m->ns);
+  memcpy(r, m->sr, sizeof(int32_t) * m->ns);
+  memcpy(ql, m->sql, m->ns);
+  memcpy(qr, m->sqr, m->ns);
+}
+
+void orc_mesh_detj(void *h, double *detJ) {
+  orc_mesh *m = (orc_mesh *)h;
+  memcpy(detJ, m->detJ, sizeof(double) * m->ne);
+}
+
+/* ======================================================================= */
+/* Coloring (Sec. 3.1)                                                       */
+/* ======================================================================= */
+/* Reading of "randomly": xorshift64 (Marsaglia 2003), state = seed or
+ * 0x9E3779B97F4A7C15 when seed = 0; one draw is x ^= x<<13, x ^= x>>7,
+ * x ^= x<<17; pick(n) = (draw >> 32) mod n, drawn even when n = 1. */
+typedef struct {
+  uint64_t x;
+} orc_rng;
+static uint64_t rng_draw(orc_rng *g) {
+  uint64_t x = g->x;
+  x ^= x << 13;
+  x ^= x >> 7;
+  x ^= x << 17;
+  g->x = x;
+  return x;
+}
+static int rng_pick(orc_rng *g, int n) { return (int)((rng_draw(g) >> 32) % (uint64_t)n); }
+
+/* colors (1..nc) that no other face of left(k) or right(k) carries, ascending */
+static int avail_colors(const orc_mesh *m, const int8_t *col, int nc, int64_t k, int *out) {
+  int used[16] = {0};
+  int32_t el[2] = {m->sl[k], m->sr[k]};
+  for (int side = 0; side < 2; ++side) {
+    if (el[side] < 0) continue;
+    for (int q = 0; q < m->nfpe; ++q) {
+      int32_t f = m->es[(int64_t)el[side] * m->nfpe + q];
+      if (f != k && col[f] > 0) used[col[f]] = 1;
+    }
+  }
+  int n = 0;
+  for (int c = 1; c <= nc; ++c)
+    if (!used[c]) out[n++] = c;
+  return n;
+}
+
+/* stats[0] = conflicts left by the greedy pass, [1] = swaps, [2] = loop breaks,
+ * [3] = deferrals.  Returns 0, or 1 when the swap cap was exceeded. */
+int orc_color(void *h, int nc, uint64_t seed, int64_t max_swaps, int8_t *col, int64_t *stats) {
+  orc_mesh *m = (orc_mesh *)h;
+  int64_t ns = m->ns;
+  if (nc < m->nfpe || nc > 15) return fail("color: bad color count");
+  if (max_swaps <= 0) max_swaps = 1000 * ns;
+  orc_rng g = {seed ? seed : 0x9E3779B97F4A7C15ull};
+  for (int64_t k = 0; k < ns; ++k) col[k] = -1;
+  /* FIFO of uncolored faces as a ring buffer; it never holds a face twice */
+  int64_t cap = ns + 1, head = 0, tail = 0, qlen = 0;
+  int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * cap);
+  int64_t *stamp = (int64_t *)malloc(sizeof(int64_t) * ns);
+  for (int64_t k = 0; k < ns; ++k) stamp[k] = -1;
+  int av[16];
+  /* modified greedy: a random nonconflicting color from C, or -1 */
+  for (int64_t k = 0; k < ns; ++k) {
+    int n = avail_colors(m, col, nc, k, av);
+    if (n == 0) {
+      queue[tail] = k;
+      tail = (tail + 1) % cap;
+      ++qlen;
+    } else {
+      col[k] = (int8_t)av[rng_pick(&g, n)];
+    }
+  }
+  stats[0] = qlen;
+  stats[1] = stats[2] = stats[3] = 0;
+  int64_t work = 0, chain = 0;
+  int rc = 0;
+  while (qlen > 0) {
+    int64_t e = queue[head];
+    head = (head + 1) % cap;
+    --qlen;
+    if (col[e] >= 0) continue;
+    ++chain;
+    stamp[e] = chain;
+    int64_t prev = -1;
+    for (;;) {
+      int n = avail_colors(m, col, nc, e, av);
+      if (n > 0) {
+        col[e] = (int8_t)av[rng_pick(&g, n)];
+        break;
+      }
+      /* candidate swaps that do not raise the conflict count: faces f of
+       * left(e) then right(e), in local order, f != e, f != prev, colored,
+       * whose color occurs once among all faces of left(e), right(e) but e */
+      int64_t cand[16];
+      int nca = 0;
+      int cnt[16] = {0};
+      int32_t el[2] = {m->sl[e], m->sr[e]};
+      for (int side = 0; side < 2; ++side)
+        for (int q = 0; q < m->nfpe; ++q) {
+          int32_t f = m->es[(int64_t)el[side] * m->nfpe + q];
+          if (f != e && col[f] > 0) cnt[col[f]]++;
+        }
+      for (int side = 0; side < 2; ++side)
+        for (int q = 0; q < m->nfpe; ++q) {
+          int32_t f = m->es[(int64_t)el[side] * m->nfpe + q];
+          if (f == e || f == prev || col[f] <= 0) continue;
+          if (cnt[col[f]] == 1) cand[nca++] = f;
+        }
+      if (nca > 0) {
+        int64_t f = cand[rng_pick(&g, nca)];
+        if (stamp[f] != chain) {
+          if (++work > max_swaps) { rc = 1; goto done; }
+          col[e] = col[f];
+          col[f] = -1;
+          prev = e;
+          e = f;
+          stamp[f] = chain;
+          stats[1]++;
+          continue;
+        }
+      }
+      /* loop break: the smallest color carried by a face a of left(e) and a
+       * face b of right(e); e takes it, a and b become conflicts (Sec. 3.1) */
+      if (++work > max_swaps) { rc = 1; goto done; }
+      int32_t fa = -1, fb = -1;
+      for (int c = 1; c <= nc && fa < 0; ++c) {
+        int32_t a = -1, b = -1;
+        for (int q = 0; q < m->nfpe; ++q) {
+          int32_t f = m->es[(int64_t)el[0] * m->nfpe + q];
+          if (f != e && col[f] == c) a = f;
+          if (el[1] >= 0) {
+            int32_t f2 = m->es[(int64_t)el[1] * m->nfpe + q];
+            if (f2 != e && col[f2] == c) b = f2;
+          }
+        }
+        if (a >= 0 && b >= 0) {
+          fa = a;
+          fb = b;
+          col[e] = (int8_t)c;
+        }
+      }
+      if (fa >= 0) {
+        col[fa] = -1;
+        col[fb] = -1;
+        queue[tail] = fa;
+        tail = (tail + 1) % cap;
+        queue[tail] = fb;
+        tail = (tail + 1) % cap;
+        qlen += 2;
+        stats[2]++;
+      } else {
+        /* reading: no color is shared by the two sides (possible only when
+         * another conflict touches e); defer e to the back of the queue */
+        queue[tail] = e;
+        tail = (tail + 1) % cap;
+        qlen += 1;
+        stats[3]++;
+      }
+      break;
+    }
+  }
+done:
+  free(queue);
+  free(stamp);
+  if (rc) return fail("color: swap cap exceeded"), 1;
+  return 0;
+}
+
+/* Naive greedy (Sec. 1): the first color not used by the faces of left and
+ * right; needs up to 5 colors on triangles, 7 on tetrahedra. */
+int orc_color_naive(void *h, int8_t *col) {
+  orc_mesh *m = (orc_mesh *)h;
+  int maxc = 0;
+  for (int64_t k = 0; k < m->ns; ++k) col[k] = -1;
+  for (int64_t k = 0; k < m->ns; ++k) {
+    int av[16];
+    if (avail_colors(m, col, 15, k, av) == 0) return fail("naive: more than 15 colors");
+    col[k] = (int8_t)av[0];
+    if (av[0] > maxc) maxc = av[0];
+  }
+  return maxc;
+}
+
+/* ======================================================================= */
+/* Reordering (Sec. 5, Tables 5 and 6)                                      */
+/* ======================================================================= */
+/* Edges stable-sorted by color.  The k-th color-1 edge's left element becomes
+ * element k; the right elements of the interior color-1 edges follow, from
+ * N1 on, in the same order (= N1 + k on a closed mesh); elements reached by
+ * no color-1 edge are appended in original order (reading).  Within each
+ * color >= 2 edges are sorted by new left id, ties by original id. */
+static const int32_t *g_newl; /* qsort context */
+static int edge_cmp_left(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  if (g_newl[x] != g_newl[y]) return g_newl[x] < g_newl[y] ? -1 : 1;
+  return x < y ? -1 : (x > y);
+}
+
+int orc_reorder(void *h, int nc, const int8_t *col, int32_t *elem_new_of_old,
+                int32_t *side_new_of_old, int32_t *offsets) {
+  orc_mesh *m = (orc_mesh *)h;
+  int64_t ns = m->ns, ne = m->ne;
+  for (int c = 0; c <= nc; ++c) offsets[c] = 0;
+  for (int64_t k = 0; k < ns; ++k) {
+    if (col[k] < 1 || col[k] > nc) return fail("reorder: uncolored edge");
+    offsets[col[k]]++;
+  }
+  for (int c = 1; c <= nc; ++c) offsets[c] += offsets[c - 1];
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ns);
+  int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (nc + 1));
+  for (int c = 0; c <= nc; ++c) fill[c] = offsets[c > 0 ? c - 1 : 0];
+  for (int c = 1; c <= nc; ++c) fill[c] = offsets[c - 1];
+  for (int64_t k = 0; k < ns; ++k) order[fill[col[k]]++] = (int32_t)k; /* stable */
+  for (int64_t e = 0; e < ne; ++e) elem_new_of_old[e] = -1;
+  int32_t next = 0, n1 = offsets[1];
+  for (int32_t i = 0; i < n1; ++i) {
+    int32_t l = m->sl[order[i]];
+    if (elem_new_of_old[l] < 0) elem_new_of_old[l] = next++;
+  }
+  for (int32_t i = 0; i < n1; ++i) {
+    int32_t r = m->sr[order[i]];
+    if (r >= 0 && elem_new_of_old[r] < 0) elem_new_of_old[r] = next++;
+  }
+  for (int64_t e = 0; e < ne; ++e)
+    if (elem_new_of_old[e] < 0) elem_new_of_old[e] = next++;
+  int32_t *newl = (int32_t *)malloc(sizeof(int32_t) * ns);
+  for (int64_t k = 0; k < ns; ++k) newl[k] = elem_new_of_old[m->sl[k]];
+  g_newl = newl;
+  for (int c = 2; c <= nc; ++c)
+    qsort(order + offsets[c - 1], offsets[c] - offsets[c - 1], sizeof(int32_t), edge_cmp_left);
+  for (int32_t i = 0; i < ns; ++i) side_new_of_old[order[i]] = i;
+  free(order);
+  free(fill);
+  free(newl);
+  return 0;
+}
+
+/* ======================================================================= */
+/* Physics: Euler flux and local Lax-Friedrichs flux                        */
+/* ======================================================================= */
+/* Euler: U = (rho, rho u, rho v[, rho w], E), p = (gamma-1)(E - rho|u|^2/2).
+ * Reading of "Lax-Friedrichs": local (Rusanov) at each quadrature point,
+ *   F* = (F(U-).n + F(U+).n)/2 - lambda (U+ - U-)/2,
+ *   lambda = max(|u-.n| + c-, |u+.n| + c+),  c = sqrt(gamma p / rho).
+ * Linear advection (M = 1, F = a u) is kept for the exactness pins; there the
+ * same formula is the upwind flux. */
+#define ORC_GAMMA 1.4
+enum { ORC_EULER = 0, ORC_ADVECTION = 1 };
+
+static void euler_flux_n(int dim, const double *U, const double *n, double *Fn, double *lam) {
+  double rho = U[0], E = U[dim + 1];
+  double vel[3] = {0, 0, 0}, q2 = 0.0, un = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    vel[a] = U[1 + a] / rho;
+    q2 += vel[a] * vel[a];
+    un += vel[a] * n[a];
+  }
+  double p = (ORC_GAMMA - 1.0) * (E - 0.5 * rho * q2);
+  Fn[0] = rho * un;
+  for (int a = 0; a < dim; ++a) Fn[1 + a] = U[1 + a] * un + p * n[a];
+  Fn[dim + 1] = (E + p) * un;
+  *lam = fabs(un) + sqrt(ORC_GAMMA * p / rho);
+}
+
+/* physical flux in direction a (for the volume term) */
+static void euler_flux_dir(int dim, const double *U, int a, double *F) {
+  double n[3] = {0, 0, 0}, lam;
+  n[a] = 1.0;
+  euler_flux_n(dim, U, n, F, &lam);
+}
+
+typedef struct {
+  int kind, dim, M;
+  double adv[3];
+} orc_phys;
+
+static void phys_flux_dir(const orc_phys *ph, const double *U, int a, double *F) {
+  if (ph->kind == ORC_EULER) euler_flux_dir(ph->dim, U, a, F);
+  else F[0] = ph->adv[a] * U[0];
+}
+
+static void num_flux(const orc_phys *ph, const double *Um, const double *Up, const double *n,
+                     double *Fs) {
+  if (ph->kind == ORC_EULER) {
+    double Fm[ORC_MAXM], Fp[ORC_MAXM], lm, lp;
+    euler_flux_n(ph->dim, Um, n, Fm, &lm);
+    euler_flux_n(ph->dim, Up, n, Fp, &lp);
+    double lam = lm > lp ? lm : lp;
+    for (int k = 0; k < ph->M; ++k) Fs[k] = 0.5 * (Fm[k] + Fp[k]) - 0.5 * lam * (Up[k] - Um[k]);
+  } else {
+    double an = 0.0;
+    for (int a = 0; a < ph->dim; ++a) an += ph->adv[a] * n[a];
+    Fs[0] = 0.5 * an * (Um[0] + Up[0]) - 0.5 * fabs(an) * (Up[0] - Um[0]);
+  }
+}
+
+/* exported for the flux pins */
+int orc_lf_flux(int dim, const double *Um, const double *Up, const double *n, double *Fs) {
+  orc_phys ph = {ORC_EULER, dim, dim + 2, {0, 0, 0}};
+  num_flux(&ph, Um, Up, n, Fs);
+  return 0;
+}
+
+/* ======================================================================= */
+/* Eq. 2, element by element                                                */
+/* ======================================================================= */
+
+static int basis_eval(int dim, int p, const double *x, double *phi, double *d0, double *d1,
+                      double *d2) {
+  if (dim == 2) return orc_basis_tri(p, x[0], x[1], phi, d0, d1);
+  return orc_basis_tet(p, x[0], x[1], x[2], phi, d0, d1, d2);
+}
+
+/* reference coordinates of physical point x in element e (nearest periodic
+ * image of x to the element's centroid) */
+static void ref_coords(const orc_mesh *m, int64_t e, const double *x, double *rs) {
+  int dim = m->dim;
+  const double *X = m->X + e * m->nvpe * dim;
+  double xs[3];
+  for (int a = 0; a < dim; ++a) {
+    double cen = 0.0;
+    for (int k = 0; k < m->nvpe; ++k) cen += X[k * dim + a];
+    cen /= m->nvpe;
+    xs[a] = x[a];
+    if (m->periodic) xs[a] += m->L[a] * round((cen - x[a]) / m->L[a]);
+  }
+  const double *Ji = m->Jinv + e * dim * dim;
+  for (int k = 0; k < dim; ++k) {
+    double v = 0.0;
+    for (int a = 0; a < dim; ++a) v += Ji[k * dim + a] * (xs[a] - X[a]);
+    rs[k] = v;
+  }
+}
+
+static void eval_state(int dim, int p, int M, int Np, const double *c, const double *rs,
+                       double *U) {
+  double phi[ORC_MAXNP];
+  basis_eval(dim, p, rs, phi, NULL, NULL, NULL);
+  for (int k = 0; k < M; ++k) {
+    double v = 0.0;
+    for (int j = 0; j < Np; ++j) v += c[k * Np + j] * phi[j];
+    U[k] = v;
+  }
+}
+
+/* Quadrature rules of one call, computed once.  Default sizes (reading, fixed
+ * by the configurations' "7-pt edge / 16-pt area" at p = 3): triangle edges
+ * 2p+1 Gauss points, triangle areas (p+1)^2; tetrahedron faces (p+2)^2,
+ * volumes (p+2)^3.  Face points are given in the face's own parameters:
+ * t in [0,1] along an edge, (sigma, tau) on a triangular face; face weights
+ * sum to 1. */
+typedef struct {
+  int dim, nv, nf;
+  double *vr, *vs, *vt, *vw;
+  double *fa, *fb, *fw;
+} orc_rules;
+
+static int default_face_n1(int dim, int p) { return dim == 2 ? 2 * p + 1 : p + 2; }
+static int default_vol_n1(int dim, int p) { return dim == 2 ? p + 1 : p + 2; }
+
+static void rules_free(orc_rules *R) {
+  free(R->vr);
+  free(R->vs);
+  free(R->vt);
+  free(R->vw);
+  free(R->fa);
+  free(R->fb);
+  free(R->fw);
+  memset(R, 0, sizeof *R);
+}
+
+static int rules_make(int dim, int nf1, int nv1, orc_rules *R) {
+  memset(R, 0, sizeof *R);
+  R->dim = dim;
+  if (nf1 < 1 || nf1 > 64 || nv1 < 1 || nv1 > 64) return fail("rules: size out of range");
+  R->nv = dim == 2 ? nv1 * nv1 : nv1 * nv1 * nv1;
+  R->vr = (double *)malloc(sizeof(double) * R->nv);
+  R->vs = (double *)malloc(sizeof(double) * R->nv);
+  R->vt = (double *)calloc(R->nv, sizeof(double));
+  R->vw = (double *)malloc(sizeof(double) * R->nv);
+  int rc = dim == 2 ? orc_tri_rule(nv1, R->vr, R->vs, R->vw)
+                    : orc_tet_rule(nv1, R->vr, R->vs, R->vt, R->vw);
+  if (rc) return rc;
+  R->nf = dim == 2 ? nf1 : nf1 * nf1;
+  R->fa = (double *)malloc(sizeof(double) * R->nf);
+  R->fb = (double *)calloc(R->nf, sizeof(double));
+  R->fw = (double *)malloc(sizeof(double) * R->nf);
+  if (dim == 2) {
+    double xg[64], wg[64];
+    if (orc_gauss_legendre(nf1, xg, wg)) return -1;
+    for (int i = 0; i < nf1; ++i) {
+      R->fa[i] = 0.5 * (1.0 + xg[i]);
+      R->fw[i] = 0.5 * wg[i];
+    }
+  } else {
+    if (orc_tri_rule(nf1, R->fa, R->fb, R->fw)) return -1;
+    for (int i = 0; i < R->nf; ++i) R->fw[i] *= 2.0;
+  }
+  return 0;
+}
+
+/* One face of element e, in physical space: its measure, its outward unit
+ * normal (pointing away from the opposite vertex) and its quadrature points. */
+typedef struct {
+  int nq;
+  double meas, n[3];
+  double *x; /* nq * 3 */
+  const double *w;
+} orc_face;
+
+static void face_geometry(const orc_mesh *m, int64_t e, int q, const orc_rules *R, orc_face *F) {
+  int dim = m->dim;
+  const double *X = m->X + e * m->nvpe * dim;
+  int fv[3];
+  face_verts(dim, q, fv);
+  const double *A = X + fv[0] * dim, *B = X + fv[1] * dim;
+  const double *O = dim == 2 ? X + ((q + 2) % 3) * dim : X + q * dim; /* opposite vertex */
+  double u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) u[a] = B[a] - A[a];
+  if (dim == 2) {
+    F->meas = sqrt(u[0] * u[0] + u[1] * u[1]);
+    F->n[0] = u[1] / F->meas;
+    F->n[1] = -u[0] / F->meas;
+    F->n[2] = 0.0;
+  } else {
+    const double *C = X + fv[2] * dim;
+    for (int a = 0; a < 3; ++a) v[a] = C[a] - A[a];
+    double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    double nn = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    F->meas = 0.5 * nn;
+    for (int a = 0; a < 3; ++a) F->n[a] = cr[a] / nn;
+  }
+  double side = 0.0;
+  for (int a = 0; a < dim; ++a) side += F->n[a] * (O[a] - A[a]);
+  if (side > 0.0)
+    for (int a = 0; a < dim; ++a) F->n[a] = -F->n[a];
+  F->nq = R->nf;
+  F->w = R->fw;
+  for (int i = 0; i < R->nf; ++i)
+    for (int a = 0; a < dim; ++a) F->x[i * 3 + a] = A[a] + R->fa[i] * u[a] + R->fb[i] * v[a];
+}
+
+/* rhs[e][k][j] = d c_{e,k,j} / dt for the listed elements (all when
+ * nelem < 0; then rhs is [E][M][Np], else [nelem][M][Np] in list order).
+ * c is [E][M][Np] in original element order.  kind 0 = Euler, 1 = linear
+ * advection with velocity adv.  nq_face1 / nq_vol1 override the 1-D point
+ * counts (0 = defaults).  Boundary faces use the transmissive state U+ = U-
+ * (reading; the configurations are periodic). */
+int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double *rhs,
+            const int64_t *elems, int64_t nelem, int nq_face1, int nq_vol1) {
+  orc_mesh *m = (orc_mesh *)h;
+  int dim = m->dim;
+  if (p < 0 || p > ORC_MAXP) return fail("rhs: p out of range");
+  int Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  orc_phys ph = {kind, dim, kind == ORC_EULER ? dim + 2 : 1, {0, 0, 0}};
+  if (adv)
+    for (int a = 0; a < dim; ++a) ph.adv[a] = adv[a];
+  int M = ph.M;
+  orc_rules R;
+  if (rules_make(dim, nq_face1 > 0 ? nq_face1 : default_face_n1(dim, p),
+                 nq_vol1 > 0 ? nq_vol1 : default_vol_n1(dim, p), &R)) {
+    rules_free(&R);
+    return -1;
+  }
+  orc_face F;
+  F.x = (double *)malloc(sizeof(double) * 3 * R.nf);
+  int64_t count = nelem < 0 ? m->ne : nelem;
+  for (int64_t ii = 0; ii < count; ++ii) {
+    int64_t e = nelem < 0 ? ii : elems[ii];
+    const double *ce = c + e * M * Np;
+    double *re = rhs + ii * M * Np;
+    for (int i = 0; i < M * Np; ++i) re[i] = 0.0;
+    const double *Ji = m->Jinv + e * dim * dim;
+    /* volume integral: sum_q w_q F(U_q) . (J^-T grad_ref phi_j) */
+    for (int q = 0; q < R.nv; ++q) {
+      double x[3] = {R.vr[q], R.vs[q], R.vt[q]};
+      double phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM];
+      basis_eval(dim, p, x, phi, d[0], d[1], d[2]);
+      for (int k = 0; k < M; ++k) {
+        double v = 0.0;
+        for (int j = 0; j < Np; ++j) v += ce[k * Np + j] * phi[j];
+        U[k] = v;
+      }
+      for (int a = 0; a < dim; ++a) {
+        double Fa[ORC_MAXM];
+        phys_flux_dir(&ph, U, a, Fa);
+        for (int j = 0; j < Np; ++j) {
+          double gx = 0.0; /* d phi_j / d x_a */
+          for (int r = 0; r < dim; ++r) gx += Ji[r * dim + a] * d[r][j];
+          for (int k = 0; k < M; ++k) re[k * Np + j] += R.vw[q] * Fa[k] * gx;
+        }
+      }
+    }
+    /* surface integrals: - (1/detJ) sum_faces |f| sum_q w_q phi_j(x_q) F*(U_e, U_nb, n) */
+    for (int f = 0; f < m->nfpe; ++f) {
+      face_geometry(m, e, f, &R, &F);
+      int32_t nb = m->enb[e * m->nfpe + f];
+      double scale = F.meas / m->detJ[e];
+      for (int q = 0; q < F.nq; ++q) {
+        double rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];
+        ref_coords(m, e, F.x + 3 * q, rs);
+        eval_state(dim, p, M, Np, ce, rs, Um);
+        if (nb >= 0) {
+          double rn[3];
+          ref_coords(m, nb, F.x + 3 * q, rn);
+          eval_state(dim, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
+        } else {
+          for (int k = 0; k < M; ++k) Up[k] = Um[k];
+        }
+        num_flux(&ph, Um, Up, F.n, Fs);
+        basis_eval(dim, p, rs, phi, NULL, NULL, NULL);
+        for (int j = 0; j < Np; ++j)
+          for (int k = 0; k < M; ++k) re[k * Np + j] -= scale * F.w[q] * phi[j] * Fs[k];
+      }
+    }
+  }
+  free(F.x);
+  rules_free(&R);
+  return 0;
+}
+
+/* ======================================================================= */
+/* Time step and SSP-RK3 (readings; the paper defers the solver to [giuliani]) */
+/* ======================================================================= */
+/* dt = cfl * min_i r_i / ((2p+1) lambda_i); r_i = dim |element| / |boundary|
+ * (the inradius), lambda_i = max over the element's volume points of |u|+c. */
+int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
+  orc_mesh *m = (orc_mesh *)h;
+  int dim = m->dim, M = dim + 2, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  orc_rules R;
+  if (rules_make(dim, 1, default_vol_n1(dim, p), &R)) {
+    rules_free(&R);
+    return -1;
+  }
+  orc_face F;
+  F.x = (double *)malloc(sizeof(double) * 3 * R.nf);
+  double best = INFINITY;
+  for (int64_t e = 0; e < m->ne; ++e) {
+    double lam = 0.0;
+    for (int q = 0; q < R.nv; ++q) {
+      double x[3] = {R.vr[q], R.vs[q], R.vt[q]}, U[ORC_MAXM];
+      eval_state(dim, p, M, Np, c + e * M * Np, x, U);
+      double rho = U[0], q2 = 0.0;
+      for (int a = 0; a < dim; ++a) q2 += (U[1 + a] / rho) * (U[1 + a] / rho);
+      double pr = (ORC_GAMMA - 1.0) * (U[dim + 1] - 0.5 * rho * q2);
+      double l = sqrt(q2) + sqrt(ORC_GAMMA * pr / rho);
+      if (l > lam) lam = l;
+    }
+    double bnd = 0.0;
+    for (int f = 0; f < m->nfpe; ++f) {
+      face_geometry(m, e, f, &R, &F);
+      bnd += F.meas;
+    }
+    double vol = m->detJ[e] / (dim == 2 ? 2.0 : 6.0);
+    double r = dim * vol / bnd;
+    double v = r / ((2 * p + 1) * lam);
+    if (v < best) best = v;
+  }
+  free(F.x);
+  rules_free(&R);
+  *dt_out = cfl * best;
+  return 0;
+}
+
+/* One SSP-RK3 (Shu-Osher) step of the Euler system, in place:
+ *   u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+ *   u  = 1/3 u + 2/3 (u2 + dt L(u2)).
+ * dt comes from the state at the start of the step, or is dt_in when > 0. */
+int orc_rk_step(void *h, int p, double *c, double cfl, double dt_in, double *dt_out) {
+  orc_mesh *m = (orc_mesh *)h;
+  int dim = m->dim, M = dim + 2, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  int64_t n = m->ne * M * Np;
+  double dt = dt_in;
+  if (!(dt > 0.0) && orc_dt(h, p, c, cfl, &dt)) return -1;
+  double *u1 = (double *)malloc(sizeof(double) * n), *u2 = (double *)malloc(sizeof(double) * n);
+  double *L = (double *)malloc(sizeof(double) * n);
+  int rc = orc_rhs(h, p, ORC_EULER, NULL, c, L, NULL, -1, 0, 0);
+  for (int64_t i = 0; i < n && !rc; ++i) u1[i] = c[i] + dt * L[i];
+  if (!rc) rc = orc_rhs(h, p, ORC_EULER, NULL, u1, L, NULL, -1, 0, 0);
+  for (int64_t i = 0; i < n && !rc; ++i) u2[i] = 0.75 * c[i] + 0.25 * (u1[i] + dt * L[i]);
+  if (!rc) rc = orc_rhs(h, p, ORC_EULER, NULL, u2, L, NULL, -1, 0, 0);
+  for (int64_t i = 0; i < n && !rc; ++i) c[i] = c[i] / 3.0 + 2.0 / 3.0 * (u2[i] + dt * L[i]);
+  free(u1);
+  free(u2);
+  free(L);
+  if (dt_out) *dt_out = dt;
+  return rc;
+}
+
+/* ======================================================================= */
+/* Initial conditions: L2 projection onto the orthonormal basis             */
+/* ======================================================================= */
+int orc_num_vol_points(int dim, int p) {
+  int n1 = default_vol_n1(dim, p);
+  return dim == 2 ? n1 * n1 : n1 * n1 * n1;
+}
+
+/* physical coordinates (unwrapped per element) of the volume points of a
+ * rule with n1 points per direction (0 = default), [E][Nq][dim]; optional
+ * physical weights [E][Nq] and DG solution values U [E][Nq][M] of c. */
+int orc_eval_points(void *h, int p, int M, const double *c, int n1, double *xyz, double *w,
+                    double *U) {
+  orc_mesh *m = (orc_mesh *)h;
+  int dim = m->dim, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  orc_rules R;
+  if (rules_make(dim, 1, n1 > 0 ? n1 : default_vol_n1(dim, p), &R)) {
+    rules_free(&R);
+    return -1;
+  }
+  for (int64_t e = 0; e < m->ne; ++e) {
+    const double *X = m->X + e * m->nvpe * dim;
+    for (int q = 0; q < R.nv; ++q) {
+      double rs[3] = {R.vr[q], R.vs[q], R.vt[q]};
+      for (int a = 0; a < dim; ++a) {
+        double v = X[a];
+        for (int k = 0; k < dim; ++k) v += (X[(k + 1) * dim + a] - X[a]) * rs[k];
+        if (xyz) xyz[(e * R.nv + q) * dim + a] = v;
+      }
+      if (w) w[e * R.nv + q] = R.vw[q] * m->detJ[e];
+      if (U) eval_state(dim, p, M, Np, c + e * M * Np, rs, U + (e * R.nv + q) * M);
+    }
+  }
+  int nq = R.nv;
+  rules_free(&R);
+  return nq;
+}
+
+/* L2 projection: with a basis orthonormal on the reference element the
+ * coefficients are c[e][k][j] = sum_q w_q U_k(x_q) phi_j(x_q) over the
+ * default volume rule; vals is [E][Nq][M] at the points of orc_eval_points. */
+int orc_project(void *h, int p, int M, const double *vals, double *c) {
+  orc_mesh *m = (orc_mesh *)h;
+  int dim = m->dim, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  orc_rules R;
+  if (rules_make(dim, 1, default_vol_n1(dim, p), &R)) {
+    rules_free(&R);
+    return -1;
+  }
+  for (int64_t e = 0; e < m->ne; ++e) {
+    double *ce = c + e * M * Np;
+    for (int i = 0; i < M * Np; ++i) ce[i] = 0.0;
+    for (int q = 0; q < R.nv; ++q) {
+      double x[3] = {R.vr[q], R.vs[q], R.vt[q]}, phi[ORC_MAXNP];
+      basis_eval(dim, p, x, phi, NULL, NULL, NULL);
+      for (int k = 0; k < M; ++k)
+        for (int j = 0; j < Np; ++j) ce[k * Np + j] += R.vw[q] * vals[(e * R.nv + q) * M + k] * phi[j];
+    }
+  }
+  rules_free(&R);
+  return 0;
+}

@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs shared by the library's callers, the tests and the bench.
+
+This module only *generates inputs*: mesh vertex/element lists, random modal
+coefficient arrays and the point values of the isentropic-vortex field.  It
+contains none of the DG method's arithmetic (no basis, quadrature, geometry,
+flux, coloring or time stepping), so the CUDA path and the CPU oracle can both
+draw their inputs from here without sharing any of the computation they are
+checked on.
+
+The paper's meshes (rectangles A-E, NACA-0012, spherical shells, Table 1-3) are
+not available; the generators below build meshes of the same kind and scale:
+
+* ``periodic_square_tri``: an ``n x n`` periodic unit square, every grid square
+  split into two triangles, optionally with every vertex jittered uniformly by
+  up to ``jitter * h`` in x and y.  Periodic meshes have no boundary, so every
+  element has exactly one edge of each color, as for the closed spherical
+  meshes of Table 1.
+* ``open_square_tri``: the same split on a non-periodic square (boundary edges).
+* ``periodic_cube_tet``: an ``n^3`` periodic unit cube, each cube split into six
+  tetrahedra along its main diagonal (Kuhn/Freudenthal split).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+@dataclass
+class MeshInput:
+    """Vertex and element lists in the layout ``dgc_mesh_create`` takes."""
+
+    dim: int
+    xyz: np.ndarray  # (nv, dim) float64
+    ev: np.ndarray  # (ne, dim+1) int32, CCW triangles / positive-volume tets
+    periodic_len: np.ndarray | None  # (dim,) float64 or None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def ne(self) -> int:
+        return int(self.ev.shape[0])
+
+    @property
+    def nv(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def periodic_square_tri(n: int, jitter: float = 0.0, seed: int | None = None) -> MeshInput:
+    """``n x n`` periodic unit square, each square split into two CCW triangles.
+
+    Vertex (i, j) has id ``j*n + i`` and sits at ``(i/n, j/n)`` (plus jitter);
+    vertex ids wrap, so periodic edges are shared by vertex id.  Square (i, j),
+    numbered j-major, becomes [(i,j), (i+1,j), (i+1,j+1)] and
+    [(i,j), (i+1,j+1), (i,j+1)].  ``n >= 3`` keeps every edge key unique.
+    """
+    if n < 3:
+        raise ValueError("periodic meshes need n >= 3")
+    h = 1.0 / n
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    xyz = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        xyz += rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+
+    def vid(i, j):
+        return (j % n) * n + (i % n)
+
+    i = ii.ravel()
+    j = jj.ravel()
+    a = vid(i, j)
+    b = vid(i + 1, j)
+    c = vid(i + 1, j + 1)
+    d = vid(i, j + 1)
+    ev = np.empty((2 * n * n, 3), dtype=np.int32)
+    ev[0::2] = np.stack([a, b, c], axis=1)
+    ev[1::2] = np.stack([a, c, d], axis=1)
+    return MeshInput(2, xyz, ev, np.array([1.0, 1.0]), name=f"periodic_square_tri_{n}x{n}",
+                     meta={"n": n, "jitter": jitter, "seed": seed})
+
+
+def open_square_tri(n: int, jitter: float = 0.0, seed: int | None = None) -> MeshInput:
+    """Non-periodic ``n x n`` unit square split like ``periodic_square_tri``.
+
+    It has ``(n+1)^2`` vertices and ``4n`` boundary edges.  Only interior
+    vertices are jittered.
+    """
+    h = 1.0 / n
+    ii, jj = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
+    xyz = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+        interior = ((ii.ravel() > 0) & (ii.ravel() < n) & (jj.ravel() > 0) & (jj.ravel() < n))
+        xyz[interior] += d[interior]
+    ci, cj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    i = ci.ravel()
+    j = cj.ravel()
+
+    def vid(i, j):
+        return j * (n + 1) + i
+
+    a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+    ev = np.empty((2 * n * n, 3), dtype=np.int32)
+    ev[0::2] = np.stack([a, b, c], axis=1)
+    ev[1::2] = np.stack([a, c, d], axis=1)
+    return MeshInput(2, xyz, ev, None, name=f"open_square_tri_{n}x{n}", meta={"n": n})
+
+
+# The six tetrahedra of the Kuhn split of the unit cube: the path 000 -> 111
+# visits the axes in the order of each permutation.
+_KUHN_PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def periodic_cube_tet(n: int) -> MeshInput:
+    """``n^3`` periodic unit cube, each cube split into six Kuhn tetrahedra.
+
+    Vertex (i, j, k) has id ``(k*n + j)*n + i``.  Each tetrahedron is the
+    monotone path 000 -> 111 along one permutation of the axes; vertices are
+    ordered so that the volume is positive.
+    """
+    if n < 3:
+        raise ValueError("periodic meshes need n >= 3")
+    h = 1.0 / n
+    g = np.arange(n)
+    kk, jj, ii = np.meshgrid(g, g, g, indexing="ij")
+    xyz = np.stack([ii.ravel() * h, jj.ravel() * h, kk.ravel() * h], axis=1).astype(np.float64)
+    cells = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)  # cube-major (k, j, i)
+
+    def vid(p):
+        return ((p[:, 2] % n) * n + (p[:, 1] % n)) * n + (p[:, 0] % n)
+
+    tets = []
+    for perm in _KUHN_PERMS:
+        p0 = cells.copy()
+        p1 = p0.copy()
+        p1[:, perm[0]] += 1
+        p2 = p1.copy()
+        p2[:, perm[1]] += 1
+        p3 = p2.copy()
+        p3[:, perm[2]] += 1
+        verts = [vid(p0), vid(p1), vid(p2), vid(p3)]
+        # orientation: the sign of the permutation decides the volume sign
+        e1 = np.eye(3)[perm[0]]
+        e2 = e1 + np.eye(3)[perm[1]]
+        e3 = np.ones(3)
+        vol = np.linalg.det(np.stack([e1, e2, e3]))
+        if vol < 0:
+            verts[1], verts[2] = verts[2], verts[1]
+        tets.append(np.stack(verts, axis=1))
+    ev = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return MeshInput(3, xyz, ev, np.array([1.0, 1.0, 1.0]), name=f"periodic_cube_tet_{n}^3x6",
+                     meta={"n": n})
+
+
+def random_state(ne: int, m: int, np_: int, seed: int, amp: float = 3e-3,
+                 mean=(0.7, 0.1, -0.05, 1.8), spread: float = 0.05) -> np.ndarray:
+    """Random modal coefficients ``c[e][m][j]`` (float64), with a positive mean mode.
+
+    Mode 0 of each component is ``mean[m]`` plus a uniform spread; the higher
+    modes are uniform in ``(-amp, amp)``.  With the defaults the state stays
+    well inside the physical region (positive density and pressure).
+    """
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-amp, amp, size=(ne, m, np_))
+    mean = np.asarray(mean, dtype=np.float64)
+    if mean.size != m:
+        mean = np.resize(mean, m)
+    c[:, :, 0] = mean[None, :] * (1.0 + rng.uniform(-spread, spread, size=(ne, m)))
+    return np.ascontiguousarray(c)
+
+
+def uniform_perturbation(shape, seed: int, amp: float = 1e-3) -> np.ndarray:
+    """Uniform ``(-amp, amp)`` perturbation added to projected coefficients."""
+    return np.random.default_rng(seed).uniform(-amp, amp, size=shape)
+
+
+def vortex_field(x: np.ndarray, y: np.ndarray, t: float = 0.0, beta: float = 5.0,
+                 xc: float = 0.5, yc: float = 0.5, uinf: float = 1.0, vinf: float = 1.0,
+                 radius: float = 0.1, period: float = 1.0, gamma: float = GAMMA) -> np.ndarray:
+    """Conserved variables of the isentropic vortex at points (x, y), time t.
+
+    The classic vortex on ``[-5, 5]^2`` is scaled by ``radius`` onto the
+    periodic unit square and advected with ``(uinf, vinf)``; the distance to the
+    centre is taken on the nearest periodic image.  Returns an array of shape
+    ``x.shape + (4,)`` holding ``(rho, rho u, rho v, E)``.
+    """
+    dx = x - xc - uinf * t
+    dy = y - yc - vinf * t
+    dx = dx - period * np.round(dx / period)
+    dy = dy - period * np.round(dy / period)
+    xt = dx / radius
+    yt = dy / radius
+    f = np.exp(0.5 * (1.0 - xt * xt - yt * yt))
+    rho = (1.0 - (gamma - 1.0) * beta * beta / (8.0 * gamma * math.pi ** 2) * f * f) ** (1.0 / (gamma - 1.0))
+    u = uinf - beta / (2.0 * math.pi) * yt * f
+    v = vinf + beta / (2.0 * math.pi) * xt * f
+    p = rho ** gamma
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E], axis=-1)
+
+
+def vortex_tube_field(x, y, z, t: float = 0.0, **kw) -> np.ndarray:
+    """3D isentropic vortex tube: the 2D vortex in (x, y), w = 0, constant in z.
+
+    Returns ``(rho, rho u, rho v, rho w, E)`` of shape ``x.shape + (5,)``.
+    """
+    q = vortex_field(x, y, t, **kw)
+    out = np.zeros(q.shape[:-1] + (5,), dtype=np.float64)
+    out[..., 0:3] = q[..., 0:3]
+    out[..., 4] = q[..., 3]
+    return out
+
+
+# --- Named workloads (sizes as stated) -------------------------------------------------
+
+def square_vortex_p1_32x32() -> dict:
+    """2048-triangle periodic square, p=1, vortex beta=5 at the centre, CFL 0.3, 100 RK3 steps."""
+    return dict(mesh=periodic_square_tri(32), p=1, beta=5.0, xc=0.5, yc=0.5, cfl=0.3, steps=100)
+
+
+def jittered_square_vortex_p3_724x724(n: int = 724) -> dict:
+    """1,048,352-triangle periodic square (724x724, nodes jittered +-0.2h, seed 1601), p=3.
+
+    Initial state: vortex beta=5 at the centre, projected, plus a uniform
+    (-1e-3, 1e-3) perturbation of every coefficient (seed 7613).
+    """
+    return dict(mesh=periodic_square_tri(n, jitter=0.2, seed=1601), p=3, beta=5.0, xc=0.5,
+                yc=0.5, perturb=1e-3, perturb_seed=7613, cfl=0.3)
+
+
+def cube_tube_p2_64(n: int = 64) -> dict:
+    """64^3 periodic cube x 6 Kuhn tets = 1,572,864 tets, p=2, vortex tube."""
+    return dict(mesh=periodic_cube_tet(n), p=2, beta=5.0, xc=0.5, yc=0.5, cfl=0.3)
+
+
+def batched_square_meshes(count: int = 64, seed: int = 5, e_min: float = 1e3,
+                          e_max: float = 2e5) -> list[dict]:
+    """Independent periodic square meshes of uneven size and order.
+
+    Element counts are log-uniform on [e_min, e_max] (grid ``n = round(sqrt(E/2))``),
+    p uniform in {1, 2, 3}, vortex strength in U[3, 6], centre in U[0.3, 0.7]^2.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        e = math.exp(rng.uniform(math.log(e_min), math.log(e_max)))
+        n = max(3, int(round(math.sqrt(e / 2.0))))
+        p = int(rng.integers(1, 4))
+        beta = float(rng.uniform(3.0, 6.0))
+        xc, yc = (float(v) for v in rng.uniform(0.3, 0.7, size=2))
+        out.append(dict(n=n, p=p, beta=beta, xc=xc, yc=yc))
+    return out
