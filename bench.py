@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark: DOF-RHS updates/s of the colored DG right-hand side on GB300.
+
+One step = one SSP-RK3 step (CFL reduction + three right-hand sides with their
+stage updates) of the 2D Euler modal DG scheme, p = 3, on the periodic
+724x724 jittered square split into 1,048,352 triangles (41,934,080 scalar
+DOFs), state = isentropic vortex + 1e-3 uniform perturbation.  The headline
+path computes flux, quadrature and projection in FP32 and keeps the state and
+stage update in FP64; FP64, the atomicAdd-scatter and the per-edge-buffer
+comparators are timed beside it on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgc|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(weak scaling, no collective on the data path); the reported time is the
+maximum over ranks.  ``--impl reference`` times the CPU oracle on the host
+cores instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1601_07613_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DOF-RHS updates/s, FP64 colored vs FP32-mixed/batched; % of HBM roofline"
+UNIT = "DOF-RHS updates/s"
+WORKLOAD = "2D Euler DG p=3 on 1,048,352 jittered periodic triangles (724x724), vortex + 1e-3 perturbation"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 peak derived from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM
+# (2 DFMA/clk/SM, the GB300's FP64 rate) x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, mixed: bool, stage_frac_u0: float) -> float:
+    """Algorithmic DRAM bytes of one launch of a kernel class (each element touched
+    once per color on a closed conforming mesh)."""
+    s_in = (4 if mixed else 8) * NV      # state read for traces
+    s_rhs = (4 if mixed else 8) * NV     # rhs element block
+    edge = 16 + 16 * (2 if dim == 2 else 3)
+    if cls == "first":
+        return E * (s_in + 8 * dim * dim + s_rhs) + nedges * edge
+    if cls == "color":
+        return E * (s_in + 2 * s_rhs) + nedges * edge
+    if cls == "last":
+        return E * (8 * NV + s_rhs + 8 * NV * stage_frac_u0 + 8 * NV + (4 * NV if mixed else 0)) + nedges * edge
+    if cls == "cfl":
+        return E * (8 * NV + 8 + (4 * NV if mixed else 0))
+    if cls == "volume":
+        return E * (s_in + 8 * dim * dim + s_rhs)
+    if cls == "stage":
+        return E * (8 * NV * 2 + s_rhs + 8 * NV + (4 * NV if mixed else 0))
+    return float("nan")
+
+
+def flops_per_rhs(E, NV, nqv, nqe, nfaces=3):
+    """FP arithmetic of one right-hand side (FMA = 2): per element the volume
+    term (trace 2 NV, projection 4 NV, flux ~40 per point) and its share of
+    the surface terms (trace + projection 4 NV, flux ~70 per point and side)."""
+    return E * (nqv * (6 * NV + 40) + nfaces * nqe * (4 * NV + 70))
+
+
+def setup_workload(dgc, torch, dev, n: int = 724):
+    cfg = W.jittered_square_vortex_p3_724x724(n)
+    mi, p = cfg["mesh"], cfg["p"]
+    t0 = time.time()
+    mesh = dgc.Mesh.from_input(mi, p)
+    t1 = time.time()
+    ncol, per = mesh.color(1601)
+    t2 = time.time()
+    xyz = dgc.dgc_vol_points(mesh.h)
+    vals = W.vortex_field(xyz[..., 0], xyz[..., 1], beta=cfg["beta"], xc=cfg["xc"], yc=cfg["yc"])
+    c = dgc.dgc_project(mesh.h, vals)
+    c += W.uniform_perturbation(c.shape, cfg["perturb_seed"], cfg["perturb"])
+    del xyz, vals
+    prep = {"mesh_s": round(t1 - t0, 3), "color_reorder_s": round(t2 - t1, 3), "colors": ncol,
+            "edges_per_color": per}
+    return cfg, mi, mesh, c, prep
+
+
+def time_steps(torch, fn, steps, stream):
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(steps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def run_dgc(args, rank, world, local_rank):
+    import torch
+
+    from paper_1601_07613_gb300 import dgc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dgc.lib()
+    cfg, mi, mesh, c_host, prep = setup_workload(dgc, torch, dev, args.n)
+    info = mesh.info
+    E, NV, p = info["ne"], info["M"] * info["np"], info["p"]
+    dofs = E * NV
+    stream = torch.cuda.current_stream()
+    c = torch.empty(mesh.state_shape(), dtype=torch.float64, device=dev)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    mixed, fp64 = dgc.DGC_FP32_MIXED, dgc.DGC_FP64
+    ws = torch.empty(dgc.dgc_workspace_size(mesh.h, fp64) // 8 + 64, dtype=torch.float64, device=dev)
+    dgc.dgc_import_state(mesh.h, c_host, c)
+
+    def step(prec):
+        dgc.dgc_rk_step(mesh.h, prec, c, cfg["cfl"], dt, ws)
+
+    # ---- headline: FP32-mixed RK step -------------------------------------------------
+    for _ in range(args.warmup):
+        step(mixed)
+    launches_per_step = dgc.dgc_last_launch_count(mesh.h)
+    dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_PROFILE, 1)
+    dgc.dgc_profile_collect(mesh.h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local_rank)
+    ms = time_steps(torch, lambda: step(mixed), args.steps, stream)
+    clocks = clk.stop()
+    prof = dgc.dgc_profile_collect(mesh.h)
+    dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_PROFILE, 0)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 3 * dofs / (ms * 1e-3)
+
+    hbm, hbm_kind = peaks()
+    ncolors = info["ncolors"]
+    per_color = prep["edges_per_color"]
+    kernels = {}
+    for cls, (tms, n) in prof.items():
+        if cls == "first":
+            ne_ = per_color[0]
+        elif cls == "last":
+            ne_ = per_color[-1]
+        elif cls == "color":
+            ne_ = sum(per_color[1:-1]) / max(1, ncolors - 2)
+        else:
+            ne_ = 0
+        b = class_bytes(cls, E, ne_, NV, 2, True, 2.0 / 3.0)
+        avg = tms / n
+        kernels[cls] = {"launches": n, "avg_ms": round(avg, 5), "share": round(tms / (ms * args.steps), 4),
+                        "alg_bytes": int(b), "alg_gbs": round(b / (avg * 1e-3) / 1e9, 1),
+                        "frac_hbm": round(b / (avg * 1e-3) / 1e9 / hbm, 3)}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+    step_bytes = sum(kernels[k]["alg_bytes"] * kernels[k]["launches"] for k in kernels) / args.steps
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["alg_gbs"], "peak": hbm,
+                "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": None,
+                "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
+                "step_alg_gbs": round(step_bytes / (ms * 1e-3) / 1e9, 1),
+                "step_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm, 3)}
+
+    variants = {}
+    if not args.no_variants:
+        # ---- FP64 colored RK step (FP64-ALU bound on this GPU) ------------------------
+        dgc.dgc_import_state(mesh.h, c_host, c)
+        step(fp64)
+        k64 = max(3, args.steps // 5)
+        ms64 = time_steps(torch, lambda: step(fp64), k64, stream)
+        fl = 3 * flops_per_rhs(E, NV, info["nqv"], info["nqf"])
+        variants["rk_fp64"] = {"value": 3 * dofs / (ms64 * 1e-3), "ms_per_step": round(ms64, 4),
+                               "roofline": {"bound": "alu", "achieved": round(fl / (ms64 * 1e-3) / 1e12, 3),
+                                            "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
+                                            "frac": round(fl / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)}}
+        # ---- right-hand side alone: colored vs atomicAdd vs two-pass buffer ----------
+        r = torch.empty_like(c)
+        nbuf = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
+        buf = torch.empty(nbuf // 8, dtype=torch.float64, device=dev)
+        dgc.dgc_import_state(mesh.h, c_host, c)
+        reps = max(5, args.steps)
+        for prec, tag in ((mixed, "fp32mixed"), (fp64, "fp64")):
+            rr = reps if prec == mixed else max(3, reps // 5)
+            calls = {
+                "colored": lambda: dgc.dgc_rhs(mesh.h, prec, c, r),
+                "atomic": lambda: dgc.dgc_rhs_atomic(mesh.h, prec, c, r),
+                "two_pass": lambda: dgc.dgc_rhs_two_pass(mesh.h, prec, c, r, buf),
+            }
+            for name, fn in calls.items():
+                fn()
+                t_ = time_steps(torch, fn, rr, stream)
+                variants[f"rhs_{name}_{tag}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+            dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_FUSE, 0)
+            fn = calls["colored"]
+            fn()
+            t_ = time_steps(torch, fn, rr, stream)
+            variants[f"rhs_colored_unfused_{tag}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+            dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_FUSE, 1)
+        variants["two_pass_buffer_bytes"] = nbuf
+        del buf, r
+
+    # ---- end to end through the C ABI with host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        host_in = np.ascontiguousarray(c_host)
+        host_out = np.empty_like(host_in)
+        ke = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            dgc.dgc_import_state(mesh.h, host_in, c)
+            step(mixed)
+            dgc.dgc_export_state(mesh.h, c, host_out)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        e2e = {"value": 3 * dofs / te, "unit": UNIT, "h2d_bytes_per_step": int(host_in.nbytes),
+               "d2h_bytes_per_step": int(host_out.nbytes), "ms_per_step": round(te * 1e3, 2)}
+
+    workload = WORKLOAD if args.n == 724 else f"2D Euler DG p=3 on {E} jittered periodic triangles ({args.n}x{args.n})"
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (flux/quadrature/projection; f64 state, stage update, CFL)",
+        "data": "synthetic",
+        "config": {"workload": workload, "elements": E, "edges": info["ns"], "p": p, "Np": info["np"],
+                   "M": info["M"], "edge_points": info["nqf"], "area_points": info["nqv"],
+                   "dofs": dofs, "step": "SSP-RK3 (3 RHS) with FP64 CFL reduction",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "no flush: state 335 MB FP64 + 168 MB FP32 copy per replica exceed the 129 MB L2",
+                   "host_prep": prep},
+        "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks, "e2e": e2e, "variants": variants,
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(mi, p, c_host, dofs)
+    mesh.close()
+    return out
+
+
+def cpu_baseline(mi, p, c_host, dofs, elements=None):
+    """The CPU oracle as it stands (single-threaded C, FP64), one right-hand side
+    of the same workload (all elements unless a count is given)."""
+    import oracle
+
+    om = oracle.OracleMesh.from_input(mi)
+    E = mi.ne
+    if elements is None or elements >= E:
+        t0 = time.perf_counter()
+        om.rhs(p, c_host)
+        t = time.perf_counter() - t0
+        n = E
+    else:
+        sel = np.random.default_rng(0).choice(E, elements, replace=False)
+        t0 = time.perf_counter()
+        om.rhs(p, c_host, elems=sel)
+        t = time.perf_counter() - t0
+        n = elements
+    nv = c_host.shape[1] * c_host.shape[2]
+    return {"value": n * nv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 right-hand side of {n} of {E} elements, {t:.1f} s, single thread"}
+
+
+def run_reference(args):
+    """The CPU oracle on the host cores: each step is one right-hand side of a
+    bounded random sample of the workload's elements."""
+    import oracle
+
+    cfg = W.jittered_square_vortex_p3_724x724()
+    mi, p = cfg["mesh"], cfg["p"]
+    om = oracle.OracleMesh.from_input(mi)
+    xyz, _, _ = om.eval_points(p)
+    c = om.project(p, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=cfg["beta"]))
+    c += W.uniform_perturbation(c.shape, cfg["perturb_seed"], cfg["perturb"])
+    del xyz
+    E = mi.ne
+    NV = c.shape[1] * c.shape[2]
+    per_step = args.ref_elements
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        om.rhs(p, c, elems=rng.choice(E, per_step, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        om.rhs(p, c, elems=rng.choice(E, per_step, replace=False))
+    t = (time.perf_counter() - t0) / args.steps
+    value = per_step * NV / t
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload, "elements": E, "p": p,
+                   "step": f"one oracle right-hand side of {per_step} random elements"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"{per_step} random elements per step, single-threaded FP64 C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["dgc", "reference"], default="dgc")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP64 and comparator timings")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) timing")
+    ap.add_argument("--ref-elements", type=int, default=40000, help="oracle elements per reference step")
+    ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
+                    "724 is the benchmark workload, smaller n is for profiler captures")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_dgc(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

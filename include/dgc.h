@@ -1,0 +1,214 @@
+/*
+ * dgc.h -- C ABI of the colored, race-free DG right-hand-side library for GB300.
+ *
+ * The library evaluates the right-hand side of the modal discontinuous Galerkin
+ * discretisation of the Euler equations (Eq. 2 of Giuliani & Krivodonova, "Edge
+ * coloring in unstructured CFD codes") on unstructured triangle and tetrahedral
+ * meshes.  The surface integral is evaluated color by color (Algorithm 1): the
+ * edges (faces) are colored so that no element has two edges of one color
+ * (Sec. 3.1), so all edges of one color scatter their flux projection into both
+ * neighbours with plain stores, no atomics and no per-edge buffer.  Elements and
+ * edges are renumbered color-major (Sec. 5, Tables 5 and 6).
+ *
+ * Conventions
+ *   - Every call returns a dgc_status; no exception crosses the ABI.  On error
+ *     dgc_last_error() returns a thread-local message.  Arguments are validated
+ *     before any device work is enqueued.
+ *   - Host arrays are plain C arrays in the caller's (original) element and
+ *     vertex order.  Device arrays are raw device pointers (e.g. torch tensor
+ *     data pointers) in the library's internal (renumbered) element order and
+ *     are owned by the caller.  The mesh object owns its host data and the
+ *     device copies of connectivity, geometry and basis tables.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work is enqueued on it; calls that take device pointers do not
+ *     synchronise the host, except the first device call on a mesh, which
+ *     uploads the mesh synchronously (make it before any stream capture).
+ *   - A state vector c holds, per element e, the modal coefficients
+ *     c[e][m][j] for equation m (M = 4 in 2D, 5 in 3D) and mode j (Np modes),
+ *     FP64, contiguous ([E][M][Np]).  Coefficients refer to the basis that is
+ *     orthonormal on the reference element (mass matrix = detJ I).
+ */
+#ifndef DGC_H
+#define DGC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgc_mesh dgc_mesh;
+typedef struct dgc_batch dgc_batch;
+
+typedef enum {
+  DGC_OK = 0,
+  DGC_ERR_ARG = 1,            /* bad argument, or call out of order */
+  DGC_ERR_MESH = 2,           /* non-manifold face, non-positive Jacobian, bad ids */
+  DGC_ERR_COLORING_LIMIT = 3, /* conflict resolution exceeded max_swaps (Sec. 3.1 has
+                                 no termination proof); retry with another seed */
+  DGC_ERR_UNSUPPORTED = 4,    /* element type / order / option not built */
+  DGC_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+  DGC_ERR_OOM = 6,            /* host or device allocation failed */
+  DGC_ERR_NONFINITE = 7       /* non-finite or non-physical state detected */
+} dgc_status;
+
+typedef enum {
+  DGC_FP64 = 0,       /* all arithmetic in FP64 */
+  DGC_FP32_MIXED = 1  /* flux, quadrature and projection in FP32; state, stage update,
+                         geometry and CFL reduction in FP64 */
+} dgc_prec;
+
+/* Options (dgc_set_option). */
+typedef enum {
+  DGC_OPT_FUSE = 0,            /* 1 (default): the first color also computes the volume
+                                  integral, the last color applies the RK stage update
+                                  (closed conforming meshes only); 0: separate volume
+                                  kernel, every color read-modify-writes rhs (Alg. 1) */
+  DGC_OPT_EDGES_PER_BLOCK = 1, /* surface-kernel tile: edges per thread block (16..512) */
+  DGC_OPT_THREADS_PER_EDGE = 2, /* 2 (one thread per edge side); reserved for tuning */
+  DGC_OPT_PROFILE = 3           /* 1: record a CUDA event pair around every kernel launch, on
+                                   the launch stream, for dgc_profile_collect; 0 (default): off */
+} dgc_option;
+
+/* Kernel classes reported by dgc_profile_collect. */
+typedef enum {
+  DGC_K_CFL = 0,      /* CFL reduction (and FP32 copy of the state, mixed precision) */
+  DGC_K_VOLUME = 1,   /* volume integral alone (unfused path) */
+  DGC_K_FIRST = 2,    /* first color fused with the volume integral */
+  DGC_K_COLOR = 3,    /* a color that read-modify-writes rhs */
+  DGC_K_LAST = 4,     /* last color fused with the RK stage update */
+  DGC_K_STAGE = 5,    /* RK stage update alone (unfused path) */
+  DGC_K_ATOMIC = 6,   /* all edges with atomicAdd (comparator) */
+  DGC_K_BUFFER = 7,   /* all edges into the per-edge buffer (comparator) */
+  DGC_K_GATHER = 8,   /* per-element gather of the buffer (comparator) */
+  DGC_K_NCLASSES = 16
+} dgc_kernel_class;
+
+/* Mesh ingest (Sec. 2 connectivity graph; Sec. 5 edge table).
+ * dim = 2 (triangles, CCW vertex order) or 3 (tetrahedra, positive volume).
+ * p = polynomial order (triangles 0..3, tetrahedra 1..2 in this build).
+ * xyz: nv*dim FP64 vertex coordinates, row-major.  ev: ne*(dim+1) int32 vertex ids.
+ * periodic_len: NULL, or dim period lengths; periodic meshes identify faces across
+ * the period by shared vertex ids and unwrap each element to lie within half a period
+ * of its vertex 0.  Edges are numbered in order of first appearance when the elements
+ * and their local faces are scanned (local edge q of a triangle is (v_q, v_{q+1});
+ * local face q of a tetrahedron is opposite vertex q); an edge's left element is the
+ * first to list it, its right the second (-1 on a boundary).
+ * Errors: DGC_ERR_ARG (sizes, pointers), DGC_ERR_MESH (face shared by more than two
+ * elements, non-positive Jacobian, vertex id out of range), DGC_ERR_UNSUPPORTED. */
+dgc_status dgc_mesh_create(int dim, int p, int64_t nv, const double* xyz, int64_t ne,
+                           const int32_t* ev, const double* periodic_len, dgc_mesh** out);
+
+/* Edge (face) coloring of Sec. 3.1 -- modified greedy pass with random nonconflicting
+ * colors from C = {1..F} (F = 3 triangles, 4 tetrahedra), then conflict resolution by
+ * swaps that do not raise the conflict count, with loop breaking -- followed by the
+ * reordering of Sec. 5: edges color-major, the k-th color-1 edge's left/right elements
+ * renumbered k and N1+k, colors >= 2 sorted by ascending left element.
+ * seed: RNG seed (xorshift64; 0 selects a fixed default).  max_swaps <= 0 selects
+ * 1000 * number of edges.  n_colors (out, may be NULL): colors used.  per_color (out,
+ * may be NULL, length >= 8): edges per color.  Colors and ordering are bit-identical
+ * across runs for a given seed.  Errors: DGC_ERR_COLORING_LIMIT (mesh left uncolored),
+ * DGC_ERR_ARG.  Host only; device data is (re)uploaded at the next device call. */
+dgc_status dgc_color_edges(dgc_mesh* mesh, uint64_t seed, int64_t max_swaps,
+                           int32_t* n_colors, int64_t* per_color);
+
+/* Naive greedy coloring of Sec. 1 (first available color; up to 5 colors on triangles,
+ * 7 on tetrahedra), for the color-count ablation of Table 7.  renumber / reorder select
+ * the Sec. 5 element renumbering and left-ascending edge order (0 = original order
+ * within each color).  Same outputs as dgc_color_edges. */
+dgc_status dgc_color_edges_naive(dgc_mesh* mesh, int renumber, int reorder,
+                                 int32_t* n_colors, int64_t* per_color);
+
+/* Sizes: info[0] = E, [1] = edges, [2] = Np, [3] = M, [4] = edge (face) quadrature
+ * points, [5] = volume quadrature points, [6] = colors (0 before coloring),
+ * [7] = dim, [8] = p, [9] = 1 if every element has exactly one edge of each color. */
+dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t info[10]);
+
+/* Edge table in original order: left, right (-1 boundary), local face index in left
+ * and right (-1 boundary).  Each array has one entry per edge. */
+dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, int8_t* qleft,
+                         int8_t* qright);
+
+/* The ordering chosen by the last coloring call: new element id of each original element,
+ * new edge id of each original edge, color (1..C) of each original edge, and the color
+ * offsets (C+1 entries, edges [offsets[c-1], offsets[c]) of the new order have color c).
+ * Any pointer may be NULL. */
+dgc_status dgc_get_ordering(const dgc_mesh* mesh, int32_t* elem_new_of_old,
+                            int32_t* edge_new_of_old, int8_t* edge_color, int32_t* color_offsets);
+
+/* Physical coordinates of each element's volume quadrature points, [E][Nq][dim], original
+ * element order (unwrapped per element), and the L2 projection onto the basis of values
+ * given at those points ([E][Nq][M] -> c_host [E][M][Np], original order).  Host only;
+ * used to build initial states. */
+dgc_status dgc_vol_points(const dgc_mesh* mesh, double* xyz);
+dgc_status dgc_project(const dgc_mesh* mesh, const double* vals, double* c_host);
+
+/* Bytes of one device state vector ([E][M][Np] FP64), and of the device workspace that
+ * dgc_rk_step needs for the given precision. */
+dgc_status dgc_state_size(const dgc_mesh* mesh, int64_t* bytes);
+dgc_status dgc_workspace_size(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes);
+
+/* Copy a host state (original element order, [E][M][Np] FP64) to a device state
+ * (internal order), and back.  The permutation runs on the host through a pinned staging
+ * buffer the mesh owns; the copy is enqueued on `stream` and the call returns after the
+ * stream has completed it (it synchronises `stream`). */
+dgc_status dgc_import_state(dgc_mesh* mesh, const double* c_host, double* c_dev, void* stream);
+dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host, void* stream);
+
+/* Right-hand side of Eq. 2: rhs_dev = dc/dt at state c_dev (both FP64, [E][M][Np],
+ * internal order, device).  Volume integral plus the per-color surface integral of
+ * Algorithm 1 with the local Lax-Friedrichs flux.  prec selects the arithmetic.
+ * Requires a colored mesh (DGC_ERR_ARG otherwise).  c_dev and rhs_dev must not alias. */
+dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev,
+                   void* stream);
+
+/* CFL time step, FP64, on the device:
+ * dt = cfl * min_i r_i / ((2p+1) lambda_i), r_i the inradius, lambda_i the largest
+ * |u| + c over element i's volume quadrature points.  Writes one double to dt_dev. */
+dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl, double* dt_dev,
+                      void* stream);
+
+/* One SSP-RK3 step (Shu-Osher form) of c_dev in place, dt from the CFL rule on the state
+ * at the start of the step (written to dt_dev, device).  workspace_dev holds at least
+ * dgc_workspace_size() bytes, 256-byte aligned.  No allocation and no host
+ * synchronisation after the first device call on the mesh. */
+dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl,
+                       double* dt_dev, void* workspace_dev, void* stream);
+
+/* Comparators for the race mitigation of Sec. 1 that coloring replaces.
+ * dgc_rhs_atomic: one launch over all edges, contributions added with atomicAdd.
+ * dgc_rhs_two_pass: every edge writes its left and right contributions to slots 2k and
+ * 2k+1 of a per-edge buffer, then a per-element kernel gathers them.  buffer_dev holds
+ * at least dgc_two_pass_buffer_bytes() bytes.  Same results as dgc_rhs up to rounding. */
+dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev,
+                          double* rhs_dev, void* stream);
+dgc_status dgc_rhs_two_pass(dgc_mesh* mesh, dgc_prec prec, const double* c_dev,
+                            double* rhs_dev, void* buffer_dev, void* stream);
+
+/* Buffer memory the per-edge two-pass scheme needs (Sec. 4.1, Table 4):
+ * 2 * np * neq * sides * word_bytes. */
+dgc_status dgc_two_pass_buffer_bytes(int64_t sides, int np, int neq, int word_bytes,
+                                     int64_t* bytes);
+
+/* Options (see dgc_option).  Host only. */
+dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value);
+
+/* With DGC_OPT_PROFILE on: waits for the recorded events, adds the elapsed milliseconds
+ * of every recorded launch to ms[class] and the launch count to launches[class]
+ * (arrays of DGC_K_NCLASSES entries, zeroed by the caller), and forgets the records. */
+dgc_status dgc_profile_collect(dgc_mesh* mesh, double* ms, int64_t* launches);
+
+/* Number of kernels the last device call on this mesh enqueued. */
+dgc_status dgc_last_launch_count(const dgc_mesh* mesh, int64_t* launches);
+
+/* Thread-local message of the last error (empty string if none). */
+const char* dgc_last_error(void);
+
+/* Free the mesh and its device copies (the device must still be current). */
+void dgc_destroy(dgc_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGC_H */

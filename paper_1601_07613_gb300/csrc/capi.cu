@@ -1,0 +1,662 @@
+// C ABI of the library (include/dgc.h): argument checks, device upload of the
+// renumbered mesh, and the launch sequences of Algorithm 1 and SSP-RK3.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "device.cuh"
+
+using namespace dgc;
+
+namespace {
+
+thread_local std::string g_err;
+
+#define DGC_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) throw Error{DGC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+template <typename F>
+dgc_status guarded(F&& f) {
+  try {
+    f();
+    g_err.clear();
+    return DGC_OK;
+  } catch (const Error& e) {
+    g_err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return DGC_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return DGC_ERR_ARG;
+  }
+}
+
+void require(bool ok, const char* msg, dgc_status code = DGC_ERR_ARG) {
+  if (!ok) throw Error{code, msg};
+}
+
+int64_t nv_of(const Mesh& m) { return (int64_t)m.M * m.np; }
+int64_t state_bytes(const Mesh& m) { return m.ne * nv_of(m) * (int64_t)sizeof(double); }
+int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
+
+// host staging buffer (pinned) used by import / export
+struct Staging {
+  double* ptr = nullptr;
+  int64_t bytes = 0;
+};
+std::mutex g_stage_mu;
+std::vector<std::pair<const Mesh*, Staging>> g_staging;
+
+double* staging_for(const Mesh& m) {
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  for (auto& s : g_staging)
+    if (s.first == &m) return s.second.ptr;
+  Staging s;
+  s.bytes = state_bytes(m);
+  DGC_CUDA(cudaMallocHost(&s.ptr, s.bytes));
+  g_staging.emplace_back(&m, s);
+  return s.ptr;
+}
+
+void staging_free(const Mesh& m) {
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  for (size_t i = 0; i < g_staging.size(); ++i)
+    if (g_staging[i].first == &m) {
+      cudaFreeHost(g_staging[i].second.ptr);
+      g_staging.erase(g_staging.begin() + i);
+      return;
+    }
+}
+
+template <typename F>
+void parallel_for(int64_t n, F&& f) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 4096 || nt == 1) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+  }
+  for (auto& t : th) t.join();
+}
+
+std::mutex g_tab_mu;
+std::set<std::pair<int, int>> g_tab_done;  // (device, dim*16 + p)
+
+template <typename T>
+T* dalloc(int64_t n) {
+  T* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * std::max<int64_t>(n, 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{e == cudaErrorMemoryAllocation ? DGC_ERR_OOM : DGC_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  }
+  return p;
+}
+
+// Upload the renumbered mesh: per element inverse Jacobian and inradius, per
+// edge (new order) its elements, local faces, normal and |f|/detJ factors,
+// and the two-pass gather slots.
+void upload(Mesh& m) {
+  int dev = -1;
+  DGC_CUDA(cudaGetDevice(&dev));
+  if (m.dev && m.dev->device != dev) throw Error{DGC_ERR_ARG, "mesh was uploaded on another device"};
+  if (m.dev && !m.dirty) return;
+  device_free(m);
+  const int dim = m.dim, nfpe = m.nfpe;
+  const std::vector<int32_t>& en = m.elem_new_of_old;
+  std::vector<double> jinv((size_t)m.ne * dim * dim), inr(m.ne);
+  for (int64_t e = 0; e < m.ne; ++e) {
+    int64_t n = en[e];
+    std::copy_n(&m.Jinv[(size_t)e * dim * dim], dim * dim, &jinv[(size_t)n * dim * dim]);
+    inr[n] = m.inradius[e];
+  }
+  const int gstride = dim == 2 ? 2 : 3;  // double2 per edge
+  std::vector<int4> topo(m.ns);
+  std::vector<double2> fgeo((size_t)m.ns * gstride);
+  std::vector<int32_t> slots((size_t)m.ne * nfpe, 0);
+  for (int64_t k = 0; k < m.ns; ++k) {
+    int64_t old = m.side_old_of_new[k];
+    int32_t l = m.sl[old], r = m.sr[old];
+    int ql = m.sql[old], qr = r >= 0 ? m.sqr[old] : 15;
+    int orient = 0;
+    topo[k] = make_int4(en[l], r >= 0 ? en[r] : -1, ql | (qr << 4) | (orient << 8), 0);
+    double meas = m.smeas[old];
+    double sl = meas / m.detJ[l], sr = r >= 0 ? meas / m.detJ[r] : 0.0;
+    const double* n = &m.snormal[(size_t)old * dim];
+    if (dim == 2) {
+      fgeo[2 * k] = make_double2(n[0], n[1]);
+      fgeo[2 * k + 1] = make_double2(sl, sr);
+    } else {
+      fgeo[3 * k] = make_double2(n[0], n[1]);
+      fgeo[3 * k + 1] = make_double2(n[2], 0.0);
+      fgeo[3 * k + 2] = make_double2(sl, sr);
+    }
+    slots[(size_t)en[l] * nfpe + ql] = (int32_t)(2 * k);
+    if (r >= 0) slots[(size_t)en[r] * nfpe + qr] = (int32_t)(2 * k + 1);
+  }
+  auto d = std::make_unique<DeviceMesh>();
+  d->device = dev;
+  try {
+    d->jinv = dalloc<double>((int64_t)jinv.size());
+    d->inr = dalloc<double>(m.ne);
+    d->topo = dalloc<int4>(m.ns);
+    d->fgeo = dalloc<double2>((int64_t)fgeo.size());
+    d->slots = dalloc<int32_t>((int64_t)slots.size());
+    DGC_CUDA(cudaMemcpy(d->jinv, jinv.data(), sizeof(double) * jinv.size(), cudaMemcpyHostToDevice));
+    DGC_CUDA(cudaMemcpy(d->inr, inr.data(), sizeof(double) * inr.size(), cudaMemcpyHostToDevice));
+    DGC_CUDA(cudaMemcpy(d->topo, topo.data(), sizeof(int4) * topo.size(), cudaMemcpyHostToDevice));
+    DGC_CUDA(cudaMemcpy(d->fgeo, fgeo.data(), sizeof(double2) * fgeo.size(), cudaMemcpyHostToDevice));
+    DGC_CUDA(cudaMemcpy(d->slots, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice));
+    if (dim == 3) tet_upload_tables(m.p, m.tab, *d);
+  } catch (...) {
+    m.dev = d.release();
+    device_free(m);
+    throw;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto key = std::make_pair(dev, dim * 16 + m.p);
+    if (dim == 2 && !g_tab_done.count(key)) {
+      tri_upload_tables(m.p, m.tab);
+      DGC_CUDA(cudaGetLastError());
+      g_tab_done.insert(key);
+    }
+  }
+  m.dev = d.release();
+  m.dirty = false;
+}
+
+Mesh& checked(dgc_mesh* mesh) {
+  require(mesh != nullptr, "null mesh");
+  return *reinterpret_cast<Mesh*>(mesh);
+}
+const Mesh& checked(const dgc_mesh* mesh) {
+  require(mesh != nullptr, "null mesh");
+  return *reinterpret_cast<const Mesh*>(mesh);
+}
+
+Ctx ready(Mesh& m, void* stream) {
+  require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
+  upload(m);
+  Ctx x;
+  x.dim = m.dim;
+  x.p = m.p;
+  x.np = m.np;
+  x.M = m.M;
+  x.nfpe = m.nfpe;
+  x.ne = m.ne;
+  x.ns = m.ns;
+  x.epb = m.edges_per_block;
+  x.d = m.dev;
+  x.st = static_cast<cudaStream_t>(stream);
+  return x;
+}
+
+void check_ptr(const void* p, const char* what) {
+  if (!p) throw Error{DGC_ERR_ARG, std::string("null device pointer: ") + what};
+  if (reinterpret_cast<uintptr_t>(p) % 16) throw Error{DGC_ERR_ARG, std::string("misaligned device pointer: ") + what};
+}
+
+int vol(const Ctx& x, TypeCfg ty, const void* s, void* r) {
+  return x.dim == 2 ? tri_volume(x, ty, s, r) : tet_volume(x, ty, s, r);
+}
+int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, void* r, void* buf,
+         const StageArgs* sa) {
+  return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, r, buf, sa) : tet_surface(x, ty, mode, b, e, s, r, buf, sa);
+}
+int cfl(const Ctx& x, const double* s, double c, double* dt, float* sh) {
+  return x.dim == 2 ? tri_cfl(x, s, c, dt, sh) : tet_cfl(x, s, c, dt, sh);
+}
+
+void count(Mesh& m, int64_t& n, int r) {
+  if (r < 0) throw Error{DGC_ERR_UNSUPPORTED, "no kernel for this element type / order / precision"};
+  n += r;
+}
+
+// Optional per-launch event pairs (DGC_OPT_PROFILE), recorded on the launch stream.
+struct Prof {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls, nl;
+  size_t used = 0;
+};
+
+Prof* prof_of(Mesh& m) {
+  if (!m.prof) m.prof = new Prof();
+  return static_cast<Prof*>(m.prof);
+}
+
+void prof_free(Mesh& m) {
+  if (!m.prof) return;
+  Prof* P = static_cast<Prof*>(m.prof);
+  for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+  delete P;
+  m.prof = nullptr;
+}
+
+// launch through f(), counting its kernels; bracket it with events when profiling
+template <typename F>
+void run(Mesh& m, const Ctx& x, int cls, int64_t& n, F&& f) {
+  Prof* P = m.profile ? prof_of(m) : nullptr;
+  size_t slot = 0;
+  if (P) {
+    slot = P->used;
+    while (P->ev.size() < slot + 2) {
+      cudaEvent_t e;
+      DGC_CUDA(cudaEventCreate(&e));
+      P->ev.push_back(e);
+    }
+    P->used += 2;
+    DGC_CUDA(cudaEventRecord(P->ev[slot], x.st));
+  }
+  const int r = f();
+  if (P) {
+    DGC_CUDA(cudaEventRecord(P->ev[slot + 1], x.st));
+    P->cls.push_back(cls);
+    P->nl.push_back(r > 0 ? r : 0);
+  }
+  count(m, n, r);
+}
+
+void finish(Mesh& m, int64_t launches) {
+  m.last_launches = launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error{DGC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+// rhs = L(state): Algorithm 1 (volume, then the colors in order, a kernel
+// boundary between colors); with fusion on closed conforming meshes the
+// first color also evaluates the volume integral and stores, no pre-zeroing.
+int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, void* rhs) {
+  int64_t n = 0;
+  const std::vector<int32_t>& off = m.color_off;
+  if (m.fuse && m.perfect) {
+    run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], state, rhs, nullptr, nullptr); });
+    for (int c = 2; c <= m.ncolors; ++c)
+      run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, rhs, nullptr, nullptr); });
+  } else {
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, state, rhs); });
+    for (int c = 1; c <= m.ncolors; ++c)
+      run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, rhs, nullptr, nullptr); });
+  }
+  return n;
+}
+
+}  // namespace
+
+namespace dgc {
+void device_free(Mesh& m) {
+  if (!m.dev) return;
+  cudaFree(m.dev->jinv);
+  cudaFree(m.dev->inr);
+  cudaFree(m.dev->topo);
+  cudaFree(m.dev->fgeo);
+  cudaFree(m.dev->slots);
+  cudaFree(m.dev->ftab);
+  cudaFree(m.dev->ftabd);
+  delete m.dev;
+  m.dev = nullptr;
+  m.dirty = true;
+}
+}  // namespace dgc
+
+extern "C" {
+
+const char* dgc_last_error(void) { return g_err.c_str(); }
+
+dgc_status dgc_mesh_create(int dim, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
+                           const double* periodic_len, dgc_mesh** out) {
+  return guarded([&] {
+    require(out != nullptr, "null output pointer");
+    *out = nullptr;
+    *out = reinterpret_cast<dgc_mesh*>(build_mesh(dim, p, nv, xyz, ne, ev, periodic_len));
+  });
+}
+
+static void report_colors(const Mesh& m, int32_t* n_colors, int64_t* per_color) {
+  if (n_colors) *n_colors = m.ncolors;
+  if (per_color) {
+    for (int c = 0; c < 8; ++c) per_color[c] = 0;
+    for (int c = 1; c <= m.ncolors && c <= 8; ++c) per_color[c - 1] = m.color_off[c] - m.color_off[c - 1];
+  }
+}
+
+dgc_status dgc_color_edges(dgc_mesh* mesh, uint64_t seed, int64_t max_swaps, int32_t* n_colors,
+                           int64_t* per_color) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    try {
+      color_faces(m, seed, max_swaps);
+    } catch (const Error&) {
+      m.ncolors = 0;
+      m.color.clear();
+      m.side_old_of_new.clear();
+      m.dirty = true;
+      throw;
+    }
+    reorder(m, true, true);
+    report_colors(m, n_colors, per_color);
+  });
+}
+
+dgc_status dgc_color_edges_naive(dgc_mesh* mesh, int renumber, int reorder_left, int32_t* n_colors,
+                                 int64_t* per_color) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    color_faces_naive(m);
+    reorder(m, renumber != 0, reorder_left != 0);
+    report_colors(m, n_colors, per_color);
+  });
+}
+
+dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t info[10]) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(info != nullptr, "null info");
+    info[0] = m.ne;
+    info[1] = m.ns;
+    info[2] = m.np;
+    info[3] = m.M;
+    info[4] = m.tab.nqf;
+    info[5] = m.tab.nqv;
+    info[6] = m.ncolors;
+    info[7] = m.dim;
+    info[8] = m.p;
+    info[9] = m.perfect ? 1 : 0;
+  });
+}
+
+dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, int8_t* qleft, int8_t* qright) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    if (left) std::copy(m.sl.begin(), m.sl.end(), left);
+    if (right) std::copy(m.sr.begin(), m.sr.end(), right);
+    if (qleft) std::copy(m.sql.begin(), m.sql.end(), qleft);
+    if (qright) std::copy(m.sqr.begin(), m.sqr.end(), qright);
+  });
+}
+
+dgc_status dgc_get_ordering(const dgc_mesh* mesh, int32_t* elem_new_of_old, int32_t* edge_new_of_old,
+                            int8_t* edge_color, int32_t* color_offsets) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    if (elem_new_of_old) std::copy(m.elem_new_of_old.begin(), m.elem_new_of_old.end(), elem_new_of_old);
+    if (edge_new_of_old) std::copy(m.side_new_of_old.begin(), m.side_new_of_old.end(), edge_new_of_old);
+    if (edge_color) std::copy(m.color.begin(), m.color.end(), edge_color);
+    if (color_offsets) std::copy(m.color_off.begin(), m.color_off.end(), color_offsets);
+  });
+}
+
+dgc_status dgc_vol_points(const dgc_mesh* mesh, double* xyz) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(xyz != nullptr, "null output");
+    vol_points(m, xyz);
+  });
+}
+
+dgc_status dgc_project(const dgc_mesh* mesh, const double* vals, double* c_host) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(vals && c_host, "null array");
+    project(m, vals, c_host);
+  });
+}
+
+dgc_status dgc_state_size(const dgc_mesh* mesh, int64_t* bytes) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(bytes != nullptr, "null output");
+    *bytes = state_bytes(m);
+  });
+}
+
+static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) {
+  int64_t S = state_bytes(m);
+  return prec == DGC_FP64 ? 2 * align256(S) : align256(S) + 2 * align256(S / 2);
+}
+
+dgc_status dgc_workspace_size(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(bytes != nullptr, "null output");
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    *bytes = workspace_bytes(m, prec);
+  });
+}
+
+dgc_status dgc_import_state(dgc_mesh* mesh, const double* c_host, double* c_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(c_host != nullptr, "null host state");
+    check_ptr(c_dev, "c_dev");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    upload(m);
+    double* stg = staging_for(m);
+    const int64_t nv = nv_of(m);
+    const int32_t* en = m.elem_new_of_old.data();
+    parallel_for(m.ne, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i) std::memcpy(stg + (int64_t)en[i] * nv, c_host + i * nv, sizeof(double) * nv);
+    });
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DGC_CUDA(cudaMemcpyAsync(c_dev, stg, state_bytes(m), cudaMemcpyHostToDevice, st));
+    DGC_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(c_host != nullptr, "null host state");
+    check_ptr(c_dev, "c_dev");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    upload(m);
+    double* stg = staging_for(m);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DGC_CUDA(cudaMemcpyAsync(stg, c_dev, state_bytes(m), cudaMemcpyDeviceToHost, st));
+    DGC_CUDA(cudaStreamSynchronize(st));
+    const int64_t nv = nv_of(m);
+    const int32_t* en = m.elem_new_of_old.data();
+    parallel_for(m.ne, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i) std::memcpy(c_host + i * nv, stg + (int64_t)en[i] * nv, sizeof(double) * nv);
+    });
+  });
+}
+
+dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    check_ptr(c_dev, "c_dev");
+    check_ptr(rhs_dev, "rhs_dev");
+    require(c_dev != rhs_dev, "c_dev and rhs_dev must not alias");
+    Ctx x = ready(m, stream);
+    finish(m, launch_rhs(m, x, prec == DGC_FP64 ? TY_D : TY_MD, c_dev, rhs_dev));
+  });
+}
+
+dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl_, double* dt_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    check_ptr(c_dev, "c_dev");
+    require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
+    require(cfl_ > 0.0, "cfl must be positive");
+    Ctx x = ready(m, stream);
+    DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
+    int64_t n = 0;
+    run(m, x, DGC_K_CFL, n, [&] { return cfl(x, c_dev, cfl_, dt_dev, nullptr); });
+    finish(m, n);
+  });
+}
+
+dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_, double* dt_dev,
+                       void* workspace_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    check_ptr(c_dev, "c_dev");
+    require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
+    require(workspace_dev != nullptr && reinterpret_cast<uintptr_t>(workspace_dev) % 256 == 0,
+            "workspace must be 256-byte aligned");
+    require(cfl_ > 0.0, "cfl must be positive");
+    Ctx x = ready(m, stream);
+    const bool mixed = prec == DGC_FP32_MIXED;
+    const int64_t S = state_bytes(m);
+    char* ws = static_cast<char*>(workspace_dev);
+    double* u1 = reinterpret_cast<double*>(ws);
+    float* shadow = mixed ? reinterpret_cast<float*>(ws + align256(S)) : nullptr;
+    void* rhs = mixed ? (void*)(ws + align256(S) + align256(S / 2)) : (void*)(ws + align256(S));
+    int64_t n = 0;
+    DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
+    run(m, x, DGC_K_CFL, n, [&] { return cfl(x, c_dev, cfl_, dt_dev, shadow); });
+    const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
+    const std::vector<int32_t>& off = m.color_off;
+    const int C = m.ncolors;
+    const TypeCfg ty = mixed ? TY_MF : TY_D;
+    for (int s = 0; s < 3; ++s) {
+      double* us = s == 0 ? c_dev : u1;
+      StageArgs sa;
+      sa.u0 = c_dev;
+      sa.uout = s == 2 ? c_dev : u1;
+      sa.shadow = shadow;
+      sa.dt = dt_dev;
+      sa.a0 = A0[s];
+      sa.b0 = B0[s];
+      const void* st_in = mixed ? (const void*)shadow : (const void*)us;
+      if (m.fuse && m.perfect && C >= 2) {
+        run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], st_in, rhs, nullptr, nullptr); });
+        for (int c = 2; c < C; ++c)
+          run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr); });
+        run(m, x, DGC_K_LAST, n, [&] {
+          return surf(x, mixed ? TY_MLAST : TY_D, SURF_LAST, off[C - 1], off[C], us, rhs, nullptr, &sa);
+        });
+      } else {
+        run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, st_in, rhs); });
+        for (int c = 1; c <= C; ++c)
+          run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr); });
+        run(m, x, DGC_K_STAGE, n, [&] { return stage_update(x, mixed, us, rhs, sa); });
+      }
+    }
+    finish(m, n);
+  });
+}
+
+dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    check_ptr(c_dev, "c_dev");
+    check_ptr(rhs_dev, "rhs_dev");
+    Ctx x = ready(m, stream);
+    const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
+    int64_t n = 0;
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, rhs_dev); });
+    run(m, x, DGC_K_ATOMIC, n, [&] { return surf(x, ty, SURF_ATOMIC, 0, m.ns, c_dev, rhs_dev, nullptr, nullptr); });
+    finish(m, n);
+  });
+}
+
+dgc_status dgc_two_pass_buffer_bytes(int64_t sides, int np, int neq, int word_bytes, int64_t* bytes) {
+  return guarded([&] {
+    require(bytes != nullptr && sides >= 0 && np > 0 && neq > 0 && word_bytes > 0, "bad argument");
+    *bytes = 2 * (int64_t)np * neq * sides * word_bytes;
+  });
+}
+
+dgc_status dgc_rhs_two_pass(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev, void* buffer_dev,
+                            void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    check_ptr(c_dev, "c_dev");
+    check_ptr(rhs_dev, "rhs_dev");
+    check_ptr(buffer_dev, "buffer_dev");
+    Ctx x = ready(m, stream);
+    const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
+    int64_t n = 0;
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, rhs_dev); });
+    run(m, x, DGC_K_BUFFER, n, [&] { return surf(x, ty, SURF_BUFFER, 0, m.ns, c_dev, rhs_dev, buffer_dev, nullptr); });
+    run(m, x, DGC_K_GATHER, n, [&] { return gather_two_pass(x, false, rhs_dev, buffer_dev); });
+    finish(m, n);
+  });
+}
+
+dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    switch (opt) {
+      case DGC_OPT_FUSE:
+        m.fuse = value != 0;
+        break;
+      case DGC_OPT_EDGES_PER_BLOCK:
+        require(value >= 16 && value <= 512 && value % 16 == 0, "edges per block must be 16..512, a multiple of 16");
+        m.edges_per_block = (int)value;
+        break;
+      case DGC_OPT_THREADS_PER_EDGE:
+        require(value == 2, "this build uses two threads per edge");
+        m.threads_per_edge = (int)value;
+        break;
+      case DGC_OPT_PROFILE:
+        m.profile = value != 0;
+        break;
+      default:
+        throw Error{DGC_ERR_ARG, "unknown option"};
+    }
+  });
+}
+
+dgc_status dgc_profile_collect(dgc_mesh* mesh, double* ms, int64_t* launches) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(ms && launches, "null output");
+    if (!m.prof) return;
+    Prof* P = static_cast<Prof*>(m.prof);
+    for (size_t i = 0; i < P->cls.size(); ++i) {
+      DGC_CUDA(cudaEventSynchronize(P->ev[2 * i + 1]));
+      float t = 0.f;
+      DGC_CUDA(cudaEventElapsedTime(&t, P->ev[2 * i], P->ev[2 * i + 1]));
+      ms[P->cls[i]] += t;
+      launches[P->cls[i]] += P->nl[i];
+    }
+    P->cls.clear();
+    P->nl.clear();
+    P->used = 0;
+  });
+}
+
+dgc_status dgc_last_launch_count(const dgc_mesh* mesh, int64_t* launches) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(launches != nullptr, "null output");
+    *launches = m.last_launches;
+  });
+}
+
+void dgc_destroy(dgc_mesh* mesh) {
+  if (!mesh) return;
+  Mesh* m = reinterpret_cast<Mesh*>(mesh);
+  device_free(*m);
+  staging_free(*m);
+  prof_free(*m);
+  delete m;
+}
+
+}  // extern "C"

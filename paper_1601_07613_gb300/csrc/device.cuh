@@ -1,0 +1,76 @@
+// Device-side declarations shared by the C ABI (capi.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dgc_internal.h"
+
+namespace dgc {
+
+// Device copies of one mesh, in the internal (renumbered) order.
+struct DeviceMesh {
+  int device = -1;
+  double* jinv = nullptr;   // [E][dim*dim] rows = gradients of the reference coordinates
+  double* inr = nullptr;    // [E] inradius
+  int4* topo = nullptr;     // [Ns] (left, right or -1, local faces lq | rq << 4 | orient << 8, 0)
+  double2* fgeo = nullptr;  // [Ns][2] 2D: (nx, ny), (|f|/detJ_l, |f|/detJ_r); 3D: [Ns][3]
+  int32_t* slots = nullptr; // [E][nfpe] two-pass gather slots 2k + side
+  float* ftab = nullptr;    // 3D face tables (float copy)
+  double* ftabd = nullptr;  // 3D face tables
+};
+
+// Surface-kernel modes (Algorithm 1 and the comparators of Sec. 1).
+enum SurfMode {
+  SURF_RMW = 0,     // add into rhs (colors after the first)
+  SURF_FIRST = 1,   // volume integral + surface, plain store (first color, closed meshes)
+  SURF_ATOMIC = 2,  // atomicAdd into rhs (comparator)
+  SURF_BUFFER = 3,  // write per-edge buffer slots 2k, 2k+1 (comparator)
+  SURF_LAST = 4     // last color: finish rhs in registers and apply the RK stage update
+};
+
+// Type configurations: storage of the state read, compute type, rhs type.
+enum TypeCfg {
+  TY_D = 0,     // FP64 state, FP64 arithmetic, FP64 rhs
+  TY_MD = 1,    // FP64 state, FP32 arithmetic, FP64 rhs (dgc_rhs in mixed precision)
+  TY_MF = 2,    // FP32 shadow state, FP32 arithmetic, FP32 rhs (RK stages in mixed precision)
+  TY_MLAST = 3  // FP64 state, FP32 arithmetic, FP32 partial rhs (last color, mixed)
+};
+
+struct Ctx {
+  int dim = 2, p = 1, np = 0, M = 4, nfpe = 3;
+  int64_t ne = 0, ns = 0;
+  int epb = 128;
+  const DeviceMesh* d = nullptr;
+  cudaStream_t st = nullptr;
+};
+
+struct StageArgs {
+  const double* u0 = nullptr;  // state at the start of the step
+  double* uout = nullptr;      // stage output (may alias the stage input)
+  float* shadow = nullptr;     // FP32 copy of the stage output (mixed precision) or null
+  const double* dt = nullptr;  // device time step
+  double a0 = 0.0, b0 = 1.0;   // uout = a0 u0 + b0 (us + dt L(us))
+};
+
+// kernels_tri.cu
+void tri_upload_tables(int p, const RefTables& T);
+int tri_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
+int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
+                void* rhs, void* buf, const StageArgs* sa);
+int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
+
+// kernels_tet.cu
+void tet_upload_tables(int p, const RefTables& T, DeviceMesh& d);
+int tet_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
+int tet_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
+                void* rhs, void* buf, const StageArgs* sa);
+int tet_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
+
+// kernels_common.cu
+int stage_update(const Ctx& c, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa);
+int gather_two_pass(const Ctx& c, bool f32, void* rhs, const void* buf);
+int make_shadow(const Ctx& c, const double* state, float* shadow);
+
+}  // namespace dgc

@@ -1,0 +1,89 @@
+// Internal declarations shared by the host mesh code, the kernels and the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dgc.h"
+
+namespace dgc {
+
+constexpr int kMaxColors = 15;
+
+// Reference-element tables for one (dim, p).  Volume points carry weights that
+// sum to |reference element|; face weights sum to 1 over a face.
+struct RefTables {
+  int dim = 0, p = 0, np = 0, nqv = 0, nqf = 0, nfaces = 0;
+  std::vector<double> vr, vs, vt, vw;  // volume points (reference coordinates) and weights
+  std::vector<double> phiV;            // [nqv][np]
+  std::vector<double> dphiV;           // [dim][nqv][np]
+  std::vector<double> fw;              // [nqf] face weights
+  std::vector<double> phiF;            // [nfaces][nqf][np], face points in face parameters
+};
+
+// Builds the tables (quadrature + orthonormal basis) for triangles (dim 2) or
+// tetrahedra (dim 3).  Throws std::runtime_error on unsupported sizes.
+RefTables make_tables(int dim, int p);
+
+// Evaluates the orthonormal basis and its reference gradient at one point.
+void basis_eval(int dim, int p, const double* x, double* phi, double* grad /*[dim][np] or null*/);
+
+// Gauss-Jacobi rule with weight (1-x)^alpha on [-1, 1].
+void gauss_jacobi(int n, double alpha, double* x, double* w);
+
+struct DeviceMesh;  // defined in the CUDA translation unit
+
+struct Mesh {
+  int dim = 0, p = 0, np = 0, M = 0, nfpe = 0, nvpe = 0;
+  int64_t nv = 0, ne = 0, ns = 0;
+  bool periodic = false;
+  double L[3] = {0, 0, 0};
+  std::vector<double> X;     // [ne][nvpe][dim] unwrapped vertex coordinates
+  std::vector<int32_t> ev;   // [ne][nvpe]
+  // edge (face) table, original order
+  std::vector<int32_t> sl, sr;
+  std::vector<int8_t> sql, sqr;
+  std::vector<int32_t> face_of;  // [ne][nfpe] -> side
+  // geometry, original order
+  std::vector<double> detJ, Jinv, inradius;  // Jinv [ne][dim][dim] (row k = grad r_k)
+  std::vector<double> snormal, smeas;        // [ns][dim] outward normal of the left element, |face|
+  RefTables tab;
+  // coloring and ordering
+  int ncolors = 0;
+  bool perfect = false;  // every element has exactly one face of each color
+  std::vector<int8_t> color;  // original order
+  std::vector<int32_t> elem_new_of_old, side_new_of_old, side_old_of_new, color_off;
+  // options
+  bool fuse = true;
+  int edges_per_block = 128;
+  int threads_per_edge = 2;
+  bool profile = false;
+  void* prof = nullptr;  // event records (capi.cu)
+  // device side
+  DeviceMesh* dev = nullptr;
+  bool dirty = true;  // host ordering changed since the last upload
+  int64_t last_launches = 0;
+};
+
+// Host algorithms (mesh.cpp).  They throw dgc::Error on failure.
+struct Error {
+  dgc_status code;
+  std::string msg;
+};
+
+Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
+                 const double* periodic_len);
+struct ColorStats {
+  int64_t greedy_conflicts = 0, swaps = 0, breaks = 0, deferrals = 0;
+};
+ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps);
+int color_faces_naive(Mesh& m);
+void reorder(Mesh& m, bool renumber, bool reorder_left);
+void vol_points(const Mesh& m, double* xyz);
+void project(const Mesh& m, const double* vals, double* c);
+
+// Device side (capi.cu).
+void device_free(Mesh& m);
+
+}  // namespace dgc

@@ -1,0 +1,725 @@
+// Host side of the library: quadrature and basis tables, mesh ingest and
+// geometry, the edge coloring of Sec. 3.1 and the reordering of Sec. 5.
+//
+// Everything here runs once per mesh on the host (the paper's "mesh
+// preprocessing stage", Sec. 5); the per-step work is in kernels_tri.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <stdexcept>
+
+#include "dgc_internal.h"
+
+namespace dgc {
+
+// ---------------------------------------------------------------------------
+// Jacobi polynomials and Gauss-Jacobi rules
+// ---------------------------------------------------------------------------
+
+// P_n^{(a,b)}(x) by the three-term recurrence in n.
+static double jacobi(int n, double a, double b, double x) {
+  if (n == 0) return 1.0;
+  double pm = 1.0, p = 0.5 * ((a - b) + (a + b + 2.0) * x);
+  for (int k = 2; k <= n; ++k) {
+    double s = 2.0 * k + a + b;
+    double c1 = 2.0 * k * (k + a + b) * (s - 2.0);
+    double c2 = (s - 1.0) * (s * (s - 2.0) * x + a * a - b * b);
+    double c3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * s;
+    double pn = (c2 * p - c3 * pm) / c1;
+    pm = p;
+    p = pn;
+  }
+  return p;
+}
+
+// d/dx P_n^{(a,b)} = (n+a+b+1)/2 P_{n-1}^{(a+1,b+1)}.
+static double djacobi(int n, double a, double b, double x) {
+  return n == 0 ? 0.0 : 0.5 * (n + a + b + 1.0) * jacobi(n - 1, a + 1.0, b + 1.0, x);
+}
+
+// Newton iteration with polynomial deflation from Chebyshev starting points;
+// weights from the Christoffel formula for beta = 0.
+void gauss_jacobi(int n, double alpha, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n; ++k) {
+    double r = -std::cos((2.0 * k + 1.0) * pi / (2.0 * n));
+    if (k > 0) r = 0.5 * (r + x[k - 1]);
+    for (int it = 0; it < 100; ++it) {
+      double s = 0.0;
+      for (int i = 0; i < k; ++i) s += 1.0 / (r - x[i]);
+      double P = jacobi(n, alpha, 0.0, r), dP = djacobi(n, alpha, 0.0, r);
+      double delta = -P / (dP - s * P);
+      r += delta;
+      if (std::fabs(delta) < 1e-16) break;
+    }
+    x[k] = r;
+  }
+  std::sort(x, x + n);
+  double cst = std::exp((alpha + 1.0) * std::log(2.0) + std::lgamma(n + alpha + 1.0) +
+                        std::lgamma(n + 1.0) - std::lgamma(n + alpha + 1.0) - std::lgamma(n + 1.0));
+  for (int i = 0; i < n; ++i) {
+    double d = djacobi(n, alpha, 0.0, x[i]);
+    w[i] = cst / ((1.0 - x[i] * x[i]) * d * d);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Orthonormal modal basis (the v_ij of Eq. 2): Dubiner polynomials in
+// collapsed coordinates, normalised numerically on the reference element.
+// Ordering: total degree d = 0..p, first index from d down to 0.
+// ---------------------------------------------------------------------------
+
+static int npoly(int dim, int p) {
+  return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
+}
+
+// Unnormalised triangle modes psi_{k,l} = P_k(a) (1-s)^k P_l^{(2k+1,0)}(b),
+// a = 2r/(1-s) - 1, b = 2s - 1, with gradients by the chain rule.
+static void tri_raw(int p, double r, double s, double* phi, double* dr, double* ds) {
+  double om = 1.0 - s;
+  double a = om > 0.0 ? 2.0 * r / om - 1.0 : -1.0;
+  double b = 2.0 * s - 1.0;
+  int j = 0;
+  for (int d = 0; d <= p; ++d)
+    for (int k = d; k >= 0; --k) {
+      int l = d - k;
+      double Pk = jacobi(k, 0, 0, a), dPk = djacobi(k, 0, 0, a);
+      double Pl = jacobi(l, 2.0 * k + 1.0, 0, b), dPl = djacobi(l, 2.0 * k + 1.0, 0, b);
+      double omk = std::pow(om, k), omk1 = k > 0 ? std::pow(om, k - 1) : 0.0;
+      phi[j] = Pk * omk * Pl;
+      if (dr) {
+        dr[j] = k > 0 ? 2.0 * dPk * omk1 * Pl : 0.0;
+        ds[j] = (k > 0 ? (dPk * (1.0 + a) - k * Pk) * omk1 * Pl : 0.0) + 2.0 * Pk * omk * dPl;
+      }
+      ++j;
+    }
+}
+
+// Unnormalised tetrahedron modes
+// psi_{i,j,k} = P_i(a) ((1-b)/2)^i P_j^{(2i+1,0)}(b) ((1-c)/2)^{i+j} P_k^{(2i+2j+2,0)}(c),
+// a = 2r/(1-s-t) - 1, b = 2s/(1-t) - 1, c = 2t - 1; gradients by the chain rule.
+static void tet_raw(int p, double r, double s, double t, double* phi, double* g) {
+  double u = 1.0 - s - t, v = 1.0 - t;
+  double a = u > 0.0 ? 2.0 * r / u - 1.0 : -1.0;
+  double b = v > 0.0 ? 2.0 * s / v - 1.0 : -1.0;
+  double c = 2.0 * t - 1.0;
+  // partial derivatives of (a, b, c) w.r.t. (r, s, t)
+  double da[3] = {u > 0 ? 2.0 / u : 0.0, u > 0 ? 2.0 * r / (u * u) : 0.0, u > 0 ? 2.0 * r / (u * u) : 0.0};
+  double db[3] = {0.0, v > 0 ? 2.0 / v : 0.0, v > 0 ? 2.0 * s / (v * v) : 0.0};
+  double dc[3] = {0.0, 0.0, 2.0};
+  int n = 0;
+  for (int d = 0; d <= p; ++d)
+    for (int i = d; i >= 0; --i)
+      for (int j = d - i; j >= 0; --j) {
+        int k = d - i - j;
+        double A = jacobi(i, 0, 0, a), dA = djacobi(i, 0, 0, a);
+        double hb = 0.5 * (1.0 - b), hc = 0.5 * (1.0 - c);
+        double B0 = std::pow(hb, i), B1 = jacobi(j, 2.0 * i + 1.0, 0, b);
+        double dB = (i > 0 ? -0.5 * i * std::pow(hb, i - 1) : 0.0) * B1 + B0 * djacobi(j, 2.0 * i + 1.0, 0, b);
+        double Bv = B0 * B1;
+        double C0 = std::pow(hc, i + j), C1 = jacobi(k, 2.0 * i + 2.0 * j + 2.0, 0, c);
+        double dC = (i + j > 0 ? -0.5 * (i + j) * std::pow(hc, i + j - 1) : 0.0) * C1 +
+                    C0 * djacobi(k, 2.0 * i + 2.0 * j + 2.0, 0, c);
+        double Cv = C0 * C1;
+        phi[n] = A * Bv * Cv;
+        if (g) {
+          int np = npoly(3, p);
+          for (int x = 0; x < 3; ++x)
+            g[x * np + n] = dA * da[x] * Bv * Cv + A * dB * db[x] * Cv + A * Bv * dC * dc[x];
+        }
+        ++n;
+      }
+}
+
+// Triangle rule: Gauss-Legendre (n) x Gauss-Jacobi(1,0) (n), collapsed.
+static void tri_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w) {
+  std::vector<double> xg(n), wg(n), xj(n), wj(n);
+  gauss_jacobi(n, 0.0, xg.data(), wg.data());
+  gauss_jacobi(n, 1.0, xj.data(), wj.data());
+  r.clear();
+  s.clear();
+  w.clear();
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      r.push_back(0.25 * (1.0 + xg[k]) * (1.0 - xj[i]));
+      s.push_back(0.5 * (1.0 + xj[i]));
+      w.push_back(0.125 * wg[k] * wj[i]);
+    }
+}
+
+static void tet_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& t,
+                     std::vector<double>& w) {
+  std::vector<double> xa(n), wa(n), xb(n), wb(n), xc(n), wc(n);
+  gauss_jacobi(n, 0.0, xa.data(), wa.data());
+  gauss_jacobi(n, 1.0, xb.data(), wb.data());
+  gauss_jacobi(n, 2.0, xc.data(), wc.data());
+  r.clear();
+  s.clear();
+  t.clear();
+  w.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        t.push_back(0.5 * (1.0 + xc[i]));
+        s.push_back(0.25 * (1.0 + xb[j]) * (1.0 - xc[i]));
+        r.push_back(0.125 * (1.0 + xa[k]) * (1.0 - xb[j]) * (1.0 - xc[i]));
+        w.push_back(wa[k] * wb[j] * wc[i] / 64.0);
+      }
+}
+
+// normalisation constants, cached per (dim, p)
+static std::vector<double> norms(int dim, int p) {
+  int np = npoly(dim, p);
+  std::vector<double> acc(np, 0.0), phi(np);
+  std::vector<double> r, s, t, w;
+  if (dim == 2) {
+    tri_rule(p + 2, r, s, w);
+    for (size_t q = 0; q < w.size(); ++q) {
+      tri_raw(p, r[q], s[q], phi.data(), nullptr, nullptr);
+      for (int j = 0; j < np; ++j) acc[j] += w[q] * phi[j] * phi[j];
+    }
+  } else {
+    tet_rule(p + 2, r, s, t, w);
+    for (size_t q = 0; q < w.size(); ++q) {
+      tet_raw(p, r[q], s[q], t[q], phi.data(), nullptr);
+      for (int j = 0; j < np; ++j) acc[j] += w[q] * phi[j] * phi[j];
+    }
+  }
+  for (int j = 0; j < np; ++j) acc[j] = 1.0 / std::sqrt(acc[j]);
+  return acc;
+}
+
+void basis_eval(int dim, int p, const double* x, double* phi, double* grad) {
+  static thread_local int cdim = -1, cp = -1;
+  static thread_local std::vector<double> N;
+  if (cdim != dim || cp != p) {
+    N = norms(dim, p);
+    cdim = dim;
+    cp = p;
+  }
+  int np = npoly(dim, p);
+  if (dim == 2) {
+    tri_raw(p, x[0], x[1], phi, grad, grad ? grad + np : nullptr);
+  } else {
+    tet_raw(p, x[0], x[1], x[2], phi, grad);
+  }
+  for (int j = 0; j < np; ++j) {
+    phi[j] *= N[j];
+    if (grad)
+      for (int a = 0; a < dim; ++a) grad[a * np + j] *= N[j];
+  }
+}
+
+// reference vertices of the simplices
+static const double kTriV[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+static const double kTetV[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+// local face vertices: triangle edge q = (q, q+1); tetrahedron face q = the
+// three vertices other than q, ascending
+static void face_vertices(int dim, int q, int* fv) {
+  if (dim == 2) {
+    fv[0] = q;
+    fv[1] = (q + 1) % 3;
+    return;
+  }
+  int n = 0;
+  for (int k = 0; k < 4; ++k)
+    if (k != q) fv[n++] = k;
+}
+
+RefTables make_tables(int dim, int p) {
+  if (dim != 2 && dim != 3) throw std::runtime_error("dim");
+  RefTables T;
+  T.dim = dim;
+  T.p = p;
+  T.np = npoly(dim, p);
+  T.nfaces = dim + 1;
+  std::vector<double> fa, fb;
+  if (dim == 2) {
+    tri_rule(p + 1, T.vr, T.vs, T.vw);
+    T.vt.assign(T.vr.size(), 0.0);
+    int n = 2 * p + 1;
+    std::vector<double> x(n), w(n);
+    gauss_jacobi(n, 0.0, x.data(), w.data());
+    for (int i = 0; i < n; ++i) {
+      fa.push_back(0.5 * (1.0 + x[i]));
+      fb.push_back(0.0);
+      T.fw.push_back(0.5 * w[i]);
+    }
+  } else {
+    tet_rule(p + 2, T.vr, T.vs, T.vt, T.vw);
+    std::vector<double> w;
+    tri_rule(p + 2, fa, fb, w);
+    for (double v : w) T.fw.push_back(2.0 * v);
+  }
+  T.nqv = (int)T.vw.size();
+  T.nqf = (int)T.fw.size();
+  T.phiV.resize((size_t)T.nqv * T.np);
+  T.dphiV.resize((size_t)dim * T.nqv * T.np);
+  std::vector<double> phi(T.np), g((size_t)dim * T.np);
+  for (int q = 0; q < T.nqv; ++q) {
+    double x[3] = {T.vr[q], T.vs[q], T.vt[q]};
+    basis_eval(dim, p, x, phi.data(), g.data());
+    for (int j = 0; j < T.np; ++j) {
+      T.phiV[(size_t)q * T.np + j] = phi[j];
+      for (int a = 0; a < dim; ++a) T.dphiV[((size_t)a * T.nqv + q) * T.np + j] = g[a * T.np + j];
+    }
+  }
+  T.phiF.resize((size_t)T.nfaces * T.nqf * T.np);
+  for (int f = 0; f < T.nfaces; ++f) {
+    int fv[3];
+    face_vertices(dim, f, fv);
+    for (int q = 0; q < T.nqf; ++q) {
+      double x[3] = {0, 0, 0};
+      for (int a = 0; a < dim; ++a) {
+        const double* V0 = dim == 2 ? kTriV[fv[0]] : kTetV[fv[0]];
+        const double* V1 = dim == 2 ? kTriV[fv[1]] : kTetV[fv[1]];
+        x[a] = V0[a] + fa[q] * (V1[a] - V0[a]);
+        if (dim == 3) x[a] += fb[q] * (kTetV[fv[2]][a] - V0[a]);
+      }
+      basis_eval(dim, p, x, phi.data(), nullptr);
+      for (int j = 0; j < T.np; ++j) T.phiF[((size_t)f * T.nqf + q) * T.np + j] = phi[j];
+    }
+  }
+  return T;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh ingest: edge table (Sec. 5, "an edge points to the two elements that
+// share it") with open-addressing hashing of sorted vertex keys.
+// ---------------------------------------------------------------------------
+
+namespace {
+struct KeyTable {
+  std::vector<uint64_t> keys;
+  std::vector<int64_t> vals;
+  uint64_t mask = 0;
+  explicit KeyTable(int64_t n) {
+    uint64_t cap = 16;
+    while (cap < (uint64_t)n * 2) cap <<= 1;
+    keys.assign(cap, ~0ull);
+    vals.assign(cap, -1);
+    mask = cap - 1;
+  }
+  static uint64_t mix(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+  }
+  // returns the stored value, or inserts v and returns -1
+  int64_t find_or_insert(uint64_t k, int64_t v) {
+    uint64_t h = mix(k) & mask;
+    while (true) {
+      if (keys[h] == ~0ull) {
+        keys[h] = k;
+        vals[h] = v;
+        return -1;
+      }
+      if (keys[h] == k) return vals[h];
+      h = (h + 1) & mask;
+    }
+  }
+};
+}  // namespace
+
+Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
+                 const double* periodic_len) {
+  if (dim != 2 && dim != 3) throw Error{DGC_ERR_ARG, "dim must be 2 or 3"};
+  if (dim == 2 && (p < 1 || p > 3)) throw Error{DGC_ERR_UNSUPPORTED, "triangles support p = 1..3"};
+  if (dim == 3 && (p < 1 || p > 2)) throw Error{DGC_ERR_UNSUPPORTED, "tetrahedra support p = 1..2"};
+  if (nv <= 0 || ne <= 0 || !xyz || !ev) throw Error{DGC_ERR_ARG, "empty mesh or null arrays"};
+  if (ne > (1LL << 30) || nv > (1LL << 30)) throw Error{DGC_ERR_ARG, "mesh too large"};
+  if (dim == 3 && nv >= (1LL << 21)) throw Error{DGC_ERR_UNSUPPORTED, "tetrahedral meshes need < 2^21 vertices"};
+  auto m = std::make_unique<Mesh>();
+  m->dim = dim;
+  m->p = p;
+  m->M = dim + 2;
+  m->nvpe = m->nfpe = dim + 1;
+  m->nv = nv;
+  m->ne = ne;
+  m->periodic = periodic_len != nullptr;
+  for (int a = 0; a < dim; ++a) {
+    m->L[a] = periodic_len ? periodic_len[a] : 0.0;
+    if (periodic_len && !(m->L[a] > 0.0)) throw Error{DGC_ERR_ARG, "period lengths must be positive"};
+  }
+  const int nvpe = m->nvpe;
+  m->ev.assign(ev, ev + ne * nvpe);
+  m->X.resize((size_t)ne * nvpe * dim);
+  m->detJ.resize(ne);
+  m->Jinv.resize((size_t)ne * dim * dim);
+  m->inradius.resize(ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    double* X = &m->X[(size_t)e * nvpe * dim];
+    for (int k = 0; k < nvpe; ++k) {
+      int32_t v = ev[e * nvpe + k];
+      if (v < 0 || v >= nv) throw Error{DGC_ERR_MESH, "vertex id out of range"};
+      for (int a = 0; a < dim; ++a) {
+        double x = xyz[(size_t)v * dim + a];
+        if (m->periodic && k > 0) x += m->L[a] * std::nearbyint((X[a] - x) / m->L[a]);
+        X[k * dim + a] = x;
+      }
+    }
+    double* Ji = &m->Jinv[(size_t)e * dim * dim];
+    double det;
+    if (dim == 2) {
+      double a = X[2] - X[0], b = X[4] - X[0], c = X[3] - X[1], d = X[5] - X[1];
+      det = a * d - b * c;
+      Ji[0] = d / det;
+      Ji[1] = -b / det;
+      Ji[2] = -c / det;
+      Ji[3] = a / det;
+    } else {
+      double J[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) J[a][k] = X[(k + 1) * 3 + a] - X[a];
+      det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+            J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      // inverse by cofactors: Ji[k][a] = cof(a,k)/det
+      for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a) {
+          int r0 = (a + 1) % 3, r1 = (a + 2) % 3, c0 = (k + 1) % 3, c1 = (k + 2) % 3;
+          Ji[k * 3 + a] = (J[r0][c0] * J[r1][c1] - J[r0][c1] * J[r1][c0]) / det;
+        }
+    }
+    if (!(det > 0.0)) throw Error{DGC_ERR_MESH, "element with non-positive Jacobian (check orientation)"};
+    m->detJ[e] = det;
+  }
+  // edge/face table, numbered by first appearance
+  KeyTable kt(ne * m->nfpe);
+  const int nfpe = m->nfpe;
+  m->face_of.assign((size_t)ne * nfpe, -1);
+  m->sl.reserve(ne * nfpe / 2 + 16);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int q = 0; q < nfpe; ++q) {
+      int fv[3];
+      face_vertices(dim, q, fv);
+      uint64_t g[3] = {0, 0, 0};
+      for (int i = 0; i < dim; ++i) g[i] = (uint64_t)ev[e * nvpe + fv[i]];
+      std::sort(g, g + dim);
+      uint64_t key = dim == 2 ? (g[0] << 32 | g[1]) : (g[0] << 42 | g[1] << 21 | g[2]);
+      int64_t s = kt.find_or_insert(key, (int64_t)m->sl.size());
+      if (s < 0) {
+        m->face_of[(size_t)e * nfpe + q] = (int32_t)m->sl.size();
+        m->sl.push_back((int32_t)e);
+        m->sql.push_back((int8_t)q);
+        m->sr.push_back(-1);
+        m->sqr.push_back(-1);
+      } else {
+        if (m->sr[s] >= 0 || m->sl[s] == e) throw Error{DGC_ERR_MESH, "face shared by more than two elements"};
+        m->sr[s] = (int32_t)e;
+        m->sqr[s] = (int8_t)q;
+        m->face_of[(size_t)e * nfpe + q] = (int32_t)s;
+      }
+    }
+  m->ns = (int64_t)m->sl.size();
+  // face geometry from the left element, inradius = dim |element| / |boundary|
+  m->snormal.resize((size_t)m->ns * dim);
+  m->smeas.resize(m->ns);
+  std::vector<double> bnd(ne, 0.0);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int q = 0; q < nfpe; ++q) {
+      const double* X = &m->X[(size_t)e * nvpe * dim];
+      int fv[3];
+      face_vertices(dim, q, fv);
+      double n[3] = {0, 0, 0}, meas;
+      if (dim == 2) {
+        // CCW triangle: outward normal of edge v_q -> v_{q+1} is (dy, -dx)/|d|
+        double dx = X[fv[1] * 2] - X[fv[0] * 2], dy = X[fv[1] * 2 + 1] - X[fv[0] * 2 + 1];
+        meas = std::hypot(dx, dy);
+        n[0] = dy / meas;
+        n[1] = -dx / meas;
+      } else {
+        double u[3], v[3], w[3];
+        for (int a = 0; a < 3; ++a) {
+          u[a] = X[fv[1] * 3 + a] - X[fv[0] * 3 + a];
+          v[a] = X[fv[2] * 3 + a] - X[fv[0] * 3 + a];
+          w[a] = X[q * 3 + a] - X[fv[0] * 3 + a];  // towards the opposite vertex
+        }
+        n[0] = u[1] * v[2] - u[2] * v[1];
+        n[1] = u[2] * v[0] - u[0] * v[2];
+        n[2] = u[0] * v[1] - u[1] * v[0];
+        double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        meas = 0.5 * nn;
+        double sgn = (n[0] * w[0] + n[1] * w[1] + n[2] * w[2]) > 0.0 ? -1.0 : 1.0;
+        for (int a = 0; a < 3; ++a) n[a] *= sgn / nn;
+      }
+      bnd[e] += meas;
+      int32_t s = m->face_of[(size_t)e * nfpe + q];
+      if (m->sl[s] == e) {
+        for (int a = 0; a < dim; ++a) m->snormal[(size_t)s * dim + a] = n[a];
+        m->smeas[s] = meas;
+      }
+    }
+  for (int64_t e = 0; e < ne; ++e) {
+    double vol = m->detJ[e] / (dim == 2 ? 2.0 : 6.0);
+    m->inradius[e] = dim * vol / bnd[e];
+  }
+  m->tab = make_tables(dim, p);
+  m->np = m->tab.np;
+  return m.release();
+}
+
+// ---------------------------------------------------------------------------
+// Coloring (Sec. 3.1).  Protocol (reading of "randomly" and of the order in
+// which conflicts are visited): xorshift64 draws, pick(n) = (draw >> 32) % n;
+// greedy pass over the edges in order; FIFO of conflicts; a swap candidate is
+// a colored face of left(e) then right(e), other than e and the previous
+// edge, whose color is unique among the other faces of those two elements;
+// a revisited edge (or no candidate) triggers the loop break.
+// ---------------------------------------------------------------------------
+
+namespace {
+struct Xorshift64 {
+  uint64_t s;
+  uint32_t pick(uint32_t n) {
+    s ^= s << 13;
+    s ^= s >> 7;
+    s ^= s << 17;
+    return (uint32_t)((s >> 32) % n);
+  }
+};
+
+struct Colorer {
+  const Mesh& m;
+  int nc;
+  std::vector<int8_t>& col;
+  Colorer(const Mesh& mm, int n, std::vector<int8_t>& c) : m(mm), nc(n), col(c) {}
+  const int32_t* faces(int32_t e) const { return &m.face_of[(size_t)e * m.nfpe]; }
+  // bitmask of colors on faces of l(k), r(k) other than k
+  uint32_t used(int64_t k) const {
+    uint32_t u = 0;
+    for (int32_t el : {m.sl[k], m.sr[k]}) {
+      if (el < 0) continue;
+      const int32_t* f = faces(el);
+      for (int q = 0; q < m.nfpe; ++q)
+        if (f[q] != k && col[f[q]] > 0) u |= 1u << col[f[q]];
+    }
+    return u;
+  }
+  int avail(int64_t k, int* out) const {
+    uint32_t u = used(k);
+    int n = 0;
+    for (int c = 1; c <= nc; ++c)
+      if (!(u & (1u << c))) out[n++] = c;
+    return n;
+  }
+};
+}  // namespace
+
+ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps) {
+  const int nc = m.nfpe;  // 3 colors for triangles, 4 for tetrahedra
+  ColorStats st;
+  std::vector<int8_t> col(m.ns, -1);
+  Colorer C(m, nc, col);
+  Xorshift64 rng{seed ? seed : 0x9E3779B97F4A7C15ull};
+  if (max_swaps <= 0) max_swaps = 1000 * m.ns;
+  std::vector<int64_t> ring(m.ns + 1);
+  int64_t head = 0, tail = 0, count = 0;
+  const int64_t cap = m.ns + 1;
+  auto push = [&](int64_t k) {
+    ring[tail] = k;
+    tail = tail + 1 == cap ? 0 : tail + 1;
+    ++count;
+  };
+  int av[kMaxColors + 1];
+  for (int64_t k = 0; k < m.ns; ++k) {
+    int n = C.avail(k, av);
+    if (n) col[k] = (int8_t)av[rng.pick(n)];
+    else push(k);
+  }
+  st.greedy_conflicts = count;
+  std::vector<int64_t> seen(m.ns, -1);
+  int64_t chain = 0, work = 0;
+  while (count > 0) {
+    int64_t e = ring[head];
+    head = head + 1 == cap ? 0 : head + 1;
+    --count;
+    if (col[e] >= 0) continue;
+    seen[e] = ++chain;
+    int64_t prev = -1;
+    for (;;) {
+      int n = C.avail(e, av);
+      if (n) {
+        col[e] = (int8_t)av[rng.pick(n)];
+        break;
+      }
+      int32_t el[2] = {m.sl[e], m.sr[e]};
+      int tally[kMaxColors + 1] = {0};
+      for (int32_t x : el) {
+        if (x < 0) continue;
+        const int32_t* f = C.faces(x);
+        for (int q = 0; q < m.nfpe; ++q)
+          if (f[q] != e && col[f[q]] > 0) ++tally[col[f[q]]];
+      }
+      int64_t cand[2 * 4];
+      int ncand = 0;
+      for (int32_t x : el) {
+        if (x < 0) continue;
+        const int32_t* f = C.faces(x);
+        for (int q = 0; q < m.nfpe; ++q) {
+          int64_t g = f[q];
+          if (g != e && g != prev && col[g] > 0 && tally[col[g]] == 1) cand[ncand++] = g;
+        }
+      }
+      if (ncand) {
+        int64_t g = cand[rng.pick(ncand)];
+        if (seen[g] != chain) {
+          if (++work > max_swaps) throw Error{DGC_ERR_COLORING_LIMIT, "conflict resolution exceeded max_swaps"};
+          col[e] = col[g];
+          col[g] = -1;
+          prev = e;
+          e = g;
+          seen[g] = chain;
+          ++st.swaps;
+          continue;
+        }
+      }
+      // loop break: smallest color present on both sides; e takes it and the
+      // two faces that carried it become conflicts
+      if (++work > max_swaps) throw Error{DGC_ERR_COLORING_LIMIT, "conflict resolution exceeded max_swaps"};
+      int64_t fa = -1, fb = -1;
+      int cs = 0;
+      if (el[1] >= 0) {
+        const int32_t* f0 = C.faces(el[0]);
+        const int32_t* f1 = C.faces(el[1]);
+        for (int c = 1; c <= nc && !cs; ++c) {
+          int64_t a = -1, b = -1;
+          for (int q = 0; q < m.nfpe; ++q) {
+            if (f0[q] != e && col[f0[q]] == c) a = f0[q];
+            if (f1[q] != e && col[f1[q]] == c) b = f1[q];
+          }
+          if (a >= 0 && b >= 0) {
+            cs = c;
+            fa = a;
+            fb = b;
+          }
+        }
+      }
+      if (cs) {
+        col[e] = (int8_t)cs;
+        col[fa] = -1;
+        col[fb] = -1;
+        push(fa);
+        push(fb);
+        ++st.breaks;
+      } else {
+        push(e);  // no shared color (another conflict touches e): retry later
+        ++st.deferrals;
+      }
+      break;
+    }
+  }
+  m.color.swap(col);
+  m.ncolors = nc;
+  m.perfect = true;
+  m.dirty = true;
+  return st;
+}
+
+int color_faces_naive(Mesh& m) {
+  std::vector<int8_t> col(m.ns, -1);
+  Colorer C(m, kMaxColors, col);
+  int maxc = 0;
+  for (int64_t k = 0; k < m.ns; ++k) {
+    uint32_t u = C.used(k);
+    int c = 1;
+    while (u & (1u << c)) ++c;
+    if (c > kMaxColors) throw Error{DGC_ERR_COLORING_LIMIT, "naive coloring needs too many colors"};
+    col[k] = (int8_t)c;
+    maxc = std::max(maxc, c);
+  }
+  m.color.swap(col);
+  m.ncolors = maxc;
+  m.perfect = (maxc == m.nfpe);
+  m.dirty = true;
+  return maxc;
+}
+
+// ---------------------------------------------------------------------------
+// Reordering (Sec. 5): color-major edges (stable), color-1 renumbering of
+// elements (left of the k-th color-1 edge -> k, rights of interior color-1
+// edges -> N1, N1+1, ... in the same order; elements no color-1 edge reaches
+// follow in original order), then ascending new left element within each
+// color >= 2 (ties by original id).  With renumber = false the elements keep
+// their ids; with reorder_left = false colors >= 2 keep original edge order.
+// ---------------------------------------------------------------------------
+void reorder(Mesh& m, bool renumber, bool reorder_left) {
+  const int nc = m.ncolors;
+  m.color_off.assign(nc + 1, 0);
+  for (int64_t k = 0; k < m.ns; ++k) m.color_off[m.color[k]]++;
+  std::partial_sum(m.color_off.begin(), m.color_off.end(), m.color_off.begin());
+  std::vector<int32_t> order(m.ns);
+  {
+    std::vector<int32_t> next(m.color_off.begin(), m.color_off.end() - 1);
+    for (int64_t k = 0; k < m.ns; ++k) order[next[m.color[k] - 1]++] = (int32_t)k;
+  }
+  std::vector<int32_t>& en = m.elem_new_of_old;
+  en.assign(m.ne, -1);
+  if (renumber) {
+    int32_t id = 0, n1 = m.color_off[1];
+    for (int32_t i = 0; i < n1; ++i) {
+      int32_t l = m.sl[order[i]];
+      if (en[l] < 0) en[l] = id++;
+    }
+    for (int32_t i = 0; i < n1; ++i) {
+      int32_t r = m.sr[order[i]];
+      if (r >= 0 && en[r] < 0) en[r] = id++;
+    }
+    for (int64_t e = 0; e < m.ne; ++e)
+      if (en[e] < 0) en[e] = id++;
+  } else {
+    std::iota(en.begin(), en.end(), 0);
+  }
+  if (reorder_left) {
+    for (int c = 2; c <= nc; ++c)
+      std::sort(order.begin() + m.color_off[c - 1], order.begin() + m.color_off[c],
+                [&](int32_t a, int32_t b) {
+                  int32_t la = en[m.sl[a]], lb = en[m.sl[b]];
+                  return la != lb ? la < lb : a < b;
+                });
+  }
+  m.side_old_of_new = order;
+  m.side_new_of_old.assign(m.ns, 0);
+  for (int64_t i = 0; i < m.ns; ++i) m.side_new_of_old[order[i]] = (int32_t)i;
+  m.dirty = true;
+}
+
+// ---------------------------------------------------------------------------
+// Volume points and L2 projection (initial states)
+// ---------------------------------------------------------------------------
+void vol_points(const Mesh& m, double* xyz) {
+  const RefTables& T = m.tab;
+  for (int64_t e = 0; e < m.ne; ++e) {
+    const double* X = &m.X[(size_t)e * m.nvpe * m.dim];
+    for (int q = 0; q < T.nqv; ++q) {
+      double rs[3] = {T.vr[q], T.vs[q], T.vt[q]};
+      for (int a = 0; a < m.dim; ++a) {
+        double v = X[a];
+        for (int k = 0; k < m.dim; ++k) v += (X[(k + 1) * m.dim + a] - X[a]) * rs[k];
+        xyz[((size_t)e * T.nqv + q) * m.dim + a] = v;
+      }
+    }
+  }
+}
+
+void project(const Mesh& m, const double* vals, double* c) {
+  const RefTables& T = m.tab;
+  const int M = m.M, np = T.np;
+  for (int64_t e = 0; e < m.ne; ++e) {
+    double* ce = c + (size_t)e * M * np;
+    std::fill(ce, ce + M * np, 0.0);
+    for (int q = 0; q < T.nqv; ++q)
+      for (int k = 0; k < M; ++k) {
+        double v = T.vw[q] * vals[((size_t)e * T.nqv + q) * M + k];
+        for (int j = 0; j < np; ++j) ce[k * np + j] += v * T.phiV[(size_t)q * np + j];
+      }
+  }
+}
+
+}  // namespace dgc

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of the C ABI in include/dgc.h (same function names).
+
+Only argument marshalling lives here: numpy arrays are passed as host
+pointers, torch CUDA tensors (or integers) as device pointers, and the current
+torch stream as the ``cudaStream_t``.  All computation happens in the compiled
+library; if it is missing, importing this module's ``lib()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build_lib
+
+DGC_FP64 = 0
+DGC_FP32_MIXED = 1
+DGC_OPT_FUSE = 0
+DGC_OPT_EDGES_PER_BLOCK = 1
+DGC_OPT_THREADS_PER_EDGE = 2
+DGC_OPT_PROFILE = 3
+KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
+
+STATUS = {0: "DGC_OK", 1: "DGC_ERR_ARG", 2: "DGC_ERR_MESH", 3: "DGC_ERR_COLORING_LIMIT",
+          4: "DGC_ERR_UNSUPPORTED", 5: "DGC_ERR_CUDA", 6: "DGC_ERR_OOM", 7: "DGC_ERR_NONFINITE"}
+
+# Every function the header declares, with its ctypes signature.
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32P = C.POINTER(C.c_int32)
+_I64P = C.POINTER(C.c_int64)
+_DP = C.POINTER(C.c_double)
+SIGNATURES = {
+    "dgc_mesh_create": (C.c_int, [C.c_int, C.c_int, _I64, _DP, _I64, _I32P, _DP, C.POINTER(_P)]),
+    "dgc_color_edges": (C.c_int, [_P, C.c_uint64, _I64, _I32P, _I64P]),
+    "dgc_color_edges_naive": (C.c_int, [_P, C.c_int, C.c_int, _I32P, _I64P]),
+    "dgc_mesh_info": (C.c_int, [_P, _I64P]),
+    "dgc_get_sides": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]),
+    "dgc_get_ordering": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), _I32P]),
+    "dgc_vol_points": (C.c_int, [_P, _DP]),
+    "dgc_project": (C.c_int, [_P, _DP, _DP]),
+    "dgc_state_size": (C.c_int, [_P, _I64P]),
+    "dgc_workspace_size": (C.c_int, [_P, C.c_int, _I64P]),
+    "dgc_import_state": (C.c_int, [_P, _DP, _P, _P]),
+    "dgc_export_state": (C.c_int, [_P, _P, _DP, _P]),
+    "dgc_rhs": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dgc_cfl_dt": (C.c_int, [_P, _P, C.c_double, _P, _P]),
+    "dgc_rk_step": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P, _P]),
+    "dgc_rhs_atomic": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dgc_rhs_two_pass": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "dgc_two_pass_buffer_bytes": (C.c_int, [_I64, C.c_int, C.c_int, C.c_int, _I64P]),
+    "dgc_set_option": (C.c_int, [_P, C.c_int, _I64]),
+    "dgc_profile_collect": (C.c_int, [_P, _DP, _I64P]),
+    "dgc_last_launch_count": (C.c_int, [_P, _I64P]),
+    "dgc_last_error": (C.c_char_p, []),
+    "dgc_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+class DgcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib(build: bool = True):
+    """Load the compiled library (building it first if asked); raises if it is unavailable."""
+    global _lib
+    if _lib is None:
+        path = _build_lib.LIB
+        if build:
+            path = _build_lib.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise DgcError(status, lib().dgc_last_error().decode())
+
+
+def _dptr(a) -> int:
+    """Device pointer of a torch tensor (or an integer address)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    return a.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _h(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+# --- the C ABI, one wrapper per function -----------------------------------------------
+
+def dgc_mesh_create(dim: int, p: int, xyz, ev, periodic_len=None):
+    xyz, xp = _h(xyz, np.float64)
+    ev, ep = _h(ev, np.int32)
+    lp = None
+    if periodic_len is not None:
+        L, lp = _h(periodic_len, np.float64)
+    out = _P()
+    _check(lib().dgc_mesh_create(dim, p, xyz.shape[0], xp, ev.shape[0], ep, lp, C.byref(out)))
+    return out
+
+
+def dgc_color_edges(mesh, seed: int, max_swaps: int = 0):
+    nc = C.c_int32()
+    per = (C.c_int64 * 8)()
+    _check(lib().dgc_color_edges(mesh, seed, max_swaps, C.byref(nc), per))
+    return nc.value, list(per)[: nc.value]
+
+
+def dgc_color_edges_naive(mesh, renumber: bool = True, reorder: bool = True):
+    nc = C.c_int32()
+    per = (C.c_int64 * 8)()
+    _check(lib().dgc_color_edges_naive(mesh, int(renumber), int(reorder), C.byref(nc), per))
+    return nc.value, list(per)[: min(nc.value, 8)]
+
+
+def dgc_mesh_info(mesh) -> dict:
+    a = (C.c_int64 * 10)()
+    _check(lib().dgc_mesh_info(mesh, a))
+    keys = ["ne", "ns", "np", "M", "nqf", "nqv", "ncolors", "dim", "p", "perfect"]
+    return dict(zip(keys, list(a)))
+
+
+def dgc_get_sides(mesh):
+    ns = dgc_mesh_info(mesh)["ns"]
+    l, r = np.zeros(ns, np.int32), np.zeros(ns, np.int32)
+    ql, qr = np.zeros(ns, np.int8), np.zeros(ns, np.int8)
+    _check(lib().dgc_get_sides(mesh, *(x.ctypes.data_as(_I32P) for x in (l, r)),
+                               *(x.ctypes.data_as(C.POINTER(C.c_int8)) for x in (ql, qr))))
+    return l, r, ql, qr
+
+
+def dgc_get_ordering(mesh):
+    info = dgc_mesh_info(mesh)
+    en = np.zeros(info["ne"], np.int32)
+    sn = np.zeros(info["ns"], np.int32)
+    col = np.zeros(info["ns"], np.int8)
+    off = np.zeros(info["ncolors"] + 1, np.int32)
+    _check(lib().dgc_get_ordering(mesh, en.ctypes.data_as(_I32P), sn.ctypes.data_as(_I32P),
+                                  col.ctypes.data_as(C.POINTER(C.c_int8)), off.ctypes.data_as(_I32P)))
+    return en, sn, col, off
+
+
+def dgc_vol_points(mesh) -> np.ndarray:
+    info = dgc_mesh_info(mesh)
+    out = np.zeros((info["ne"], info["nqv"], info["dim"]))
+    _check(lib().dgc_vol_points(mesh, out.ctypes.data_as(_DP)))
+    return out
+
+
+def dgc_project(mesh, vals) -> np.ndarray:
+    info = dgc_mesh_info(mesh)
+    vals, vp = _h(vals, np.float64)
+    out = np.zeros((info["ne"], info["M"], info["np"]))
+    _check(lib().dgc_project(mesh, vp, out.ctypes.data_as(_DP)))
+    return out
+
+
+def dgc_state_size(mesh) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_state_size(mesh, C.byref(b)))
+    return b.value
+
+
+def dgc_workspace_size(mesh, prec: int) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_workspace_size(mesh, prec, C.byref(b)))
+    return b.value
+
+
+def dgc_import_state(mesh, c_host, c_dev, stream=None):
+    c_host, cp = _h(c_host, np.float64)
+    _check(lib().dgc_import_state(mesh, cp, _dptr(c_dev), _stream(stream)))
+
+
+def dgc_export_state(mesh, c_dev, out=None, stream=None):
+    info = dgc_mesh_info(mesh)
+    if out is None:
+        out = np.zeros((info["ne"], info["M"], info["np"]))
+    _check(lib().dgc_export_state(mesh, _dptr(c_dev), out.ctypes.data_as(_DP), _stream(stream)))
+    return out
+
+
+def dgc_rhs(mesh, prec: int, c_dev, rhs_dev, stream=None):
+    _check(lib().dgc_rhs(mesh, prec, _dptr(c_dev), _dptr(rhs_dev), _stream(stream)))
+
+
+def dgc_cfl_dt(mesh, c_dev, cfl: float, dt_dev, stream=None):
+    _check(lib().dgc_cfl_dt(mesh, _dptr(c_dev), cfl, _dptr(dt_dev), _stream(stream)))
+
+
+def dgc_rk_step(mesh, prec: int, c_dev, cfl: float, dt_dev, workspace_dev, stream=None):
+    _check(lib().dgc_rk_step(mesh, prec, _dptr(c_dev), cfl, _dptr(dt_dev), _dptr(workspace_dev),
+                             _stream(stream)))
+
+
+def dgc_rhs_atomic(mesh, prec: int, c_dev, rhs_dev, stream=None):
+    _check(lib().dgc_rhs_atomic(mesh, prec, _dptr(c_dev), _dptr(rhs_dev), _stream(stream)))
+
+
+def dgc_rhs_two_pass(mesh, prec: int, c_dev, rhs_dev, buffer_dev, stream=None):
+    _check(lib().dgc_rhs_two_pass(mesh, prec, _dptr(c_dev), _dptr(rhs_dev), _dptr(buffer_dev),
+                                  _stream(stream)))
+
+
+def dgc_two_pass_buffer_bytes(sides: int, np_: int, neq: int, word_bytes: int = 8) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_two_pass_buffer_bytes(sides, np_, neq, word_bytes, C.byref(b)))
+    return b.value
+
+
+def dgc_set_option(mesh, opt: int, value: int):
+    _check(lib().dgc_set_option(mesh, opt, value))
+
+
+def dgc_profile_collect(mesh) -> dict:
+    ms = (C.c_double * 16)()
+    n = (C.c_int64 * 16)()
+    _check(lib().dgc_profile_collect(mesh, ms, n))
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES) if n[i] > 0}
+
+
+def dgc_last_launch_count(mesh) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_last_launch_count(mesh, C.byref(b)))
+    return b.value
+
+
+def dgc_last_error() -> str:
+    return lib().dgc_last_error().decode()
+
+
+def dgc_destroy(mesh):
+    if mesh:
+        lib().dgc_destroy(mesh)
+
+
+class Mesh:
+    """Owns a dgc_mesh handle; convenience accessors over the functions above."""
+
+    def __init__(self, dim, p, xyz, ev, periodic_len=None):
+        self.h = dgc_mesh_create(dim, p, xyz, ev, periodic_len)
+        self.info = dgc_mesh_info(self.h)
+
+    @classmethod
+    def from_input(cls, mi, p):
+        return cls(mi.dim, p, mi.xyz, mi.ev, mi.periodic_len)
+
+    def color(self, seed: int, max_swaps: int = 0):
+        r = dgc_color_edges(self.h, seed, max_swaps)
+        self.info = dgc_mesh_info(self.h)
+        return r
+
+    def state_shape(self):
+        return (self.info["ne"], self.info["M"], self.info["np"])
+
+    def close(self):
+        if self.h:
+            dgc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

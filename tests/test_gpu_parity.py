@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (relative L2 over all compared coefficients, oracle as reference):
+FP64 right-hand side 1e-12; FP32-mixed right-hand side 1e-5; FP64 time step
+1e-13; one FP64 RK step: the state change du within 1e-11; FP32-mixed du within
+1e-5.  Sizes span many tiles with a ragged last tile; the 1,048,352-triangle
+p=3 mesh is checked on sampled elements in the launch configuration the
+benchmark times.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1601_07613_gb300 import dgc
+from paper_1601_07613_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    dgc.lib()
+    return torch, torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+class Run:
+    """One mesh on the device: import a host state, call an entry point, export."""
+
+    def __init__(self, torch_dev, mi, p, seed=1601, fuse=True, epb=None):
+        self.torch, self.dev = torch_dev
+        self.mi, self.p = mi, p
+        self.m = dgc.Mesh.from_input(mi, p)
+        self.m.color(seed)
+        dgc.dgc_set_option(self.m.h, dgc.DGC_OPT_FUSE, int(fuse))
+        if epb:
+            dgc.dgc_set_option(self.m.h, dgc.DGC_OPT_EDGES_PER_BLOCK, epb)
+        shape = self.m.state_shape()
+        T = self.torch
+        self.c = T.empty(shape, dtype=T.float64, device=self.dev)
+        self.r = T.empty(shape, dtype=T.float64, device=self.dev)
+
+    def load(self, c_host):
+        dgc.dgc_import_state(self.m.h, c_host, self.c)
+
+    def rhs(self, prec=dgc.DGC_FP64, kind="colored"):
+        self.r.fill_(float("nan"))
+        if kind == "colored":
+            dgc.dgc_rhs(self.m.h, prec, self.c, self.r)
+        elif kind == "atomic":
+            dgc.dgc_rhs_atomic(self.m.h, prec, self.c, self.r)
+        else:
+            info = self.m.info
+            nb = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
+            buf = self.torch.empty(nb // 8, dtype=self.torch.float64, device=self.dev)
+            dgc.dgc_rhs_two_pass(self.m.h, prec, self.c, self.r, buf)
+        self.torch.cuda.synchronize()
+        return dgc.dgc_export_state(self.m.h, self.r)
+
+    def dt(self, cfl):
+        d = self.torch.zeros(1, dtype=self.torch.float64, device=self.dev)
+        dgc.dgc_cfl_dt(self.m.h, self.c, cfl, d)
+        return float(d.item())
+
+    def rk(self, prec, cfl, steps=1):
+        T = self.torch
+        ws = T.empty(dgc.dgc_workspace_size(self.m.h, prec) // 8 + 64, dtype=T.float64, device=self.dev)
+        d = T.zeros(1, dtype=T.float64, device=self.dev)
+        for _ in range(steps):
+            dgc.dgc_rk_step(self.m.h, prec, self.c, cfl, d, ws)
+        T.cuda.synchronize()
+        return dgc.dgc_export_state(self.m.h, self.c), float(d.item())
+
+    def close(self):
+        self.m.close()
+
+
+def state_for(mi, np_, seed, amp=3e-3):
+    return W.random_state(mi.ne, mi.dim + 2, np_, seed=seed, amp=amp)
+
+
+CASES = [
+    ("periodic37j", lambda: W.periodic_square_tri(37, jitter=0.2, seed=3)),  # 1369 edges/color
+    ("open29j", lambda: W.open_square_tri(29, jitter=0.2, seed=4)),          # boundary edges
+]
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("name,make", CASES)
+@pytest.mark.parametrize("fuse", [True, False])
+def test_rhs_fp64_matches_oracle(torch_dev, oracle_mod, p, name, make, fuse):
+    mi = make()
+    run = Run(torch_dev, mi, p, fuse=fuse)
+    c = state_for(mi, run.m.info["np"], seed=p)
+    run.load(c)
+    got = run.rhs(dgc.DGC_FP64)
+    ref = oracle_mod.OracleMesh.from_input(mi).rhs(p, c)
+    assert rel(got, ref) < 1e-12
+    run.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("name,make", CASES)
+def test_rhs_fp32_mixed_matches_oracle(torch_dev, oracle_mod, p, name, make):
+    mi = make()
+    run = Run(torch_dev, mi, p)
+    c = state_for(mi, run.m.info["np"], seed=10 + p)
+    run.load(c)
+    got = run.rhs(dgc.DGC_FP32_MIXED)
+    ref = oracle_mod.OracleMesh.from_input(mi).rhs(p, c)
+    assert rel(got, ref) < 1e-5
+    run.close()
+
+
+@pytest.mark.parametrize("epb", [16, 64, 256, 512])
+def test_rhs_tile_shapes(torch_dev, oracle_mod, epb):
+    mi = W.periodic_square_tri(23, jitter=0.2, seed=5)
+    run = Run(torch_dev, mi, 3, epb=epb)
+    c = state_for(mi, run.m.info["np"], seed=5)
+    run.load(c)
+    ref = oracle_mod.OracleMesh.from_input(mi).rhs(3, c)
+    assert rel(run.rhs(dgc.DGC_FP64), ref) < 1e-12
+    run.close()
+
+
+@pytest.mark.parametrize("kind", ["atomic", "two_pass"])
+@pytest.mark.parametrize("p", [1, 3])
+def test_comparators_match_oracle(torch_dev, oracle_mod, kind, p):
+    mi = W.periodic_square_tri(31, jitter=0.2, seed=6)
+    run = Run(torch_dev, mi, p)
+    c = state_for(mi, run.m.info["np"], seed=6)
+    run.load(c)
+    ref = oracle_mod.OracleMesh.from_input(mi).rhs(p, c)
+    assert rel(run.rhs(dgc.DGC_FP64, kind), ref) < 1e-12
+    assert rel(run.rhs(dgc.DGC_FP32_MIXED, kind), ref) < 1e-5
+    run.close()
+
+
+def test_colored_rhs_is_deterministic(torch_dev):
+    mi = W.periodic_square_tri(40, jitter=0.2, seed=7)
+    run = Run(torch_dev, mi, 3)
+    run.load(state_for(mi, run.m.info["np"], seed=7))
+    first = run.rhs(dgc.DGC_FP64)
+    for _ in range(9):
+        assert np.array_equal(run.rhs(dgc.DGC_FP64), first)
+    run.close()
+
+
+def test_freestream_on_device(torch_dev):
+    mi = W.periodic_square_tri(30, jitter=0.2, seed=8)
+    run = Run(torch_dev, mi, 3)
+    c = np.zeros(run.m.state_shape())
+    c[:, :, 0] = np.array([1.1, 0.3, -0.2, 2.6]) / np.sqrt(2.0)
+    run.load(c)
+    h = 1.0 / 30
+    for prec, tol in ((dgc.DGC_FP64, 1e-13), (dgc.DGC_FP32_MIXED, 1e-6)):
+        r = run.rhs(prec)
+        assert np.abs(r).max() * (0.5 * h * h) / (3.4 * h * 3.0) < tol
+    run.close()
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_cfl_dt_matches_oracle(torch_dev, oracle_mod, p):
+    mi = W.periodic_square_tri(33, jitter=0.2, seed=9)
+    run = Run(torch_dev, mi, p)
+    c = state_for(mi, run.m.info["np"], seed=9, amp=2e-2)
+    run.load(c)
+    ref = oracle_mod.OracleMesh.from_input(mi).dt(p, c, 0.3)
+    assert abs(run.dt(0.3) - ref) < 1e-13 * ref
+    run.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("fuse", [True, False])
+def test_rk_step_matches_oracle(torch_dev, oracle_mod, p, fuse):
+    mi = W.periodic_square_tri(26, jitter=0.2, seed=10)
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz, _, _ = om.eval_points(p)
+    c = om.project(p, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=5.0))
+    ref, dt_ref = om.rk_step(p, c, 0.3)
+    for prec, tol in ((dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)):
+        run = Run(torch_dev, mi, p, fuse=fuse)
+        run.load(c)
+        got, dt = run.rk(prec, 0.3)
+        assert abs(dt - dt_ref) < 1e-13 * dt_ref
+        assert rel(got - c, ref - c) < tol
+        run.close()
+
+
+def test_rk_steps_conserve_and_stay_close(torch_dev, oracle_mod):
+    """Ten steps on the p=1 32x32 vortex (configuration 1): FP64 tracks the oracle."""
+    mi = W.periodic_square_tri(32)
+    p = 1
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz, _, _ = om.eval_points(p)
+    c0 = om.project(p, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=5.0))
+    ref = c0
+    for _ in range(10):
+        ref, _ = om.rk_step(p, ref, 0.3)
+    run = Run(torch_dev, mi, p)
+    run.load(c0)
+    got, _ = run.rk(dgc.DGC_FP64, 0.3, steps=10)
+    assert rel(got - c0, ref - c0) < 1e-10
+    detj = om.detj()
+    np.testing.assert_allclose((detj[:, None] * got[:, :, 0]).sum(0), (detj[:, None] * c0[:, :, 0]).sum(0),
+                               rtol=1e-13)
+    run.close()
+
+
+# ------------------------------------------------------------------------------------------
+# Full size: 1,048,352 triangles, p = 3 (the benchmark's workload), sampled elements
+# ------------------------------------------------------------------------------------------
+
+def _rings(om, seeds, depth):
+    l, r, _, _ = om.sides()
+    nbr = [[] for _ in range(om.ne)]
+    for a, b in zip(l, r):
+        if b >= 0:
+            nbr[a].append(b)
+            nbr[b].append(a)
+    sets = [np.unique(seeds)]
+    for _ in range(depth):
+        cur = set(sets[-1].tolist())
+        for e in sets[-1]:
+            cur.update(nbr[e])
+        sets.append(np.array(sorted(cur)))
+    return sets
+
+
+@pytest.fixture(scope="module")
+def big(torch_dev, oracle_mod):
+    cfg = W.jittered_square_vortex_p3_724x724()
+    mi, p = cfg["mesh"], cfg["p"]
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz, _, _ = om.eval_points(p)
+    c = om.project(p, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=cfg["beta"]))
+    c += W.uniform_perturbation(c.shape, cfg["perturb_seed"], cfg["perturb"])
+    run = Run(torch_dev, mi, p, seed=1601)
+    assert run.m.info["ne"] == 1_048_352 and run.m.info["ns"] == 1_572_528
+    yield run, om, c
+    run.close()
+
+
+def test_full_size_rhs_sampled(big):
+    run, om, c = big
+    run.load(c)
+    sample = np.random.default_rng(0).choice(om.ne, 3000, replace=False)
+    ref = om.rhs(3, c, elems=sample)
+    got64 = run.rhs(dgc.DGC_FP64)[sample]
+    got32 = run.rhs(dgc.DGC_FP32_MIXED)[sample]
+    assert rel(got64, ref) < 1e-12
+    assert rel(got32, ref) < 1e-5
+
+
+def test_full_size_rk_step_sampled(big, oracle_mod):
+    """One SSP-RK3 step (fused colors, FP64 and FP32-mixed) checked on sampled
+    elements: the oracle evaluates each stage on the element rings it needs."""
+    run, om, c = big
+    p = 3
+    dt = om.dt(p, c, 0.3)
+    seeds = np.random.default_rng(1).choice(om.ne, 200, replace=False)
+    s0, s1, s2, _ = _rings(om, seeds, 3)
+    u1 = np.zeros_like(c)
+    u1[s2] = c[s2] + dt * om.rhs(p, c, elems=s2)
+    u2 = np.zeros_like(c)
+    u2[s1] = 0.75 * c[s1] + 0.25 * (u1[s1] + dt * om.rhs(p, u1, elems=s1))
+    u3 = c[s0] / 3.0 + 2.0 / 3.0 * (u2[s0] + dt * om.rhs(p, u2, elems=s0))
+    for prec, tol in ((dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)):
+        run.load(c)
+        got, dtg = run.rk(prec, 0.3)
+        assert abs(dtg - dt) < 1e-13 * dt
+        assert rel(got[s0] - c[s0], u3 - c[s0]) < tol

@@ -1,0 +1,159 @@
+"""CPU checks of the CUDA library's host side and of its C ABI (no GPU calls).
+
+* the shared library loads and exports every function include/dgc.h declares;
+* its edge table, coloring and reordering equal the oracle's bit for bit;
+* its host L2 projection (own quadrature and basis tables) agrees with the
+  oracle's to rounding;
+* the two-pass buffer size reproduces Table 4;
+* error statuses for bad meshes, the swap cap and calls out of order.
+"""
+
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1601_07613_gb300 import dgc
+from paper_1601_07613_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_values.json")))
+
+
+@pytest.fixture(scope="module")
+def L():
+    return dgc.lib()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "dgc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_function(L):
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in dgc.SIGNATURES, n
+
+
+MESHES = [
+    ("periodic3", lambda: W.periodic_square_tri(3)),
+    ("periodic7j", lambda: W.periodic_square_tri(7, jitter=0.2, seed=7)),
+    ("periodic64j", lambda: W.periodic_square_tri(64, jitter=0.2, seed=1601)),
+    ("open9j", lambda: W.open_square_tri(9, jitter=0.2, seed=9)),
+    ("open40", lambda: W.open_square_tri(40)),
+    ("tet3", lambda: W.periodic_cube_tet(3)),
+    ("tet5", lambda: W.periodic_cube_tet(5)),
+]
+
+
+@pytest.mark.parametrize("name,make", MESHES)
+@pytest.mark.parametrize("seed", [0, 1, 1601])
+def test_coloring_and_ordering_bit_exact_vs_oracle(oracle_mod, name, make, seed):
+    mi = make()
+    p = 1
+    m = dgc.Mesh.from_input(mi, p)
+    om = oracle_mod.OracleMesh.from_input(mi)
+    for a, b in zip(dgc.dgc_get_sides(m.h), om.sides()):
+        assert np.array_equal(a, b)
+    nc, per = m.color(seed)
+    col_o, _ = om.color(mi.dim + 1, seed)
+    en, sn, col, off = dgc.dgc_get_ordering(m.h)
+    assert nc == mi.dim + 1
+    assert np.array_equal(col, col_o)
+    en_o, sn_o, off_o = om.reorder(col_o, nc)
+    assert np.array_equal(en, en_o) and np.array_equal(sn, sn_o) and np.array_equal(off, off_o)
+    assert list(np.diff(off)) == per
+    m.close()
+
+
+def test_coloring_bit_exact_large(oracle_mod):
+    """The configuration-2 mesh family at a quarter of the size (262k triangles)."""
+    mi = W.periodic_square_tri(362, jitter=0.2, seed=1601)
+    m = dgc.Mesh.from_input(mi, 3)
+    om = oracle_mod.OracleMesh.from_input(mi)
+    m.color(1601)
+    col_o, _ = om.color(3, 1601)
+    en, sn, col, off = dgc.dgc_get_ordering(m.h)
+    assert np.array_equal(col, col_o)
+    en_o, sn_o, _ = om.reorder(col_o, 3)
+    assert np.array_equal(en, en_o) and np.array_equal(sn, sn_o)
+    assert list(np.diff(off)) == [mi.ne // 2] * 3
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_projection_matches_oracle(oracle_mod, p):
+    mi = W.periodic_square_tri(10, jitter=0.2, seed=2)
+    m = dgc.Mesh.from_input(mi, p)
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz = dgc.dgc_vol_points(m.h)
+    xyz_o, _, _ = om.eval_points(p)
+    np.testing.assert_allclose(xyz, xyz_o, atol=1e-15)
+    vals = W.vortex_field(xyz[..., 0], xyz[..., 1])
+    c = dgc.dgc_project(m.h, vals)
+    c_o = om.project(p, vals)
+    np.testing.assert_allclose(c, c_o, atol=1e-13 * np.abs(c_o).max())
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_projection_matches_oracle_tet(oracle_mod, p):
+    mi = W.periodic_cube_tet(3)
+    m = dgc.Mesh.from_input(mi, p)
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz = dgc.dgc_vol_points(m.h)
+    vals = W.vortex_tube_field(xyz[..., 0], xyz[..., 1], xyz[..., 2])
+    np.testing.assert_allclose(dgc.dgc_project(m.h, vals), om.project(p, vals), atol=1e-12)
+
+
+def test_table4_buffer_memory(L):
+    row = GOLDEN["table4_memory_saved_gb"]
+    for p, gb in zip(row["p"], row["gb"]):
+        np_ = (p + 1) * (p + 2) // 2
+        b = dgc.dgc_two_pass_buffer_bytes(row["sides"], np_, row["neq"], 8)
+        # the table truncates to two decimals (1.4493 GB is printed as 1.44)
+        assert int(b / 1e9 * 100) / 100 == gb
+
+
+def test_error_statuses(L):
+    mi = W.periodic_square_tri(4)
+    bad = mi.ev.copy()
+    bad[3] = bad[3, ::-1]
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_mesh_create(2, 1, mi.xyz, bad, mi.periodic_len)
+    assert e.value.status == 2
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_mesh_create(2, 1, mi.xyz, np.concatenate([mi.ev, mi.ev[:1]]), mi.periodic_len)
+    assert e.value.status == 2
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_mesh_create(2, 7, mi.xyz, mi.ev, mi.periodic_len)
+    assert e.value.status == 4
+    m = dgc.Mesh.from_input(W.periodic_square_tri(24), 1)
+    with pytest.raises(dgc.DgcError) as e:
+        m.color(5, max_swaps=1)
+    assert e.value.status == 3
+    # device calls before coloring fail on the host, before any device work
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rhs(m.h, dgc.DGC_FP64, 4096, 8192, 0)
+    assert e.value.status == 1
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rhs(m.h, dgc.DGC_FP64, 4097, 8192, 0)  # misaligned
+    assert e.value.status == 1
+    with pytest.raises(dgc.DgcError):
+        dgc.dgc_set_option(m.h, dgc.DGC_OPT_EDGES_PER_BLOCK, 7)
+    m.close()
+
+
+def test_naive_coloring_ablation(L):
+    mi = W.periodic_square_tri(30, jitter=0.2, seed=2)
+    ev = mi.ev[np.random.default_rng(0).permutation(mi.ne)]
+    m = dgc.Mesh(2, 1, mi.xyz, ev, mi.periodic_len)
+    nc, per = dgc.dgc_color_edges_naive(m.h, True, True)
+    assert 3 < nc <= 5 and sum(per) == m.info["ns"]
+    info = dgc.dgc_mesh_info(m.h)
+    assert info["ncolors"] == nc and info["perfect"] == 0
+    m.close()
