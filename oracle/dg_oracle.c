@@ -938,6 +938,26 @@ static void face_geometry(const orc_mesh *m, int64_t e, int q, const orc_rules *
     for (int a = 0; a < dim; ++a) F->x[i * 3 + a] = A[a] + R->fa[i] * u[a] + R->fb[i] * v[a];
 }
 
+/* Reading (Algorithm 1 evaluates one numerical flux per edge or face and adds
+ * it to both elements): a face's quadrature points are the ones of its left
+ * element's parameterisation of that face, for both elements.  On a triangle
+ * edge the Gauss points are symmetric and either side gives the same points;
+ * on a tetrahedral face the collapsed rule is not symmetric under a
+ * permutation of the face's vertices, and a per-element choice would evaluate
+ * the flux at different points on the two sides (not conservative). */
+static void face_points_of_left(const orc_mesh *m, int64_t e, int f, const orc_rules *R, orc_face *F) {
+  int32_t s = m->es[e * m->nfpe + f];
+  int64_t l = m->sl[s];
+  if (l == e) return;
+  int dim = m->dim, fv[3];
+  const double *X = m->X + l * m->nvpe * dim;
+  face_verts(dim, m->sql[s], fv);
+  const double *A = X + fv[0] * dim, *B = X + fv[1] * dim, *C = dim == 3 ? X + fv[2] * dim : A;
+  for (int i = 0; i < R->nf; ++i)
+    for (int a = 0; a < dim; ++a)
+      F->x[i * 3 + a] = A[a] + R->fa[i] * (B[a] - A[a]) + R->fb[i] * (C[a] - A[a]);
+}
+
 /* rhs[e][k][j] = d c_{e,k,j} / dt for the listed elements (all when
  * nelem < 0; then rhs is [E][M][Np], else [nelem][M][Np] in list order).
  * c is [E][M][Np] in original element order.  kind 0 = Euler, 1 = linear
@@ -991,7 +1011,8 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
     }
     /* surface integrals: - (1/detJ) sum_faces |f| sum_q w_q phi_j(x_q) F*(U_e, U_nb, n) */
     for (int f = 0; f < m->nfpe; ++f) {
-      face_geometry(m, e, f, &R, &F);
+      face_geometry(m, e, f, &R, &F);  /* own outward normal and measure */
+      face_points_of_left(m, e, f, &R, &F);
       int32_t nb = m->enb[e * m->nfpe + f];
       double scale = F.meas / m->detJ[e];
       for (int q = 0; q < F.nq; ++q) {

@@ -157,6 +157,47 @@ def periodic_cube_tet(n: int) -> MeshInput:
                      meta={"n": n})
 
 
+def open_cube_tet(n: int, jitter: float = 0.0, seed: int | None = None) -> MeshInput:
+    """Non-periodic ``n^3`` unit cube split like ``periodic_cube_tet``.
+
+    It has ``(n+1)^3`` vertices and boundary faces on the six sides; only
+    interior vertices are jittered.
+    """
+    h = 1.0 / n
+    g = np.arange(n + 1)
+    kk, jj, ii = np.meshgrid(g, g, g, indexing="ij")
+    xyz = np.stack([ii.ravel() * h, jj.ravel() * h, kk.ravel() * h], axis=1).astype(np.float64)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+        inner = np.all((xyz > 0.5 * h) & (xyz < 1.0 - 0.5 * h), axis=1)
+        xyz[inner] += d[inner]
+    c = np.arange(n)
+    ck, cj, ci = np.meshgrid(c, c, c, indexing="ij")
+    cells = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)
+
+    def vid(p):
+        return (p[:, 2] * (n + 1) + p[:, 1]) * (n + 1) + p[:, 0]
+
+    tets = []
+    for perm in _KUHN_PERMS:
+        p0 = cells.copy()
+        p1 = p0.copy()
+        p1[:, perm[0]] += 1
+        p2 = p1.copy()
+        p2[:, perm[1]] += 1
+        p3 = p2.copy()
+        p3[:, perm[2]] += 1
+        verts = [vid(p0), vid(p1), vid(p2), vid(p3)]
+        e1 = np.eye(3)[perm[0]]
+        e2 = e1 + np.eye(3)[perm[1]]
+        if np.linalg.det(np.stack([e1, e2, np.ones(3)])) < 0:
+            verts[1], verts[2] = verts[2], verts[1]
+        tets.append(np.stack(verts, axis=1))
+    ev = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return MeshInput(3, xyz, ev, None, name=f"open_cube_tet_{n}^3x6", meta={"n": n})
+
+
 def random_state(ne: int, m: int, np_: int, seed: int, amp: float = 3e-3,
                  mean=(0.7, 0.1, -0.05, 1.8), spread: float = 0.05) -> np.ndarray:
     """Random modal coefficients ``c[e][m][j]`` (float64), with a positive mean mode.

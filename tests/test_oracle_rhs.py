@@ -183,3 +183,52 @@ def test_design_order_vortex(oracle_mod, p, ns):
     e = [_vortex_error(oracle_mod, n, p, 0.02, 0.3) for n in ns]
     order = np.log(e[0] / e[1]) / np.log(ns[1] / ns[0])
     assert order > p + 0.6, (e, order)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_conservation_periodic_tet(oracle_mod, p):
+    """Face contributions cancel on a closed tetrahedral mesh: one flux per
+    face, evaluated at one set of points for both elements."""
+    m = oracle_mod.OracleMesh.from_input(W.periodic_cube_tet(4))
+    c = W.random_state(m.ne, 5, oracle_mod.npoly(3, p), seed=p, amp=2e-2,
+                       mean=(0.5, 0.05, -0.04, 0.03, 1.3))
+    rhs = m.rhs(p, c)
+    detj = m.detj()
+    total = (detj[:, None] * rhs[:, :, 0]).sum(axis=0)
+    scale = (detj[:, None] * np.abs(rhs[:, :, 0])).sum(axis=0)
+    assert np.all(np.abs(total) < 1e-13 * scale)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_linear_advection_global_polynomial_closed_form_tet(oracle_mod, p):
+    """3D form of the closed form: u a global polynomial of degree p on an open
+    Kuhn cube => d u_h/dt = -a.grad u exactly."""
+    m = oracle_mod.OracleMesh.from_input(W.open_cube_tet(3, jitter=0.15, seed=3))
+    a = np.array([0.7, -1.3, 0.4])
+    ncoef = (p + 1) * (p + 2) * (p + 3) // 6
+    coef = np.random.default_rng(p).uniform(-1, 1, size=ncoef)
+
+    def poly3(x, y, z):
+        v, gx, gy, gz = (np.zeros_like(x) for _ in range(4))
+        k = 0
+        for d in range(p + 1):
+            for i in range(d + 1):
+                for j in range(d - i + 1):
+                    l = d - i - j
+                    v += coef[k] * x ** i * y ** j * z ** l
+                    if i:
+                        gx += coef[k] * i * x ** (i - 1) * y ** j * z ** l
+                    if j:
+                        gy += coef[k] * j * x ** i * y ** (j - 1) * z ** l
+                    if l:
+                        gz += coef[k] * l * x ** i * y ** j * z ** (l - 1)
+                    k += 1
+        return v, gx, gy, gz
+
+    xyz, _, _ = m.eval_points(p, M=1)
+    u = poly3(xyz[..., 0], xyz[..., 1], xyz[..., 2])[0]
+    c = m.project(p, u[..., None])
+    rhs = m.rhs(p, c, kind=oracle_mod.ADVECTION, adv=a)
+    xyz2, _, U = m.eval_points(p, c=rhs, n1=p + 3)
+    _, gx, gy, gz = poly3(xyz2[..., 0], xyz2[..., 1], xyz2[..., 2])
+    np.testing.assert_allclose(U[..., 0], -(a[0] * gx + a[1] * gy + a[2] * gz), atol=1e-11)
