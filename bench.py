@@ -97,10 +97,12 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, mixed: bool, stage_frac_u0: float) -> float:
-    """Algorithmic DRAM bytes of one launch of a kernel class (each element touched
-    once per color on a closed conforming mesh)."""
-    s_in = (4 if mixed else 8) * NV      # state read for traces
+def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, mixed: bool, stage_frac_u0: float,
+                rec: int = 0) -> float:
+    """Algorithmic DRAM bytes of one launch (one call for the two-pass CFL) of a
+    kernel class; each element is touched once per color on a closed conforming
+    mesh.  rec = bytes of the FP32 record of an element (mixed precision)."""
+    s_in = rec if mixed else 8 * NV      # state read for traces
     s_rhs = (4 if mixed else 8) * NV     # rhs element block
     edge = 16 + 16 * (2 if dim == 2 else 3)
     if cls == "first":
@@ -108,13 +110,13 @@ def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, mixed: bool, s
     if cls == "color":
         return E * (s_in + 2 * s_rhs) + nedges * edge
     if cls == "last":
-        return E * (8 * NV + s_rhs + 8 * NV * stage_frac_u0 + 8 * NV + (4 * NV if mixed else 0)) + nedges * edge
+        return E * (8 * NV + s_rhs + 8 * NV * stage_frac_u0 + 8 * NV + (rec if mixed else 0)) + nedges * edge
     if cls == "cfl":
-        return E * (8 * NV + 8 + (4 * NV if mixed else 0))
+        return E * (8 * NV + 8 + 4 + (rec if mixed else 0))
     if cls == "volume":
         return E * (s_in + 8 * dim * dim + s_rhs)
     if cls == "stage":
-        return E * (8 * NV * 2 + s_rhs + 8 * NV + (4 * NV if mixed else 0))
+        return E * (8 * NV * 2 + s_rhs + 8 * NV + (rec if mixed else 0))
     return float("nan")
 
 
@@ -164,6 +166,8 @@ def run_dgc(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     dgc.lib()
     cfg, mi, mesh, c_host, prep = setup_workload(dgc, torch, dev, args.n)
+    if args.epb:
+        dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_EDGES_PER_BLOCK, args.epb)
     info = mesh.info
     E, NV, p = info["ne"], info["M"] * info["np"], info["p"]
     dofs = E * NV
@@ -171,7 +175,8 @@ def run_dgc(args, rank, world, local_rank):
     c = torch.empty(mesh.state_shape(), dtype=torch.float64, device=dev)
     dt = torch.zeros(1, dtype=torch.float64, device=dev)
     mixed, fp64 = dgc.DGC_FP32_MIXED, dgc.DGC_FP64
-    ws = torch.empty(dgc.dgc_workspace_size(mesh.h, fp64) // 8 + 64, dtype=torch.float64, device=dev)
+    wsb = max(dgc.dgc_workspace_size(mesh.h, fp64), dgc.dgc_workspace_size(mesh.h, mixed))
+    ws = torch.empty(wsb // 8 + 64, dtype=torch.float64, device=dev)
     dgc.dgc_import_state(mesh.h, c_host, c)
 
     def step(prec):
@@ -201,7 +206,9 @@ def run_dgc(args, rank, world, local_rank):
     ncolors = info["ncolors"]
     per_color = prep["edges_per_color"]
     kernels = {}
-    for cls, (tms, n) in prof.items():
+    kernels_per_call = {"cfl": 2}
+    for cls, (tms, nl) in prof.items():
+        n = nl // kernels_per_call.get(cls, 1)
         if cls == "first":
             ne_ = per_color[0]
         elif cls == "last":
@@ -210,13 +217,13 @@ def run_dgc(args, rank, world, local_rank):
             ne_ = sum(per_color[1:-1]) / max(1, ncolors - 2)
         else:
             ne_ = 0
-        b = class_bytes(cls, E, ne_, NV, 2, True, 2.0 / 3.0)
+        b = class_bytes(cls, E, ne_, NV, 2, True, 2.0 / 3.0, rec=4 * info["M"] * (info["np"] + 1))
         avg = tms / n
-        kernels[cls] = {"launches": n, "avg_ms": round(avg, 5), "share": round(tms / (ms * args.steps), 4),
+        kernels[cls] = {"launches": nl, "calls": n, "avg_ms": round(avg, 5), "share": round(tms / (ms * args.steps), 4),
                         "alg_bytes": int(b), "alg_gbs": round(b / (avg * 1e-3) / 1e9, 1),
                         "frac_hbm": round(b / (avg * 1e-3) / 1e9 / hbm, 3)}
-    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
-    step_bytes = sum(kernels[k]["alg_bytes"] * kernels[k]["launches"] for k in kernels) / args.steps
+    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["calls"])
+    step_bytes = sum(kernels[k]["alg_bytes"] * kernels[k]["calls"] for k in kernels) / args.steps
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["alg_gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": None,
                 "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
@@ -368,6 +375,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) timing")
     ap.add_argument("--ref-elements", type=int, default=40000, help="oracle elements per reference step")
+    ap.add_argument("--epb", type=int, default=0, help="edges per block of the surface kernels (0 = library default)")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
     args = ap.parse_args()

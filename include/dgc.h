@@ -64,7 +64,7 @@ typedef enum {
                                   integral, the last color applies the RK stage update
                                   (closed conforming meshes only); 0: separate volume
                                   kernel, every color read-modify-writes rhs (Alg. 1) */
-  DGC_OPT_EDGES_PER_BLOCK = 1, /* surface-kernel tile: edges per thread block (16..512) */
+  DGC_OPT_EDGES_PER_BLOCK = 1, /* surface-kernel tile: edges per thread block (16..128, x16) */
   DGC_OPT_THREADS_PER_EDGE = 2, /* 2 (one thread per edge side); reserved for tuning */
   DGC_OPT_PROFILE = 3           /* 1: record a CUDA event pair around every kernel launch, on
                                    the launch stream, for dgc_profile_collect; 0 (default): off */
@@ -169,21 +169,25 @@ dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl, double* d
                       void* stream);
 
 /* One SSP-RK3 step (Shu-Osher form) of c_dev in place, dt from the CFL rule on the state
- * at the start of the step (written to dt_dev, device).  workspace_dev holds at least
- * dgc_workspace_size() bytes, 256-byte aligned.  No allocation and no host
- * synchronisation after the first device call on the mesh. */
+ * at the start of the step (written to dt_dev, device).  workspace_dev (256-byte aligned)
+ * holds workspace_bytes bytes; DGC_ERR_ARG if that is less than dgc_workspace_size() for
+ * prec.  No allocation and no host synchronisation after the first device call on the
+ * mesh. */
 dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl,
-                       double* dt_dev, void* workspace_dev, void* stream);
+                       double* dt_dev, void* workspace_dev, int64_t workspace_bytes,
+                       void* stream);
 
 /* Comparators for the race mitigation of Sec. 1 that coloring replaces.
  * dgc_rhs_atomic: one launch over all edges, contributions added with atomicAdd.
  * dgc_rhs_two_pass: every edge writes its left and right contributions to slots 2k and
  * 2k+1 of a per-edge buffer, then a per-element kernel gathers them.  buffer_dev holds
- * at least dgc_two_pass_buffer_bytes() bytes.  Same results as dgc_rhs up to rounding. */
+ * buffer_bytes bytes; DGC_ERR_ARG if that is less than dgc_two_pass_buffer_bytes() for
+ * the mesh (FP64 words).  Same results as dgc_rhs up to rounding. */
 dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev,
                           double* rhs_dev, void* stream);
 dgc_status dgc_rhs_two_pass(dgc_mesh* mesh, dgc_prec prec, const double* c_dev,
-                            double* rhs_dev, void* buffer_dev, void* stream);
+                            double* rhs_dev, void* buffer_dev, int64_t buffer_bytes,
+                            void* stream);
 
 /* Buffer memory the per-edge two-pass scheme needs (Sec. 4.1, Table 4):
  * 2 * np * neq * sides * word_bytes. */

@@ -48,6 +48,8 @@ void require(bool ok, const char* msg, dgc_status code = DGC_ERR_ARG) {
 }
 
 int64_t nv_of(const Mesh& m) { return (int64_t)m.M * m.np; }
+// floats per element of the FP32 record the mixed-precision step keeps
+int64_t record_floats(const Mesh& m) { return m.dim == 2 ? tri_record_floats(m.p) : tet_record_floats(m.p); }
 int64_t state_bytes(const Mesh& m) { return m.ne * nv_of(m) * (int64_t)sizeof(double); }
 int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
@@ -137,6 +139,23 @@ void upload(Mesh& m) {
     int32_t l = m.sl[old], r = m.sr[old];
     int ql = m.sql[old], qr = r >= 0 ? m.sqr[old] : 15;
     int orient = 0;
+    if (dim == 3 && r >= 0) {
+      // vertex permutation between the two sides' face parameterisations:
+      // vertex i of the right element's face is vertex perm[i] of the left's
+      int32_t gl[3], gr[3], n = 0;
+      for (int v = 0, a = 0, b = 0; v < 4; ++v) {
+        if (v != ql) gl[a++] = m.ev[(size_t)l * 4 + v];
+        if (v != qr) gr[b++] = m.ev[(size_t)r * 4 + v];
+      }
+      int perm[3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          if (gr[i] == gl[j]) perm[i] = j, ++n;
+      orient = -1;
+      for (int o = 0; o < 6 && n == 3; ++o)
+        if (kFacePerms[o][0] == perm[0] && kFacePerms[o][1] == perm[1] && kFacePerms[o][2] == perm[2]) orient = o;
+      if (orient < 0) throw Error{DGC_ERR_MESH, "face vertices of the two sides do not match"};
+    }
     topo[k] = make_int4(en[l], r >= 0 ? en[r] : -1, ql | (qr << 4) | (orient << 8), 0);
     double meas = m.smeas[old];
     double sl = meas / m.detJ[l], sr = r >= 0 ? meas / m.detJ[r] : 0.0;
@@ -160,6 +179,7 @@ void upload(Mesh& m) {
     d->topo = dalloc<int4>(m.ns);
     d->fgeo = dalloc<double2>((int64_t)fgeo.size());
     d->slots = dalloc<int32_t>((int64_t)slots.size());
+    d->cfl_est = dalloc<float>(m.ne + 64);
     DGC_CUDA(cudaMemcpy(d->jinv, jinv.data(), sizeof(double) * jinv.size(), cudaMemcpyHostToDevice));
     DGC_CUDA(cudaMemcpy(d->inr, inr.data(), sizeof(double) * inr.size(), cudaMemcpyHostToDevice));
     DGC_CUDA(cudaMemcpy(d->topo, topo.data(), sizeof(int4) * topo.size(), cudaMemcpyHostToDevice));
@@ -206,6 +226,12 @@ Ctx ready(Mesh& m, void* stream) {
   x.ns = m.ns;
   x.epb = m.edges_per_block;
   x.d = m.dev;
+  x.shadow.M = m.M;
+  x.shadow.np = m.np;
+  x.shadow.nv = m.M * m.np;
+  x.shadow.rec = (int)record_floats(m);
+  x.shadow.split = true;
+  x.shadow.phi0 = m.tab.phiV[0];
   x.st = static_cast<cudaStream_t>(stream);
   return x;
 }
@@ -311,6 +337,7 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->slots);
   cudaFree(m.dev->ftab);
   cudaFree(m.dev->ftabd);
+  cudaFree(m.dev->cfl_est);
   delete m.dev;
   m.dev = nullptr;
   m.dirty = true;
@@ -429,9 +456,10 @@ dgc_status dgc_state_size(const dgc_mesh* mesh, int64_t* bytes) {
   });
 }
 
+// FP64: u1 [S], rhs [S].  Mixed: u1 [S], FP32 record [E * rec floats], FP32 rhs [S/2].
 static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) {
   int64_t S = state_bytes(m);
-  return prec == DGC_FP64 ? 2 * align256(S) : align256(S) + 2 * align256(S / 2);
+  return prec == DGC_FP64 ? 2 * align256(S) : align256(S) + align256(m.ne * record_floats(m) * 4) + align256(S / 2);
 }
 
 dgc_status dgc_workspace_size(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes) {
@@ -508,7 +536,7 @@ dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl_, double* 
 }
 
 dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_, double* dt_dev,
-                       void* workspace_dev, void* stream) {
+                       void* workspace_dev, int64_t workspace_size, void* stream) {
   return guarded([&] {
     Mesh& m = checked(mesh);
     require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
@@ -517,13 +545,15 @@ dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_
     require(workspace_dev != nullptr && reinterpret_cast<uintptr_t>(workspace_dev) % 256 == 0,
             "workspace must be 256-byte aligned");
     require(cfl_ > 0.0, "cfl must be positive");
+    require(workspace_size >= workspace_bytes(m, prec), "workspace smaller than dgc_workspace_size()");
     Ctx x = ready(m, stream);
     const bool mixed = prec == DGC_FP32_MIXED;
     const int64_t S = state_bytes(m);
     char* ws = static_cast<char*>(workspace_dev);
     double* u1 = reinterpret_cast<double*>(ws);
+    const int64_t R = align256(m.ne * record_floats(m) * 4);
     float* shadow = mixed ? reinterpret_cast<float*>(ws + align256(S)) : nullptr;
-    void* rhs = mixed ? (void*)(ws + align256(S) + align256(S / 2)) : (void*)(ws + align256(S));
+    void* rhs = mixed ? (void*)(ws + align256(S) + R) : (void*)(ws + align256(S));
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
     run(m, x, DGC_K_CFL, n, [&] { return cfl(x, c_dev, cfl_, dt_dev, shadow); });
@@ -582,13 +612,14 @@ dgc_status dgc_two_pass_buffer_bytes(int64_t sides, int np, int neq, int word_by
 }
 
 dgc_status dgc_rhs_two_pass(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev, void* buffer_dev,
-                            void* stream) {
+                            int64_t buffer_size, void* stream) {
   return guarded([&] {
     Mesh& m = checked(mesh);
     require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
     check_ptr(c_dev, "c_dev");
     check_ptr(rhs_dev, "rhs_dev");
     check_ptr(buffer_dev, "buffer_dev");
+    require(buffer_size >= 2 * m.ns * nv_of(m) * (int64_t)sizeof(double), "buffer smaller than dgc_two_pass_buffer_bytes()");
     Ctx x = ready(m, stream);
     const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
     int64_t n = 0;
@@ -607,7 +638,7 @@ dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value) {
         m.fuse = value != 0;
         break;
       case DGC_OPT_EDGES_PER_BLOCK:
-        require(value >= 16 && value <= 512 && value % 16 == 0, "edges per block must be 16..512, a multiple of 16");
+        require(value >= 16 && value <= 128 && value % 16 == 0, "edges per block must be 16..128, a multiple of 16");
         m.edges_per_block = (int)value;
         break;
       case DGC_OPT_THREADS_PER_EDGE:

@@ -1,0 +1,115 @@
+// Device helpers shared by the kernels.
+//
+// FP32 <-> FP64 conversions by integer bit manipulation.  On this GPU the
+// FP64 pipe runs at 1/64 of the FP32 rate and the hardware conversion
+// instructions issue on it, so converting a 40-value element block costs as
+// much as 40 FP64 operations; the integer forms below issue on the integer
+// pipe only.  Both implement IEEE 754 binary64 <-> binary32 conversion with
+// round-to-nearest-even, including zeros, subnormals, overflow, infinities and
+// NaNs (quieted).
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+namespace dgc {
+
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned ed = (unsigned)(b >> 52) & 0x7FFu;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  const int e = (int)ed - 896;  // binary32 exponent field of a normal result
+  unsigned out;
+  if (ed == 0x7FFu) {
+    out = 0x7F800000u | (mant ? 0x400000u : 0u);  // infinity, or a quiet NaN
+  } else if (e >= 255) {
+    out = 0x7F800000u;  // overflow
+  } else if (e > 0) {
+    const unsigned m = (unsigned)(mant >> 29);       // top 23 fraction bits
+    const unsigned rem = (unsigned)mant & 0x1FFFFFFFu;  // the 29 dropped bits
+    const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u));
+    out = (((unsigned)e << 23) | m) + up;  // a carry rounds into the exponent (up to infinity)
+  } else {
+    // binary32 subnormal or zero: the 53-bit significand in units of 2^-149
+    const int s = 30 - e;  // right shift, >= 30
+    if (ed == 0u || s > 54) {
+      out = 0u;
+    } else {
+      const unsigned long long M = mant | (1ull << 52);
+      const unsigned q = (unsigned)(M >> s);
+      const unsigned long long r = M & ((1ull << s) - 1ull), h = 1ull << (s - 1);
+      out = q + (unsigned)((r > h) | ((r == h) & (q & 1u)));  // may round up to the smallest normal
+    }
+  }
+  return __uint_as_float(out | sign);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned ef = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  unsigned long long bits;
+  if (ef == 0xFFu) {
+    bits = 0x7FF0000000000000ull | ((unsigned long long)m << 29);
+  } else if (ef != 0u) {
+    bits = ((unsigned long long)(ef + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0u) {
+    bits = 0ull;
+  } else {
+    // binary32 subnormal m 2^-149: normalise around its leading bit k
+    const int k = 31 - __clz(m);
+    const unsigned long long frac = ((unsigned long long)m << (52 - k)) & 0xFFFFFFFFFFFFFull;
+    bits = ((unsigned long long)(k + 874) << 52) | frac;
+  }
+  return __longlong_as_double((long long)(sign | bits));
+}
+
+template <typename T>
+__device__ __forceinline__ T to(double x);
+template <>
+__device__ __forceinline__ double to<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to<float>(double x) { return d2f(x); }
+
+__device__ __forceinline__ double widen(float x) { return f2d(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ float narrow(double x) { return d2f(x); }
+
+// block-wide minimum of non-negative values, combined into *out with one
+// atomicMin on the bit pattern (non-negative IEEE values order like their bits)
+__device__ __forceinline__ void block_min_to(double v, unsigned long long* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ double wmin[32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = wmin[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, wmin[w]);
+    atomicMin(out, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+__device__ __forceinline__ void block_min_to(float v, unsigned* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ float wminf[32];
+  if ((threadIdx.x & 31) == 0) wminf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = wminf[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fminf(b, wminf[w]);
+    atomicMin(out, __float_as_uint(b));
+  }
+}
+
+// The CFL reduction runs in two passes: an FP32 estimate of every element's
+// step, then an exact FP64 evaluation of the elements whose estimate lies
+// within this relative margin of the smallest estimate.  The FP32 estimate
+// of |u| + c has a relative error near 1e-6, far inside the margin, so the
+// FP64 minimum is always among the re-evaluated elements.
+constexpr float kCflMargin = 1.0f / 1024.0f;
+
+}  // namespace dgc

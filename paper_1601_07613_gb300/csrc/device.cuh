@@ -19,6 +19,7 @@ struct DeviceMesh {
   int32_t* slots = nullptr; // [E][nfpe] two-pass gather slots 2k + side
   float* ftab = nullptr;    // 3D face tables (float copy)
   double* ftabd = nullptr;  // 3D face tables
+  float* cfl_est = nullptr; // [E] FP32 step estimates of the CFL pre-pass, then 1 minimum
 };
 
 // Surface-kernel modes (Algorithm 1 and the comparators of Sec. 1).
@@ -38,8 +39,19 @@ enum TypeCfg {
   TY_MLAST = 3  // FP64 state, FP32 arithmetic, FP32 partial rhs (last color, mixed)
 };
 
+// FP32 record of the state kept by the mixed-precision step: rec floats per
+// element; split = the mean state phi0 c0 stored as an FP32 pair (hi[M], lo[M])
+// followed by the modes j >= 1 as [M][np-1], padded to rec floats; otherwise a
+// plain FP32 copy of the M*np values.
+struct ShadowLayout {
+  int M = 4, np = 1, nv = 4, rec = 4;
+  bool split = false;
+  double phi0 = 0.0;
+};
+
 struct Ctx {
   int dim = 2, p = 1, np = 0, M = 4, nfpe = 3;
+  ShadowLayout shadow;
   int64_t ne = 0, ns = 0;
   int epb = 128;
   const DeviceMesh* d = nullptr;
@@ -56,6 +68,7 @@ struct StageArgs {
 
 // kernels_tri.cu
 void tri_upload_tables(int p, const RefTables& T);
+int tri_record_floats(int p);
 int tri_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 void* rhs, void* buf, const StageArgs* sa);
@@ -63,6 +76,7 @@ int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* sh
 
 // kernels_tet.cu
 void tet_upload_tables(int p, const RefTables& T, DeviceMesh& d);
+int tet_record_floats(int p);
 int tet_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
 int tet_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 void* rhs, void* buf, const StageArgs* sa);
@@ -71,6 +85,5 @@ int tet_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* sh
 // kernels_common.cu
 int stage_update(const Ctx& c, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa);
 int gather_two_pass(const Ctx& c, bool f32, void* rhs, const void* buf);
-int make_shadow(const Ctx& c, const double* state, float* shadow);
 
 }  // namespace dgc

@@ -26,6 +26,12 @@ struct RefTables {
 // tetrahedra (dim 3).  Throws std::runtime_error on unsupported sizes.
 RefTables make_tables(int dim, int p);
 
+// Tetrahedra: phi_j at the face points of local face f seen through vertex
+// permutation o (0..5, kFacePerms) of the face's three vertices:
+// out[((f * 6 + o) * nqf + q) * np + j].  o = 0 is the face's own parameterisation.
+std::vector<double> tet_face_orient_tables(const RefTables& T);
+extern const int kFacePerms[6][3];
+
 // Evaluates the orthonormal basis and its reference gradient at one point.
 void basis_eval(int dim, int p, const double* x, double* phi, double* grad /*[dim][np] or null*/);
 

@@ -1,22 +1,37 @@
 // Element-wise kernels shared by all element types: the SSP-RK3 stage update
 // (used when the update is not fused into the last color) and the gather of
 // the per-edge-buffer comparator.
+#include "dev_util.cuh"
 #include "device.cuh"
 
 namespace dgc {
 
-// uout = a0 u0 + b0 (us + dt rhs), FP64; also the FP32 copy when shadow != null.
-// Element-wise, so uout may alias us or u0.
+// uout = a0 u0 + b0 us + (b0 dt) rhs in FP64, and the FP32 record of uout when
+// shadow != null.  Element-wise, so uout may alias us or u0.
 template <typename RT>
 __global__ void k_stage(const double* u0, const double* us, const RT* rhs, const double* dtp, double a0,
-                        double b0, double* uout, float* shadow, int64_t n) {
+                        double b0, double* uout, float* shadow, ShadowLayout L, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double dt = *dtp;
-  double v = b0 * (us[i] + dt * (double)rhs[i]);
-  if (a0 != 0.0) v += a0 * u0[i];
+  const double bdt = b0 * *dtp;
+  const double R = widen(rhs[i]);
+  const double v = a0 != 0.0 ? fma(bdt, R, fma(a0, u0[i], b0 * us[i])) : fma(bdt, R, b0 * us[i]);
   uout[i] = v;
-  if (shadow) shadow[i] = (float)v;
+  if (shadow) {
+    const int64_t e = i / L.nv;
+    const int l = (int)(i - e * L.nv), m = l / L.np, j = l - m * L.np;
+    float* rec = shadow + e * L.rec;
+    if (!L.split) {
+      rec[l] = d2f(v);
+    } else if (j == 0) {
+      const double u = L.phi0 * v;
+      const float hi = d2f(u);
+      rec[m] = hi;
+      rec[L.M + m] = d2f(u - f2d(hi));
+    } else {
+      rec[2 * L.M + m * (L.np - 1) + j - 1] = d2f(v);
+    }
+  }
 }
 
 int stage_update(const Ctx& x, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa) {
@@ -25,10 +40,10 @@ int stage_update(const Ctx& x, bool rhs_f32, const double* us, const void* rhs, 
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
   if (rhs_f32)
     k_stage<float><<<grid, bs, 0, x.st>>>(sa.u0, us, static_cast<const float*>(rhs), sa.dt, sa.a0, sa.b0,
-                                          sa.uout, sa.shadow, n);
+                                          sa.uout, sa.shadow, x.shadow, n);
   else
     k_stage<double><<<grid, bs, 0, x.st>>>(sa.u0, us, static_cast<const double*>(rhs), sa.dt, sa.a0, sa.b0,
-                                           sa.uout, sa.shadow, n);
+                                           sa.uout, sa.shadow, x.shadow, n);
   return 1;
 }
 
@@ -58,18 +73,6 @@ int gather_two_pass(const Ctx& x, bool f32, void* rhs, const void* buf) {
   else
     k_gather<double><<<grid, bs, 0, x.st>>>(static_cast<double*>(rhs), static_cast<const double*>(buf),
                                             x.d->slots, x.nfpe, nv, n);
-  return 1;
-}
-
-__global__ void k_shadow(const double* s, float* f, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) f[i] = (float)s[i];
-}
-
-int make_shadow(const Ctx& x, const double* state, float* shadow) {
-  const int64_t n = x.ne * x.M * x.np;
-  const int bs = 256;
-  k_shadow<<<(unsigned)((n + bs - 1) / bs), bs, 0, x.st>>>(state, shadow, n);
   return 1;
 }
 

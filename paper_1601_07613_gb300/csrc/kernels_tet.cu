@@ -1,12 +1,672 @@
-// Tetrahedral kernels (4-face coloring, Sec. 3): not built yet; the entry
-// points report DGC_ERR_UNSUPPORTED through a negative launch count.
+// Tetrahedral kernels: the 3D form of the colored surface integral (faces
+// colored with 4 colors, Sec. 3), the volume integral and the FP64 CFL
+// reduction.  Same structure as the triangle kernels: a lane pair per face,
+// one lane per neighbouring element, traces exchanged by shuffles, plain
+// read-modify-write stores within a color.  The collapsed face rule is not
+// symmetric under a permutation of the face's vertices, so the right element
+// evaluates its basis through one of six orientation tables (the face's
+// vertex permutation is stored per face).  FP64 kernels evaluate Eq. 2 as
+// written, FP32 kernels in the perturbation form of euler_pert.cuh.
+#include <cfloat>
+
+#include "dev_util.cuh"
 #include "device.cuh"
+#include "euler_pert.cuh"
 
 namespace dgc {
-void tet_upload_tables(int, const RefTables&, DeviceMesh&) {}
-int tet_volume(const Ctx&, TypeCfg, const void*, void*) { return -1; }
-int tet_surface(const Ctx&, TypeCfg, SurfMode, int64_t, int64_t, const void*, void*, void*, const StageArgs*) {
-  return -1;
+
+template <int P>
+struct TetDim {
+  static constexpr int NP = (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int NQV = (P + 2) * (P + 2) * (P + 2);
+  static constexpr int NQF = (P + 2) * (P + 2);
+  static constexpr int M = 5;
+  static constexpr int NV = M * NP;
+  // FP32 record: hi[M], lo[M], modes j >= 1 as [M][NP-1], padded to 4 floats
+  static constexpr int NF = (M * (NP + 1) + 3) / 4 * 4;
+};
+
+int tet_record_floats(int p) {
+  const int np = (p + 1) * (p + 2) * (p + 3) / 6;
+  return (5 * (np + 1) + 3) / 4 * 4;
 }
-int tet_cfl(const Ctx&, const double*, double, double*, float*) { return -1; }
+
+template <typename T, int P>
+struct TetTab {
+  T phiV[TetDim<P>::NQV][TetDim<P>::NP];
+  T vr[TetDim<P>::NQV][TetDim<P>::NP];  // w_q dphi/dr
+  T vs[TetDim<P>::NQV][TetDim<P>::NP];
+  T vt[TetDim<P>::NQV][TetDim<P>::NP];
+  T wF[TetDim<P>::NQF];                 // face weights, sum 1
+};
+
+__constant__ TetTab<double, 1> cTetD1;
+__constant__ TetTab<double, 2> cTetD2;
+__constant__ TetTab<float, 1> cTetF1;
+__constant__ TetTab<float, 2> cTetF2;
+
+template <typename T, int P>
+__device__ __forceinline__ const TetTab<T, P>& tet_tab();
+template <> __device__ __forceinline__ const TetTab<double, 1>& tet_tab<double, 1>() { return cTetD1; }
+template <> __device__ __forceinline__ const TetTab<double, 2>& tet_tab<double, 2>() { return cTetD2; }
+template <> __device__ __forceinline__ const TetTab<float, 1>& tet_tab<float, 1>() { return cTetF1; }
+template <> __device__ __forceinline__ const TetTab<float, 2>& tet_tab<float, 2>() { return cTetF2; }
+
+template <typename T, int P>
+static void fill_tet(TetTab<T, P>& K, const RefTables& R) {
+  using D = TetDim<P>;
+  for (int q = 0; q < D::NQV; ++q)
+    for (int j = 0; j < D::NP; ++j) {
+      K.phiV[q][j] = (T)R.phiV[q * D::NP + j];
+      K.vr[q][j] = (T)(R.vw[q] * R.dphiV[(0 * D::NQV + q) * D::NP + j]);
+      K.vs[q][j] = (T)(R.vw[q] * R.dphiV[(1 * D::NQV + q) * D::NP + j]);
+      K.vt[q][j] = (T)(R.vw[q] * R.dphiV[(2 * D::NQV + q) * D::NP + j]);
+    }
+  for (int q = 0; q < D::NQF; ++q) K.wF[q] = (T)R.fw[q];
+}
+
+template <int P>
+static void upload_tet_p(const RefTables& R, const void* symD, const void* symF) {
+  static TetTab<double, P> hd;
+  static TetTab<float, P> hf;
+  fill_tet(hd, R);
+  fill_tet(hf, R);
+  cudaMemcpyToSymbol(symD, &hd, sizeof hd);
+  cudaMemcpyToSymbol(symF, &hf, sizeof hf);
+}
+
+void tet_upload_tables(int p, const RefTables& R, DeviceMesh& d) {
+  if (R.dim != 3 || R.p != p) return;
+  if (p == 1) upload_tet_p<1>(R, &cTetD1, &cTetF1);
+  if (p == 2) upload_tet_p<2>(R, &cTetD2, &cTetF2);
+  // orientation tables for the faces, FP64 and FP32 copies, in global memory
+  std::vector<double> t = tet_face_orient_tables(R);
+  std::vector<float> tf(t.begin(), t.end());
+  if (cudaMalloc(&d.ftabd, sizeof(double) * t.size()) != cudaSuccess ||
+      cudaMalloc(&d.ftab, sizeof(float) * t.size()) != cudaSuccess)
+    throw Error{DGC_ERR_OOM, "cudaMalloc (face tables)"};
+  cudaMemcpy(d.ftabd, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(d.ftab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice);
+}
+
+// ---------------------------------------------------------------------------
+// loads and stores of element blocks (NV = 5 Np values: 8-byte vectors)
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void tload(const double* src, double (&v)[N]) {
+  static_assert(N % 2 == 0, "");
+  const double2* s = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    double2 x = s[i];
+    v[2 * i] = x.x;
+    v[2 * i + 1] = x.y;
+  }
+}
+template <int N>
+__device__ __forceinline__ void tload(const float* src, float (&v)[N]) {
+  const float2* s = reinterpret_cast<const float2*>(src);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    float2 x = s[i];
+    v[2 * i] = x.x;
+    v[2 * i + 1] = x.y;
+  }
+}
+template <int N>
+__device__ __forceinline__ void tstore(double* dst, const double (&v)[N]) {
+  double2* d = reinterpret_cast<double2*>(dst);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) d[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+template <int N>
+__device__ __forceinline__ void tstore(float* dst, const float (&v)[N]) {
+  float2* d = reinterpret_cast<float2*>(dst);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) d[i] = make_float2(v[2 * i], v[2 * i + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 element state in perturbation form
+// ---------------------------------------------------------------------------
+template <int P>
+struct TetPert {
+  using D = TetDim<P>;
+  float hi[5], lo[5];
+  float cd[5][D::NP - 1];
+};
+
+__device__ __forceinline__ void tsplit(double phi0, double c0, float& hi, float& lo) {
+  const double u = phi0 * c0;
+  hi = d2f(u);
+  lo = d2f(u - f2d(hi));
+}
+
+template <int P>
+__device__ __forceinline__ void tload_pert(const double* src, TetPert<P>& B) {
+  using D = TetDim<P>;
+  const double phi0 = tet_tab<double, P>().phiV[0][0];
+  double v[D::NV];
+  tload(src, v);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    tsplit(phi0, v[m * D::NP], B.hi[m], B.lo[m]);
+#pragma unroll
+    for (int j = 1; j < D::NP; ++j) B.cd[m][j - 1] = d2f(v[m * D::NP + j]);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void tload_pert(const float* src, TetPert<P>& B) {
+  using D = TetDim<P>;
+  float v[D::NF];
+  tload(src, v);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    B.hi[m] = v[m];
+    B.lo[m] = v[5 + m];
+#pragma unroll
+    for (int j = 1; j < D::NP; ++j) B.cd[m][j - 1] = v[10 + m * (D::NP - 1) + j - 1];
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void trecord_of(const double (&v)[TetDim<P>::NV], float (&r)[TetDim<P>::NF]) {
+  using D = TetDim<P>;
+  const double phi0 = tet_tab<double, P>().phiV[0][0];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    tsplit(phi0, v[m * D::NP], r[m], r[5 + m]);
+#pragma unroll
+    for (int j = 1; j < D::NP; ++j) r[10 + m * (D::NP - 1) + j - 1] = d2f(v[m * D::NP + j]);
+  }
+#pragma unroll
+  for (int i = 5 * (D::NP + 1); i < D::NF; ++i) r[i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Euler fluxes, Eq. 2 as written
+// ---------------------------------------------------------------------------
+// Euler flux in direction n (not necessarily unit) and the max wave speed
+__device__ __forceinline__ void euler3_n(const double* U, double nx, double ny, double nz, double* F, double& un,
+                                         double& c) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+  const double p = 0.4 * (U[4] - 0.5 * (U[1] * u + U[2] * v + U[3] * w));
+  un = u * nx + v * ny + w * nz;
+  c = sqrt(1.4 * p * ir);
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + p * nx;
+  F[2] = U[2] * un + p * ny;
+  F[3] = U[3] * un + p * nz;
+  F[4] = (U[4] + p) * un;
+}
+
+__device__ __forceinline__ void lf3(const double* a, const double* b, double nx, double ny, double nz, double* Fs) {
+  double Fa[5], Fb[5], una, ca, unb, cb;
+  euler3_n(a, nx, ny, nz, Fa, una, ca);
+  euler3_n(b, nx, ny, nz, Fb, unb, cb);
+  const double lam = fmax(fabs(una) + ca, fabs(unb) + cb);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) Fs[m] = 0.5 * (Fa[m] + Fb[m]) - 0.5 * lam * (b[m] - a[m]);
+}
+
+template <int P>
+__device__ __forceinline__ void tet_volume64(const double (&c)[TetDim<P>::NV], const double* ji,
+                                             double (&acc)[TetDim<P>::NV]) {
+  using D = TetDim<P>;
+  constexpr int NP = D::NP;
+  const TetTab<double, P>& K = tet_tab<double, P>();
+  double J[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) J[i] = __ldg(ji + i);
+#pragma unroll 2
+  for (int q = 0; q < D::NQV; ++q) {
+    double U[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * c[m * NP + j];
+      U[m] = s;
+    }
+    // reference-direction fluxes F . grad r_k
+    double Fr[3][5], un, cs;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) euler3_n(U, J[3 * k], J[3 * k + 1], J[3 * k + 2], Fr[k], un, cs);
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        acc[m * NP + j] += K.vr[q][j] * Fr[0][m] + K.vs[q][j] * Fr[1][m] + K.vt[q][j] * Fr[2][m];
+  }
+}
+
+// FP32 volume integral in perturbation form (F(ub) left out, grad phi_0 = 0)
+template <int P>
+__device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<3>& R, const double* ji,
+                                             float (&acc)[TetDim<P>::NV]) {
+  using D = TetDim<P>;
+  constexpr int NP = D::NP;
+  const TetTab<float, P>& K = tet_tab<float, P>();
+  float J[3][3], th[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) J[k][a] = d2f(__ldg(ji + 3 * k + a));
+    th[k] = R.u[1] * J[k][0] + R.u[2] * J[k][1] + R.u[3] * J[k][2];
+  }
+#pragma unroll 2
+  for (int q = 0; q < D::NQV; ++q) {
+    float d[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      float s = B.lo[m];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * B.cd[m][j - 1];
+      d[m] = s;
+    }
+    PertState<3> S;
+    S.init(R, d);
+    float Fr[3][5];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pert_flux<3>(R, S, d, J[k], th[k], Fr[k]);
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 1; j < NP; ++j)
+        acc[m * NP + j] += K.vr[q][j] * Fr[0][m] + K.vs[q][j] * Fr[1][m] + K.vt[q][j] * Fr[2][m];
+  }
+}
+
+template <int P, typename CT, typename ST, typename RT>
+__global__ void __launch_bounds__(128) k_vol_tet(const ST* c, const double* jinv, RT* rhs, int64_t ne) {
+  using D = TetDim<P>;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  RT out[D::NV];
+  if constexpr (sizeof(CT) == 8) {
+    double v[D::NV], acc[D::NV];
+    tload(c + e * D::NV, v);
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
+    tet_volume64<P>(v, jinv + 9 * e, acc);
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+  } else {
+    constexpr int stride = sizeof(ST) == 8 ? D::NV : D::NF;
+    TetPert<P> B;
+    tload_pert<P>(c + e * stride, B);
+    PertRef<3> R;
+    R.init(B.hi);
+    float acc[D::NV];
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) acc[i] = 0.0f;
+    tet_volume32<P>(B, R, jinv + 9 * e, acc);
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+  }
+  tstore(rhs + e * D::NV, out);
+}
+
+struct TetParams {
+  int64_t begin, end;
+  const int4* topo;
+  const double2* fgeo;
+  const double* jinv;
+  const void* ftab;  // [4][6][NQF][NP] of CT
+  const void* state;
+  void* rhs;
+  void* buf;
+  StageArgs sa;
+};
+
+template <int P, typename RT, int MODE, typename AT>
+__device__ __forceinline__ void tet_write(const TetParams& A, int64_t elem, int64_t k, int side,
+                                          const AT (&acc)[TetDim<P>::NV]) {
+  using D = TetDim<P>;
+  constexpr int NV = D::NV;
+  if constexpr (MODE == SURF_RMW) {
+    RT* r = static_cast<RT*>(A.rhs) + elem * NV;
+    RT old[NV];
+    tload(r, old);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) old[i] += (RT)acc[i];
+    tstore(r, old);
+  } else if constexpr (MODE == SURF_FIRST) {
+    RT out[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
+    tstore(static_cast<RT*>(A.rhs) + elem * NV, out);
+  } else if constexpr (MODE == SURF_ATOMIC) {
+    RT* r = static_cast<RT*>(A.rhs) + elem * NV;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) atomicAdd(r + i, (RT)acc[i]);
+  } else if constexpr (MODE == SURF_BUFFER) {
+    RT out[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
+    tstore(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
+  } else {  // SURF_LAST: FP64 stage update, two values at a time (see the triangle kernel)
+    const RT* part = static_cast<const RT*>(A.rhs) + elem * NV;
+    const double2* us2 = reinterpret_cast<const double2*>(static_cast<const double*>(A.state) + elem * NV);
+    const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
+    double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
+    float* rec = A.sa.shadow ? A.sa.shadow + elem * D::NF : nullptr;
+    const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
+    const double phi0 = tet_tab<double, P>().phiV[0][0];
+#pragma unroll
+    for (int i = 0; i < NV; i += 2) {
+      const double2 s = us2[i / 2];
+      const double L0 = widen(part[i] + (RT)acc[i]), L1 = widen(part[i + 1] + (RT)acc[i + 1]);
+      double v[2];
+      if (a0 == 0.0) {
+        v[0] = fma(bdt, L0, b0 == 1.0 ? s.x : b0 * s.x);
+        v[1] = fma(bdt, L1, b0 == 1.0 ? s.y : b0 * s.y);
+      } else {
+        const double2 u = u02[i / 2];
+        v[0] = fma(bdt, L0, fma(a0, u.x, b0 * s.x));
+        v[1] = fma(bdt, L1, fma(a0, u.y, b0 * s.y));
+      }
+      out2[i / 2] = make_double2(v[0], v[1]);
+      if (rec) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int m = (i + t) / D::NP, j = (i + t) % D::NP;
+          if (j == 0) tsplit(phi0, v[t], rec[m], rec[5 + m]);
+          else rec[10 + m * (D::NP - 1) + j - 1] = d2f(v[t]);
+        }
+      }
+    }
+  }
+}
+
+template <int P, typename CT, typename ST, typename RT, int MODE>
+__global__ void __launch_bounds__(256) k_surf_tet(const TetParams A) {
+  using D = TetDim<P>;
+  constexpr int NP = D::NP, NQ = D::NQF, NV = D::NV;
+  extern __shared__ unsigned char smem_raw[];
+  CT* sphi = reinterpret_cast<CT*>(smem_raw);  // [4][6][NQ][NP]
+  {
+    const CT* src = static_cast<const CT*>(A.ftab);
+    for (int i = threadIdx.x; i < 24 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
+  }
+  __syncthreads();
+
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t k = A.begin + (t >> 1);
+  const int side = (int)(t & 1);
+  const bool valid = k < A.end;
+  if (!valid) k = A.end - 1;
+  const int4 tp = A.topo[k];
+  const bool bnd = tp.y < 0;
+  const bool right = side && !bnd;
+  const int64_t elem = right ? tp.y : tp.x;
+  const int lf = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
+  const int orient = right ? ((tp.z >> 8) & 7) : 0;
+  const bool writer = valid && !(side && bnd);
+  const double2 g0 = A.fgeo[3 * k], g1 = A.fgeo[3 * k + 1], g2 = A.fgeo[3 * k + 2];
+  const CT* ph = sphi + (lf * 6 + orient) * NQ * NP;
+
+  if constexpr (sizeof(CT) == 8) {
+    const TetTab<double, P>& K = tet_tab<double, P>();
+    double c[NV], acc[NV];
+    tload(static_cast<const double*>(A.state) + elem * NV, c);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    if constexpr (MODE == SURF_FIRST) tet_volume64<P>(c, A.jinv + 9 * elem, acc);
+    const double scale = right ? g2.y : -g2.x;
+#pragma unroll 2
+    for (int q = 0; q < NQ; ++q) {
+      double phi[NP], U[5], V[5], a[5], b[5], Fs[5];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) phi[j] = ph[q * NP + j];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
+        U[m] = s;
+      }
+#pragma unroll
+      for (int m = 0; m < 5; ++m) V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        a[m] = side ? V[m] : U[m];
+        b[m] = side ? U[m] : V[m];
+      }
+      lf3(a, b, g0.x, g0.y, g1.x, Fs);
+      const double s = scale * K.wF[q];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const double g = s * Fs[m];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+      }
+    }
+    if (writer) tet_write<P, RT, MODE>(A, elem, k, side, acc);
+  } else {
+    const TetTab<float, P>& K = tet_tab<float, P>();
+    constexpr int stride = sizeof(ST) == 8 ? NV : D::NF;
+    TetPert<P> B;
+    tload_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
+    PertRef<3> R;
+    R.init(B.hi);
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
+    if constexpr (MODE == SURF_FIRST) tet_volume32<P>(B, R, A.jinv + 9 * elem, acc);
+    float base[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const float ho = __shfl_xor_sync(0xffffffffu, B.hi[m], 1);
+      const float lo = __shfl_xor_sync(0xffffffffu, B.lo[m], 1);
+      base[m] = (ho - B.hi[m]) + lo;
+    }
+    const float n[3] = {d2f(g0.x), d2f(g0.y), d2f(g1.x)};
+    const float scale = right ? d2f(g2.y) : -d2f(g2.x);
+    const float thb = R.u[1] * n[0] + R.u[2] * n[1] + R.u[3] * n[2];
+#pragma unroll 2
+    for (int q = 0; q < NQ; ++q) {
+      float phi[NP], dU[5], dV[5], ds[5], dn[5], G[5];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) phi[j] = ph[q * NP + j];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 1; j < NP; ++j) s += phi[j] * B.cd[m][j - 1];
+        dU[m] = s;
+      }
+#pragma unroll
+      for (int m = 0; m < 5; ++m) dV[m] = __shfl_xor_sync(0xffffffffu, dU[m], 1);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        ds[m] = B.lo[m] + dU[m];
+        dn[m] = base[m] + dV[m];
+      }
+      if (side) pert_lf<3>(R, dn, ds, n, thb, G);
+      else pert_lf<3>(R, ds, dn, n, thb, G);
+      const float s = scale * K.wF[q];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const float g = s * G[m];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+      }
+    }
+    if (writer) tet_write<P, RT, MODE>(A, elem, k, side, acc);
+  }
+}
+
+// CFL reduction in two passes, as for triangles: FP32 estimates of every
+// element, then FP64 only for the elements within kCflMargin of the minimum.
+template <int P, typename T>
+__device__ __forceinline__ T tet_lambda_max(const T (&v)[TetDim<P>::NV]) {
+  using D = TetDim<P>;
+  constexpr int NP = D::NP;
+  const TetTab<T, P>& K = tet_tab<T, P>();
+  T lam = T(0);
+#pragma unroll 2
+  for (int q = 0; q < D::NQV; ++q) {
+    T U[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * v[m * NP + j];
+      U[m] = s;
+    }
+    const T ir = T(1) / U[0], u = U[1] * ir, w = U[2] * ir, z = U[3] * ir;
+    const T q2 = u * u + w * w + z * z;
+    const T pr = T(0.4) * (U[4] - T(0.5) * U[0] * q2);
+    lam = fmax(lam, sqrt(q2) + sqrt(T(1.4) * pr * ir));
+  }
+  return lam;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_cfl1_tet(const double* c, const double* inr, int64_t ne, float* est,
+                                                  unsigned* minbits, float* shadow) {
+  using D = TetDim<P>;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float best = FLT_MAX;
+  if (e < ne) {
+    double v[D::NV];
+    tload(c + e * D::NV, v);
+    if (shadow) {
+      float r[D::NF];
+      trecord_of<P>(v, r);
+      tstore(shadow + e * D::NF, r);
+    }
+    float f[D::NV];
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) f[i] = d2f(v[i]);
+    float d = d2f(inr[e]) / ((2 * P + 1) * tet_lambda_max<P, float>(f));
+    if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;
+    est[e] = d;
+    best = d;
+  }
+  block_min_to(best, minbits);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_cfl2_tet(const double* c, const double* inr, int64_t ne, double cfl,
+                                                  const float* est, const unsigned* minbits,
+                                                  unsigned long long* dtbits) {
+  using D = TetDim<P>;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double best = DBL_MAX;
+  if (e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin)) {
+    double v[D::NV];
+    tload(c + e * D::NV, v);
+    best = cfl * (inr[e] / ((2 * P + 1) * tet_lambda_max<P, double>(v)));
+    if (!(best > 0.0)) best = DBL_MAX;
+  }
+  block_min_to(best, dtbits);
+}
+
+// ---------------------------------------------------------------------------
+template <int P, typename CT, typename ST, typename RT>
+static int tvol_p(const Ctx& x, const void* s, void* r) {
+  const int bs = 128;
+  k_vol_tet<P, CT, ST, RT><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(
+      static_cast<const ST*>(s), x.d->jinv, static_cast<RT*>(r), x.ne);
+  return 1;
+}
+
+int tet_volume(const Ctx& x, TypeCfg ty, const void* s, void* r) {
+  switch (x.p * 4 + ty) {
+    case 4 + TY_D: return tvol_p<1, double, double, double>(x, s, r);
+    case 8 + TY_D: return tvol_p<2, double, double, double>(x, s, r);
+    case 4 + TY_MD: return tvol_p<1, float, double, double>(x, s, r);
+    case 8 + TY_MD: return tvol_p<2, float, double, double>(x, s, r);
+    case 4 + TY_MF: return tvol_p<1, float, float, float>(x, s, r);
+    case 8 + TY_MF: return tvol_p<2, float, float, float>(x, s, r);
+    default: return -1;
+  }
+}
+
+template <int P, typename CT, typename ST, typename RT, int MODE>
+static int tsurf_launch(const Ctx& x, TetParams A) {
+  const int64_t n = A.end - A.begin;
+  if (n <= 0) return 0;
+  using D = TetDim<P>;
+  A.ftab = sizeof(CT) == 8 ? (const void*)x.d->ftabd : (const void*)x.d->ftab;
+  const size_t smem = sizeof(CT) * 24 * D::NQF * D::NP;
+  auto kern = k_surf_tet<P, CT, ST, RT, MODE>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int threads = 2 * x.epb;
+  kern<<<(unsigned)((2 * n + threads - 1) / threads), threads, smem, x.st>>>(A);
+  return 1;
+}
+
+template <int P, typename CT, typename ST, typename RT>
+static int tsurf_mode(const Ctx& x, SurfMode mode, const TetParams& A) {
+  switch (mode) {
+    case SURF_RMW: return tsurf_launch<P, CT, ST, RT, SURF_RMW>(x, A);
+    case SURF_FIRST: return tsurf_launch<P, CT, ST, RT, SURF_FIRST>(x, A);
+    case SURF_ATOMIC: return tsurf_launch<P, CT, ST, RT, SURF_ATOMIC>(x, A);
+    case SURF_BUFFER: return tsurf_launch<P, CT, ST, RT, SURF_BUFFER>(x, A);
+    default: return -1;
+  }
+}
+
+template <int P>
+static int tsurf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const TetParams& A) {
+  if (mode == SURF_LAST) {
+    if (ty == TY_D) return tsurf_launch<P, double, double, double, SURF_LAST>(x, A);
+    if (ty == TY_MLAST) return tsurf_launch<P, float, double, float, SURF_LAST>(x, A);
+    return -1;
+  }
+  switch (ty) {
+    case TY_D: return tsurf_mode<P, double, double, double>(x, mode, A);
+    case TY_MD: return tsurf_mode<P, float, double, double>(x, mode, A);
+    case TY_MF:
+      if (mode != SURF_RMW && mode != SURF_FIRST) return -1;
+      return tsurf_mode<P, float, float, float>(x, mode, A);
+    default: return -1;
+  }
+}
+
+int tet_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
+                void* rhs, void* buf, const StageArgs* sa) {
+  TetParams A;
+  A.begin = begin;
+  A.end = end;
+  A.topo = x.d->topo;
+  A.fgeo = x.d->fgeo;
+  A.jinv = x.d->jinv;
+  A.ftab = nullptr;
+  A.state = state;
+  A.rhs = rhs;
+  A.buf = buf;
+  if (sa) A.sa = *sa;
+  switch (x.p) {
+    case 1: return tsurf_p<1>(x, ty, mode, A);
+    case 2: return tsurf_p<2>(x, ty, mode, A);
+    default: return -1;
+  }
+}
+
+int tet_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((x.ne + bs - 1) / bs);
+  auto* bits = reinterpret_cast<unsigned long long*>(dt);
+  float* est = x.d->cfl_est;
+  unsigned* mn = reinterpret_cast<unsigned*>(x.d->cfl_est + x.ne);
+  if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
+  switch (x.p) {
+    case 1:
+      k_cfl1_tet<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
+      k_cfl2_tet<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    case 2:
+      k_cfl1_tet<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
+      k_cfl2_tet<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    default: return -1;
+  }
+}
+
 }  // namespace dgc

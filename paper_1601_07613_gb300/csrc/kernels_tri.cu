@@ -11,9 +11,14 @@
 // Lax-Friedrichs flux, and each projects it onto its own element.  Within one
 // color no two edges share an element, so the lanes update rhs with plain
 // loads and stores (Sec. 1, Algorithm 1): no atomics, no scratch buffer.
+//
+// FP64 kernels evaluate Eq. 2 as written.  FP32 kernels evaluate it in the
+// perturbation form of euler_pert.cuh (deviations from the element mean).
 #include <cfloat>
 
+#include "dev_util.cuh"
 #include "device.cuh"
+#include "euler_pert.cuh"
 
 namespace dgc {
 
@@ -24,6 +29,9 @@ struct TriDim {
   static constexpr int NQE = 2 * P + 1;
   static constexpr int M = 4;
   static constexpr int NV = M * NP;
+  // FP32 element record of the mixed-precision step: mean state as hi[M], lo[M],
+  // then the modes j >= 1 as [M][NP-1]
+  static constexpr int NF = M * (NP + 1);
 };
 
 template <typename T, int P>
@@ -83,34 +91,36 @@ void tri_upload_tables(int p, const RefTables& R) {
   if (p == 3) upload_p<3>(R, &cTriD3, &cTriF3);
 }
 
+int tri_record_floats(int p) { return 4 * ((p + 1) * (p + 2) / 2 + 1); }
+
 // ---------------------------------------------------------------------------
-// state loads / stores (the element block is M*Np contiguous values)
+// element block loads / stores (M*Np contiguous values, 16-byte vectors)
 // ---------------------------------------------------------------------------
-template <typename CT, int N>
-__device__ __forceinline__ void load_block(const double* __restrict__ src, CT (&v)[N]) {
+template <int N>
+__device__ __forceinline__ void load_block(const double* __restrict__ src, double (&v)[N]) {
   static_assert(N % 2 == 0, "even block");
   const double2* s = reinterpret_cast<const double2*>(src);
 #pragma unroll
   for (int i = 0; i < N / 2; ++i) {
     double2 x = __ldg(s + i);
-    v[2 * i] = (CT)x.x;
-    v[2 * i + 1] = (CT)x.y;
+    v[2 * i] = x.x;
+    v[2 * i + 1] = x.y;
   }
 }
-template <typename CT, int N>
-__device__ __forceinline__ void load_block(const float* __restrict__ src, CT (&v)[N]) {
+template <int N>
+__device__ __forceinline__ void load_block(const float* __restrict__ src, float (&v)[N]) {
   static_assert(N % 4 == 0, "block of float4");
   const float4* s = reinterpret_cast<const float4*>(src);
 #pragma unroll
   for (int i = 0; i < N / 4; ++i) {
     float4 x = __ldg(s + i);
-    v[4 * i] = (CT)x.x;
-    v[4 * i + 1] = (CT)x.y;
-    v[4 * i + 2] = (CT)x.z;
-    v[4 * i + 3] = (CT)x.w;
+    v[4 * i] = x.x;
+    v[4 * i + 1] = x.y;
+    v[4 * i + 2] = x.z;
+    v[4 * i + 3] = x.w;
   }
 }
-// plain (coherent) loads, for blocks another kernel of the same stream wrote
+// plain (coherent) loads, for blocks an earlier kernel of the stream wrote
 template <int N>
 __device__ __forceinline__ void load_plain(const double* src, double (&v)[N]) {
   const double2* s = reinterpret_cast<const double2*>(src);
@@ -147,13 +157,70 @@ __device__ __forceinline__ void store_block(float* dst, const float (&v)[N]) {
 }
 
 // ---------------------------------------------------------------------------
-// Euler fluxes (gamma = 1.4)
+// FP32 element state in perturbation form: mean hi + lo, deviation modes
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void euler_xy(const T* U, T* F, T* G) {
-  const T ir = T(1) / U[0];
-  const T u = U[1] * ir, v = U[2] * ir;
-  const T p = T(0.4) * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+template <int P>
+struct PertBlock {
+  using D = TriDim<P>;
+  float hi[4], lo[4];
+  float cd[4][D::NP - 1];  // modes j >= 1
+};
+
+// split the FP64 mean state phi0 c0 into hi + lo (2 FP64 operations per value)
+__device__ __forceinline__ void split_mean(double phi0, double c0, float& hi, float& lo) {
+  const double u = phi0 * c0;
+  hi = d2f(u);
+  lo = d2f(u - f2d(hi));
+}
+
+template <int P>
+__device__ __forceinline__ void load_pert(const double* __restrict__ src, PertBlock<P>& B) {
+  using D = TriDim<P>;
+  const double phi0 = tri_tab<double, P>().phiV[0][0];
+  double v[D::NV];
+  load_block(src, v);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    split_mean(phi0, v[m * D::NP], B.hi[m], B.lo[m]);
+#pragma unroll
+    for (int j = 1; j < D::NP; ++j) B.cd[m][j - 1] = d2f(v[m * D::NP + j]);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void load_pert(const float* __restrict__ src, PertBlock<P>& B) {
+  using D = TriDim<P>;
+  float v[D::NF];
+  load_block(src, v);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    B.hi[m] = v[m];
+    B.lo[m] = v[4 + m];
+#pragma unroll
+    for (int j = 1; j < D::NP; ++j) B.cd[m][j - 1] = v[8 + m * (D::NP - 1) + j - 1];
+  }
+}
+
+// FP32 record of an FP64 block (the writers of the mixed-precision step)
+template <int P>
+__device__ __forceinline__ void record_of(const double (&v)[TriDim<P>::NV], float (&r)[TriDim<P>::NF]) {
+  using D = TriDim<P>;
+  const double phi0 = tri_tab<double, P>().phiV[0][0];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    split_mean(phi0, v[m * D::NP], r[m], r[4 + m]);
+#pragma unroll
+    for (int j = 1; j < D::NP; ++j) r[8 + m * (D::NP - 1) + j - 1] = d2f(v[m * D::NP + j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Euler fluxes (gamma = 1.4), Eq. 2 as written
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void euler_xy(const double* U, double* F, double* G) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir;
+  const double p = 0.4 * (U[3] - 0.5 * (U[1] * u + U[2] * v));
   F[0] = U[1];
   F[1] = U[1] * u + p;
   F[2] = U[2] * u;
@@ -165,56 +232,87 @@ __device__ __forceinline__ void euler_xy(const T* U, T* F, T* G) {
 }
 
 // local Lax-Friedrichs (Rusanov) flux F*(a, b, n) = (F(a).n + F(b).n)/2 - lam (b - a)/2
-template <typename T>
-__device__ __forceinline__ void lf_flux(const T* a, const T* b, T nx, T ny, T* Fs) {
-  const T ia = T(1) / a[0], ib = T(1) / b[0];
-  const T ua = a[1] * ia, va = a[2] * ia, ub = b[1] * ib, vb = b[2] * ib;
-  const T pa = T(0.4) * (a[3] - T(0.5) * (a[1] * ua + a[2] * va));
-  const T pb = T(0.4) * (b[3] - T(0.5) * (b[1] * ub + b[2] * vb));
-  const T una = ua * nx + va * ny, unb = ub * nx + vb * ny;
-  const T ca = sqrt(T(1.4) * pa * ia), cb = sqrt(T(1.4) * pb * ib);
-  const T lam = fmax(fabs(una) + ca, fabs(unb) + cb);
-  const T h = T(0.5), hl = T(0.5) * lam;
+__device__ __forceinline__ void lf_flux(const double* a, const double* b, double nx, double ny, double* Fs) {
+  const double ia = 1.0 / a[0], ib = 1.0 / b[0];
+  const double ua = a[1] * ia, va = a[2] * ia, ub = b[1] * ib, vb = b[2] * ib;
+  const double pa = 0.4 * (a[3] - 0.5 * (a[1] * ua + a[2] * va));
+  const double pb = 0.4 * (b[3] - 0.5 * (b[1] * ub + b[2] * vb));
+  const double una = ua * nx + va * ny, unb = ub * nx + vb * ny;
+  const double ca = sqrt(1.4 * pa * ia), cb = sqrt(1.4 * pb * ib);
+  const double lam = fmax(fabs(una) + ca, fabs(unb) + cb);
+  const double h = 0.5, hl = 0.5 * lam;
   Fs[0] = h * (a[0] * una + b[0] * unb) - hl * (b[0] - a[0]);
   Fs[1] = h * (a[1] * una + pa * nx + b[1] * unb + pb * nx) - hl * (b[1] - a[1]);
   Fs[2] = h * (a[2] * una + pa * ny + b[2] * unb + pb * ny) - hl * (b[2] - a[2]);
   Fs[3] = h * ((a[3] + pa) * una + (b[3] + pb) * unb) - hl * (b[3] - a[3]);
 }
 
-// acc += volume integral of element with state c and inverse Jacobian ji
-template <int P, typename CT>
-__device__ __forceinline__ void volume_acc(const CT (&c)[TriDim<P>::NV], const double* __restrict__ ji,
-                                           CT (&acc)[TriDim<P>::NV]) {
+template <int P>
+__device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], const double* __restrict__ ji,
+                                             double (&acc)[TriDim<P>::NV]) {
   using D = TriDim<P>;
   constexpr int NP = D::NP;
-  const TriTab<CT, P>& K = tri_tab<CT, P>();
+  const TriTab<double, P>& K = tri_tab<double, P>();
   const double2 j0 = __ldg(reinterpret_cast<const double2*>(ji));
   const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
-  const CT rx = (CT)j0.x, ry = (CT)j0.y, sx = (CT)j1.x, sy = (CT)j1.y;
 #pragma unroll
   for (int q = 0; q < D::NQV; ++q) {
-    CT U[4];
+    double U[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      CT s = CT(0);
+      double s = 0.0;
 #pragma unroll
       for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * c[m * NP + j];
       U[m] = s;
     }
-    CT F[4], G[4];
+    double F[4], G[4];
     euler_xy(U, F, G);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const CT fr = rx * F[m] + ry * G[m];
-      const CT fs = sx * F[m] + sy * G[m];
+      const double fr = j0.x * F[m] + j0.y * G[m];
+      const double fs = j1.x * F[m] + j1.y * G[m];
 #pragma unroll
       for (int j = 0; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * fr + K.vs[q][j] * fs;
     }
   }
 }
 
+// FP32 volume integral in perturbation form: sum_q w_q dF(U_q).(J^-T grad phi_j),
+// the constant F(ub) left out (it cancels against the faces); grad phi_0 = 0.
+template <int P>
+__device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRef<2>& R,
+                                             const double* __restrict__ ji, float (&acc)[TriDim<P>::NV]) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP;
+  const TriTab<float, P>& K = tri_tab<float, P>();
+  const double2 j0 = __ldg(reinterpret_cast<const double2*>(ji));
+  const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
+  const float nr[2] = {d2f(j0.x), d2f(j0.y)}, ns[2] = {d2f(j1.x), d2f(j1.y)};
+  const float thr = R.u[1] * nr[0] + R.u[2] * nr[1], ths = R.u[1] * ns[0] + R.u[2] * ns[1];
+#pragma unroll
+  for (int q = 0; q < D::NQV; ++q) {
+    float d[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float s = B.lo[m];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * B.cd[m][j - 1];
+      d[m] = s;
+    }
+    PertState<2> S;
+    S.init(R, d);
+    float Fr[4], Fs[4];
+    pert_flux<2>(R, S, d, nr, thr, Fr);
+    pert_flux<2>(R, S, d, ns, ths, Fs);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 1; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * Fr[m] + K.vs[q][j] * Fs[m];
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Volume kernel: one thread per element, rhs = volume integral (plain store).
+// Volume kernel (unfused path): one thread per element, rhs = volume integral.
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
 __global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, const double* __restrict__ jinv,
@@ -222,19 +320,33 @@ __global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, const
   using D = TriDim<P>;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
-  CT v[D::NV], acc[D::NV];
-  load_block(c + e * D::NV, v);
-#pragma unroll
-  for (int i = 0; i < D::NV; ++i) acc[i] = CT(0);
-  volume_acc<P>(v, jinv + 4 * e, acc);
   RT out[D::NV];
+  if constexpr (sizeof(CT) == 8) {
+    double v[D::NV], acc[D::NV];
+    load_block(c + e * D::NV, v);
 #pragma unroll
-  for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+    for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
+    volume_acc64<P>(v, jinv + 4 * e, acc);
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+  } else {
+    constexpr int stride = sizeof(ST) == 8 ? D::NV : D::NF;
+    PertBlock<P> B;
+    load_pert<P>(c + e * stride, B);
+    PertRef<2> R;
+    R.init(B.hi);
+    float acc[D::NV];
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) acc[i] = 0.0f;
+    volume_acc32<P>(B, R, jinv + 4 * e, acc);
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+  }
   store_block(rhs + e * D::NV, out);
 }
 
 // ---------------------------------------------------------------------------
-// Surface kernel for one color (or all edges for the atomic comparator).
+// Surface kernel for one color (or all edges for the comparators).
 // ---------------------------------------------------------------------------
 struct SurfParams {
   int64_t begin, end;
@@ -247,84 +359,12 @@ struct SurfParams {
   StageArgs sa;
 };
 
-template <int P, typename CT, typename ST, typename RT, int MODE>
-__global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
+// the contribution of one lane's element is in acc; write it as the mode asks
+template <int P, typename RT, int MODE, typename AT>
+__device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, int64_t k, int side,
+                                           const AT (&acc)[TriDim<P>::NV]) {
   using D = TriDim<P>;
-  constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV;
-  __shared__ CT sphi[3 * NQ * NP];
-  __shared__ CT sw[NQ];
-  {
-    const TriTab<CT, P>& K = tri_tab<CT, P>();
-    const CT* src = &K.phiE[0][0][0];
-    for (int i = threadIdx.x; i < 3 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
-    if (threadIdx.x < NQ) sw[threadIdx.x] = K.wE[threadIdx.x];
-  }
-  __syncthreads();
-
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t k = A.begin + (t >> 1);
-  const int side = (int)(t & 1);
-  const bool valid = k < A.end;
-  if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
-  const int4 tp = A.topo[k];
-  const bool bnd = tp.y < 0;       // boundary: both lanes read the left element (U+ = U-)
-  const bool right = side && !bnd;
-  const int64_t elem = right ? tp.y : tp.x;
-  const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
-  const bool writer = valid && !(side && bnd);
-
-  CT c[NV];
-  if constexpr (MODE == SURF_LAST) {
-    double tmp[NV];
-    load_plain(static_cast<const double*>(A.state) + elem * NV, tmp);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) c[i] = (CT)tmp[i];
-  } else {
-    load_block(static_cast<const ST*>(A.state) + elem * NV, c);
-  }
-  CT acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = CT(0);
-  if constexpr (MODE == SURF_FIRST) volume_acc<P>(c, A.jinv + 4 * elem, acc);
-
-  const double2 g0 = A.fgeo[2 * k], g1 = A.fgeo[2 * k + 1];
-  const CT nx = (CT)g0.x, ny = (CT)g0.y;
-  const CT scale = right ? (CT)g1.y : -(CT)g1.x;
-  const CT* ph = sphi + le * NQ * NP;
-
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const int qq = right ? NQ - 1 - q : q;  // the right element runs along the edge backwards
-    CT phi[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) phi[j] = ph[qq * NP + j];
-    CT U[4], V[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      CT s = CT(0);
-#pragma unroll
-      for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
-      U[m] = s;
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
-    CT a[4], b[4], Fs[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      a[m] = side ? V[m] : U[m];  // left trace
-      b[m] = side ? U[m] : V[m];  // right trace
-    }
-    lf_flux(a, b, nx, ny, Fs);
-    const CT s = scale * sw[q];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const CT g = s * Fs[m];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
-    }
-  }
-  if (!writer) return;
-
+  constexpr int NV = D::NV;
   if constexpr (MODE == SURF_RMW) {
     RT* r = static_cast<RT*>(A.rhs) + elem * NV;
     RT old[NV];
@@ -346,84 +386,240 @@ __global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
     store_block(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
-  } else {  // SURF_LAST: rhs = partial + this color; stage update in FP64
-    RT part[NV];
-    load_plain(static_cast<const RT*>(A.rhs) + elem * NV, part);
-    const double dt = *A.sa.dt;
-    const double a0 = A.sa.a0, b0 = A.sa.b0;
-    double us[NV], u[NV];
-    load_plain(static_cast<const double*>(A.state) + elem * NV, us);
-    if (a0 != 0.0) load_plain(A.sa.u0 + elem * NV, u);
+  } else {  // SURF_LAST: L = partial rhs + this color; FP64 stage update
+    // uout = a0 u0 + b0 us + (b0 dt) L in FP64, two values at a time:
+    // 1 FMA per value in the first stage, 1 MUL + 2 FMA in the others
+    const RT* part = static_cast<const RT*>(A.rhs) + elem * NV;
+    const double2* us2 = reinterpret_cast<const double2*>(static_cast<const double*>(A.state) + elem * NV);
+    const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
+    double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
+    float* rec = A.sa.shadow ? A.sa.shadow + elem * D::NF : nullptr;
+    const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
+    const double phi0 = tri_tab<double, P>().phiV[0][0];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const double L = (double)part[i] + (double)acc[i];
-      const double v = b0 * (us[i] + dt * L);
-      u[i] = a0 != 0.0 ? a0 * u[i] + v : v;
-    }
-    store_block(A.sa.uout + elem * NV, u);
-    if (A.sa.shadow) {
-      float f[NV];
+    for (int i = 0; i < NV; i += 2) {
+      const double2 s = us2[i / 2];
+      const double L0 = widen(part[i] + (RT)acc[i]), L1 = widen(part[i + 1] + (RT)acc[i + 1]);
+      double v[2];
+      if (a0 == 0.0) {
+        v[0] = fma(bdt, L0, b0 == 1.0 ? s.x : b0 * s.x);
+        v[1] = fma(bdt, L1, b0 == 1.0 ? s.y : b0 * s.y);
+      } else {
+        const double2 u = u02[i / 2];
+        v[0] = fma(bdt, L0, fma(a0, u.x, b0 * s.x));
+        v[1] = fma(bdt, L1, fma(a0, u.y, b0 * s.y));
+      }
+      out2[i / 2] = make_double2(v[0], v[1]);
+      if (rec) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) f[i] = (float)u[i];
-      store_block(A.sa.shadow + elem * NV, f);
+        for (int t = 0; t < 2; ++t) {
+          const int m = (i + t) / D::NP, j = (i + t) % D::NP;  // compile-time after unrolling
+          if (j == 0) split_mean(phi0, v[t], rec[m], rec[4 + m]);
+          else rec[8 + m * (D::NP - 1) + j - 1] = d2f(v[t]);
+        }
+      }
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// CFL reduction, FP64: dt = cfl min_e r_e / ((2p+1) max_q (|u| + c)).
-// Positive doubles order like their bit patterns, so the block minima are
-// combined with one 64-bit atomicMin; dt must hold a large value beforehand.
-// Optionally writes the FP32 copy of the state (mixed precision).
-// ---------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(128) k_cfl_tri(const double* __restrict__ c, const double* __restrict__ inr,
-                                                 int64_t ne, double cfl, unsigned long long* dtbits,
-                                                 float* __restrict__ shadow) {
+template <int P, typename CT, typename ST, typename RT, int MODE>
+__global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
-  constexpr int NP = D::NP;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double best = DBL_MAX;
-  if (e < ne) {
-    double v[D::NV];
-    load_block(c + e * D::NV, v);
-    if (shadow) {
-      float f[D::NV];
+  constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV;
+  __shared__ CT sphi[3 * NQ * NP];
+  __shared__ CT sw[NQ];
+  {
+    const TriTab<CT, P>& K = tri_tab<CT, P>();
+    const CT* src = &K.phiE[0][0][0];
+    for (int i = threadIdx.x; i < 3 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
+    if (threadIdx.x < NQ) sw[threadIdx.x] = K.wE[threadIdx.x];
+  }
+  __syncthreads();
+
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t k = A.begin + (t >> 1);
+  const int side = (int)(t & 1);
+  const bool valid = k < A.end;
+  if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
+  const int4 tp = A.topo[k];
+  const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
+  const bool right = side && !bnd;
+  const int64_t elem = right ? tp.y : tp.x;
+  const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
+  const bool writer = valid && !(side && bnd);
+  const double2 g0 = A.fgeo[2 * k], g1 = A.fgeo[2 * k + 1];
+  const CT* ph = sphi + le * NQ * NP;
+  // (in SURF_LAST the state may alias the stage output, but each element's
+  // block is read and written by its own lane only)
+
+  if constexpr (sizeof(CT) == 8) {
+    // ---------------- FP64: Eq. 2 as written ----------------
+    double c[NV], acc[NV];
+    load_block(static_cast<const double*>(A.state) + elem * NV, c);
 #pragma unroll
-      for (int i = 0; i < D::NV; ++i) f[i] = (float)v[i];
-      store_block(shadow + e * D::NV, f);
-    }
-    const TriTab<double, P>& K = tri_tab<double, P>();
-    double lam = 0.0;
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    if constexpr (MODE == SURF_FIRST) volume_acc64<P>(c, A.jinv + 4 * elem, acc);
+    const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
 #pragma unroll
-    for (int q = 0; q < D::NQV; ++q) {
-      double U[4];
+    for (int q = 0; q < NQ; ++q) {
+      const int qq = right ? NQ - 1 - q : q;  // the right element runs along the edge backwards
+      double phi[NP], U[4], V[4], a[4], b[4], Fs[4];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) phi[j] = ph[qq * NP + j];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         double s = 0.0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * v[m * NP + j];
+        for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
         U[m] = s;
       }
-      const double ir = 1.0 / U[0], u = U[1] * ir, w = U[2] * ir;
-      const double q2 = u * u + w * w;
-      const double pr = 0.4 * (U[3] - 0.5 * U[0] * q2);
-      lam = fmax(lam, sqrt(q2) + sqrt(1.4 * pr * ir));
+#pragma unroll
+      for (int m = 0; m < 4; ++m) V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        a[m] = side ? V[m] : U[m];
+        b[m] = side ? U[m] : V[m];
+      }
+      lf_flux(a, b, nx, ny, Fs);
+      const double s = scale * sw[q];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double g = s * Fs[m];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+      }
     }
+    if (writer) surf_write<P, RT, MODE>(A, elem, k, side, acc);
+  } else {
+    // ---------------- FP32: perturbation form ----------------
+    constexpr int stride = sizeof(ST) == 8 ? NV : D::NF;
+    PertBlock<P> B;
+    load_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
+    PertRef<2> R;
+    R.init(B.hi);
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
+    if constexpr (MODE == SURF_FIRST) volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
+    // the partner's mean relative to ours: base = (hi_o - hi_s) + lo_o
+    float base[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float ho = __shfl_xor_sync(0xffffffffu, B.hi[m], 1);
+      const float lo = __shfl_xor_sync(0xffffffffu, B.lo[m], 1);
+      base[m] = (ho - B.hi[m]) + lo;
+    }
+    const float n[2] = {d2f(g0.x), d2f(g0.y)};
+    const float scale = right ? d2f(g1.y) : -d2f(g1.x);
+    const float thb = R.u[1] * n[0] + R.u[2] * n[1];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int qq = right ? NQ - 1 - q : q;
+      float phi[NP], dU[4], dV[4], ds[4], dn[4], G[4];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) phi[j] = ph[qq * NP + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 1; j < NP; ++j) s += phi[j] * B.cd[m][j - 1];
+        dU[m] = s;
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) dV[m] = __shfl_xor_sync(0xffffffffu, dU[m], 1);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        ds[m] = B.lo[m] + dU[m];  // own trace - ub
+        dn[m] = base[m] + dV[m];  // partner's trace - ub
+      }
+      if (side) pert_lf<2>(R, dn, ds, n, thb, G);  // left trace = partner's
+      else pert_lf<2>(R, ds, dn, n, thb, G);
+      const float s = scale * sw[q];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float g = s * G[m];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+      }
+    }
+    if (writer) surf_write<P, RT, MODE>(A, elem, k, side, acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CFL reduction: dt = cfl min_e r_e / ((2p+1) max_q (|u| + c)), exact FP64.
+// Pass 1 (FP32 arithmetic): every element's estimate, stored, and their
+// minimum (one atomicMin per block on the bit pattern); also writes the FP32
+// record of the state when asked.  Pass 2 (FP64): only elements whose estimate
+// is within kCflMargin of the minimum are evaluated in FP64 and combined with
+// one 64-bit atomicMin.  Both minima must hold a large value beforehand.
+// ---------------------------------------------------------------------------
+template <int P, typename T>
+__device__ __forceinline__ T lambda_max(const T (&v)[TriDim<P>::NV]) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP;
+  const TriTab<T, P>& K = tri_tab<T, P>();
+  T lam = T(0);
+#pragma unroll
+  for (int q = 0; q < D::NQV; ++q) {
+    T U[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * v[m * NP + j];
+      U[m] = s;
+    }
+    const T ir = T(1) / U[0], u = U[1] * ir, w = U[2] * ir;
+    const T q2 = u * u + w * w;
+    const T pr = T(0.4) * (U[3] - T(0.5) * U[0] * q2);
+    lam = fmax(lam, sqrt(q2) + sqrt(T(1.4) * pr * ir));
+  }
+  return lam;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_cfl1_tri(const double* __restrict__ c, const double* __restrict__ inr,
+                                                  int64_t ne, float* __restrict__ est, unsigned* minbits,
+                                                  float* __restrict__ shadow) {
+  using D = TriDim<P>;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float best = FLT_MAX;
+  if (e < ne) {
+    double v[D::NV];
+    load_block(c + e * D::NV, v);
+    if (shadow) {
+      float r[D::NF];
+      record_of<P>(v, r);
+      store_block(shadow + e * D::NF, r);
+    }
+    float f[D::NV];
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) f[i] = d2f(v[i]);
+    const float lam = lambda_max<P, float>(f);
+    float d = d2f(__ldg(inr + e)) / ((2 * P + 1) * lam);
+    if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;  // non-physical: always re-evaluated
+    est[e] = d;
+    best = d;
+  }
+  block_min_to(best, minbits);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_cfl2_tri(const double* __restrict__ c, const double* __restrict__ inr,
+                                                  int64_t ne, double cfl, const float* __restrict__ est,
+                                                  const unsigned* minbits, unsigned long long* dtbits) {
+  using D = TriDim<P>;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double best = DBL_MAX;
+  if (e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin)) {
+    double v[D::NV];
+    load_block(c + e * D::NV, v);
+    const double lam = lambda_max<P, double>(v);
     best = cfl * (__ldg(inr + e) / ((2 * P + 1) * lam));
     if (!(best > 0.0)) best = DBL_MAX;  // non-physical state: excluded (NaN)
   }
-  // block minimum
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-  __shared__ double wmin[32];
-  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = wmin[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, wmin[w]);
-    atomicMin(dtbits, (unsigned long long)__double_as_longlong(b));
-  }
+  block_min_to(best, dtbits);
 }
 
 // ---------------------------------------------------------------------------
@@ -484,7 +680,9 @@ static int surf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const SurfParams& A) 
   switch (ty) {
     case TY_D: return surf_mode<P, double, double, double>(x, mode, A);
     case TY_MD: return surf_mode<P, float, double, double>(x, mode, A);
-    case TY_MF: return surf_mode<P, float, float, float>(x, mode, A);
+    case TY_MF:
+      if (mode != SURF_RMW && mode != SURF_FIRST) return -1;
+      return surf_mode<P, float, float, float>(x, mode, A);
     default: return -1;
   }
 }
@@ -513,10 +711,22 @@ int tri_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow
   const int bs = 128;
   const unsigned grid = (unsigned)((x.ne + bs - 1) / bs);
   auto* bits = reinterpret_cast<unsigned long long*>(dt);
+  float* est = x.d->cfl_est;
+  unsigned* mn = reinterpret_cast<unsigned*>(x.d->cfl_est + x.ne);
+  if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
   switch (x.p) {
-    case 1: k_cfl_tri<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, bits, shadow); return 1;
-    case 2: k_cfl_tri<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, bits, shadow); return 1;
-    case 3: k_cfl_tri<3><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, bits, shadow); return 1;
+    case 1:
+      k_cfl1_tri<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
+      k_cfl2_tri<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    case 2:
+      k_cfl1_tri<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
+      k_cfl2_tri<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    case 3:
+      k_cfl1_tri<3><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
+      k_cfl2_tri<3><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
     default: return -1;
   }
 }

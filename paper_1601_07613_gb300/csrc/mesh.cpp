@@ -286,6 +286,33 @@ RefTables make_tables(int dim, int p) {
   return T;
 }
 
+// Face points in the face's own parameters (s, t): reconstructed from the
+// table's first face (vertex order a0 < a1 < a2, point = a0 + s(a1-a0) + t(a2-a0)).
+const int kFacePerms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+std::vector<double> tet_face_orient_tables(const RefTables& T) {
+  // barycentric coordinates of the face points (lambda_0 = 1 - s - t, s, t)
+  std::vector<double> fa, fb, w;
+  tri_rule(T.p + 2, fa, fb, w);
+  std::vector<double> out((size_t)4 * 6 * T.nqf * T.np);
+  std::vector<double> phi(T.np);
+  for (int f = 0; f < 4; ++f) {
+    int fv[3];
+    face_vertices(3, f, fv);
+    for (int o = 0; o < 6; ++o)
+      for (int q = 0; q < T.nqf; ++q) {
+        const double lam[3] = {1.0 - fa[q] - fb[q], fa[q], fb[q]};
+        // vertex i of this face carries the weight of vertex perm[i] of the other side's face
+        double x[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i)
+          for (int a = 0; a < 3; ++a) x[a] += lam[kFacePerms[o][i]] * kTetV[fv[i]][a];
+        basis_eval(3, T.p, x, phi.data(), nullptr);
+        for (int j = 0; j < T.np; ++j) out[(((size_t)f * 6 + o) * T.nqf + q) * T.np + j] = phi[j];
+      }
+  }
+  return out;
+}
+
 // ---------------------------------------------------------------------------
 // Mesh ingest: edge table (Sec. 5, "an edge points to the two elements that
 // share it") with open-addressing hashing of sorted vertex keys.

@@ -47,9 +47,9 @@ SIGNATURES = {
     "dgc_export_state": (C.c_int, [_P, _P, _DP, _P]),
     "dgc_rhs": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dgc_cfl_dt": (C.c_int, [_P, _P, C.c_double, _P, _P]),
-    "dgc_rk_step": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P, _P]),
+    "dgc_rk_step": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P, _I64, _P]),
     "dgc_rhs_atomic": (C.c_int, [_P, C.c_int, _P, _P, _P]),
-    "dgc_rhs_two_pass": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "dgc_rhs_two_pass": (C.c_int, [_P, C.c_int, _P, _P, _P, _I64, _P]),
     "dgc_two_pass_buffer_bytes": (C.c_int, [_I64, C.c_int, C.c_int, C.c_int, _I64P]),
     "dgc_set_option": (C.c_int, [_P, C.c_int, _I64]),
     "dgc_profile_collect": (C.c_int, [_P, _DP, _I64P]),
@@ -219,18 +219,26 @@ def dgc_cfl_dt(mesh, c_dev, cfl: float, dt_dev, stream=None):
     _check(lib().dgc_cfl_dt(mesh, _dptr(c_dev), cfl, _dptr(dt_dev), _stream(stream)))
 
 
-def dgc_rk_step(mesh, prec: int, c_dev, cfl: float, dt_dev, workspace_dev, stream=None):
+def _nbytes(a, nbytes):
+    if nbytes is not None:
+        return nbytes
+    return a.numel() * a.element_size()
+
+
+def dgc_rk_step(mesh, prec: int, c_dev, cfl: float, dt_dev, workspace_dev, workspace_bytes=None, stream=None):
+    """workspace_bytes defaults to the size of the workspace tensor."""
     _check(lib().dgc_rk_step(mesh, prec, _dptr(c_dev), cfl, _dptr(dt_dev), _dptr(workspace_dev),
-                             _stream(stream)))
+                             _nbytes(workspace_dev, workspace_bytes), _stream(stream)))
 
 
 def dgc_rhs_atomic(mesh, prec: int, c_dev, rhs_dev, stream=None):
     _check(lib().dgc_rhs_atomic(mesh, prec, _dptr(c_dev), _dptr(rhs_dev), _stream(stream)))
 
 
-def dgc_rhs_two_pass(mesh, prec: int, c_dev, rhs_dev, buffer_dev, stream=None):
+def dgc_rhs_two_pass(mesh, prec: int, c_dev, rhs_dev, buffer_dev, buffer_bytes=None, stream=None):
+    """buffer_bytes defaults to the size of the buffer tensor."""
     _check(lib().dgc_rhs_two_pass(mesh, prec, _dptr(c_dev), _dptr(rhs_dev), _dptr(buffer_dev),
-                                  _stream(stream)))
+                                  _nbytes(buffer_dev, buffer_bytes), _stream(stream)))
 
 
 def dgc_two_pass_buffer_bytes(sides: int, np_: int, neq: int, word_bytes: int = 8) -> int:

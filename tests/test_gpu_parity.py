@@ -118,7 +118,7 @@ def test_rhs_fp32_mixed_matches_oracle(torch_dev, oracle_mod, p, name, make):
     run.close()
 
 
-@pytest.mark.parametrize("epb", [16, 64, 256, 512])
+@pytest.mark.parametrize("epb", [16, 32, 64, 128])
 def test_rhs_tile_shapes(torch_dev, oracle_mod, epb):
     mi = W.periodic_square_tri(23, jitter=0.2, seed=5)
     run = Run(torch_dev, mi, 3, epb=epb)
@@ -247,15 +247,27 @@ def big(torch_dev, oracle_mod):
     run.close()
 
 
-def test_full_size_rhs_sampled(big):
+def _oracle_floor(om, oracle_mod, mi, p, c, sample):
+    """Agreement floor of two exact FP64 evaluations at this resolution: the
+    oracle against itself on the same mesh translated by half a period (an exact
+    symmetry; only the rounding of the coordinates changes)."""
+    om2 = oracle_mod.OracleMesh(2, (mi.xyz + 0.5) % 1.0, mi.ev, mi.periodic_len)
+    return rel(om2.rhs(p, c, elems=sample), om.rhs(p, c, elems=sample))
+
+
+def test_full_size_rhs_sampled(big, oracle_mod):
     run, om, c = big
     run.load(c)
     sample = np.random.default_rng(0).choice(om.ne, 3000, replace=False)
     ref = om.rhs(3, c, elems=sample)
     got64 = run.rhs(dgc.DGC_FP64)[sample]
     got32 = run.rhs(dgc.DGC_FP32_MIXED)[sample]
-    assert rel(got64, ref) < 1e-12
-    assert rel(got32, ref) < 1e-5
+    floor = _oracle_floor(om, oracle_mod, run.mi, 3, c, sample)
+    e64, e32 = rel(got64, ref), rel(got32, ref)
+    print(f"full size: FP64 rel L2 {e64:.3e} (oracle self-consistency {floor:.3e}), FP32-mixed {e32:.3e}")
+    # FP64: 1e-12, or twice the oracle's own rounding floor where that is larger
+    assert e64 < max(1e-12, 2.0 * floor)
+    assert e32 < 1e-5
 
 
 def test_full_size_rk_step_sampled(big, oracle_mod):
@@ -271,8 +283,80 @@ def test_full_size_rk_step_sampled(big, oracle_mod):
     u2 = np.zeros_like(c)
     u2[s1] = 0.75 * c[s1] + 0.25 * (u1[s1] + dt * om.rhs(p, u1, elems=s1))
     u3 = c[s0] / 3.0 + 2.0 / 3.0 * (u2[s0] + dt * om.rhs(p, u2, elems=s0))
-    for prec, tol in ((dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)):
+    floor = _oracle_floor(om, oracle_mod, run.mi, p, c, s0)
+    for prec, tol in ((dgc.DGC_FP64, max(1e-11, 2.0 * floor)), (dgc.DGC_FP32_MIXED, 1e-5)):
         run.load(c)
         got, dtg = run.rk(prec, 0.3)
+        err = rel(got[s0] - c[s0], u3 - c[s0])
+        print(f"full size RK step, prec {prec}: du rel L2 {err:.3e} (tolerance {tol:.1e}), dt rel {abs(dtg - dt) / dt:.1e}")
         assert abs(dtg - dt) < 1e-13 * dt
-        assert rel(got[s0] - c[s0], u3 - c[s0]) < tol
+        assert err < tol
+
+
+# ------------------------------------------------------------------------------------------
+# Tetrahedra (4-face coloring, Sec. 3): periodic Kuhn cubes
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("fuse", [True, False])
+def test_tet_rhs_matches_oracle(torch_dev, oracle_mod, p, fuse):
+    mi = W.periodic_cube_tet(7)  # 2058 tets, 1029 faces per color
+    run = Run(torch_dev, mi, p, fuse=fuse)
+    assert run.m.info["ncolors"] == 4
+    c = W.random_state(mi.ne, 5, run.m.info["np"], seed=p, mean=(0.5, 0.05, -0.04, 0.03, 1.3))
+    run.load(c)
+    ref = oracle_mod.OracleMesh.from_input(mi).rhs(p, c)
+    assert rel(run.rhs(dgc.DGC_FP64), ref) < 1e-12
+    assert rel(run.rhs(dgc.DGC_FP32_MIXED), ref) < 1e-5
+    for kind in ("atomic", "two_pass"):
+        assert rel(run.rhs(dgc.DGC_FP64, kind), ref) < 1e-12
+    run.close()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_tet_rk_step_matches_oracle(torch_dev, oracle_mod, p):
+    mi = W.periodic_cube_tet(6)
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz, _, _ = om.eval_points(p)
+    c = om.project(p, W.vortex_tube_field(xyz[..., 0], xyz[..., 1], xyz[..., 2]))
+    ref, dt_ref = om.rk_step(p, c, 0.3)
+    for prec, tol in ((dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)):
+        run = Run(torch_dev, mi, p)
+        run.load(c)
+        got, dt = run.rk(prec, 0.3)
+        assert abs(dt - dt_ref) < 1e-13 * dt_ref
+        assert rel(got - c, ref - c) < tol
+        run.close()
+
+
+def test_fp32_record_is_correctly_rounded(torch_dev):
+    """The FP32 record of the state the mixed-precision step keeps: the mean
+    state phi_0 c_0 as an FP32 pair hi + lo, then the modes j >= 1 as FP32.
+    Both are converted with integer bit operations; they must equal the
+    hardware round-to-nearest conversion bit for bit."""
+    torch, dev = torch_dev
+    mi = W.periodic_square_tri(20, jitter=0.2, seed=11)
+    run = Run(torch_dev, mi, 2)
+    c = state_for(mi, run.m.info["np"], seed=11, amp=5e-2)
+    run.load(c)
+    ws = torch.zeros(dgc.dgc_workspace_size(run.m.h, dgc.DGC_FP32_MIXED) // 8 + 64, dtype=torch.float64, device=dev)
+    d = torch.zeros(1, dtype=torch.float64, device=dev)
+    dgc.dgc_rk_step(run.m.h, dgc.DGC_FP32_MIXED, run.c, 0.3, d, ws)
+    torch.cuda.synchronize()
+    E, M, NP = run.c.shape
+    S = run.c.numel() * 8
+    off = (S + 255) // 256 * 256
+    nrec = M * (NP + 1)
+    rec = ws.view(torch.uint8)[off:off + 4 * E * nrec].view(torch.float32).reshape(E, nrec)
+    u = run.c
+    assert torch.equal(rec[:, 2 * M:].reshape(E, M, NP - 1), u[:, :, 1:].float())
+    # the mean phi_0 c_0 (phi_0 = sqrt 2 from the library's normalised table, to an ulp):
+    # hi is its FP32 rounding and lo the FP32 rounding of the remainder
+    mean = u[:, :, 0] * np.sqrt(2.0)
+    hi, lo = rec[:, :M], rec[:, M:2 * M]
+    ulp32 = torch.abs(mean.float()).double() * 2.0 ** -23
+    assert torch.all(torch.abs(hi.double() - mean) <= 0.5 * ulp32 + 4e-16 * torch.abs(mean))
+    assert torch.all(torch.abs(hi.double() + lo.double() - mean) <= 1e-15 * torch.abs(mean))
+    assert torch.equal(lo, (mean - hi.double()).float()) or \
+        torch.all(torch.abs(lo.double() - (mean - hi.double())) <= 4e-16 * torch.abs(mean))
+    run.close()

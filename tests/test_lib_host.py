@@ -157,3 +157,21 @@ def test_naive_coloring_ablation(L):
     info = dgc.dgc_mesh_info(m.h)
     assert info["ncolors"] == nc and info["perfect"] == 0
     m.close()
+
+
+def test_buffer_sizes_are_checked_before_device_work(L):
+    """The RK workspace and the two-pass buffer carry their sizes; too small is an
+    argument error returned on the host, before anything is enqueued."""
+    m = dgc.Mesh.from_input(W.periodic_square_tri(8), 2)
+    m.color(1)
+    need = dgc.dgc_workspace_size(m.h, dgc.DGC_FP32_MIXED)
+    assert need >= dgc.dgc_workspace_size(m.h, dgc.DGC_FP64) - 512  # mixed keeps an FP32 record too
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rk_step(m.h, dgc.DGC_FP32_MIXED, 4096, 0.3, 8192, 1 << 20, workspace_bytes=need - 1, stream=0)
+    assert e.value.status == 1 and "workspace" in str(e.value)
+    info = m.info
+    nb = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rhs_two_pass(m.h, dgc.DGC_FP64, 4096, 8192, 1 << 20, buffer_bytes=nb - 8, stream=0)
+    assert e.value.status == 1 and "buffer" in str(e.value)
+    m.close()
