@@ -66,8 +66,10 @@ typedef enum {
                                   kernel, every color read-modify-writes rhs (Alg. 1) */
   DGC_OPT_EDGES_PER_BLOCK = 1, /* surface-kernel tile: edges per thread block (16..128, x16) */
   DGC_OPT_THREADS_PER_EDGE = 2, /* 2 (one thread per edge side); reserved for tuning */
-  DGC_OPT_PROFILE = 3           /* 1: record a CUDA event pair around every kernel launch, on
+  DGC_OPT_PROFILE = 3,          /* 1: record a CUDA event pair around every kernel launch, on
                                    the launch stream, for dgc_profile_collect; 0 (default): off */
+  DGC_OPT_GRAPH = 4             /* batches: 1 (default) capture the step in a CUDA graph on the
+                                   first call and replay it; 0: launch the kernels directly */
 } dgc_option;
 
 /* Kernel classes reported by dgc_profile_collect. */
@@ -86,7 +88,7 @@ typedef enum {
 
 /* Mesh ingest (Sec. 2 connectivity graph; Sec. 5 edge table).
  * dim = 2 (triangles, CCW vertex order) or 3 (tetrahedra, positive volume).
- * p = polynomial order (triangles 0..3, tetrahedra 1..2 in this build).
+ * p = polynomial order (triangles 1..3, tetrahedra 1..2 in this build).
  * xyz: nv*dim FP64 vertex coordinates, row-major.  ev: ne*(dim+1) int32 vertex ids.
  * periodic_len: NULL, or dim period lengths; periodic meshes identify faces across
  * the period by shared vertex ids and unwrap each element to lie within half a period
@@ -205,8 +207,38 @@ dgc_status dgc_profile_collect(dgc_mesh* mesh, double* ms, int64_t* launches);
 /* Number of kernels the last device call on this mesh enqueued. */
 dgc_status dgc_last_launch_count(const dgc_mesh* mesh, int64_t* launches);
 
+/* Batches: many independent triangle meshes of uneven size and order advanced together.
+ * Each kernel class of the SSP-RK3 step (CFL passes; first / middle / last color of
+ * Algorithm 1 in each stage) is ONE persistent launch over all meshes: the work is cut
+ * into tiles of at most DGC_OPT_EDGES_PER_BLOCK edges (128 elements for the CFL), tiles
+ * sorted by order p, each block walking tiles blockIdx, blockIdx + gridDim, ...  With
+ * DGC_OPT_GRAPH (default) the 12 launches of a step are captured in a CUDA graph on the
+ * first call and replayed while the buffers, precision, tile size and cfl stay the same.
+ * The meshes must be colored triangle meshes in which every element has one edge of each
+ * of the 3 colors (closed conforming meshes), and must outlive the batch.
+ *   dgc_batch_rk_step: c_devs = host array of n device states (each [E_i][4][Np_i], FP64);
+ *   dt_devs = device array of n doubles (each mesh's CFL step); workspace of
+ *   dgc_batch_workspace_size() bytes, 256-byte aligned.  The first call with a new set of
+ *   buffers uploads the meshes and the tile tables synchronously (make it before any
+ *   capture); later calls are asynchronous.  Results equal dgc_rk_step on each mesh.
+ *   dgc_batch_autotune: runs 1 + reps steps per tile size (16, 32, 64, 128 edges per
+ *   block) -- the states advance -- keeps the fastest and returns it, with the measured
+ *   ms per step in ms_per_step[4] (may be NULL). */
+dgc_status dgc_batch_create(int n, dgc_mesh* const* meshes, dgc_batch** out);
+dgc_status dgc_batch_workspace_size(const dgc_batch* batch, dgc_prec prec, int64_t* bytes);
+dgc_status dgc_batch_set_option(dgc_batch* batch, dgc_option opt, int64_t value);
+dgc_status dgc_batch_rk_step(dgc_batch* batch, dgc_prec prec, double* const* c_devs, double cfl,
+                             double* dt_devs, void* workspace_dev, int64_t workspace_bytes,
+                             void* stream);
+dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_devs, double cfl,
+                              double* dt_devs, void* workspace_dev, int64_t workspace_bytes,
+                              int reps, void* stream, int64_t* best_epb, double* ms_per_step);
+dgc_status dgc_batch_launch_count(const dgc_batch* batch, int64_t* launches);
+void dgc_batch_destroy(dgc_batch* batch);
+
 /* Thread-local message of the last error (empty string if none). */
 const char* dgc_last_error(void);
+
 
 /* Free the mesh and its device copies (the device must still be current). */
 void dgc_destroy(dgc_mesh* mesh);

@@ -5,6 +5,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <set>
 #include <string>
 #include <thread>
@@ -688,6 +689,285 @@ void dgc_destroy(dgc_mesh* mesh) {
   staging_free(*m);
   prof_free(*m);
   delete m;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent triangle meshes (uneven size and order): one
+// persistent launch per kernel class and RK stage covers every mesh, the whole
+// step optionally replayed from a CUDA graph.
+// ---------------------------------------------------------------------------
+struct dgc_batch {
+  std::vector<Mesh*> meshes;
+  int epb = 64;
+  bool use_graph = true;
+  int device = -1;
+  // device tables, rebuilt when the call's buffers or the tile size change
+  BatchMeshDev* dmeshes = nullptr;
+  BatchTile* dtiles = nullptr;  // colors 1..C then elements
+  int tile_off[8] = {0};        // tile ranges: color c in [tile_off[c-1], tile_off[c]), elements last
+  int ncolors = 0;
+  std::vector<double*> key_c;
+  double* key_dt = nullptr;
+  void* key_ws = nullptr;
+  int key_prec = -1, key_epb = -1;
+  cudaGraphExec_t exec = nullptr;
+  double graph_cfl = 0.0;
+  cudaStream_t graph_stream = nullptr;
+  int64_t launches = 0;
+};
+
+namespace {
+
+void batch_release(dgc_batch& b) {
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  b.exec = nullptr;
+  cudaFree(b.dmeshes);
+  cudaFree(b.dtiles);
+  b.dmeshes = nullptr;
+  b.dtiles = nullptr;
+  b.key_prec = -1;
+}
+
+int64_t batch_ws_bytes(const dgc_batch& b, dgc_prec prec) {
+  int64_t t = 0;
+  for (const Mesh* m : b.meshes) t += workspace_bytes(*m, prec);
+  return t;
+}
+
+// descriptors and tiles for this call's buffers (host work + one synchronous upload)
+void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* dt_devs, void* ws) {
+  const int n = (int)b.meshes.size();
+  bool same = b.dmeshes && b.key_prec == (int)prec && b.key_dt == dt_devs && b.key_ws == ws && b.key_epb == b.epb;
+  for (int i = 0; same && i < n; ++i) same = b.key_c[i] == c_devs[i];
+  if (same) return;
+  batch_release(b);
+  const bool mixed = prec == DGC_FP32_MIXED;
+  std::vector<BatchMeshDev> hm(n);
+  char* w = static_cast<char*>(ws);
+  for (int i = 0; i < n; ++i) {
+    Mesh& m = *b.meshes[i];
+    upload(m);
+    const int64_t S = state_bytes(m), R = align256(m.ne * record_floats(m) * 4);
+    BatchMeshDev& d = hm[i];
+    d.p = m.p;
+    d.ne = m.ne;
+    d.topo = m.dev->topo;
+    d.fgeo = m.dev->fgeo;
+    d.jinv = m.dev->jinv;
+    d.inr = m.dev->inr;
+    d.est = m.dev->cfl_est;
+    d.c = c_devs[i];
+    d.dt = dt_devs + i;
+    d.u1 = reinterpret_cast<double*>(w);
+    d.rec = mixed ? reinterpret_cast<float*>(w + align256(S)) : nullptr;
+    d.rhs = mixed ? (void*)(w + align256(S) + R) : (void*)(w + align256(S));
+    w += workspace_bytes(m, prec);
+  }
+  // tiles: every color's edges, then the elements; heavier orders first
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b.meshes[a]->p > b.meshes[c]->p; });
+  std::vector<BatchTile> tiles;
+  b.ncolors = b.meshes[0]->ncolors;
+  b.tile_off[0] = 0;
+  for (int c = 1; c <= b.ncolors; ++c) {
+    for (int i : order) {
+      const Mesh& m = *b.meshes[i];
+      for (int64_t s = m.color_off[c - 1]; s < m.color_off[c]; s += b.epb)
+        tiles.push_back({i, m.p, s, std::min<int64_t>(s + b.epb, m.color_off[c])});
+    }
+    b.tile_off[c] = (int)tiles.size();
+  }
+  for (int i : order) {
+    const Mesh& m = *b.meshes[i];
+    for (int64_t e = 0; e < m.ne; e += 128) tiles.push_back({i, m.p, e, std::min<int64_t>(e + 128, m.ne)});
+  }
+  b.tile_off[b.ncolors + 1] = (int)tiles.size();
+  b.dmeshes = dalloc<BatchMeshDev>(n);
+  b.dtiles = dalloc<BatchTile>((int64_t)tiles.size());
+  DGC_CUDA(cudaMemcpy(b.dmeshes, hm.data(), sizeof(BatchMeshDev) * n, cudaMemcpyHostToDevice));
+  DGC_CUDA(cudaMemcpy(b.dtiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
+  b.key_c.assign(c_devs, c_devs + n);
+  b.key_dt = dt_devs;
+  b.key_ws = ws;
+  b.key_prec = (int)prec;
+  b.key_epb = b.epb;
+}
+
+// the launches of one step: reset, CFL (2), then per stage the three colors
+int64_t batch_enqueue(dgc_batch& b, dgc_prec prec, double cfl_, cudaStream_t st) {
+  const bool mixed = prec == DGC_FP32_MIXED;
+  const int n = (int)b.meshes.size(), C = b.ncolors;
+  const int threads = 2 * b.epb;
+  int64_t launches = batch_init(st, b.dmeshes, n);
+  const BatchTile* et = b.dtiles + b.tile_off[C];
+  launches += batch_cfl(st, b.dmeshes, et, b.tile_off[C + 1] - b.tile_off[C], cfl_, mixed);
+  const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int s = 0; s < 3; ++s)
+    for (int c = 1; c <= C; ++c) {
+      const SurfMode mode = c == 1 ? SURF_FIRST : (c == C ? SURF_LAST : SURF_RMW);
+      const int r = batch_surf(st, b.dmeshes, b.dtiles + b.tile_off[c - 1], b.tile_off[c] - b.tile_off[c - 1], s,
+                               A0[s], B0[s], mode, mixed, threads);
+      if (r < 0) throw Error{DGC_ERR_UNSUPPORTED, "no batched kernel for this configuration"};
+      launches += r;
+    }
+  return launches;
+}
+
+dgc_batch& checked_batch(dgc_batch* b) {
+  require(b != nullptr, "null batch");
+  return *b;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgc_status dgc_batch_create(int n, dgc_mesh* const* meshes, dgc_batch** out) {
+  return guarded([&] {
+    require(out != nullptr && meshes != nullptr && n > 0, "need a positive number of meshes");
+    *out = nullptr;
+    auto b = std::make_unique<dgc_batch>();
+    for (int i = 0; i < n; ++i) {
+      Mesh& m = checked(meshes[i]);
+      require(m.dim == 2, "batches hold triangle meshes");
+      require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
+              "batched meshes must be colored with 3 colors, every element with one edge of each color");
+      b->meshes.push_back(&m);
+    }
+    *out = b.release();
+  });
+}
+
+dgc_status dgc_batch_workspace_size(const dgc_batch* batch, dgc_prec prec, int64_t* bytes) {
+  return guarded([&] {
+    require(batch != nullptr && bytes != nullptr, "null argument");
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    *bytes = batch_ws_bytes(*batch, prec);
+  });
+}
+
+dgc_status dgc_batch_set_option(dgc_batch* batch, dgc_option opt, int64_t value) {
+  return guarded([&] {
+    dgc_batch& b = checked_batch(batch);
+    if (opt == DGC_OPT_EDGES_PER_BLOCK) {
+      require(value >= 16 && value <= 128 && value % 16 == 0, "edges per block must be 16..128, a multiple of 16");
+      b.epb = (int)value;
+    } else if (opt == DGC_OPT_GRAPH) {
+      b.use_graph = value != 0;
+      if (b.exec) cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    } else {
+      throw Error{DGC_ERR_ARG, "option not available for batches"};
+    }
+  });
+}
+
+dgc_status dgc_batch_rk_step(dgc_batch* batch, dgc_prec prec, double* const* c_devs, double cfl_, double* dt_devs,
+                             void* workspace_dev, int64_t workspace_size, void* stream) {
+  return guarded([&] {
+    dgc_batch& b = checked_batch(batch);
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    require(c_devs != nullptr, "null state array");
+    for (size_t i = 0; i < b.meshes.size(); ++i) check_ptr(c_devs[i], "c_devs[i]");
+    require(dt_devs != nullptr && reinterpret_cast<uintptr_t>(dt_devs) % 8 == 0, "dt_devs must be an aligned device array");
+    require(workspace_dev != nullptr && reinterpret_cast<uintptr_t>(workspace_dev) % 256 == 0,
+            "workspace must be 256-byte aligned");
+    require(workspace_size >= batch_ws_bytes(b, prec), "workspace smaller than dgc_batch_workspace_size()");
+    require(cfl_ > 0.0, "cfl must be positive");
+    int dev = -1;
+    DGC_CUDA(cudaGetDevice(&dev));
+    require(b.device < 0 || b.device == dev, "batch was used on another device");
+    b.device = dev;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    batch_prepare(b, prec, c_devs, dt_devs, workspace_dev);
+    if (!b.use_graph) {
+      b.launches = batch_enqueue(b, prec, cfl_, st);
+    } else {
+      if (!b.exec || b.graph_cfl != cfl_) {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        cudaGraph_t g = nullptr;
+        DGC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int64_t n = 0;
+        try {
+          n = batch_enqueue(b, prec, cfl_, st);
+        } catch (...) {
+          cudaStreamEndCapture(st, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        DGC_CUDA(cudaStreamEndCapture(st, &g));
+        cudaError_t e = cudaGraphInstantiate(&b.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) throw Error{DGC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+        b.graph_cfl = cfl_;
+        b.launches = n;
+      }
+      DGC_CUDA(cudaGraphLaunch(b.exec, st));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error{DGC_ERR_CUDA, std::string("batched step: ") + cudaGetErrorString(e)};
+  });
+}
+
+dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_devs, double cfl_, double* dt_devs,
+                              void* workspace_dev, int64_t workspace_size, int reps, void* stream,
+                              int64_t* best_epb, double* ms_per_step) {
+  return guarded([&] {
+    dgc_batch& b = checked_batch(batch);
+    require(reps > 0 && best_epb != nullptr, "bad argument");
+    const int cand[4] = {16, 32, 64, 128};
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    DGC_CUDA(cudaEventCreate(&e0));
+    DGC_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int besti = 0;
+    for (int k = 0; k < 4; ++k) {
+      b.epb = cand[k];
+      if (b.exec) cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+      dgc_status s = dgc_batch_rk_step(batch, prec, c_devs, cfl_, dt_devs, workspace_dev, workspace_size, stream);
+      if (s != DGC_OK) throw Error{s, g_err};
+      DGC_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) {
+        s = dgc_batch_rk_step(batch, prec, c_devs, cfl_, dt_devs, workspace_dev, workspace_size, stream);
+        if (s != DGC_OK) throw Error{s, g_err};
+      }
+      DGC_CUDA(cudaEventRecord(e1, st));
+      DGC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      DGC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      const double per = ms / reps;
+      if (ms_per_step) ms_per_step[k] = per;
+      if (per < best) {
+        best = per;
+        besti = k;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b.epb = cand[besti];
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    b.exec = nullptr;
+    *best_epb = b.epb;
+  });
+}
+
+dgc_status dgc_batch_launch_count(const dgc_batch* batch, int64_t* launches) {
+  return guarded([&] {
+    require(batch != nullptr && launches != nullptr, "null argument");
+    *launches = batch->launches;
+  });
+}
+
+void dgc_batch_destroy(dgc_batch* batch) {
+  if (!batch) return;
+  batch_release(*batch);
+  delete batch;
 }
 
 }  // extern "C"

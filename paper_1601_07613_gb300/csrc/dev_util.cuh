@@ -14,7 +14,9 @@
 
 namespace dgc {
 
-__device__ __forceinline__ float d2f(double x) {
+// Full conversions (every input class); called out of line for the rare
+// inputs the fast paths below do not cover.
+static __device__ __noinline__ float d2f_any(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
   const unsigned ed = (unsigned)(b >> 52) & 0x7FFu;
@@ -45,7 +47,7 @@ __device__ __forceinline__ float d2f(double x) {
   return __uint_as_float(out | sign);
 }
 
-__device__ __forceinline__ double f2d(float f) {
+static __device__ __noinline__ double f2d_any(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
   const unsigned ef = (u >> 23) & 0xFFu;
@@ -64,6 +66,32 @@ __device__ __forceinline__ double f2d(float f) {
     bits = ((unsigned long long)(k + 874) << 52) | frac;
   }
   return __longlong_as_double((long long)(sign | bits));
+}
+
+// Fast paths.  binary64 -> binary32 for results in the normal range: adding
+// 0x0FFFFFFF plus the lowest kept bit to the 29 dropped bits rounds to nearest
+// even, the carry running into the exponent field (up to infinity); the
+// exponent is then rebiased by 1023 - 127.  binary32 -> binary64 for normal
+// inputs is a shift and a rebias.  Anything else goes to the calls above.
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned ed = (unsigned)(b >> 52) & 0x7FFu;
+  if (ed - 897u < 254u) {  // binary32 exponent field 1..254
+    const unsigned long long t = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
+    const unsigned mag = (unsigned)((t >> 29) & 0x3FFFFFFFFull) - (896u << 23);
+    return __uint_as_float(mag | ((unsigned)(b >> 32) & 0x80000000u));
+  }
+  return d2f_any(x);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xFFu;
+  if (ef - 1u < 254u) {  // normal
+    const unsigned long long bits = ((unsigned long long)(u & 0x7FFFFFFFu) << 29) + (896ull << 52);
+    return __longlong_as_double((long long)(bits | ((unsigned long long)(u & 0x80000000u) << 32)));
+  }
+  return f2d_any(f);
 }
 
 template <typename T>

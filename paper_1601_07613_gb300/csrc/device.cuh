@@ -66,8 +66,34 @@ struct StageArgs {
   double a0 = 0.0, b0 = 1.0;   // uout = a0 u0 + b0 (us + dt L(us))
 };
 
+// One mesh of a batch, as the batched kernels see it (device array).
+struct BatchMeshDev {
+  int p = 0, pad = 0;
+  int64_t ne = 0;
+  const int4* topo = nullptr;
+  const double2* fgeo = nullptr;
+  const double* jinv = nullptr;
+  const double* inr = nullptr;
+  float* est = nullptr;   // CFL estimates [ne], minimum at [ne]
+  double* c = nullptr;    // state (caller's)
+  double* u1 = nullptr;   // stage state (workspace)
+  float* rec = nullptr;   // FP32 record (workspace, mixed precision)
+  void* rhs = nullptr;    // rhs (workspace)
+  double* dt = nullptr;   // this mesh's time step (caller's)
+};
+
+// A range of one mesh's edges (of one color) or elements, at most one block's work.
+struct BatchTile {
+  int32_t mesh = 0, p = 0;
+  int64_t begin = 0, end = 0;
+};
+
 // kernels_tri.cu
 void tri_upload_tables(int p, const RefTables& T);
+int batch_init(cudaStream_t st, const BatchMeshDev* d, int n);
+int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, double cfl, bool mixed);
+int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage, double a0,
+               double b0, SurfMode mode, bool mixed, int threads);
 int tri_record_floats(int p);
 int tri_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,

@@ -62,7 +62,7 @@ struct Mesh {
   std::vector<int32_t> elem_new_of_old, side_new_of_old, side_old_of_new, color_off;
   // options
   bool fuse = true;
-  int edges_per_block = 128;
+  int edges_per_block = 64;
   int threads_per_edge = 2;
   bool profile = false;
   void* prof = nullptr;  // event records (capi.cu)

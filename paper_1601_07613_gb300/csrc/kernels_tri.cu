@@ -15,12 +15,22 @@
 // FP64 kernels evaluate Eq. 2 as written.  FP32 kernels evaluate it in the
 // perturbation form of euler_pert.cuh (deviations from the element mean).
 #include <cfloat>
+#include <type_traits>
 
 #include "dev_util.cuh"
 #include "device.cuh"
 #include "euler_pert.cuh"
 
 namespace dgc {
+
+// Unrolling of the quadrature-point loops: fully unrolled p = 3 kernels run to
+// several thousand instructions and stall on instruction fetch.
+#ifndef DGC_QUNROLL
+#define DGC_QUNROLL 1
+#endif
+#define DGC_PRAGMA_(x) _Pragma(#x)
+#define DGC_PRAGMA(x) DGC_PRAGMA_(x)
+#define DGC_UNROLL_Q DGC_PRAGMA(unroll DGC_QUNROLL)
 
 template <int P>
 struct TriDim {
@@ -255,7 +265,7 @@ __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], c
   const TriTab<double, P>& K = tri_tab<double, P>();
   const double2 j0 = __ldg(reinterpret_cast<const double2*>(ji));
   const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
-#pragma unroll
+  DGC_UNROLL_Q
   for (int q = 0; q < D::NQV; ++q) {
     double U[4];
 #pragma unroll
@@ -289,7 +299,7 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
   const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
   const float nr[2] = {d2f(j0.x), d2f(j0.y)}, ns[2] = {d2f(j1.x), d2f(j1.y)};
   const float thr = R.u[1] * nr[0] + R.u[2] * nr[1], ths = R.u[1] * ns[0] + R.u[2] * ns[1];
-#pragma unroll
+  DGC_UNROLL_Q
   for (int q = 0; q < D::NQV; ++q) {
     float d[4];
 #pragma unroll
@@ -422,25 +432,42 @@ __device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, in
   }
 }
 
+// edge tables of order P into shared memory (the block's threads cooperate)
+template <int P, typename CT>
+__device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw) {
+  using D = TriDim<P>;
+  const TriTab<CT, P>& K = tri_tab<CT, P>();
+  const CT* src = &K.phiE[0][0][0];
+  for (int i = threadIdx.x; i < 3 * D::NQE * D::NP; i += blockDim.x) sphi[i] = src[i];
+  if (threadIdx.x < D::NQE) sw[threadIdx.x] = K.wE[threadIdx.x];
+}
+
+// One lane of the pair that handles edge k (side 0: left element, 1: right).
+// Lanes with valid = false shadow a real edge (so both lanes of every pair
+// take part in the shuffles) and write nothing.
+template <int P, typename CT, typename ST, typename RT, int MODE>
+__device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool valid, int side, const CT* sphi,
+                                          const CT* sw);
+
 template <int P, typename CT, typename ST, typename RT, int MODE>
 __global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
-  constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV;
-  __shared__ CT sphi[3 * NQ * NP];
-  __shared__ CT sw[NQ];
-  {
-    const TriTab<CT, P>& K = tri_tab<CT, P>();
-    const CT* src = &K.phiE[0][0][0];
-    for (int i = threadIdx.x; i < 3 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
-    if (threadIdx.x < NQ) sw[threadIdx.x] = K.wE[threadIdx.x];
-  }
+  __shared__ CT sphi[3 * D::NQE * D::NP];
+  __shared__ CT sw[D::NQE];
+  stage_edge_tables<P, CT>(sphi, sw);
   __syncthreads();
-
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t k = A.begin + (t >> 1);
-  const int side = (int)(t & 1);
   const bool valid = k < A.end;
   if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
+  surf_pair<P, CT, ST, RT, MODE>(A, k, valid, (int)(t & 1), sphi, sw);
+}
+
+template <int P, typename CT, typename ST, typename RT, int MODE>
+__device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool valid, int side, const CT* sphi,
+                                          const CT* sw) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV;
   const int4 tp = A.topo[k];
   const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
   const bool right = side && !bnd;
@@ -460,7 +487,7 @@ __global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
     if constexpr (MODE == SURF_FIRST) volume_acc64<P>(c, A.jinv + 4 * elem, acc);
     const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
-#pragma unroll
+    DGC_UNROLL_Q
     for (int q = 0; q < NQ; ++q) {
       const int qq = right ? NQ - 1 - q : q;  // the right element runs along the edge backwards
       double phi[NP], U[4], V[4], a[4], b[4], Fs[4];
@@ -512,7 +539,7 @@ __global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
     const float n[2] = {d2f(g0.x), d2f(g0.y)};
     const float scale = right ? d2f(g1.y) : -d2f(g1.x);
     const float thb = R.u[1] * n[0] + R.u[2] * n[1];
-#pragma unroll
+    DGC_UNROLL_Q
     for (int q = 0; q < NQ; ++q) {
       const int qq = right ? NQ - 1 - q : q;
       float phi[NP], dU[4], dV[4], ds[4], dn[4], G[4];
@@ -578,30 +605,65 @@ __device__ __forceinline__ T lambda_max(const T (&v)[TriDim<P>::NV]) {
   return lam;
 }
 
+// FP32 estimate of max_q (|u| + c) from the FP32 record (mean pair + modes)
+template <int P>
+__device__ __forceinline__ float lambda_max_rec(const float (&r)[TriDim<P>::NF]) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP;
+  const TriTab<float, P>& K = tri_tab<float, P>();
+  float lam = 0.0f;
+  DGC_UNROLL_Q
+  for (int q = 0; q < D::NQV; ++q) {
+    float U[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float s = r[4 + m];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[8 + m * (NP - 1) + j - 1];
+      U[m] = r[m] + s;
+    }
+    const float ir = 1.0f / U[0], u = U[1] * ir, w = U[2] * ir;
+    const float q2 = u * u + w * w;
+    const float pr = 0.4f * (U[3] - 0.5f * U[0] * q2);
+    lam = fmaxf(lam, sqrtf(q2) + sqrtf(1.4f * pr * ir));
+  }
+  return lam;
+}
+
+// pass 1 for element e: its FP32 estimate (stored), and its FP32 record
+template <int P>
+__device__ __forceinline__ float cfl1_elem(const double* __restrict__ c, const double* __restrict__ inr, int64_t e,
+                                           float* __restrict__ est, float* __restrict__ shadow) {
+  using D = TriDim<P>;
+  double v[D::NV];
+  load_block(c + e * D::NV, v);
+  float r[D::NF];
+  record_of<P>(v, r);
+  if (shadow) store_block(shadow + e * D::NF, r);
+  float d = d2f(__ldg(inr + e)) / ((2 * P + 1) * lambda_max_rec<P>(r));
+  if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;  // non-physical: always re-evaluated
+  est[e] = d;
+  return d;
+}
+
+// pass 2 for element e: the FP64 step if e is a candidate, else DBL_MAX
+template <int P>
+__device__ __forceinline__ double cfl2_elem(const double* __restrict__ c, const double* __restrict__ inr, int64_t e,
+                                            double cfl, const float* __restrict__ est, float minest) {
+  using D = TriDim<P>;
+  if (!(est[e] <= minest * (1.0f + kCflMargin))) return DBL_MAX;
+  double v[D::NV];
+  load_block(c + e * D::NV, v);
+  const double best = cfl * (__ldg(inr + e) / ((2 * P + 1) * lambda_max<P, double>(v)));
+  return best > 0.0 ? best : DBL_MAX;  // non-physical state: excluded (NaN)
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_cfl1_tri(const double* __restrict__ c, const double* __restrict__ inr,
                                                   int64_t ne, float* __restrict__ est, unsigned* minbits,
                                                   float* __restrict__ shadow) {
-  using D = TriDim<P>;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float best = FLT_MAX;
-  if (e < ne) {
-    double v[D::NV];
-    load_block(c + e * D::NV, v);
-    if (shadow) {
-      float r[D::NF];
-      record_of<P>(v, r);
-      store_block(shadow + e * D::NF, r);
-    }
-    float f[D::NV];
-#pragma unroll
-    for (int i = 0; i < D::NV; ++i) f[i] = d2f(v[i]);
-    const float lam = lambda_max<P, float>(f);
-    float d = d2f(__ldg(inr + e)) / ((2 * P + 1) * lam);
-    if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;  // non-physical: always re-evaluated
-    est[e] = d;
-    best = d;
-  }
+  const float best = e < ne ? cfl1_elem<P>(c, inr, e, est, shadow) : FLT_MAX;
   block_min_to(best, minbits);
 }
 
@@ -609,17 +671,155 @@ template <int P>
 __global__ void __launch_bounds__(128) k_cfl2_tri(const double* __restrict__ c, const double* __restrict__ inr,
                                                   int64_t ne, double cfl, const float* __restrict__ est,
                                                   const unsigned* minbits, unsigned long long* dtbits) {
-  using D = TriDim<P>;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double best = DBL_MAX;
-  if (e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin)) {
-    double v[D::NV];
-    load_block(c + e * D::NV, v);
-    const double lam = lambda_max<P, double>(v);
-    best = cfl * (__ldg(inr + e) / ((2 * P + 1) * lam));
-    if (!(best > 0.0)) best = DBL_MAX;  // non-physical state: excluded (NaN)
-  }
+  const double best = e < ne ? cfl2_elem<P>(c, inr, e, cfl, est, __uint_as_float(*minbits)) : DBL_MAX;
   block_min_to(best, dtbits);
+}
+
+// ---------------------------------------------------------------------------
+// Batched meshes: one persistent launch per kernel class covering every mesh.
+// The host cuts each mesh's color (or element) range into tiles of at most
+// one block's worth of work, sorted by order p; each block walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... and re-stages the edge tables of
+// shared memory only when p changes (at most a few times per block).
+// ---------------------------------------------------------------------------
+template <int MODE, bool MIXED>
+__global__ void __launch_bounds__(256) k_batch_surf(const BatchMeshDev* __restrict__ meshes,
+                                                    const BatchTile* __restrict__ tiles, int nt, int stage,
+                                                    double a0, double b0) {
+  using CT = typename std::conditional<MIXED, float, double>::type;
+  using RT = CT;
+  using ST = typename std::conditional<MIXED && MODE != SURF_LAST, float, double>::type;
+  __shared__ CT sphi[3 * TriDim<3>::NQE * TriDim<3>::NP];
+  __shared__ CT sw[TriDim<3>::NQE];
+  int curp = 0;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const BatchTile T = tiles[ti];
+    if (T.p != curp) {  // block-uniform
+      __syncthreads();
+      if (T.p == 1) stage_edge_tables<1, CT>(sphi, sw);
+      else if (T.p == 2) stage_edge_tables<2, CT>(sphi, sw);
+      else stage_edge_tables<3, CT>(sphi, sw);
+      __syncthreads();
+      curp = T.p;
+    }
+    const BatchMeshDev& B = meshes[T.mesh];
+    SurfParams A;
+    A.begin = T.begin;
+    A.end = T.end;
+    A.topo = B.topo;
+    A.fgeo = B.fgeo;
+    A.jinv = B.jinv;
+    double* us = stage == 0 ? B.c : B.u1;
+    A.state = (MIXED && MODE != SURF_LAST) ? (const void*)B.rec : (const void*)us;
+    A.rhs = B.rhs;
+    A.buf = nullptr;
+    A.sa.u0 = B.c;
+    A.sa.uout = stage == 2 ? B.c : B.u1;
+    A.sa.shadow = MIXED ? B.rec : nullptr;
+    A.sa.dt = B.dt;
+    A.sa.a0 = a0;
+    A.sa.b0 = b0;
+    int64_t k = T.begin + (threadIdx.x >> 1);
+    const bool valid = k < T.end;
+    if (!valid) k = T.end - 1;
+    const int side = threadIdx.x & 1;
+    if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, valid, side, sphi, sw);
+    else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, valid, side, sphi, sw);
+    else surf_pair<3, CT, ST, RT, MODE>(A, k, valid, side, sphi, sw);
+  }
+}
+
+// dt and the FP32 minimum of every mesh set to a large value
+__global__ void k_batch_init(const BatchMeshDev* __restrict__ meshes, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  *reinterpret_cast<unsigned long long*>(meshes[i].dt) = 0x7F7F7F7F7F7F7F7Full;
+  *reinterpret_cast<unsigned*>(meshes[i].est + meshes[i].ne) = 0x7F7F7F7Fu;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_batch_cfl1(const BatchMeshDev* __restrict__ meshes,
+                                                    const BatchTile* __restrict__ tiles, int nt) {
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const BatchTile T = tiles[ti];
+    const BatchMeshDev& B = meshes[T.mesh];
+    const int64_t e = T.begin + threadIdx.x;
+    float best = FLT_MAX;
+    if (e < T.end) {
+      float* sh = MIXED ? B.rec : nullptr;
+      if (T.p == 1) best = cfl1_elem<1>(B.c, B.inr, e, B.est, sh);
+      else if (T.p == 2) best = cfl1_elem<2>(B.c, B.inr, e, B.est, sh);
+      else best = cfl1_elem<3>(B.c, B.inr, e, B.est, sh);
+    }
+    block_min_to(best, reinterpret_cast<unsigned*>(B.est + B.ne));
+    __syncthreads();  // the block minimum's shared slots are reused by the next tile
+  }
+}
+
+__global__ void __launch_bounds__(128) k_batch_cfl2(const BatchMeshDev* __restrict__ meshes,
+                                                    const BatchTile* __restrict__ tiles, int nt, double cfl) {
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const BatchTile T = tiles[ti];
+    const BatchMeshDev& B = meshes[T.mesh];
+    const int64_t e = T.begin + threadIdx.x;
+    double best = DBL_MAX;
+    if (e < T.end) {
+      const float mn = __uint_as_float(*reinterpret_cast<const unsigned*>(B.est + B.ne));
+      if (T.p == 1) best = cfl2_elem<1>(B.c, B.inr, e, cfl, B.est, mn);
+      else if (T.p == 2) best = cfl2_elem<2>(B.c, B.inr, e, cfl, B.est, mn);
+      else best = cfl2_elem<3>(B.c, B.inr, e, cfl, B.est, mn);
+    }
+    block_min_to(best, reinterpret_cast<unsigned long long*>(B.dt));
+    __syncthreads();
+  }
+}
+
+static int persistent_grid(const void* kern, int threads, int ntiles) {
+  int dev = 0, sms = 0, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
+  const int g = sms * (per > 0 ? per : 1);
+  return ntiles < g ? (ntiles > 0 ? ntiles : 1) : g;
+}
+
+int batch_init(cudaStream_t st, const BatchMeshDev* d, int n) {
+  k_batch_init<<<(n + 127) / 128, 128, 0, st>>>(d, n);
+  return 1;
+}
+
+int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, double cfl, bool mixed) {
+  if (nt <= 0) return 0;
+  const void* k1 = mixed ? (const void*)k_batch_cfl1<true> : (const void*)k_batch_cfl1<false>;
+  const int g1 = persistent_grid(k1, 128, nt), g2 = persistent_grid((const void*)k_batch_cfl2, 128, nt);
+  if (mixed) k_batch_cfl1<true><<<g1, 128, 0, st>>>(d, tiles, nt);
+  else k_batch_cfl1<false><<<g1, 128, 0, st>>>(d, tiles, nt);
+  k_batch_cfl2<<<g2, 128, 0, st>>>(d, tiles, nt, cfl);
+  return 2;
+}
+
+template <int MODE, bool MIXED>
+static int batch_surf_launch(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage,
+                             double a0, double b0, int threads) {
+  if (nt <= 0) return 0;
+  const int g = persistent_grid((const void*)k_batch_surf<MODE, MIXED>, threads, nt);
+  k_batch_surf<MODE, MIXED><<<g, threads, 0, st>>>(d, tiles, nt, stage, a0, b0);
+  return 1;
+}
+
+int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage, double a0,
+               double b0, SurfMode mode, bool mixed, int threads) {
+  if (mixed) {
+    if (mode == SURF_FIRST) return batch_surf_launch<SURF_FIRST, true>(st, d, tiles, nt, stage, a0, b0, threads);
+    if (mode == SURF_RMW) return batch_surf_launch<SURF_RMW, true>(st, d, tiles, nt, stage, a0, b0, threads);
+    if (mode == SURF_LAST) return batch_surf_launch<SURF_LAST, true>(st, d, tiles, nt, stage, a0, b0, threads);
+  } else {
+    if (mode == SURF_FIRST) return batch_surf_launch<SURF_FIRST, false>(st, d, tiles, nt, stage, a0, b0, threads);
+    if (mode == SURF_RMW) return batch_surf_launch<SURF_RMW, false>(st, d, tiles, nt, stage, a0, b0, threads);
+    if (mode == SURF_LAST) return batch_surf_launch<SURF_LAST, false>(st, d, tiles, nt, stage, a0, b0, threads);
+  }
+  return -1;
 }
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,7 @@ DGC_OPT_FUSE = 0
 DGC_OPT_EDGES_PER_BLOCK = 1
 DGC_OPT_THREADS_PER_EDGE = 2
 DGC_OPT_PROFILE = 3
+DGC_OPT_GRAPH = 4
 KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
 
 STATUS = {0: "DGC_OK", 1: "DGC_ERR_ARG", 2: "DGC_ERR_MESH", 3: "DGC_ERR_COLORING_LIMIT",
@@ -55,6 +56,14 @@ SIGNATURES = {
     "dgc_profile_collect": (C.c_int, [_P, _DP, _I64P]),
     "dgc_last_launch_count": (C.c_int, [_P, _I64P]),
     "dgc_last_error": (C.c_char_p, []),
+    "dgc_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
+    "dgc_batch_workspace_size": (C.c_int, [_P, C.c_int, _I64P]),
+    "dgc_batch_set_option": (C.c_int, [_P, C.c_int, _I64]),
+    "dgc_batch_rk_step": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, _P, _P, _I64, _P]),
+    "dgc_batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, _P, _P, _I64, C.c_int, _P, _I64P,
+                                     _DP]),
+    "dgc_batch_launch_count": (C.c_int, [_P, _I64P]),
+    "dgc_batch_destroy": (None, [_P]),
     "dgc_destroy": (None, [_P]),
 }
 
@@ -262,6 +271,57 @@ def dgc_last_launch_count(mesh) -> int:
     b = C.c_int64()
     _check(lib().dgc_last_launch_count(mesh, C.byref(b)))
     return b.value
+
+
+def _ptr_array(tensors):
+    arr = (_P * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _dptr(t)
+    return arr
+
+
+def dgc_batch_create(meshes):
+    handles = (_P * len(meshes))(*[m.h if isinstance(m, Mesh) else m for m in meshes])
+    out = _P()
+    _check(lib().dgc_batch_create(len(meshes), handles, C.byref(out)))
+    return out
+
+
+def dgc_batch_workspace_size(batch, prec: int) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_batch_workspace_size(batch, prec, C.byref(b)))
+    return b.value
+
+
+def dgc_batch_set_option(batch, opt: int, value: int):
+    _check(lib().dgc_batch_set_option(batch, opt, value))
+
+
+def dgc_batch_rk_step(batch, prec: int, c_devs, cfl: float, dt_devs, workspace_dev, workspace_bytes=None,
+                      stream=None):
+    _check(lib().dgc_batch_rk_step(batch, prec, _ptr_array(c_devs), cfl, _dptr(dt_devs), _dptr(workspace_dev),
+                                   _nbytes(workspace_dev, workspace_bytes), _stream(stream)))
+
+
+def dgc_batch_autotune(batch, prec: int, c_devs, cfl: float, dt_devs, workspace_dev, reps: int = 5,
+                       workspace_bytes=None, stream=None):
+    best = C.c_int64()
+    ms = (C.c_double * 4)()
+    _check(lib().dgc_batch_autotune(batch, prec, _ptr_array(c_devs), cfl, _dptr(dt_devs), _dptr(workspace_dev),
+                                    _nbytes(workspace_dev, workspace_bytes), reps, _stream(stream),
+                                    C.byref(best), ms))
+    return best.value, dict(zip((16, 32, 64, 128), list(ms)))
+
+
+def dgc_batch_launch_count(batch) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_batch_launch_count(batch, C.byref(b)))
+    return b.value
+
+
+def dgc_batch_destroy(batch):
+    if batch:
+        lib().dgc_batch_destroy(batch)
 
 
 def dgc_last_error() -> str:
