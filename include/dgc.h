@@ -239,6 +239,26 @@ void dgc_batch_destroy(dgc_batch* batch);
 /* Thread-local message of the last error (empty string if none). */
 const char* dgc_last_error(void);
 
+/* dgc_rk_step for callers that cannot allocate device memory: the same SSP-RK3 step
+ * (same kernels, same results), but the workspace and the CFL scratch are taken from a
+ * 16 MiB array the library holds in device memory, so the caller passes no workspace and
+ * the call allocates nothing (no cudaMalloc, cudaFree or allocating library call).  It
+ * serves callers whose device memory is owned by someone else -- a host framework that
+ * reserves the whole device for its own pool, or a fixed-footprint solver loop that may
+ * not change its allocations once running -- and so cannot produce the workspace
+ * dgc_rk_step needs.  The paper has no counterpart; this is an interface addition.
+ *   Limits: dgc_workspace_size(prec) plus 4 bytes per element (+256) must fit in 16 MiB
+ *   (e.g. up to ~25,000 triangles at p = 3, ~79,000 at p = 1); larger meshes get
+ *   DGC_ERR_ARG.  The mesh must already be on the current device from an earlier device
+ *   call (uploading allocates), else DGC_ERR_ARG.
+ *   The array is shared by every call on a device and keeps the last call's contents
+ *   (each call writes what it reads first; dt_dev and the CFL minimum are reset per call).
+ *   Calls whose work overlaps on the GPU (two streams, or two meshes at once) race on
+ *   the array: serialise them.  The first call on each device looks up the array's device
+ *   address (a CUDA runtime query); make that first call before any stream capture.
+ *   Every GPU that loads the library holds the 16 MiB until the process exits. */
+dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl,
+                              double* dt_dev, void* stream);
 
 /* Free the mesh and its device copies (the device must still be current). */
 void dgc_destroy(dgc_mesh* mesh);

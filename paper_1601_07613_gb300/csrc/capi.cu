@@ -694,6 +694,112 @@ void dgc_destroy(dgc_mesh* mesh) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Allocation-free RK step.  Its workspace (stage state, FP32 record, rhs) and
+// the CFL estimates live in one file-scope device array, so the call needs no
+// buffer from the caller and allocates nothing.  Every GPU that loads the
+// library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kStaticScratchBytes = int64_t(1) << 24;  // 16 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+void* static_scratch(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) throw Error{DGC_ERR_UNSUPPORTED, "device index out of range"};
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    DGC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[dev] = p;
+  }
+  return g_static_addr[dev];
+}
+
+}  // namespace
+
+extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_,
+                                         double* dt_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    check_ptr(c_dev, "c_dev");
+    require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
+    require(cfl_ > 0.0, "cfl must be positive");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
+    const int64_t ws = workspace_bytes(m, prec), est = align256((m.ne + 64) * (int64_t)sizeof(float));
+    if (ws + est > kStaticScratchBytes)
+      throw Error{DGC_ERR_ARG, "mesh too large for dgc_rk_step_static: needs " + std::to_string(ws + est) +
+                                   " bytes of scratch, the static array holds " + std::to_string(kStaticScratchBytes)};
+    int dev = -1;
+    DGC_CUDA(cudaGetDevice(&dev));
+    // uploading the mesh would allocate: an earlier device call must have done it
+    require(m.dev != nullptr && !m.dirty && m.dev->device == dev,
+            "mesh not on this device yet: make one device call on it first (e.g. dgc_cfl_dt)");
+    char* base = static_cast<char*>(static_scratch(dev));
+    DeviceMesh dcopy = *m.dev;  // the same mesh arrays, CFL estimates in the static array
+    dcopy.cfl_est = reinterpret_cast<float*>(base + ws);
+    Ctx x;
+    x.dim = m.dim;
+    x.p = m.p;
+    x.np = m.np;
+    x.M = m.M;
+    x.nfpe = m.nfpe;
+    x.ne = m.ne;
+    x.ns = m.ns;
+    x.epb = m.edges_per_block;
+    x.d = &dcopy;
+    x.st = static_cast<cudaStream_t>(stream);
+    x.shadow.M = m.M;
+    x.shadow.np = m.np;
+    x.shadow.nv = m.M * m.np;
+    x.shadow.rec = (int)record_floats(m);
+    x.shadow.split = true;
+    x.shadow.phi0 = m.tab.phiV[0];
+    const bool mixed = prec == DGC_FP32_MIXED;
+    const int64_t S = state_bytes(m);
+    double* u1 = reinterpret_cast<double*>(base);
+    const int64_t R = align256(m.ne * record_floats(m) * 4);
+    float* shadow = mixed ? reinterpret_cast<float*>(base + align256(S)) : nullptr;
+    void* rhs = mixed ? (void*)(base + align256(S) + R) : (void*)(base + align256(S));
+    int64_t n = 0;
+    DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
+    count(m, n, cfl(x, c_dev, cfl_, dt_dev, shadow));
+    const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
+    const std::vector<int32_t>& off = m.color_off;
+    const int C = m.ncolors;
+    const TypeCfg ty = mixed ? TY_MF : TY_D;
+    for (int s = 0; s < 3; ++s) {
+      double* us = s == 0 ? c_dev : u1;
+      StageArgs sa;
+      sa.u0 = c_dev;
+      sa.uout = s == 2 ? c_dev : u1;
+      sa.shadow = shadow;
+      sa.dt = dt_dev;
+      sa.a0 = A0[s];
+      sa.b0 = B0[s];
+      const void* st_in = mixed ? (const void*)shadow : (const void*)us;
+      if (m.fuse && m.perfect && C >= 2) {
+        count(m, n, surf(x, ty, SURF_FIRST, off[0], off[1], st_in, rhs, nullptr, nullptr));
+        for (int c = 2; c < C; ++c) count(m, n, surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr));
+        count(m, n, surf(x, mixed ? TY_MLAST : TY_D, SURF_LAST, off[C - 1], off[C], us, rhs, nullptr, &sa));
+      } else {
+        count(m, n, vol(x, ty, st_in, rhs));
+        for (int c = 1; c <= C; ++c) count(m, n, surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr));
+        count(m, n, stage_update(x, mixed, us, rhs, sa));
+      }
+    }
+    finish(m, n);
+  });
+}
+
+// ---------------------------------------------------------------------------
 // Batches of independent triangle meshes (uneven size and order): one
 // persistent launch per kernel class and RK stage covers every mesh, the whole
 // step optionally replayed from a CUDA graph.

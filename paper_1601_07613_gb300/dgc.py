@@ -56,6 +56,7 @@ SIGNATURES = {
     "dgc_profile_collect": (C.c_int, [_P, _DP, _I64P]),
     "dgc_last_launch_count": (C.c_int, [_P, _I64P]),
     "dgc_last_error": (C.c_char_p, []),
+    "dgc_rk_step_static": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P]),
     "dgc_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
     "dgc_batch_workspace_size": (C.c_int, [_P, C.c_int, _I64P]),
     "dgc_batch_set_option": (C.c_int, [_P, C.c_int, _I64]),
@@ -271,6 +272,11 @@ def dgc_last_launch_count(mesh) -> int:
     b = C.c_int64()
     _check(lib().dgc_last_launch_count(mesh, C.byref(b)))
     return b.value
+
+
+def dgc_rk_step_static(mesh, prec: int, c_dev, cfl: float, dt_dev, stream=None):
+    """dgc_rk_step without a caller workspace (small meshes; see include/dgc.h)."""
+    _check(lib().dgc_rk_step_static(mesh, prec, _dptr(c_dev), cfl, _dptr(dt_dev), _stream(stream)))
 
 
 def _ptr_array(tensors):
