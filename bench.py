@@ -267,6 +267,7 @@ def run_dgc(args, rank, world, local_rank):
             dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_FUSE, 1)
         variants["two_pass_buffer_bytes"] = nbuf
         del buf, r
+        variants.update(run_batched(dgc, torch, dev, stream, args))
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
     e2e = None
@@ -303,6 +304,45 @@ def run_dgc(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(mi, p, c_host, dofs)
     mesh.close()
+    return out
+
+
+def run_batched(dgc, torch, dev, stream, args):
+    """64 independent periodic meshes, element counts log-uniform on [1e3, 2e5],
+    p uniform in {1, 2, 3}, random vortices: one persistent launch per kernel class
+    and stage over all meshes, replayed from a CUDA graph, tile size autotuned."""
+    specs = W.batched_square_meshes()
+    meshes, states = [], []
+    for i, s in enumerate(specs):
+        m = dgc.Mesh.from_input(W.periodic_square_tri(s["n"], jitter=0.2, seed=500 + i), s["p"])
+        m.color(1601 + i)
+        xyz = dgc.dgc_vol_points(m.h)
+        c = dgc.dgc_project(m.h, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=s["beta"], xc=s["xc"], yc=s["yc"]))
+        meshes.append(m)
+        states.append(c)
+    dofs = sum(m.info["ne"] * m.info["M"] * m.info["np"] for m in meshes)
+    cdev = [torch.empty(m.state_shape(), dtype=torch.float64, device=dev) for m in meshes]
+    for m, c, d in zip(meshes, states, cdev):
+        dgc.dgc_import_state(m.h, c, d)
+    batch = dgc.dgc_batch_create(meshes)
+    out = {}
+    try:
+        for prec, tag in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
+            ws = torch.empty(dgc.dgc_batch_workspace_size(batch, prec) // 8 + 64, dtype=torch.float64, device=dev)
+            dts = torch.zeros(len(meshes), dtype=torch.float64, device=dev)
+            best, tune = dgc.dgc_batch_autotune(batch, prec, cdev, 0.3, dts, ws, reps=3 if tag == "fp32mixed" else 1)
+            k = max(3, args.steps) if tag == "fp32mixed" else 3
+            ms = time_steps(torch, lambda: dgc.dgc_batch_rk_step(batch, prec, cdev, 0.3, dts, ws), k, stream)
+            out[f"batched_{tag}"] = {
+                "value": 3 * dofs / (ms * 1e-3), "ms_per_step": round(ms, 4), "meshes": len(meshes),
+                "elements": sum(m.info["ne"] for m in meshes), "dofs": dofs,
+                "launches_per_step": dgc.dgc_batch_launch_count(batch), "graph": True,
+                "edges_per_block": best, "autotune_ms": {str(e): round(v, 4) for e, v in tune.items()}}
+            del ws
+    finally:
+        dgc.dgc_batch_destroy(batch)
+        for m in meshes:
+            m.close()
     return out
 
 

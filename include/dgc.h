@@ -131,6 +131,37 @@ dgc_status dgc_mesh_info(const dgc_mesh* mesh, int64_t info[10]);
 dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, int8_t* qleft,
                          int8_t* qright);
 
+/* Nonconforming refinement and its 6-color edge map (Sec. 3.2).  Splits each listed
+ * triangle (original element ids; duplicates ignored; n = 0 refines nothing) into four by
+ * its edge midpoints, one level, on a mesh colored by dgc_color_edges with 3 colors.
+ *   Elements: every refined element is replaced in place by its children [v0, m01, m20],
+ *     [m01, v1, m12], [m20, m12, v2], [m01, m12, m20] (new midpoint vertices numbered after
+ *     the existing ones, one per split edge in edge order); the original element order of
+ *     all later calls is this expanded order.
+ *   Colors: a split edge of color c gives its half next to the endpoint with the smaller
+ *     vertex id color c and the other half c + 3 (the map ((c + 3m - 4) mod 6) + 1 with the
+ *     child number m counted from the smaller vertex id, so both neighbours agree); interior
+ *     edges take the color of the parallel parent edge; other edges keep theirs.  The result
+ *     uses colors 1..6 and no element has two edges of one color.
+ *   Edges: the original edges in order (one edge, or its two halves first-child first),
+ *     then three interior edges per refined element.  A half whose other neighbour stays
+ *     coarse is a hanging edge: left = the fine child, right = the coarse element, whose
+ *     basis is evaluated on that half of its edge (dgc_get_hanging).
+ * The mesh is then reordered as by dgc_color_edges (Sec. 5; elements no color-1 edge reaches
+ * are numbered last, in original order).  Errors: DGC_ERR_UNSUPPORTED (tetrahedra, a mesh
+ * already refined), DGC_ERR_ARG (not colored with 3 colors, id out of range).  Host only;
+ * states sized for the old mesh are invalid afterwards. */
+dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems);
+
+/* Per edge (original order): the half (0: next to the coarse element's local edge's first
+ * vertex, 1: the other) of the right element's local edge that a hanging edge covers, or
+ * -1 for a conforming or boundary edge. */
+dgc_status dgc_get_hanging(const dgc_mesh* mesh, int8_t* half);
+
+/* Element vertex ids [E][dim+1] and unwrapped vertex coordinates [E][dim+1][dim], original
+ * element order (either pointer may be NULL). */
+dgc_status dgc_get_elements(const dgc_mesh* mesh, int32_t* ev, double* xyz);
+
 /* The ordering chosen by the last coloring call: new element id of each original element,
  * new edge id of each original edge, color (1..C) of each original edge, and the color
  * offsets (C+1 entries, edges [offsets[c-1], offsets[c]) of the new order have color c).

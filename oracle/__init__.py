@@ -92,6 +92,14 @@ def lib():
             L.orc_num_vol_points.argtypes = [C.c_int, C.c_int]
             L.orc_eval_points.argtypes = [P, C.c_int, C.c_int, dp, C.c_int, dp, dp, dp]
             L.orc_project.argtypes = [P, C.c_int, C.c_int, dp, dp]
+            L.orc_refine.restype = P
+            L.orc_refine.argtypes = [P, C.POINTER(C.c_int8), C.POINTER(C.c_uint8)]
+            L.orc_mesh_nelem.restype = C.c_int64
+            L.orc_mesh_nelem.argtypes = [P]
+            L.orc_mesh_nvert.restype = C.c_int64
+            L.orc_mesh_nvert.argtypes = [P]
+            L.orc_mesh_elements.argtypes = [P, C.POINTER(C.c_int32), dp]
+            L.orc_mesh_refined.argtypes = [P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]
             _lib = L
     return _lib
 
@@ -176,6 +184,36 @@ class OracleMesh:
     @classmethod
     def from_input(cls, mi):
         return cls(mi.dim, mi.xyz, mi.ev, mi.periodic_len)
+
+    def refine(self, col: np.ndarray, elems) -> "OracleMesh":
+        """One level of refinement of the listed elements with the 6-color map of
+        Sec. 3.2 (dg_oracle.c, orc_refine); col holds this mesh's colors 1..3.
+        The new mesh carries .colors and .hanging (per side)."""
+        col = np.ascontiguousarray(col, dtype=np.int8)
+        flag = np.zeros(self.ne, np.uint8)
+        flag[np.asarray(elems, dtype=np.int64)] = 1
+        h = lib().orc_refine(self._h, _i8(col), flag.ctypes.data_as(C.POINTER(C.c_uint8)))
+        if not h:
+            raise ValueError("oracle: " + lib().orc_last_error().decode())
+        m = OracleMesh.__new__(OracleMesh)
+        m.dim = self.dim
+        m._h = h
+        m.ne = int(lib().orc_mesh_nelem(h))
+        m.ns = int(lib().orc_mesh_nsides(h))
+        m.nv = int(lib().orc_mesh_nvert(h))
+        m._L = self._L
+        m.colors = np.zeros(m.ns, np.int8)
+        m.hanging = np.zeros(m.ns, np.int8)
+        _check(lib().orc_mesh_refined(h, _i8(m.colors), _i8(m.hanging)))
+        return m
+
+    def elements(self):
+        """Vertex ids [E][dim+1] and unwrapped coordinates [E][dim+1][dim]."""
+        nvpe = self.dim + 1
+        ev = np.zeros((self.ne, nvpe), np.int32)
+        X = np.zeros((self.ne, nvpe, self.dim))
+        lib().orc_mesh_elements(self._h, _i32(ev), _d(X))
+        return ev, X
 
     def __del__(self):
         h = getattr(self, "_h", None)

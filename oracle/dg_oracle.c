@@ -301,6 +301,10 @@ typedef struct {
   /* geometry, FP64 */
   double *detJ;   /* ne */
   double *Jinv;   /* ne * dim * dim, row k = grad of reference coordinate k */
+  /* nonconforming meshes only (orc_refine), NULL otherwise */
+  int32_t *es2;   /* ne * nfpe: second side on a split edge of a coarse element, -1 if none */
+  int8_t *shalf;  /* per side: half of the right element's edge a hanging side covers, or -1 */
+  int8_t *col;    /* per side: color from the map of Sec. 3.2 */
 } orc_mesh;
 
 static void face_verts(int dim, int q, int *fv) {
@@ -363,6 +367,18 @@ static double det_and_inv(int dim, const double *J, double *Ji) {
 
 void orc_mesh_free(void *h);
 
+/* detJ and J^-1 of element e from its unwrapped coordinates; -1 if detJ <= 0 */
+static int elem_geometry(orc_mesh *m, int64_t e) {
+  int dim = m->dim;
+  double J[9];
+  const double *X = m->X + e * m->nvpe * dim;
+  for (int a = 0; a < dim; ++a)
+    for (int k = 0; k < dim; ++k) J[a * dim + k] = X[(k + 1) * dim + a] - X[a];
+  double det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
+  m->detJ[e] = det;
+  return det > 0.0 ? 0 : -1;
+}
+
 void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
                    const double *L) {
   if (dim != 2 && dim != 3) return fail("mesh: dim must be 2 or 3"), (void *)0;
@@ -398,16 +414,10 @@ void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int
         m->X[(e * nvpe + k) * dim + a] = x;
       }
     }
-    double J[9];
-    const double *X = m->X + e * nvpe * dim;
-    for (int a = 0; a < dim; ++a)
-      for (int k = 0; k < dim; ++k) J[a * dim + k] = X[(k + 1) * dim + a] - X[a];
-    double det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
-    if (!(det > 0.0)) {
+    if (elem_geometry(m, e)) {
       orc_mesh_free(m);
       return fail("mesh: element with non-positive Jacobian"), (void *)0;
     }
-    m->detJ[e] = det;
   }
   /* face table by sorting keys */
   int64_t nent = ne * nfpe;
@@ -488,6 +498,9 @@ void orc_mesh_free(void *h) {
   free(m->enb);
   free(m->detJ);
   free(m->Jinv);
+  free(m->es2);
+  free(m->shalf);
+  free(m->col);
   free(m);
 }
 
@@ -734,6 +747,238 @@ int orc_reorder(void *h, int nc, const int8_t *col, int32_t *elem_new_of_old,
 }
 
 /* ======================================================================= */
+/* Nonconforming refinement and its 6-color map (Sec. 3.2)                  */
+/* ======================================================================= */
+/* One level of isotropic refinement of the flagged triangles of a conforming
+ * triangle mesh whose edges carry colors 1..3.  A flagged triangle (v0, v1, v2)
+ * is split through the midpoints m_k of its edges k = (v_k, v_k+1) into the
+ * corner triangles (v0, m0, m2), (m0, v1, m1), (m2, m1, v2) and the middle
+ * triangle (m0, m1, m2), numbered in place of the parent in that order.  The
+ * midpoint of a split edge is a new vertex; ids nv, nv+1, ... follow the order
+ * of the split edges.
+ *
+ * Colors (Sec. 3.2): the two halves m = 1, 2 of a split edge of color c get
+ * ((c + 3m - 4) mod 6) + 1, that is c and c + 3; an edge inside a refined
+ * triangle takes the color of the parent edge it is parallel to (the edge
+ * joining the midpoints of parent edges a and b is parallel to the third one);
+ * the other edges keep their colors.
+ * Readings:
+ *  - half m = 1 is the one touching the endpoint of the parent edge with the
+ *    smaller vertex id.  The paper counts the halves counterclockwise per
+ *    element; two refined neighbours would count in opposite directions, so the
+ *    count is fixed by the global vertex order instead.
+ *  - Sides are listed as: each parent side in order (itself, or its halves with
+ *    m = 1 first), then for each refined triangle in element order its three
+ *    interior edges, with the corner children 0, 1, 2 as left elements and the
+ *    middle child as the right one.
+ *  - A half whose other neighbour is not refined is a hanging side: the fine
+ *    child is its left element and the coarse neighbour its right one.  shalf
+ *    gives which half of the coarse element's local edge it covers: 0 for the
+ *    half at the edge's first vertex, 1 for the other.
+ * Children and local edges are found by matching vertex ids, not from a fixed
+ * table.  Returns a new mesh (orc_mesh_free), or NULL. */
+
+/* local edge q of element e of mesh m joining vertices x and y, or -1 */
+static int find_edge(const orc_mesh *m, int64_t e, int32_t x, int32_t y) {
+  for (int q = 0; q < 3; ++q) {
+    int32_t a = m->ev[e * 3 + q], b = m->ev[e * 3 + (q + 1) % 3];
+    if ((a == x && b == y) || (a == y && b == x)) return q;
+  }
+  return -1;
+}
+
+void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
+  const orc_mesh *b = (const orc_mesh *)h;
+  if (b->dim != 2) return fail("refine: triangles only"), (void *)0;
+  int64_t ne0 = b->ne, ns0 = b->ns, ne = 0, nv = b->nv, nref = 0;
+  int64_t *first = (int64_t *)malloc(sizeof(int64_t) * ne0);
+  for (int64_t e = 0; e < ne0; ++e) {
+    first[e] = ne;
+    ne += flag[e] ? 4 : 1;
+    nref += flag[e] ? 1 : 0;
+  }
+  int32_t *mid = (int32_t *)malloc(sizeof(int32_t) * ns0);
+  for (int64_t s = 0; s < ns0; ++s) {
+    int32_t l = b->sl[s], r = b->sr[s];
+    mid[s] = (flag[l] || (r >= 0 && flag[r])) ? (int32_t)nv++ : -1;
+  }
+  orc_mesh *m = (orc_mesh *)calloc(1, sizeof *m);
+  m->dim = 2;
+  m->nvpe = m->nfpe = 3;
+  m->nv = nv;
+  m->ne = ne;
+  m->periodic = b->periodic;
+  m->L[0] = b->L[0];
+  m->L[1] = b->L[1];
+  m->ev = (int32_t *)malloc(sizeof(int32_t) * ne * 3);
+  m->X = (double *)malloc(sizeof(double) * ne * 6);
+  m->detJ = (double *)malloc(sizeof(double) * ne);
+  m->Jinv = (double *)malloc(sizeof(double) * ne * 4);
+  int bad = 0;
+  for (int64_t e = 0; e < ne0; ++e) {
+    const int32_t *v = b->ev + e * 3;
+    const double *P = b->X + e * 6;
+    int64_t n = first[e];
+    if (!flag[e]) {
+      memcpy(m->ev + n * 3, v, sizeof(int32_t) * 3);
+      memcpy(m->X + n * 6, P, sizeof(double) * 6);
+      continue;
+    }
+    int32_t mv[3];
+    double Q[3][2];
+    for (int k = 0; k < 3; ++k) {
+      mv[k] = mid[b->es[e * 3 + k]];
+      for (int a = 0; a < 2; ++a) Q[k][a] = 0.5 * (P[k * 2 + a] + P[((k + 1) % 3) * 2 + a]);
+    }
+    /* children as (vertex id, coordinates) */
+    int32_t cid[4][3] = {{v[0], mv[0], mv[2]}, {mv[0], v[1], mv[1]}, {mv[2], mv[1], v[2]}, {mv[0], mv[1], mv[2]}};
+    const double *cx[4][3] = {{P, Q[0], Q[2]}, {Q[0], P + 2, Q[1]}, {Q[2], Q[1], P + 4}, {Q[0], Q[1], Q[2]}};
+    for (int c = 0; c < 4; ++c)
+      for (int k = 0; k < 3; ++k) {
+        m->ev[(n + c) * 3 + k] = cid[c][k];
+        m->X[((n + c) * 3 + k) * 2 + 0] = cx[c][k][0];
+        m->X[((n + c) * 3 + k) * 2 + 1] = cx[c][k][1];
+      }
+  }
+  int64_t cap = 2 * ns0 + 3 * nref, ns = 0;
+  m->sl = (int32_t *)malloc(sizeof(int32_t) * cap);
+  m->sr = (int32_t *)malloc(sizeof(int32_t) * cap);
+  m->sql = (int8_t *)malloc(cap);
+  m->sqr = (int8_t *)malloc(cap);
+  m->shalf = (int8_t *)malloc(cap);
+  m->col = (int8_t *)malloc(cap);
+#define ADD_SIDE(L_, R_, QL_, QR_, H_, C_)                                        \
+  do {                                                                           \
+    m->sl[ns] = (int32_t)(L_);                                                   \
+    m->sr[ns] = (int32_t)(R_);                                                   \
+    m->sql[ns] = (int8_t)(QL_);                                                  \
+    m->sqr[ns] = (int8_t)(QR_);                                                  \
+    m->shalf[ns] = (int8_t)(H_);                                                 \
+    m->col[ns] = (int8_t)(C_);                                                   \
+    ++ns;                                                                        \
+  } while (0)
+  for (int64_t s = 0; s < ns0; ++s) {
+    int32_t l = b->sl[s], r = b->sr[s];
+    int c = col[s];
+    int Rl = flag[l] != 0, Rr = r >= 0 && flag[r] != 0;
+    if (!Rl && !Rr) {
+      ADD_SIDE(first[l], r >= 0 ? first[r] : -1, b->sql[s], r >= 0 ? b->sqr[s] : -1, -1, c);
+      continue;
+    }
+    int32_t va = b->ev[l * 3 + b->sql[s]], vb = b->ev[l * 3 + (b->sql[s] + 1) % 3];
+    for (int half = 1; half <= 2; ++half) {
+      int32_t Pv = (half == 1) == (va < vb) ? va : vb; /* endpoint this half touches */
+      int cm = (c + 3 * half - 4) % 6 + 1;
+      /* the fine element(s) holding the half (Pv, mid) and their local edge */
+      int64_t fl = -1, fr = -1;
+      int ql = -1, qr = -1;
+      for (int k = 0; k < 4 && Rl; ++k)
+        if ((ql = find_edge(m, first[l] + k, Pv, mid[s])) >= 0) {
+          fl = first[l] + k;
+          break;
+        }
+      for (int k = 0; k < 4 && Rr; ++k)
+        if ((qr = find_edge(m, first[r] + k, Pv, mid[s])) >= 0) {
+          fr = first[r] + k;
+          break;
+        }
+      if ((Rl && fl < 0) || (Rr && fr < 0)) bad = 1;
+      if (r < 0) {
+        ADD_SIDE(fl, -1, ql, -1, -1, cm);
+      } else if (Rl && Rr) {
+        ADD_SIDE(fl, fr, ql, qr, -1, cm);
+      } else if (Rl) { /* coarse right neighbour */
+        int qc = b->sqr[s];
+        ADD_SIDE(fl, first[r], ql, qc, b->ev[r * 3 + qc] == Pv ? 0 : 1, cm);
+      } else { /* coarse left element: the fine child becomes the left one */
+        int qc = b->sql[s];
+        ADD_SIDE(fr, first[l], qr, qc, b->ev[l * 3 + qc] == Pv ? 0 : 1, cm);
+      }
+    }
+  }
+  for (int64_t e = 0; e < ne0; ++e) {
+    if (!flag[e]) continue;
+    int64_t n = first[e];
+    for (int k = 0; k < 3; ++k) { /* the interior edge of corner child k */
+      int q = -1, qm = -1, ea = -1, eb = -1;
+      for (int t = 0; t < 3 && q < 0; ++t)
+        if (m->ev[(n + k) * 3 + t] >= b->nv && m->ev[(n + k) * 3 + (t + 1) % 3] >= b->nv) q = t;
+      if (q < 0) {
+        bad = 1;
+        continue;
+      }
+      int32_t x = m->ev[(n + k) * 3 + q], y = m->ev[(n + k) * 3 + (q + 1) % 3];
+      qm = find_edge(m, n + 3, x, y);
+      for (int t = 0; t < 3; ++t) {
+        int32_t mt = mid[b->es[e * 3 + t]];
+        if (mt == x || mt == y) {
+          if (ea < 0) ea = t;
+          else eb = t;
+        }
+      }
+      if (qm < 0 || ea < 0 || eb < 0) {
+        bad = 1;
+        continue;
+      }
+      ADD_SIDE(n + k, n + 3, q, qm, -1, col[b->es[e * 3 + (3 - ea - eb)]]);
+    }
+  }
+#undef ADD_SIDE
+  m->ns = ns;
+  m->es = (int32_t *)malloc(sizeof(int32_t) * ne * 3);
+  m->es2 = (int32_t *)malloc(sizeof(int32_t) * ne * 3);
+  m->enb = (int32_t *)malloc(sizeof(int32_t) * ne * 3);
+  for (int64_t i = 0; i < ne * 3; ++i) m->es[i] = m->es2[i] = -1;
+  for (int64_t t = 0; t < ns && !bad; ++t) {
+    int64_t il = (int64_t)m->sl[t] * 3 + m->sql[t];
+    if (m->es[il] >= 0) bad = 1;
+    m->es[il] = (int32_t)t;
+    m->enb[il] = m->sr[t];
+    if (m->sr[t] >= 0) {
+      int64_t ir = (int64_t)m->sr[t] * 3 + m->sqr[t];
+      if (m->es[ir] < 0) {
+        m->es[ir] = (int32_t)t;
+        m->enb[ir] = m->sl[t];
+      } else if (m->shalf[t] >= 0 && m->es2[ir] < 0) {
+        m->es2[ir] = (int32_t)t;
+      } else {
+        bad = 1;
+      }
+    }
+  }
+  for (int64_t i = 0; i < ne * 3 && !bad; ++i)
+    if (m->es[i] < 0) bad = 1;
+  for (int64_t e = 0; e < ne && !bad; ++e)
+    if (elem_geometry(m, e)) bad = 1;
+  free(first);
+  free(mid);
+  if (bad) {
+    orc_mesh_free(m);
+    return fail("refine: inconsistent refined mesh"), (void *)0;
+  }
+  return m;
+}
+
+int64_t orc_mesh_nelem(void *h) { return ((orc_mesh *)h)->ne; }
+int64_t orc_mesh_nvert(void *h) { return ((orc_mesh *)h)->nv; }
+
+/* element vertex ids and unwrapped coordinates */
+void orc_mesh_elements(void *h, int32_t *ev, double *X) {
+  orc_mesh *m = (orc_mesh *)h;
+  memcpy(ev, m->ev, sizeof(int32_t) * m->ne * m->nvpe);
+  memcpy(X, m->X, sizeof(double) * m->ne * m->nvpe * m->dim);
+}
+
+/* colors of a refined mesh and the hanging half of each side (-1 conforming) */
+int orc_mesh_refined(void *h, int8_t *col, int8_t *half) {
+  orc_mesh *m = (orc_mesh *)h;
+  if (!m->col) return fail("mesh: not refined");
+  memcpy(col, m->col, m->ns);
+  memcpy(half, m->shalf, m->ns);
+  return 0;
+}
+
+/* ======================================================================= */
 /* Physics: Euler flux and local Lax-Friedrichs flux                        */
 /* ======================================================================= */
 /* Euler: U = (rho, rho u, rho v[, rho w], E), p = (gamma-1)(E - rho|u|^2/2).
@@ -945,8 +1190,7 @@ static void face_geometry(const orc_mesh *m, int64_t e, int q, const orc_rules *
  * on a tetrahedral face the collapsed rule is not symmetric under a
  * permutation of the face's vertices, and a per-element choice would evaluate
  * the flux at different points on the two sides (not conservative). */
-static void face_points_of_left(const orc_mesh *m, int64_t e, int f, const orc_rules *R, orc_face *F) {
-  int32_t s = m->es[e * m->nfpe + f];
+static void face_points_of_left(const orc_mesh *m, int64_t e, int32_t s, const orc_rules *R, orc_face *F) {
   int64_t l = m->sl[s];
   if (l == e) return;
   int dim = m->dim, fv[3];
@@ -1009,11 +1253,22 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
         }
       }
     }
-    /* surface integrals: - (1/detJ) sum_faces |f| sum_q w_q phi_j(x_q) F*(U_e, U_nb, n) */
-    for (int f = 0; f < m->nfpe; ++f) {
+    /* surface integrals: - (1/detJ) sum_faces |f| sum_q w_q phi_j(x_q) F*(U_e, U_nb, n);
+     * a coarse element's split edge is integrated as its two halves, each with
+     * the points and length of the fine neighbour's edge (Sec. 3.2) */
+    for (int sub = 0; sub < 2 * m->nfpe; ++sub) {
+      int f = sub % m->nfpe;
+      int32_t s = sub < m->nfpe ? m->es[e * m->nfpe + f] : (m->es2 ? m->es2[e * m->nfpe + f] : -1);
+      if (s < 0) continue;
       face_geometry(m, e, f, &R, &F);  /* own outward normal and measure */
-      face_points_of_left(m, e, f, &R, &F);
-      int32_t nb = m->enb[e * m->nfpe + f];
+      face_points_of_left(m, e, s, &R, &F);
+      int32_t nb = m->sl[s] == e ? m->sr[s] : m->sl[s];
+      if (m->shalf && m->shalf[s] >= 0 && m->sr[s] == e) {
+        const double *Xl = m->X + (int64_t)m->sl[s] * 6;
+        int q = m->sql[s];
+        double dx = Xl[((q + 1) % 3) * 2] - Xl[q * 2], dy = Xl[((q + 1) % 3) * 2 + 1] - Xl[q * 2 + 1];
+        F.meas = sqrt(dx * dx + dy * dy);
+      }
       double scale = F.meas / m->detJ[e];
       for (int q = 0; q < F.nq; ++q) {
         double rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];

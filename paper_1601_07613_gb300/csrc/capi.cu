@@ -23,7 +23,10 @@ thread_local std::string g_err;
 #define DGC_CUDA(call)                                                                      \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
-    if (e_ != cudaSuccess) throw Error{DGC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError(); /* a failed call leaves its code pending; do not report it twice */ \
+      throw Error{DGC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};        \
+    }                                                                                       \
   } while (0)
 
 template <typename F>
@@ -134,11 +137,13 @@ void upload(Mesh& m) {
   const int gstride = dim == 2 ? 2 : 3;  // double2 per edge
   std::vector<int4> topo(m.ns);
   std::vector<double2> fgeo((size_t)m.ns * gstride);
-  std::vector<int32_t> slots((size_t)m.ne * nfpe, 0);
+  const int slot_w = m.refined ? 2 * nfpe : nfpe;
+  std::vector<int32_t> slots((size_t)m.ne * slot_w, -1);
   for (int64_t k = 0; k < m.ns; ++k) {
     int64_t old = m.side_old_of_new[k];
     int32_t l = m.sl[old], r = m.sr[old];
-    int ql = m.sql[old], qr = r >= 0 ? m.sqr[old] : 15;
+    const int h = m.shalf.empty() ? -1 : m.shalf[old];
+    int ql = m.sql[old], qr = r < 0 ? 15 : (h >= 0 ? 3 + 2 * m.sqr[old] + h : m.sqr[old]);
     int orient = 0;
     if (dim == 3 && r >= 0) {
       // vertex permutation between the two sides' face parameterisations:
@@ -169,11 +174,17 @@ void upload(Mesh& m) {
       fgeo[3 * k + 1] = make_double2(n[2], 0.0);
       fgeo[3 * k + 2] = make_double2(sl, sr);
     }
-    slots[(size_t)en[l] * nfpe + ql] = (int32_t)(2 * k);
-    if (r >= 0) slots[(size_t)en[r] * nfpe + qr] = (int32_t)(2 * k + 1);
+    slots[(size_t)en[l] * slot_w + ql] = (int32_t)(2 * k);
+    if (r >= 0) {
+      const int q = m.sqr[old];
+      int32_t* sr_ = &slots[(size_t)en[r] * slot_w];
+      sr_[sr_[q] < 0 ? q : nfpe + q] = (int32_t)(2 * k + 1);
+    }
   }
   auto d = std::make_unique<DeviceMesh>();
   d->device = dev;
+  d->slot_w = slot_w;
+  d->edge_tables = m.refined ? 9 : 3;
   try {
     d->jinv = dalloc<double>((int64_t)jinv.size());
     d->inr = dalloc<double>(m.ne);
@@ -418,6 +429,40 @@ dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, in
     if (right) std::copy(m.sr.begin(), m.sr.end(), right);
     if (qleft) std::copy(m.sql.begin(), m.sql.end(), qleft);
     if (qright) std::copy(m.sqr.begin(), m.sqr.end(), qright);
+  });
+}
+
+dgc_status dgc_get_hanging(const dgc_mesh* mesh, int8_t* half) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(half != nullptr, "null argument");
+    if (m.shalf.empty()) std::fill_n(half, m.ns, (int8_t)-1);
+    else std::copy(m.shalf.begin(), m.shalf.end(), half);
+  });
+}
+
+dgc_status dgc_get_elements(const dgc_mesh* mesh, int32_t* ev, double* xyz) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    if (ev) std::copy(m.ev.begin(), m.ev.end(), ev);
+    if (xyz) std::copy(m.X.begin(), m.X.end(), xyz);
+  });
+}
+
+dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.dim == 2, "nonconforming refinement is implemented for triangle meshes", DGC_ERR_UNSUPPORTED);
+    require(!m.refined, "the mesh is already refined (one level is supported)", DGC_ERR_UNSUPPORTED);
+    require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
+            "refine a mesh colored by dgc_color_edges with 3 colors");
+    require(n >= 0 && (n == 0 || elems != nullptr), "bad element list");
+    std::vector<uint8_t> flag(m.ne, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      require(elems[i] >= 0 && elems[i] < m.ne, "element id out of range");
+      flag[elems[i]] = 1;
+    }
+    refine(m, flag);
   });
 }
 
@@ -820,7 +865,9 @@ struct dgc_batch {
   int key_prec = -1, key_epb = -1;
   cudaGraphExec_t exec = nullptr;
   double graph_cfl = 0.0;
-  cudaStream_t graph_stream = nullptr;
+  // the step is captured on this library-owned stream (capture is not allowed
+  // on the legacy default stream a caller may pass) and launched on the caller's
+  cudaStream_t capture_stream = nullptr;
   int64_t launches = 0;
 };
 
@@ -829,6 +876,8 @@ namespace {
 void batch_release(dgc_batch& b) {
   if (b.exec) cudaGraphExecDestroy(b.exec);
   b.exec = nullptr;
+  if (b.capture_stream) cudaStreamDestroy(b.capture_stream);
+  b.capture_stream = nullptr;
   cudaFree(b.dmeshes);
   cudaFree(b.dtiles);
   b.dmeshes = nullptr;
@@ -996,16 +1045,19 @@ dgc_status dgc_batch_rk_step(dgc_batch* batch, dgc_prec prec, double* const* c_d
         if (b.exec) cudaGraphExecDestroy(b.exec);
         b.exec = nullptr;
         cudaGraph_t g = nullptr;
-        DGC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        if (!b.capture_stream) DGC_CUDA(cudaStreamCreateWithFlags(&b.capture_stream, cudaStreamNonBlocking));
+        const cudaStream_t cs = b.capture_stream;
+        DGC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         int64_t n = 0;
         try {
-          n = batch_enqueue(b, prec, cfl_, st);
+          n = batch_enqueue(b, prec, cfl_, cs);
         } catch (...) {
-          cudaStreamEndCapture(st, &g);
+          cudaStreamEndCapture(cs, &g);
           if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
           throw;
         }
-        DGC_CUDA(cudaStreamEndCapture(st, &g));
+        DGC_CUDA(cudaStreamEndCapture(cs, &g));
         cudaError_t e = cudaGraphInstantiate(&b.exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) throw Error{DGC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};

@@ -14,9 +14,14 @@ struct DeviceMesh {
   int device = -1;
   double* jinv = nullptr;   // [E][dim*dim] rows = gradients of the reference coordinates
   double* inr = nullptr;    // [E] inradius
-  int4* topo = nullptr;     // [Ns] (left, right or -1, local faces lq | rq << 4 | orient << 8, 0)
+  // [Ns] (left, right or -1, lq | rq << 4 | orient << 8, 0).  On triangles rq is
+  // the right element's edge table: its local edge 0..2, or 3 + 2 f + h for
+  // half h of local edge f (coarse side of a hanging edge), 15 on a boundary
+  int4* topo = nullptr;
   double2* fgeo = nullptr;  // [Ns][2] 2D: (nx, ny), (|f|/detJ_l, |f|/detJ_r); 3D: [Ns][3]
-  int32_t* slots = nullptr; // [E][nfpe] two-pass gather slots 2k + side
+  int32_t* slots = nullptr; // [E][slot_w] two-pass gather slots 2k + side, -1 unused
+  int slot_w = 3;           // sides per element at most (nfpe; 2 nfpe when refined)
+  int edge_tables = 3;      // triangle edge tables the surface kernels stage (3, or 9 when refined)
   float* ftab = nullptr;    // 3D face tables (float copy)
   double* ftabd = nullptr;  // 3D face tables
   float* cfl_est = nullptr; // [E] FP32 step estimates of the CFL pre-pass, then 1 minimum

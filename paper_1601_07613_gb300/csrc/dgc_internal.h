@@ -20,6 +20,9 @@ struct RefTables {
   std::vector<double> dphiV;           // [dim][nqv][np]
   std::vector<double> fw;              // [nqf] face weights
   std::vector<double> phiF;            // [nfaces][nqf][np], face points in face parameters
+  // triangles: phi_j on half h of local edge f, at edge parameter (h + t_q) / 2,
+  // [nfaces][2][nqf][np] (the coarse side of a hanging edge, Sec. 3.2)
+  std::vector<double> phiH;
 };
 
 // Builds the tables (quadrature + orthonormal basis) for triangles (dim 2) or
@@ -50,7 +53,11 @@ struct Mesh {
   // edge (face) table, original order
   std::vector<int32_t> sl, sr;
   std::vector<int8_t> sql, sqr;
-  std::vector<int32_t> face_of;  // [ne][nfpe] -> side
+  std::vector<int32_t> face_of;  // [ne][nfpe] -> side (the first of two on a split edge)
+  // nonconforming meshes (Sec. 3.2): half (0 or 1) of the right element's local
+  // edge that side s covers, -1 for a conforming side; empty when conforming
+  std::vector<int8_t> shalf;
+  bool refined = false;
   // geometry, original order
   std::vector<double> detJ, Jinv, inradius;  // Jinv [ne][dim][dim] (row k = grad r_k)
   std::vector<double> snormal, smeas;        // [ns][dim] outward normal of the left element, |face|
@@ -86,6 +93,7 @@ struct ColorStats {
 ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps);
 int color_faces_naive(Mesh& m);
 void reorder(Mesh& m, bool renumber, bool reorder_left);
+void refine(Mesh& m, const std::vector<uint8_t>& flag);
 void vol_points(const Mesh& m, double* xyz);
 void project(const Mesh& m, const double* vals, double* c);
 

@@ -49,15 +49,15 @@ int stage_update(const Ctx& x, bool rhs_f32, const double* us, const void* rhs, 
 
 // rhs[e][v] += sum_f buf[slot(e, f)][v]  (second pass of the buffer scheme, Sec. 1)
 template <typename RT>
-__global__ void k_gather(RT* rhs, const RT* buf, const int32_t* slots, int nfpe, int nv, int64_t n) {
+__global__ void k_gather(RT* rhs, const RT* buf, const int32_t* slots, int slot_w, int nv, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = i / nv;
   const int v = (int)(i - e * nv);
   RT s = rhs[i];
-  for (int f = 0; f < nfpe; ++f) {
-    const int64_t slot = slots[e * nfpe + f];
-    s += buf[slot * nv + v];
+  for (int f = 0; f < slot_w; ++f) {
+    const int64_t slot = slots[e * slot_w + f];
+    if (slot >= 0) s += buf[slot * nv + v];
   }
   rhs[i] = s;
 }
@@ -69,10 +69,10 @@ int gather_two_pass(const Ctx& x, bool f32, void* rhs, const void* buf) {
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
   if (f32)
     k_gather<float><<<grid, bs, 0, x.st>>>(static_cast<float*>(rhs), static_cast<const float*>(buf),
-                                           x.d->slots, x.nfpe, nv, n);
+                                           x.d->slots, x.d->slot_w, nv, n);
   else
     k_gather<double><<<grid, bs, 0, x.st>>>(static_cast<double*>(rhs), static_cast<const double*>(buf),
-                                            x.d->slots, x.nfpe, nv, n);
+                                            x.d->slots, x.d->slot_w, nv, n);
   return 1;
 }
 

@@ -49,7 +49,9 @@ struct TriTab {
   T phiV[TriDim<P>::NQV][TriDim<P>::NP];  // phi_j at volume points
   T vr[TriDim<P>::NQV][TriDim<P>::NP];    // w_q dphi_j/dr
   T vs[TriDim<P>::NQV][TriDim<P>::NP];    // w_q dphi_j/ds
-  T phiE[3][TriDim<P>::NQE][TriDim<P>::NP];  // phi_j at the points of local edge 0..2
+  // phi_j at the points of local edge f = 0..2, then at those of half h of
+  // local edge f as [3 + 2 f + h] (the coarse side of a hanging edge)
+  T phiE[9][TriDim<P>::NQE][TriDim<P>::NP];
   T wE[TriDim<P>::NQE];                      // edge weights, sum 1
 };
 
@@ -81,6 +83,9 @@ static void fill_tab(TriTab<T, P>& K, const RefTables& R) {
   for (int f = 0; f < 3; ++f)
     for (int q = 0; q < D::NQE; ++q)
       for (int j = 0; j < D::NP; ++j) K.phiE[f][q][j] = (T)R.phiF[(f * D::NQE + q) * D::NP + j];
+  for (int t = 0; t < 6; ++t)
+    for (int q = 0; q < D::NQE; ++q)
+      for (int j = 0; j < D::NP; ++j) K.phiE[3 + t][q][j] = (T)R.phiH[(t * D::NQE + q) * D::NP + j];
   for (int q = 0; q < D::NQE; ++q) K.wE[q] = (T)R.fw[q];
 }
 
@@ -367,6 +372,7 @@ struct SurfParams {
   void* rhs;
   void* buf;
   StageArgs sa;
+  int ntab;  // edge tables to stage (3, or 9 on meshes with hanging edges)
 };
 
 // the contribution of one lane's element is in acc; write it as the mode asks
@@ -432,13 +438,14 @@ __device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, in
   }
 }
 
-// edge tables of order P into shared memory (the block's threads cooperate)
+// the first ntab edge tables of order P into shared memory (the block's
+// threads cooperate): 3 on conforming meshes, 9 with hanging edges
 template <int P, typename CT>
-__device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw) {
+__device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw, int ntab = 3) {
   using D = TriDim<P>;
   const TriTab<CT, P>& K = tri_tab<CT, P>();
   const CT* src = &K.phiE[0][0][0];
-  for (int i = threadIdx.x; i < 3 * D::NQE * D::NP; i += blockDim.x) sphi[i] = src[i];
+  for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) sphi[i] = src[i];
   if (threadIdx.x < D::NQE) sw[threadIdx.x] = K.wE[threadIdx.x];
 }
 
@@ -452,9 +459,9 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool v
 template <int P, typename CT, typename ST, typename RT, int MODE>
 __global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
-  __shared__ CT sphi[3 * D::NQE * D::NP];
+  __shared__ CT sphi[9 * D::NQE * D::NP];
   __shared__ CT sw[D::NQE];
-  stage_edge_tables<P, CT>(sphi, sw);
+  stage_edge_tables<P, CT>(sphi, sw, A.ntab);
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t k = A.begin + (t >> 1);
@@ -898,6 +905,7 @@ int tri_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t 
   A.state = state;
   A.rhs = rhs;
   A.buf = buf;
+  A.ntab = x.d->edge_tables;
   if (sa) A.sa = *sa;
   switch (x.p) {
     case 1: return surf_p<1>(x, ty, mode, A);

@@ -283,6 +283,19 @@ RefTables make_tables(int dim, int p) {
       for (int j = 0; j < T.np; ++j) T.phiF[((size_t)f * T.nqf + q) * T.np + j] = phi[j];
     }
   }
+  if (dim == 2) {
+    T.phiH.resize((size_t)3 * 2 * T.nqf * T.np);
+    for (int f = 0; f < 3; ++f)
+      for (int h = 0; h < 2; ++h)
+        for (int q = 0; q < T.nqf; ++q) {
+          const double t = 0.5 * (h + fa[q]);
+          const double* V0 = kTriV[f];
+          const double* V1 = kTriV[(f + 1) % 3];
+          double x[3] = {V0[0] + t * (V1[0] - V0[0]), V0[1] + t * (V1[1] - V0[1]), 0.0};
+          basis_eval(dim, p, x, phi.data(), nullptr);
+          for (int j = 0; j < T.np; ++j) T.phiH[(((size_t)f * 2 + h) * T.nqf + q) * T.np + j] = phi[j];
+        }
+  }
   return T;
 }
 
@@ -354,6 +367,91 @@ struct KeyTable {
 };
 }  // namespace
 
+// detJ and the inverse Jacobian of element e from its unwrapped coordinates.
+static void element_jacobian(Mesh& m, int64_t e) {
+  const int dim = m.dim;
+  const double* X = &m.X[(size_t)e * m.nvpe * dim];
+  double* Ji = &m.Jinv[(size_t)e * dim * dim];
+  double det;
+  if (dim == 2) {
+    double a = X[2] - X[0], b = X[4] - X[0], c = X[3] - X[1], d = X[5] - X[1];
+    det = a * d - b * c;
+    Ji[0] = d / det;
+    Ji[1] = -b / det;
+    Ji[2] = -c / det;
+    Ji[3] = a / det;
+  } else {
+    double J[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) J[a][k] = X[(k + 1) * 3 + a] - X[a];
+    det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+          J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    // inverse by cofactors: Ji[k][a] = cof(a,k)/det
+    for (int k = 0; k < 3; ++k)
+      for (int a = 0; a < 3; ++a) {
+        int r0 = (a + 1) % 3, r1 = (a + 2) % 3, c0 = (k + 1) % 3, c1 = (k + 2) % 3;
+        Ji[k * 3 + a] = (J[r0][c0] * J[r1][c1] - J[r0][c1] * J[r1][c0]) / det;
+      }
+  }
+  if (!(det > 0.0)) throw Error{DGC_ERR_MESH, "element with non-positive Jacobian (check orientation)"};
+  m.detJ[e] = det;
+}
+
+// Outward unit normal and measure of local face q of element e (from its
+// unwrapped coordinates).
+static double face_normal(const Mesh& m, int64_t e, int q, double* n) {
+  const int dim = m.dim;
+  const double* X = &m.X[(size_t)e * m.nvpe * dim];
+  int fv[3];
+  face_vertices(dim, q, fv);
+  double meas;
+  n[0] = n[1] = n[2] = 0.0;
+  if (dim == 2) {
+    // CCW triangle: outward normal of edge v_q -> v_{q+1} is (dy, -dx)/|d|
+    double dx = X[fv[1] * 2] - X[fv[0] * 2], dy = X[fv[1] * 2 + 1] - X[fv[0] * 2 + 1];
+    meas = std::hypot(dx, dy);
+    n[0] = dy / meas;
+    n[1] = -dx / meas;
+  } else {
+    double u[3], v[3], w[3];
+    for (int a = 0; a < 3; ++a) {
+      u[a] = X[fv[1] * 3 + a] - X[fv[0] * 3 + a];
+      v[a] = X[fv[2] * 3 + a] - X[fv[0] * 3 + a];
+      w[a] = X[q * 3 + a] - X[fv[0] * 3 + a];  // towards the opposite vertex
+    }
+    n[0] = u[1] * v[2] - u[2] * v[1];
+    n[1] = u[2] * v[0] - u[0] * v[2];
+    n[2] = u[0] * v[1] - u[1] * v[0];
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    meas = 0.5 * nn;
+    double sgn = (n[0] * w[0] + n[1] * w[1] + n[2] * w[2]) > 0.0 ? -1.0 : 1.0;
+    for (int a = 0; a < 3; ++a) n[a] *= sgn / nn;
+  }
+  return meas;
+}
+
+// Face geometry from the left element (normal, measure: on a hanging side the
+// left element is the fine one, so the measure is the half edge's), and the
+// inradius dim |element| / |boundary| from each element's own faces.
+static void side_geometry(Mesh& m) {
+  const int dim = m.dim;
+  m.snormal.assign((size_t)m.ns * dim, 0.0);
+  m.smeas.assign(m.ns, 0.0);
+  for (int64_t s = 0; s < m.ns; ++s) {
+    double n[3];
+    m.smeas[s] = face_normal(m, m.sl[s], m.sql[s], n);
+    for (int a = 0; a < dim; ++a) m.snormal[(size_t)s * dim + a] = n[a];
+  }
+  m.inradius.resize(m.ne);
+  for (int64_t e = 0; e < m.ne; ++e) {
+    double bnd = 0.0, n[3];
+    for (int q = 0; q < m.nfpe; ++q) bnd += face_normal(m, e, q, n);
+    double vol = m.detJ[e] / (dim == 2 ? 2.0 : 6.0);
+    m.inradius[e] = dim * vol / bnd;
+  }
+}
+
 Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
                  const double* periodic_len) {
   if (dim != 2 && dim != 3) throw Error{DGC_ERR_ARG, "dim must be 2 or 3"};
@@ -391,31 +489,7 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
         X[k * dim + a] = x;
       }
     }
-    double* Ji = &m->Jinv[(size_t)e * dim * dim];
-    double det;
-    if (dim == 2) {
-      double a = X[2] - X[0], b = X[4] - X[0], c = X[3] - X[1], d = X[5] - X[1];
-      det = a * d - b * c;
-      Ji[0] = d / det;
-      Ji[1] = -b / det;
-      Ji[2] = -c / det;
-      Ji[3] = a / det;
-    } else {
-      double J[3][3];
-      for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) J[a][k] = X[(k + 1) * 3 + a] - X[a];
-      det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-            J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-      // inverse by cofactors: Ji[k][a] = cof(a,k)/det
-      for (int k = 0; k < 3; ++k)
-        for (int a = 0; a < 3; ++a) {
-          int r0 = (a + 1) % 3, r1 = (a + 2) % 3, c0 = (k + 1) % 3, c1 = (k + 2) % 3;
-          Ji[k * 3 + a] = (J[r0][c0] * J[r1][c1] - J[r0][c1] * J[r1][c0]) / det;
-        }
-    }
-    if (!(det > 0.0)) throw Error{DGC_ERR_MESH, "element with non-positive Jacobian (check orientation)"};
-    m->detJ[e] = det;
+    element_jacobian(*m, e);
   }
   // edge/face table, numbered by first appearance
   KeyTable kt(ne * m->nfpe);
@@ -445,48 +519,7 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
       }
     }
   m->ns = (int64_t)m->sl.size();
-  // face geometry from the left element, inradius = dim |element| / |boundary|
-  m->snormal.resize((size_t)m->ns * dim);
-  m->smeas.resize(m->ns);
-  std::vector<double> bnd(ne, 0.0);
-  for (int64_t e = 0; e < ne; ++e)
-    for (int q = 0; q < nfpe; ++q) {
-      const double* X = &m->X[(size_t)e * nvpe * dim];
-      int fv[3];
-      face_vertices(dim, q, fv);
-      double n[3] = {0, 0, 0}, meas;
-      if (dim == 2) {
-        // CCW triangle: outward normal of edge v_q -> v_{q+1} is (dy, -dx)/|d|
-        double dx = X[fv[1] * 2] - X[fv[0] * 2], dy = X[fv[1] * 2 + 1] - X[fv[0] * 2 + 1];
-        meas = std::hypot(dx, dy);
-        n[0] = dy / meas;
-        n[1] = -dx / meas;
-      } else {
-        double u[3], v[3], w[3];
-        for (int a = 0; a < 3; ++a) {
-          u[a] = X[fv[1] * 3 + a] - X[fv[0] * 3 + a];
-          v[a] = X[fv[2] * 3 + a] - X[fv[0] * 3 + a];
-          w[a] = X[q * 3 + a] - X[fv[0] * 3 + a];  // towards the opposite vertex
-        }
-        n[0] = u[1] * v[2] - u[2] * v[1];
-        n[1] = u[2] * v[0] - u[0] * v[2];
-        n[2] = u[0] * v[1] - u[1] * v[0];
-        double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        meas = 0.5 * nn;
-        double sgn = (n[0] * w[0] + n[1] * w[1] + n[2] * w[2]) > 0.0 ? -1.0 : 1.0;
-        for (int a = 0; a < 3; ++a) n[a] *= sgn / nn;
-      }
-      bnd[e] += meas;
-      int32_t s = m->face_of[(size_t)e * nfpe + q];
-      if (m->sl[s] == e) {
-        for (int a = 0; a < dim; ++a) m->snormal[(size_t)s * dim + a] = n[a];
-        m->smeas[s] = meas;
-      }
-    }
-  for (int64_t e = 0; e < ne; ++e) {
-    double vol = m->detJ[e] / (dim == 2 ? 2.0 : 6.0);
-    m->inradius[e] = dim * vol / bnd[e];
-  }
+  side_geometry(*m);
   m->tab = make_tables(dim, p);
   m->np = m->tab.np;
   return m.release();
@@ -714,6 +747,154 @@ void reorder(Mesh& m, bool renumber, bool reorder_left) {
   m.side_old_of_new = order;
   m.side_new_of_old.assign(m.ns, 0);
   for (int64_t i = 0; i < m.ns; ++i) m.side_new_of_old[order[i]] = (int32_t)i;
+  m.dirty = true;
+}
+
+// ---------------------------------------------------------------------------
+// Nonconforming refinement and its 6-color map (Sec. 3.2).  One level of
+// quadrisection of the flagged triangles of a conforming mesh colored with
+// three colors.  Triangle (v0, v1, v2) with edge midpoints m01, m12, m20 is
+// replaced, in place, by the children [v0, m01, m20], [m01, v1, m12],
+// [m20, m12, v2] and [m01, m12, m20].  Corner child k holds the halves of the
+// parent's local edges that meet at v_k, on its own local edges of the same
+// index.  Edge colors:
+//  - the half of a parent edge of color c next to the edge's endpoint with the
+//    smaller vertex id is the first child (m = 1), the other the second
+//    (m = 2); child m gets ((c + 3m - 4) mod 6) + 1, i.e. c or c + 3.  (Reading:
+//    the paper counts children counterclockwise per element; two refined
+//    neighbours run along their common edge in opposite directions, so the
+//    count is fixed once, by the global vertex order, for both sides.)
+//  - an interior edge takes the color of the parent edge it is parallel to;
+//  - edges of unrefined neighbours keep their colors.
+// Side order: the base sides in order (one side, or its two halves, first
+// child first), then three interior sides per refined element, in element
+// order.  A half whose other neighbour is not refined is a hanging side: the
+// fine child is its left element, the coarse element its right one, and shalf
+// records which half of the coarse element's local edge it covers (0: the half
+// next to the coarse edge's first vertex).
+// ---------------------------------------------------------------------------
+void refine(Mesh& m, const std::vector<uint8_t>& flag) {
+  const int64_t ne0 = m.ne, ns0 = m.ns;
+  std::vector<int64_t> first(ne0);
+  int64_t ne = 0;
+  for (int64_t e = 0; e < ne0; ++e) {
+    first[e] = ne;
+    ne += flag[e] ? 4 : 1;
+  }
+  if (ne > (1LL << 30)) throw Error{DGC_ERR_ARG, "refined mesh too large"};
+  std::vector<int32_t> mid(ns0, -1);  // midpoint vertex of each split base edge
+  int64_t nv = m.nv;
+  for (int64_t s = 0; s < ns0; ++s)
+    if (flag[m.sl[s]] || (m.sr[s] >= 0 && flag[m.sr[s]])) mid[s] = (int32_t)nv++;
+  if (nv > (1LL << 30)) throw Error{DGC_ERR_ARG, "refined mesh too large"};
+
+  std::vector<double> X((size_t)ne * 6);
+  std::vector<int32_t> ev((size_t)ne * 3);
+  for (int64_t e = 0; e < ne0; ++e) {
+    const double* P = &m.X[(size_t)e * 6];
+    const int32_t* v = &m.ev[(size_t)e * 3];
+    const int64_t n = first[e];
+    if (!flag[e]) {
+      std::copy_n(P, 6, &X[(size_t)n * 6]);
+      std::copy_n(v, 3, &ev[(size_t)n * 3]);
+      continue;
+    }
+    double Q[3][2];
+    int32_t mv[3];
+    for (int k = 0; k < 3; ++k) {
+      const int k1 = (k + 1) % 3;
+      for (int a = 0; a < 2; ++a) Q[k][a] = 0.5 * (P[k * 2 + a] + P[k1 * 2 + a]);
+      mv[k] = mid[m.face_of[(size_t)e * 3 + k]];
+    }
+    const int32_t cv[4][3] = {{v[0], mv[0], mv[2]}, {mv[0], v[1], mv[1]}, {mv[2], mv[1], v[2]}, {mv[0], mv[1], mv[2]}};
+    const double* cx[4][3] = {{P, Q[0], Q[2]}, {Q[0], P + 2, Q[1]}, {Q[2], Q[1], P + 4}, {Q[0], Q[1], Q[2]}};
+    for (int c = 0; c < 4; ++c)
+      for (int k = 0; k < 3; ++k) {
+        ev[(size_t)(n + c) * 3 + k] = cv[c][k];
+        for (int a = 0; a < 2; ++a) X[((size_t)(n + c) * 3 + k) * 2 + a] = cx[c][k][a];
+      }
+  }
+
+  std::vector<int32_t> sl, sr;
+  std::vector<int8_t> sql, sqr, half, col;
+  const size_t cap = (size_t)ns0 * 2 + (size_t)(ne - ne0);
+  sl.reserve(cap), sr.reserve(cap), sql.reserve(cap), sqr.reserve(cap), half.reserve(cap), col.reserve(cap);
+  auto add = [&](int64_t l, int64_t r, int ql, int qr, int h, int c) {
+    sl.push_back((int32_t)l);
+    sr.push_back((int32_t)r);
+    sql.push_back((int8_t)ql);
+    sqr.push_back((int8_t)qr);
+    half.push_back((int8_t)h);
+    col.push_back((int8_t)c);
+  };
+  for (int64_t s = 0; s < ns0; ++s) {
+    const int32_t l = m.sl[s], r = m.sr[s];
+    const int ql = m.sql[s], qr = m.sqr[s], c = m.color[s];
+    const bool Rl = flag[l] != 0, Rr = r >= 0 && flag[r] != 0;
+    if (!Rl && !Rr) {
+      add(first[l], r >= 0 ? first[r] : -1, ql, r >= 0 ? qr : -1, -1, c);
+      continue;
+    }
+    // l runs along the edge from a to b, r (if any) from b to a
+    const int32_t a = m.ev[(size_t)l * 3 + ql], b = m.ev[(size_t)l * 3 + (ql + 1) % 3];
+    for (int child = 1; child <= 2; ++child) {
+      const int32_t P = child == 1 ? std::min(a, b) : std::max(a, b);  // endpoint the half touches
+      const int cc = (c + 3 * child - 4) % 6 + 1;
+      const int64_t lc = first[l] + (P == a ? ql : (ql + 1) % 3);
+      if (r < 0) {
+        add(lc, -1, ql, -1, -1, cc);
+        continue;
+      }
+      const int64_t rc = first[r] + (P == b ? qr : (qr + 1) % 3);
+      if (Rl && Rr) add(lc, rc, ql, qr, -1, cc);
+      else if (Rl) add(lc, first[r], ql, qr, P == b ? 0 : 1, cc);
+      else add(rc, first[l], qr, ql, P == a ? 0 : 1, cc);
+    }
+  }
+  for (int64_t e = 0; e < ne0; ++e) {
+    if (!flag[e]) continue;
+    const int64_t n = first[e];
+    int c[3];
+    for (int k = 0; k < 3; ++k) c[k] = m.color[m.face_of[(size_t)e * 3 + k]];
+    add(n + 0, n + 3, 1, 2, -1, c[1]);  // m01-m20, parallel to parent edge 1
+    add(n + 1, n + 3, 2, 0, -1, c[2]);  // m12-m01, parallel to parent edge 2
+    add(n + 2, n + 3, 0, 1, -1, c[0]);  // m20-m12, parallel to parent edge 0
+  }
+  const int64_t ns = (int64_t)sl.size();
+  std::vector<int32_t> face_of((size_t)ne * 3, -1);
+  for (int64_t s = 0; s < ns; ++s) {
+    int32_t& fl = face_of[(size_t)sl[s] * 3 + sql[s]];
+    if (fl >= 0) throw Error{DGC_ERR_MESH, "refinement: local edge listed twice"};
+    fl = (int32_t)s;
+    if (sr[s] >= 0) {
+      int32_t& fr = face_of[(size_t)sr[s] * 3 + sqr[s]];
+      if (fr < 0) fr = (int32_t)s;
+      else if (half[s] < 0) throw Error{DGC_ERR_MESH, "refinement: local edge listed twice"};
+    }
+  }
+  for (int32_t f : face_of)
+    if (f < 0) throw Error{DGC_ERR_MESH, "refinement: element edge without a side"};
+
+  m.ne = ne;
+  m.nv = nv;
+  m.ns = ns;
+  m.X.swap(X);
+  m.ev.swap(ev);
+  m.sl.swap(sl);
+  m.sr.swap(sr);
+  m.sql.swap(sql);
+  m.sqr.swap(sqr);
+  m.shalf.swap(half);
+  m.color.swap(col);
+  m.face_of.swap(face_of);
+  m.detJ.assign(ne, 0.0);
+  m.Jinv.assign((size_t)ne * 4, 0.0);
+  for (int64_t e = 0; e < ne; ++e) element_jacobian(m, e);
+  side_geometry(m);
+  m.refined = true;
+  m.ncolors = 6;
+  m.perfect = false;
+  reorder(m, true, true);
   m.dirty = true;
 }
 

@@ -39,6 +39,9 @@ SIGNATURES = {
     "dgc_color_edges_naive": (C.c_int, [_P, C.c_int, C.c_int, _I32P, _I64P]),
     "dgc_mesh_info": (C.c_int, [_P, _I64P]),
     "dgc_get_sides": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]),
+    "dgc_refine": (C.c_int, [_P, _I64, _I32P]),
+    "dgc_get_hanging": (C.c_int, [_P, C.POINTER(C.c_int8)]),
+    "dgc_get_elements": (C.c_int, [_P, _I32P, _DP]),
     "dgc_get_ordering": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), _I32P]),
     "dgc_vol_points": (C.c_int, [_P, _DP]),
     "dgc_project": (C.c_int, [_P, _DP, _DP]),
@@ -168,6 +171,26 @@ def dgc_get_sides(mesh):
     _check(lib().dgc_get_sides(mesh, *(x.ctypes.data_as(_I32P) for x in (l, r)),
                                *(x.ctypes.data_as(C.POINTER(C.c_int8)) for x in (ql, qr))))
     return l, r, ql, qr
+
+
+def dgc_refine(mesh, elems):
+    e = np.ascontiguousarray(np.asarray(elems, dtype=np.int32).ravel())
+    _check(lib().dgc_refine(mesh, len(e), e.ctypes.data_as(_I32P)))
+
+
+def dgc_get_hanging(mesh):
+    h = np.zeros(dgc_mesh_info(mesh)["ns"], np.int8)
+    _check(lib().dgc_get_hanging(mesh, h.ctypes.data_as(C.POINTER(C.c_int8))))
+    return h
+
+
+def dgc_get_elements(mesh):
+    info = dgc_mesh_info(mesh)
+    nvpe = info["dim"] + 1
+    ev = np.zeros((info["ne"], nvpe), np.int32)
+    X = np.zeros((info["ne"], nvpe, info["dim"]))
+    _check(lib().dgc_get_elements(mesh, ev.ctypes.data_as(_I32P), X.ctypes.data_as(_DP)))
+    return ev, X
 
 
 def dgc_get_ordering(mesh):
@@ -354,6 +377,10 @@ class Mesh:
         r = dgc_color_edges(self.h, seed, max_swaps)
         self.info = dgc_mesh_info(self.h)
         return r
+
+    def refine(self, elems):
+        dgc_refine(self.h, elems)
+        self.info = dgc_mesh_info(self.h)
 
     def state_shape(self):
         return (self.info["ne"], self.info["M"], self.info["np"])

@@ -279,6 +279,27 @@ def cube_tube_p2_64(n: int = 64) -> dict:
     return dict(mesh=periodic_cube_tet(n), p=2, beta=5.0, xc=0.5, yc=0.5, cfl=0.3)
 
 
+def elements_near(mi: MeshInput, center, radius: float) -> np.ndarray:
+    """Ids of the elements whose centroid lies within ``radius`` of ``center``
+    (centroids of the element's vertices unwrapped next to its first vertex)."""
+    X = mi.xyz[mi.ev]  # [E][nvpe][dim]
+    if mi.periodic_len is not None:
+        L = np.asarray(mi.periodic_len)
+        X = X - L * np.round((X - X[:, :1, :]) / L)
+    cen = X.mean(axis=1)
+    d = cen - np.asarray(center, dtype=np.float64)
+    return np.nonzero((d * d).sum(axis=1) < radius * radius)[0].astype(np.int32)
+
+
+def refined_square_vortex_p2_256(n: int = 256, radius: float = 0.2) -> dict:
+    """Nonconforming workload: the periodic n x n x 2 triangle mesh, every
+    element whose centroid lies within ``radius`` of the vortex centre split
+    once into four (Sec. 3.2); p = 2, vortex strength 5, CFL 0.3."""
+    mi = periodic_square_tri(n)
+    return dict(mesh=mi, refine=elements_near(mi, (0.5, 0.5), radius), p=2, beta=5.0,
+                xc=0.5, yc=0.5, cfl=0.3, steps=200)
+
+
 def batched_square_meshes(count: int = 64, seed: int = 5, e_min: float = 1e3,
                           e_max: float = 2e5) -> list[dict]:
     """Independent periodic square meshes of uneven size and order.
