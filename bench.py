@@ -97,26 +97,34 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, mixed: bool, stage_frac_u0: float,
-                rec: int = 0) -> float:
+def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, form: str, rec: int = 0) -> float:
     """Algorithmic DRAM bytes of one launch (one call for the two-pass CFL) of a
-    kernel class; each element is touched once per color on a closed conforming
-    mesh.  rec = bytes of the FP32 record of an element (mixed precision)."""
-    s_in = rec if mixed else 8 * NV      # state read for traces
-    s_rhs = (4 if mixed else 8) * NV     # rhs element block
+    kernel class, averaged over the three RK stages; each element is touched once
+    per color on a closed conforming mesh.  form: "fp64", or "mixed" / "kahan"
+    (the FP32 forms, increment form of the step); rec = bytes of an element's FP32
+    record.  Per element, FP32 forms, last color: stage 0 reads the record and
+    the partial rhs and writes the increment and the stage record (2 rec + 8 NV);
+    stage 1 also reads rec0 and the increment (3 rec + 12 NV); stage 2 reads the
+    record, rhs, increment and the state, writes the state (rec + 24 NV): on
+    average (6 rec + 44 NV) / 3.  (The Kahan pair state of a triangle has the FP64
+    state's size.)"""
+    f32 = form != "fp64"
+    s_in = rec if f32 else 8 * NV      # state read for traces
+    s_rhs = (4 if f32 else 8) * NV     # rhs element block
     edge = 16 + 16 * (2 if dim == 2 else 3)
     if cls == "first":
         return E * (s_in + 8 * dim * dim + s_rhs) + nedges * edge
     if cls == "color":
         return E * (s_in + 2 * s_rhs) + nedges * edge
     if cls == "last":
-        return E * (8 * NV + s_rhs + 8 * NV * stage_frac_u0 + 8 * NV + (rec if mixed else 0)) + nedges * edge
+        per = (6 * rec + 44 * NV) / 3 if f32 else 8 * NV * (3 + 2.0 / 3.0)
+        return E * per + nedges * edge
     if cls == "cfl":
-        return E * (8 * NV + 8 + 4 + (rec if mixed else 0))
+        return E * ((rec + 12) if form == "kahan" else (8 * NV + 12 + (rec if f32 else 0)))
     if cls == "volume":
         return E * (s_in + 8 * dim * dim + s_rhs)
     if cls == "stage":
-        return E * (8 * NV * 2 + s_rhs + 8 * NV + (rec if mixed else 0))
+        return E * ((4 * rec + 44 * NV) / 3 if f32 else 8 * NV * (3 + 2.0 / 3.0))
     return float("nan")
 
 
@@ -217,7 +225,7 @@ def run_dgc(args, rank, world, local_rank):
             ne_ = sum(per_color[1:-1]) / max(1, ncolors - 2)
         else:
             ne_ = 0
-        b = class_bytes(cls, E, ne_, NV, 2, True, 2.0 / 3.0, rec=4 * info["M"] * (info["np"] + 1))
+        b = class_bytes(cls, E, ne_, NV, 2, "mixed", rec=4 * info["M"] * (info["np"] + 1))
         avg = tms / n
         kernels[cls] = {"launches": nl, "calls": n, "avg_ms": round(avg, 5), "share": round(tms / (ms * args.steps), 4),
                         "alg_bytes": int(b), "alg_gbs": round(b / (avg * 1e-3) / 1e9, 1),
@@ -242,6 +250,16 @@ def run_dgc(args, rank, world, local_rank):
                                "roofline": {"bound": "alu", "achieved": round(fl / (ms64 * 1e-3) / 1e12, 3),
                                             "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
                                             "frac": round(fl / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)}}
+        # ---- Kahan form: FP32 pair state, compensated update --------------------------
+        kst = torch.empty(dgc.dgc_state_bytes(mesh.h, dgc.DGC_FP32_KAHAN) // 4, dtype=torch.float32, device=dev)
+        wsk = torch.empty(dgc.dgc_workspace_size(mesh.h, dgc.DGC_FP32_KAHAN) // 8 + 64, dtype=torch.float64,
+                          device=dev)
+        dgc.dgc_import_state_prec(mesh.h, dgc.DGC_FP32_KAHAN, c_host, kst)
+        stepk = lambda: dgc.dgc_rk_step(mesh.h, dgc.DGC_FP32_KAHAN, kst, cfg["cfl"], dt, wsk)
+        stepk()
+        msk = time_steps(torch, stepk, max(3, args.steps), stream)
+        variants["rk_fp32kahan"] = {"value": 3 * dofs / (msk * 1e-3), "ms_per_step": round(msk, 4)}
+        del wsk
         # ---- right-hand side alone: colored vs atomicAdd vs two-pass buffer ----------
         r = torch.empty_like(c)
         nbuf = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
@@ -268,6 +286,7 @@ def run_dgc(args, rank, world, local_rank):
         variants["two_pass_buffer_bytes"] = nbuf
         del buf, r
         variants.update(run_batched(dgc, torch, dev, stream, args))
+        variants.update(run_other_meshes(dgc, torch, dev, stream, args))
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
     e2e = None
@@ -343,6 +362,65 @@ def run_batched(dgc, torch, dev, stream, args):
         dgc.dgc_batch_destroy(batch)
         for m in meshes:
             m.close()
+    return out
+
+
+def run_other_meshes(dgc, torch, dev, stream, args):
+    """The other two workloads, each an RK step in FP64 and in mixed precision,
+    and its right-hand side colored / atomicAdd / two-pass:
+    1,572,864 periodic Kuhn tetrahedra at p = 2 (4 face colors; seeded random
+    state), and
+    the 256 x 256 x 2 periodic triangle mesh refined once within radius 0.2 of the
+    centre (180,512 elements, hanging edges, 6 colors) at p = 2."""
+    out = {}
+    tube = W.cube_tube_p2_64()
+    ref = W.refined_square_vortex_p2_256()
+    for tag, mi, p, refine in (("tet_p2_64cube", tube["mesh"], tube["p"], None),
+                               ("nonconforming_p2_256", ref["mesh"], ref["p"], ref["refine"])):
+        t0 = time.perf_counter()
+        m = dgc.Mesh.from_input(mi, p)
+        m.color(1601)
+        if refine is not None:
+            m.refine(refine)
+        prep_s = time.perf_counter() - t0
+        info = m.info
+        if mi.dim == 3:
+            # seeded mean state + perturbed modes (projecting the tube at 100M
+            # volume points costs minutes of host time; the kernels' work does not
+            # depend on the field)
+            c_host = W.random_state(info["ne"], 5, info["np"], seed=7, amp=3e-3, mean=(0.7, 0.1, -0.05, 0.03, 1.8))
+        else:
+            xyz = dgc.dgc_vol_points(m.h)
+            c_host = dgc.dgc_project(m.h, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=5.0))
+        dofs = info["ne"] * info["M"] * info["np"]
+        c = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+        r = torch.empty_like(c)
+        dt = torch.zeros(1, dtype=torch.float64, device=dev)
+        entry = {"elements": info["ne"], "faces": info["ns"], "p": p, "dofs": dofs, "colors": info["ncolors"],
+                 "host_mesh_color_s": round(prep_s, 2)}
+        for prec, name in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
+            ws = torch.empty(dgc.dgc_workspace_size(m.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
+            dgc.dgc_import_state(m.h, c_host, c)
+            fn = lambda: dgc.dgc_rk_step(m.h, prec, c, 0.3, dt, ws)
+            fn()
+            k = max(3, args.steps // (1 if prec == dgc.DGC_FP32_MIXED else 5))
+            ms = time_steps(torch, fn, k, stream)
+            entry[f"rk_{name}"] = {"value": 3 * dofs / (ms * 1e-3), "ms_per_step": round(ms, 4),
+                                   "launches_per_step": dgc.dgc_last_launch_count(m.h)}
+            del ws
+            nbuf = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
+            buf = torch.empty(nbuf // 8, dtype=torch.float64, device=dev)
+            dgc.dgc_import_state(m.h, c_host, c)
+            for kind, call in (("colored", lambda: dgc.dgc_rhs(m.h, prec, c, r)),
+                               ("atomic", lambda: dgc.dgc_rhs_atomic(m.h, prec, c, r)),
+                               ("two_pass", lambda: dgc.dgc_rhs_two_pass(m.h, prec, c, r, buf))):
+                call()
+                t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
+                entry[f"rhs_{kind}_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+            del buf
+        out[tag] = entry
+        del c, r
+        m.close()
     return out
 
 

@@ -52,10 +52,19 @@ typedef enum {
   DGC_ERR_NONFINITE = 7       /* non-finite or non-physical state detected */
 } dgc_status;
 
+/* Precision forms.  The two FP32 forms evaluate the flux, quadrature and projection of
+ * Eq. 2 in FP32 and keep geometry and the CFL reduction in FP64.  In both the
+ * SSP-RK3 stages are carried as FP32 increments delta_{s+1} = b_s (delta_s + dt L(u_s)),
+ * b = (1, 1/4, 2/3), around the state u0 at the start of the step, and the state is
+ * updated once per step, u = u0 + delta_3, at full precision:
+ *   DGC_FP32_MIXED: FP64 state [E][M][Np] (one FP64 FMA per value per step);
+ *   DGC_FP32_KAHAN: FP32 pair state (hi + lo per value), updated by Kahan's compensated
+ *     summation; no FP64 arithmetic but the CFL reduction.  Triangles.  Its device layout
+ *     (dgc_state_bytes) is written and read by dgc_import_state_prec / _export_. */
 typedef enum {
-  DGC_FP64 = 0,       /* all arithmetic in FP64 */
-  DGC_FP32_MIXED = 1  /* flux, quadrature and projection in FP32; state, stage update,
-                         geometry and CFL reduction in FP64 */
+  DGC_FP64 = 0,        /* all arithmetic in FP64, Eq. 2 as written, FP64 stage update */
+  DGC_FP32_MIXED = 1,  /* FP32 flux with an FP64 state */
+  DGC_FP32_KAHAN = 2   /* FP32 flux with a compensated FP32 pair state */
 } dgc_prec;
 
 /* Options (dgc_set_option). */
@@ -188,11 +197,22 @@ dgc_status dgc_workspace_size(const dgc_mesh* mesh, dgc_prec prec, int64_t* byte
 dgc_status dgc_import_state(dgc_mesh* mesh, const double* c_host, double* c_dev, void* stream);
 dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host, void* stream);
 
-/* Right-hand side of Eq. 2: rhs_dev = dc/dt at state c_dev (both FP64, [E][M][Np],
- * internal order, device).  Volume integral plus the per-color surface integral of
- * Algorithm 1 with the local Lax-Friedrichs flux.  prec selects the arithmetic.
- * Requires a colored mesh (DGC_ERR_ARG otherwise).  c_dev and rhs_dev must not alias. */
-dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev,
+/* The same for the device state of a precision form: DGC_FP64 and DGC_FP32_MIXED are the
+ * FP64 state above; DGC_FP32_KAHAN converts to and from its FP32 pair layout (per element:
+ * hi and lo of the mean phi0 c0, hi of the modes j >= 1, then lo of those modes; the host
+ * side stays [E][M][Np] FP64).  dgc_state_bytes gives the device bytes of either. */
+dgc_status dgc_state_bytes(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes);
+dgc_status dgc_import_state_prec(dgc_mesh* mesh, dgc_prec prec, const double* c_host, void* c_dev,
+                                 void* stream);
+dgc_status dgc_export_state_prec(dgc_mesh* mesh, dgc_prec prec, const void* c_dev, double* c_host,
+                                 void* stream);
+
+/* Right-hand side of Eq. 2: rhs_dev = dc/dt at state c_dev (FP64 rhs [E][M][Np],
+ * internal order, device; c_dev in the layout of prec: FP64, or the Kahan pair state).
+ * Volume integral plus the per-color surface integral of Algorithm 1 with the local
+ * Lax-Friedrichs flux.  prec selects the arithmetic.  Requires a colored mesh
+ * (DGC_ERR_ARG otherwise).  c_dev and rhs_dev must not alias. */
+dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const void* c_dev, double* rhs_dev,
                    void* stream);
 
 /* CFL time step, FP64, on the device:
@@ -206,7 +226,7 @@ dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl, double* d
  * holds workspace_bytes bytes; DGC_ERR_ARG if that is less than dgc_workspace_size() for
  * prec.  No allocation and no host synchronisation after the first device call on the
  * mesh. */
-dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl,
+dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl,
                        double* dt_dev, void* workspace_dev, int64_t workspace_bytes,
                        void* stream);
 
@@ -288,7 +308,7 @@ const char* dgc_last_error(void);
  *   the array: serialise them.  The first call on each device looks up the array's device
  *   address (a CUDA runtime query); make that first call before any stream capture.
  *   Every GPU that loads the library holds the 16 MiB until the process exits. */
-dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl,
+dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl,
                               double* dt_dev, void* stream);
 
 /* Free the mesh and its device copies (the device must still be current). */

@@ -54,6 +54,8 @@ void require(bool ok, const char* msg, dgc_status code = DGC_ERR_ARG) {
 int64_t nv_of(const Mesh& m) { return (int64_t)m.M * m.np; }
 // floats per element of the FP32 record the mixed-precision step keeps
 int64_t record_floats(const Mesh& m) { return m.dim == 2 ? tri_record_floats(m.p) : tet_record_floats(m.p); }
+// floats per element of the FP32 pair state of the Kahan form (triangles)
+int64_t kahan_floats(const Mesh& m) { return tri_kahan_floats(m.p); }
 int64_t state_bytes(const Mesh& m) { return m.ne * nv_of(m) * (int64_t)sizeof(double); }
 int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 
@@ -253,12 +255,14 @@ void check_ptr(const void* p, const char* what) {
   if (reinterpret_cast<uintptr_t>(p) % 16) throw Error{DGC_ERR_ARG, std::string("misaligned device pointer: ") + what};
 }
 
-int vol(const Ctx& x, TypeCfg ty, const void* s, void* r) {
-  return x.dim == 2 ? tri_volume(x, ty, s, r) : tet_volume(x, ty, s, r);
+// ss: floats per element of an FP32 state (record or Kahan state), 0 for FP64 states
+int vol(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r) {
+  return x.dim == 2 ? tri_volume(x, ty, s, ss, r) : tet_volume(x, ty, s, ss, r);
 }
-int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, void* r, void* buf,
+int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, int ss, void* r, void* buf,
          const StageArgs* sa) {
-  return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, r, buf, sa) : tet_surface(x, ty, mode, b, e, s, r, buf, sa);
+  return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, ss, r, buf, sa)
+                    : tet_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
 }
 int cfl(const Ctx& x, const double* s, double c, double* dt, float* sh) {
   return x.dim == 2 ? tri_cfl(x, s, c, dt, sh) : tet_cfl(x, s, c, dt, sh);
@@ -322,19 +326,125 @@ void finish(Mesh& m, int64_t launches) {
 // rhs = L(state): Algorithm 1 (volume, then the colors in order, a kernel
 // boundary between colors); with fusion on closed conforming meshes the
 // first color also evaluates the volume integral and stores, no pre-zeroing.
-int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, void* rhs) {
+int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss, void* rhs) {
   int64_t n = 0;
   const std::vector<int32_t>& off = m.color_off;
   if (m.fuse && m.perfect) {
-    run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], state, rhs, nullptr, nullptr); });
+    run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], state, ss, rhs, nullptr, nullptr); });
     for (int c = 2; c <= m.ncolors; ++c)
-      run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, rhs, nullptr, nullptr); });
+      run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, ss, rhs, nullptr, nullptr); });
   } else {
-    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, state, rhs); });
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, state, ss, rhs); });
     for (int c = 1; c <= m.ncolors; ++c)
-      run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, rhs, nullptr, nullptr); });
+      run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, ss, rhs, nullptr, nullptr); });
   }
   return n;
+}
+
+// Workspace of one RK step, each part 256-byte aligned (S = FP64 state bytes,
+// R = FP32 record bytes):
+//   FP64:         u1 [S] (stage state), rhs [S]
+//   FP32 mixed:   rec0 [R] (record of u0), recs [R] (record of the stage state),
+//                 delta [S/2] (stage increment), rhs [S/2]
+//   FP32 Kahan:   recs [R], delta [S/2], rhs [S/2]  (the state's first part is u0's record)
+struct Workspace {
+  double* u1 = nullptr;
+  float *rec0 = nullptr, *recs = nullptr, *delta = nullptr;
+  void* rhs = nullptr;
+  int64_t bytes = 0;
+};
+
+Workspace carve(const Mesh& m, dgc_prec prec, char* base) {
+  Workspace w;
+  const int64_t S = state_bytes(m), R = align256(m.ne * record_floats(m) * 4);
+  int64_t o = 0;
+  auto take = [&](int64_t b) {
+    char* p = base ? base + o : nullptr;
+    o += align256(b);
+    return p;
+  };
+  if (prec == DGC_FP64) {
+    w.u1 = reinterpret_cast<double*>(take(S));
+    w.rhs = take(S);
+  } else {
+    if (prec == DGC_FP32_MIXED) w.rec0 = reinterpret_cast<float*>(take(R));
+    w.recs = reinterpret_cast<float*>(take(R));
+    w.delta = reinterpret_cast<float*>(take(S / 2));
+    w.rhs = take(S / 2);
+  }
+  w.bytes = o;
+  return w;
+}
+
+// One SSP-RK3 step.  Per stage: FIRST + COLOR... + LAST (volume integral fused
+// into the first color, stage update into the last) on meshes where every
+// element has one edge of each color, else VOLUME + every color + STAGE.
+// launch(cls, f) issues the kernels of f() and counts them.
+template <typename Launch>
+void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cfl_, double* dt, const Workspace& w,
+                  Launch&& launch) {
+  const std::vector<int32_t>& off = m.color_off;
+  const int C = m.ncolors;
+  const bool fused = m.fuse && m.perfect && C >= 2;
+  if (prec == DGC_FP64) {
+    double* c64 = static_cast<double*>(c);
+    launch(DGC_K_CFL, [&] { return cfl(x, c64, cfl_, dt, nullptr); });
+    const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int s = 0; s < 3; ++s) {
+      double* us = s == 0 ? c64 : w.u1;
+      StageArgs sa;
+      sa.u0 = c64;
+      sa.uout = s == 2 ? c64 : w.u1;
+      sa.dt = dt;
+      sa.a0 = A0[s];
+      sa.b0 = B0[s];
+      if (fused) {
+        launch(DGC_K_FIRST, [&] { return surf(x, TY_D, SURF_FIRST, off[0], off[1], us, 0, w.rhs, nullptr, nullptr); });
+        for (int k = 2; k < C; ++k)
+          launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
+        launch(DGC_K_LAST, [&] { return surf(x, TY_D, SURF_LAST, off[C - 1], off[C], us, 0, w.rhs, nullptr, &sa); });
+      } else {
+        launch(DGC_K_VOLUME, [&] { return vol(x, TY_D, us, 0, w.rhs); });
+        for (int k = 1; k <= C; ++k)
+          launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
+        launch(DGC_K_STAGE, [&] { return stage_update(x, false, us, w.rhs, sa); });
+      }
+    }
+    return;
+  }
+  // FP32 forms, increment form of the step (incr_form.cuh)
+  const bool kahan = prec == DGC_FP32_KAHAN;
+  float* ks = kahan ? static_cast<float*>(c) : nullptr;
+  const int nf = (int)record_floats(m), kf = kahan ? (int)kahan_floats(m) : 0;
+  const float* rec0 = kahan ? ks : w.rec0;
+  const int rec0_stride = kahan ? kf : nf;
+  if (kahan) launch(DGC_K_CFL, [&] { return tri_cfl_kahan(x, ks, cfl_, dt); });
+  else launch(DGC_K_CFL, [&] { return cfl(x, static_cast<double*>(c), cfl_, dt, w.rec0); });
+  for (int s = 0; s < 3; ++s) {
+    const float* in = s == 0 ? rec0 : w.recs;
+    const int ss = s == 0 ? rec0_stride : nf;
+    StageArgs sa;
+    sa.u0 = kahan ? nullptr : static_cast<double*>(c);
+    sa.uout = kahan ? nullptr : static_cast<double*>(c);
+    sa.dt = dt;
+    sa.stage = s;
+    sa.rec0 = rec0;
+    sa.rec0_stride = rec0_stride;
+    sa.rec_out = w.recs;
+    sa.delta = w.delta;
+    sa.kstate = ks;
+    if (fused) {
+      launch(DGC_K_FIRST, [&] { return surf(x, TY_MF, SURF_FIRST, off[0], off[1], in, ss, w.rhs, nullptr, nullptr); });
+      for (int k = 2; k < C; ++k)
+        launch(DGC_K_COLOR, [&] { return surf(x, TY_MF, SURF_RMW, off[k - 1], off[k], in, ss, w.rhs, nullptr, nullptr); });
+      launch(DGC_K_LAST, [&] { return surf(x, TY_MF, SURF_LAST, off[C - 1], off[C], in, ss, w.rhs, nullptr, &sa); });
+    } else {
+      launch(DGC_K_VOLUME, [&] { return vol(x, TY_MF, in, ss, w.rhs); });
+      for (int k = 1; k <= C; ++k)
+        launch(DGC_K_COLOR, [&] { return surf(x, TY_MF, SURF_RMW, off[k - 1], off[k], in, ss, w.rhs, nullptr, nullptr); });
+      launch(DGC_K_STAGE, [&] { return incr_stage_update(x, static_cast<const float*>(w.rhs), sa); });
+    }
+  }
 }
 
 }  // namespace
@@ -502,18 +612,34 @@ dgc_status dgc_state_size(const dgc_mesh* mesh, int64_t* bytes) {
   });
 }
 
-// FP64: u1 [S], rhs [S].  Mixed: u1 [S], FP32 record [E * rec floats], FP32 rhs [S/2].
-static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) {
-  int64_t S = state_bytes(m);
-  return prec == DGC_FP64 ? 2 * align256(S) : align256(S) + align256(m.ne * record_floats(m) * 4) + align256(S / 2);
+static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) { return carve(m, prec, nullptr).bytes; }
+
+static void require_prec(const Mesh& m, dgc_prec prec) {
+  require(prec == DGC_FP64 || prec == DGC_FP32_MIXED || prec == DGC_FP32_KAHAN, "unknown precision");
+  require(prec != DGC_FP32_KAHAN || m.dim == 2, "the Kahan form is implemented for triangle meshes",
+          DGC_ERR_UNSUPPORTED);
+}
+
+// bytes of one device state of the given precision form
+static int64_t state_bytes_prec(const Mesh& m, dgc_prec prec) {
+  return prec == DGC_FP32_KAHAN ? m.ne * kahan_floats(m) * (int64_t)sizeof(float) : state_bytes(m);
 }
 
 dgc_status dgc_workspace_size(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes) {
   return guarded([&] {
     const Mesh& m = checked(mesh);
     require(bytes != nullptr, "null output");
-    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    require_prec(m, prec);
     *bytes = workspace_bytes(m, prec);
+  });
+}
+
+dgc_status dgc_state_bytes(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(bytes != nullptr, "null output");
+    require_prec(m, prec);
+    *bytes = state_bytes_prec(m, prec);
   });
 }
 
@@ -555,15 +681,88 @@ dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host,
   });
 }
 
-dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev, void* stream) {
+// Kahan pair state of one element from its FP64 coefficients [M][Np]: the
+// record (hi, lo of the mean phi0 c0; hi of the modes j >= 1), then lo of the
+// modes; the inverse on export.
+static void kahan_pack(const Mesh& m, const double* c, float* k) {
+  const int M = m.M, np = m.np, nf = (int)record_floats(m), kf = (int)kahan_floats(m);
+  const double phi0 = m.tab.phiV[0];
+  std::fill(k, k + kf, 0.0f);
+  for (int a = 0; a < M; ++a) {
+    const double u = phi0 * c[a * np];
+    const float hi = (float)u;
+    k[a] = hi;
+    k[M + a] = (float)(u - (double)hi);
+    for (int j = 1; j < np; ++j) {
+      const double v = c[a * np + j];
+      const float h = (float)v;
+      k[2 * M + a * (np - 1) + j - 1] = h;
+      k[nf + a * (np - 1) + j - 1] = (float)(v - (double)h);
+    }
+  }
+}
+static void kahan_unpack(const Mesh& m, const float* k, double* c) {
+  const int M = m.M, np = m.np, nf = (int)record_floats(m);
+  const double phi0 = m.tab.phiV[0];
+  for (int a = 0; a < M; ++a) {
+    c[a * np] = ((double)k[a] + (double)k[M + a]) / phi0;
+    for (int j = 1; j < np; ++j)
+      c[a * np + j] = (double)k[2 * M + a * (np - 1) + j - 1] + (double)k[nf + a * (np - 1) + j - 1];
+  }
+}
+
+dgc_status dgc_import_state_prec(dgc_mesh* mesh, dgc_prec prec, const double* c_host, void* c_dev, void* stream) {
+  if (prec != DGC_FP32_KAHAN) return dgc_import_state(mesh, c_host, static_cast<double*>(c_dev), stream);
   return guarded([&] {
     Mesh& m = checked(mesh);
-    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    require_prec(m, prec);
+    require(c_host != nullptr, "null host state");
+    check_ptr(c_dev, "c_dev");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    upload(m);
+    float* stg = reinterpret_cast<float*>(staging_for(m));
+    const int64_t nv = nv_of(m), kf = kahan_floats(m);
+    const int32_t* en = m.elem_new_of_old.data();
+    parallel_for(m.ne, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i) kahan_pack(m, c_host + i * nv, stg + (int64_t)en[i] * kf);
+    });
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DGC_CUDA(cudaMemcpyAsync(c_dev, stg, state_bytes_prec(m, prec), cudaMemcpyHostToDevice, st));
+    DGC_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+dgc_status dgc_export_state_prec(dgc_mesh* mesh, dgc_prec prec, const void* c_dev, double* c_host, void* stream) {
+  if (prec != DGC_FP32_KAHAN) return dgc_export_state(mesh, static_cast<const double*>(c_dev), c_host, stream);
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require_prec(m, prec);
+    require(c_host != nullptr, "null host state");
+    check_ptr(c_dev, "c_dev");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    upload(m);
+    float* stg = reinterpret_cast<float*>(staging_for(m));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DGC_CUDA(cudaMemcpyAsync(stg, c_dev, state_bytes_prec(m, prec), cudaMemcpyDeviceToHost, st));
+    DGC_CUDA(cudaStreamSynchronize(st));
+    const int64_t nv = nv_of(m), kf = kahan_floats(m);
+    const int32_t* en = m.elem_new_of_old.data();
+    parallel_for(m.ne, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i) kahan_unpack(m, stg + (int64_t)en[i] * kf, c_host + i * nv);
+    });
+  });
+}
+
+dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const void* c_dev, double* rhs_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require_prec(m, prec);
     check_ptr(c_dev, "c_dev");
     check_ptr(rhs_dev, "rhs_dev");
     require(c_dev != rhs_dev, "c_dev and rhs_dev must not alias");
     Ctx x = ready(m, stream);
-    finish(m, launch_rhs(m, x, prec == DGC_FP64 ? TY_D : TY_MD, c_dev, rhs_dev));
+    if (prec == DGC_FP32_KAHAN) finish(m, launch_rhs(m, x, TY_KD, c_dev, (int)kahan_floats(m), rhs_dev));
+    else finish(m, launch_rhs(m, x, prec == DGC_FP64 ? TY_D : TY_MD, c_dev, 0, rhs_dev));
   });
 }
 
@@ -581,11 +780,11 @@ dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl_, double* 
   });
 }
 
-dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_, double* dt_dev,
+dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_, double* dt_dev,
                        void* workspace_dev, int64_t workspace_size, void* stream) {
   return guarded([&] {
     Mesh& m = checked(mesh);
-    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    require_prec(m, prec);
     check_ptr(c_dev, "c_dev");
     require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
     require(workspace_dev != nullptr && reinterpret_cast<uintptr_t>(workspace_dev) % 256 == 0,
@@ -593,44 +792,10 @@ dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_
     require(cfl_ > 0.0, "cfl must be positive");
     require(workspace_size >= workspace_bytes(m, prec), "workspace smaller than dgc_workspace_size()");
     Ctx x = ready(m, stream);
-    const bool mixed = prec == DGC_FP32_MIXED;
-    const int64_t S = state_bytes(m);
-    char* ws = static_cast<char*>(workspace_dev);
-    double* u1 = reinterpret_cast<double*>(ws);
-    const int64_t R = align256(m.ne * record_floats(m) * 4);
-    float* shadow = mixed ? reinterpret_cast<float*>(ws + align256(S)) : nullptr;
-    void* rhs = mixed ? (void*)(ws + align256(S) + R) : (void*)(ws + align256(S));
+    const Workspace w = carve(m, prec, static_cast<char*>(workspace_dev));
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
-    run(m, x, DGC_K_CFL, n, [&] { return cfl(x, c_dev, cfl_, dt_dev, shadow); });
-    const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
-    const std::vector<int32_t>& off = m.color_off;
-    const int C = m.ncolors;
-    const TypeCfg ty = mixed ? TY_MF : TY_D;
-    for (int s = 0; s < 3; ++s) {
-      double* us = s == 0 ? c_dev : u1;
-      StageArgs sa;
-      sa.u0 = c_dev;
-      sa.uout = s == 2 ? c_dev : u1;
-      sa.shadow = shadow;
-      sa.dt = dt_dev;
-      sa.a0 = A0[s];
-      sa.b0 = B0[s];
-      const void* st_in = mixed ? (const void*)shadow : (const void*)us;
-      if (m.fuse && m.perfect && C >= 2) {
-        run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], st_in, rhs, nullptr, nullptr); });
-        for (int c = 2; c < C; ++c)
-          run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr); });
-        run(m, x, DGC_K_LAST, n, [&] {
-          return surf(x, mixed ? TY_MLAST : TY_D, SURF_LAST, off[C - 1], off[C], us, rhs, nullptr, &sa);
-        });
-      } else {
-        run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, st_in, rhs); });
-        for (int c = 1; c <= C; ++c)
-          run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr); });
-        run(m, x, DGC_K_STAGE, n, [&] { return stage_update(x, mixed, us, rhs, sa); });
-      }
-    }
+    rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int cls, auto&& f) { run(m, x, cls, n, f); });
     finish(m, n);
   });
 }
@@ -644,8 +809,8 @@ dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, do
     Ctx x = ready(m, stream);
     const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
     int64_t n = 0;
-    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, rhs_dev); });
-    run(m, x, DGC_K_ATOMIC, n, [&] { return surf(x, ty, SURF_ATOMIC, 0, m.ns, c_dev, rhs_dev, nullptr, nullptr); });
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, 0, rhs_dev); });
+    run(m, x, DGC_K_ATOMIC, n, [&] { return surf(x, ty, SURF_ATOMIC, 0, m.ns, c_dev, 0, rhs_dev, nullptr, nullptr); });
     finish(m, n);
   });
 }
@@ -669,8 +834,8 @@ dgc_status dgc_rhs_two_pass(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, 
     Ctx x = ready(m, stream);
     const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
     int64_t n = 0;
-    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, rhs_dev); });
-    run(m, x, DGC_K_BUFFER, n, [&] { return surf(x, ty, SURF_BUFFER, 0, m.ns, c_dev, rhs_dev, buffer_dev, nullptr); });
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, 0, rhs_dev); });
+    run(m, x, DGC_K_BUFFER, n, [&] { return surf(x, ty, SURF_BUFFER, 0, m.ns, c_dev, 0, rhs_dev, buffer_dev, nullptr); });
     run(m, x, DGC_K_GATHER, n, [&] { return gather_two_pass(x, false, rhs_dev, buffer_dev); });
     finish(m, n);
   });
@@ -769,11 +934,11 @@ void* static_scratch(int dev) {
 
 }  // namespace
 
-extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, double* c_dev, double cfl_,
+extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_,
                                          double* dt_dev, void* stream) {
   return guarded([&] {
     Mesh& m = checked(mesh);
-    require(prec == DGC_FP64 || prec == DGC_FP32_MIXED, "unknown precision");
+    require_prec(m, prec);
     check_ptr(c_dev, "c_dev");
     require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
     require(cfl_ > 0.0, "cfl must be positive");
@@ -807,39 +972,10 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, double* 
     x.shadow.rec = (int)record_floats(m);
     x.shadow.split = true;
     x.shadow.phi0 = m.tab.phiV[0];
-    const bool mixed = prec == DGC_FP32_MIXED;
-    const int64_t S = state_bytes(m);
-    double* u1 = reinterpret_cast<double*>(base);
-    const int64_t R = align256(m.ne * record_floats(m) * 4);
-    float* shadow = mixed ? reinterpret_cast<float*>(base + align256(S)) : nullptr;
-    void* rhs = mixed ? (void*)(base + align256(S) + R) : (void*)(base + align256(S));
+    const Workspace w = carve(m, prec, base);
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
-    count(m, n, cfl(x, c_dev, cfl_, dt_dev, shadow));
-    const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
-    const std::vector<int32_t>& off = m.color_off;
-    const int C = m.ncolors;
-    const TypeCfg ty = mixed ? TY_MF : TY_D;
-    for (int s = 0; s < 3; ++s) {
-      double* us = s == 0 ? c_dev : u1;
-      StageArgs sa;
-      sa.u0 = c_dev;
-      sa.uout = s == 2 ? c_dev : u1;
-      sa.shadow = shadow;
-      sa.dt = dt_dev;
-      sa.a0 = A0[s];
-      sa.b0 = B0[s];
-      const void* st_in = mixed ? (const void*)shadow : (const void*)us;
-      if (m.fuse && m.perfect && C >= 2) {
-        count(m, n, surf(x, ty, SURF_FIRST, off[0], off[1], st_in, rhs, nullptr, nullptr));
-        for (int c = 2; c < C; ++c) count(m, n, surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr));
-        count(m, n, surf(x, mixed ? TY_MLAST : TY_D, SURF_LAST, off[C - 1], off[C], us, rhs, nullptr, &sa));
-      } else {
-        count(m, n, vol(x, ty, st_in, rhs));
-        for (int c = 1; c <= C; ++c) count(m, n, surf(x, ty, SURF_RMW, off[c - 1], off[c], st_in, rhs, nullptr, nullptr));
-        count(m, n, stage_update(x, mixed, us, rhs, sa));
-      }
-    }
+    rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int, auto&& f) { count(m, n, f()); });
     finish(m, n);
   });
 }
@@ -898,13 +1034,12 @@ void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* d
   for (int i = 0; same && i < n; ++i) same = b.key_c[i] == c_devs[i];
   if (same) return;
   batch_release(b);
-  const bool mixed = prec == DGC_FP32_MIXED;
   std::vector<BatchMeshDev> hm(n);
   char* w = static_cast<char*>(ws);
   for (int i = 0; i < n; ++i) {
     Mesh& m = *b.meshes[i];
     upload(m);
-    const int64_t S = state_bytes(m), R = align256(m.ne * record_floats(m) * 4);
+    const Workspace part = carve(m, prec, w);
     BatchMeshDev& d = hm[i];
     d.p = m.p;
     d.ne = m.ne;
@@ -915,10 +1050,12 @@ void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* d
     d.est = m.dev->cfl_est;
     d.c = c_devs[i];
     d.dt = dt_devs + i;
-    d.u1 = reinterpret_cast<double*>(w);
-    d.rec = mixed ? reinterpret_cast<float*>(w + align256(S)) : nullptr;
-    d.rhs = mixed ? (void*)(w + align256(S) + R) : (void*)(w + align256(S));
-    w += workspace_bytes(m, prec);
+    d.u1 = part.u1;
+    d.rec0 = part.rec0;
+    d.recs = part.recs;
+    d.delta = part.delta;
+    d.rhs = part.rhs;
+    w += part.bytes;
   }
   // tiles: every color's edges, then the elements; heavier orders first
   std::vector<int> order(n);

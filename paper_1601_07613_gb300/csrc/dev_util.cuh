@@ -106,7 +106,11 @@ __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ float narrow(double x) { return d2f(x); }
 
 // block-wide minimum of non-negative values, combined into *out with one
-// atomicMin on the bit pattern (non-negative IEEE values order like their bits)
+// atomicMin on the bit pattern (non-negative IEEE values order like their bits).
+// The atomic is skipped when the block's minimum is not below the value read
+// from L2 first: *out only decreases, so a stale read is never too small, and
+// a skipped block could not have lowered it.  Most blocks skip, which keeps
+// thousands of same-address atomics from serialising at the end of the pass.
 __device__ __forceinline__ void block_min_to(double v, unsigned long long* out) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -116,7 +120,8 @@ __device__ __forceinline__ void block_min_to(double v, unsigned long long* out) 
   if (threadIdx.x == 0) {
     double b = wmin[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, wmin[w]);
-    atomicMin(out, (unsigned long long)__double_as_longlong(b));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(b);
+    if (bits < __ldcg(out)) atomicMin(out, bits);
   }
 }
 
@@ -129,7 +134,8 @@ __device__ __forceinline__ void block_min_to(float v, unsigned* out) {
   if (threadIdx.x == 0) {
     float b = wminf[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fminf(b, wminf[w]);
-    atomicMin(out, __float_as_uint(b));
+    const unsigned bits = __float_as_uint(b);
+    if (bits < __ldcg(out)) atomicMin(out, bits);
   }
 }
 

@@ -40,8 +40,8 @@ enum SurfMode {
 enum TypeCfg {
   TY_D = 0,     // FP64 state, FP64 arithmetic, FP64 rhs
   TY_MD = 1,    // FP64 state, FP32 arithmetic, FP64 rhs (dgc_rhs in mixed precision)
-  TY_MF = 2,    // FP32 shadow state, FP32 arithmetic, FP32 rhs (RK stages in mixed precision)
-  TY_MLAST = 3  // FP64 state, FP32 arithmetic, FP32 partial rhs (last color, mixed)
+  TY_MF = 2,    // FP32 record, FP32 arithmetic, FP32 rhs (RK stages of the FP32 forms)
+  TY_KD = 3     // FP32 record (Kahan state), FP32 arithmetic, FP64 rhs (dgc_rhs, Kahan form)
 };
 
 // FP32 record of the state kept by the mixed-precision step: rec floats per
@@ -64,11 +64,18 @@ struct Ctx {
 };
 
 struct StageArgs {
-  const double* u0 = nullptr;  // state at the start of the step
-  double* uout = nullptr;      // stage output (may alias the stage input)
-  float* shadow = nullptr;     // FP32 copy of the stage output (mixed precision) or null
+  // FP64 form: uout = a0 u0 + b0 (us + dt L(us))
+  const double* u0 = nullptr;  // FP64 state at the start of the step
+  double* uout = nullptr;      // FP64 stage output (may alias the stage input)
   const double* dt = nullptr;  // device time step
-  double a0 = 0.0, b0 = 1.0;   // uout = a0 u0 + b0 (us + dt L(us))
+  double a0 = 0.0, b0 = 1.0;
+  // FP32 forms, increment form of the step (incr_form.cuh)
+  int stage = 0;                // 0, 1, 2
+  const float* rec0 = nullptr;  // FP32 record of u0 (the Kahan state itself in the Kahan form)
+  int rec0_stride = 0;          // floats per element of rec0
+  float* rec_out = nullptr;     // FP32 record of the next stage's state (stages 0, 1)
+  float* delta = nullptr;       // [E][M*Np] stage increment
+  float* kstate = nullptr;      // Kahan form: the FP32 pair state (stride rec0_stride); else null
 };
 
 // One mesh of a batch, as the batched kernels see it (device array).
@@ -81,8 +88,10 @@ struct BatchMeshDev {
   const double* inr = nullptr;
   float* est = nullptr;   // CFL estimates [ne], minimum at [ne]
   double* c = nullptr;    // state (caller's)
-  double* u1 = nullptr;   // stage state (workspace)
-  float* rec = nullptr;   // FP32 record (workspace, mixed precision)
+  double* u1 = nullptr;   // FP64 stage state (workspace, FP64 form)
+  float* rec0 = nullptr;  // FP32 record of u0 (workspace, mixed precision)
+  float* recs = nullptr;  // FP32 record of the stage state (workspace, mixed precision)
+  float* delta = nullptr; // FP32 stage increment (workspace, mixed precision)
   void* rhs = nullptr;    // rhs (workspace)
   double* dt = nullptr;   // this mesh's time step (caller's)
 };
@@ -100,21 +109,25 @@ int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, in
 int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage, double a0,
                double b0, SurfMode mode, bool mixed, int threads);
 int tri_record_floats(int p);
-int tri_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
+// sstride: floats per element of an FP32 state (record or Kahan state); ignored for FP64 states
+int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs);
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
-                void* rhs, void* buf, const StageArgs* sa);
+                int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
+int tri_kahan_floats(int p);
+int tri_cfl_kahan(const Ctx& c, const float* kstate, double cfl, double* dt);
 
 // kernels_tet.cu
 void tet_upload_tables(int p, const RefTables& T, DeviceMesh& d);
 int tet_record_floats(int p);
-int tet_volume(const Ctx& c, TypeCfg ty, const void* state, void* rhs);
+int tet_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs);
 int tet_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
-                void* rhs, void* buf, const StageArgs* sa);
+                int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tet_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
 
 // kernels_common.cu
 int stage_update(const Ctx& c, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa);
+int incr_stage_update(const Ctx& c, const float* rhs, const StageArgs& sa);
 int gather_two_pass(const Ctx& c, bool f32, void* rhs, const void* buf);
 
 }  // namespace dgc

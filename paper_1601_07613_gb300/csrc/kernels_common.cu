@@ -3,47 +3,69 @@
 // the per-edge-buffer comparator.
 #include "dev_util.cuh"
 #include "device.cuh"
+#include "incr_form.cuh"
 
 namespace dgc {
 
-// uout = a0 u0 + b0 us + (b0 dt) rhs in FP64, and the FP32 record of uout when
-// shadow != null.  Element-wise, so uout may alias us or u0.
-template <typename RT>
-__global__ void k_stage(const double* u0, const double* us, const RT* rhs, const double* dtp, double a0,
-                        double b0, double* uout, float* shadow, ShadowLayout L, int64_t n) {
+// FP64 form: uout = a0 u0 + b0 us + (b0 dt) rhs.  Element-wise, so uout may
+// alias us or u0.
+__global__ void k_stage(const double* u0, const double* us, const double* rhs, const double* dtp, double a0,
+                        double b0, double* uout, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double bdt = b0 * *dtp;
-  const double R = widen(rhs[i]);
-  const double v = a0 != 0.0 ? fma(bdt, R, fma(a0, u0[i], b0 * us[i])) : fma(bdt, R, b0 * us[i]);
-  uout[i] = v;
-  if (shadow) {
-    const int64_t e = i / L.nv;
-    const int l = (int)(i - e * L.nv), m = l / L.np, j = l - m * L.np;
-    float* rec = shadow + e * L.rec;
-    if (!L.split) {
-      rec[l] = d2f(v);
-    } else if (j == 0) {
-      const double u = L.phi0 * v;
-      const float hi = d2f(u);
-      rec[m] = hi;
-      rec[L.M + m] = d2f(u - f2d(hi));
-    } else {
-      rec[2 * L.M + m * (L.np - 1) + j - 1] = d2f(v);
-    }
-  }
+  uout[i] = a0 != 0.0 ? fma(bdt, rhs[i], fma(a0, u0[i], b0 * us[i])) : fma(bdt, rhs[i], b0 * us[i]);
 }
 
-int stage_update(const Ctx& x, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa) {
+int stage_update(const Ctx& x, bool, const double* us, const void* rhs, const StageArgs& sa) {
   const int64_t n = x.ne * x.M * x.np;
   const int bs = 256;
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
-  if (rhs_f32)
-    k_stage<float><<<grid, bs, 0, x.st>>>(sa.u0, us, static_cast<const float*>(rhs), sa.dt, sa.a0, sa.b0,
-                                          sa.uout, sa.shadow, x.shadow, n);
-  else
-    k_stage<double><<<grid, bs, 0, x.st>>>(sa.u0, us, static_cast<const double*>(rhs), sa.dt, sa.a0, sa.b0,
-                                           sa.uout, sa.shadow, x.shadow, n);
+  k_stage<<<grid, bs, 0, x.st>>>(sa.u0, us, static_cast<const double*>(rhs), sa.dt, sa.a0, sa.b0, sa.uout, n);
+  return 1;
+}
+
+// FP32 forms: one SSP-RK3 stage in increment form (incr_form.cuh), one value
+// per thread, for meshes whose last color does not reach every element.
+// Record entries: hi[m], lo[m] at m and M + m, mode j >= 1 at 2M + m(np-1) + j-1;
+// Kahan state: the record, then lo of the modes at rec + m(np-1) + j-1.
+__global__ void k_incr_stage(const float* __restrict__ rhs, StageArgs S, ShadowLayout L, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = i / L.nv;
+  const int l = (int)(i - e * L.nv), m = l / L.np, j = l - m * L.np;
+  const F2 dtp = split_f2(*S.dt);
+  const float dL = mul_f2(rhs[i], dtp);
+  float d = S.stage == 0 ? dL : (S.stage == 1 ? 0.25f * (S.delta[i] + dL) : S.delta[i] + dL);
+  const int mode_ix = 2 * L.M + m * (L.np - 1) + j - 1;
+  if (S.stage < 2) {
+    S.delta[i] = d;
+    const float* r0 = S.rec0 + e * S.rec0_stride;
+    float* ro = S.rec_out + e * L.rec;
+    if (j == 0) {
+      float h = r0[m], lo = r0[L.M + m];
+      pair_add_scaled(h, lo, d, split_f2(L.phi0));
+      ro[m] = h;
+      ro[L.M + m] = lo;
+    } else {
+      ro[mode_ix] = r0[mode_ix] + d;
+    }
+    if (l == 0)
+      for (int k = L.M * (L.np + 1); k < L.rec; ++k) ro[k] = 0.0f;  // padding
+  } else if (S.kstate) {
+    float* ks = S.kstate + e * S.rec0_stride;
+    if (j == 0) kahan_add(ks[m], ks[L.M + m], mul_f2(d, split_f2(2.0 / 3.0 * L.phi0)));
+    else kahan_add(ks[mode_ix], ks[L.rec + m * (L.np - 1) + j - 1], mul_f2(d, split_f2(2.0 / 3.0)));
+  } else {
+    S.uout[i] = fma(2.0 / 3.0, f2d(d), S.u0[i]);
+  }
+}
+
+int incr_stage_update(const Ctx& x, const float* rhs, const StageArgs& sa) {
+  const int64_t n = x.ne * x.M * x.np;
+  const int bs = 256;
+  const unsigned grid = (unsigned)((n + bs - 1) / bs);
+  k_incr_stage<<<grid, bs, 0, x.st>>>(rhs, sa, x.shadow, n);
   return 1;
 }
 

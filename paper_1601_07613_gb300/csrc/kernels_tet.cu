@@ -12,6 +12,7 @@
 #include "dev_util.cuh"
 #include "device.cuh"
 #include "euler_pert.cuh"
+#include "incr_form.cuh"
 
 namespace dgc {
 
@@ -280,7 +281,7 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
 }
 
 template <int P, typename CT, typename ST, typename RT>
-__global__ void __launch_bounds__(128) k_vol_tet(const ST* c, const double* jinv, RT* rhs, int64_t ne) {
+__global__ void __launch_bounds__(128) k_vol_tet(const ST* c, int sstride, const double* jinv, RT* rhs, int64_t ne) {
   using D = TetDim<P>;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(128) k_vol_tet(const ST* c, const double* jinv
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
   } else {
-    constexpr int stride = sizeof(ST) == 8 ? D::NV : D::NF;
+    const int64_t stride = sizeof(ST) == 8 ? D::NV : sstride;
     TetPert<P> B;
     tload_pert<P>(c + e * stride, B);
     PertRef<3> R;
@@ -319,6 +320,7 @@ struct TetParams {
   void* rhs;
   void* buf;
   StageArgs sa;
+  int sstride;  // floats per element of an FP32 state (record)
 };
 
 template <int P, typename RT, int MODE, typename AT>
@@ -347,14 +349,13 @@ __device__ __forceinline__ void tet_write(const TetParams& A, int64_t elem, int6
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
     tstore(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
-  } else {  // SURF_LAST: FP64 stage update, two values at a time (see the triangle kernel)
+  } else {  // SURF_LAST, FP64 form: FP64 stage update, two values at a time (see the triangle kernel)
+    static_assert(sizeof(RT) == 8, "the FP32 forms finish the step in incr_last");
     const RT* part = static_cast<const RT*>(A.rhs) + elem * NV;
     const double2* us2 = reinterpret_cast<const double2*>(static_cast<const double*>(A.state) + elem * NV);
     const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
     double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
-    float* rec = A.sa.shadow ? A.sa.shadow + elem * D::NF : nullptr;
     const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
-    const double phi0 = tet_tab<double, P>().phiV[0][0];
 #pragma unroll
     for (int i = 0; i < NV; i += 2) {
       const double2 s = us2[i / 2];
@@ -369,14 +370,6 @@ __device__ __forceinline__ void tet_write(const TetParams& A, int64_t elem, int6
         v[1] = fma(bdt, L1, fma(a0, u.y, b0 * s.y));
       }
       out2[i / 2] = make_double2(v[0], v[1]);
-      if (rec) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const int m = (i + t) / D::NP, j = (i + t) % D::NP;
-          if (j == 0) tsplit(phi0, v[t], rec[m], rec[5 + m]);
-          else rec[10 + m * (D::NP - 1) + j - 1] = d2f(v[t]);
-        }
-      }
     }
   }
 }
@@ -447,7 +440,7 @@ __global__ void __launch_bounds__(256) k_surf_tet(const TetParams A) {
     if (writer) tet_write<P, RT, MODE>(A, elem, k, side, acc);
   } else {
     const TetTab<float, P>& K = tet_tab<float, P>();
-    constexpr int stride = sizeof(ST) == 8 ? NV : D::NF;
+    const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
     TetPert<P> B;
     tload_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
     PertRef<3> R;
@@ -495,7 +488,18 @@ __global__ void __launch_bounds__(256) k_surf_tet(const TetParams A) {
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
     }
-    if (writer) tet_write<P, RT, MODE>(A, elem, k, side, acc);
+    if constexpr (MODE == SURF_LAST) {
+      // the element's right-hand side is complete: SSP-RK3 stage in increment form
+      if (writer) {
+        float L[NV];
+        ldv<NV>(static_cast<const float*>(A.rhs) + elem * NV, L);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) L[i] += acc[i];
+        incr_last<5, NP>(A.sa, elem, L, B, tet_tab<double, P>().phiV[0][0]);
+      }
+    } else if (writer) {
+      tet_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
   }
 }
 
@@ -568,21 +572,21 @@ __global__ void __launch_bounds__(128) k_cfl2_tet(const double* c, const double*
 
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
-static int tvol_p(const Ctx& x, const void* s, void* r) {
+static int tvol_p(const Ctx& x, const void* s, int ss, void* r) {
   const int bs = 128;
   k_vol_tet<P, CT, ST, RT><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(
-      static_cast<const ST*>(s), x.d->jinv, static_cast<RT*>(r), x.ne);
+      static_cast<const ST*>(s), ss, x.d->jinv, static_cast<RT*>(r), x.ne);
   return 1;
 }
 
-int tet_volume(const Ctx& x, TypeCfg ty, const void* s, void* r) {
+int tet_volume(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r) {
   switch (x.p * 4 + ty) {
-    case 4 + TY_D: return tvol_p<1, double, double, double>(x, s, r);
-    case 8 + TY_D: return tvol_p<2, double, double, double>(x, s, r);
-    case 4 + TY_MD: return tvol_p<1, float, double, double>(x, s, r);
-    case 8 + TY_MD: return tvol_p<2, float, double, double>(x, s, r);
-    case 4 + TY_MF: return tvol_p<1, float, float, float>(x, s, r);
-    case 8 + TY_MF: return tvol_p<2, float, float, float>(x, s, r);
+    case 4 + TY_D: return tvol_p<1, double, double, double>(x, s, ss, r);
+    case 8 + TY_D: return tvol_p<2, double, double, double>(x, s, ss, r);
+    case 4 + TY_MD: return tvol_p<1, float, double, double>(x, s, ss, r);
+    case 8 + TY_MD: return tvol_p<2, float, double, double>(x, s, ss, r);
+    case 4 + TY_MF: return tvol_p<1, float, float, float>(x, s, ss, r);
+    case 8 + TY_MF: return tvol_p<2, float, float, float>(x, s, ss, r);
     default: return -1;
   }
 }
@@ -616,7 +620,7 @@ template <int P>
 static int tsurf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const TetParams& A) {
   if (mode == SURF_LAST) {
     if (ty == TY_D) return tsurf_launch<P, double, double, double, SURF_LAST>(x, A);
-    if (ty == TY_MLAST) return tsurf_launch<P, float, double, float, SURF_LAST>(x, A);
+    if (ty == TY_MF) return tsurf_launch<P, float, float, float, SURF_LAST>(x, A);
     return -1;
   }
   switch (ty) {
@@ -630,10 +634,11 @@ static int tsurf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const TetParams& A) 
 }
 
 int tet_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
-                void* rhs, void* buf, const StageArgs* sa) {
+                int sstride, void* rhs, void* buf, const StageArgs* sa) {
   TetParams A;
   A.begin = begin;
   A.end = end;
+  A.sstride = sstride;
   A.topo = x.d->topo;
   A.fgeo = x.d->fgeo;
   A.jinv = x.d->jinv;

@@ -20,6 +20,7 @@
 #include "dev_util.cuh"
 #include "device.cuh"
 #include "euler_pert.cuh"
+#include "incr_form.cuh"
 
 namespace dgc {
 
@@ -330,7 +331,7 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
 // Volume kernel (unfused path): one thread per element, rhs = volume integral.
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
-__global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, const double* __restrict__ jinv,
+__global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, int sstride, const double* __restrict__ jinv,
                                                  RT* __restrict__ rhs, int64_t ne) {
   using D = TriDim<P>;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, const
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
   } else {
-    constexpr int stride = sizeof(ST) == 8 ? D::NV : D::NF;
+    const int64_t stride = sizeof(ST) == 8 ? D::NV : sstride;
     PertBlock<P> B;
     load_pert<P>(c + e * stride, B);
     PertRef<2> R;
@@ -372,7 +373,8 @@ struct SurfParams {
   void* rhs;
   void* buf;
   StageArgs sa;
-  int ntab;  // edge tables to stage (3, or 9 on meshes with hanging edges)
+  int ntab;     // edge tables to stage (3, or 9 on meshes with hanging edges)
+  int sstride;  // floats per element of an FP32 state (record or Kahan state)
 };
 
 // the contribution of one lane's element is in acc; write it as the mode asks
@@ -402,16 +404,15 @@ __device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, in
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
     store_block(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
-  } else {  // SURF_LAST: L = partial rhs + this color; FP64 stage update
-    // uout = a0 u0 + b0 us + (b0 dt) L in FP64, two values at a time:
+  } else {  // SURF_LAST, FP64 form: L = partial rhs + this color; FP64 stage update
+    // uout = a0 u0 + b0 us + (b0 dt) L, two values at a time:
     // 1 FMA per value in the first stage, 1 MUL + 2 FMA in the others
+    static_assert(sizeof(RT) == 8, "the FP32 forms finish the step in incr_last");
     const RT* part = static_cast<const RT*>(A.rhs) + elem * NV;
     const double2* us2 = reinterpret_cast<const double2*>(static_cast<const double*>(A.state) + elem * NV);
     const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
     double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
-    float* rec = A.sa.shadow ? A.sa.shadow + elem * D::NF : nullptr;
     const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
-    const double phi0 = tri_tab<double, P>().phiV[0][0];
 #pragma unroll
     for (int i = 0; i < NV; i += 2) {
       const double2 s = us2[i / 2];
@@ -426,14 +427,6 @@ __device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, in
         v[1] = fma(bdt, L1, fma(a0, u.y, b0 * s.y));
       }
       out2[i / 2] = make_double2(v[0], v[1]);
-      if (rec) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const int m = (i + t) / D::NP, j = (i + t) % D::NP;  // compile-time after unrolling
-          if (j == 0) split_mean(phi0, v[t], rec[m], rec[4 + m]);
-          else rec[8 + m * (D::NP - 1) + j - 1] = d2f(v[t]);
-        }
-      }
     }
   }
 }
@@ -456,8 +449,15 @@ template <int P, typename CT, typename ST, typename RT, int MODE>
 __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool valid, int side, const CT* sphi,
                                           const CT* sw);
 
+// FP32 surface kernels: minimum resident blocks of 256 threads the compiler
+// must allow per SM (register cap 65536 / (256 * min)); 1 leaves the register
+// count free.  FP64 kernels are never capped.
+#ifndef DGC_SURF_MINB
+#define DGC_SURF_MINB 1
+#endif
+
 template <int P, typename CT, typename ST, typename RT, int MODE>
-__global__ void __launch_bounds__(256) k_surf_tri(const SurfParams A) {
+__global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_SURF_MINB : 1)) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
   __shared__ CT sphi[9 * D::NQE * D::NP];
   __shared__ CT sw[D::NQE];
@@ -485,6 +485,7 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool v
   const CT* ph = sphi + le * NQ * NP;
   // (in SURF_LAST the state may alias the stage output, but each element's
   // block is read and written by its own lane only)
+  if (writer) prefetch_epilogue<MODE, NV, D::NF, RT>(A.rhs, A.sa, elem);
 
   if constexpr (sizeof(CT) == 8) {
     // ---------------- FP64: Eq. 2 as written ----------------
@@ -526,7 +527,7 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool v
     if (writer) surf_write<P, RT, MODE>(A, elem, k, side, acc);
   } else {
     // ---------------- FP32: perturbation form ----------------
-    constexpr int stride = sizeof(ST) == 8 ? NV : D::NF;
+    const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
     PertBlock<P> B;
     load_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
     PertRef<2> R;
@@ -576,7 +577,18 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool v
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
     }
-    if (writer) surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    if constexpr (MODE == SURF_LAST) {
+      // the element's right-hand side is complete: SSP-RK3 stage in increment form
+      if (writer) {
+        float L[NV];
+        load_plain(static_cast<const float*>(A.rhs) + elem * NV, L);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) L[i] += acc[i];
+        incr_last<4, NP>(A.sa, elem, L, B, tri_tab<double, P>().phiV[0][0]);
+      }
+    } else if (writer) {
+      surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
   }
 }
 
@@ -683,6 +695,75 @@ __global__ void __launch_bounds__(128) k_cfl2_tri(const double* __restrict__ c, 
   block_min_to(best, dtbits);
 }
 
+// Kahan form: pass 1 reads the record part of the FP32 pair state (no record to
+// write); pass 2 evaluates candidates in FP64 from hi + lo of every value.
+int tri_kahan_floats(int p) { return 8 * ((p + 1) * (p + 2) / 2); }
+
+template <int P>
+__global__ void __launch_bounds__(128) k_cfl1_tri_k(const float* __restrict__ ks, const double* __restrict__ inr,
+                                                    int64_t ne, float* __restrict__ est, unsigned* minbits) {
+  using D = TriDim<P>;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float best = FLT_MAX;
+  if (e < ne) {
+    float r[D::NF];
+    load_block(ks + e * (8 * D::NP), r);
+    float d = d2f(__ldg(inr + e)) / ((2 * P + 1) * lambda_max_rec<P>(r));
+    if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;
+    est[e] = d;
+    best = d;
+  }
+  block_min_to(best, minbits);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_cfl2_tri_k(const float* __restrict__ ks, const double* __restrict__ inr,
+                                                    int64_t ne, double cfl, const float* __restrict__ est,
+                                                    const unsigned* minbits, unsigned long long* dtbits) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP, NM = NP - 1;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double best = DBL_MAX;
+  if (e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin)) {
+    const float* k = ks + e * (8 * NP);
+    const double phi0 = tri_tab<double, P>().phiV[0][0];
+    double v[D::NV];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[m * NP] = (f2d(k[m]) + f2d(k[4 + m])) / phi0;
+#pragma unroll
+      for (int j = 0; j < NM; ++j) v[m * NP + 1 + j] = f2d(k[8 + m * NM + j]) + f2d(k[D::NF + m * NM + j]);
+    }
+    const double b = cfl * (__ldg(inr + e) / ((2 * P + 1) * lambda_max<P, double>(v)));
+    best = b > 0.0 ? b : DBL_MAX;
+  }
+  block_min_to(best, dtbits);
+}
+
+int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((x.ne + bs - 1) / bs);
+  auto* bits = reinterpret_cast<unsigned long long*>(dt);
+  float* est = x.d->cfl_est;
+  unsigned* mn = reinterpret_cast<unsigned*>(x.d->cfl_est + x.ne);
+  if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
+  switch (x.p) {
+    case 1:
+      k_cfl1_tri_k<1><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
+      k_cfl2_tri_k<1><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    case 2:
+      k_cfl1_tri_k<2><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
+      k_cfl2_tri_k<2><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    case 3:
+      k_cfl1_tri_k<3><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
+      k_cfl2_tri_k<3><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      return 2;
+    default: return -1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Batched meshes: one persistent launch per kernel class covering every mesh.
 // The host cuts each mesh's color (or element) range into tiles of at most
@@ -696,7 +777,7 @@ __global__ void __launch_bounds__(256) k_batch_surf(const BatchMeshDev* __restri
                                                     double a0, double b0) {
   using CT = typename std::conditional<MIXED, float, double>::type;
   using RT = CT;
-  using ST = typename std::conditional<MIXED && MODE != SURF_LAST, float, double>::type;
+  using ST = CT;
   __shared__ CT sphi[3 * TriDim<3>::NQE * TriDim<3>::NP];
   __shared__ CT sw[TriDim<3>::NQE];
   int curp = 0;
@@ -717,16 +798,28 @@ __global__ void __launch_bounds__(256) k_batch_surf(const BatchMeshDev* __restri
     A.topo = B.topo;
     A.fgeo = B.fgeo;
     A.jinv = B.jinv;
-    double* us = stage == 0 ? B.c : B.u1;
-    A.state = (MIXED && MODE != SURF_LAST) ? (const void*)B.rec : (const void*)us;
+    if (MIXED) {
+      const int nf = 4 * ((T.p + 1) * (T.p + 2) / 2 + 1);
+      A.state = stage == 0 ? B.rec0 : B.recs;
+      A.sstride = nf;
+      A.sa.u0 = B.c;
+      A.sa.uout = B.c;
+      A.sa.stage = stage;
+      A.sa.rec0 = B.rec0;
+      A.sa.rec0_stride = nf;
+      A.sa.rec_out = B.recs;
+      A.sa.delta = B.delta;
+      A.sa.kstate = nullptr;
+    } else {
+      A.state = stage == 0 ? B.c : B.u1;
+      A.sa.u0 = B.c;
+      A.sa.uout = stage == 2 ? B.c : B.u1;
+      A.sa.a0 = a0;
+      A.sa.b0 = b0;
+    }
     A.rhs = B.rhs;
     A.buf = nullptr;
-    A.sa.u0 = B.c;
-    A.sa.uout = stage == 2 ? B.c : B.u1;
-    A.sa.shadow = MIXED ? B.rec : nullptr;
     A.sa.dt = B.dt;
-    A.sa.a0 = a0;
-    A.sa.b0 = b0;
     int64_t k = T.begin + (threadIdx.x >> 1);
     const bool valid = k < T.end;
     if (!valid) k = T.end - 1;
@@ -754,7 +847,7 @@ __global__ void __launch_bounds__(128) k_batch_cfl1(const BatchMeshDev* __restri
     const int64_t e = T.begin + threadIdx.x;
     float best = FLT_MAX;
     if (e < T.end) {
-      float* sh = MIXED ? B.rec : nullptr;
+      float* sh = MIXED ? B.rec0 : nullptr;
       if (T.p == 1) best = cfl1_elem<1>(B.c, B.inr, e, B.est, sh);
       else if (T.p == 2) best = cfl1_elem<2>(B.c, B.inr, e, B.est, sh);
       else best = cfl1_elem<3>(B.c, B.inr, e, B.est, sh);
@@ -833,25 +926,30 @@ int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, i
 // launchers
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
-static int vol_p(const Ctx& x, const void* s, void* r) {
+static int vol_p(const Ctx& x, const void* s, int sstride, void* r) {
   const int bs = 128;
   const int64_t grid = (x.ne + bs - 1) / bs;
-  k_vol_tri<P, CT, ST, RT><<<(unsigned)grid, bs, 0, x.st>>>(static_cast<const ST*>(s), x.d->jinv,
+  k_vol_tri<P, CT, ST, RT><<<(unsigned)grid, bs, 0, x.st>>>(static_cast<const ST*>(s), sstride, x.d->jinv,
                                                              static_cast<RT*>(r), x.ne);
   return 1;
 }
 
-int tri_volume(const Ctx& x, TypeCfg ty, const void* s, void* r) {
-  switch (x.p * 4 + ty) {
-    case 4 + TY_D: return vol_p<1, double, double, double>(x, s, r);
-    case 8 + TY_D: return vol_p<2, double, double, double>(x, s, r);
-    case 12 + TY_D: return vol_p<3, double, double, double>(x, s, r);
-    case 4 + TY_MD: return vol_p<1, float, double, double>(x, s, r);
-    case 8 + TY_MD: return vol_p<2, float, double, double>(x, s, r);
-    case 12 + TY_MD: return vol_p<3, float, double, double>(x, s, r);
-    case 4 + TY_MF: return vol_p<1, float, float, float>(x, s, r);
-    case 8 + TY_MF: return vol_p<2, float, float, float>(x, s, r);
-    case 12 + TY_MF: return vol_p<3, float, float, float>(x, s, r);
+template <int P>
+static int vol_ty(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r) {
+  switch (ty) {
+    case TY_D: return vol_p<P, double, double, double>(x, s, ss, r);
+    case TY_MD: return vol_p<P, float, double, double>(x, s, ss, r);
+    case TY_MF: return vol_p<P, float, float, float>(x, s, ss, r);
+    case TY_KD: return vol_p<P, float, float, double>(x, s, ss, r);
+    default: return -1;
+  }
+}
+
+int tri_volume(const Ctx& x, TypeCfg ty, const void* s, int sstride, void* r) {
+  switch (x.p) {
+    case 1: return vol_ty<1>(x, ty, s, sstride, r);
+    case 2: return vol_ty<2>(x, ty, s, sstride, r);
+    case 3: return vol_ty<3>(x, ty, s, sstride, r);
     default: return -1;
   }
 }
@@ -881,7 +979,7 @@ template <int P>
 static int surf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const SurfParams& A) {
   if (mode == SURF_LAST) {
     if (ty == TY_D) return surf_launch<P, double, double, double, SURF_LAST>(x, A);
-    if (ty == TY_MLAST) return surf_launch<P, float, double, float, SURF_LAST>(x, A);
+    if (ty == TY_MF) return surf_launch<P, float, float, float, SURF_LAST>(x, A);
     return -1;
   }
   switch (ty) {
@@ -890,15 +988,20 @@ static int surf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const SurfParams& A) 
     case TY_MF:
       if (mode != SURF_RMW && mode != SURF_FIRST) return -1;
       return surf_mode<P, float, float, float>(x, mode, A);
+    case TY_KD:
+      if (mode == SURF_RMW) return surf_launch<P, float, float, double, SURF_RMW>(x, A);
+      if (mode == SURF_FIRST) return surf_launch<P, float, float, double, SURF_FIRST>(x, A);
+      return -1;
     default: return -1;
   }
 }
 
 int tri_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
-                void* rhs, void* buf, const StageArgs* sa) {
+                int sstride, void* rhs, void* buf, const StageArgs* sa) {
   SurfParams A;
   A.begin = begin;
   A.end = end;
+  A.sstride = sstride;
   A.topo = x.d->topo;
   A.fgeo = x.d->fgeo;
   A.jinv = x.d->jinv;

@@ -17,6 +17,7 @@ from . import _build_lib
 
 DGC_FP64 = 0
 DGC_FP32_MIXED = 1
+DGC_FP32_KAHAN = 2
 DGC_OPT_FUSE = 0
 DGC_OPT_EDGES_PER_BLOCK = 1
 DGC_OPT_THREADS_PER_EDGE = 2
@@ -48,6 +49,9 @@ SIGNATURES = {
     "dgc_state_size": (C.c_int, [_P, _I64P]),
     "dgc_workspace_size": (C.c_int, [_P, C.c_int, _I64P]),
     "dgc_import_state": (C.c_int, [_P, _DP, _P, _P]),
+    "dgc_state_bytes": (C.c_int, [_P, C.c_int, _I64P]),
+    "dgc_import_state_prec": (C.c_int, [_P, C.c_int, _DP, _P, _P]),
+    "dgc_export_state_prec": (C.c_int, [_P, C.c_int, _P, _DP, _P]),
     "dgc_export_state": (C.c_int, [_P, _P, _DP, _P]),
     "dgc_rhs": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dgc_cfl_dt": (C.c_int, [_P, _P, C.c_double, _P, _P]),
@@ -241,6 +245,25 @@ def dgc_export_state(mesh, c_dev, out=None, stream=None):
     if out is None:
         out = np.zeros((info["ne"], info["M"], info["np"]))
     _check(lib().dgc_export_state(mesh, _dptr(c_dev), out.ctypes.data_as(_DP), _stream(stream)))
+    return out
+
+
+def dgc_state_bytes(mesh, prec: int) -> int:
+    b = C.c_int64()
+    _check(lib().dgc_state_bytes(mesh, prec, C.byref(b)))
+    return b.value
+
+
+def dgc_import_state_prec(mesh, prec: int, c_host, c_dev, stream=None):
+    c_host, cp = _h(c_host, np.float64)
+    _check(lib().dgc_import_state_prec(mesh, prec, cp, _dptr(c_dev), _stream(stream)))
+
+
+def dgc_export_state_prec(mesh, prec: int, c_dev, out=None, stream=None):
+    info = dgc_mesh_info(mesh)
+    if out is None:
+        out = np.zeros((info["ne"], info["M"], info["np"]))
+    _check(lib().dgc_export_state_prec(mesh, prec, _dptr(c_dev), out.ctypes.data_as(_DP), _stream(stream)))
     return out
 
 

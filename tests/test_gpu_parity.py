@@ -329,34 +329,46 @@ def test_tet_rk_step_matches_oracle(torch_dev, oracle_mod, p):
         run.close()
 
 
-def test_fp32_record_is_correctly_rounded(torch_dev):
-    """The FP32 record of the state the mixed-precision step keeps: the mean
-    state phi_0 c_0 as an FP32 pair hi + lo, then the modes j >= 1 as FP32.
-    Both are converted with integer bit operations; they must equal the
-    hardware round-to-nearest conversion bit for bit."""
+def test_fp32_records_of_the_mixed_step(torch_dev):
+    """The FP32 records the mixed-precision step keeps (workspace: record of u0,
+    record of the stage state, FP32 increment, rhs; each 256-byte aligned).
+    * rec0, written by the CFL pass from the FP64 state: the mean phi_0 c_0 as an
+      FP32 pair hi + lo, the modes j >= 1 as FP32, converted with integer bit
+      operations; they must equal round-to-nearest bit for bit.
+    * the stage record after the step holds u0 + delta_2 (increment form): its
+      modes are rec0's plus delta_2's in one FP32 addition, bit for bit, and its
+      mean pair is the compensated sum, hi + lo = mean + phi_0 delta_2 to 2^-46."""
     torch, dev = torch_dev
     mi = W.periodic_square_tri(20, jitter=0.2, seed=11)
     run = Run(torch_dev, mi, 2)
     c = state_for(mi, run.m.info["np"], seed=11, amp=5e-2)
     run.load(c)
+    u0 = run.c.clone()
     ws = torch.zeros(dgc.dgc_workspace_size(run.m.h, dgc.DGC_FP32_MIXED) // 8 + 64, dtype=torch.float64, device=dev)
     d = torch.zeros(1, dtype=torch.float64, device=dev)
     dgc.dgc_rk_step(run.m.h, dgc.DGC_FP32_MIXED, run.c, 0.3, d, ws)
     torch.cuda.synchronize()
-    E, M, NP = run.c.shape
-    S = run.c.numel() * 8
-    off = (S + 255) // 256 * 256
+    E, M, NP = u0.shape
     nrec = M * (NP + 1)
-    rec = ws.view(torch.uint8)[off:off + 4 * E * nrec].view(torch.float32).reshape(E, nrec)
-    u = run.c
-    assert torch.equal(rec[:, 2 * M:].reshape(E, M, NP - 1), u[:, :, 1:].float())
+    R = (4 * E * nrec + 255) // 256 * 256
+    raw = ws.view(torch.uint8)
+    rec0 = raw[:4 * E * nrec].view(torch.float32).reshape(E, nrec)
+    recs = raw[R:R + 4 * E * nrec].view(torch.float32).reshape(E, nrec)
+    delta = raw[2 * R:2 * R + 4 * E * M * NP].view(torch.float32).reshape(E, M, NP)
+    assert torch.equal(rec0[:, 2 * M:].reshape(E, M, NP - 1), u0[:, :, 1:].float())
     # the mean phi_0 c_0 (phi_0 = sqrt 2 from the library's normalised table, to an ulp):
     # hi is its FP32 rounding and lo the FP32 rounding of the remainder
-    mean = u[:, :, 0] * np.sqrt(2.0)
-    hi, lo = rec[:, :M], rec[:, M:2 * M]
+    mean = u0[:, :, 0] * np.sqrt(2.0)
+    hi, lo = rec0[:, :M], rec0[:, M:2 * M]
     ulp32 = torch.abs(mean.float()).double() * 2.0 ** -23
     assert torch.all(torch.abs(hi.double() - mean) <= 0.5 * ulp32 + 4e-16 * torch.abs(mean))
     # the pair carries 48 significant bits: hi + lo = mean to 2^-47 relative
     assert torch.all(torch.abs(hi.double() + lo.double() - mean) <= 2.0 ** -47 * torch.abs(mean))
     assert torch.all(torch.abs(lo.double() - (mean - hi.double())) <= 2.0 ** -47 * torch.abs(mean))
+    # stage record = rec0 (+) delta_2
+    assert torch.equal(recs[:, 2 * M:].reshape(E, M, NP - 1), rec0[:, 2 * M:].reshape(E, M, NP - 1) + delta[:, :, 1:])
+    mean2 = hi.double() + lo.double() + np.sqrt(2.0) * delta[:, :, 0].double()
+    got2 = recs[:, :M].double() + recs[:, M:2 * M].double()
+    assert torch.all(torch.abs(got2 - mean2) <= 2.0 ** -46 * torch.abs(mean2))
+    assert delta.abs().max() > 0
     run.close()
