@@ -165,6 +165,39 @@ def time_steps(torch, fn, steps, stream):
     return s.elapsed_time(e) / steps
 
 
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources and headers the kernels are built from; the
+    DRAM traffic quoted below holds only for the sources it was measured with."""
+    import hashlib
+
+    root = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1601_07613_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(root)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(root, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
+# over the launches of each class) from the launch list of this benchmark's own
+# command, profiles/launch_list_rk_fp32mixed_p3_1048352tri.md, taken with the
+# kernel sources of hash TRAFFIC_SOURCES.
+TRAFFIC_SOURCES = None
+TRAFFIC_BYTES = {}
+
+
+def replica_throughput(torch, ms: float, world: int, units_per_step: float, dev):
+    """Replicas only: every rank runs the whole workload; the job's time per step
+    is the slowest rank's (all-reduce MAX), and the throughput counts the units
+    of all ranks.  Returns (ms per step, units per second)."""
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_step / (ms * 1e-3)
+
+
 def run_dgc(args, rank, world, local_rank):
     import torch
 
@@ -204,11 +237,7 @@ def run_dgc(args, rank, world, local_rank):
     clocks = clk.stop()
     prof = dgc.dgc_profile_collect(mesh.h)
     dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_PROFILE, 0)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 3 * dofs / (ms * 1e-3)
+    ms, value = replica_throughput(torch, ms, world, 3 * dofs, dev)
 
     hbm, hbm_kind = peaks()
     ncolors = info["ncolors"]
@@ -232,8 +261,9 @@ def run_dgc(args, rank, world, local_rank):
                         "frac_hbm": round(b / (avg * 1e-3) / 1e9 / hbm, 3)}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["calls"])
     step_bytes = sum(kernels[k]["alg_bytes"] * kernels[k]["calls"] for k in kernels) / args.steps
+    traffic = TRAFFIC_BYTES.get(dom) if TRAFFIC_SOURCES == kernel_source_hash() and args.n == 724 else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["alg_gbs"], "peak": hbm,
-                "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": None,
+                "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
                 "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
                 "step_alg_gbs": round(step_bytes / (ms * 1e-3) / 1e9, 1),
                 "step_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm, 3)}
@@ -287,12 +317,15 @@ def run_dgc(args, rank, world, local_rank):
         del buf, r
         variants.update(run_batched(dgc, torch, dev, stream, args))
         variants.update(run_other_meshes(dgc, torch, dev, stream, args))
+        variants.update(run_table7(dgc, torch, dev, stream, args, cfg, c_host))
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
     e2e = None
     if not args.no_e2e:
-        host_in = np.ascontiguousarray(c_host)
-        host_out = np.empty_like(host_in)
+        # page-locked host buffers (the transfers a caller with pinned memory makes)
+        host_in = torch.empty(c_host.shape, dtype=torch.float64, pin_memory=True).numpy()
+        host_in[...] = c_host
+        host_out = torch.empty(c_host.shape, dtype=torch.float64, pin_memory=True).numpy()
         ke = 3
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -417,11 +450,63 @@ def run_other_meshes(dgc, torch, dev, stream, args):
                 call()
                 t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
                 entry[f"rhs_{kind}_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+            dgc.dgc_set_option(m.h, dgc.DGC_OPT_FUSE, 0)
+            call = lambda: dgc.dgc_rhs(m.h, prec, c, r)
+            call()
+            t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
+            entry[f"rhs_colored_unfused_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+            dgc.dgc_set_option(m.h, dgc.DGC_OPT_FUSE, 1)
             del buf
         out[tag] = entry
         del c, r
         m.close()
     return out
+
+
+def run_table7(dgc, torch, dev, stream, args, cfg, c_base):
+    """Color count and data ordering on GB300 (the ablation of Table 7): the
+    naive greedy (5 colors) or the modified coloring (3), with and without the
+    color-1 element renumbering and the left-ascending edge order of Sec. 5.
+    The mesh is the benchmark's with its element list in a seeded random order,
+    standing in for a mesh generator's unstructured numbering (on the grid's own
+    order the naive greedy already finds 3 colors).  Each row times the mixed RK
+    step and the FP64 right-hand side; pct = speed-up over the first row."""
+    mi = cfg["mesh"]
+    perm = np.random.default_rng(1601).permutation(mi.ne)
+    m = dgc.Mesh(2, cfg["p"], mi.xyz, mi.ev[perm], mi.periodic_len)
+    c_host = np.ascontiguousarray(c_base[perm])  # the same elements (same vertex lists), permuted
+    info = m.info
+    dofs = info["ne"] * info["M"] * info["np"]
+    c = torch.empty((info["ne"], info["M"], info["np"]), dtype=torch.float64, device=dev)
+    r = torch.empty_like(c)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    rows = []
+    for colors, renumber, reorder in ((5, False, False), (3, False, False), (5, True, False), (3, True, False),
+                                      (5, True, True), (3, True, True)):
+        if colors == 5:
+            nc, _ = dgc.dgc_color_edges_naive(m.h, renumber, reorder)
+        else:
+            nc, _ = dgc.dgc_color_edges(m.h, 1601, 0)
+            dgc.dgc_reorder(m.h, renumber, reorder)
+        ws = torch.empty(dgc.dgc_workspace_size(m.h, dgc.DGC_FP32_MIXED) // 8 + 64, dtype=torch.float64, device=dev)
+        dgc.dgc_import_state(m.h, c_host, c)
+        fn = lambda: dgc.dgc_rk_step(m.h, dgc.DGC_FP32_MIXED, c, cfg["cfl"], dt, ws)
+        fn()
+        t_rk = time_steps(torch, fn, max(3, args.steps // 2), stream)
+        dgc.dgc_import_state(m.h, c_host, c)
+        fr = lambda: dgc.dgc_rhs(m.h, dgc.DGC_FP64, c, r)
+        fr()
+        t_rhs = time_steps(torch, fr, 3, stream)
+        rows.append({"colors": int(nc), "renumber": renumber, "reorder": reorder,
+                     "rk_fp32mixed_ms": round(t_rk, 4), "rhs_fp64_ms": round(t_rhs, 4),
+                     "launches_per_step": dgc.dgc_last_launch_count(m.h)})
+        del ws
+    for row in rows:
+        row["pct_rk"] = round(100.0 * (rows[0]["rk_fp32mixed_ms"] - row["rk_fp32mixed_ms"]) / rows[0]["rk_fp32mixed_ms"], 1)
+        row["pct_rhs_fp64"] = round(100.0 * (rows[0]["rhs_fp64_ms"] - row["rhs_fp64_ms"]) / rows[0]["rhs_fp64_ms"], 1)
+    m.close()
+    return {"table7_ablation": {"mesh": "1,048,352 jittered periodic triangles, element list in seeded random order",
+                                "p": cfg["p"], "dofs": dofs, "rows": rows}}
 
 
 def cpu_baseline(mi, p, c_host, dofs, elements=None):

@@ -130,6 +130,13 @@ dgc_status dgc_color_edges(dgc_mesh* mesh, uint64_t seed, int64_t max_swaps,
 dgc_status dgc_color_edges_naive(dgc_mesh* mesh, int renumber, int reorder,
                                  int32_t* n_colors, int64_t* per_color);
 
+/* Re-applies the ordering of Sec. 5 to the current coloring with each part switched on or
+ * off (the ablation of Table 7): renumber = the color-1 element renumbering, reorder_left
+ * = ascending left element within colors >= 2 (0: original order within each color; edges
+ * stay color-major).  States imported before the call are in the old element order.
+ * DGC_ERR_ARG if the mesh is not colored.  Host only. */
+dgc_status dgc_reorder(dgc_mesh* mesh, int renumber, int reorder_left);
+
 /* Sizes: info[0] = E, [1] = edges, [2] = Np, [3] = M, [4] = edge (face) quadrature
  * points, [5] = volume quadrature points, [6] = colors (0 before coloring),
  * [7] = dim, [8] = p, [9] = 1 if every element has exactly one edge of each color. */

@@ -194,6 +194,8 @@ void upload(Mesh& m) {
     d->fgeo = dalloc<double2>((int64_t)fgeo.size());
     d->slots = dalloc<int32_t>((int64_t)slots.size());
     d->cfl_est = dalloc<float>(m.ne + 64);
+    d->perm = dalloc<int32_t>(m.ne);
+    DGC_CUDA(cudaMemcpy(d->perm, en.data(), sizeof(int32_t) * m.ne, cudaMemcpyHostToDevice));
     DGC_CUDA(cudaMemcpy(d->jinv, jinv.data(), sizeof(double) * jinv.size(), cudaMemcpyHostToDevice));
     DGC_CUDA(cudaMemcpy(d->inr, inr.data(), sizeof(double) * inr.size(), cudaMemcpyHostToDevice));
     DGC_CUDA(cudaMemcpy(d->topo, topo.data(), sizeof(int4) * topo.size(), cudaMemcpyHostToDevice));
@@ -256,8 +258,8 @@ void check_ptr(const void* p, const char* what) {
 }
 
 // ss: floats per element of an FP32 state (record or Kahan state), 0 for FP64 states
-int vol(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r) {
-  return x.dim == 2 ? tri_volume(x, ty, s, ss, r) : tet_volume(x, ty, s, ss, r);
+int vol(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r, int64_t e0 = 0) {
+  return x.dim == 2 ? tri_volume(x, ty, s, ss, r, e0) : tet_volume(x, ty, s, ss, r, e0);
 }
 int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, int ss, void* r, void* buf,
          const StageArgs* sa) {
@@ -326,11 +328,19 @@ void finish(Mesh& m, int64_t launches) {
 // rhs = L(state): Algorithm 1 (volume, then the colors in order, a kernel
 // boundary between colors); with fusion on closed conforming meshes the
 // first color also evaluates the volume integral and stores, no pre-zeroing.
+// The first color carries the volume integral (plain store) when it reaches
+// every element once (closed conforming meshes), or, after the color-1
+// renumbering, the elements [0, reached) it does reach; the rest get a volume
+// kernel of their own.
+bool first_fused(const Mesh& m) { return m.fuse && (m.perfect || m.reached >= 0); }
+int64_t unreached(const Mesh& m) { return m.perfect ? m.ne : m.reached; }
+
 int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss, void* rhs) {
   int64_t n = 0;
   const std::vector<int32_t>& off = m.color_off;
-  if (m.fuse && m.perfect) {
+  if (first_fused(m)) {
     run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], state, ss, rhs, nullptr, nullptr); });
+    run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, state, ss, rhs, unreached(m)); });
     for (int c = 2; c <= m.ncolors; ++c)
       run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, ss, rhs, nullptr, nullptr); });
   } else {
@@ -404,8 +414,13 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
           launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
         launch(DGC_K_LAST, [&] { return surf(x, TY_D, SURF_LAST, off[C - 1], off[C], us, 0, w.rhs, nullptr, &sa); });
       } else {
-        launch(DGC_K_VOLUME, [&] { return vol(x, TY_D, us, 0, w.rhs); });
-        for (int k = 1; k <= C; ++k)
+        int k0 = 1;
+        if (first_fused(m)) {
+          launch(DGC_K_FIRST, [&] { return surf(x, TY_D, SURF_FIRST, off[0], off[1], us, 0, w.rhs, nullptr, nullptr); });
+          k0 = 2;
+        }
+        launch(DGC_K_VOLUME, [&] { return vol(x, TY_D, us, 0, w.rhs, k0 == 2 ? unreached(m) : 0); });
+        for (int k = k0; k <= C; ++k)
           launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
         launch(DGC_K_STAGE, [&] { return stage_update(x, false, us, w.rhs, sa); });
       }
@@ -439,8 +454,13 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
         launch(DGC_K_COLOR, [&] { return surf(x, TY_MF, SURF_RMW, off[k - 1], off[k], in, ss, w.rhs, nullptr, nullptr); });
       launch(DGC_K_LAST, [&] { return surf(x, TY_MF, SURF_LAST, off[C - 1], off[C], in, ss, w.rhs, nullptr, &sa); });
     } else {
-      launch(DGC_K_VOLUME, [&] { return vol(x, TY_MF, in, ss, w.rhs); });
-      for (int k = 1; k <= C; ++k)
+      int k0 = 1;
+      if (first_fused(m)) {
+        launch(DGC_K_FIRST, [&] { return surf(x, TY_MF, SURF_FIRST, off[0], off[1], in, ss, w.rhs, nullptr, nullptr); });
+        k0 = 2;
+      }
+      launch(DGC_K_VOLUME, [&] { return vol(x, TY_MF, in, ss, w.rhs, k0 == 2 ? unreached(m) : 0); });
+      for (int k = k0; k <= C; ++k)
         launch(DGC_K_COLOR, [&] { return surf(x, TY_MF, SURF_RMW, off[k - 1], off[k], in, ss, w.rhs, nullptr, nullptr); });
       launch(DGC_K_STAGE, [&] { return incr_stage_update(x, static_cast<const float*>(w.rhs), sa); });
     }
@@ -457,6 +477,8 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->topo);
   cudaFree(m.dev->fgeo);
   cudaFree(m.dev->slots);
+  cudaFree(m.dev->perm);
+  cudaFree(m.dev->xfer);
   cudaFree(m.dev->ftab);
   cudaFree(m.dev->ftabd);
   cudaFree(m.dev->cfl_est);
@@ -512,6 +534,14 @@ dgc_status dgc_color_edges_naive(dgc_mesh* mesh, int renumber, int reorder_left,
     color_faces_naive(m);
     reorder(m, renumber != 0, reorder_left != 0);
     report_colors(m, n_colors, per_color);
+  });
+}
+
+dgc_status dgc_reorder(dgc_mesh* mesh, int renumber, int reorder_left) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    reorder(m, renumber != 0, reorder_left != 0);
   });
 }
 
@@ -643,6 +673,24 @@ dgc_status dgc_state_bytes(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes) 
   });
 }
 
+// Host <-> device state copies.  The element permutation runs on the device
+// (one pass over the state); a pinned (page-locked or registered) host buffer is
+// copied directly, any other goes through the mesh's pinned staging buffer with
+// one flat copy.
+static bool host_is_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+static double* xfer_of(Mesh& m) {
+  if (!m.dev->xfer) m.dev->xfer = dalloc<double>(m.ne * nv_of(m));
+  return m.dev->xfer;
+}
+
 dgc_status dgc_import_state(dgc_mesh* mesh, const double* c_host, double* c_dev, void* stream) {
   return guarded([&] {
     Mesh& m = checked(mesh);
@@ -650,14 +698,19 @@ dgc_status dgc_import_state(dgc_mesh* mesh, const double* c_host, double* c_dev,
     check_ptr(c_dev, "c_dev");
     require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
     upload(m);
-    double* stg = staging_for(m);
-    const int64_t nv = nv_of(m);
-    const int32_t* en = m.elem_new_of_old.data();
-    parallel_for(m.ne, [&](int64_t b, int64_t e) {
-      for (int64_t i = b; i < e; ++i) std::memcpy(stg + (int64_t)en[i] * nv, c_host + i * nv, sizeof(double) * nv);
-    });
+    double* x = xfer_of(m);
+    const int64_t S = state_bytes(m);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DGC_CUDA(cudaMemcpyAsync(c_dev, stg, state_bytes(m), cudaMemcpyHostToDevice, st));
+    if (host_is_pinned(c_host)) {
+      DGC_CUDA(cudaMemcpyAsync(x, c_host, S, cudaMemcpyHostToDevice, st));
+    } else {
+      double* stg = staging_for(m);
+      const int64_t n = m.ne * nv_of(m);
+      parallel_for(n, [&](int64_t b, int64_t e) { std::memcpy(stg + b, c_host + b, sizeof(double) * (e - b)); });
+      DGC_CUDA(cudaMemcpyAsync(x, stg, S, cudaMemcpyHostToDevice, st));
+    }
+    permute_blocks(st, c_dev, x, m.dev->perm, (int)nv_of(m), m.ne, true);
+    DGC_CUDA(cudaGetLastError());
     DGC_CUDA(cudaStreamSynchronize(st));
   });
 }
@@ -669,15 +722,21 @@ dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host,
     check_ptr(c_dev, "c_dev");
     require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
     upload(m);
-    double* stg = staging_for(m);
+    double* x = xfer_of(m);
+    const int64_t S = state_bytes(m);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DGC_CUDA(cudaMemcpyAsync(stg, c_dev, state_bytes(m), cudaMemcpyDeviceToHost, st));
-    DGC_CUDA(cudaStreamSynchronize(st));
-    const int64_t nv = nv_of(m);
-    const int32_t* en = m.elem_new_of_old.data();
-    parallel_for(m.ne, [&](int64_t b, int64_t e) {
-      for (int64_t i = b; i < e; ++i) std::memcpy(c_host + i * nv, stg + (int64_t)en[i] * nv, sizeof(double) * nv);
-    });
+    permute_blocks(st, x, c_dev, m.dev->perm, (int)nv_of(m), m.ne, false);
+    DGC_CUDA(cudaGetLastError());
+    if (host_is_pinned(c_host)) {
+      DGC_CUDA(cudaMemcpyAsync(c_host, x, S, cudaMemcpyDeviceToHost, st));
+      DGC_CUDA(cudaStreamSynchronize(st));
+    } else {
+      double* stg = staging_for(m);
+      DGC_CUDA(cudaMemcpyAsync(stg, x, S, cudaMemcpyDeviceToHost, st));
+      DGC_CUDA(cudaStreamSynchronize(st));
+      const int64_t n = m.ne * nv_of(m);
+      parallel_for(n, [&](int64_t b, int64_t e) { std::memcpy(c_host + b, stg + b, sizeof(double) * (e - b)); });
+    }
   });
 }
 

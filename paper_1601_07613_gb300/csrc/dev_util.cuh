@@ -72,7 +72,9 @@ static __device__ __noinline__ double f2d_any(float f) {
 // 0x0FFFFFFF plus the lowest kept bit to the 29 dropped bits rounds to nearest
 // even, the carry running into the exponent field (up to infinity); the
 // exponent is then rebiased by 1023 - 127.  binary32 -> binary64 for normal
-// inputs is a shift and a rebias.  Anything else goes to the calls above.
+// inputs is a shift and a rebias.  Signed zeros (frequent: uniform regions give
+// exact zero increments) are handled inline too.  Anything else goes to the
+// calls above.
 __device__ __forceinline__ float d2f(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned ed = (unsigned)(b >> 52) & 0x7FFu;
@@ -81,6 +83,7 @@ __device__ __forceinline__ float d2f(double x) {
     const unsigned mag = (unsigned)((t >> 29) & 0x3FFFFFFFFull) - (896u << 23);
     return __uint_as_float(mag | ((unsigned)(b >> 32) & 0x80000000u));
   }
+  if ((b << 1) == 0ull) return __uint_as_float((unsigned)(b >> 32));  // +-0
   return d2f_any(x);
 }
 
@@ -91,6 +94,7 @@ __device__ __forceinline__ double f2d(float f) {
     const unsigned long long bits = ((unsigned long long)(u & 0x7FFFFFFFu) << 29) + (896ull << 52);
     return __longlong_as_double((long long)(bits | ((unsigned long long)(u & 0x80000000u) << 32)));
   }
+  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // +-0
   return f2d_any(f);
 }
 

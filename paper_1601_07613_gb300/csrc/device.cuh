@@ -25,6 +25,8 @@ struct DeviceMesh {
   float* ftab = nullptr;    // 3D face tables (float copy)
   double* ftabd = nullptr;  // 3D face tables
   float* cfl_est = nullptr; // [E] FP32 step estimates of the CFL pre-pass, then 1 minimum
+  int32_t* perm = nullptr;  // [E] internal element id of each original element (import / export)
+  double* xfer = nullptr;   // [E][M*Np] state in original order (import / export; allocated on first use)
 };
 
 // Surface-kernel modes (Algorithm 1 and the comparators of Sec. 1).
@@ -110,7 +112,8 @@ int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, i
                double b0, SurfMode mode, bool mixed, int threads);
 int tri_record_floats(int p);
 // sstride: floats per element of an FP32 state (record or Kahan state); ignored for FP64 states
-int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs);
+// volume kernels cover elements [e0, ne)
+int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs, int64_t e0 = 0);
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
@@ -120,7 +123,7 @@ int tri_cfl_kahan(const Ctx& c, const float* kstate, double cfl, double* dt);
 // kernels_tet.cu
 void tet_upload_tables(int p, const RefTables& T, DeviceMesh& d);
 int tet_record_floats(int p);
-int tet_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs);
+int tet_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs, int64_t e0 = 0);
 int tet_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tet_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
@@ -129,5 +132,9 @@ int tet_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* sh
 int stage_update(const Ctx& c, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa);
 int incr_stage_update(const Ctx& c, const float* rhs, const StageArgs& sa);
 int gather_two_pass(const Ctx& c, bool f32, void* rhs, const void* buf);
+// element blocks of nv doubles between original and internal order:
+// to_internal: dst[perm[e]] = src[e]; else dst[e] = src[perm[e]]
+int permute_blocks(cudaStream_t st, double* dst, const double* src, const int32_t* perm, int nv, int64_t ne,
+                   bool to_internal);
 
 }  // namespace dgc

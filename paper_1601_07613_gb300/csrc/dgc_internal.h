@@ -67,6 +67,9 @@ struct Mesh {
   bool perfect = false;  // every element has exactly one face of each color
   std::vector<int8_t> color;  // original order
   std::vector<int32_t> elem_new_of_old, side_new_of_old, side_old_of_new, color_off;
+  // with the color-1 renumbering: elements [0, reached) are those color 1
+  // reaches (each exactly once); -1 without the renumbering
+  int64_t reached = -1;
   // options
   bool fuse = true;
   int edges_per_block = 64;

@@ -154,6 +154,9 @@ __device__ __forceinline__ void prefetch_epilogue(const void* rhs, const StageAr
 // Epilogue of the last color in increment form for element e, whose complete
 // FP32 right-hand side is L.  B holds the record the fluxes used (the record of
 // u0 at stage 0).  phi0 = the constant basis function.
+// Every branch issues its loads before its stores: the stores may alias what
+// is read (the same arrays), so the compiler keeps a load that follows a store
+// behind it, and a load-store-load sequence costs one memory round trip each.
 template <int M, int NP, typename Blk>
 __device__ __forceinline__ void incr_last(const StageArgs& S, int64_t e, const float (&L)[M * NP], const Blk& B,
                                           double phi0) {
@@ -162,23 +165,11 @@ __device__ __forceinline__ void incr_last(const StageArgs& S, int64_t e, const f
   const F2 dtp = split_f2(dt);
   float d[NV];
   float* dp = S.delta + e * NV;
-  if (S.stage == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) d[i] = mul_f2(L[i], dtp);
-  } else {
-    ldv<NV>(dp, d);
-    if (S.stage == 1) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) d[i] = 0.25f * (d[i] + mul_f2(L[i], dtp));
-    } else {  // delta_2 + dt L; b_2 = 2/3 is applied by the state update
-#pragma unroll
-      for (int i = 0; i < NV; ++i) d[i] = d[i] + mul_f2(L[i], dtp);
-    }
-  }
   if (S.stage < 2) {
-    stv<NV>(dp, d);
     float r[NF];
     if (S.stage == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) d[i] = mul_f2(L[i], dtp);
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         r[m] = B.hi[m];
@@ -187,7 +178,10 @@ __device__ __forceinline__ void incr_last(const StageArgs& S, int64_t e, const f
         for (int j = 0; j < NM; ++j) r[2 * M + m * NM + j] = B.cd[m][j];
       }
     } else {
+      ldv<NV>(dp, d);
       ld4<NF>(S.rec0 + e * S.rec0_stride, r);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) d[i] = 0.25f * (d[i] + mul_f2(L[i], dtp));
     }
     const F2 p0 = split_f2(phi0);
 #pragma unroll
@@ -198,8 +192,15 @@ __device__ __forceinline__ void incr_last(const StageArgs& S, int64_t e, const f
     }
 #pragma unroll
     for (int i = M * (NP + 1); i < NF; ++i) r[i] = 0.0f;
+    stv<NV>(dp, d);
     st4<NF>(S.rec_out + e * NF, r);
-  } else if (S.kstate) {
+    return;
+  }
+  // stage 2: delta_2 + dt L; b_2 = 2/3 is applied by the state update
+  ldv<NV>(dp, d);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) d[i] = d[i] + mul_f2(L[i], dtp);
+  if (S.kstate) {
     float* ks = S.kstate + e * S.rec0_stride;
     float r[NF], lo[LOM];
     ld4<NF>(ks, r);
@@ -214,12 +215,22 @@ __device__ __forceinline__ void incr_last(const StageArgs& S, int64_t e, const f
     st4<NF>(ks, r);
     st4<LOM>(ks + NF, lo);
   } else {
+    // FP64 state: u = u0 + (2/3) f64(d), in chunks of CH value pairs (all of a
+    // chunk's loads before its stores; u0 was prefetched into L2)
+    constexpr int H = NV / 2, CH = 5;
     const double2* u0 = reinterpret_cast<const double2*>(S.u0 + e * NV);
     double2* u = reinterpret_cast<double2*>(S.uout + e * NV);
 #pragma unroll
-    for (int i = 0; i < NV / 2; ++i) {
-      const double2 a = u0[i];
-      u[i] = make_double2(fma(2.0 / 3.0, f2d(d[2 * i]), a.x), fma(2.0 / 3.0, f2d(d[2 * i + 1]), a.y));
+    for (int c0 = 0; c0 < H; c0 += CH) {
+      double2 a[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+        if (c0 + i < H) a[i] = u0[c0 + i];
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+        if (c0 + i < H)
+          u[c0 + i] = make_double2(fma(2.0 / 3.0, f2d(d[2 * (c0 + i)]), a[i].x),
+                                   fma(2.0 / 3.0, f2d(d[2 * (c0 + i) + 1]), a[i].y));
     }
   }
 }

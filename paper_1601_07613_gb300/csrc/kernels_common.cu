@@ -98,4 +98,29 @@ int gather_two_pass(const Ctx& x, bool f32, void* rhs, const void* buf) {
   return 1;
 }
 
+// Element blocks between original and internal order, two doubles per thread
+// (nv is even): one pass over the state in each direction.
+__global__ void k_permute(double2* __restrict__ dst, const double2* __restrict__ src, const int32_t* __restrict__ perm,
+                          int nv2, int64_t n, bool to_internal) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = i / nv2;
+  const int v = (int)(i - e * nv2);
+  const int64_t pe = perm[e];
+  if (to_internal) dst[pe * nv2 + v] = src[i];
+  else dst[i] = src[pe * nv2 + v];
+}
+
+int permute_blocks(cudaStream_t st, double* dst, const double* src, const int32_t* perm, int nv, int64_t ne,
+                   bool to_internal) {
+  const int nv2 = nv / 2;
+  const int64_t n = ne * nv2;
+  const int bs = 256;
+  if (n <= 0) return 0;
+  k_permute<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(reinterpret_cast<double2*>(dst),
+                                                         reinterpret_cast<const double2*>(src), perm, nv2, n,
+                                                         to_internal);
+  return 1;
+}
+
 }  // namespace dgc

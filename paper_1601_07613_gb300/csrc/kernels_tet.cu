@@ -281,9 +281,10 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
 }
 
 template <int P, typename CT, typename ST, typename RT>
-__global__ void __launch_bounds__(128) k_vol_tet(const ST* c, int sstride, const double* jinv, RT* rhs, int64_t ne) {
+__global__ void __launch_bounds__(128) k_vol_tet(const ST* c, int sstride, const double* jinv, RT* rhs, int64_t e0,
+                                                 int64_t ne) {
   using D = TetDim<P>;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   RT out[D::NV];
   if constexpr (sizeof(CT) == 8) {
@@ -349,28 +350,43 @@ __device__ __forceinline__ void tet_write(const TetParams& A, int64_t elem, int6
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
     tstore(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
-  } else {  // SURF_LAST, FP64 form: FP64 stage update, two values at a time (see the triangle kernel)
-    static_assert(sizeof(RT) == 8, "the FP32 forms finish the step in incr_last");
-    const RT* part = static_cast<const RT*>(A.rhs) + elem * NV;
-    const double2* us2 = reinterpret_cast<const double2*>(static_cast<const double*>(A.state) + elem * NV);
-    const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
-    double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
-    const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
+  }
+}
+
+// Last color, FP64 form (as fp64_last for triangles): us = the state block the
+// fluxes used (registers); chunks of CH value pairs, loads before stores.
+template <int P>
+__device__ __forceinline__ void tet_fp64_last(const TetParams& A, int64_t elem, const double (&acc)[TetDim<P>::NV],
+                                              const double (&us)[TetDim<P>::NV]) {
+  constexpr int NV = TetDim<P>::NV, H = NV / 2, CH = 5;
+  const double2* part = reinterpret_cast<const double2*>(static_cast<const double*>(A.rhs) + elem * NV);
+  const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
+  double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
+  const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
 #pragma unroll
-    for (int i = 0; i < NV; i += 2) {
-      const double2 s = us2[i / 2];
-      const double L0 = widen(part[i] + (RT)acc[i]), L1 = widen(part[i + 1] + (RT)acc[i + 1]);
-      double v[2];
-      if (a0 == 0.0) {
-        v[0] = fma(bdt, L0, b0 == 1.0 ? s.x : b0 * s.x);
-        v[1] = fma(bdt, L1, b0 == 1.0 ? s.y : b0 * s.y);
-      } else {
-        const double2 u = u02[i / 2];
-        v[0] = fma(bdt, L0, fma(a0, u.x, b0 * s.x));
-        v[1] = fma(bdt, L1, fma(a0, u.y, b0 * s.y));
+  for (int c0 = 0; c0 < H; c0 += CH) {
+    double2 pr[CH], u[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (c0 + i < H) {
+        pr[i] = part[c0 + i];
+        if (a0 != 0.0) u[i] = u02[c0 + i];
       }
-      out2[i / 2] = make_double2(v[0], v[1]);
-    }
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (c0 + i < H) {
+        const int v = 2 * (c0 + i);
+        const double L0 = pr[i].x + acc[v], L1 = pr[i].y + acc[v + 1];
+        double w0, w1;
+        if (a0 == 0.0) {
+          w0 = fma(bdt, L0, b0 == 1.0 ? us[v] : b0 * us[v]);
+          w1 = fma(bdt, L1, b0 == 1.0 ? us[v + 1] : b0 * us[v + 1]);
+        } else {
+          w0 = fma(bdt, L0, fma(a0, u[i].x, b0 * us[v]));
+          w1 = fma(bdt, L1, fma(a0, u[i].y, b0 * us[v + 1]));
+        }
+        out2[c0 + i] = make_double2(w0, w1);
+      }
   }
 }
 
@@ -437,7 +453,11 @@ __global__ void __launch_bounds__(256) k_surf_tet(const TetParams A) {
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
     }
-    if (writer) tet_write<P, RT, MODE>(A, elem, k, side, acc);
+    if constexpr (MODE == SURF_LAST) {
+      if (writer) tet_fp64_last<P>(A, elem, acc, c);
+    } else if (writer) {
+      tet_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
   } else {
     const TetTab<float, P>& K = tet_tab<float, P>();
     const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
@@ -554,39 +574,68 @@ __global__ void __launch_bounds__(128) k_cfl1_tet(const double* c, const double*
   block_min_to(best, minbits);
 }
 
+// Pass 2: each candidate is evaluated in FP64 by the whole warp, one volume
+// point per lane (a GB300 FP64 warp instruction occupies the FP64 pipe for ~64
+// cycles, so one lane running every point would take tens of microseconds).
 template <int P>
 __global__ void __launch_bounds__(128) k_cfl2_tet(const double* c, const double* inr, int64_t ne, double cfl,
                                                   const float* est, const unsigned* minbits,
                                                   unsigned long long* dtbits) {
   using D = TetDim<P>;
+  constexpr int NP = D::NP;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool cand = e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin);
+  unsigned mask = __ballot_sync(0xffffffffu, cand);
   double best = DBL_MAX;
-  if (e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin)) {
+  const TetTab<double, P>& K = tet_tab<double, P>();
+  while (mask) {
+    const int src = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const long long ec = __shfl_sync(0xffffffffu, (long long)e, src);
     double v[D::NV];
-    tload(c + e * D::NV, v);
-    best = cfl * (inr[e] / ((2 * P + 1) * tet_lambda_max<P, double>(v)));
-    if (!(best > 0.0)) best = DBL_MAX;
+    tload(c + ec * D::NV, v);
+    double lam = 0.0;
+    for (int q = threadIdx.x & 31; q < D::NQV; q += 32) {
+      double U[5];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        double sum = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) sum += K.phiV[q][j] * v[m * NP + j];
+        U[m] = sum;
+      }
+      const double ir = 1.0 / U[0], u = U[1] * ir, w = U[2] * ir, z = U[3] * ir;
+      const double q2 = u * u + w * w + z * z;
+      const double pr = 0.4 * (U[4] - 0.5 * U[0] * q2);
+      lam = fmax(lam, sqrt(q2) + sqrt(1.4 * pr * ir));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+    const double b = cfl * (inr[ec] / ((2 * P + 1) * lam));
+    if ((threadIdx.x & 31) == src) best = b > 0.0 ? b : DBL_MAX;
   }
   block_min_to(best, dtbits);
 }
 
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
-static int tvol_p(const Ctx& x, const void* s, int ss, void* r) {
+static int tvol_p(const Ctx& x, const void* s, int ss, void* r, int64_t e0) {
   const int bs = 128;
-  k_vol_tet<P, CT, ST, RT><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(
-      static_cast<const ST*>(s), ss, x.d->jinv, static_cast<RT*>(r), x.ne);
+  const int64_t n = x.ne - e0;
+  if (n <= 0) return 0;
+  k_vol_tet<P, CT, ST, RT><<<(unsigned)((n + bs - 1) / bs), bs, 0, x.st>>>(
+      static_cast<const ST*>(s), ss, x.d->jinv, static_cast<RT*>(r), e0, x.ne);
   return 1;
 }
 
-int tet_volume(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r) {
+int tet_volume(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r, int64_t e0) {
   switch (x.p * 4 + ty) {
-    case 4 + TY_D: return tvol_p<1, double, double, double>(x, s, ss, r);
-    case 8 + TY_D: return tvol_p<2, double, double, double>(x, s, ss, r);
-    case 4 + TY_MD: return tvol_p<1, float, double, double>(x, s, ss, r);
-    case 8 + TY_MD: return tvol_p<2, float, double, double>(x, s, ss, r);
-    case 4 + TY_MF: return tvol_p<1, float, float, float>(x, s, ss, r);
-    case 8 + TY_MF: return tvol_p<2, float, float, float>(x, s, ss, r);
+    case 4 + TY_D: return tvol_p<1, double, double, double>(x, s, ss, r, e0);
+    case 8 + TY_D: return tvol_p<2, double, double, double>(x, s, ss, r, e0);
+    case 4 + TY_MD: return tvol_p<1, float, double, double>(x, s, ss, r, e0);
+    case 8 + TY_MD: return tvol_p<2, float, double, double>(x, s, ss, r, e0);
+    case 4 + TY_MF: return tvol_p<1, float, float, float>(x, s, ss, r, e0);
+    case 8 + TY_MF: return tvol_p<2, float, float, float>(x, s, ss, r, e0);
     default: return -1;
   }
 }

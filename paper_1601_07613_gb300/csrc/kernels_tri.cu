@@ -14,6 +14,7 @@
 //
 // FP64 kernels evaluate Eq. 2 as written.  FP32 kernels evaluate it in the
 // perturbation form of euler_pert.cuh (deviations from the element mean).
+#include <algorithm>
 #include <cfloat>
 #include <type_traits>
 
@@ -332,9 +333,9 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
 __global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, int sstride, const double* __restrict__ jinv,
-                                                 RT* __restrict__ rhs, int64_t ne) {
+                                                 RT* __restrict__ rhs, int64_t e0, int64_t ne) {
   using D = TriDim<P>;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   RT out[D::NV];
   if constexpr (sizeof(CT) == 8) {
@@ -404,30 +405,46 @@ __device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, in
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
     store_block(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
-  } else {  // SURF_LAST, FP64 form: L = partial rhs + this color; FP64 stage update
-    // uout = a0 u0 + b0 us + (b0 dt) L, two values at a time:
-    // 1 FMA per value in the first stage, 1 MUL + 2 FMA in the others
-    static_assert(sizeof(RT) == 8, "the FP32 forms finish the step in incr_last");
-    const RT* part = static_cast<const RT*>(A.rhs) + elem * NV;
-    const double2* us2 = reinterpret_cast<const double2*>(static_cast<const double*>(A.state) + elem * NV);
-    const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
-    double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
-    const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
+  }
+}
+
+// Last color, FP64 form: L = partial rhs + this color, uout = a0 u0 + b0 us +
+// (b0 dt) L (1 FMA per value in the first stage, 1 MUL + 2 FMA in the
+// others).  us is the state block the fluxes used (in registers).  In chunks
+// of CH value pairs, every chunk's loads before its stores (uout may alias us
+// and u0, so the compiler keeps later loads behind earlier stores).
+template <int P>
+__device__ __forceinline__ void fp64_last(const SurfParams& A, int64_t elem, const double (&acc)[TriDim<P>::NV],
+                                          const double (&us)[TriDim<P>::NV]) {
+  constexpr int NV = TriDim<P>::NV, H = NV / 2, CH = 5;
+  const double2* part = reinterpret_cast<const double2*>(static_cast<const double*>(A.rhs) + elem * NV);
+  const double2* u02 = reinterpret_cast<const double2*>(A.sa.u0 + elem * NV);
+  double2* out2 = reinterpret_cast<double2*>(A.sa.uout + elem * NV);
+  const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
 #pragma unroll
-    for (int i = 0; i < NV; i += 2) {
-      const double2 s = us2[i / 2];
-      const double L0 = widen(part[i] + (RT)acc[i]), L1 = widen(part[i + 1] + (RT)acc[i + 1]);
-      double v[2];
-      if (a0 == 0.0) {
-        v[0] = fma(bdt, L0, b0 == 1.0 ? s.x : b0 * s.x);
-        v[1] = fma(bdt, L1, b0 == 1.0 ? s.y : b0 * s.y);
-      } else {
-        const double2 u = u02[i / 2];
-        v[0] = fma(bdt, L0, fma(a0, u.x, b0 * s.x));
-        v[1] = fma(bdt, L1, fma(a0, u.y, b0 * s.y));
+  for (int c0 = 0; c0 < H; c0 += CH) {
+    double2 pr[CH], u[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (c0 + i < H) {
+        pr[i] = part[c0 + i];
+        if (a0 != 0.0) u[i] = u02[c0 + i];
       }
-      out2[i / 2] = make_double2(v[0], v[1]);
-    }
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (c0 + i < H) {
+        const int v = 2 * (c0 + i);
+        const double L0 = pr[i].x + acc[v], L1 = pr[i].y + acc[v + 1];
+        double w0, w1;
+        if (a0 == 0.0) {
+          w0 = fma(bdt, L0, b0 == 1.0 ? us[v] : b0 * us[v]);
+          w1 = fma(bdt, L1, b0 == 1.0 ? us[v + 1] : b0 * us[v + 1]);
+        } else {
+          w0 = fma(bdt, L0, fma(a0, u[i].x, b0 * us[v]));
+          w1 = fma(bdt, L1, fma(a0, u[i].y, b0 * us[v + 1]));
+        }
+        out2[c0 + i] = make_double2(w0, w1);
+      }
   }
 }
 
@@ -446,14 +463,16 @@ __device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw, int ntab = 3
 // Lanes with valid = false shadow a real edge (so both lanes of every pair
 // take part in the shuffles) and write nothing.
 template <int P, typename CT, typename ST, typename RT, int MODE>
-__device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool valid, int side, const CT* sphi,
-                                          const CT* sw);
+__device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
+                                          const CT* sphi, const CT* sw);
+
 
 // FP32 surface kernels: minimum resident blocks of 256 threads the compiler
-// must allow per SM (register cap 65536 / (256 * min)); 1 leaves the register
-// count free.  FP64 kernels are never capped.
+// must allow per SM (register cap 65536 / (256 * min)).  2 caps them at 128
+// registers (a few spills) for 16 resident warps per SM instead of 12; measured
+// 4-7% faster than no cap at p = 3.  FP64 kernels are never capped.
 #ifndef DGC_SURF_MINB
-#define DGC_SURF_MINB 1
+#define DGC_SURF_MINB 2
 #endif
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
@@ -463,19 +482,20 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_SURF_MINB : 1)) k_
   __shared__ CT sw[D::NQE];
   stage_edge_tables<P, CT>(sphi, sw, A.ntab);
   __syncthreads();
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t k = A.begin + (t >> 1);
+  const int side = threadIdx.x & 1;
+  int64_t k = A.begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1);
   const bool valid = k < A.end;
   if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
-  surf_pair<P, CT, ST, RT, MODE>(A, k, valid, (int)(t & 1), sphi, sw);
+  const int4 tp = A.topo[k];
+  if (valid) prefetch_epilogue<MODE, TriDim<P>::NV, TriDim<P>::NF, RT>(A.rhs, A.sa, side && tp.y >= 0 ? tp.y : tp.x);
+  surf_pair<P, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
 }
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
-__device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool valid, int side, const CT* sphi,
-                                          const CT* sw) {
+__device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
+                                          const CT* sphi, const CT* sw) {
   using D = TriDim<P>;
   constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV;
-  const int4 tp = A.topo[k];
   const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
   const bool right = side && !bnd;
   const int64_t elem = right ? tp.y : tp.x;
@@ -485,7 +505,6 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool v
   const CT* ph = sphi + le * NQ * NP;
   // (in SURF_LAST the state may alias the stage output, but each element's
   // block is read and written by its own lane only)
-  if (writer) prefetch_epilogue<MODE, NV, D::NF, RT>(A.rhs, A.sa, elem);
 
   if constexpr (sizeof(CT) == 8) {
     // ---------------- FP64: Eq. 2 as written ----------------
@@ -524,7 +543,11 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, bool v
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
     }
-    if (writer) surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    if constexpr (MODE == SURF_LAST) {
+      if (writer) fp64_last<P>(A, elem, acc, c);
+    } else if (writer) {
+      surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
   } else {
     // ---------------- FP32: perturbation form ----------------
     const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
@@ -624,6 +647,35 @@ __device__ __forceinline__ T lambda_max(const T (&v)[TriDim<P>::NV]) {
   return lam;
 }
 
+// The same FP64 maximum evaluated by the whole warp for one element (lane q
+// takes the points q, q + 32, ...), valid in every lane.  A GB300 FP64 warp
+// instruction occupies the FP64 pipe for ~64 cycles, so one lane alone running
+// all points would take tens of microseconds.
+template <int P>
+__device__ __forceinline__ double lambda_max_warp(const double (&v)[TriDim<P>::NV]) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP;
+  const TriTab<double, P>& K = tri_tab<double, P>();
+  double lam = 0.0;
+  for (int q = threadIdx.x & 31; q < D::NQV; q += 32) {
+    double U[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * v[m * NP + j];
+      U[m] = s;
+    }
+    const double ir = 1.0 / U[0], u = U[1] * ir, w = U[2] * ir;
+    const double q2 = u * u + w * w;
+    const double pr = 0.4 * (U[3] - 0.5 * U[0] * q2);
+    lam = fmax(lam, sqrt(q2) + sqrt(1.4 * pr * ir));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  return lam;
+}
+
 // FP32 estimate of max_q (|u| + c) from the FP32 record (mean pair + modes)
 template <int P>
 __device__ __forceinline__ float lambda_max_rec(const float (&r)[TriDim<P>::NF]) {
@@ -641,10 +693,10 @@ __device__ __forceinline__ float lambda_max_rec(const float (&r)[TriDim<P>::NF])
       for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[8 + m * (NP - 1) + j - 1];
       U[m] = r[m] + s;
     }
-    const float ir = 1.0f / U[0], u = U[1] * ir, w = U[2] * ir;
+    const float ir = rcp_fast(U[0]), u = U[1] * ir, w = U[2] * ir;
     const float q2 = u * u + w * w;
     const float pr = 0.4f * (U[3] - 0.5f * U[0] * q2);
-    lam = fmaxf(lam, sqrtf(q2) + sqrtf(1.4f * pr * ir));
+    lam = fmaxf(lam, sqrt_fast(q2) + sqrt_fast(1.4f * pr * ir));
   }
   return lam;
 }
@@ -665,16 +717,40 @@ __device__ __forceinline__ float cfl1_elem(const double* __restrict__ c, const d
   return d;
 }
 
-// pass 2 for element e: the FP64 step if e is a candidate, else DBL_MAX
-template <int P>
-__device__ __forceinline__ double cfl2_elem(const double* __restrict__ c, const double* __restrict__ inr, int64_t e,
-                                            double cfl, const float* __restrict__ est, float minest) {
+// Pass 2 for the warp's elements e (e < 0: none): the FP64 step of each
+// candidate (estimate within kCflMargin of the minimum), evaluated one
+// candidate at a time by the whole warp; DBL_MAX for the others.  All 32 lanes
+// must call it.  KAHAN: the state is the FP32 pair layout (values hi + lo, the
+// mean as phi0 c0), else FP64 coefficients.
+template <int P, bool KAHAN>
+__device__ __forceinline__ double cfl2_warp(const void* __restrict__ state, const double* __restrict__ inr,
+                                            int64_t e, double cfl, const float* __restrict__ est, float minest) {
   using D = TriDim<P>;
-  if (!(est[e] <= minest * (1.0f + kCflMargin))) return DBL_MAX;
-  double v[D::NV];
-  load_block(c + e * D::NV, v);
-  const double best = cfl * (__ldg(inr + e) / ((2 * P + 1) * lambda_max<P, double>(v)));
-  return best > 0.0 ? best : DBL_MAX;  // non-physical state: excluded (NaN)
+  constexpr int NP = D::NP, NM = NP - 1;
+  const bool cand = e >= 0 && est[e] <= minest * (1.0f + kCflMargin);
+  unsigned mask = __ballot_sync(0xffffffffu, cand);
+  double best = DBL_MAX;
+  while (mask) {
+    const int src = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const long long ec = __shfl_sync(0xffffffffu, (long long)e, src);
+    double v[D::NV];
+    if constexpr (KAHAN) {
+      const float* k = static_cast<const float*>(state) + ec * (8 * NP);
+      const double phi0 = tri_tab<double, P>().phiV[0][0];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        v[m * NP] = (f2d(k[m]) + f2d(k[4 + m])) / phi0;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) v[m * NP + 1 + j] = f2d(k[8 + m * NM + j]) + f2d(k[D::NF + m * NM + j]);
+      }
+    } else {
+      load_block(static_cast<const double*>(state) + ec * D::NV, v);
+    }
+    const double b = cfl * (__ldg(inr + ec) / ((2 * P + 1) * lambda_max_warp<P>(v)));
+    if ((threadIdx.x & 31) == src) best = b > 0.0 ? b : DBL_MAX;  // non-physical state: excluded (NaN)
+  }
+  return best;
 }
 
 template <int P>
@@ -686,12 +762,12 @@ __global__ void __launch_bounds__(128) k_cfl1_tri(const double* __restrict__ c, 
   block_min_to(best, minbits);
 }
 
-template <int P>
-__global__ void __launch_bounds__(128) k_cfl2_tri(const double* __restrict__ c, const double* __restrict__ inr,
+template <int P, bool KAHAN>
+__global__ void __launch_bounds__(128) k_cfl2_tri(const void* __restrict__ c, const double* __restrict__ inr,
                                                   int64_t ne, double cfl, const float* __restrict__ est,
                                                   const unsigned* minbits, unsigned long long* dtbits) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double best = e < ne ? cfl2_elem<P>(c, inr, e, cfl, est, __uint_as_float(*minbits)) : DBL_MAX;
+  const double best = cfl2_warp<P, KAHAN>(c, inr, e < ne ? e : -1, cfl, est, __uint_as_float(*minbits));
   block_min_to(best, dtbits);
 }
 
@@ -716,30 +792,6 @@ __global__ void __launch_bounds__(128) k_cfl1_tri_k(const float* __restrict__ ks
   block_min_to(best, minbits);
 }
 
-template <int P>
-__global__ void __launch_bounds__(128) k_cfl2_tri_k(const float* __restrict__ ks, const double* __restrict__ inr,
-                                                    int64_t ne, double cfl, const float* __restrict__ est,
-                                                    const unsigned* minbits, unsigned long long* dtbits) {
-  using D = TriDim<P>;
-  constexpr int NP = D::NP, NM = NP - 1;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double best = DBL_MAX;
-  if (e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin)) {
-    const float* k = ks + e * (8 * NP);
-    const double phi0 = tri_tab<double, P>().phiV[0][0];
-    double v[D::NV];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      v[m * NP] = (f2d(k[m]) + f2d(k[4 + m])) / phi0;
-#pragma unroll
-      for (int j = 0; j < NM; ++j) v[m * NP + 1 + j] = f2d(k[8 + m * NM + j]) + f2d(k[D::NF + m * NM + j]);
-    }
-    const double b = cfl * (__ldg(inr + e) / ((2 * P + 1) * lambda_max<P, double>(v)));
-    best = b > 0.0 ? b : DBL_MAX;
-  }
-  block_min_to(best, dtbits);
-}
-
 int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
   const int bs = 128;
   const unsigned grid = (unsigned)((x.ne + bs - 1) / bs);
@@ -750,15 +802,15 @@ int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
   switch (x.p) {
     case 1:
       k_cfl1_tri_k<1><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
-      k_cfl2_tri_k<1><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      k_cfl2_tri<1, true><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
       k_cfl1_tri_k<2><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
-      k_cfl2_tri_k<2><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      k_cfl2_tri<2, true><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 3:
       k_cfl1_tri_k<3><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
-      k_cfl2_tri_k<3><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      k_cfl2_tri<3, true><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }
@@ -824,9 +876,10 @@ __global__ void __launch_bounds__(256) k_batch_surf(const BatchMeshDev* __restri
     const bool valid = k < T.end;
     if (!valid) k = T.end - 1;
     const int side = threadIdx.x & 1;
-    if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, valid, side, sphi, sw);
-    else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, valid, side, sphi, sw);
-    else surf_pair<3, CT, ST, RT, MODE>(A, k, valid, side, sphi, sw);
+    const int4 tp = A.topo[k];
+    if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+    else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+    else surf_pair<3, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
   }
 }
 
@@ -862,14 +915,12 @@ __global__ void __launch_bounds__(128) k_batch_cfl2(const BatchMeshDev* __restri
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const BatchTile T = tiles[ti];
     const BatchMeshDev& B = meshes[T.mesh];
-    const int64_t e = T.begin + threadIdx.x;
-    double best = DBL_MAX;
-    if (e < T.end) {
-      const float mn = __uint_as_float(*reinterpret_cast<const unsigned*>(B.est + B.ne));
-      if (T.p == 1) best = cfl2_elem<1>(B.c, B.inr, e, cfl, B.est, mn);
-      else if (T.p == 2) best = cfl2_elem<2>(B.c, B.inr, e, cfl, B.est, mn);
-      else best = cfl2_elem<3>(B.c, B.inr, e, cfl, B.est, mn);
-    }
+    const int64_t e = T.begin + threadIdx.x < T.end ? T.begin + threadIdx.x : -1;
+    const float mn = __uint_as_float(*reinterpret_cast<const unsigned*>(B.est + B.ne));
+    double best;
+    if (T.p == 1) best = cfl2_warp<1, false>(B.c, B.inr, e, cfl, B.est, mn);
+    else if (T.p == 2) best = cfl2_warp<2, false>(B.c, B.inr, e, cfl, B.est, mn);
+    else best = cfl2_warp<3, false>(B.c, B.inr, e, cfl, B.est, mn);
     block_min_to(best, reinterpret_cast<unsigned long long*>(B.dt));
     __syncthreads();
   }
@@ -926,30 +977,31 @@ int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, i
 // launchers
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
-static int vol_p(const Ctx& x, const void* s, int sstride, void* r) {
+static int vol_p(const Ctx& x, const void* s, int sstride, void* r, int64_t e0) {
   const int bs = 128;
-  const int64_t grid = (x.ne + bs - 1) / bs;
-  k_vol_tri<P, CT, ST, RT><<<(unsigned)grid, bs, 0, x.st>>>(static_cast<const ST*>(s), sstride, x.d->jinv,
-                                                             static_cast<RT*>(r), x.ne);
+  const int64_t n = x.ne - e0;
+  if (n <= 0) return 0;
+  k_vol_tri<P, CT, ST, RT><<<(unsigned)((n + bs - 1) / bs), bs, 0, x.st>>>(static_cast<const ST*>(s), sstride,
+                                                                          x.d->jinv, static_cast<RT*>(r), e0, x.ne);
   return 1;
 }
 
 template <int P>
-static int vol_ty(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r) {
+static int vol_ty(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r, int64_t e0) {
   switch (ty) {
-    case TY_D: return vol_p<P, double, double, double>(x, s, ss, r);
-    case TY_MD: return vol_p<P, float, double, double>(x, s, ss, r);
-    case TY_MF: return vol_p<P, float, float, float>(x, s, ss, r);
-    case TY_KD: return vol_p<P, float, float, double>(x, s, ss, r);
+    case TY_D: return vol_p<P, double, double, double>(x, s, ss, r, e0);
+    case TY_MD: return vol_p<P, float, double, double>(x, s, ss, r, e0);
+    case TY_MF: return vol_p<P, float, float, float>(x, s, ss, r, e0);
+    case TY_KD: return vol_p<P, float, float, double>(x, s, ss, r, e0);
     default: return -1;
   }
 }
 
-int tri_volume(const Ctx& x, TypeCfg ty, const void* s, int sstride, void* r) {
+int tri_volume(const Ctx& x, TypeCfg ty, const void* s, int sstride, void* r, int64_t e0) {
   switch (x.p) {
-    case 1: return vol_ty<1>(x, ty, s, sstride, r);
-    case 2: return vol_ty<2>(x, ty, s, sstride, r);
-    case 3: return vol_ty<3>(x, ty, s, sstride, r);
+    case 1: return vol_ty<1>(x, ty, s, sstride, r, e0);
+    case 2: return vol_ty<2>(x, ty, s, sstride, r, e0);
+    case 3: return vol_ty<3>(x, ty, s, sstride, r, e0);
     default: return -1;
   }
 }
@@ -1028,15 +1080,15 @@ int tri_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow
   switch (x.p) {
     case 1:
       k_cfl1_tri<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tri<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      k_cfl2_tri<1, false><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
       k_cfl1_tri<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tri<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      k_cfl2_tri<2, false><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 3:
       k_cfl1_tri<3><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tri<3><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      k_cfl2_tri<3, false><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }

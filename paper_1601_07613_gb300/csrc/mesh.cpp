@@ -731,10 +731,12 @@ void reorder(Mesh& m, bool renumber, bool reorder_left) {
       int32_t r = m.sr[order[i]];
       if (r >= 0 && en[r] < 0) en[r] = id++;
     }
+    m.reached = id;
     for (int64_t e = 0; e < m.ne; ++e)
       if (en[e] < 0) en[e] = id++;
   } else {
     std::iota(en.begin(), en.end(), 0);
+    m.reached = -1;
   }
   if (reorder_left) {
     for (int c = 2; c <= nc; ++c)

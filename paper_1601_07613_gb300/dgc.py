@@ -41,6 +41,7 @@ SIGNATURES = {
     "dgc_mesh_info": (C.c_int, [_P, _I64P]),
     "dgc_get_sides": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]),
     "dgc_refine": (C.c_int, [_P, _I64, _I32P]),
+    "dgc_reorder": (C.c_int, [_P, C.c_int, C.c_int]),
     "dgc_get_hanging": (C.c_int, [_P, C.POINTER(C.c_int8)]),
     "dgc_get_elements": (C.c_int, [_P, _I32P, _DP]),
     "dgc_get_ordering": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), _I32P]),
@@ -175,6 +176,10 @@ def dgc_get_sides(mesh):
     _check(lib().dgc_get_sides(mesh, *(x.ctypes.data_as(_I32P) for x in (l, r)),
                                *(x.ctypes.data_as(C.POINTER(C.c_int8)) for x in (ql, qr))))
     return l, r, ql, qr
+
+
+def dgc_reorder(mesh, renumber: bool, reorder_left: bool):
+    _check(lib().dgc_reorder(mesh, int(renumber), int(reorder_left)))
 
 
 def dgc_refine(mesh, elems):

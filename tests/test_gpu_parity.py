@@ -372,3 +372,92 @@ def test_fp32_records_of_the_mixed_step(torch_dev):
     assert torch.all(torch.abs(got2 - mean2) <= 2.0 ** -46 * torch.abs(mean2))
     assert delta.abs().max() > 0
     run.close()
+
+
+def test_fp32_record_conversion_special_values(torch_dev):
+    """The record writer converts FP64 modes to FP32 with integer operations
+    (fast path for normal results and zeros, an out-of-line path for the rest).
+    With special values placed in the modes (the CFL pass writes rec0 before
+    any stage), every converted mode must equal the hardware round-to-nearest
+    conversion bit for bit, NaN payload aside."""
+    torch, dev = torch_dev
+    mi = W.periodic_square_tri(12, jitter=0.2, seed=12)
+    run = Run(torch_dev, mi, 2)
+    E, M, NP = run.m.info["ne"], 4, run.m.info["np"]
+    c = state_for(mi, NP, seed=3)
+    specials = np.array([0.0, -0.0, 1e-40, -3e-42, 1.4e-45, 7e-46, 1e-50, -1e-300, 1.0 + 2.0 ** -24,
+                         1.0 + 3 * 2.0 ** -24, 1.0 - 2.0 ** -25, 3.4028235e38, 3.4028236e38, -3.5e38, 1e300,
+                         np.inf, -np.inf, np.nan, 1.1754943508222875e-38, 1.1754942e-38, 5.877471754111438e-39,
+                         2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -151, 123.456, -7.25e-20])
+    vals = np.resize(specials, (E, M, NP - 1))
+    c[:, :, 1:] = vals
+    run.load(c)
+    ws = torch.zeros(dgc.dgc_workspace_size(run.m.h, dgc.DGC_FP32_MIXED) // 8 + 64, dtype=torch.float64, device=dev)
+    d = torch.zeros(1, dtype=torch.float64, device=dev)
+    u0 = run.c.clone()
+    dgc.dgc_rk_step(run.m.h, dgc.DGC_FP32_MIXED, run.c, 0.3, d, ws)
+    torch.cuda.synchronize()
+    nrec = M * (NP + 1)
+    rec0 = ws.view(torch.uint8)[:4 * E * nrec].view(torch.float32).reshape(E, nrec)
+    got = rec0[:, 2 * M:].reshape(E, M, NP - 1)
+    want = u0[:, :, 1:].float()
+    nan = torch.isnan(want)
+    assert torch.equal(torch.isnan(got), nan)
+    assert torch.equal(got[~nan].view(torch.int32), want[~nan].view(torch.int32))
+    run.close()
+
+
+@pytest.mark.parametrize("renumber", [True, False])
+@pytest.mark.parametrize("prec,tol", [(dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)])
+def test_naive_five_colors_match_oracle(torch_dev, oracle_mod, renumber, prec, tol):
+    """The naive greedy's 5 colors (Table 7): no element has every color, so the
+    first color carries the volume integral only for the elements it reaches
+    (after the color-1 renumbering; a volume kernel covers the rest), or the
+    plain volume + colors sequence runs (without it)."""
+    mi = W.periodic_square_tri(24, jitter=0.2, seed=13)
+    ev = mi.ev[np.random.default_rng(2).permutation(mi.ne)]
+    torch, dev = torch_dev
+    m = dgc.Mesh(2, 2, mi.xyz, ev, mi.periodic_len)
+    nc, _ = dgc.dgc_color_edges_naive(m.h, renumber, True)
+    assert nc > 3
+    om = oracle_mod.OracleMesh(2, mi.xyz, ev, mi.periodic_len)
+    c = state_for(mi, 6, seed=4)
+    ref_rhs = om.rhs(2, c)
+    ref, dt_ref = om.rk_step(2, c, 0.3)
+    cd = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    r = torch.empty_like(cd)
+    dgc.dgc_import_state(m.h, c, cd)
+    dgc.dgc_rhs(m.h, prec, cd, r)
+    torch.cuda.synchronize()
+    assert rel(dgc.dgc_export_state(m.h, r), ref_rhs) < (1e-12 if prec == dgc.DGC_FP64 else 1e-5)
+    ws = torch.empty(dgc.dgc_workspace_size(m.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
+    d = torch.zeros(1, dtype=torch.float64, device=dev)
+    dgc.dgc_rk_step(m.h, prec, cd, 0.3, d, ws)
+    torch.cuda.synchronize()
+    got = dgc.dgc_export_state(m.h, cd)
+    assert abs(d.item() - dt_ref) < 1e-13 * dt_ref
+    assert rel(got - c, ref - c) < tol
+    m.close()
+
+
+def test_import_export_pinned_and_pageable(torch_dev):
+    """State copies permute on the device; pinned host buffers are copied
+    directly, pageable ones through the staging buffer.  Both round-trip
+    exactly, and the device holds host element i at its internal id."""
+    torch, dev = torch_dev
+    mi = W.periodic_square_tri(19, jitter=0.2, seed=14)
+    run = Run(torch_dev, mi, 3)
+    c = state_for(mi, run.m.info["np"], seed=6)
+    pinned = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
+    pinned[...] = c
+    dgc.dgc_import_state(run.m.h, pinned, run.c)
+    en = dgc.dgc_get_ordering(run.m.h)[0]
+    assert np.array_equal(run.c.cpu().numpy()[en], c)
+    back = dgc.dgc_export_state(run.m.h, run.c)  # pageable
+    assert np.array_equal(back, c)
+    outp = torch.empty(c.shape, dtype=torch.float64, pin_memory=True).numpy()
+    dgc.dgc_export_state(run.m.h, run.c, outp)
+    assert np.array_equal(outp, c)
+    dgc.dgc_import_state(run.m.h, np.ascontiguousarray(c[::-1][::-1]), run.c)  # pageable in
+    assert np.array_equal(run.c.cpu().numpy()[en], c)
+    run.close()

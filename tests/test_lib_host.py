@@ -159,6 +159,38 @@ def test_naive_coloring_ablation(L):
     m.close()
 
 
+@pytest.mark.parametrize("renumber,reorder", [(False, False), (True, False), (False, True), (True, True)])
+def test_reorder_switches(L, oracle_mod, renumber, reorder):
+    """The Table 7 ordering switches on an existing coloring: edges stay
+    color-major (stable by original id); without renumbering elements keep their
+    ids; without the left sort colors >= 2 keep original edge order; with both on
+    the result equals the full Sec. 5 ordering (and the oracle's)."""
+    mi = W.periodic_square_tri(14, jitter=0.2, seed=3)
+    m = dgc.Mesh.from_input(mi, 1)
+    m.color(5)
+    en_full, sn_full, col, off = dgc.dgc_get_ordering(m.h)
+    dgc.dgc_reorder(m.h, renumber, reorder)
+    en, sn, col2, off2 = dgc.dgc_get_ordering(m.h)
+    np.testing.assert_array_equal(col2, col)
+    np.testing.assert_array_equal(off2, off)
+    order = np.empty(len(sn), np.int64)
+    order[sn] = np.arange(len(sn))  # original edge at each new position
+    assert np.all(np.diff(col[order]) >= 0)  # color-major
+    if not renumber:
+        np.testing.assert_array_equal(en, np.arange(mi.ne))
+    l, _, _, _ = dgc.dgc_get_sides(m.h)
+    for c in range(2, len(off)):
+        seg = order[off[c - 1]:off[c]]
+        if reorder:
+            assert np.all(np.diff(en[l[seg]]) >= 0)
+        else:
+            assert np.all(np.diff(seg) > 0)
+    if renumber and reorder:
+        np.testing.assert_array_equal(en, en_full)
+        np.testing.assert_array_equal(sn, sn_full)
+    m.close()
+
+
 def test_buffer_sizes_are_checked_before_device_work(L):
     """The RK workspace and the two-pass buffer carry their sizes; too small is an
     argument error returned on the host, before anything is enqueued."""
