@@ -183,8 +183,8 @@ def kernel_source_hash() -> str:
 # over the launches of each class) from the launch list of this benchmark's own
 # command, profiles/launch_list_rk_fp32mixed_p3_1048352tri.md, taken with the
 # kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = None
-TRAFFIC_BYTES = {}
+TRAFFIC_SOURCES = "aae42fedd6a1e139"
+TRAFFIC_BYTES = {"last": 1160241152, "first": 364635819, "color": 592329660, "cfl": 495727872}
 
 
 def replica_throughput(torch, ms: float, world: int, units_per_step: float, dev):
@@ -267,6 +267,16 @@ def run_dgc(args, rank, world, local_rank):
                 "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
                 "step_alg_gbs": round(step_bytes / (ms * 1e-3) / 1e9, 1),
                 "step_frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm, 3)}
+    # the paper-structure model of one RHS with an FP32 state block S: volume pass,
+    # then per edge read both neighbours and read-modify-write both rhs blocks,
+    # (2 + 3F) S + 40 + (F/2) 48 bytes per element (F = 3 edges); timed as the
+    # RK step / 3, which also carries the CFL pass and the stage updates
+    S32 = 4 * NV
+    pm_bytes = E * ((2 + 3 * 3) * S32 + 40 + 1.5 * 48)
+    t_rhs = ms / 3.0
+    roofline["paper_structure"] = {"bytes_per_rhs": int(pm_bytes), "t_rhs_ms": round(t_rhs, 4),
+                                   "gbs": round(pm_bytes / (t_rhs * 1e-3) / 1e9, 1),
+                                   "frac": round(pm_bytes / (t_rhs * 1e-3) / 1e9 / hbm, 3)}
 
     variants = {}
     if not args.no_variants:

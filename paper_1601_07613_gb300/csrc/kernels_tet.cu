@@ -203,14 +203,6 @@ __device__ __forceinline__ void euler3_n(const double* U, double nx, double ny, 
   F[4] = (U[4] + p) * un;
 }
 
-__device__ __forceinline__ void lf3(const double* a, const double* b, double nx, double ny, double nz, double* Fs) {
-  double Fa[5], Fb[5], una, ca, unb, cb;
-  euler3_n(a, nx, ny, nz, Fa, una, ca);
-  euler3_n(b, nx, ny, nz, Fb, unb, cb);
-  const double lam = fmax(fabs(una) + ca, fabs(unb) + cb);
-#pragma unroll
-  for (int m = 0; m < 5; ++m) Fs[m] = 0.5 * (Fa[m] + Fb[m]) - 0.5 * lam * (b[m] - a[m]);
-}
 
 template <int P>
 __device__ __forceinline__ void tet_volume64(const double (&c)[TetDim<P>::NV], const double* ji,
@@ -437,14 +429,24 @@ __global__ void __launch_bounds__(256) k_surf_tet(const TetParams A) {
         for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
         U[m] = s;
       }
+      // each lane evaluates its own side (one division, one square root) and
+      // exchanges the normal flux and wave speed with its partner; the sums
+      // below are commutative, so both lanes get the same bits
+      double Fo[5], Fp[5], uno, co;
+      euler3_n(U, g0.x, g0.y, g1.x, Fo, uno, co);
+      const double wo = fabs(uno) + co;
 #pragma unroll
-      for (int m = 0; m < 5; ++m) V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+      for (int m = 0; m < 5; ++m) {
+        V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+        Fp[m] = __shfl_xor_sync(0xffffffffu, Fo[m], 1);
+      }
+      const double lam = fmax(wo, __shfl_xor_sync(0xffffffffu, wo, 1));
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
         a[m] = side ? V[m] : U[m];
         b[m] = side ? U[m] : V[m];
+        Fs[m] = 0.5 * (Fo[m] + Fp[m]) - (0.5 * lam) * (b[m] - a[m]);
       }
-      lf3(a, b, g0.x, g0.y, g1.x, Fs);
       const double s = scale * K.wF[q];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {

@@ -248,21 +248,22 @@ __device__ __forceinline__ void euler_xy(const double* U, double* F, double* G) 
   G[3] = (U[3] + p) * v;
 }
 
-// local Lax-Friedrichs (Rusanov) flux F*(a, b, n) = (F(a).n + F(b).n)/2 - lam (b - a)/2
-__device__ __forceinline__ void lf_flux(const double* a, const double* b, double nx, double ny, double* Fs) {
-  const double ia = 1.0 / a[0], ib = 1.0 / b[0];
-  const double ua = a[1] * ia, va = a[2] * ia, ub = b[1] * ib, vb = b[2] * ib;
-  const double pa = 0.4 * (a[3] - 0.5 * (a[1] * ua + a[2] * va));
-  const double pb = 0.4 * (b[3] - 0.5 * (b[1] * ub + b[2] * vb));
-  const double una = ua * nx + va * ny, unb = ub * nx + vb * ny;
-  const double ca = sqrt(1.4 * pa * ia), cb = sqrt(1.4 * pb * ib);
-  const double lam = fmax(fabs(una) + ca, fabs(unb) + cb);
-  const double h = 0.5, hl = 0.5 * lam;
-  Fs[0] = h * (a[0] * una + b[0] * unb) - hl * (b[0] - a[0]);
-  Fs[1] = h * (a[1] * una + pa * nx + b[1] * unb + pb * nx) - hl * (b[1] - a[1]);
-  Fs[2] = h * (a[2] * una + pa * ny + b[2] * unb + pb * ny) - hl * (b[2] - a[2]);
-  Fs[3] = h * ((a[3] + pa) * una + (b[3] + pb) * unb) - hl * (b[3] - a[3]);
+// One side's half of the local Lax-Friedrichs flux at an edge point: its
+// normal flux F(U).n and wave speed |u.n| + c.  Each lane of an edge pair
+// evaluates its own trace (one division and one square root) and exchanges
+// the result with its partner.
+__device__ __forceinline__ void lf_side(const double* U, double nx, double ny, double* Fn, double& w) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir;
+  const double p = 0.4 * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+  const double un = u * nx + v * ny;
+  Fn[0] = U[0] * un;
+  Fn[1] = U[1] * un + p * nx;
+  Fn[2] = U[2] * un + p * ny;
+  Fn[3] = (U[3] + p) * un;
+  w = fabs(un) + sqrt(1.4 * p * ir);
 }
+
 
 template <int P>
 __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], const double* __restrict__ ji,
@@ -527,14 +528,23 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
         for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
         U[m] = s;
       }
+      // own side's normal flux and wave speed, then the partner's
+      double Fo[4], Fp[4], wo;
+      lf_side(U, nx, ny, Fo, wo);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+      for (int m = 0; m < 4; ++m) {
+        V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+        Fp[m] = __shfl_xor_sync(0xffffffffu, Fo[m], 1);
+      }
+      const double lam = fmax(wo, __shfl_xor_sync(0xffffffffu, wo, 1));
+      // F* = (F(a).n + F(b).n)/2 - lam (b - a)/2 with a = left, b = right: the
+      // sums are commutative, so both lanes get the same bits (conservation)
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         a[m] = side ? V[m] : U[m];
         b[m] = side ? U[m] : V[m];
+        Fs[m] = 0.5 * (Fo[m] + Fp[m]) - (0.5 * lam) * (b[m] - a[m]);
       }
-      lf_flux(a, b, nx, ny, Fs);
       const double s = scale * sw[q];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
