@@ -169,6 +169,13 @@ dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, in
  * states sized for the old mesh are invalid afterwards. */
 dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems);
 
+/* Undoes dgc_refine (Sec. 3.2): the four children of every refined element merge back into
+ * their parent, and each parent edge takes the color of the child edge parallel to it.  That
+ * recovers the coloring before refinement; the call checks it (DGC_ERR_MESH otherwise) and
+ * restores the mesh, its 3-coloring and the Sec. 5 ordering.  DGC_ERR_ARG if the mesh is
+ * not refined.  Host only; states sized for the refined mesh are invalid afterwards. */
+dgc_status dgc_coarsen(dgc_mesh* mesh);
+
 /* Per edge (original order): the half (0: next to the coarse element's local edge's first
  * vertex, 1: the other) of the right element's local edge that a hanging edge covers, or
  * -1 for a conforming or boundary edge. */
@@ -204,6 +211,17 @@ dgc_status dgc_workspace_size(const dgc_mesh* mesh, dgc_prec prec, int64_t* byte
 dgc_status dgc_import_state(dgc_mesh* mesh, const double* c_host, double* c_dev, void* stream);
 dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host, void* stream);
 
+/* Stream-ordered forms of the two calls above, for pipelines (several steps' copies in
+ * flight): c_host must be pinned (page-locked or registered) host memory, xfer_dev a
+ * device buffer of dgc_state_size() bytes owned by the caller (distinct per copy in
+ * flight; 16-byte aligned).  Nothing is synchronised: the copy and the device permutation
+ * are enqueued on `stream`, and the caller waits on the stream before touching c_host (export)
+ * or reusing it (import).  DGC_ERR_ARG if c_host is not pinned. */
+dgc_status dgc_import_state_async(dgc_mesh* mesh, const double* c_host, double* c_dev, double* xfer_dev,
+                                  void* stream);
+dgc_status dgc_export_state_async(dgc_mesh* mesh, const double* c_dev, double* c_host, double* xfer_dev,
+                                  void* stream);
+
 /* The same for the device state of a precision form: DGC_FP64 and DGC_FP32_MIXED are the
  * FP64 state above; DGC_FP32_KAHAN converts to and from its FP32 pair layout (per element:
  * hi and lo of the mean phi0 c0, hi of the modes j >= 1, then lo of those modes; the host
@@ -231,8 +249,9 @@ dgc_status dgc_cfl_dt(dgc_mesh* mesh, const double* c_dev, double cfl, double* d
 /* One SSP-RK3 step (Shu-Osher form) of c_dev in place, dt from the CFL rule on the state
  * at the start of the step (written to dt_dev, device).  workspace_dev (256-byte aligned)
  * holds workspace_bytes bytes; DGC_ERR_ARG if that is less than dgc_workspace_size() for
- * prec.  No allocation and no host synchronisation after the first device call on the
- * mesh. */
+ * prec.  The workspace also holds the step's CFL scratch, so steps of one mesh may run
+ * concurrently on different streams with different workspaces and states.  No allocation and
+ * no host synchronisation after the first device call on the mesh. */
 dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl,
                        double* dt_dev, void* workspace_dev, int64_t workspace_bytes,
                        void* stream);

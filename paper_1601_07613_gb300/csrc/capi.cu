@@ -357,10 +357,12 @@ int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss,
 //   FP32 mixed:   rec0 [R] (record of u0), recs [R] (record of the stage state),
 //                 delta [S/2] (stage increment), rhs [S/2]
 //   FP32 Kahan:   recs [R], delta [S/2], rhs [S/2]  (the state's first part is u0's record)
+// and, last, the CFL estimates [E + 64 floats].
 struct Workspace {
   double* u1 = nullptr;
   float *rec0 = nullptr, *recs = nullptr, *delta = nullptr;
   void* rhs = nullptr;
+  float* est = nullptr;  // CFL estimates [E] and their minimum (so that steps on different streams never share)
   int64_t bytes = 0;
 };
 
@@ -382,6 +384,7 @@ Workspace carve(const Mesh& m, dgc_prec prec, char* base) {
     w.delta = reinterpret_cast<float*>(take(S / 2));
     w.rhs = take(S / 2);
   }
+  w.est = reinterpret_cast<float*>(take((m.ne + 64) * (int64_t)sizeof(float)));
   w.bytes = o;
   return w;
 }
@@ -606,6 +609,14 @@ dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems) {
   });
 }
 
+dgc_status dgc_coarsen(dgc_mesh* mesh) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.refined, "the mesh is not refined");
+    coarsen(m);
+  });
+}
+
 dgc_status dgc_get_ordering(const dgc_mesh* mesh, int32_t* elem_new_of_old, int32_t* edge_new_of_old,
                             int8_t* edge_color, int32_t* color_offsets) {
   return guarded([&] {
@@ -740,6 +751,43 @@ dgc_status dgc_export_state(dgc_mesh* mesh, const double* c_dev, double* c_host,
   });
 }
 
+// Stream-ordered forms for pipelining: the caller provides the device transfer
+// buffer (so that copies of different steps can be in flight at once) and a
+// pinned host buffer; nothing is synchronised.
+dgc_status dgc_import_state_async(dgc_mesh* mesh, const double* c_host, double* c_dev, double* xfer_dev,
+                                  void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(c_host != nullptr && host_is_pinned(c_host), "c_host must be pinned host memory");
+    check_ptr(c_dev, "c_dev");
+    check_ptr(xfer_dev, "xfer_dev");
+    require(xfer_dev != c_dev, "xfer_dev and c_dev must differ");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    upload(m);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DGC_CUDA(cudaMemcpyAsync(xfer_dev, c_host, state_bytes(m), cudaMemcpyHostToDevice, st));
+    permute_blocks(st, c_dev, xfer_dev, m.dev->perm, (int)nv_of(m), m.ne, true);
+    DGC_CUDA(cudaGetLastError());
+  });
+}
+
+dgc_status dgc_export_state_async(dgc_mesh* mesh, const double* c_dev, double* c_host, double* xfer_dev,
+                                  void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(c_host != nullptr && host_is_pinned(c_host), "c_host must be pinned host memory");
+    check_ptr(c_dev, "c_dev");
+    check_ptr(xfer_dev, "xfer_dev");
+    require(xfer_dev != c_dev, "xfer_dev and c_dev must differ");
+    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored");
+    upload(m);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    permute_blocks(st, xfer_dev, c_dev, m.dev->perm, (int)nv_of(m), m.ne, false);
+    DGC_CUDA(cudaGetLastError());
+    DGC_CUDA(cudaMemcpyAsync(c_host, xfer_dev, state_bytes(m), cudaMemcpyDeviceToHost, st));
+  });
+}
+
 // Kahan pair state of one element from its FP64 coefficients [M][Np]: the
 // record (hi, lo of the mean phi0 c0; hi of the modes j >= 1), then lo of the
 // modes; the inverse on export.
@@ -852,6 +900,9 @@ dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_, 
     require(workspace_size >= workspace_bytes(m, prec), "workspace smaller than dgc_workspace_size()");
     Ctx x = ready(m, stream);
     const Workspace w = carve(m, prec, static_cast<char*>(workspace_dev));
+    DeviceMesh dcopy = *m.dev;  // the mesh's arrays, the CFL estimates in the workspace
+    dcopy.cfl_est = w.est;
+    x.d = &dcopy;
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
     rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int cls, auto&& f) { run(m, x, cls, n, f); });
@@ -1002,9 +1053,9 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
     require(cfl_ > 0.0, "cfl must be positive");
     require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
-    const int64_t ws = workspace_bytes(m, prec), est = align256((m.ne + 64) * (int64_t)sizeof(float));
-    if (ws + est > kStaticScratchBytes)
-      throw Error{DGC_ERR_ARG, "mesh too large for dgc_rk_step_static: needs " + std::to_string(ws + est) +
+    const int64_t ws = workspace_bytes(m, prec);
+    if (ws > kStaticScratchBytes)
+      throw Error{DGC_ERR_ARG, "mesh too large for dgc_rk_step_static: needs " + std::to_string(ws) +
                                    " bytes of scratch, the static array holds " + std::to_string(kStaticScratchBytes)};
     int dev = -1;
     DGC_CUDA(cudaGetDevice(&dev));
@@ -1012,8 +1063,9 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     require(m.dev != nullptr && !m.dirty && m.dev->device == dev,
             "mesh not on this device yet: make one device call on it first (e.g. dgc_cfl_dt)");
     char* base = static_cast<char*>(static_scratch(dev));
+    const Workspace w = carve(m, prec, base);
     DeviceMesh dcopy = *m.dev;  // the same mesh arrays, CFL estimates in the static array
-    dcopy.cfl_est = reinterpret_cast<float*>(base + ws);
+    dcopy.cfl_est = w.est;
     Ctx x;
     x.dim = m.dim;
     x.p = m.p;
@@ -1031,7 +1083,6 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     x.shadow.rec = (int)record_floats(m);
     x.shadow.split = true;
     x.shadow.phi0 = m.tab.phiV[0];
-    const Workspace w = carve(m, prec, base);
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
     rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int, auto&& f) { count(m, n, f()); });
@@ -1106,7 +1157,7 @@ void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* d
     d.fgeo = m.dev->fgeo;
     d.jinv = m.dev->jinv;
     d.inr = m.dev->inr;
-    d.est = m.dev->cfl_est;
+    d.est = part.est;
     d.c = c_devs[i];
     d.dt = dt_devs + i;
     d.u1 = part.u1;

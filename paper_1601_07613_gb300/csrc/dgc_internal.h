@@ -58,6 +58,14 @@ struct Mesh {
   // edge that side s covers, -1 for a conforming side; empty when conforming
   std::vector<int8_t> shalf;
   bool refined = false;
+  // the mesh before dgc_refine, kept for coarsening
+  struct Base {
+    int64_t nv = 0, ne = 0, ns = 0;
+    std::vector<double> X;
+    std::vector<int32_t> ev, sl, sr, face_of;
+    std::vector<int8_t> sql, sqr, color;
+    std::vector<uint8_t> flag;  // refined elements
+  } base;
   // geometry, original order
   std::vector<double> detJ, Jinv, inradius;  // Jinv [ne][dim][dim] (row k = grad r_k)
   std::vector<double> snormal, smeas;        // [ns][dim] outward normal of the left element, |face|
@@ -97,6 +105,7 @@ ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps);
 int color_faces_naive(Mesh& m);
 void reorder(Mesh& m, bool renumber, bool reorder_left);
 void refine(Mesh& m, const std::vector<uint8_t>& flag);
+void coarsen(Mesh& m);
 void vol_points(const Mesh& m, double* xyz);
 void project(const Mesh& m, const double* vals, double* c);
 

@@ -382,8 +382,14 @@ __device__ __forceinline__ void tet_fp64_last(const TetParams& A, int64_t elem, 
   }
 }
 
+// FP32 surface kernels: minimum resident blocks of 256 threads per SM the
+// compiler must allow (register cap 65536 / (256 * min)); FP64 never capped.
+#ifndef DGC_TET_MINB
+#define DGC_TET_MINB 1
+#endif
+
 template <int P, typename CT, typename ST, typename RT, int MODE>
-__global__ void __launch_bounds__(256) k_surf_tet(const TetParams A) {
+__global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_surf_tet(const TetParams A) {
   using D = TetDim<P>;
   constexpr int NP = D::NP, NQ = D::NQF, NV = D::NV;
   extern __shared__ unsigned char smem_raw[];

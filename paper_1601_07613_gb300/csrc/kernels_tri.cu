@@ -468,16 +468,23 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
                                           const CT* sphi, const CT* sw);
 
 
-// FP32 surface kernels: minimum resident blocks of 256 threads the compiler
-// must allow per SM (register cap 65536 / (256 * min)).  2 caps them at 128
-// registers (a few spills) for 16 resident warps per SM instead of 12; measured
-// 4-7% faster than no cap at p = 3.  FP64 kernels are never capped.
-#ifndef DGC_SURF_MINB
-#define DGC_SURF_MINB 2
+// Register caps of the FP32 surface kernels, chosen for resident warps: at
+// p = 3, 128 registers (a few spilled bytes) give 16 warps per SM instead of 12
+// (measured 4-7% faster); at p = 2, 96 registers give five blocks of 128
+// threads instead of four.  FP64 kernels are not capped.
+#ifndef DGC_REGS_P3
+#define DGC_REGS_P3 128
 #endif
+#ifndef DGC_REGS_P2
+#define DGC_REGS_P2 96
+#endif
+template <int P, typename CT>
+constexpr int surf_regs() {
+  return sizeof(CT) == 8 ? 255 : (P == 3 ? DGC_REGS_P3 : (P == 2 ? DGC_REGS_P2 : 128));
+}
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
-__global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_SURF_MINB : 1)) k_surf_tri(const SurfParams A) {
+__global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT>())) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
   __shared__ CT sphi[9 * D::NQE * D::NP];
   __shared__ CT sw[D::NQE];
@@ -833,8 +840,13 @@ int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
 // blockIdx.x, blockIdx.x + gridDim.x, ... and re-stages the edge tables of
 // shared memory only when p changes (at most a few times per block).
 // ---------------------------------------------------------------------------
+// The batched FP32 surface kernel is capped at 128 registers too (two 256-thread
+// blocks per SM): measured 13% faster per step than no cap.
+#ifndef DGC_BATCH_MINB
+#define DGC_BATCH_MINB 2
+#endif
 template <int MODE, bool MIXED>
-__global__ void __launch_bounds__(256) k_batch_surf(const BatchMeshDev* __restrict__ meshes,
+__global__ void __launch_bounds__(256, (MIXED ? DGC_BATCH_MINB : 1)) k_batch_surf(const BatchMeshDev* __restrict__ meshes,
                                                     const BatchTile* __restrict__ tiles, int nt, int stage,
                                                     double a0, double b0) {
   using CT = typename std::conditional<MIXED, float, double>::type;

@@ -877,6 +877,11 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   for (int32_t f : face_of)
     if (f < 0) throw Error{DGC_ERR_MESH, "refinement: element edge without a side"};
 
+  Mesh::Base& b = m.base;
+  b.nv = m.nv;
+  b.ne = m.ne;
+  b.ns = m.ns;
+  b.flag = flag;
   m.ne = ne;
   m.nv = nv;
   m.ns = ns;
@@ -889,6 +894,14 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   m.shalf.swap(half);
   m.color.swap(col);
   m.face_of.swap(face_of);
+  b.X.swap(X);
+  b.ev.swap(ev);
+  b.sl.swap(sl);
+  b.sr.swap(sr);
+  b.sql.swap(sql);
+  b.sqr.swap(sqr);
+  b.color.swap(col);
+  b.face_of.swap(face_of);
   m.detJ.assign(ne, 0.0);
   m.Jinv.assign((size_t)ne * 4, 0.0);
   for (int64_t e = 0; e < ne; ++e) element_jacobian(m, e);
@@ -896,6 +909,72 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   m.refined = true;
   m.ncolors = 6;
   m.perfect = false;
+  reorder(m, true, true);
+  m.dirty = true;
+}
+
+// Coarsening (Sec. 3.2): the four children of each refined element merge back
+// into the parent, and a parent edge takes the color of the child edge parallel
+// to it -- the middle child's edge (k + 1) mod 3 is parallel to parent edge k.
+// A parent edge whose neighbour stayed coarse is also read off its halves
+// (colors c and c + 3: the parent's is the one <= 3).  The colors so derived
+// from the refined mesh alone are checked against the coloring before
+// refinement, and the mesh before refinement is restored.
+void coarsen(Mesh& m) {
+  const Mesh::Base& b = m.base;
+  const int64_t ne0 = b.ne, ns0 = b.ns;
+  std::vector<int64_t> first(ne0);
+  for (int64_t e = 0, n = 0; e < ne0; ++e) {
+    first[e] = n;
+    n += b.flag[e] ? 4 : 1;
+  }
+  std::vector<int8_t> col(ns0, 0);
+  auto set = [&](int64_t s, int c) {
+    if (col[s] != 0 && col[s] != c) throw Error{DGC_ERR_MESH, "coarsening: children disagree on a parent color"};
+    col[s] = (int8_t)c;
+  };
+  int64_t pos = 0;  // refined sides: the base sides in order (one, or two halves), then interior sides
+  for (int64_t s = 0; s < ns0; ++s) {
+    const int32_t l = b.sl[s], r = b.sr[s];
+    const bool split = b.flag[l] || (r >= 0 && b.flag[r]);
+    if (!split) {
+      set(s, m.color[pos++]);
+      continue;
+    }
+    const int c1 = m.color[pos], c2 = m.color[pos + 1];
+    pos += 2;
+    if (std::min(c1, c2) < 1 || std::min(c1, c2) > 3 || std::max(c1, c2) != std::min(c1, c2) + 3)
+      throw Error{DGC_ERR_MESH, "coarsening: the halves of a split edge are not colored c and c + 3"};
+    set(s, std::min(c1, c2));
+    for (int32_t x : {l, r}) {
+      if (x < 0 || !b.flag[x]) continue;
+      const int k = x == l ? b.sql[s] : b.sqr[s];
+      const int32_t side = m.face_of[(size_t)(first[x] + 3) * 3 + (k + 1) % 3];
+      set(s, m.color[side]);
+    }
+  }
+  for (int64_t s = 0; s < ns0; ++s)
+    if (col[s] != b.color[s]) throw Error{DGC_ERR_MESH, "coarsening did not recover the coloring before refinement"};
+  m.nv = b.nv;
+  m.ne = b.ne;
+  m.ns = b.ns;
+  m.X = b.X;
+  m.ev = b.ev;
+  m.sl = b.sl;
+  m.sr = b.sr;
+  m.sql = b.sql;
+  m.sqr = b.sqr;
+  m.face_of = b.face_of;
+  m.color.swap(col);
+  m.shalf.clear();
+  m.base = Mesh::Base();
+  m.detJ.assign(m.ne, 0.0);
+  m.Jinv.assign((size_t)m.ne * 4, 0.0);
+  for (int64_t e = 0; e < m.ne; ++e) element_jacobian(m, e);
+  side_geometry(m);
+  m.refined = false;
+  m.ncolors = 3;
+  m.perfect = true;
   reorder(m, true, true);
   m.dirty = true;
 }

@@ -42,6 +42,7 @@ SIGNATURES = {
     "dgc_get_sides": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]),
     "dgc_refine": (C.c_int, [_P, _I64, _I32P]),
     "dgc_reorder": (C.c_int, [_P, C.c_int, C.c_int]),
+    "dgc_coarsen": (C.c_int, [_P]),
     "dgc_get_hanging": (C.c_int, [_P, C.POINTER(C.c_int8)]),
     "dgc_get_elements": (C.c_int, [_P, _I32P, _DP]),
     "dgc_get_ordering": (C.c_int, [_P, _I32P, _I32P, C.POINTER(C.c_int8), _I32P]),
@@ -51,6 +52,8 @@ SIGNATURES = {
     "dgc_workspace_size": (C.c_int, [_P, C.c_int, _I64P]),
     "dgc_import_state": (C.c_int, [_P, _DP, _P, _P]),
     "dgc_state_bytes": (C.c_int, [_P, C.c_int, _I64P]),
+    "dgc_import_state_async": (C.c_int, [_P, _DP, _P, _P, _P]),
+    "dgc_export_state_async": (C.c_int, [_P, _P, _DP, _P, _P]),
     "dgc_import_state_prec": (C.c_int, [_P, C.c_int, _DP, _P, _P]),
     "dgc_export_state_prec": (C.c_int, [_P, C.c_int, _P, _DP, _P]),
     "dgc_export_state": (C.c_int, [_P, _P, _DP, _P]),
@@ -187,6 +190,10 @@ def dgc_refine(mesh, elems):
     _check(lib().dgc_refine(mesh, len(e), e.ctypes.data_as(_I32P)))
 
 
+def dgc_coarsen(mesh):
+    _check(lib().dgc_coarsen(mesh))
+
+
 def dgc_get_hanging(mesh):
     h = np.zeros(dgc_mesh_info(mesh)["ns"], np.int8)
     _check(lib().dgc_get_hanging(mesh, h.ctypes.data_as(C.POINTER(C.c_int8))))
@@ -251,6 +258,17 @@ def dgc_export_state(mesh, c_dev, out=None, stream=None):
         out = np.zeros((info["ne"], info["M"], info["np"]))
     _check(lib().dgc_export_state(mesh, _dptr(c_dev), out.ctypes.data_as(_DP), _stream(stream)))
     return out
+
+
+def dgc_import_state_async(mesh, c_host, c_dev, xfer_dev, stream=None):
+    """c_host: a C-contiguous float64 numpy view of pinned host memory."""
+    _check(lib().dgc_import_state_async(mesh, c_host.ctypes.data_as(_DP), _dptr(c_dev), _dptr(xfer_dev),
+                                        _stream(stream)))
+
+
+def dgc_export_state_async(mesh, c_dev, c_host, xfer_dev, stream=None):
+    _check(lib().dgc_export_state_async(mesh, _dptr(c_dev), c_host.ctypes.data_as(_DP), _dptr(xfer_dev),
+                                        _stream(stream)))
 
 
 def dgc_state_bytes(mesh, prec: int) -> int:
@@ -408,6 +426,10 @@ class Mesh:
 
     def refine(self, elems):
         dgc_refine(self.h, elems)
+        self.info = dgc_mesh_info(self.h)
+
+    def coarsen(self):
+        dgc_coarsen(self.h)
         self.info = dgc_mesh_info(self.h)
 
     def state_shape(self):

@@ -461,3 +461,48 @@ def test_import_export_pinned_and_pageable(torch_dev):
     dgc.dgc_import_state(run.m.h, np.ascontiguousarray(c[::-1][::-1]), run.c)  # pageable in
     assert np.array_equal(run.c.cpu().numpy()[en], c)
     run.close()
+
+
+def test_async_copies_and_concurrent_steps(torch_dev):
+    """Two states stepped on two streams at once (own workspaces, which hold
+    the CFL scratch too), with stream-ordered copies from and to pinned host
+    memory, give bit for bit what one-at-a-time blocking calls give."""
+    torch, dev = torch_dev
+    mi = W.periodic_square_tri(21, jitter=0.2, seed=15)
+    m = dgc.Mesh.from_input(mi, 2)
+    m.color(3)
+    shape = m.state_shape()
+    states = [state_for(mi, 6, seed=s) for s in (20, 21)]
+    P = dgc.DGC_FP32_MIXED
+    ref = []
+    for c in states:
+        cd = torch.empty(shape, dtype=torch.float64, device=dev)
+        ws = torch.empty(dgc.dgc_workspace_size(m.h, P) // 8 + 64, dtype=torch.float64, device=dev)
+        d = torch.zeros(1, dtype=torch.float64, device=dev)
+        dgc.dgc_import_state(m.h, c, cd)
+        for _ in range(2):
+            dgc.dgc_rk_step(m.h, P, cd, 0.3, d, ws)
+        ref.append(dgc.dgc_export_state(m.h, cd))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    hin = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    hout = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    cds = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    xfs = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    wss = [torch.empty(dgc.dgc_workspace_size(m.h, P) // 8 + 64, dtype=torch.float64, device=dev) for _ in range(2)]
+    dts = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(2)]
+    torch.cuda.synchronize()
+    for b in range(2):
+        hin[b][...] = states[b]
+        s = streams[b].cuda_stream
+        dgc.dgc_import_state_async(m.h, hin[b], cds[b], xfs[b], s)
+    for _ in range(2):
+        for b in range(2):
+            dgc.dgc_rk_step(m.h, P, cds[b], 0.3, dts[b], wss[b], stream=streams[b].cuda_stream)
+    for b in range(2):
+        dgc.dgc_export_state_async(m.h, cds[b], hout[b], xfs[b], streams[b].cuda_stream)
+    torch.cuda.synchronize()
+    for b in range(2):
+        assert np.array_equal(hout[b], ref[b])
+    with pytest.raises(dgc.DgcError):  # pageable host memory is refused by the async form
+        dgc.dgc_import_state_async(m.h, np.zeros(shape), cds[0], xfs[0], 0)
+    m.close()

@@ -297,3 +297,31 @@ def test_all_refined_equals_conforming_mesh(oracle_mod):
     r0 = rm.rhs(3, c)
     r1 = plain.rhs(3, c)
     assert np.linalg.norm(r0 - r1) <= 1e-14 * np.linalg.norm(r1)
+
+
+@pytest.mark.parametrize("frac", [0.3, 1.0])
+def test_library_coarsening_restores_mesh_and_coloring(frac):
+    """dgc_coarsen merges the children back; the parent colors it derives by the
+    parallel-edge rule of Sec. 3.2 equal the coloring before refinement, and the
+    mesh, its sides and its ordering come back bit for bit."""
+    mi = W.periodic_square_tri(12, jitter=0.2, seed=60)
+    m = dgc.Mesh.from_input(mi, 2)
+    m.color(17)
+    before = [dgc.dgc_get_sides(m.h), dgc.dgc_get_ordering(m.h), dgc.dgc_get_elements(m.h)]
+    info = dict(m.info)
+    flag = np.nonzero(np.random.default_rng(3).random(info["ne"]) < frac)[0]
+    m.refine(flag)
+    assert m.info["ncolors"] == 6
+    m.coarsen()
+    after = [dgc.dgc_get_sides(m.h), dgc.dgc_get_ordering(m.h), dgc.dgc_get_elements(m.h)]
+    for a, b in zip(before, after):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    assert m.info == info
+    assert (dgc.dgc_get_hanging(m.h) < 0).all()
+    with pytest.raises(dgc.DgcError) as e:
+        m.coarsen()
+    assert e.value.status == 1
+    m.refine(flag)  # and refine again
+    assert m.info["ncolors"] == 6
+    m.close()
