@@ -223,9 +223,9 @@ dgc_status dgc_export_state_async(dgc_mesh* mesh, const double* c_dev, double* c
                                   void* stream);
 
 /* The same for the device state of a precision form: DGC_FP64 and DGC_FP32_MIXED are the
- * FP64 state above; DGC_FP32_KAHAN converts to and from its FP32 pair layout (per element:
- * hi and lo of the mean phi0 c0, hi of the modes j >= 1, then lo of those modes; the host
- * side stays [E][M][Np] FP64).  dgc_state_bytes gives the device bytes of either. */
+ * FP64 state above; DGC_FP32_KAHAN converts to and from its FP32 pair layout (per element,
+ * mode-major with the M values of a mode together: hi and lo of the mean phi0 c0, hi of the
+ * modes j >= 1, then lo of those modes; the host side stays [E][M][Np] FP64).  dgc_state_bytes gives the device bytes of either. */
 dgc_status dgc_state_bytes(const dgc_mesh* mesh, dgc_prec prec, int64_t* bytes);
 dgc_status dgc_import_state_prec(dgc_mesh* mesh, dgc_prec prec, const double* c_host, void* c_dev,
                                  void* stream);

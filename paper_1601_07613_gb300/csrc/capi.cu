@@ -247,6 +247,7 @@ Ctx ready(Mesh& m, void* stream) {
   x.shadow.nv = m.M * m.np;
   x.shadow.rec = (int)record_floats(m);
   x.shadow.split = true;
+  x.shadow.mode_major = m.dim == 2;
   x.shadow.phi0 = m.tab.phiV[0];
   x.st = static_cast<cudaStream_t>(stream);
   return x;
@@ -788,9 +789,10 @@ dgc_status dgc_export_state_async(dgc_mesh* mesh, const double* c_dev, double* c
   });
 }
 
-// Kahan pair state of one element from its FP64 coefficients [M][Np]: the
-// record (hi, lo of the mean phi0 c0; hi of the modes j >= 1), then lo of the
-// modes; the inverse on export.
+// Kahan pair state of one element (triangles) from its FP64 coefficients
+// [M][Np], mode-major: hi and lo of the mean phi0 c0 ([M] each), hi of mode
+// j >= 1 at M (j + 1), then lo of mode j >= 1 at nf + M (j - 1); the inverse on
+// export.
 static void kahan_pack(const Mesh& m, const double* c, float* k) {
   const int M = m.M, np = m.np, nf = (int)record_floats(m), kf = (int)kahan_floats(m);
   const double phi0 = m.tab.phiV[0];
@@ -803,8 +805,8 @@ static void kahan_pack(const Mesh& m, const double* c, float* k) {
     for (int j = 1; j < np; ++j) {
       const double v = c[a * np + j];
       const float h = (float)v;
-      k[2 * M + a * (np - 1) + j - 1] = h;
-      k[nf + a * (np - 1) + j - 1] = (float)(v - (double)h);
+      k[M * (j + 1) + a] = h;
+      k[nf + M * (j - 1) + a] = (float)(v - (double)h);
     }
   }
 }
@@ -813,8 +815,7 @@ static void kahan_unpack(const Mesh& m, const float* k, double* c) {
   const double phi0 = m.tab.phiV[0];
   for (int a = 0; a < M; ++a) {
     c[a * np] = ((double)k[a] + (double)k[M + a]) / phi0;
-    for (int j = 1; j < np; ++j)
-      c[a * np + j] = (double)k[2 * M + a * (np - 1) + j - 1] + (double)k[nf + a * (np - 1) + j - 1];
+    for (int j = 1; j < np; ++j) c[a * np + j] = (double)k[M * (j + 1) + a] + (double)k[nf + M * (j - 1) + a];
   }
 }
 
@@ -1082,6 +1083,7 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     x.shadow.nv = m.M * m.np;
     x.shadow.rec = (int)record_floats(m);
     x.shadow.split = true;
+    x.shadow.mode_major = m.dim == 2;
     x.shadow.phi0 = m.tab.phiV[0];
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));

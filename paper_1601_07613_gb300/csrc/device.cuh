@@ -53,6 +53,7 @@ enum TypeCfg {
 struct ShadowLayout {
   int M = 4, np = 1, nv = 4, rec = 4;
   bool split = false;
+  bool mode_major = false;  // FP32 buffers as [NP][M] (triangles), else [M][NP]
   double phi0 = 0.0;
 };
 

@@ -121,36 +121,6 @@ __device__ __forceinline__ void st4(float* dst, const float (&v)[N]) {
   for (int i = 0; i < N / 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
 
-// Bulk prefetch of one element block into L2 (a hint: no completion to wait
-// for).  p 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Prefetches, at the start of a surface kernel, what a writer lane reads after
-// its flux loop: the rhs block of a read-modify-write, and in the last color
-// the partial rhs and the stage operands of incr_last (FP32 forms) or of the
-// FP64 stage update.
-template <int MODE, int NV, int NF, typename RT>
-__device__ __forceinline__ void prefetch_epilogue(const void* rhs, const StageArgs& S, int64_t e) {
-  if constexpr (MODE == SURF_RMW || MODE == SURF_LAST)
-    prefetch_l2(static_cast<const RT*>(rhs) + e * NV, (unsigned)(NV * sizeof(RT)));
-  if constexpr (MODE == SURF_LAST) {
-    if constexpr (sizeof(RT) == 4) {
-      if (S.stage >= 1) {
-        prefetch_l2(S.delta + e * NV, NV * 4);
-        if (S.stage == 1) prefetch_l2(S.rec0 + e * S.rec0_stride, NF * 4);
-      }
-      if (S.stage == 2) {
-        if (S.kstate) prefetch_l2(S.kstate + e * S.rec0_stride, (unsigned)(S.rec0_stride * 4));
-        else prefetch_l2(S.u0 + e * NV, NV * 8);
-      }
-    } else if (S.a0 != 0.0) {
-      prefetch_l2(S.u0 + e * NV, NV * 8);
-    }
-  }
-}
-
 // Epilogue of the last color in increment form for element e, whose complete
 // FP32 right-hand side is L.  B holds the record the fluxes used (the record of
 // u0 at stage 0).  phi0 = the constant basis function.

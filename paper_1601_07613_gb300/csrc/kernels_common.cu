@@ -27,17 +27,21 @@ int stage_update(const Ctx& x, bool, const double* us, const void* rhs, const St
 
 // FP32 forms: one SSP-RK3 stage in increment form (incr_form.cuh), one value
 // per thread, for meshes whose last color does not reach every element.
-// Record entries: hi[m], lo[m] at m and M + m, mode j >= 1 at 2M + m(np-1) + j-1;
-// Kahan state: the record, then lo of the modes at rec + m(np-1) + j-1.
+// Thread i is entry i of the FP32 rhs and increment blocks: mode-major ([Np][M],
+// triangles) or [M][Np] (tetrahedra), as L.mode_major says; the FP64 state is
+// [M][Np].  Record entries: hi[m], lo[m] at m and M + m; mode j >= 1 at
+// M (j + 1) + m (mode-major) or 2M + m(np-1) + j-1.  Kahan state: the record,
+// then lo of mode j >= 1 at rec + M (j - 1) + m (triangles only).
 __global__ void k_incr_stage(const float* __restrict__ rhs, StageArgs S, ShadowLayout L, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = i / L.nv;
-  const int l = (int)(i - e * L.nv), m = l / L.np, j = l - m * L.np;
+  const int l = (int)(i - e * L.nv);
+  const int m = L.mode_major ? l % L.M : l / L.np, j = L.mode_major ? l / L.M : l % L.np;
   const F2 dtp = split_f2(*S.dt);
   const float dL = mul_f2(rhs[i], dtp);
   float d = S.stage == 0 ? dL : (S.stage == 1 ? 0.25f * (S.delta[i] + dL) : S.delta[i] + dL);
-  const int mode_ix = 2 * L.M + m * (L.np - 1) + j - 1;
+  const int mode_ix = L.mode_major ? L.M * (j + 1) + m : 2 * L.M + m * (L.np - 1) + j - 1;
   if (S.stage < 2) {
     S.delta[i] = d;
     const float* r0 = S.rec0 + e * S.rec0_stride;
@@ -55,9 +59,10 @@ __global__ void k_incr_stage(const float* __restrict__ rhs, StageArgs S, ShadowL
   } else if (S.kstate) {
     float* ks = S.kstate + e * S.rec0_stride;
     if (j == 0) kahan_add(ks[m], ks[L.M + m], mul_f2(d, split_f2(2.0 / 3.0 * L.phi0)));
-    else kahan_add(ks[mode_ix], ks[L.rec + m * (L.np - 1) + j - 1], mul_f2(d, split_f2(2.0 / 3.0)));
+    else kahan_add(ks[mode_ix], ks[L.rec + L.M * (j - 1) + m], mul_f2(d, split_f2(2.0 / 3.0)));
   } else {
-    S.uout[i] = fma(2.0 / 3.0, f2d(d), S.u0[i]);
+    const int64_t u = e * L.nv + m * L.np + j;
+    S.uout[u] = fma(2.0 / 3.0, f2d(d), S.u0[u]);
   }
 }
 

@@ -6,11 +6,12 @@
 //           - sum_faces |f|/detJ sum_q w_q phi_j(x_q) F*(U-, U+, n).
 // Each edge k is handled by a lane pair: the even lane owns the left element,
 // the odd lane the right one.  A lane loads its element's modal block with
-// 16-byte vector loads, evaluates its trace at the edge points, exchanges it
-// with its partner by one shuffle per component, both lanes evaluate the
-// Lax-Friedrichs flux, and each projects it onto its own element.  Within one
-// color no two edges share an element, so the lanes update rhs with plain
-// loads and stores (Sec. 1, Algorithm 1): no atomics, no scratch buffer.
+// 16-byte vector loads, evaluates its trace and the normal flux and wave speed
+// of its own side at the edge points, exchanges them with its partner by
+// shuffles, forms the Lax-Friedrichs flux, and projects it onto its own
+// element.  Within one color no two edges share an element, so the lanes
+// update rhs with plain loads and stores (Sec. 1, Algorithm 1): no atomics,
+// no scratch buffer.
 //
 // FP64 kernels evaluate Eq. 2 as written.  FP32 kernels evaluate it in the
 // perturbation form of euler_pert.cuh (deviations from the element mean).
@@ -101,12 +102,7 @@ static void upload_p(const RefTables& R, const void* symD, const void* symF) {
   cudaMemcpyToSymbol(symF, &hf, sizeof hf);
 }
 
-void tri_upload_tables(int p, const RefTables& R) {
-  if (R.dim != 2 || R.p != p) return;
-  if (p == 1) upload_p<1>(R, &cTriD1, &cTriF1);
-  if (p == 2) upload_p<2>(R, &cTriD2, &cTriF2);
-  if (p == 3) upload_p<3>(R, &cTriD3, &cTriF3);
-}
+
 
 int tri_record_floats(int p) { return 4 * ((p + 1) * (p + 2) / 2 + 1); }
 
@@ -174,7 +170,16 @@ __device__ __forceinline__ void store_block(float* dst, const float (&v)[N]) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 element state in perturbation form: mean hi + lo, deviation modes
+// FP32 element state in perturbation form: mean hi + lo, deviation modes.
+//
+// The FP32 buffers of the triangle kernels are mode-major: the M = 4 values of
+// mode j of an element form one float4.  Per element:
+//   record (NF = 4 (NP + 1) floats): hi of the mean phi0 c0 [4], its lo [4],
+//     then mode j = 1 .. NP-1 at 4 (j + 1);
+//   Kahan pair state (8 NP floats): the record, then lo of mode j >= 1 at
+//     NF + 4 (j - 1);
+//   FP32 right-hand side and increment (4 NP floats): mode j at 4 j.
+// FP64 blocks (state, FP64 right-hand side) stay [M][NP].
 // ---------------------------------------------------------------------------
 template <int P>
 struct PertBlock {
@@ -214,7 +219,7 @@ __device__ __forceinline__ void load_pert(const float* __restrict__ src, PertBlo
     B.hi[m] = v[m];
     B.lo[m] = v[4 + m];
 #pragma unroll
-    for (int j = 1; j < D::NP; ++j) B.cd[m][j - 1] = v[8 + m * (D::NP - 1) + j - 1];
+    for (int j = 1; j < D::NP; ++j) B.cd[m][j - 1] = v[4 * (j + 1) + m];
   }
 }
 
@@ -227,7 +232,7 @@ __device__ __forceinline__ void record_of(const double (&v)[TriDim<P>::NV], floa
   for (int m = 0; m < 4; ++m) {
     split_mean(phi0, v[m * D::NP], r[m], r[4 + m]);
 #pragma unroll
-    for (int j = 1; j < D::NP; ++j) r[8 + m * (D::NP - 1) + j - 1] = d2f(v[m * D::NP + j]);
+    for (int j = 1; j < D::NP; ++j) r[4 * (j + 1) + m] = d2f(v[m * D::NP + j]);
   }
 }
 
@@ -329,6 +334,19 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
   }
 }
 
+// An element's right-hand side from a [M][NP] register block: mode-major when
+// FP32, [M][NP] when FP64.
+template <int P, typename RT, typename AT>
+__device__ __forceinline__ void store_rhs(RT* dst, const AT (&acc)[TriDim<P>::NV]) {
+  constexpr int NP = TriDim<P>::NP, NV = TriDim<P>::NV;
+  RT out[NV];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) out[sizeof(RT) == 4 ? 4 * j + m : m * NP + j] = (RT)acc[m * NP + j];
+  store_block(dst, out);
+}
+
 // ---------------------------------------------------------------------------
 // Volume kernel (unfused path): one thread per element, rhs = volume integral.
 // ---------------------------------------------------------------------------
@@ -357,8 +375,8 @@ __global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, int s
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) acc[i] = 0.0f;
     volume_acc32<P>(B, R, jinv + 4 * e, acc);
-#pragma unroll
-    for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+    store_rhs<P>(rhs + e * D::NV, acc);
+    return;
   }
   store_block(rhs + e * D::NV, out);
 }
@@ -460,6 +478,515 @@ __device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw, int ntab = 3
   if (threadIdx.x < D::NQE) sw[threadIdx.x] = K.wE[threadIdx.x];
 }
 
+// ---------------------------------------------------------------------------
+// FP32 surface integral of one lane (perturbation form, euler_pert.cuh).
+//
+// On an edge, phi_j is a polynomial of degree <= P in the edge parameter xi,
+// so phi_j(x(xi)) = sum_k T_jk L_k(xi) exactly (Legendre polynomials L_k,
+// k <= P; T_jk by Gauss quadrature, a table per local edge, half edge and
+// direction).  The lane then works with P+1 edge coefficients instead of the
+// NP modes at the 2P+1 points:
+//  1. a_k = lo dk0 + sum_{j>=1} T_jk c_j (one mode of the record at a time),
+//     and the trace deviations t_q = u(x_q) - ub = sum_k L_k(xi_q) a_k;
+//  2. at each point the lane's own flux difference dF = (F(u) - F(ub)).n and
+//     wave speed, exchanged with the partner lane, which evaluated its side
+//     relative to its own reference ub'; the local Lax-Friedrichs flux minus
+//     F(ub).n is then
+//        G = (dF + dF' + (F(ub') - F(ub)).n) / 2 - lam (u_R - u_L) / 2,
+//     with the bracket evaluated once per edge in perturbation form (deviation
+//     ub' - ub), so every term stays proportional to a deviation;
+//  3. b_k = sum_q w_q G_q L_k(xi_q), and sum_q w_q G_q phi_j(x_q) =
+//     sum_k T_jk b_k for one mode j at a time (four values), handed to the
+//     epilogue of the mode as soon as it is complete.
+// The point loops use L_k(xi_q), the same for every lane (constant memory);
+// the per-lane tables T are read from shared memory, one float4 per mode.
+// ---------------------------------------------------------------------------
+
+// Edge tables of the FP32 kernels.  Tk[d][le][j][k]: T_jk of table le (3 local
+// edges, then the 6 half edges of a hanging edge's coarse side) with the points
+// in the left element's order (d = 0) or reversed, as the right element meets
+// them (d = 1; T_jk (-1)^k); k padded to 4.  Lq[q][k] = L_k(xi_q).
+template <int P>
+struct TriEdgeK {
+  float Tk[2][9][TriDim<P>::NP][4];
+  float Lq[TriDim<P>::NQE][4];
+};
+__constant__ TriEdgeK<1> cTriK1;
+__constant__ TriEdgeK<2> cTriK2;
+__constant__ TriEdgeK<3> cTriK3;
+template <int P>
+__device__ __forceinline__ const TriEdgeK<P>& tri_ek();
+template <> __device__ __forceinline__ const TriEdgeK<1>& tri_ek<1>() { return cTriK1; }
+template <> __device__ __forceinline__ const TriEdgeK<2>& tri_ek<2>() { return cTriK2; }
+template <> __device__ __forceinline__ const TriEdgeK<3>& tri_ek<3>() { return cTriK3; }
+
+// T by Gauss-Legendre quadrature on the table's own point values (exact: the
+// integrand phi_j L_k has degree <= 2P, the rule 2P+1 points).
+template <int P>
+static void fill_edge_k(TriEdgeK<P>& E, const RefTables& R) {
+  using D = TriDim<P>;
+  constexpr int NQ = D::NQE, NP = D::NP;
+  double x[NQ], w[NQ], L[NQ][4];
+  gauss_jacobi(NQ, 0.0, x, w);
+  for (int q = 0; q < NQ; ++q) {
+    L[q][0] = 1.0;
+    L[q][1] = x[q];
+    for (int k = 2; k < 4; ++k) L[q][k] = ((2 * k - 1) * x[q] * L[q][k - 1] - (k - 1) * L[q][k - 2]) / k;
+    for (int k = 0; k < 4; ++k) E.Lq[q][k] = k <= P ? (float)L[q][k] : 0.0f;
+  }
+  for (int d = 0; d < 2; ++d)
+    for (int le = 0; le < 9; ++le)
+      for (int j = 0; j < NP; ++j)
+        for (int k = 0; k < 4; ++k) {
+          double s = 0.0;
+          if (k <= P)
+            for (int q = 0; q < NQ; ++q) {
+              const int qq = d ? NQ - 1 - q : q;
+              const double v = le < 3 ? R.phiF[((size_t)le * NQ + qq) * NP + j]
+                                      : R.phiH[((size_t)(le - 3) * NQ + qq) * NP + j];
+              s += w[q] * v * L[q][k];
+            }
+          E.Tk[d][le][j][k] = (float)(0.5 * (2 * k + 1) * s);
+        }
+}
+
+template <int P>
+static void upload_ek(const RefTables& R, const void* sym) {
+  static TriEdgeK<P> h;
+  fill_edge_k(h, R);
+  cudaMemcpyToSymbol(sym, &h, sizeof h);
+}
+
+// Shared-memory copy of Tk for the tables a mesh uses: block (d, le) of NP
+// float4 rows, the block stride an odd number of float4 so that lanes reading
+// different blocks fall into different banks.
+template <int P>
+struct ETab32 {
+  static constexpr int NQ = TriDim<P>::NQE, NP = TriDim<P>::NP;
+  static constexpr int BLK = 4 * (NP | 1);
+  static constexpr int SIZE = 2 * 9 * BLK;
+};
+
+template <int P>
+__device__ __forceinline__ void stage_etab32(float* s, int ntab) {
+  using T = ETab32<P>;
+  const TriEdgeK<P>& E = tri_ek<P>();
+  for (int i = threadIdx.x; i < 2 * ntab * T::BLK; i += blockDim.x) {
+    const int b = i / T::BLK, r = i - b * T::BLK;
+    const int d = b / ntab, le = b - d * ntab;
+    s[i] = r < 4 * T::NP ? E.Tk[d][le][r / 4][r % 4] : 0.0f;
+  }
+}
+
+// shared-memory float4 read kept where it is written (the compiler would
+// otherwise hoist the table reads of all modes and hold them in registers)
+__device__ __forceinline__ float4 lds4(const float4* p) {
+  float4 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+
+__device__ __forceinline__ float4 f4_add(float4 a, const float (&b)[4]) {
+  return make_float4(a.x + b[0], a.y + b[1], a.z + b[2], a.w + b[3]);
+}
+__device__ __forceinline__ float4 f4_mul_f2(float4 a, F2 c) {
+  return make_float4(mul_f2(a.x, c), mul_f2(a.y, c), mul_f2(a.z, c), mul_f2(a.w, c));
+}
+
+// sum_k T_jk b_k for the four variables (row = T_j., P+1 coefficients)
+template <int P>
+__device__ __forceinline__ void mode_sum(const float4 row, const float (&b)[P + 1][4], float (&a)[4]) {
+  const float t[4] = {row.x, row.y, row.z, row.w};
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float s = t[0] * b[0][m];
+#pragma unroll
+    for (int k = 1; k <= P; ++k) s = fmaf(t[k], b[k][m], s);
+    a[m] = s;
+  }
+}
+
+// Modes per batch of the last-color epilogue, per stage (stage 2 of the mixed
+// form needs an even batch: it pairs modes into double2)
+#ifndef DGC_JB0
+#define DGC_JB0 4
+#endif
+#ifndef DGC_JB1
+#define DGC_JB1 4
+#endif
+#ifndef DGC_JB2
+#define DGC_JB2 4
+#endif
+
+// Loop 3 with the last-color epilogue in increment form (incr_form.cuh) for
+// STG = the stage (0, 1, 2), or 3 for stage 2 of the Kahan form: L_j = partial
+// rhs + this color, then the stage of the increment and of the record (stages
+// 0, 1), the FP64 state of the mixed form, in place, u = u0 + (2/3) delta
+// (STG 2), or the Kahan pair state (STG 3).  The modes go in batches of JB
+// whose loads are all issued before the batch's stores, so that a batch costs
+// one memory round trip.  The buffers are distinct arrays.
+template <int P, int STG>
+__device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P + 1][4],
+                                           const float4* __restrict__ part, float4* __restrict__ dp,
+                                           const float4* __restrict__ r0, float4* __restrict__ ro,
+                                           float4* __restrict__ ks, double* __restrict__ u, double dt,
+                                           double phi0) {
+  static_assert(STG >= 0 && STG <= 3, "stage");
+  constexpr int NP = TriDim<P>::NP, NF4 = NP + 1;
+  // modes per batch: stage 2 of an FP64 state pairs modes (j, j+1) into double2
+  constexpr int JB = STG == 0 ? DGC_JB0 : STG == 1 ? DGC_JB1 : DGC_JB2;
+  constexpr bool PAIRS = NP % 2 == 0, kahan = STG == 3;
+  static_assert(STG != 2 || !PAIRS || JB % 2 == 0, "stage 2 pairs modes: even batches");
+  const F2 dtp = split_f2(dt);
+  float dk[PAIRS ? 1 : NP][4];  // stage 2, FP64 state, odd NP: every mode's increment
+#pragma unroll
+  for (int j0 = 0; j0 < NP; j0 += JB) {
+    float4 pa[JB], da[JB], ha[JB], la[JB];
+    double2 ua[(JB + 1) / 2][4];  // stage 2, FP64 state: modes (j0 + 2h, j0 + 2h + 1) of variable m
+#pragma unroll
+    for (int i = 0; i < JB; ++i) {
+      const int j = j0 + i;
+      if (j >= NP) continue;
+      pa[i] = part[j];
+      if (STG >= 1) da[i] = dp[j];
+      if (STG <= 1) {
+        ha[i] = r0[j == 0 ? 0 : j + 1];
+        if (j == 0) la[i] = r0[1];
+      } else if (kahan) {
+        ha[i] = ks[j == 0 ? 0 : j + 1];
+        la[i] = ks[j == 0 ? 1 : NF4 + j - 1];
+      }
+    }
+    if constexpr (STG == 2 && PAIRS) {
+      const double2* a2 = reinterpret_cast<const double2*>(u);
+#pragma unroll
+      for (int h = 0; h < JB / 2; ++h)
+        if (j0 + 2 * h < NP)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) ua[h][m] = a2[(m * NP + j0 + 2 * h) / 2];
+    }
+    float dfirst[4];  // stage 2, FP64 state: the first mode of the current pair
+#pragma unroll
+    for (int i = 0; i < JB; ++i) {
+      const int j = j0 + i;
+      if (j >= NP) continue;
+      float a[4];
+      mode_sum<P>(lds4(tb + j), b, a);
+      const float4 dL = f4_mul_f2(f4_add(pa[i], a), dtp);
+      if constexpr (STG < 2) {
+        float4 d = dL;
+        if (STG == 1)
+          d = make_float4(0.25f * (da[i].x + dL.x), 0.25f * (da[i].y + dL.y), 0.25f * (da[i].z + dL.z),
+                          0.25f * (da[i].w + dL.w));
+        dp[j] = d;
+        if (j == 0) {
+          float4 h = ha[i], l = la[i];
+          const F2 p0 = split_f2(phi0);
+          pair_add_scaled(h.x, l.x, d.x, p0);
+          pair_add_scaled(h.y, l.y, d.y, p0);
+          pair_add_scaled(h.z, l.z, d.z, p0);
+          pair_add_scaled(h.w, l.w, d.w, p0);
+          ro[0] = h;
+          ro[1] = l;
+        } else {
+          ro[j + 1] = make_float4(ha[i].x + d.x, ha[i].y + d.y, ha[i].z + d.z, ha[i].w + d.w);
+        }
+      } else {
+        // stage 2: delta_2 + dt L; b_2 = 2/3 is applied by the state update
+        const float d[4] = {da[i].x + dL.x, da[i].y + dL.y, da[i].z + dL.z, da[i].w + dL.w};
+        if constexpr (kahan) {
+          float4 h = ha[i], l = la[i];
+          const F2 c = split_f2(j == 0 ? 2.0 / 3.0 * phi0 : 2.0 / 3.0);
+          kahan_add(h.x, l.x, mul_f2(d[0], c));
+          kahan_add(h.y, l.y, mul_f2(d[1], c));
+          kahan_add(h.z, l.z, mul_f2(d[2], c));
+          kahan_add(h.w, l.w, mul_f2(d[3], c));
+          ks[j == 0 ? 0 : j + 1] = h;
+          ks[j == 0 ? 1 : NF4 + j - 1] = l;
+        } else if constexpr (PAIRS) {
+          // u = u0 + (2/3) f64(delta): modes (j-1, j) of each variable as one double2
+          if (i % 2 == 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) dfirst[m] = d[m];
+          } else {
+            double2* o2 = reinterpret_cast<double2*>(u);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+              o2[(m * NP + j - 1) / 2] = make_double2(fma(2.0 / 3.0, f2d(dfirst[m]), ua[i / 2][m].x),
+                                                      fma(2.0 / 3.0, f2d(d[m]), ua[i / 2][m].y));
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) dk[j][m] = d[m];
+        }
+      }
+    }
+  }
+  if constexpr (STG == 2 && !PAIRS) {
+    // odd NP (p = 1, 12 values): u = u0 + (2/3) f64(delta) over the [M][NP]
+    // FP64 block, all loads before the stores
+    constexpr int H = 2 * NP;
+    double2* u2 = reinterpret_cast<double2*>(u);
+    double2 a[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) a[i] = u2[i];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const int v = 2 * i, m0 = v / NP, j0 = v % NP, m1 = (v + 1) / NP, j1 = (v + 1) % NP;
+      u2[i] = make_double2(fma(2.0 / 3.0, f2d(dk[j0][m0]), a[i].x), fma(2.0 / 3.0, f2d(dk[j1][m1]), a[i].y));
+    }
+  }
+}
+
+// Per-edge constants of a lane's flux evaluation: the partner's reference
+// relative to ours dl = ub' - ub (exchanged), the FP32 normal and the lane's
+// edge measure (signed: the left element receives minus the flux), m_b.n, the
+// references' flux difference fb = (F(ub') - F(ub)).n, and the sign of the
+// jump: (u_R - u_L)/2 = sg (dl + t' - t), the own trace being u_L on side 0.
+// All 32 lanes must call init.
+struct EdgeConst {
+  float dl[4], n[2], scale, thb, fb[4], sg;
+  __device__ __forceinline__ void init(const PertRef<2>& R, const float (&hi)[4], double2 g0, double2 g1,
+                                       bool right, int side) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) dl[m] = __shfl_xor_sync(0xffffffffu, hi[m], 1) - hi[m];
+    n[0] = d2f(g0.x);
+    n[1] = d2f(g0.y);
+    scale = right ? d2f(g1.y) : -d2f(g1.x);
+    thb = R.u[1] * n[0] + R.u[2] * n[1];
+    PertState<2> S;
+    S.init(R, dl);
+    pert_flux<2>(R, S, dl, n, thb, fb);
+    sg = side ? -0.5f : 0.5f;
+  }
+};
+
+// Local Lax-Friedrichs flux minus F(ub).n at one edge point, from the lane's
+// own trace deviation t = u - ub and the partner lane's.  Each lane evaluates
+// its own side and exchanges one value per variable: with
+//   A = dF/2 + sg lam t   (the partner's A' = dF'/2 - sg lam t'),
+//   G = (dF + dF' + fb)/2 - sg lam (dl + t' - t) = A + A' + fb/2 - sg lam dl.
+// All 32 lanes must call it.
+__device__ __forceinline__ void lf_exchange(const PertRef<2>& R, const EdgeConst& E, const float (&t)[4],
+                                            float (&G)[4]) {
+  PertState<2> S;
+  S.init(R, t);
+  float dF[4];
+  pert_flux<2>(R, S, t, E.n, E.thb, dF);
+  const float w = pert_wave<2>(R, S, t, E.n, E.thb);
+  const float lam = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, 1));
+  const float sl = E.sg * lam;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const float a = fmaf(sl, t[m], 0.5f * dF[m]);
+    G[m] = (a + __shfl_xor_sync(0xffffffffu, a, 1)) + fmaf(-sl, E.dl[m], 0.5f * E.fb[m]);
+  }
+}
+
+// se: the edge tables (ETab32) in shared memory.
+template <int P, typename ST, typename RT, int MODE, int STG = -1>
+__device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
+                                          const float* se) {
+  using D = TriDim<P>;
+  using T = ETab32<P>;
+  constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV, K1 = P + 1;
+  // the FP32 path writes FP32 right-hand sides only in the colored modes
+  static_assert(sizeof(RT) == 8 || MODE == SURF_FIRST || MODE == SURF_RMW || MODE == SURF_LAST, "FP32 rhs modes");
+  const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
+  const bool right = side && !bnd;
+  const int64_t elem = right ? tp.y : tp.x;
+  const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
+  const bool writer = valid && !(side && bnd);
+  const double2 g0 = A.fgeo[2 * k], g1 = A.fgeo[2 * k + 1];
+  const float4* tb = reinterpret_cast<const float4*>(se + ((right ? A.ntab : 0) + le) * T::BLK);
+  const TriTab<float, P>& K = tri_tab<float, P>();
+  const TriEdgeK<P>& EK = tri_ek<P>();
+
+  // The element's state.  The first color (volume integral) and FP64 states
+  // take it as a [M][NP] block; the other colors load the FP32 record as it is
+  // stored (mode-major), all of it in flight at once.
+  constexpr bool BLOCK = MODE == SURF_FIRST || sizeof(ST) == 8;
+  PertBlock<P> B;
+  float4 rv[BLOCK ? 1 : D::NF / 4];
+  float hi[4], lo[4];
+  if constexpr (BLOCK) {
+    const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
+    load_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      hi[m] = B.hi[m];
+      lo[m] = B.lo[m];
+    }
+  } else {
+    const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(A.state) + elem * A.sstride);
+#pragma unroll
+    for (int i = 0; i < D::NF / 4; ++i) rv[i] = __ldg(src + i);
+    hi[0] = rv[0].x, hi[1] = rv[0].y, hi[2] = rv[0].z, hi[3] = rv[0].w;
+    lo[0] = rv[1].x, lo[1] = rv[1].y, lo[2] = rv[1].z, lo[3] = rv[1].w;
+  }
+  PertRef<2> R;
+  R.init(hi);
+
+  // 1. edge coefficients a_k of the trace deviation
+  float ak[K1][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    ak[0][m] = lo[m];
+#pragma unroll
+    for (int kk = 1; kk < K1; ++kk) ak[kk][m] = 0.0f;
+  }
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    float c[4];
+    if constexpr (BLOCK) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) c[m] = B.cd[m][j - 1];
+    } else {
+      const float4 v = rv[j + 1];
+      c[0] = v.x, c[1] = v.y, c[2] = v.z, c[3] = v.w;
+    }
+    const float4 row = lds4(tb + j);
+    const float tr[4] = {row.x, row.y, row.z, row.w};
+#pragma unroll
+    for (int kk = 0; kk < K1; ++kk)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) ak[kk][m] = fmaf(tr[kk], c[m], ak[kk][m]);
+  }
+
+  if constexpr (MODE == SURF_FIRST) {
+    // First color: the volume integral, then the edge's points one at a time
+    // (the record stays in registers for the volume integral anyway).
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
+    volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
+    EdgeConst E;
+    E.init(R, hi, g0, g1, right, side);
+    float bk[K1][4];
+#pragma unroll
+    for (int kk = 0; kk < K1; ++kk)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) bk[kk][m] = 0.0f;
+    DGC_UNROLL_Q
+    for (int q = 0; q < NQ; ++q) {
+      float L[K1], t[4], G[4];
+#pragma unroll
+      for (int kk = 0; kk < K1; ++kk) L[kk] = EK.Lq[q][kk];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        float v = ak[0][m];
+#pragma unroll
+        for (int kk = 1; kk < K1; ++kk) v = fmaf(L[kk], ak[kk][m], v);
+        t[m] = v;
+      }
+      lf_exchange(R, E, t, G);
+      const float s = E.scale * K.wE[q];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float g = s * G[m];
+#pragma unroll
+        for (int kk = 0; kk < K1; ++kk) bk[kk][m] = fmaf(L[kk], g, bk[kk][m]);
+      }
+    }
+    if (!writer) return;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      float a[4];
+      mode_sum<P>(lds4(tb + j), bk, a);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[m * NP + j] += a[m];
+    }
+    if constexpr (sizeof(RT) == 4) store_rhs<P>(static_cast<float*>(A.rhs) + elem * NV, acc);
+    else surf_write<P, RT, MODE>(A, elem, k, side, acc);
+  } else {
+    // 2. fluxes at every point; then 3. b_k = sum_q w_q G_q L_k(xi_q)
+    EdgeConst E;
+    E.init(R, hi, g0, g1, right, side);
+    float bk[K1][4];
+#pragma unroll
+    for (int kk = 0; kk < K1; ++kk)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) bk[kk][m] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      float t[4], G[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        float v = ak[0][m];
+#pragma unroll
+        for (int kk = 1; kk < K1; ++kk) v = fmaf(EK.Lq[q][kk], ak[kk][m], v);
+        t[m] = v;
+      }
+      lf_exchange(R, E, t, G);
+      const float s = E.scale * K.wE[q];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float g = s * G[m];
+#pragma unroll
+        for (int kk = 0; kk < K1; ++kk) bk[kk][m] = fmaf(EK.Lq[q][kk], g, bk[kk][m]);
+      }
+    }
+
+    // modes and epilogue
+    if (!writer) return;
+    if constexpr (MODE == SURF_LAST) {
+      // (the FP64 state of the mixed form is updated in place: S.u0 == S.uout)
+      const StageArgs& S = A.sa;
+      const float4* part = reinterpret_cast<const float4*>(static_cast<const float*>(A.rhs) + elem * NV);
+      float4* dp = reinterpret_cast<float4*>(S.delta + elem * NV);
+      const float4* r0 = reinterpret_cast<const float4*>(S.rec0 + elem * S.rec0_stride);
+      float4* ro = reinterpret_cast<float4*>(S.rec_out + elem * D::NF);
+      float4* ks = S.kstate ? reinterpret_cast<float4*>(S.kstate + elem * S.rec0_stride) : nullptr;
+      double* u = S.uout ? S.uout + elem * NV : nullptr;
+      const double dt = *S.dt, phi0 = tri_tab<double, P>().phiV[0][0];
+      const int stage = STG >= 0 ? STG : (S.stage == 2 && ks ? 3 : S.stage);
+      if (stage == 0) last_modes<P, 0>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
+      else if (stage == 1) last_modes<P, 1>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
+      else if (stage == 2) last_modes<P, 2>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
+      else last_modes<P, 3>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
+    } else if constexpr (sizeof(RT) == 4) {
+      // read-modify-write in batches of JB modes, each batch's loads first
+      constexpr int JB = 5;
+      float4* r = reinterpret_cast<float4*>(static_cast<float*>(A.rhs) + elem * NV);
+#pragma unroll
+      for (int j0 = 0; j0 < NP; j0 += JB) {
+        float4 o[JB];
+#pragma unroll
+        for (int i = 0; i < JB; ++i)
+          if (j0 + i < NP) o[i] = r[j0 + i];
+#pragma unroll
+        for (int i = 0; i < JB; ++i) {
+          if (j0 + i >= NP) continue;
+          float a[4];
+          mode_sum<P>(lds4(tb + j0 + i), bk, a);
+          r[j0 + i] = f4_add(o[i], a);
+        }
+      }
+    } else {
+      float acc[NV];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        float a[4];
+        mode_sum<P>(lds4(tb + j), bk, a);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m * NP + j] = a[m];
+      }
+      surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
+  }
+}
+
+void tri_upload_tables(int p, const RefTables& R) {
+  if (R.dim != 2 || R.p != p) return;
+  if (p == 1) upload_p<1>(R, &cTriD1, &cTriF1);
+  if (p == 2) upload_p<2>(R, &cTriD2, &cTriF2);
+  if (p == 3) upload_p<3>(R, &cTriD3, &cTriF3);
+  if (p == 1) upload_ek<1>(R, &cTriK1);
+  if (p == 2) upload_ek<2>(R, &cTriK2);
+  if (p == 3) upload_ek<3>(R, &cTriK3);
+}
+
 // One lane of the pair that handles edge k (side 0: left element, 1: right).
 // Lanes with valid = false shadow a real edge (so both lanes of every pair
 // take part in the shuffles) and write nothing.
@@ -468,36 +995,66 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
                                           const CT* sphi, const CT* sw);
 
 
-// Register caps of the FP32 surface kernels, chosen for resident warps: at
-// p = 3, 128 registers (a few spilled bytes) give 16 warps per SM instead of 12
-// (measured 4-7% faster); at p = 2, 96 registers give five blocks of 128
-// threads instead of four.  FP64 kernels are not capped.
+// Register caps of the FP32 surface kernels, chosen for resident warps
+// (blocks of 128 threads: 128 registers give 4 blocks per SM, 96 give 5, 80
+// give 6) and measured at p = 3: the middle colors and the last color's stage
+// 0 at 80; its stages 1 and 2, whose batches of four modes hold three operand
+// arrays, at 96; the first color (volume integral) and the kernels reading an
+// FP64 state (right-hand side calls and comparators), which keep the element
+// block in registers, at 128.  FP64 kernels are not capped.
+#ifndef DGC_REGS_P3_FIRST
+#define DGC_REGS_P3_FIRST 128
+#endif
 #ifndef DGC_REGS_P3
-#define DGC_REGS_P3 128
+#define DGC_REGS_P3 80
+#endif
+#ifndef DGC_REGS_P3_LAST
+#define DGC_REGS_P3_LAST 80
+#endif
+#ifndef DGC_REGS_P3_LAST12
+#define DGC_REGS_P3_LAST12 96
+#endif
+#ifndef DGC_REGS_P2_FIRST
+#define DGC_REGS_P2_FIRST 96
 #endif
 #ifndef DGC_REGS_P2
-#define DGC_REGS_P2 96
+#define DGC_REGS_P2 80
 #endif
-template <int P, typename CT>
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG>
 constexpr int surf_regs() {
-  return sizeof(CT) == 8 ? 255 : (P == 3 ? DGC_REGS_P3 : (P == 2 ? DGC_REGS_P2 : 128));
+  return sizeof(CT) == 8                        ? 255
+         : P == 3 && (sizeof(ST) == 8 || sizeof(RT) == 8 || MODE == SURF_FIRST) ? DGC_REGS_P3_FIRST
+         : P == 3 && MODE == SURF_LAST && STG >= 1 ? DGC_REGS_P3_LAST12
+         : P == 3 && MODE == SURF_LAST          ? DGC_REGS_P3_LAST
+         : P == 3                               ? DGC_REGS_P3
+         : P == 2 && (sizeof(ST) == 8 || sizeof(RT) == 8 || MODE == SURF_FIRST) ? DGC_REGS_P2_FIRST
+         : P == 2 && MODE == SURF_LAST && STG >= 1 ? DGC_REGS_P2_FIRST
+         : P == 2                               ? DGC_REGS_P2
+                                                : 128;
 }
 
-template <int P, typename CT, typename ST, typename RT, int MODE>
-__global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT>())) k_surf_tri(const SurfParams A) {
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1>
+__global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MODE, STG>())) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
-  __shared__ CT sphi[9 * D::NQE * D::NP];
-  __shared__ CT sw[D::NQE];
-  stage_edge_tables<P, CT>(sphi, sw, A.ntab);
-  __syncthreads();
   const int side = threadIdx.x & 1;
   int64_t k = A.begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1);
   const bool valid = k < A.end;
   if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
   const int4 tp = A.topo[k];
-  if (valid) prefetch_epilogue<MODE, TriDim<P>::NV, TriDim<P>::NF, RT>(A.rhs, A.sa, side && tp.y >= 0 ? tp.y : tp.x);
-  surf_pair<P, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+  if constexpr (sizeof(CT) == 4) {
+    __shared__ __align__(16) float se[ETab32<P>::SIZE];
+    stage_etab32<P>(se, A.ntab);
+    __syncthreads();
+    surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se);
+  } else {
+    __shared__ double sphi[9 * D::NQE * D::NP];
+    __shared__ double sw[D::NQE];
+    stage_edge_tables<P, double>(sphi, sw, A.ntab);
+    __syncthreads();
+    surf_pair<P, double, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+  }
 }
+
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
 __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
@@ -514,7 +1071,8 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
   // (in SURF_LAST the state may alias the stage output, but each element's
   // block is read and written by its own lane only)
 
-  if constexpr (sizeof(CT) == 8) {
+  static_assert(sizeof(CT) == 8, "FP64 lanes; the FP32 ones are surf_fp32");
+  {
     // ---------------- FP64: Eq. 2 as written ----------------
     double c[NV], acc[NV];
     load_block(static_cast<const double*>(A.state) + elem * NV, c);
@@ -562,70 +1120,6 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
     }
     if constexpr (MODE == SURF_LAST) {
       if (writer) fp64_last<P>(A, elem, acc, c);
-    } else if (writer) {
-      surf_write<P, RT, MODE>(A, elem, k, side, acc);
-    }
-  } else {
-    // ---------------- FP32: perturbation form ----------------
-    const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
-    PertBlock<P> B;
-    load_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
-    PertRef<2> R;
-    R.init(B.hi);
-    float acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
-    if constexpr (MODE == SURF_FIRST) volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
-    // the partner's mean relative to ours: base = (hi_o - hi_s) + lo_o
-    float base[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const float ho = __shfl_xor_sync(0xffffffffu, B.hi[m], 1);
-      const float lo = __shfl_xor_sync(0xffffffffu, B.lo[m], 1);
-      base[m] = (ho - B.hi[m]) + lo;
-    }
-    const float n[2] = {d2f(g0.x), d2f(g0.y)};
-    const float scale = right ? d2f(g1.y) : -d2f(g1.x);
-    const float thb = R.u[1] * n[0] + R.u[2] * n[1];
-    DGC_UNROLL_Q
-    for (int q = 0; q < NQ; ++q) {
-      const int qq = right ? NQ - 1 - q : q;
-      float phi[NP], dU[4], dV[4], ds[4], dn[4], G[4];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) phi[j] = ph[qq * NP + j];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        float s = 0.0f;
-#pragma unroll
-        for (int j = 1; j < NP; ++j) s += phi[j] * B.cd[m][j - 1];
-        dU[m] = s;
-      }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) dV[m] = __shfl_xor_sync(0xffffffffu, dU[m], 1);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        ds[m] = B.lo[m] + dU[m];  // own trace - ub
-        dn[m] = base[m] + dV[m];  // partner's trace - ub
-      }
-      if (side) pert_lf<2>(R, dn, ds, n, thb, G);  // left trace = partner's
-      else pert_lf<2>(R, ds, dn, n, thb, G);
-      const float s = scale * sw[q];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const float g = s * G[m];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
-      }
-    }
-    if constexpr (MODE == SURF_LAST) {
-      // the element's right-hand side is complete: SSP-RK3 stage in increment form
-      if (writer) {
-        float L[NV];
-        load_plain(static_cast<const float*>(A.rhs) + elem * NV, L);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) L[i] += acc[i];
-        incr_last<4, NP>(A.sa, elem, L, B, tri_tab<double, P>().phiV[0][0]);
-      }
     } else if (writer) {
       surf_write<P, RT, MODE>(A, elem, k, side, acc);
     }
@@ -707,7 +1201,7 @@ __device__ __forceinline__ float lambda_max_rec(const float (&r)[TriDim<P>::NF])
     for (int m = 0; m < 4; ++m) {
       float s = r[4 + m];
 #pragma unroll
-      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[8 + m * (NP - 1) + j - 1];
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[4 * (j + 1) + m];
       U[m] = r[m] + s;
     }
     const float ir = rcp_fast(U[0]), u = U[1] * ir, w = U[2] * ir;
@@ -743,7 +1237,7 @@ template <int P, bool KAHAN>
 __device__ __forceinline__ double cfl2_warp(const void* __restrict__ state, const double* __restrict__ inr,
                                             int64_t e, double cfl, const float* __restrict__ est, float minest) {
   using D = TriDim<P>;
-  constexpr int NP = D::NP, NM = NP - 1;
+  constexpr int NP = D::NP;
   const bool cand = e >= 0 && est[e] <= minest * (1.0f + kCflMargin);
   unsigned mask = __ballot_sync(0xffffffffu, cand);
   double best = DBL_MAX;
@@ -759,7 +1253,7 @@ __device__ __forceinline__ double cfl2_warp(const void* __restrict__ state, cons
       for (int m = 0; m < 4; ++m) {
         v[m * NP] = (f2d(k[m]) + f2d(k[4 + m])) / phi0;
 #pragma unroll
-        for (int j = 0; j < NM; ++j) v[m * NP + 1 + j] = f2d(k[8 + m * NM + j]) + f2d(k[D::NF + m * NM + j]);
+        for (int j = 1; j < NP; ++j) v[m * NP + j] = f2d(k[4 * (j + 1) + m]) + f2d(k[D::NF + 4 * (j - 1) + m]);
       }
     } else {
       load_block(static_cast<const double*>(state) + ec * D::NV, v);
@@ -852,16 +1346,25 @@ __global__ void __launch_bounds__(256, (MIXED ? DGC_BATCH_MINB : 1)) k_batch_sur
   using CT = typename std::conditional<MIXED, float, double>::type;
   using RT = CT;
   using ST = CT;
-  __shared__ CT sphi[3 * TriDim<3>::NQE * TriDim<3>::NP];
+  // edge tables of the current order: FP32 in the mode-outer layout, FP64 as
+  // [table][point][mode]
+  constexpr int TAB = MIXED ? 2 * 3 * ETab32<3>::BLK : 3 * TriDim<3>::NQE * TriDim<3>::NP;
+  __shared__ __align__(16) CT sphi[TAB];
   __shared__ CT sw[TriDim<3>::NQE];
   int curp = 0;
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const BatchTile T = tiles[ti];
     if (T.p != curp) {  // block-uniform
       __syncthreads();
-      if (T.p == 1) stage_edge_tables<1, CT>(sphi, sw);
-      else if (T.p == 2) stage_edge_tables<2, CT>(sphi, sw);
-      else stage_edge_tables<3, CT>(sphi, sw);
+      if constexpr (MIXED) {
+        if (T.p == 1) stage_etab32<1>(sphi, 3);
+        else if (T.p == 2) stage_etab32<2>(sphi, 3);
+        else stage_etab32<3>(sphi, 3);
+      } else {
+        if (T.p == 1) stage_edge_tables<1, CT>(sphi, sw);
+        else if (T.p == 2) stage_edge_tables<2, CT>(sphi, sw);
+        else stage_edge_tables<3, CT>(sphi, sw);
+      }
       __syncthreads();
       curp = T.p;
     }
@@ -893,15 +1396,22 @@ __global__ void __launch_bounds__(256, (MIXED ? DGC_BATCH_MINB : 1)) k_batch_sur
     }
     A.rhs = B.rhs;
     A.buf = nullptr;
+    A.ntab = 3;
     A.sa.dt = B.dt;
     int64_t k = T.begin + (threadIdx.x >> 1);
     const bool valid = k < T.end;
     if (!valid) k = T.end - 1;
     const int side = threadIdx.x & 1;
     const int4 tp = A.topo[k];
-    if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
-    else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
-    else surf_pair<3, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+    if constexpr (MIXED) {
+      if (T.p == 1) surf_fp32<1, ST, RT, MODE>(A, k, tp, valid, side, sphi);
+      else if (T.p == 2) surf_fp32<2, ST, RT, MODE>(A, k, tp, valid, side, sphi);
+      else surf_fp32<3, ST, RT, MODE>(A, k, tp, valid, side, sphi);
+    } else {
+      if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+      else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+      else surf_pair<3, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+    }
   }
 }
 
@@ -1028,13 +1538,13 @@ int tri_volume(const Ctx& x, TypeCfg ty, const void* s, int sstride, void* r, in
   }
 }
 
-template <int P, typename CT, typename ST, typename RT, int MODE>
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1>
 static int surf_launch(const Ctx& x, const SurfParams& A) {
   const int64_t n = A.end - A.begin;
   if (n <= 0) return 0;
   const int threads = 2 * x.epb;
   const int64_t grid = (2 * n + threads - 1) / threads;
-  k_surf_tri<P, CT, ST, RT, MODE><<<(unsigned)grid, threads, 0, x.st>>>(A);
+  k_surf_tri<P, CT, ST, RT, MODE, STG><<<(unsigned)grid, threads, 0, x.st>>>(A);
   return 1;
 }
 
@@ -1053,15 +1563,21 @@ template <int P>
 static int surf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const SurfParams& A) {
   if (mode == SURF_LAST) {
     if (ty == TY_D) return surf_launch<P, double, double, double, SURF_LAST>(x, A);
-    if (ty == TY_MF) return surf_launch<P, float, float, float, SURF_LAST>(x, A);
+    if (ty == TY_MF) {  // one kernel per stage of the increment form (3: stage 2 of the Kahan form)
+      if (A.sa.stage == 0) return surf_launch<P, float, float, float, SURF_LAST, 0>(x, A);
+      if (A.sa.stage == 1) return surf_launch<P, float, float, float, SURF_LAST, 1>(x, A);
+      if (A.sa.kstate) return surf_launch<P, float, float, float, SURF_LAST, 3>(x, A);
+      return surf_launch<P, float, float, float, SURF_LAST, 2>(x, A);
+    }
     return -1;
   }
   switch (ty) {
     case TY_D: return surf_mode<P, double, double, double>(x, mode, A);
     case TY_MD: return surf_mode<P, float, double, double>(x, mode, A);
     case TY_MF:
-      if (mode != SURF_RMW && mode != SURF_FIRST) return -1;
-      return surf_mode<P, float, float, float>(x, mode, A);
+      if (mode == SURF_RMW) return surf_launch<P, float, float, float, SURF_RMW>(x, A);
+      if (mode == SURF_FIRST) return surf_launch<P, float, float, float, SURF_FIRST>(x, A);
+      return -1;
     case TY_KD:
       if (mode == SURF_RMW) return surf_launch<P, float, float, double, SURF_RMW>(x, A);
       if (mode == SURF_FIRST) return surf_launch<P, float, float, double, SURF_FIRST>(x, A);

@@ -331,7 +331,9 @@ def test_tet_rk_step_matches_oracle(torch_dev, oracle_mod, p):
 
 def test_fp32_records_of_the_mixed_step(torch_dev):
     """The FP32 records the mixed-precision step keeps (workspace: record of u0,
-    record of the stage state, FP32 increment, rhs; each 256-byte aligned).
+    record of the stage state, FP32 increment, rhs; each 256-byte aligned; the
+    triangle kernels' FP32 blocks are mode-major: hi[M], lo[M], then one [M]
+    group per mode j >= 1; increment [Np][M]).
     * rec0, written by the CFL pass from the FP64 state: the mean phi_0 c_0 as an
       FP32 pair hi + lo, the modes j >= 1 as FP32, converted with integer bit
       operations; they must equal round-to-nearest bit for bit.
@@ -354,8 +356,12 @@ def test_fp32_records_of_the_mixed_step(torch_dev):
     raw = ws.view(torch.uint8)
     rec0 = raw[:4 * E * nrec].view(torch.float32).reshape(E, nrec)
     recs = raw[R:R + 4 * E * nrec].view(torch.float32).reshape(E, nrec)
-    delta = raw[2 * R:2 * R + 4 * E * M * NP].view(torch.float32).reshape(E, M, NP)
-    assert torch.equal(rec0[:, 2 * M:].reshape(E, M, NP - 1), u0[:, :, 1:].float())
+    delta = raw[2 * R:2 * R + 4 * E * M * NP].view(torch.float32).reshape(E, NP, M).transpose(1, 2)
+
+    def modes(r):  # [E][M][Np-1] from the mode-major record
+        return r[:, 2 * M:].reshape(E, NP - 1, M).transpose(1, 2)
+
+    assert torch.equal(modes(rec0), u0[:, :, 1:].float())
     # the mean phi_0 c_0 (phi_0 = sqrt 2 from the library's normalised table, to an ulp):
     # hi is its FP32 rounding and lo the FP32 rounding of the remainder
     mean = u0[:, :, 0] * np.sqrt(2.0)
@@ -366,7 +372,7 @@ def test_fp32_records_of_the_mixed_step(torch_dev):
     assert torch.all(torch.abs(hi.double() + lo.double() - mean) <= 2.0 ** -47 * torch.abs(mean))
     assert torch.all(torch.abs(lo.double() - (mean - hi.double())) <= 2.0 ** -47 * torch.abs(mean))
     # stage record = rec0 (+) delta_2
-    assert torch.equal(recs[:, 2 * M:].reshape(E, M, NP - 1), rec0[:, 2 * M:].reshape(E, M, NP - 1) + delta[:, :, 1:])
+    assert torch.equal(modes(recs), modes(rec0) + delta[:, :, 1:])
     mean2 = hi.double() + lo.double() + np.sqrt(2.0) * delta[:, :, 0].double()
     got2 = recs[:, :M].double() + recs[:, M:2 * M].double()
     assert torch.all(torch.abs(got2 - mean2) <= 2.0 ** -46 * torch.abs(mean2))
@@ -399,7 +405,7 @@ def test_fp32_record_conversion_special_values(torch_dev):
     torch.cuda.synchronize()
     nrec = M * (NP + 1)
     rec0 = ws.view(torch.uint8)[:4 * E * nrec].view(torch.float32).reshape(E, nrec)
-    got = rec0[:, 2 * M:].reshape(E, M, NP - 1)
+    got = rec0[:, 2 * M:].reshape(E, NP - 1, M).transpose(1, 2)  # mode-major record
     want = u0[:, :, 1:].float()
     nan = torch.isnan(want)
     assert torch.equal(torch.isnan(got), nan)
