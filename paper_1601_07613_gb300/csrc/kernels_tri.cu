@@ -1334,15 +1334,20 @@ int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
 // blockIdx.x, blockIdx.x + gridDim.x, ... and re-stages the edge tables of
 // shared memory only when p changes (at most a few times per block).
 // ---------------------------------------------------------------------------
-// The batched FP32 surface kernel is capped at 128 registers too (two 256-thread
-// blocks per SM): measured 13% faster per step than no cap.
-#ifndef DGC_BATCH_MINB
-#define DGC_BATCH_MINB 2
+// The batched FP32 surface kernels take the register caps of the p = 3
+// kernels above (the order with the most registers) plus a few for the tile
+// loop's state; one kernel per RK stage of the last color (STG), as there.
+#ifndef DGC_BATCH_EXTRA_REGS
+#define DGC_BATCH_EXTRA_REGS 16
 #endif
-template <int MODE, bool MIXED>
-__global__ void __launch_bounds__(256, (MIXED ? DGC_BATCH_MINB : 1)) k_batch_surf(const BatchMeshDev* __restrict__ meshes,
-                                                    const BatchTile* __restrict__ tiles, int nt, int stage,
-                                                    double a0, double b0) {
+template <int MODE, bool MIXED, int STG>
+constexpr int batch_regs() {
+  return !MIXED ? 255 : surf_regs<3, float, float, float, MODE, STG>() + DGC_BATCH_EXTRA_REGS;
+}
+template <int MODE, bool MIXED, int STG = -1>
+__global__ void __launch_bounds__(256) __maxnreg__((batch_regs<MODE, MIXED, STG>()))
+    k_batch_surf(const BatchMeshDev* __restrict__ meshes, const BatchTile* __restrict__ tiles, int nt, int stage,
+                 double a0, double b0) {
   using CT = typename std::conditional<MIXED, float, double>::type;
   using RT = CT;
   using ST = CT;
@@ -1404,9 +1409,9 @@ __global__ void __launch_bounds__(256, (MIXED ? DGC_BATCH_MINB : 1)) k_batch_sur
     const int side = threadIdx.x & 1;
     const int4 tp = A.topo[k];
     if constexpr (MIXED) {
-      if (T.p == 1) surf_fp32<1, ST, RT, MODE>(A, k, tp, valid, side, sphi);
-      else if (T.p == 2) surf_fp32<2, ST, RT, MODE>(A, k, tp, valid, side, sphi);
-      else surf_fp32<3, ST, RT, MODE>(A, k, tp, valid, side, sphi);
+      if (T.p == 1) surf_fp32<1, ST, RT, MODE, STG>(A, k, tp, valid, side, sphi);
+      else if (T.p == 2) surf_fp32<2, ST, RT, MODE, STG>(A, k, tp, valid, side, sphi);
+      else surf_fp32<3, ST, RT, MODE, STG>(A, k, tp, valid, side, sphi);
     } else {
       if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
       else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
@@ -1482,12 +1487,12 @@ int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, in
   return 2;
 }
 
-template <int MODE, bool MIXED>
+template <int MODE, bool MIXED, int STG = -1>
 static int batch_surf_launch(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage,
                              double a0, double b0, int threads) {
   if (nt <= 0) return 0;
-  const int g = persistent_grid((const void*)k_batch_surf<MODE, MIXED>, threads, nt);
-  k_batch_surf<MODE, MIXED><<<g, threads, 0, st>>>(d, tiles, nt, stage, a0, b0);
+  const int g = persistent_grid((const void*)k_batch_surf<MODE, MIXED, STG>, threads, nt);
+  k_batch_surf<MODE, MIXED, STG><<<g, threads, 0, st>>>(d, tiles, nt, stage, a0, b0);
   return 1;
 }
 
@@ -1496,7 +1501,11 @@ int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, i
   if (mixed) {
     if (mode == SURF_FIRST) return batch_surf_launch<SURF_FIRST, true>(st, d, tiles, nt, stage, a0, b0, threads);
     if (mode == SURF_RMW) return batch_surf_launch<SURF_RMW, true>(st, d, tiles, nt, stage, a0, b0, threads);
-    if (mode == SURF_LAST) return batch_surf_launch<SURF_LAST, true>(st, d, tiles, nt, stage, a0, b0, threads);
+    if (mode == SURF_LAST) {  // the batch runs the mixed form only: stage 2 updates the FP64 state
+      if (stage == 0) return batch_surf_launch<SURF_LAST, true, 0>(st, d, tiles, nt, stage, a0, b0, threads);
+      if (stage == 1) return batch_surf_launch<SURF_LAST, true, 1>(st, d, tiles, nt, stage, a0, b0, threads);
+      return batch_surf_launch<SURF_LAST, true, 2>(st, d, tiles, nt, stage, a0, b0, threads);
+    }
   } else {
     if (mode == SURF_FIRST) return batch_surf_launch<SURF_FIRST, false>(st, d, tiles, nt, stage, a0, b0, threads);
     if (mode == SURF_RMW) return batch_surf_launch<SURF_RMW, false>(st, d, tiles, nt, stage, a0, b0, threads);
