@@ -77,8 +77,12 @@ typedef enum {
   DGC_OPT_THREADS_PER_EDGE = 2, /* 2 (one thread per edge side); reserved for tuning */
   DGC_OPT_PROFILE = 3,          /* 1: record a CUDA event pair around every kernel launch, on
                                    the launch stream, for dgc_profile_collect; 0 (default): off */
-  DGC_OPT_GRAPH = 4             /* batches: 1 (default) capture the step in a CUDA graph on the
+  DGC_OPT_GRAPH = 4,            /* batches: 1 (default) capture the step in a CUDA graph on the
                                    first call and replay it; 0: launch the kernels directly */
+  DGC_OPT_PDL = 5               /* meshes: 1 (default) launch the RK step's surface and CFL kernels
+                                   with programmatic dependent launch (each kernel's work that does
+                                   not read its predecessor's output overlaps the predecessor's
+                                   end); 0: plain stream order.  Results are identical. */
 } dgc_option;
 
 /* Kernel classes reported by dgc_profile_collect. */

@@ -906,6 +906,7 @@ dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_, 
     x.d = &dcopy;
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
+    x.pdl = m.pdl;
     rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int cls, auto&& f) { run(m, x, cls, n, f); });
     finish(m, n);
   });
@@ -969,6 +970,9 @@ dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value) {
         break;
       case DGC_OPT_PROFILE:
         m.profile = value != 0;
+        break;
+      case DGC_OPT_PDL:
+        m.pdl = value != 0;
         break;
       default:
         throw Error{DGC_ERR_ARG, "unknown option"};
@@ -1087,6 +1091,7 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     x.shadow.phi0 = m.tab.phiV[0];
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
+    x.pdl = m.pdl;
     rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int, auto&& f) { count(m, n, f()); });
     finish(m, n);
   });

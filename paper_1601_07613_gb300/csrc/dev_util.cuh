@@ -14,6 +14,16 @@
 
 namespace dgc {
 
+// Programmatic dependent launch.  pdl_wait() blocks until the grid launched
+// before this one on the stream has completed and its writes are visible (a
+// no-op for a launch without a programmatic dependency).  pdl_trigger() lets
+// the next grid's blocks be scheduled once every block of this grid has issued
+// it or exited.  A kernel issues pdl_trigger() only after pdl_wait(), so when a
+// grid starts, the grid two launches back has completed: it may read that
+// grid's output at once and must wait before touching its predecessor's.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Full conversions (every input class); called out of line for the rare
 // inputs the fast paths below do not cover.
 static __device__ __noinline__ float d2f_any(double x) {

@@ -64,6 +64,7 @@ struct Ctx {
   int epb = 128;
   const DeviceMesh* d = nullptr;
   cudaStream_t st = nullptr;
+  bool pdl = false;  // launch the surface and CFL kernels with programmatic dependent launch
 };
 
 struct StageArgs {

@@ -83,6 +83,7 @@ struct Mesh {
   int edges_per_block = 64;
   int threads_per_edge = 2;
   bool profile = false;
+  bool pdl = true;  // programmatic dependent launch of the RK step's kernels
   void* prof = nullptr;  // event records (capi.cu)
   // device side
   DeviceMesh* dev = nullptr;

@@ -35,6 +35,27 @@ namespace dgc {
 #define DGC_PRAGMA(x) DGC_PRAGMA_(x)
 #define DGC_UNROLL_Q DGC_PRAGMA(unroll DGC_QUNROLL)
 
+// A kernel launch on x.st; with x.pdl, as a programmatic dependent launch (the
+// kernels pair pdl_wait / pdl_trigger, dev_util.cuh).
+template <typename... KArgs, typename... Args>
+static void launch_k(const Ctx& x, void (*k)(KArgs...), unsigned grid, unsigned threads, Args... args) {
+  if (!x.pdl) {
+    k<<<grid, threads, 0, x.st>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = x.st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int P>
 struct TriDim {
   static constexpr int NP = (P + 1) * (P + 2) / 2;
@@ -803,6 +824,15 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
   const TriTab<float, P>& K = tri_tab<float, P>();
   const TriEdgeK<P>& EK = tri_ek<P>();
 
+  // The first color reads the record its predecessor (the previous stage's last
+  // color) wrote and overwrites the rhs that predecessor read: it waits at once.
+  // The other colors read records written two launches back or earlier; they
+  // wait only before their epilogue, which reads the predecessor's rhs.
+  if constexpr (MODE == SURF_FIRST) {
+    pdl_wait();
+    pdl_trigger();
+  }
+
   // The element's state.  The first color (volume integral) and FP64 states
   // take it as a [M][NP] block; the other colors load the FP32 record as it is
   // stored (mode-major), all of it in flight at once.
@@ -928,7 +958,9 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
       }
     }
 
-    // modes and epilogue
+    // modes and epilogue, after the predecessor grid has completed
+    pdl_wait();
+    pdl_trigger();
     if (!writer) return;
     if constexpr (MODE == SURF_LAST) {
       // (the FP64 state of the mixed form is updated in place: S.u0 == S.uout)
@@ -1072,6 +1104,10 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
   // block is read and written by its own lane only)
 
   static_assert(sizeof(CT) == 8, "FP64 lanes; the FP32 ones are surf_fp32");
+  if constexpr (MODE == SURF_FIRST) {  // programmatic launch: as in surf_fp32
+    pdl_wait();
+    pdl_trigger();
+  }
   {
     // ---------------- FP64: Eq. 2 as written ----------------
     double c[NV], acc[NV];
@@ -1117,6 +1153,10 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
+    }
+    if constexpr (MODE != SURF_FIRST) {
+      pdl_wait();
+      pdl_trigger();
     }
     if constexpr (MODE == SURF_LAST) {
       if (writer) fp64_last<P>(A, elem, acc, c);
@@ -1268,6 +1308,8 @@ template <int P>
 __global__ void __launch_bounds__(128) k_cfl1_tri(const double* __restrict__ c, const double* __restrict__ inr,
                                                   int64_t ne, float* __restrict__ est, unsigned* minbits,
                                                   float* __restrict__ shadow) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const float best = e < ne ? cfl1_elem<P>(c, inr, e, est, shadow) : FLT_MAX;
   block_min_to(best, minbits);
@@ -1277,6 +1319,8 @@ template <int P, bool KAHAN>
 __global__ void __launch_bounds__(128) k_cfl2_tri(const void* __restrict__ c, const double* __restrict__ inr,
                                                   int64_t ne, double cfl, const float* __restrict__ est,
                                                   const unsigned* minbits, unsigned long long* dtbits) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const double best = cfl2_warp<P, KAHAN>(c, inr, e < ne ? e : -1, cfl, est, __uint_as_float(*minbits));
   block_min_to(best, dtbits);
@@ -1290,6 +1334,8 @@ template <int P>
 __global__ void __launch_bounds__(128) k_cfl1_tri_k(const float* __restrict__ ks, const double* __restrict__ inr,
                                                     int64_t ne, float* __restrict__ est, unsigned* minbits) {
   using D = TriDim<P>;
+  pdl_wait();
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float best = FLT_MAX;
   if (e < ne) {
@@ -1312,16 +1358,16 @@ int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
   if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
   switch (x.p) {
     case 1:
-      k_cfl1_tri_k<1><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
-      k_cfl2_tri<1, true><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri_k<1>, grid, bs, ks, x.d->inr, x.ne, est, mn);
+      launch_k(x, k_cfl2_tri<1, true>, grid, bs, ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
-      k_cfl1_tri_k<2><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
-      k_cfl2_tri<2, true><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri_k<2>, grid, bs, ks, x.d->inr, x.ne, est, mn);
+      launch_k(x, k_cfl2_tri<2, true>, grid, bs, ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 3:
-      k_cfl1_tri_k<3><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, est, mn);
-      k_cfl2_tri<3, true><<<grid, bs, 0, x.st>>>(ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri_k<3>, grid, bs, ks, x.d->inr, x.ne, est, mn);
+      launch_k(x, k_cfl2_tri<3, true>, grid, bs, ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }
@@ -1553,7 +1599,7 @@ static int surf_launch(const Ctx& x, const SurfParams& A) {
   if (n <= 0) return 0;
   const int threads = 2 * x.epb;
   const int64_t grid = (2 * n + threads - 1) / threads;
-  k_surf_tri<P, CT, ST, RT, MODE, STG><<<(unsigned)grid, threads, 0, x.st>>>(A);
+  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG>, (unsigned)grid, (unsigned)threads, A);
   return 1;
 }
 
@@ -1626,16 +1672,16 @@ int tri_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow
   if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
   switch (x.p) {
     case 1:
-      k_cfl1_tri<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tri<1, false><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri<1>, grid, bs, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tri<1, false>, grid, bs, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
-      k_cfl1_tri<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tri<2, false><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri<2>, grid, bs, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tri<2, false>, grid, bs, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 3:
-      k_cfl1_tri<3><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tri<3, false><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri<3>, grid, bs, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tri<3, false>, grid, bs, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }

@@ -23,6 +23,7 @@ DGC_OPT_EDGES_PER_BLOCK = 1
 DGC_OPT_THREADS_PER_EDGE = 2
 DGC_OPT_PROFILE = 3
 DGC_OPT_GRAPH = 4
+DGC_OPT_PDL = 5
 KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
 
 STATUS = {0: "DGC_OK", 1: "DGC_ERR_ARG", 2: "DGC_ERR_MESH", 3: "DGC_ERR_COLORING_LIMIT",
