@@ -67,6 +67,28 @@ struct Ctx {
   bool pdl = false;  // launch the surface and CFL kernels with programmatic dependent launch
 };
 
+// A kernel launch on x.st with smem bytes of dynamic shared memory; with x.pdl,
+// as a programmatic dependent launch (the kernels pair pdl_wait / pdl_trigger,
+// dev_util.cuh).
+template <typename... KArgs, typename... Args>
+static void launch_k(const Ctx& x, void (*k)(KArgs...), unsigned grid, unsigned threads, size_t smem, Args... args) {
+  if (!x.pdl) {
+    k<<<grid, threads, smem, x.st>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = x.st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 struct StageArgs {
   // FP64 form: uout = a0 u0 + b0 (us + dt L(us))
   const double* u0 = nullptr;  // FP64 state at the start of the step

@@ -399,6 +399,13 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_s
     for (int i = threadIdx.x; i < 24 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
   }
   __syncthreads();
+  // programmatic launch (dev_util.cuh): the first color reads its predecessor's
+  // record and overwrites the rhs it read, so it waits at once; the other
+  // colors wait before their epilogue, which reads the predecessor's rhs
+  if constexpr (MODE == SURF_FIRST) {
+    pdl_wait();
+    pdl_trigger();
+  }
 
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t k = A.begin + (t >> 1);
@@ -461,6 +468,10 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_s
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
     }
+    if constexpr (MODE != SURF_FIRST) {
+      pdl_wait();
+      pdl_trigger();
+    }
     if constexpr (MODE == SURF_LAST) {
       if (writer) tet_fp64_last<P>(A, elem, acc, c);
     } else if (writer) {
@@ -516,6 +527,10 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_s
         for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
       }
     }
+    if constexpr (MODE != SURF_FIRST) {
+      pdl_wait();
+      pdl_trigger();
+    }
     if constexpr (MODE == SURF_LAST) {
       // the element's right-hand side is complete: SSP-RK3 stage in increment form
       if (writer) {
@@ -561,6 +576,8 @@ template <int P>
 __global__ void __launch_bounds__(128) k_cfl1_tet(const double* c, const double* inr, int64_t ne, float* est,
                                                   unsigned* minbits, float* shadow) {
   using D = TetDim<P>;
+  pdl_wait();
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float best = FLT_MAX;
   if (e < ne) {
@@ -591,6 +608,8 @@ __global__ void __launch_bounds__(128) k_cfl2_tet(const double* c, const double*
                                                   unsigned long long* dtbits) {
   using D = TetDim<P>;
   constexpr int NP = D::NP;
+  pdl_wait();
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool cand = e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin);
   unsigned mask = __ballot_sync(0xffffffffu, cand);
@@ -658,7 +677,7 @@ static int tsurf_launch(const Ctx& x, TetParams A) {
   auto kern = k_surf_tet<P, CT, ST, RT, MODE>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = 2 * x.epb;
-  kern<<<(unsigned)((2 * n + threads - 1) / threads), threads, smem, x.st>>>(A);
+  launch_k(x, kern, (unsigned)((2 * n + threads - 1) / threads), (unsigned)threads, smem, A);
   return 1;
 }
 
@@ -720,12 +739,12 @@ int tet_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow
   if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
   switch (x.p) {
     case 1:
-      k_cfl1_tet<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tet<1><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tet<1>, grid, bs, 0, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tet<1>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
-      k_cfl1_tet<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, est, mn, shadow);
-      k_cfl2_tet<2><<<grid, bs, 0, x.st>>>(s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tet<2>, grid, bs, 0, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tet<2>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }

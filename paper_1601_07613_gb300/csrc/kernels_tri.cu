@@ -35,27 +35,6 @@ namespace dgc {
 #define DGC_PRAGMA(x) DGC_PRAGMA_(x)
 #define DGC_UNROLL_Q DGC_PRAGMA(unroll DGC_QUNROLL)
 
-// A kernel launch on x.st; with x.pdl, as a programmatic dependent launch (the
-// kernels pair pdl_wait / pdl_trigger, dev_util.cuh).
-template <typename... KArgs, typename... Args>
-static void launch_k(const Ctx& x, void (*k)(KArgs...), unsigned grid, unsigned threads, Args... args) {
-  if (!x.pdl) {
-    k<<<grid, threads, 0, x.st>>>(args...);
-    return;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = x.st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k, args...);
-}
-
 template <int P>
 struct TriDim {
   static constexpr int NP = (P + 1) * (P + 2) / 2;
@@ -1358,16 +1337,16 @@ int tri_cfl_kahan(const Ctx& x, const float* ks, double cfl, double* dt) {
   if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
   switch (x.p) {
     case 1:
-      launch_k(x, k_cfl1_tri_k<1>, grid, bs, ks, x.d->inr, x.ne, est, mn);
-      launch_k(x, k_cfl2_tri<1, true>, grid, bs, ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri_k<1>, grid, bs, 0, ks, x.d->inr, x.ne, est, mn);
+      launch_k(x, k_cfl2_tri<1, true>, grid, bs, 0, ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
-      launch_k(x, k_cfl1_tri_k<2>, grid, bs, ks, x.d->inr, x.ne, est, mn);
-      launch_k(x, k_cfl2_tri<2, true>, grid, bs, ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri_k<2>, grid, bs, 0, ks, x.d->inr, x.ne, est, mn);
+      launch_k(x, k_cfl2_tri<2, true>, grid, bs, 0, ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 3:
-      launch_k(x, k_cfl1_tri_k<3>, grid, bs, ks, x.d->inr, x.ne, est, mn);
-      launch_k(x, k_cfl2_tri<3, true>, grid, bs, ks, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri_k<3>, grid, bs, 0, ks, x.d->inr, x.ne, est, mn);
+      launch_k(x, k_cfl2_tri<3, true>, grid, bs, 0, ks, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }
@@ -1599,7 +1578,7 @@ static int surf_launch(const Ctx& x, const SurfParams& A) {
   if (n <= 0) return 0;
   const int threads = 2 * x.epb;
   const int64_t grid = (2 * n + threads - 1) / threads;
-  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG>, (unsigned)grid, (unsigned)threads, A);
+  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG>, (unsigned)grid, (unsigned)threads, 0, A);
   return 1;
 }
 
@@ -1672,16 +1651,16 @@ int tri_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow
   if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
   switch (x.p) {
     case 1:
-      launch_k(x, k_cfl1_tri<1>, grid, bs, s, x.d->inr, x.ne, est, mn, shadow);
-      launch_k(x, k_cfl2_tri<1, false>, grid, bs, s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri<1>, grid, bs, 0, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tri<1, false>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 2:
-      launch_k(x, k_cfl1_tri<2>, grid, bs, s, x.d->inr, x.ne, est, mn, shadow);
-      launch_k(x, k_cfl2_tri<2, false>, grid, bs, s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri<2>, grid, bs, 0, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tri<2, false>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     case 3:
-      launch_k(x, k_cfl1_tri<3>, grid, bs, s, x.d->inr, x.ne, est, mn, shadow);
-      launch_k(x, k_cfl2_tri<3, false>, grid, bs, s, x.d->inr, x.ne, cfl, est, mn, bits);
+      launch_k(x, k_cfl1_tri<3>, grid, bs, 0, s, x.d->inr, x.ne, est, mn, shadow);
+      launch_k(x, k_cfl2_tri<3, false>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits);
       return 2;
     default: return -1;
   }

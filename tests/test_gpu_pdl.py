@@ -39,6 +39,7 @@ def _steps(torch, dev, m, prec, c_host, pdl, n=4, cfl=0.3):
         dts.append(float(dt.item()))
     torch.cuda.synchronize()
     out = dgc.dgc_export_state_prec(m.h, prec, st) if prec == dgc.DGC_FP32_KAHAN else dgc.dgc_export_state(m.h, st)
+    assert np.isfinite(out).all() and all(0.0 < d < 1.0 for d in dts)  # a physical run
     return out, dts
 
 
@@ -78,4 +79,20 @@ def test_pdl_refined_and_naive_colors_bit_identical(torch_dev):
     a, da = _steps(torch, dev, m, dgc.DGC_FP32_MIXED, c, True)
     b, db = _steps(torch, dev, m, dgc.DGC_FP32_MIXED, c, False)
     assert da == db and np.array_equal(a, b)
+    m.close()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_pdl_tetrahedra_bit_identical(torch_dev, p):
+    torch, dev = torch_dev
+    mi = W.periodic_cube_tet(5)
+    m = dgc.Mesh.from_input(mi, p)
+    m.color(1601)
+    c = W.random_state(mi.ne, 5, m.info["np"], seed=8, mean=(0.5, 0.05, -0.04, 0.03, 1.3))
+    for prec in (dgc.DGC_FP32_MIXED, dgc.DGC_FP64):
+        for fuse in (True, False):
+            dgc.dgc_set_option(m.h, dgc.DGC_OPT_FUSE, int(fuse))
+            a, da = _steps(torch, dev, m, prec, c, True, n=3)
+            b, db = _steps(torch, dev, m, prec, c, False, n=3)
+            assert da == db and np.array_equal(a, b)
     m.close()
