@@ -610,7 +610,7 @@ __device__ __forceinline__ void mode_sum(const float4 row, const float (&b)[P + 
 // Modes per batch of the last-color epilogue, per stage (stage 2 of the mixed
 // form needs an even batch: it pairs modes into double2)
 #ifndef DGC_JB0
-#define DGC_JB0 4
+#define DGC_JB0 6
 #endif
 #ifndef DGC_JB1
 #define DGC_JB1 4
@@ -1008,11 +1008,12 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 
 // Register caps of the FP32 surface kernels, chosen for resident warps
 // (blocks of 128 threads: 128 registers give 4 blocks per SM, 96 give 5, 80
-// give 6) and measured at p = 3: the middle colors and the last color's stage
-// 0 at 80; its stages 1 and 2, whose batches of four modes hold three operand
-// arrays, at 96; the first color (volume integral) and the kernels reading an
-// FP64 state (right-hand side calls and comparators), which keep the element
-// block in registers, at 128.  FP64 kernels are not capped.
+// give 6) and measured at p = 3: the middle colors at 80; the last color's
+// stage 0 (batches of six modes, two operand arrays) at 104 and its stages 1
+// and 2 (batches of four modes, three operand arrays) at 96; the first color
+// (volume integral) and the kernels reading an FP64 state (right-hand side
+// calls and comparators), which keep the element block in registers, at 128.
+// FP64 kernels are not capped.
 #ifndef DGC_REGS_P3_FIRST
 #define DGC_REGS_P3_FIRST 128
 #endif
@@ -1020,7 +1021,7 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 #define DGC_REGS_P3 80
 #endif
 #ifndef DGC_REGS_P3_LAST
-#define DGC_REGS_P3_LAST 80
+#define DGC_REGS_P3_LAST 104
 #endif
 #ifndef DGC_REGS_P3_LAST12
 #define DGC_REGS_P3_LAST12 96
