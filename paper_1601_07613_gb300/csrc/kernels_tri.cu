@@ -580,6 +580,16 @@ __device__ __forceinline__ void stage_etab32(float* s, int ntab) {
 
 // shared-memory float4 read kept where it is written (the compiler would
 // otherwise hoist the table reads of all modes and hold them in registers)
+__device__ __forceinline__ void sts4(float* p, float4 v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+// floats per lane of a shared-memory record slot: the record, as an odd number
+// of float4 so that the slots of eight consecutive lanes fall into distinct banks
+template <int P>
+__host__ __device__ constexpr int rec_slot() {
+  return 4 * ((TriDim<P>::NF / 4) | 1);
+}
 __device__ __forceinline__ float4 lds4(const float4* p) {
   float4 v;
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
@@ -627,7 +637,7 @@ __device__ __forceinline__ void mode_sum(const float4 row, const float (&b)[P + 
 // whose loads are all issued before the batch's stores, so that a batch costs
 // one memory round trip.  The buffers are distinct arrays.
 template <int P, int STG>
-__device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P + 1][4],
+__device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P + 1][4], const float4* rs,
                                            const float4* __restrict__ part, float4* __restrict__ dp,
                                            const float4* __restrict__ r0, float4* __restrict__ ro,
                                            float4* __restrict__ ks, double* __restrict__ u, double dt,
@@ -650,7 +660,10 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
       if (j >= NP) continue;
       pa[i] = part[j];
       if (STG >= 1) da[i] = dp[j];
-      if (STG <= 1) {
+      if (STG == 0 && rs) {
+        ha[i] = lds4(rs + (j == 0 ? 0 : j + 1));
+        if (j == 0) la[i] = lds4(rs + 1);
+      } else if (STG <= 1) {
         ha[i] = r0[j == 0 ? 0 : j + 1];
         if (j == 0) la[i] = r0[1];
       } else if (kahan) {
@@ -787,7 +800,7 @@ __device__ __forceinline__ void lf_exchange(const PertRef<2>& R, const EdgeConst
 // se: the edge tables (ETab32) in shared memory.
 template <int P, typename ST, typename RT, int MODE, int STG = -1>
 __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
-                                          const float* se) {
+                                          const float* se, float* rslot = nullptr) {
   using D = TriDim<P>;
   using T = ETab32<P>;
   constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV, K1 = P + 1;
@@ -831,6 +844,13 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
     const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(A.state) + elem * A.sstride);
 #pragma unroll
     for (int i = 0; i < D::NF / 4; ++i) rv[i] = __ldg(src + i);
+    if constexpr (MODE == SURF_LAST && STG == 0) {
+      // stage 0's epilogue needs this record again (it is the record of u0):
+      // it waits in the lane's shared-memory slot instead of being re-read
+      if (rslot)
+#pragma unroll
+        for (int i = 0; i < D::NF / 4; ++i) sts4(rslot + 4 * i, rv[i]);
+    }
     hi[0] = rv[0].x, hi[1] = rv[0].y, hi[2] = rv[0].z, hi[3] = rv[0].w;
     lo[0] = rv[1].x, lo[1] = rv[1].y, lo[2] = rv[1].z, lo[3] = rv[1].w;
   }
@@ -952,10 +972,11 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
       double* u = S.uout ? S.uout + elem * NV : nullptr;
       const double dt = *S.dt, phi0 = tri_tab<double, P>().phiV[0][0];
       const int stage = STG >= 0 ? STG : (S.stage == 2 && ks ? 3 : S.stage);
-      if (stage == 0) last_modes<P, 0>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
-      else if (stage == 1) last_modes<P, 1>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
-      else if (stage == 2) last_modes<P, 2>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
-      else last_modes<P, 3>(tb, bk, part, dp, r0, ro, ks, u, dt, phi0);
+      const float4* rs = reinterpret_cast<const float4*>(rslot);
+      if (stage == 0) last_modes<P, 0>(tb, bk, rs, part, dp, r0, ro, ks, u, dt, phi0);
+      else if (stage == 1) last_modes<P, 1>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
+      else if (stage == 2) last_modes<P, 2>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
+      else last_modes<P, 3>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
     } else if constexpr (sizeof(RT) == 4) {
       // read-modify-write in batches of JB modes, each batch's loads first
       constexpr int JB = 5;
@@ -1055,9 +1076,13 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
   const int4 tp = A.topo[k];
   if constexpr (sizeof(CT) == 4) {
     __shared__ __align__(16) float se[ETab32<P>::SIZE];
+    extern __shared__ float4 rslots[];  // the last color's stage 0: rec_slot<P>() floats per thread
     stage_etab32<P>(se, A.ntab);
     __syncthreads();
-    surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se);
+    float* rslot = nullptr;
+    if constexpr (MODE == SURF_LAST && STG == 0 && sizeof(ST) == 4)
+      rslot = reinterpret_cast<float*>(rslots) + threadIdx.x * rec_slot<P>();
+    surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se, rslot);
   } else {
     __shared__ double sphi[9 * D::NQE * D::NP];
     __shared__ double sw[D::NQE];
@@ -1579,7 +1604,17 @@ static int surf_launch(const Ctx& x, const SurfParams& A) {
   if (n <= 0) return 0;
   const int threads = 2 * x.epb;
   const int64_t grid = (2 * n + threads - 1) / threads;
-  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG>, (unsigned)grid, (unsigned)threads, 0, A);
+  const size_t smem =
+      MODE == SURF_LAST && STG == 0 && sizeof(ST) == 4 ? (size_t)threads * rec_slot<P>() * sizeof(float) : 0;
+  if (smem > 32 * 1024) {  // 256-thread blocks: above the default 48 KB with the static tables
+    static bool raised = false;
+    if (!raised) {
+      cudaFuncSetAttribute(k_surf_tri<P, CT, ST, RT, MODE, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           64 * 1024);
+      raised = true;
+    }
+  }
+  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG>, (unsigned)grid, (unsigned)threads, smem, A);
   return 1;
 }
 
