@@ -108,21 +108,55 @@ __device__ __forceinline__ float pert_wave(const PertRef<DIM>& R, const PertStat
   return fabsf((thb + dth) * ir) + sqrt_fast(1.4f * p * ir);
 }
 
-// Local Lax-Friedrichs flux minus F(ub).n, both traces given as deviations
-// from the same reference ub: G = (dF(dL) + dF(dR))/2 - lam (dR - dL)/2.
+// Exchanged-side form of the local Lax-Friedrichs flux for a lane pair (one
+// lane per element of an edge or face, each relative to its own element's
+// reference).  Per-face constants: the partner's reference relative to ours
+// dl = ub' - ub (exchanged), the normal, m_b.n, the references' flux difference
+// fb = (F(ub') - F(ub)).n, and sg = +1/2 on side 0 (whose own trace is the left
+// one), -1/2 on side 1.  All 32 lanes must call init.
 template <int DIM>
-__device__ __forceinline__ void pert_lf(const PertRef<DIM>& R, const float* dL, const float* dR, const float* n,
-                                        float thb, float* G) {
-  constexpr int M = DIM + 2;
-  PertState<DIM> SL, SR;
-  SL.init(R, dL);
-  SR.init(R, dR);
-  float FL[M], FR[M];
-  pert_flux<DIM>(R, SL, dL, n, thb, FL);
-  pert_flux<DIM>(R, SR, dR, n, thb, FR);
-  const float lam = fmaxf(pert_wave<DIM>(R, SL, dL, n, thb), pert_wave<DIM>(R, SR, dR, n, thb));
+struct FaceConst {
+  static constexpr int M = DIM + 2;
+  float dl[M], n[DIM], thb, fb[M], sg;
+  __device__ __forceinline__ void init(const PertRef<DIM>& R, const float (&hi)[M], const float (&nn)[DIM],
+                                       int side) {
 #pragma unroll
-  for (int k = 0; k < M; ++k) G[k] = 0.5f * (FL[k] + FR[k]) - 0.5f * lam * (dR[k] - dL[k]);
+    for (int m = 0; m < M; ++m) dl[m] = __shfl_xor_sync(0xffffffffu, hi[m], 1) - hi[m];
+    thb = 0.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      n[a] = nn[a];
+      thb += R.u[1 + a] * nn[a];
+    }
+    PertState<DIM> S;
+    S.init(R, dl);
+    pert_flux<DIM>(R, S, dl, n, thb, fb);
+    sg = side ? -0.5f : 0.5f;
+  }
+};
+
+// The flux minus F(ub).n at one point from the lane's own trace deviation
+// t = u - ub and the partner's (relative to the partner's reference): each lane
+// evaluates its own side and exchanges one value per variable,
+//   A = dF/2 + sg lam t   (the partner's A' = dF'/2 - sg lam t'),
+//   G = (dF + dF' + fb)/2 - sg lam (dl + t' - t) = A + A' + fb/2 - sg lam dl,
+// lam the larger of the two wave speeds.  All 32 lanes must call it.
+template <int DIM>
+__device__ __forceinline__ void lf_exchange(const PertRef<DIM>& R, const FaceConst<DIM>& E,
+                                            const float (&t)[DIM + 2], float (&G)[DIM + 2]) {
+  constexpr int M = DIM + 2;
+  PertState<DIM> S;
+  S.init(R, t);
+  float dF[M];
+  pert_flux<DIM>(R, S, t, E.n, E.thb, dF);
+  const float w = pert_wave<DIM>(R, S, t, E.n, E.thb);
+  const float lam = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, 1));
+  const float sl = E.sg * lam;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float a = fmaf(sl, t[m], 0.5f * dF[m]);
+    G[m] = (a + __shfl_xor_sync(0xffffffffu, a, 1)) + fmaf(-sl, E.dl[m], 0.5f * E.fb[m]);
+  }
 }
 
 }  // namespace dgc

@@ -488,19 +488,14 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_s
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
     if constexpr (MODE == SURF_FIRST) tet_volume32<P>(B, R, A.jinv + 9 * elem, acc);
-    float base[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      const float ho = __shfl_xor_sync(0xffffffffu, B.hi[m], 1);
-      const float lo = __shfl_xor_sync(0xffffffffu, B.lo[m], 1);
-      base[m] = (ho - B.hi[m]) + lo;
-    }
-    const float n[3] = {d2f(g0.x), d2f(g0.y), d2f(g1.x)};
+    // each lane evaluates its own side's flux and the pair exchanges one value
+    // per variable (euler_pert.cuh, lf_exchange)
+    FaceConst<3> E;
+    E.init(R, B.hi, {d2f(g0.x), d2f(g0.y), d2f(g1.x)}, side);
     const float scale = right ? d2f(g2.y) : -d2f(g2.x);
-    const float thb = R.u[1] * n[0] + R.u[2] * n[1] + R.u[3] * n[2];
 #pragma unroll 2
     for (int q = 0; q < NQ; ++q) {
-      float phi[NP], dU[5], dV[5], ds[5], dn[5], G[5];
+      float phi[NP], ds[5], G[5];
 #pragma unroll
       for (int j = 0; j < NP; ++j) phi[j] = ph[q * NP + j];
 #pragma unroll
@@ -508,17 +503,9 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_s
         float s = 0.0f;
 #pragma unroll
         for (int j = 1; j < NP; ++j) s += phi[j] * B.cd[m][j - 1];
-        dU[m] = s;
+        ds[m] = B.lo[m] + s;  // own trace - ub
       }
-#pragma unroll
-      for (int m = 0; m < 5; ++m) dV[m] = __shfl_xor_sync(0xffffffffu, dU[m], 1);
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        ds[m] = B.lo[m] + dU[m];
-        dn[m] = base[m] + dV[m];
-      }
-      if (side) pert_lf<3>(R, dn, ds, n, thb, G);
-      else pert_lf<3>(R, ds, dn, n, thb, G);
+      lf_exchange<3>(R, E, ds, G);
       const float s = scale * K.wF[q];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {

@@ -752,52 +752,6 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
   }
 }
 
-// Per-edge constants of a lane's flux evaluation: the partner's reference
-// relative to ours dl = ub' - ub (exchanged), the FP32 normal and the lane's
-// edge measure (signed: the left element receives minus the flux), m_b.n, the
-// references' flux difference fb = (F(ub') - F(ub)).n, and the sign of the
-// jump: (u_R - u_L)/2 = sg (dl + t' - t), the own trace being u_L on side 0.
-// All 32 lanes must call init.
-struct EdgeConst {
-  float dl[4], n[2], scale, thb, fb[4], sg;
-  __device__ __forceinline__ void init(const PertRef<2>& R, const float (&hi)[4], double2 g0, double2 g1,
-                                       bool right, int side) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) dl[m] = __shfl_xor_sync(0xffffffffu, hi[m], 1) - hi[m];
-    n[0] = d2f(g0.x);
-    n[1] = d2f(g0.y);
-    scale = right ? d2f(g1.y) : -d2f(g1.x);
-    thb = R.u[1] * n[0] + R.u[2] * n[1];
-    PertState<2> S;
-    S.init(R, dl);
-    pert_flux<2>(R, S, dl, n, thb, fb);
-    sg = side ? -0.5f : 0.5f;
-  }
-};
-
-// Local Lax-Friedrichs flux minus F(ub).n at one edge point, from the lane's
-// own trace deviation t = u - ub and the partner lane's.  Each lane evaluates
-// its own side and exchanges one value per variable: with
-//   A = dF/2 + sg lam t   (the partner's A' = dF'/2 - sg lam t'),
-//   G = (dF + dF' + fb)/2 - sg lam (dl + t' - t) = A + A' + fb/2 - sg lam dl.
-// All 32 lanes must call it.
-__device__ __forceinline__ void lf_exchange(const PertRef<2>& R, const EdgeConst& E, const float (&t)[4],
-                                            float (&G)[4]) {
-  PertState<2> S;
-  S.init(R, t);
-  float dF[4];
-  pert_flux<2>(R, S, t, E.n, E.thb, dF);
-  const float w = pert_wave<2>(R, S, t, E.n, E.thb);
-  const float lam = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, 1));
-  const float sl = E.sg * lam;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const float a = fmaf(sl, t[m], 0.5f * dF[m]);
-    G[m] = (a + __shfl_xor_sync(0xffffffffu, a, 1)) + fmaf(-sl, E.dl[m], 0.5f * E.fb[m]);
-  }
-}
-
-// se: the edge tables (ETab32) in shared memory.
 template <int P, typename ST, typename RT, int MODE, int STG = -1>
 __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
                                           const float* se, float* rslot = nullptr) {
@@ -890,8 +844,9 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
     volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
-    EdgeConst E;
-    E.init(R, hi, g0, g1, right, side);
+    FaceConst<2> E;
+    E.init(R, hi, {d2f(g0.x), d2f(g0.y)}, side);
+    const float escale = right ? d2f(g1.y) : -d2f(g1.x);  // the lane's signed edge measure
     float bk[K1][4];
 #pragma unroll
     for (int kk = 0; kk < K1; ++kk)
@@ -909,8 +864,8 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
         for (int kk = 1; kk < K1; ++kk) v = fmaf(L[kk], ak[kk][m], v);
         t[m] = v;
       }
-      lf_exchange(R, E, t, G);
-      const float s = E.scale * K.wE[q];
+      lf_exchange<2>(R, E, t, G);
+      const float s = escale * K.wE[q];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const float g = s * G[m];
@@ -930,8 +885,9 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
     else surf_write<P, RT, MODE>(A, elem, k, side, acc);
   } else {
     // 2. fluxes at every point; then 3. b_k = sum_q w_q G_q L_k(xi_q)
-    EdgeConst E;
-    E.init(R, hi, g0, g1, right, side);
+    FaceConst<2> E;
+    E.init(R, hi, {d2f(g0.x), d2f(g0.y)}, side);
+    const float escale = right ? d2f(g1.y) : -d2f(g1.x);  // the lane's signed edge measure
     float bk[K1][4];
 #pragma unroll
     for (int kk = 0; kk < K1; ++kk)
@@ -947,8 +903,8 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
         for (int kk = 1; kk < K1; ++kk) v = fmaf(EK.Lq[q][kk], ak[kk][m], v);
         t[m] = v;
       }
-      lf_exchange(R, E, t, G);
-      const float s = E.scale * K.wE[q];
+      lf_exchange<2>(R, E, t, G);
+      const float s = escale * K.wE[q];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const float g = s * G[m];
