@@ -382,14 +382,21 @@ __device__ __forceinline__ void tet_fp64_last(const TetParams& A, int64_t elem, 
   }
 }
 
-// FP32 surface kernels: minimum resident blocks of 256 threads per SM the
-// compiler must allow (register cap 65536 / (256 * min)); FP64 never capped.
+// FP32 surface kernels: a register cap (DGC_TET_REGS) and the minimum resident
+// blocks of 256 threads per SM the compiler must allow (DGC_TET_MINB); FP64
+// kernels are never capped.  At p = 2 the uncapped kernels take 176-242
+// registers (two blocks of 128 threads per SM); 168 keeps them spill-free with
+// three (measured: RK step 10.7 -> 9.2 ms on 64^3 x 6 tetrahedra).
+#ifndef DGC_TET_REGS
+#define DGC_TET_REGS 168
+#endif
 #ifndef DGC_TET_MINB
 #define DGC_TET_MINB 1
 #endif
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
-__global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1)) k_surf_tet(const TetParams A) {
+__global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
+    __maxnreg__((sizeof(CT) == 4 ? DGC_TET_REGS : 255)) k_surf_tet(const TetParams A) {
   using D = TetDim<P>;
   constexpr int NP = D::NP, NQ = D::NQF, NV = D::NV;
   extern __shared__ unsigned char smem_raw[];
