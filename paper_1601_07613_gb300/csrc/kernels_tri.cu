@@ -1429,6 +1429,8 @@ __global__ void __launch_bounds__(256) __maxnreg__((batch_regs<MODE, MIXED, STG>
 
 // dt and the FP32 minimum of every mesh set to a large value
 __global__ void k_batch_init(const BatchMeshDev* __restrict__ meshes, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   *reinterpret_cast<unsigned long long*>(meshes[i].dt) = 0x7F7F7F7F7F7F7F7Full;
@@ -1438,6 +1440,8 @@ __global__ void k_batch_init(const BatchMeshDev* __restrict__ meshes, int n) {
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_batch_cfl1(const BatchMeshDev* __restrict__ meshes,
                                                     const BatchTile* __restrict__ tiles, int nt) {
+  pdl_wait();
+  pdl_trigger();
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const BatchTile T = tiles[ti];
     const BatchMeshDev& B = meshes[T.mesh];
@@ -1456,6 +1460,8 @@ __global__ void __launch_bounds__(128) k_batch_cfl1(const BatchMeshDev* __restri
 
 __global__ void __launch_bounds__(128) k_batch_cfl2(const BatchMeshDev* __restrict__ meshes,
                                                     const BatchTile* __restrict__ tiles, int nt, double cfl) {
+  pdl_wait();
+  pdl_trigger();
   for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
     const BatchTile T = tiles[ti];
     const BatchMeshDev& B = meshes[T.mesh];
@@ -1470,6 +1476,16 @@ __global__ void __launch_bounds__(128) k_batch_cfl2(const BatchMeshDev* __restri
   }
 }
 
+// The batched step's kernels launch with programmatic dependent launch (the
+// surface kernels wait before their epilogues, the others at once); captured
+// into the step's CUDA graph they become programmatic edges.
+static Ctx pdl_ctx(cudaStream_t st) {
+  Ctx x;
+  x.st = st;
+  x.pdl = true;
+  return x;
+}
+
 static int persistent_grid(const void* kern, int threads, int ntiles) {
   int dev = 0, sms = 0, per = 1;
   cudaGetDevice(&dev);
@@ -1480,7 +1496,7 @@ static int persistent_grid(const void* kern, int threads, int ntiles) {
 }
 
 int batch_init(cudaStream_t st, const BatchMeshDev* d, int n) {
-  k_batch_init<<<(n + 127) / 128, 128, 0, st>>>(d, n);
+  launch_k(pdl_ctx(st), k_batch_init, (unsigned)((n + 127) / 128), 128u, 0, d, n);
   return 1;
 }
 
@@ -1488,9 +1504,9 @@ int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, in
   if (nt <= 0) return 0;
   const void* k1 = mixed ? (const void*)k_batch_cfl1<true> : (const void*)k_batch_cfl1<false>;
   const int g1 = persistent_grid(k1, 128, nt), g2 = persistent_grid((const void*)k_batch_cfl2, 128, nt);
-  if (mixed) k_batch_cfl1<true><<<g1, 128, 0, st>>>(d, tiles, nt);
-  else k_batch_cfl1<false><<<g1, 128, 0, st>>>(d, tiles, nt);
-  k_batch_cfl2<<<g2, 128, 0, st>>>(d, tiles, nt, cfl);
+  if (mixed) launch_k(pdl_ctx(st), k_batch_cfl1<true>, (unsigned)g1, 128u, 0, d, tiles, nt);
+  else launch_k(pdl_ctx(st), k_batch_cfl1<false>, (unsigned)g1, 128u, 0, d, tiles, nt);
+  launch_k(pdl_ctx(st), k_batch_cfl2, (unsigned)g2, 128u, 0, d, tiles, nt, cfl);
   return 2;
 }
 
@@ -1499,7 +1515,8 @@ static int batch_surf_launch(cudaStream_t st, const BatchMeshDev* d, const Batch
                              double a0, double b0, int threads) {
   if (nt <= 0) return 0;
   const int g = persistent_grid((const void*)k_batch_surf<MODE, MIXED, STG>, threads, nt);
-  k_batch_surf<MODE, MIXED, STG><<<g, threads, 0, st>>>(d, tiles, nt, stage, a0, b0);
+  launch_k(pdl_ctx(st), k_batch_surf<MODE, MIXED, STG>, (unsigned)g, (unsigned)threads, 0, d, tiles, nt, stage, a0,
+           b0);
   return 1;
 }
 
