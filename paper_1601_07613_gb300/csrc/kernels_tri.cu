@@ -578,23 +578,25 @@ __device__ __forceinline__ void stage_etab32(float* s, int ntab) {
   }
 }
 
-// shared-memory float4 read kept where it is written (the compiler would
-// otherwise hoist the table reads of all modes and hold them in registers)
+// Shared-memory float4 accesses kept where they are written (the compiler
+// would otherwise hoist the table reads of all modes and hold them in
+// registers).
 __device__ __forceinline__ void sts4(float* p, float4 v) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
-}
-// floats per lane of a shared-memory record slot: the record, as an odd number
-// of float4 so that the slots of eight consecutive lanes fall into distinct banks
-template <int P>
-__host__ __device__ constexpr int rec_slot() {
-  return 4 * ((TriDim<P>::NF / 4) | 1);
 }
 __device__ __forceinline__ float4 lds4(const float4* p) {
   float4 v;
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
   return v;
+}
+
+// floats per lane of a shared-memory record slot: the record, as an odd number
+// of float4 so that the slots of eight consecutive lanes fall into distinct banks
+template <int P>
+__host__ __device__ constexpr int rec_slot() {
+  return 4 * ((TriDim<P>::NF / 4) | 1);
 }
 
 __device__ __forceinline__ float4 f4_add(float4 a, const float (&b)[4]) {
@@ -781,7 +783,8 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
 
   // The element's state.  The first color (volume integral) and FP64 states
   // take it as a [M][NP] block; the other colors load the FP32 record as it is
-  // stored (mode-major), all of it in flight at once.
+  // stored (mode-major), all of it in flight at once (the last color's stage 0
+  // also parks it in the lane's shared-memory slot for its epilogue).
   constexpr bool BLOCK = MODE == SURF_FIRST || sizeof(ST) == 8;
   PertBlock<P> B;
   float4 rv[BLOCK ? 1 : D::NF / 4];
