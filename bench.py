@@ -604,8 +604,9 @@ def run_reference(args):
     bounded random sample of the workload's elements."""
     import oracle
 
-    cfg = W.jittered_square_vortex_p3_724x724()
+    cfg = W.jittered_square_vortex_p3_724x724(args.n)
     mi, p = cfg["mesh"], cfg["p"]
+    workload = WORKLOAD if args.n == 724 else f"2D Euler DG p=3 on {mi.ne} jittered periodic triangles ({args.n}x{args.n})"
     om = oracle.OracleMesh.from_input(mi)
     xyz, _, _ = om.eval_points(p)
     c = om.project(p, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=cfg["beta"]))
@@ -613,7 +614,7 @@ def run_reference(args):
     del xyz
     E = mi.ne
     NV = c.shape[1] * c.shape[2]
-    per_step = args.ref_elements
+    per_step = min(args.ref_elements, E)
     rng = np.random.default_rng(0)
     for _ in range(args.warmup):
         om.rhs(p, c, elems=rng.choice(E, per_step, replace=False))
