@@ -79,10 +79,11 @@ typedef enum {
                                    the launch stream, for dgc_profile_collect; 0 (default): off */
   DGC_OPT_GRAPH = 4,            /* batches: 1 (default) capture the step in a CUDA graph on the
                                    first call and replay it; 0: launch the kernels directly */
-  DGC_OPT_PDL = 5               /* meshes: 1 (default) launch the RK step's surface and CFL kernels
-                                   with programmatic dependent launch (each kernel's work that does
-                                   not read its predecessor's output overlaps the predecessor's
-                                   end); 0: plain stream order.  Results are identical. */
+  DGC_OPT_PDL = 5               /* meshes: 1 (default) launch the surface and CFL kernels of
+                                   dgc_rk_step, dgc_rhs and the comparators with programmatic
+                                   dependent launch (each kernel's work that does not read its
+                                   predecessor's output overlaps the predecessor's end); 0: plain
+                                   stream order.  Results are identical. */
 } dgc_option;
 
 /* Kernel classes reported by dgc_profile_collect. */

@@ -869,6 +869,7 @@ dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const void* c_dev, double* rhs
     check_ptr(rhs_dev, "rhs_dev");
     require(c_dev != rhs_dev, "c_dev and rhs_dev must not alias");
     Ctx x = ready(m, stream);
+    x.pdl = m.pdl;
     if (prec == DGC_FP32_KAHAN) finish(m, launch_rhs(m, x, TY_KD, c_dev, (int)kahan_floats(m), rhs_dev));
     else finish(m, launch_rhs(m, x, prec == DGC_FP64 ? TY_D : TY_MD, c_dev, 0, rhs_dev));
   });
@@ -919,6 +920,7 @@ dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, do
     check_ptr(c_dev, "c_dev");
     check_ptr(rhs_dev, "rhs_dev");
     Ctx x = ready(m, stream);
+    x.pdl = m.pdl;
     const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
     int64_t n = 0;
     run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, 0, rhs_dev); });
@@ -944,6 +946,7 @@ dgc_status dgc_rhs_two_pass(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, 
     check_ptr(buffer_dev, "buffer_dev");
     require(buffer_size >= 2 * m.ns * nv_of(m) * (int64_t)sizeof(double), "buffer smaller than dgc_two_pass_buffer_bytes()");
     Ctx x = ready(m, stream);
+    x.pdl = m.pdl;
     const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
     int64_t n = 0;
     run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, 0, rhs_dev); });

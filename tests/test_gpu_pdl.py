@@ -96,3 +96,46 @@ def test_pdl_tetrahedra_bit_identical(torch_dev, p):
             b, db = _steps(torch, dev, m, prec, c, False, n=3)
             assert da == db and np.array_equal(a, b)
     m.close()
+
+
+def _rhs(torch, dev, m, prec, c_host, pdl, kind):
+    dgc.dgc_set_option(m.h, dgc.DGC_OPT_PDL, int(pdl))
+    st = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    dgc.dgc_import_state(m.h, c_host, st)
+    r = torch.full(m.state_shape(), float("nan"), dtype=torch.float64, device=dev)
+    if kind == "colored":
+        dgc.dgc_rhs(m.h, prec, st, r)
+    elif kind == "atomic":
+        dgc.dgc_rhs_atomic(m.h, prec, st, r)
+    else:
+        info = m.info
+        nb = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
+        buf = torch.empty(nb // 8, dtype=torch.float64, device=dev)
+        dgc.dgc_rhs_two_pass(m.h, prec, st, r, buf)
+    torch.cuda.synchronize()
+    return dgc.dgc_export_state(m.h, r)
+
+
+@pytest.mark.parametrize("kind", ["colored", "atomic", "two_pass"])
+def test_pdl_rhs_forms_identical(torch_dev, kind):
+    """dgc_rhs and the comparators with and without programmatic launch, on a
+    conforming and a refined mesh: the same bits (the colored and two-pass forms
+    sum in a fixed order; the atomic form's order varies, so it is compared to
+    within its rounding)."""
+    torch, dev = torch_dev
+    mi = W.periodic_square_tri(30, jitter=0.2, seed=73)
+    for refine in (False, True):
+        m = dgc.Mesh.from_input(mi, 3)
+        m.color(1601)
+        if refine:
+            m.refine(W.elements_near(mi, (0.5, 0.5), 0.3))
+        c = W.random_state(m.info["ne"], 4, m.info["np"], seed=9)
+        for prec in (dgc.DGC_FP32_MIXED, dgc.DGC_FP64):
+            a = _rhs(torch, dev, m, prec, c, True, kind)
+            b = _rhs(torch, dev, m, prec, c, False, kind)
+            assert np.isfinite(a).all()
+            if kind == "atomic":
+                assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+            else:
+                assert np.array_equal(a, b)
+        m.close()
