@@ -4,7 +4,9 @@ A plain, slow FP64 C implementation (``dg_oracle.c``) of what the CUDA path
 computes: the edge table, the paper's coloring and reordering (Sec. 3.1, Sec. 5)
 and the modal DG right-hand side of Eq. 2 evaluated element by element, plus the
 CFL rule and SSP-RK3 step.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with
+CPU-baseline leg of ``bench.py`` may import this package.  Quadrilateral and
+hybrid triangle/quadrilateral meshes are built from a [E][4] element list (-1 as
+the fourth vertex of a triangle).  It shares no code with
 ``paper_1601_07613_gb300`` (the product), and the product never imports it.
 
 This module only builds the C file with gcc and marshals numpy arrays through
@@ -71,6 +73,13 @@ def lib():
             L.orc_tet_rule.argtypes = [C.c_int, dp, dp, dp, dp]
             L.orc_basis_tri.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, dp]
             L.orc_basis_tet.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp]
+            L.orc_basis_quad.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, dp]
+            L.orc_quad_rule.argtypes = [C.c_int, dp, dp, dp]
+            L.orc_mesh_new_quad.restype = P
+            L.orc_mesh_new_quad.argtypes = [C.c_int64, dp, C.c_int64, C.POINTER(C.c_int32), dp]
+            L.orc_mesh_is_quad.argtypes = [P]
+            L.orc_mesh_nonaffine.restype = C.c_int64
+            L.orc_mesh_nonaffine.argtypes = [P]
             L.orc_mesh_new.restype = P
             L.orc_mesh_new.argtypes = [C.c_int, C.c_int64, dp, C.c_int64, C.POINTER(C.c_int32), dp]
             L.orc_mesh_free.argtypes = [P]
@@ -128,8 +137,30 @@ def tet_rule(n: int):
     return r, s, t, w
 
 
-def npoly(dim: int, p: int) -> int:
+def quad_rule(n: int):
+    r, s, w = (np.zeros(n * n) for _ in range(3))
+    _check(lib().orc_quad_rule(n, _d(r), _d(s), _d(w)))
+    return r, s, w
+
+
+def npoly(dim: int, p: int, quad: bool = False) -> int:
+    if quad:
+        return (p + 1) ** 2
     return (p + 1) * (p + 2) // 2 if dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def basis_quad(p: int, r, s):
+    """Q_p tensor Legendre basis on [0,1]^2: phi, dphi/dr, dphi/ds, arrays (npts, (p+1)^2)."""
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    s = np.atleast_1d(np.asarray(s, dtype=np.float64))
+    n = npoly(2, p, quad=True)
+    out = [np.zeros((r.size, n)) for _ in range(3)]
+    buf = [np.zeros(n) for _ in range(3)]
+    for i in range(r.size):
+        _check(lib().orc_basis_quad(p, float(r[i]), float(s[i]), _d(buf[0]), _d(buf[1]), _d(buf[2])))
+        for k in range(3):
+            out[k][i] = buf[k]
+    return tuple(out)
 
 
 def basis_tri(p: int, r, s):
@@ -173,13 +204,21 @@ class OracleMesh:
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._ev = np.ascontiguousarray(ev, dtype=np.int32)
         self.ne = int(self._ev.shape[0])
+        self.quad = dim == 2 and self._ev.shape[1] == 4
         self._L = None if periodic_len is None else np.ascontiguousarray(periodic_len, dtype=np.float64)
-        h = lib().orc_mesh_new(dim, self._xyz.shape[0], _d(self._xyz), self.ne, _i32(self._ev),
-                               _d(self._L) if self._L is not None else None)
+        L = _d(self._L) if self._L is not None else None
+        if self.quad:
+            h = lib().orc_mesh_new_quad(self._xyz.shape[0], _d(self._xyz), self.ne, _i32(self._ev), L)
+        else:
+            h = lib().orc_mesh_new(dim, self._xyz.shape[0], _d(self._xyz), self.ne, _i32(self._ev), L)
         if not h:
             raise ValueError("oracle: " + lib().orc_last_error().decode())
         self._h = h
         self.ns = int(lib().orc_mesh_nsides(h))
+        self.nonaffine = int(lib().orc_mesh_nonaffine(h))
+
+    def np_modes(self, p: int) -> int:
+        return npoly(self.dim, p, self.quad)
 
     @classmethod
     def from_input(cls, mi):
@@ -197,6 +236,8 @@ class OracleMesh:
             raise ValueError("oracle: " + lib().orc_last_error().decode())
         m = OracleMesh.__new__(OracleMesh)
         m.dim = self.dim
+        m.quad = False
+        m.nonaffine = 0
         m._h = h
         m.ne = int(lib().orc_mesh_nelem(h))
         m.ns = int(lib().orc_mesh_nsides(h))
@@ -208,8 +249,9 @@ class OracleMesh:
         return m
 
     def elements(self):
-        """Vertex ids [E][dim+1] and unwrapped coordinates [E][dim+1][dim]."""
-        nvpe = self.dim + 1
+        """Vertex ids [E][nvpe] and unwrapped coordinates [E][nvpe][dim] (nvpe = 4 for
+        quadrilateral meshes, else dim + 1)."""
+        nvpe = 4 if self.quad else self.dim + 1
         ev = np.zeros((self.ne, nvpe), np.int32)
         X = np.zeros((self.ne, nvpe, self.dim))
         lib().orc_mesh_elements(self._h, _i32(ev), _d(X))
@@ -267,7 +309,7 @@ class OracleMesh:
             nq_face1: int = 0, nq_vol1: int = 0) -> np.ndarray:
         c = np.ascontiguousarray(c, dtype=np.float64)
         M = c.shape[1]
-        n = npoly(self.dim, p)
+        n = self.np_modes(p)
         assert c.shape == (self.ne, M, n), c.shape
         if elems is None:
             out = np.zeros_like(c)
@@ -312,6 +354,6 @@ class OracleMesh:
     def project(self, p: int, vals: np.ndarray) -> np.ndarray:
         vals = np.ascontiguousarray(vals, dtype=np.float64)
         M = vals.shape[2]
-        c = np.zeros((self.ne, M, npoly(self.dim, p)))
+        c = np.zeros((self.ne, M, self.np_modes(p)))
         _check(lib().orc_project(self._h, p, M, _d(vals), _d(c)))
         return c

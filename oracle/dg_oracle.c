@@ -20,7 +20,10 @@
  *   - the modified greedy coloring, the conflict resolution by swaps and the
  *     loop breaking of Sec. 3.1;
  *   - the color-major edge order, the color-1 element renumbering and the
- *     left-ascending order of the remaining colors of Sec. 5 (Tables 5, 6).
+ *     left-ascending order of the remaining colors of Sec. 5 (Tables 5, 6);
+ *   - quadrilateral and hybrid triangle/quadrilateral meshes, colored with
+ *     C = {1, 2, 3, 4} (Sec. 3.1, Table 2), and Eq. 2 on parallelogram
+ *     quadrilaterals.
  *
  * The paper leaves the DG ingredients to its reference [giuliani]; the readings
  * used here (orthonormal Dubiner basis, Gauss rules, local Lax-Friedrichs flux,
@@ -275,6 +278,62 @@ int orc_basis_tet(int p, double r, double s, double t, double *phi, double *dr, 
   return n;
 }
 
+/* Quadrilateral (reading: the paper colors quadrilateral meshes but leaves
+ * their DG space to [giuliani]): the tensor-product Legendre space Q_p on the
+ * reference square [0,1]^2, phi_{a,b}(r, s) = l_a(r) l_b(s), where
+ * l_n(x) = sqrt(2n+1) P_n(2x-1) is orthonormal on [0, 1]; mode j = a (p+1) + b,
+ * so mode 0 is the constant.  P_n from Bonnet's recurrence
+ * (n+1) P_{n+1}(t) = (2n+1) t P_n(t) - n P_{n-1}(t), derivatives from
+ * P'_{n+1} = P'_{n-1} + (2n+1) P_n. */
+static void legendre01(int p, double x, double *l, double *dl) {
+  double t = 2.0 * x - 1.0, P[ORC_MAXP + 2], D[ORC_MAXP + 2];
+  P[0] = 1.0;
+  D[0] = 0.0;
+  P[1] = t;
+  D[1] = 1.0;
+  for (int n = 1; n < p; ++n) {
+    P[n + 1] = ((2 * n + 1) * t * P[n] - n * P[n - 1]) / (n + 1);
+    D[n + 1] = D[n - 1] + (2 * n + 1) * P[n];
+  }
+  for (int n = 0; n <= p; ++n) {
+    double c = sqrt(2.0 * n + 1.0);
+    l[n] = c * P[n];
+    if (dl) dl[n] = 2.0 * c * D[n]; /* dt/dx = 2 */
+  }
+}
+
+static int npoly_quad(int p) { return (p + 1) * (p + 1); }
+
+int orc_basis_quad(int p, double r, double s, double *phi, double *dr, double *ds) {
+  if (p < 0 || p > ORC_MAXP) return fail("basis_quad: p out of range");
+  double lr[ORC_MAXP + 2], dlr[ORC_MAXP + 2], ls[ORC_MAXP + 2], dls[ORC_MAXP + 2];
+  legendre01(p, r, lr, dlr);
+  legendre01(p, s, ls, dls);
+  for (int a = 0; a <= p; ++a)
+    for (int b = 0; b <= p; ++b) {
+      int j = a * (p + 1) + b;
+      phi[j] = lr[a] * ls[b];
+      if (dr) dr[j] = dlr[a] * ls[b];
+      if (ds) ds[j] = lr[a] * dls[b];
+    }
+  return 0;
+}
+
+/* Square [0,1]^2: n x n Gauss-Legendre points, point i n + k at
+ * (x_i, x_k); weights sum to 1. */
+int orc_quad_rule(int n, double *r, double *s, double *w) {
+  double x[64], wg[64];
+  if (n < 1 || n > 64) return fail("quad_rule: n out of range");
+  if (orc_gauss_legendre(n, x, wg)) return -1;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      r[i * n + k] = 0.5 * (1.0 + x[i]);
+      s[i * n + k] = 0.5 * (1.0 + x[k]);
+      w[i * n + k] = 0.25 * wg[i] * wg[k];
+    }
+  return 0;
+}
+
 /* ======================================================================= */
 /* Mesh: edge/face table (Sec. 2 connectivity graph, Sec. 5 edge table)     */
 /* ======================================================================= */
@@ -282,13 +341,20 @@ int orc_basis_tet(int p, double r, double s, double t, double *phi, double *dr, 
  * vertex ids; faces are numbered in order of first appearance when elements
  * 0..E-1 and their local faces 0..F-1 are scanned; the left element is the
  * first to list the face, the right the second (-1 on a boundary).
- * Local face q of a triangle (v0,v1,v2) is (v_q, v_{q+1 mod 3}); local face q
- * of a tetrahedron is the face opposite vertex q.  Periodic meshes share
+ * Local face q of a triangle (v0,v1,v2) is (v_q, v_{q+1 mod 3}), of a
+ * quadrilateral (v0,v1,v2,v3) (v_q, v_{q+1 mod 4}); local face q of a
+ * tetrahedron is the face opposite vertex q.  Periodic meshes share
  * vertex ids across the period; each element's coordinates are unwrapped to
  * lie within half a period of its vertex 0. */
 
 typedef struct {
   int dim, nvpe, nfpe;
+  /* quadrilateral meshes: nvpe = nfpe = 4; a triangle of a hybrid mesh lists
+   * -1 as its fourth vertex and has faces 0..2 only.  nonaffine counts the
+   * elements Eq. 2 is not evaluated on here (quadrilaterals that are not
+   * parallelograms, triangles of hybrid meshes). */
+  int quad;
+  int64_t nonaffine;
   int64_t nv, ne, ns;
   double L[3];
   int periodic;
@@ -316,6 +382,26 @@ static void face_verts(int dim, int q, int *fv) {
     for (int k = 0; k < 4; ++k)
       if (k != q) fv[n++] = k;
   }
+}
+
+/* faces of element e: 4 for a quadrilateral, 3 for a triangle (also one of a
+ * hybrid mesh), 4 for a tetrahedron */
+static int elem_nfaces(const orc_mesh *m, int64_t e) {
+  if (!m->quad) return m->nfpe;
+  return m->ev[e * 4 + 3] < 0 ? 3 : 4;
+}
+
+static void face_verts_e(const orc_mesh *m, int64_t e, int q, int *fv) {
+  if (m->dim == 2) {
+    fv[0] = q;
+    fv[1] = (q + 1) % elem_nfaces(m, e);
+  } else {
+    face_verts(3, q, fv);
+  }
+}
+
+static int npoly_m(const orc_mesh *m, int p) {
+  return m->quad ? npoly_quad(p) : (m->dim == 2 ? npoly_tri(p) : npoly_tet(p));
 }
 
 typedef struct {
@@ -367,27 +453,47 @@ static double det_and_inv(int dim, const double *J, double *Ji) {
 
 void orc_mesh_free(void *h);
 
-/* detJ and J^-1 of element e from its unwrapped coordinates; -1 if detJ <= 0 */
+/* detJ and J^-1 of element e from its unwrapped coordinates; -1 if detJ <= 0.
+ * Simplices map the reference vertices (0,..), (1,0,..), (0,1,..), .. to
+ * v0, v1, v2, ..; a quadrilateral maps the square's corners (0,0), (1,0),
+ * (1,1), (0,1) to v0..v3, affinely through v0, v1, v3 (exact when it is a
+ * parallelogram, v2 = v1 + v3 - v0; otherwise counted in m->nonaffine).  A
+ * quadrilateral must also turn counterclockwise at every corner. */
 static int elem_geometry(orc_mesh *m, int64_t e) {
   int dim = m->dim;
   double J[9];
   const double *X = m->X + e * m->nvpe * dim;
+  int nf = elem_nfaces(m, e);
+  int kv[3] = {1, (m->quad && nf == 4) ? 3 : 2, 3};
   for (int a = 0; a < dim; ++a)
-    for (int k = 0; k < dim; ++k) J[a * dim + k] = X[(k + 1) * dim + a] - X[a];
+    for (int k = 0; k < dim; ++k) J[a * dim + k] = X[kv[k] * dim + a] - X[a];
   double det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
   m->detJ[e] = det;
+  if (m->quad && nf == 3) m->nonaffine++;
+  if (m->quad && nf == 4) {
+    double scale = 0.0, off = 0.0;
+    for (int c = 0; c < 4; ++c) {
+      const double *A = X + c * 2, *B = X + ((c + 1) % 4) * 2, *Cc = X + ((c + 3) % 4) * 2;
+      double cr = (B[0] - A[0]) * (Cc[1] - A[1]) - (B[1] - A[1]) * (Cc[0] - A[0]);
+      if (!(cr > 0.0)) return -1;
+      scale = fmax(scale, fabs(B[0] - A[0]) + fabs(B[1] - A[1]));
+    }
+    for (int a = 0; a < 2; ++a) off = fmax(off, fabs(X[a] + X[4 + a] - X[2 + a] - X[6 + a]));
+    if (off > 1e-12 * scale) m->nonaffine++;
+  }
   return det > 0.0 ? 0 : -1;
 }
 
-void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
-                   const double *L) {
+static void *mesh_new(int dim, int quad, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
+                      const double *L) {
   if (dim != 2 && dim != 3) return fail("mesh: dim must be 2 or 3"), (void *)0;
   if (ne <= 0 || nv <= 0 || ne > (1LL << 30) || nv > (1LL << 30))
     return fail("mesh: element or vertex count out of range"), (void *)0;
   orc_mesh *m = (orc_mesh *)calloc(1, sizeof *m);
   m->dim = dim;
-  m->nvpe = dim + 1;
-  m->nfpe = dim + 1;
+  m->quad = quad;
+  m->nvpe = quad ? 4 : dim + 1;
+  m->nfpe = quad ? 4 : dim + 1;
   m->nv = nv;
   m->ne = ne;
   m->periodic = L != NULL;
@@ -401,6 +507,10 @@ void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int
   for (int64_t e = 0; e < ne; ++e) {
     for (int k = 0; k < nvpe; ++k) {
       int32_t v = ev[e * nvpe + k];
+      if (quad && k == 3 && v == -1) {  /* triangle of a hybrid mesh */
+        for (int a = 0; a < dim; ++a) m->X[(e * nvpe + k) * dim + a] = m->X[(e * nvpe) * dim + a];
+        continue;
+      }
       if (v < 0 || v >= nv) {
         orc_mesh_free(m);
         return fail("mesh: vertex id out of range"), (void *)0;
@@ -419,26 +529,27 @@ void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int
       return fail("mesh: element with non-positive Jacobian"), (void *)0;
     }
   }
-  /* face table by sorting keys */
-  int64_t nent = ne * nfpe;
+  /* face table by sorting keys (slot e * nfpe + q; a hybrid mesh's triangles
+   * have no slot 3) */
+  int64_t nent = ne * nfpe, nkeys = 0;
   fkey *keys = (fkey *)malloc(sizeof(fkey) * nent);
   for (int64_t e = 0; e < ne; ++e)
-    for (int q = 0; q < nfpe; ++q) {
+    for (int q = 0; q < elem_nfaces(m, e); ++q) {
       int fv[3];
-      face_verts(dim, q, fv);
-      fkey *k = keys + e * nfpe + q;
+      face_verts_e(m, e, q, fv);
+      fkey *k = keys + nkeys++;
       k->k[2] = -1;
       for (int i = 0; i < dim; ++i) k->k[i] = ev[e * nvpe + fv[i]];
       sort3(k->k, dim);
       k->idx = e * nfpe + q;
     }
-  qsort(keys, nent, sizeof(fkey), fkey_cmp);
+  qsort(keys, nkeys, sizeof(fkey), fkey_cmp);
   int64_t *partner = (int64_t *)malloc(sizeof(int64_t) * nent);
   char *first = (char *)calloc(nent, 1);
   int bad = 0;
-  for (int64_t i = 0; i < nent;) {
+  for (int64_t i = 0; i < nkeys;) {
     int64_t j = i + 1;
-    while (j < nent && memcmp(keys[j].k, keys[i].k, sizeof keys[i].k) == 0) ++j;
+    while (j < nkeys && memcmp(keys[j].k, keys[i].k, sizeof keys[i].k) == 0) ++j;
     if (j - i > 2) bad = 1;
     if (j - i == 2 && keys[i].idx / nfpe == keys[i + 1].idx / nfpe) bad = 1;
     first[keys[i].idx] = 1;
@@ -459,6 +570,7 @@ void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int
   m->sr = (int32_t *)malloc(sizeof(int32_t) * nent);
   m->sql = (int8_t *)malloc(nent);
   m->sqr = (int8_t *)malloc(nent);
+  for (int64_t i = 0; i < nent; ++i) m->es[i] = m->enb[i] = -1;
   int64_t ns = 0;
   for (int64_t i = 0; i < nent; ++i) {
     if (!first[i]) continue;
@@ -484,6 +596,19 @@ void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int
   free(first);
   return m;
 }
+
+void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
+                   const double *L) {
+  return mesh_new(dim, 0, nv, xyz, ne, ev, L);
+}
+
+/* quadrilateral or hybrid mesh: ev is [ne][4], -1 as the fourth id of a triangle */
+void *orc_mesh_new_quad(int64_t nv, const double *xyz, int64_t ne, const int32_t *ev, const double *L) {
+  return mesh_new(2, 1, nv, xyz, ne, ev, L);
+}
+
+int orc_mesh_is_quad(void *h) { return ((orc_mesh *)h)->quad; }
+int64_t orc_mesh_nonaffine(void *h) { return ((orc_mesh *)h)->nonaffine; }
 
 void orc_mesh_free(void *h) {
   orc_mesh *m = (orc_mesh *)h;
@@ -546,7 +671,7 @@ static int avail_colors(const orc_mesh *m, const int8_t *col, int nc, int64_t k,
     if (el[side] < 0) continue;
     for (int q = 0; q < m->nfpe; ++q) {
       int32_t f = m->es[(int64_t)el[side] * m->nfpe + q];
-      if (f != k && col[f] > 0) used[col[f]] = 1;
+      if (f >= 0 && f != k && col[f] > 0) used[col[f]] = 1;
     }
   }
   int n = 0;
@@ -609,12 +734,12 @@ int orc_color(void *h, int nc, uint64_t seed, int64_t max_swaps, int8_t *col, in
       for (int side = 0; side < 2; ++side)
         for (int q = 0; q < m->nfpe; ++q) {
           int32_t f = m->es[(int64_t)el[side] * m->nfpe + q];
-          if (f != e && col[f] > 0) cnt[col[f]]++;
+          if (f >= 0 && f != e && col[f] > 0) cnt[col[f]]++;
         }
       for (int side = 0; side < 2; ++side)
         for (int q = 0; q < m->nfpe; ++q) {
           int32_t f = m->es[(int64_t)el[side] * m->nfpe + q];
-          if (f == e || f == prev || col[f] <= 0) continue;
+          if (f < 0 || f == e || f == prev || col[f] <= 0) continue;
           if (cnt[col[f]] == 1) cand[nca++] = f;
         }
       if (nca > 0) {
@@ -638,10 +763,10 @@ int orc_color(void *h, int nc, uint64_t seed, int64_t max_swaps, int8_t *col, in
         int32_t a = -1, b = -1;
         for (int q = 0; q < m->nfpe; ++q) {
           int32_t f = m->es[(int64_t)el[0] * m->nfpe + q];
-          if (f != e && col[f] == c) a = f;
+          if (f >= 0 && f != e && col[f] == c) a = f;
           if (el[1] >= 0) {
             int32_t f2 = m->es[(int64_t)el[1] * m->nfpe + q];
-            if (f2 != e && col[f2] == c) b = f2;
+            if (f2 >= 0 && f2 != e && col[f2] == c) b = f2;
           }
         }
         if (a >= 0 && b >= 0) {
@@ -789,7 +914,7 @@ static int find_edge(const orc_mesh *m, int64_t e, int32_t x, int32_t y) {
 
 void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   const orc_mesh *b = (const orc_mesh *)h;
-  if (b->dim != 2) return fail("refine: triangles only"), (void *)0;
+  if (b->dim != 2 || b->quad) return fail("refine: triangles only"), (void *)0;
   int64_t ne0 = b->ne, ns0 = b->ns, ne = 0, nv = b->nv, nref = 0;
   int64_t *first = (int64_t *)malloc(sizeof(int64_t) * ne0);
   for (int64_t e = 0; e < ne0; ++e) {
@@ -1048,9 +1173,10 @@ int orc_lf_flux(int dim, const double *Um, const double *Up, const double *n, do
 /* Eq. 2, element by element                                                */
 /* ======================================================================= */
 
-static int basis_eval(int dim, int p, const double *x, double *phi, double *d0, double *d1,
+static int basis_eval(const orc_mesh *m, int p, const double *x, double *phi, double *d0, double *d1,
                       double *d2) {
-  if (dim == 2) return orc_basis_tri(p, x[0], x[1], phi, d0, d1);
+  if (m->quad) return orc_basis_quad(p, x[0], x[1], phi, d0, d1);
+  if (m->dim == 2) return orc_basis_tri(p, x[0], x[1], phi, d0, d1);
   return orc_basis_tet(p, x[0], x[1], x[2], phi, d0, d1, d2);
 }
 
@@ -1075,10 +1201,10 @@ static void ref_coords(const orc_mesh *m, int64_t e, const double *x, double *rs
   }
 }
 
-static void eval_state(int dim, int p, int M, int Np, const double *c, const double *rs,
+static void eval_state(const orc_mesh *m, int p, int M, int Np, const double *c, const double *rs,
                        double *U) {
   double phi[ORC_MAXNP];
-  basis_eval(dim, p, rs, phi, NULL, NULL, NULL);
+  basis_eval(m, p, rs, phi, NULL, NULL, NULL);
   for (int k = 0; k < M; ++k) {
     double v = 0.0;
     for (int j = 0; j < Np; ++j) v += c[k * Np + j] * phi[j];
@@ -1089,7 +1215,8 @@ static void eval_state(int dim, int p, int M, int Np, const double *c, const dou
 /* Quadrature rules of one call, computed once.  Default sizes (reading, fixed
  * by the configurations' "7-pt edge / 16-pt area" at p = 3): triangle edges
  * 2p+1 Gauss points, triangle areas (p+1)^2; tetrahedron faces (p+2)^2,
- * volumes (p+2)^3.  Face points are given in the face's own parameters:
+ * volumes (p+2)^3; quadrilaterals as triangles, (p+1)^2 tensor Gauss points
+ * on the square and 2p+1 on an edge.  Face points are given in the face's own parameters:
  * t in [0,1] along an edge, (sigma, tau) on a triangular face; face weights
  * sum to 1. */
 typedef struct {
@@ -1112,7 +1239,7 @@ static void rules_free(orc_rules *R) {
   memset(R, 0, sizeof *R);
 }
 
-static int rules_make(int dim, int nf1, int nv1, orc_rules *R) {
+static int rules_make(int dim, int quad, int nf1, int nv1, orc_rules *R) {
   memset(R, 0, sizeof *R);
   R->dim = dim;
   if (nf1 < 1 || nf1 > 64 || nv1 < 1 || nv1 > 64) return fail("rules: size out of range");
@@ -1121,8 +1248,9 @@ static int rules_make(int dim, int nf1, int nv1, orc_rules *R) {
   R->vs = (double *)malloc(sizeof(double) * R->nv);
   R->vt = (double *)calloc(R->nv, sizeof(double));
   R->vw = (double *)malloc(sizeof(double) * R->nv);
-  int rc = dim == 2 ? orc_tri_rule(nv1, R->vr, R->vs, R->vw)
-                    : orc_tet_rule(nv1, R->vr, R->vs, R->vt, R->vw);
+  int rc = quad ? orc_quad_rule(nv1, R->vr, R->vs, R->vw)
+           : dim == 2 ? orc_tri_rule(nv1, R->vr, R->vs, R->vw)
+                      : orc_tet_rule(nv1, R->vr, R->vs, R->vt, R->vw);
   if (rc) return rc;
   R->nf = dim == 2 ? nf1 : nf1 * nf1;
   R->fa = (double *)malloc(sizeof(double) * R->nf);
@@ -1154,10 +1282,10 @@ typedef struct {
 static void face_geometry(const orc_mesh *m, int64_t e, int q, const orc_rules *R, orc_face *F) {
   int dim = m->dim;
   const double *X = m->X + e * m->nvpe * dim;
-  int fv[3];
-  face_verts(dim, q, fv);
+  int fv[3], nf = elem_nfaces(m, e);
+  face_verts_e(m, e, q, fv);
   const double *A = X + fv[0] * dim, *B = X + fv[1] * dim;
-  const double *O = dim == 2 ? X + ((q + 2) % 3) * dim : X + q * dim; /* opposite vertex */
+  const double *O = dim == 2 ? X + ((q + 2) % nf) * dim : X + q * dim; /* a vertex off the face */
   double u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) u[a] = B[a] - A[a];
   if (dim == 2) {
@@ -1195,7 +1323,7 @@ static void face_points_of_left(const orc_mesh *m, int64_t e, int32_t s, const o
   if (l == e) return;
   int dim = m->dim, fv[3];
   const double *X = m->X + l * m->nvpe * dim;
-  face_verts(dim, m->sql[s], fv);
+  face_verts_e(m, l, m->sql[s], fv);
   const double *A = X + fv[0] * dim, *B = X + fv[1] * dim, *C = dim == 3 ? X + fv[2] * dim : A;
   for (int i = 0; i < R->nf; ++i)
     for (int a = 0; a < dim; ++a)
@@ -1213,13 +1341,14 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim;
   if (p < 0 || p > ORC_MAXP) return fail("rhs: p out of range");
-  int Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  if (m->nonaffine) return fail("rhs: quadrilaterals must be parallelograms (hybrid meshes are colored only)");
+  int Np = npoly_m(m, p);
   orc_phys ph = {kind, dim, kind == ORC_EULER ? dim + 2 : 1, {0, 0, 0}};
   if (adv)
     for (int a = 0; a < dim; ++a) ph.adv[a] = adv[a];
   int M = ph.M;
   orc_rules R;
-  if (rules_make(dim, nq_face1 > 0 ? nq_face1 : default_face_n1(dim, p),
+  if (rules_make(dim, m->quad, nq_face1 > 0 ? nq_face1 : default_face_n1(dim, p),
                  nq_vol1 > 0 ? nq_vol1 : default_vol_n1(dim, p), &R)) {
     rules_free(&R);
     return -1;
@@ -1237,7 +1366,7 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
     for (int q = 0; q < R.nv; ++q) {
       double x[3] = {R.vr[q], R.vs[q], R.vt[q]};
       double phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM];
-      basis_eval(dim, p, x, phi, d[0], d[1], d[2]);
+      basis_eval(m, p, x, phi, d[0], d[1], d[2]);
       for (int k = 0; k < M; ++k) {
         double v = 0.0;
         for (int j = 0; j < Np; ++j) v += ce[k * Np + j] * phi[j];
@@ -1273,16 +1402,16 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
       for (int q = 0; q < F.nq; ++q) {
         double rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];
         ref_coords(m, e, F.x + 3 * q, rs);
-        eval_state(dim, p, M, Np, ce, rs, Um);
+        eval_state(m, p, M, Np, ce, rs, Um);
         if (nb >= 0) {
           double rn[3];
           ref_coords(m, nb, F.x + 3 * q, rn);
-          eval_state(dim, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
+          eval_state(m, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
         } else {
           for (int k = 0; k < M; ++k) Up[k] = Um[k];
         }
         num_flux(&ph, Um, Up, F.n, Fs);
-        basis_eval(dim, p, rs, phi, NULL, NULL, NULL);
+        basis_eval(m, p, rs, phi, NULL, NULL, NULL);
         for (int j = 0; j < Np; ++j)
           for (int k = 0; k < M; ++k) re[k * Np + j] -= scale * F.w[q] * phi[j] * Fs[k];
       }
@@ -1300,9 +1429,10 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
  * (the inradius), lambda_i = max over the element's volume points of |u|+c. */
 int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
   orc_mesh *m = (orc_mesh *)h;
-  int dim = m->dim, M = dim + 2, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  int dim = m->dim, M = dim + 2, Np = npoly_m(m, p);
+  if (m->nonaffine) return fail("dt: quadrilaterals must be parallelograms");
   orc_rules R;
-  if (rules_make(dim, 1, default_vol_n1(dim, p), &R)) {
+  if (rules_make(dim, m->quad, 1, default_vol_n1(dim, p), &R)) {
     rules_free(&R);
     return -1;
   }
@@ -1313,7 +1443,7 @@ int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
     double lam = 0.0;
     for (int q = 0; q < R.nv; ++q) {
       double x[3] = {R.vr[q], R.vs[q], R.vt[q]}, U[ORC_MAXM];
-      eval_state(dim, p, M, Np, c + e * M * Np, x, U);
+      eval_state(m, p, M, Np, c + e * M * Np, x, U);
       double rho = U[0], q2 = 0.0;
       for (int a = 0; a < dim; ++a) q2 += (U[1 + a] / rho) * (U[1 + a] / rho);
       double pr = (ORC_GAMMA - 1.0) * (U[dim + 1] - 0.5 * rho * q2);
@@ -1325,7 +1455,7 @@ int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
       face_geometry(m, e, f, &R, &F);
       bnd += F.meas;
     }
-    double vol = m->detJ[e] / (dim == 2 ? 2.0 : 6.0);
+    double vol = m->detJ[e] / (m->quad ? 1.0 : dim == 2 ? 2.0 : 6.0);
     double r = dim * vol / bnd;
     double v = r / ((2 * p + 1) * lam);
     if (v < best) best = v;
@@ -1342,7 +1472,7 @@ int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
  * dt comes from the state at the start of the step, or is dt_in when > 0. */
 int orc_rk_step(void *h, int p, double *c, double cfl, double dt_in, double *dt_out) {
   orc_mesh *m = (orc_mesh *)h;
-  int dim = m->dim, M = dim + 2, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  int dim = m->dim, M = dim + 2, Np = npoly_m(m, p);
   int64_t n = m->ne * M * Np;
   double dt = dt_in;
   if (!(dt > 0.0) && orc_dt(h, p, c, cfl, &dt)) return -1;
@@ -1375,23 +1505,26 @@ int orc_num_vol_points(int dim, int p) {
 int orc_eval_points(void *h, int p, int M, const double *c, int n1, double *xyz, double *w,
                     double *U) {
   orc_mesh *m = (orc_mesh *)h;
-  int dim = m->dim, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  int dim = m->dim, Np = npoly_m(m, p);
+  if (m->nonaffine) return fail("eval_points: quadrilaterals must be parallelograms");
   orc_rules R;
-  if (rules_make(dim, 1, n1 > 0 ? n1 : default_vol_n1(dim, p), &R)) {
+  if (rules_make(dim, m->quad, 1, n1 > 0 ? n1 : default_vol_n1(dim, p), &R)) {
     rules_free(&R);
     return -1;
   }
+  /* the reference axes run from v0 to v1, v2 (simplices) or v1, v3 (quadrilaterals) */
+  const int kv[3] = {1, m->quad ? 3 : 2, 3};
   for (int64_t e = 0; e < m->ne; ++e) {
     const double *X = m->X + e * m->nvpe * dim;
     for (int q = 0; q < R.nv; ++q) {
       double rs[3] = {R.vr[q], R.vs[q], R.vt[q]};
       for (int a = 0; a < dim; ++a) {
         double v = X[a];
-        for (int k = 0; k < dim; ++k) v += (X[(k + 1) * dim + a] - X[a]) * rs[k];
+        for (int k = 0; k < dim; ++k) v += (X[kv[k] * dim + a] - X[a]) * rs[k];
         if (xyz) xyz[(e * R.nv + q) * dim + a] = v;
       }
       if (w) w[e * R.nv + q] = R.vw[q] * m->detJ[e];
-      if (U) eval_state(dim, p, M, Np, c + e * M * Np, rs, U + (e * R.nv + q) * M);
+      if (U) eval_state(m, p, M, Np, c + e * M * Np, rs, U + (e * R.nv + q) * M);
     }
   }
   int nq = R.nv;
@@ -1404,9 +1537,9 @@ int orc_eval_points(void *h, int p, int M, const double *c, int n1, double *xyz,
  * default volume rule; vals is [E][Nq][M] at the points of orc_eval_points. */
 int orc_project(void *h, int p, int M, const double *vals, double *c) {
   orc_mesh *m = (orc_mesh *)h;
-  int dim = m->dim, Np = dim == 2 ? npoly_tri(p) : npoly_tet(p);
+  int dim = m->dim, Np = npoly_m(m, p);
   orc_rules R;
-  if (rules_make(dim, 1, default_vol_n1(dim, p), &R)) {
+  if (rules_make(dim, m->quad, 1, default_vol_n1(dim, p), &R)) {
     rules_free(&R);
     return -1;
   }
@@ -1415,7 +1548,7 @@ int orc_project(void *h, int p, int M, const double *vals, double *c) {
     for (int i = 0; i < M * Np; ++i) ce[i] = 0.0;
     for (int q = 0; q < R.nv; ++q) {
       double x[3] = {R.vr[q], R.vs[q], R.vt[q]}, phi[ORC_MAXNP];
-      basis_eval(dim, p, x, phi, NULL, NULL, NULL);
+      basis_eval(m, p, x, phi, NULL, NULL, NULL);
       for (int k = 0; k < M; ++k)
         for (int j = 0; j < Np; ++j) ce[k * Np + j] += R.vw[q] * vals[(e * R.nv + q) * M + k] * phi[j];
     }

@@ -18,6 +18,14 @@ not available; the generators below build meshes of the same kind and scale:
 * ``open_square_tri``: the same split on a non-periodic square (boundary edges).
 * ``periodic_cube_tet``: an ``n^3`` periodic unit cube, each cube split into six
   tetrahedra along its main diagonal (Kuhn/Freudenthal split).
+* ``periodic_square_quad`` / ``open_square_quad``: ``n x n`` quadrilaterals on
+  the unit square (Table 2's rectangular domains).  ``mode="parallelogram"``
+  jitters the grid lines and shifts every row of vertices sideways, so every
+  element is a parallelogram of its own width, height and slant;
+  ``mode="vertex"`` jitters every vertex (general convex quadrilaterals,
+  colored only).
+* ``hybrid_square``: the quadrilateral grid with a seeded fraction of its
+  squares split into two triangles (Table 2's hybrid tri/quad mesh).
 """
 
 from __future__ import annotations
@@ -36,7 +44,9 @@ class MeshInput:
 
     dim: int
     xyz: np.ndarray  # (nv, dim) float64
-    ev: np.ndarray  # (ne, dim+1) int32, CCW triangles / positive-volume tets
+    # (ne, dim+1) int32, CCW triangles / positive-volume tets; (ne, 4) CCW
+    # quadrilaterals, -1 as the fourth id of a triangle of a hybrid mesh
+    ev: np.ndarray
     periodic_len: np.ndarray | None  # (dim,) float64 or None
     name: str = ""
     meta: dict = field(default_factory=dict)
@@ -109,6 +119,95 @@ def open_square_tri(n: int, jitter: float = 0.0, seed: int | None = None) -> Mes
     ev[0::2] = np.stack([a, b, c], axis=1)
     ev[1::2] = np.stack([a, c, d], axis=1)
     return MeshInput(2, xyz, ev, None, name=f"open_square_tri_{n}x{n}", meta={"n": n})
+
+
+def _quad_grid(n: int, periodic: bool, mode: str, jitter: float, slant: float, seed):
+    nn = n if periodic else n + 1
+    h = 1.0 / n
+    rng = np.random.default_rng(seed)
+    ii, jj = np.meshgrid(np.arange(nn), np.arange(nn), indexing="xy")
+    i, j = ii.ravel(), jj.ravel()
+    inner_x = (i > 0) & (i < n) if not periodic else np.ones(i.size, bool)
+    inner_y = (j > 0) & (j < n) if not periodic else np.ones(j.size, bool)
+    if mode == "parallelogram":
+        # column lines x_i, row lines y_j, row shifts s_j (zero on open boundary rows)
+        xl = np.arange(nn) * h + (rng.uniform(-jitter * h, jitter * h, nn) if jitter else 0.0)
+        yl = np.arange(nn) * h + (rng.uniform(-jitter * h, jitter * h, nn) if jitter else 0.0)
+        sl = rng.uniform(-slant * h, slant * h, nn) if slant else np.zeros(nn)
+        if not periodic:
+            xl[[0, n]] = [0.0, 1.0]
+            yl[[0, n]] = [0.0, 1.0]
+            sl[[0, n]] = 0.0
+        x = xl[i] + np.where(inner_x, sl[j], 0.0)
+        y = yl[j]
+        xyz = np.stack([x, y], axis=1)
+    elif mode == "vertex":
+        xyz = np.stack([i * h, j * h], axis=1).astype(np.float64)
+        if jitter:
+            d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+            xyz[:, 0] += np.where(inner_x, d[:, 0], 0.0)
+            xyz[:, 1] += np.where(inner_y, d[:, 1], 0.0)
+    else:
+        raise ValueError(mode)
+
+    def vid(a, b):
+        return (b % nn) * nn + (a % nn)
+
+    ci, cj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    a, b = ci.ravel(), cj.ravel()
+    ev = np.stack([vid(a, b), vid(a + 1, b), vid(a + 1, b + 1), vid(a, b + 1)], axis=1).astype(np.int32)
+    return xyz.astype(np.float64), ev
+
+
+def periodic_square_quad(n: int, mode: str = "parallelogram", jitter: float = 0.0, slant: float = 0.0,
+                         seed: int | None = None) -> MeshInput:
+    """``n x n`` periodic quadrilaterals, square (i, j) numbered j-major as
+    [(i,j), (i+1,j), (i+1,j+1), (i,j+1)] (CCW).  Vertex (i, j) has id ``j*n + i``.
+
+    ``mode="parallelogram"``: column line i at ``i h + U(-jitter h, jitter h)``,
+    row line j likewise, and row j of vertices shifted by ``U(-slant h, slant h)``
+    in x, so every element is a parallelogram.  ``mode="vertex"``: every vertex
+    jittered by ``U(-jitter h, jitter h)`` in x and y.  ``n >= 3``.
+    """
+    if n < 3:
+        raise ValueError("periodic meshes need n >= 3")
+    xyz, ev = _quad_grid(n, True, mode, jitter, slant, seed)
+    return MeshInput(2, xyz, ev, np.array([1.0, 1.0]), name=f"periodic_square_quad_{n}x{n}",
+                     meta={"n": n, "mode": mode, "jitter": jitter, "slant": slant, "seed": seed})
+
+
+def open_square_quad(n: int, mode: str = "parallelogram", jitter: float = 0.0, slant: float = 0.0,
+                     seed: int | None = None) -> MeshInput:
+    """Non-periodic ``n x n`` quadrilaterals on the unit square, ``(n+1)^2`` vertices;
+    boundary vertices stay on the boundary.  With ``slant`` the interior columns of
+    each row are shifted (the elements next to x = 0 and x = 1 are then general
+    quadrilaterals), so open parallelogram meshes use ``slant=0``."""
+    xyz, ev = _quad_grid(n, False, mode, jitter, slant, seed)
+    return MeshInput(2, xyz, ev, None, name=f"open_square_quad_{n}x{n}",
+                     meta={"n": n, "mode": mode, "jitter": jitter, "slant": slant, "seed": seed})
+
+
+def hybrid_square(n: int, frac: float = 0.25, periodic: bool = True, jitter: float = 0.0,
+                  seed: int | None = None) -> MeshInput:
+    """The ``n x n`` quadrilateral grid (``mode="vertex"``) with a seeded fraction
+    ``frac`` of its squares split along the diagonal (i,j)-(i+1,j+1) into two CCW
+    triangles, listed with -1 as their fourth vertex.  Elements are numbered
+    square by square, a split square's two triangles in place of the square."""
+    base = (periodic_square_quad(n, "vertex", jitter, seed=seed) if periodic
+            else open_square_quad(n, "vertex", jitter, seed=seed))
+    rng = np.random.default_rng(None if seed is None else seed + 1)
+    split = rng.uniform(size=n * n) < frac
+    rows = []
+    for e in range(n * n):
+        a, b, c, d = base.ev[e]
+        if split[e]:
+            rows.append((a, b, c, -1))
+            rows.append((a, c, d, -1))
+        else:
+            rows.append((a, b, c, d))
+    ev = np.array(rows, dtype=np.int32)
+    return MeshInput(2, base.xyz, ev, base.periodic_len, name=f"hybrid_square_{n}x{n}",
+                     meta={"n": n, "frac": frac, "periodic": periodic, "seed": seed})
 
 
 # The six tetrahedra of the Kuhn split of the unit cube: the path 000 -> 111
