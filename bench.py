@@ -469,20 +469,26 @@ def run_batched(dgc, torch, dev, stream, args):
 
 
 def run_other_meshes(dgc, torch, dev, stream, args):
-    """The other two workloads, each an RK step in FP64 and in mixed precision,
-    and its right-hand side colored / atomicAdd / two-pass:
+    """The other workloads, each an RK step in FP64 and in mixed precision, and
+    its right-hand side colored / atomicAdd / two-pass:
     1,572,864 periodic Kuhn tetrahedra at p = 2 (4 face colors; seeded random
-    state), and
+    state),
     the 256 x 256 x 2 periodic triangle mesh refined once within radius 0.2 of the
-    centre (180,512 elements, hanging edges, 6 colors) at p = 2."""
+    centre (180,512 elements, hanging edges, 6 colors) at p = 2, and
+    656,100 periodic parallelograms (810 x 810, 4 edge colors) at p = 3.
+    On the tetrahedra and the parallelograms the mixed step also gets a per-kernel
+    breakdown from a profiled pass against the HBM roofline."""
     out = {}
     tube = W.cube_tube_p2_64()
     ref = W.refined_square_vortex_p2_256()
+    quad = W.quad_square_vortex_p3_810()
+    hbm, _ = peaks()
     for tag, mi, p, refine in (("tet_p2_64cube", tube["mesh"], tube["p"], None),
-                               ("nonconforming_p2_256", ref["mesh"], ref["p"], ref["refine"])):
+                               ("nonconforming_p2_256", ref["mesh"], ref["p"], ref["refine"]),
+                               ("quad_p3_810", quad["mesh"], quad["p"], None)):
         t0 = time.perf_counter()
         m = dgc.Mesh.from_input(mi, p)
-        m.color(1601)
+        _, per_color = m.color(1601)
         if refine is not None:
             m.refine(refine)
         prep_s = time.perf_counter() - t0
@@ -510,6 +516,24 @@ def run_other_meshes(dgc, torch, dev, stream, args):
             ms = time_steps(torch, fn, k, stream)
             entry[f"rk_{name}"] = {"value": 3 * dofs / (ms * 1e-3), "ms_per_step": round(ms, 4),
                                    "launches_per_step": dgc.dgc_last_launch_count(m.h)}
+            if prec == dgc.DGC_FP32_MIXED and refine is None:
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_PROFILE, 1)
+                dgc.dgc_profile_collect(m.h)
+                msp = time_steps(torch, fn, k, stream)
+                prof = dgc.dgc_profile_collect(m.h)
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_PROFILE, 0)
+                rec = 4 * ((info["M"] * (info["np"] + 1) + 3) // 4 * 4)
+                kern = {}
+                for cls, (tms, nl) in prof.items():
+                    n = nl // (2 if cls == "cfl" else 1)
+                    ne_ = per_color[0] if cls in ("first", "color", "last") else 0
+                    b = class_bytes(cls, info["ne"], ne_, info["M"] * info["np"], mi.dim, "mixed", rec=rec)
+                    avg = tms / n
+                    kern[cls] = {"calls": n, "avg_ms": round(avg, 5), "share": round(tms / (msp * k), 4),
+                                 "alg_bytes": int(b), "alg_gbs": round(b / (avg * 1e-3) / 1e9, 1),
+                                 "frac_hbm": round(b / (avg * 1e-3) / 1e9 / hbm, 3)}
+                entry["rk_fp32mixed"]["profiled_ms_per_step"] = round(msp, 4)
+                entry["rk_fp32mixed"]["kernels"] = kern
             del ws
             nbuf = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
             buf = torch.empty(nbuf // 8, dtype=torch.float64, device=dev)

@@ -4,7 +4,8 @@
  * The library evaluates the right-hand side of the modal discontinuous Galerkin
  * discretisation of the Euler equations (Eq. 2 of Giuliani & Krivodonova, "Edge
  * coloring in unstructured CFD codes") on unstructured triangle and tetrahedral
- * meshes.  The surface integral is evaluated color by color (Algorithm 1): the
+ * meshes, and on parallelogram quadrilateral meshes (dgc_mesh_create_elem).  The
+ * surface integral is evaluated color by color (Algorithm 1): the
  * edges (faces) are colored so that no element has two edges of one color
  * (Sec. 3.1), so all edges of one color scatter their flux projection into both
  * neighbours with plain stores, no atomics and no per-edge buffer.  Elements and
@@ -114,6 +115,33 @@ typedef enum {
  * elements, non-positive Jacobian, vertex id out of range), DGC_ERR_UNSUPPORTED. */
 dgc_status dgc_mesh_create(int dim, int p, int64_t nv, const double* xyz, int64_t ne,
                            const int32_t* ev, const double* periodic_len, dgc_mesh** out);
+
+/* Element types of dgc_mesh_create_elem. */
+typedef enum { DGC_TRI = 0, DGC_QUAD = 1, DGC_TET = 2 } dgc_elem;
+
+/* Mesh ingest by element type.  DGC_TRI and DGC_TET are dgc_mesh_create with dim 2
+ * and 3.  DGC_QUAD: quadrilaterals (Sec. 1 lists them among the meshes the method
+ * covers; Sec. 3.1 and Table 2 color them with C = {1, 2, 3, 4}).  ev is ne*4 int32,
+ * counterclockwise (every corner must turn left); local edge q is (v_q, v_{q+1 mod 4}).
+ * A row whose fourth id is -1 is a triangle: a hybrid triangle/quadrilateral mesh,
+ * also colored with 4 colors (Table 2's hybrid mesh).  The DG kernels take meshes
+ * whose elements are all parallelograms (v2 = v1 + v3 - v0 to 1e-12 of the element
+ * size): the reference square [0,1]^2 with corners (0,0), (1,0), (1,1), (0,1) at
+ * v0..v3 maps affinely, and the basis is the tensor-product Legendre space Q_p,
+ * phi_{a(p+1)+b}(r, s) = l_a(r) l_b(s), l_k(x) = sqrt(2k+1) P_k(2x-1) (Np = (p+1)^2,
+ * orthonormal on the square; p = 1..3).  Other quadrilateral and hybrid meshes can be
+ * colored, reordered and inspected; device calls on them return DGC_ERR_UNSUPPORTED.
+ * A closed quadrilateral mesh with an odd number of elements has no 4-coloring (each
+ * color would be a perfect matching of the elements); dgc_color_edges then returns
+ * DGC_ERR_COLORING_LIMIT.  Errors as dgc_mesh_create, plus DGC_ERR_MESH for a
+ * quadrilateral that is not convex and counterclockwise. */
+dgc_status dgc_mesh_create_elem(dgc_elem type, int p, int64_t nv, const double* xyz, int64_t ne,
+                                const int32_t* ev, const double* periodic_len, dgc_mesh** out);
+
+/* The mesh's element type (dgc_elem) and the number of its elements the DG kernels do
+ * not take (quadrilaterals that are not parallelograms, triangles of hybrid meshes).
+ * Either output may be NULL. */
+dgc_status dgc_mesh_element(const dgc_mesh* mesh, int32_t* type, int64_t* nonaffine);
 
 /* Edge (face) coloring of Sec. 3.1 -- modified greedy pass with random nonconflicting
  * colors from C = {1..F} (F = 3 triangles, 4 tetrahedra), then conflict resolution by

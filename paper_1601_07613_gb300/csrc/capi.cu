@@ -53,7 +53,9 @@ void require(bool ok, const char* msg, dgc_status code = DGC_ERR_ARG) {
 
 int64_t nv_of(const Mesh& m) { return (int64_t)m.M * m.np; }
 // floats per element of the FP32 record the mixed-precision step keeps
-int64_t record_floats(const Mesh& m) { return m.dim == 2 ? tri_record_floats(m.p) : tet_record_floats(m.p); }
+int64_t record_floats(const Mesh& m) {
+  return m.quad ? quad_record_floats(m.p) : m.dim == 2 ? tri_record_floats(m.p) : tet_record_floats(m.p);
+}
 // floats per element of the FP32 pair state of the Kahan form (triangles)
 int64_t kahan_floats(const Mesh& m) { return tri_kahan_floats(m.p); }
 int64_t state_bytes(const Mesh& m) { return m.ne * nv_of(m) * (int64_t)sizeof(double); }
@@ -202,6 +204,7 @@ void upload(Mesh& m) {
     DGC_CUDA(cudaMemcpy(d->fgeo, fgeo.data(), sizeof(double2) * fgeo.size(), cudaMemcpyHostToDevice));
     DGC_CUDA(cudaMemcpy(d->slots, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice));
     if (dim == 3) tet_upload_tables(m.p, m.tab, *d);
+    if (m.quad) quad_upload_tables(m.p, m.tab);
   } catch (...) {
     m.dev = d.release();
     device_free(m);
@@ -210,7 +213,7 @@ void upload(Mesh& m) {
   {
     std::lock_guard<std::mutex> lk(g_tab_mu);
     auto key = std::make_pair(dev, dim * 16 + m.p);
-    if (dim == 2 && !g_tab_done.count(key)) {
+    if (dim == 2 && !m.quad && !g_tab_done.count(key)) {
       tri_upload_tables(m.p, m.tab);
       DGC_CUDA(cudaGetLastError());
       g_tab_done.insert(key);
@@ -231,9 +234,14 @@ const Mesh& checked(const dgc_mesh* mesh) {
 
 Ctx ready(Mesh& m, void* stream) {
   require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
+  require(!m.nonaffine,
+          "the kernels take parallelogram quadrilaterals only; this mesh (general quadrilaterals or hybrid) is "
+          "colored only",
+          DGC_ERR_UNSUPPORTED);
   upload(m);
   Ctx x;
   x.dim = m.dim;
+  x.quad = m.quad;
   x.p = m.p;
   x.np = m.np;
   x.M = m.M;
@@ -247,7 +255,7 @@ Ctx ready(Mesh& m, void* stream) {
   x.shadow.nv = m.M * m.np;
   x.shadow.rec = (int)record_floats(m);
   x.shadow.split = true;
-  x.shadow.mode_major = m.dim == 2;
+  x.shadow.mode_major = m.dim == 2 && !m.quad;
   x.shadow.phi0 = m.tab.phiV[0];
   x.st = static_cast<cudaStream_t>(stream);
   return x;
@@ -260,14 +268,17 @@ void check_ptr(const void* p, const char* what) {
 
 // ss: floats per element of an FP32 state (record or Kahan state), 0 for FP64 states
 int vol(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r, int64_t e0 = 0) {
+  if (x.quad) return quad_volume(x, ty, s, ss, r, e0);
   return x.dim == 2 ? tri_volume(x, ty, s, ss, r, e0) : tet_volume(x, ty, s, ss, r, e0);
 }
 int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, int ss, void* r, void* buf,
          const StageArgs* sa) {
+  if (x.quad) return quad_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
   return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, ss, r, buf, sa)
                     : tet_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
 }
 int cfl(const Ctx& x, const double* s, double c, double* dt, float* sh) {
+  if (x.quad) return quad_cfl(x, s, c, dt, sh);
   return x.dim == 2 ? tri_cfl(x, s, c, dt, sh) : tet_cfl(x, s, c, dt, sh);
 }
 
@@ -393,13 +404,15 @@ Workspace carve(const Mesh& m, dgc_prec prec, char* base) {
 // One SSP-RK3 step.  Per stage: FIRST + COLOR... + LAST (volume integral fused
 // into the first color, stage update into the last) on meshes where every
 // element has one edge of each color, else VOLUME + every color + STAGE.
+// Quadrilateral meshes fuse the volume integral into the first color and run
+// the stage update as its own pass (no fused last color).
 // launch(cls, f) issues the kernels of f() and counts them.
 template <typename Launch>
 void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cfl_, double* dt, const Workspace& w,
                   Launch&& launch) {
   const std::vector<int32_t>& off = m.color_off;
   const int C = m.ncolors;
-  const bool fused = m.fuse && m.perfect && C >= 2;
+  const bool fused = m.fuse && m.perfect && C >= 2 && !m.quad;
   if (prec == DGC_FP64) {
     double* c64 = static_cast<double*>(c);
     launch(DGC_K_CFL, [&] { return cfl(x, c64, cfl_, dt, nullptr); });
@@ -505,6 +518,25 @@ dgc_status dgc_mesh_create(int dim, int p, int64_t nv, const double* xyz, int64_
   });
 }
 
+dgc_status dgc_mesh_create_elem(dgc_elem type, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
+                                const double* periodic_len, dgc_mesh** out) {
+  return guarded([&] {
+    require(out != nullptr, "null output pointer");
+    *out = nullptr;
+    require(type == DGC_TRI || type == DGC_QUAD || type == DGC_TET, "unknown element type");
+    const int dim = type == DGC_TET ? 3 : 2;
+    *out = reinterpret_cast<dgc_mesh*>(build_mesh(dim, p, nv, xyz, ne, ev, periodic_len, type == DGC_QUAD));
+  });
+}
+
+dgc_status dgc_mesh_element(const dgc_mesh* mesh, int32_t* type, int64_t* nonaffine) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    if (type) *type = m.quad ? DGC_QUAD : m.dim == 3 ? DGC_TET : DGC_TRI;
+    if (nonaffine) *nonaffine = m.nonaffine;
+  });
+}
+
 static void report_colors(const Mesh& m, int32_t* n_colors, int64_t* per_color) {
   if (n_colors) *n_colors = m.ncolors;
   if (per_color) {
@@ -596,7 +628,8 @@ dgc_status dgc_get_elements(const dgc_mesh* mesh, int32_t* ev, double* xyz) {
 dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems) {
   return guarded([&] {
     Mesh& m = checked(mesh);
-    require(m.dim == 2, "nonconforming refinement is implemented for triangle meshes", DGC_ERR_UNSUPPORTED);
+    require(m.dim == 2 && !m.quad, "nonconforming refinement is implemented for triangle meshes",
+            DGC_ERR_UNSUPPORTED);
     require(!m.refined, "the mesh is already refined (one level is supported)", DGC_ERR_UNSUPPORTED);
     require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
             "refine a mesh colored by dgc_color_edges with 3 colors");
@@ -658,7 +691,7 @@ static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) { return carve(m, p
 
 static void require_prec(const Mesh& m, dgc_prec prec) {
   require(prec == DGC_FP64 || prec == DGC_FP32_MIXED || prec == DGC_FP32_KAHAN, "unknown precision");
-  require(prec != DGC_FP32_KAHAN || m.dim == 2, "the Kahan form is implemented for triangle meshes",
+  require(prec != DGC_FP32_KAHAN || (m.dim == 2 && !m.quad), "the Kahan form is implemented for triangle meshes",
           DGC_ERR_UNSUPPORTED);
 }
 
@@ -1244,7 +1277,7 @@ dgc_status dgc_batch_create(int n, dgc_mesh* const* meshes, dgc_batch** out) {
     auto b = std::make_unique<dgc_batch>();
     for (int i = 0; i < n; ++i) {
       Mesh& m = checked(meshes[i]);
-      require(m.dim == 2, "batches hold triangle meshes");
+      require(m.dim == 2 && !m.quad, "batches hold triangle meshes");
       require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
               "batched meshes must be colored with 3 colors, every element with one edge of each color");
       b->meshes.push_back(&m);

@@ -59,6 +59,7 @@ struct ShadowLayout {
 
 struct Ctx {
   int dim = 2, p = 1, np = 0, M = 4, nfpe = 3;
+  bool quad = false;  // quadrilateral mesh (kernels_quad.cu)
   ShadowLayout shadow;
   int64_t ne = 0, ns = 0;
   int epb = 128;
@@ -151,6 +152,14 @@ int tet_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* r
 int tet_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tet_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
+
+// kernels_quad.cu
+void quad_upload_tables(int p, const RefTables& T);
+int quad_record_floats(int p);
+int quad_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs, int64_t e0 = 0);
+int quad_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
+                 int sstride, void* rhs, void* buf, const StageArgs* sa);
+int quad_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
 
 // kernels_common.cu
 int stage_update(const Ctx& c, bool rhs_f32, const double* us, const void* rhs, const StageArgs& sa);

@@ -15,6 +15,7 @@ constexpr int kMaxColors = 15;
 // sum to |reference element|; face weights sum to 1 over a face.
 struct RefTables {
   int dim = 0, p = 0, np = 0, nqv = 0, nqf = 0, nfaces = 0;
+  bool quad = false;  // the square [0,1]^2 with the tensor Legendre space Q_p
   std::vector<double> vr, vs, vt, vw;  // volume points (reference coordinates) and weights
   std::vector<double> phiV;            // [nqv][np]
   std::vector<double> dphiV;           // [dim][nqv][np]
@@ -23,11 +24,16 @@ struct RefTables {
   // triangles: phi_j on half h of local edge f, at edge parameter (h + t_q) / 2,
   // [nfaces][2][nqf][np] (the coarse side of a hanging edge, Sec. 3.2)
   std::vector<double> phiH;
+  // quadrilaterals: the normalised 1-D Legendre polynomials l_k(x) =
+  // sqrt(2k+1) P_k(2x-1) (phi_{a(p+1)+b}(r, s) = l_a(r) l_b(s)) at the edge
+  // points, [nqf][p+1], and at the ends x = 0 and x = 1, [p+1] each
+  std::vector<double> eleg, lend0, lend1;
 };
 
-// Builds the tables (quadrature + orthonormal basis) for triangles (dim 2) or
-// tetrahedra (dim 3).  Throws std::runtime_error on unsupported sizes.
-RefTables make_tables(int dim, int p);
+// Builds the tables (quadrature + orthonormal basis) for triangles (dim 2),
+// quadrilaterals (dim 2, quad) or tetrahedra (dim 3).  Throws
+// std::runtime_error on unsupported sizes.
+RefTables make_tables(int dim, int p, bool quad = false);
 
 // Tetrahedra: phi_j at the face points of local face f seen through vertex
 // permutation o (0..5, kFacePerms) of the face's three vertices:
@@ -36,7 +42,8 @@ std::vector<double> tet_face_orient_tables(const RefTables& T);
 extern const int kFacePerms[6][3];
 
 // Evaluates the orthonormal basis and its reference gradient at one point.
-void basis_eval(int dim, int p, const double* x, double* phi, double* grad /*[dim][np] or null*/);
+void basis_eval(int dim, int p, const double* x, double* phi, double* grad /*[dim][np] or null*/,
+                bool quad = false);
 
 // Gauss-Jacobi rule with weight (1-x)^alpha on [-1, 1].
 void gauss_jacobi(int n, double alpha, double* x, double* w);
@@ -45,6 +52,12 @@ struct DeviceMesh;  // defined in the CUDA translation unit
 
 struct Mesh {
   int dim = 0, p = 0, np = 0, M = 0, nfpe = 0, nvpe = 0;
+  // quadrilateral (or hybrid triangle/quadrilateral) mesh: nvpe = nfpe = 4, a
+  // triangle lists -1 as its fourth vertex and has no face 3 (face_of = -1);
+  // nonaffine counts the elements the kernels do not take (quadrilaterals that
+  // are not parallelograms, triangles of hybrid meshes): colored only
+  bool quad = false;
+  int64_t nonaffine = 0;
   int64_t nv = 0, ne = 0, ns = 0;
   bool periodic = false;
   double L[3] = {0, 0, 0};
@@ -98,7 +111,7 @@ struct Error {
 };
 
 Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
-                 const double* periodic_len);
+                 const double* periodic_len, bool quad = false);
 struct ColorStats {
   int64_t greedy_conflicts = 0, swaps = 0, breaks = 0, deferrals = 0;
 };

@@ -71,8 +71,45 @@ void gauss_jacobi(int n, double alpha, double* x, double* w) {
 // Ordering: total degree d = 0..p, first index from d down to 0.
 // ---------------------------------------------------------------------------
 
-static int npoly(int dim, int p) {
+static int npoly(int dim, int p, bool quad = false) {
+  if (quad) return (p + 1) * (p + 1);
   return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
+}
+
+// Unnormalised quadrilateral modes psi_{a,b} = P_a(2r-1) P_b(2s-1) on the
+// square [0,1]^2, mode a (p+1) + b, with their gradients.
+static void quad_raw(int p, double r, double s, double* phi, double* dr, double* ds) {
+  double Pr[16], Ps[16], dPr[16], dPs[16];
+  for (int k = 0; k <= p; ++k) {
+    Pr[k] = jacobi(k, 0, 0, 2.0 * r - 1.0);
+    Ps[k] = jacobi(k, 0, 0, 2.0 * s - 1.0);
+    dPr[k] = 2.0 * djacobi(k, 0, 0, 2.0 * r - 1.0);
+    dPs[k] = 2.0 * djacobi(k, 0, 0, 2.0 * s - 1.0);
+  }
+  for (int a = 0; a <= p; ++a)
+    for (int b = 0; b <= p; ++b) {
+      const int j = a * (p + 1) + b;
+      phi[j] = Pr[a] * Ps[b];
+      if (dr) {
+        dr[j] = dPr[a] * Ps[b];
+        ds[j] = Pr[a] * dPs[b];
+      }
+    }
+}
+
+// Square rule: n x n Gauss-Legendre points on [0,1]^2, weights summing to 1.
+static void quad_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w) {
+  std::vector<double> xg(n), wg(n);
+  gauss_jacobi(n, 0.0, xg.data(), wg.data());
+  r.clear();
+  s.clear();
+  w.clear();
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      r.push_back(0.5 * (1.0 + xg[i]));
+      s.push_back(0.5 * (1.0 + xg[k]));
+      w.push_back(0.25 * wg[i] * wg[k]);
+    }
 }
 
 // Unnormalised triangle modes psi_{k,l} = P_k(a) (1-s)^k P_l^{(2k+1,0)}(b),
@@ -169,12 +206,18 @@ static void tet_rule(int n, std::vector<double>& r, std::vector<double>& s, std:
       }
 }
 
-// normalisation constants, cached per (dim, p)
-static std::vector<double> norms(int dim, int p) {
-  int np = npoly(dim, p);
+// normalisation constants, cached per (dim, p, quad)
+static std::vector<double> norms(int dim, int p, bool quad) {
+  int np = npoly(dim, p, quad);
   std::vector<double> acc(np, 0.0), phi(np);
   std::vector<double> r, s, t, w;
-  if (dim == 2) {
+  if (quad) {
+    quad_rule(p + 2, r, s, w);
+    for (size_t q = 0; q < w.size(); ++q) {
+      quad_raw(p, r[q], s[q], phi.data(), nullptr, nullptr);
+      for (int j = 0; j < np; ++j) acc[j] += w[q] * phi[j] * phi[j];
+    }
+  } else if (dim == 2) {
     tri_rule(p + 2, r, s, w);
     for (size_t q = 0; q < w.size(); ++q) {
       tri_raw(p, r[q], s[q], phi.data(), nullptr, nullptr);
@@ -191,16 +234,19 @@ static std::vector<double> norms(int dim, int p) {
   return acc;
 }
 
-void basis_eval(int dim, int p, const double* x, double* phi, double* grad) {
-  static thread_local int cdim = -1, cp = -1;
+void basis_eval(int dim, int p, const double* x, double* phi, double* grad, bool quad) {
+  static thread_local int cdim = -1, cp = -1, cq = -1;
   static thread_local std::vector<double> N;
-  if (cdim != dim || cp != p) {
-    N = norms(dim, p);
+  if (cdim != dim || cp != p || cq != (int)quad) {
+    N = norms(dim, p, quad);
     cdim = dim;
     cp = p;
+    cq = (int)quad;
   }
-  int np = npoly(dim, p);
-  if (dim == 2) {
+  int np = npoly(dim, p, quad);
+  if (quad) {
+    quad_raw(p, x[0], x[1], phi, grad, grad ? grad + np : nullptr);
+  } else if (dim == 2) {
     tri_raw(p, x[0], x[1], phi, grad, grad ? grad + np : nullptr);
   } else {
     tet_raw(p, x[0], x[1], x[2], phi, grad);
@@ -212,8 +258,9 @@ void basis_eval(int dim, int p, const double* x, double* phi, double* grad) {
   }
 }
 
-// reference vertices of the simplices
+// reference vertices of the simplices and of the square
 static const double kTriV[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+static const double kQuadV[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
 static const double kTetV[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 
 // local face vertices: triangle edge q = (q, q+1); tetrahedron face q = the
@@ -229,16 +276,19 @@ static void face_vertices(int dim, int q, int* fv) {
     if (k != q) fv[n++] = k;
 }
 
-RefTables make_tables(int dim, int p) {
+RefTables make_tables(int dim, int p, bool quad) {
   if (dim != 2 && dim != 3) throw std::runtime_error("dim");
+  if (quad && dim != 2) throw std::runtime_error("quad");
   RefTables T;
   T.dim = dim;
   T.p = p;
-  T.np = npoly(dim, p);
-  T.nfaces = dim + 1;
+  T.quad = quad;
+  T.np = npoly(dim, p, quad);
+  T.nfaces = quad ? 4 : dim + 1;
   std::vector<double> fa, fb;
   if (dim == 2) {
-    tri_rule(p + 1, T.vr, T.vs, T.vw);
+    if (quad) quad_rule(p + 1, T.vr, T.vs, T.vw);
+    else tri_rule(p + 1, T.vr, T.vs, T.vw);
     T.vt.assign(T.vr.size(), 0.0);
     int n = 2 * p + 1;
     std::vector<double> x(n), w(n);
@@ -261,13 +311,34 @@ RefTables make_tables(int dim, int p) {
   std::vector<double> phi(T.np), g((size_t)dim * T.np);
   for (int q = 0; q < T.nqv; ++q) {
     double x[3] = {T.vr[q], T.vs[q], T.vt[q]};
-    basis_eval(dim, p, x, phi.data(), g.data());
+    basis_eval(dim, p, x, phi.data(), g.data(), quad);
     for (int j = 0; j < T.np; ++j) {
       T.phiV[(size_t)q * T.np + j] = phi[j];
       for (int a = 0; a < dim; ++a) T.dphiV[((size_t)a * T.nqv + q) * T.np + j] = g[a * T.np + j];
     }
   }
   T.phiF.resize((size_t)T.nfaces * T.nqf * T.np);
+  if (quad) {
+    for (int f = 0; f < 4; ++f)
+      for (int q = 0; q < T.nqf; ++q) {
+        const double* V0 = kQuadV[f];
+        const double* V1 = kQuadV[(f + 1) % 4];
+        double x[3] = {V0[0] + fa[q] * (V1[0] - V0[0]), V0[1] + fa[q] * (V1[1] - V0[1]), 0.0};
+        basis_eval(2, p, x, phi.data(), nullptr, true);
+        for (int j = 0; j < T.np; ++j) T.phiF[((size_t)f * T.nqf + q) * T.np + j] = phi[j];
+      }
+    // the 1-D factors: phi_{a(p+1)}(x, 0) = l_a(x) l_0(0) with l_0 = 1
+    T.eleg.resize((size_t)T.nqf * (p + 1));
+    T.lend0.resize(p + 1);
+    T.lend1.resize(p + 1);
+    for (int k = 0; k <= p; ++k) {
+      const double c = std::sqrt(2.0 * k + 1.0);
+      for (int q = 0; q < T.nqf; ++q) T.eleg[(size_t)q * (p + 1) + k] = c * jacobi(k, 0, 0, 2.0 * fa[q] - 1.0);
+      T.lend0[k] = c * jacobi(k, 0, 0, -1.0);
+      T.lend1[k] = c * jacobi(k, 0, 0, 1.0);
+    }
+    return T;
+  }
   for (int f = 0; f < T.nfaces; ++f) {
     int fv[3];
     face_vertices(dim, f, fv);
@@ -367,14 +438,53 @@ struct KeyTable {
 };
 }  // namespace
 
+// faces of element e: 3 (triangle, also one of a hybrid mesh), 4 (quadrilateral
+// or tetrahedron)
+static int elem_faces(const Mesh& m, int64_t e) {
+  if (!m.quad) return m.nfpe;
+  return m.ev[(size_t)e * 4 + 3] < 0 ? 3 : 4;
+}
+
+// local face q of element e: edge (v_q, v_{q+1}) of a triangle or quadrilateral,
+// the face opposite v_q of a tetrahedron
+static void elem_face_vertices(const Mesh& m, int64_t e, int q, int* fv) {
+  if (m.dim == 2) {
+    fv[0] = q;
+    fv[1] = (q + 1) % elem_faces(m, e);
+    return;
+  }
+  face_vertices(3, q, fv);
+}
+
 // detJ and the inverse Jacobian of element e from its unwrapped coordinates.
+// A quadrilateral maps the square's corners (0,0), (1,0), (1,1), (0,1) to
+// v0..v3 through v0, v1 and v3 (affine: exact for parallelograms); it must turn
+// counterclockwise at every corner, and one that is not a parallelogram is
+// counted in m.nonaffine (colored only).
 static void element_jacobian(Mesh& m, int64_t e) {
   const int dim = m.dim;
   const double* X = &m.X[(size_t)e * m.nvpe * dim];
   double* Ji = &m.Jinv[(size_t)e * dim * dim];
   double det;
   if (dim == 2) {
-    double a = X[2] - X[0], b = X[4] - X[0], c = X[3] - X[1], d = X[5] - X[1];
+    const bool q4 = m.quad && elem_faces(m, e) == 4;
+    const int v2 = q4 ? 3 : 2;  // the vertex at reference (0, 1)
+    double a = X[2] - X[0], b = X[2 * v2] - X[0], c = X[3] - X[1], d = X[2 * v2 + 1] - X[1];
+    if (q4) {
+      double scale = 0.0, off = 0.0;
+      for (int k = 0; k < 4; ++k) {
+        const double* A = X + 2 * k;
+        const double* B = X + 2 * ((k + 1) % 4);
+        const double* P = X + 2 * ((k + 3) % 4);
+        const double cr = (B[0] - A[0]) * (P[1] - A[1]) - (B[1] - A[1]) * (P[0] - A[0]);
+        if (!(cr > 0.0)) throw Error{DGC_ERR_MESH, "quadrilateral that is not convex and counterclockwise"};
+        scale = std::max(scale, std::fabs(B[0] - A[0]) + std::fabs(B[1] - A[1]));
+      }
+      for (int k = 0; k < 2; ++k) off = std::max(off, std::fabs(X[k] + X[4 + k] - X[2 + k] - X[6 + k]));
+      if (off > 1e-12 * scale) m.nonaffine++;
+    } else if (m.quad) {
+      m.nonaffine++;  // a triangle of a hybrid mesh
+    }
     det = a * d - b * c;
     Ji[0] = d / det;
     Ji[1] = -b / det;
@@ -404,11 +514,11 @@ static double face_normal(const Mesh& m, int64_t e, int q, double* n) {
   const int dim = m.dim;
   const double* X = &m.X[(size_t)e * m.nvpe * dim];
   int fv[3];
-  face_vertices(dim, q, fv);
+  elem_face_vertices(m, e, q, fv);
   double meas;
   n[0] = n[1] = n[2] = 0.0;
   if (dim == 2) {
-    // CCW triangle: outward normal of edge v_q -> v_{q+1} is (dy, -dx)/|d|
+    // CCW element: outward normal of edge v_q -> v_{q+1} is (dy, -dx)/|d|
     double dx = X[fv[1] * 2] - X[fv[0] * 2], dy = X[fv[1] * 2 + 1] - X[fv[0] * 2 + 1];
     meas = std::hypot(dx, dy);
     n[0] = dy / meas;
@@ -446,16 +556,18 @@ static void side_geometry(Mesh& m) {
   m.inradius.resize(m.ne);
   for (int64_t e = 0; e < m.ne; ++e) {
     double bnd = 0.0, n[3];
-    for (int q = 0; q < m.nfpe; ++q) bnd += face_normal(m, e, q, n);
-    double vol = m.detJ[e] / (dim == 2 ? 2.0 : 6.0);
+    for (int q = 0; q < elem_faces(m, e); ++q) bnd += face_normal(m, e, q, n);
+    const bool q4 = m.quad && elem_faces(m, e) == 4;
+    double vol = m.detJ[e] / (q4 ? 1.0 : dim == 2 ? 2.0 : 6.0);
     m.inradius[e] = dim * vol / bnd;
   }
 }
 
 Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, const int32_t* ev,
-                 const double* periodic_len) {
+                 const double* periodic_len, bool quad) {
   if (dim != 2 && dim != 3) throw Error{DGC_ERR_ARG, "dim must be 2 or 3"};
-  if (dim == 2 && (p < 1 || p > 3)) throw Error{DGC_ERR_UNSUPPORTED, "triangles support p = 1..3"};
+  if (quad && dim != 2) throw Error{DGC_ERR_ARG, "quadrilateral meshes are two-dimensional"};
+  if (dim == 2 && (p < 1 || p > 3)) throw Error{DGC_ERR_UNSUPPORTED, quad ? "quadrilaterals support p = 1..3" : "triangles support p = 1..3"};
   if (dim == 3 && (p < 1 || p > 2)) throw Error{DGC_ERR_UNSUPPORTED, "tetrahedra support p = 1..2"};
   if (nv <= 0 || ne <= 0 || !xyz || !ev) throw Error{DGC_ERR_ARG, "empty mesh or null arrays"};
   if (ne > (1LL << 30) || nv > (1LL << 30)) throw Error{DGC_ERR_ARG, "mesh too large"};
@@ -464,7 +576,8 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
   m->dim = dim;
   m->p = p;
   m->M = dim + 2;
-  m->nvpe = m->nfpe = dim + 1;
+  m->quad = quad;
+  m->nvpe = m->nfpe = quad ? 4 : dim + 1;
   m->nv = nv;
   m->ne = ne;
   m->periodic = periodic_len != nullptr;
@@ -482,6 +595,10 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
     double* X = &m->X[(size_t)e * nvpe * dim];
     for (int k = 0; k < nvpe; ++k) {
       int32_t v = ev[e * nvpe + k];
+      if (quad && k == 3 && v == -1) {  // a triangle of a hybrid mesh
+        for (int a = 0; a < dim; ++a) X[k * dim + a] = X[a];
+        continue;
+      }
       if (v < 0 || v >= nv) throw Error{DGC_ERR_MESH, "vertex id out of range"};
       for (int a = 0; a < dim; ++a) {
         double x = xyz[(size_t)v * dim + a];
@@ -497,9 +614,9 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
   m->face_of.assign((size_t)ne * nfpe, -1);
   m->sl.reserve(ne * nfpe / 2 + 16);
   for (int64_t e = 0; e < ne; ++e)
-    for (int q = 0; q < nfpe; ++q) {
+    for (int q = 0; q < elem_faces(*m, e); ++q) {
       int fv[3];
-      face_vertices(dim, q, fv);
+      elem_face_vertices(*m, e, q, fv);
       uint64_t g[3] = {0, 0, 0};
       for (int i = 0; i < dim; ++i) g[i] = (uint64_t)ev[e * nvpe + fv[i]];
       std::sort(g, g + dim);
@@ -520,7 +637,7 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
     }
   m->ns = (int64_t)m->sl.size();
   side_geometry(*m);
-  m->tab = make_tables(dim, p);
+  m->tab = make_tables(dim, p, quad);
   m->np = m->tab.np;
   return m.release();
 }
@@ -558,7 +675,7 @@ struct Colorer {
       if (el < 0) continue;
       const int32_t* f = faces(el);
       for (int q = 0; q < m.nfpe; ++q)
-        if (f[q] != k && col[f[q]] > 0) u |= 1u << col[f[q]];
+        if (f[q] >= 0 && f[q] != k && col[f[q]] > 0) u |= 1u << col[f[q]];
     }
     return u;
   }
@@ -573,7 +690,7 @@ struct Colorer {
 }  // namespace
 
 ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps) {
-  const int nc = m.nfpe;  // 3 colors for triangles, 4 for tetrahedra
+  const int nc = m.nfpe;  // 3 colors for triangles, 4 for quadrilateral (and hybrid) meshes and tetrahedra
   ColorStats st;
   std::vector<int8_t> col(m.ns, -1);
   Colorer C(m, nc, col);
@@ -615,7 +732,7 @@ ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps) {
         if (x < 0) continue;
         const int32_t* f = C.faces(x);
         for (int q = 0; q < m.nfpe; ++q)
-          if (f[q] != e && col[f[q]] > 0) ++tally[col[f[q]]];
+          if (f[q] >= 0 && f[q] != e && col[f[q]] > 0) ++tally[col[f[q]]];
       }
       int64_t cand[2 * 4];
       int ncand = 0;
@@ -624,7 +741,7 @@ ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps) {
         const int32_t* f = C.faces(x);
         for (int q = 0; q < m.nfpe; ++q) {
           int64_t g = f[q];
-          if (g != e && g != prev && col[g] > 0 && tally[col[g]] == 1) cand[ncand++] = g;
+          if (g >= 0 && g != e && g != prev && col[g] > 0 && tally[col[g]] == 1) cand[ncand++] = g;
         }
       }
       if (ncand) {
@@ -651,8 +768,8 @@ ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps) {
         for (int c = 1; c <= nc && !cs; ++c) {
           int64_t a = -1, b = -1;
           for (int q = 0; q < m.nfpe; ++q) {
-            if (f0[q] != e && col[f0[q]] == c) a = f0[q];
-            if (f1[q] != e && col[f1[q]] == c) b = f1[q];
+            if (f0[q] >= 0 && f0[q] != e && col[f0[q]] == c) a = f0[q];
+            if (f1[q] >= 0 && f1[q] != e && col[f1[q]] == c) b = f1[q];
           }
           if (a >= 0 && b >= 0) {
             cs = c;
@@ -984,13 +1101,14 @@ void coarsen(Mesh& m) {
 // ---------------------------------------------------------------------------
 void vol_points(const Mesh& m, double* xyz) {
   const RefTables& T = m.tab;
+  const int kv[3] = {1, m.quad ? 3 : 2, 3};  // the vertices at the reference axes' ends
   for (int64_t e = 0; e < m.ne; ++e) {
     const double* X = &m.X[(size_t)e * m.nvpe * m.dim];
     for (int q = 0; q < T.nqv; ++q) {
       double rs[3] = {T.vr[q], T.vs[q], T.vt[q]};
       for (int a = 0; a < m.dim; ++a) {
         double v = X[a];
-        for (int k = 0; k < m.dim; ++k) v += (X[(k + 1) * m.dim + a] - X[a]) * rs[k];
+        for (int k = 0; k < m.dim; ++k) v += (X[kv[k] * m.dim + a] - X[a]) * rs[k];
         xyz[((size_t)e * T.nqv + q) * m.dim + a] = v;
       }
     }

@@ -24,6 +24,7 @@ DGC_OPT_THREADS_PER_EDGE = 2
 DGC_OPT_PROFILE = 3
 DGC_OPT_GRAPH = 4
 DGC_OPT_PDL = 5
+DGC_TRI, DGC_QUAD, DGC_TET = 0, 1, 2  # dgc_elem
 KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
 
 STATUS = {0: "DGC_OK", 1: "DGC_ERR_ARG", 2: "DGC_ERR_MESH", 3: "DGC_ERR_COLORING_LIMIT",
@@ -37,6 +38,8 @@ _I64P = C.POINTER(C.c_int64)
 _DP = C.POINTER(C.c_double)
 SIGNATURES = {
     "dgc_mesh_create": (C.c_int, [C.c_int, C.c_int, _I64, _DP, _I64, _I32P, _DP, C.POINTER(_P)]),
+    "dgc_mesh_create_elem": (C.c_int, [C.c_int, C.c_int, _I64, _DP, _I64, _I32P, _DP, C.POINTER(_P)]),
+    "dgc_mesh_element": (C.c_int, [_P, _I32P, _I64P]),
     "dgc_color_edges": (C.c_int, [_P, C.c_uint64, _I64, _I32P, _I64P]),
     "dgc_color_edges_naive": (C.c_int, [_P, C.c_int, C.c_int, _I32P, _I64P]),
     "dgc_mesh_info": (C.c_int, [_P, _I64P]),
@@ -150,6 +153,25 @@ def dgc_mesh_create(dim: int, p: int, xyz, ev, periodic_len=None):
     out = _P()
     _check(lib().dgc_mesh_create(dim, p, xyz.shape[0], xp, ev.shape[0], ep, lp, C.byref(out)))
     return out
+
+
+def dgc_mesh_create_elem(elem: int, p: int, xyz, ev, periodic_len=None):
+    xyz, xp = _h(xyz, np.float64)
+    ev, ep = _h(ev, np.int32)
+    lp = None
+    if periodic_len is not None:
+        L, lp = _h(periodic_len, np.float64)
+    out = _P()
+    _check(lib().dgc_mesh_create_elem(elem, p, xyz.shape[0], xp, ev.shape[0], ep, lp, C.byref(out)))
+    return out
+
+
+def dgc_mesh_element(mesh):
+    """(element type DGC_TRI / DGC_QUAD / DGC_TET, elements the kernels do not take)"""
+    t = C.c_int32()
+    n = C.c_int64()
+    _check(lib().dgc_mesh_element(mesh, C.byref(t), C.byref(n)))
+    return t.value, n.value
 
 
 def dgc_color_edges(mesh, seed: int, max_swaps: int = 0):
@@ -413,8 +435,13 @@ class Mesh:
     """Owns a dgc_mesh handle; convenience accessors over the functions above."""
 
     def __init__(self, dim, p, xyz, ev, periodic_len=None):
-        self.h = dgc_mesh_create(dim, p, xyz, ev, periodic_len)
+        ev = np.asarray(ev)
+        if dim == 2 and ev.shape[1] == 4:  # quadrilateral or hybrid mesh
+            self.h = dgc_mesh_create_elem(DGC_QUAD, p, xyz, ev, periodic_len)
+        else:
+            self.h = dgc_mesh_create(dim, p, xyz, ev, periodic_len)
         self.info = dgc_mesh_info(self.h)
+        self.elem, self.nonaffine = dgc_mesh_element(self.h)
 
     @classmethod
     def from_input(cls, mi, p):

@@ -373,6 +373,15 @@ def jittered_square_vortex_p3_724x724(n: int = 724) -> dict:
                 yc=0.5, perturb=1e-3, perturb_seed=7613, cfl=0.3)
 
 
+def quad_square_vortex_p3_810(n: int = 810) -> dict:
+    """656,100 periodic parallelograms (810x810: grid lines jittered +-0.2h, rows
+    shifted +-0.3h, seed 1601), p = 3 (16 modes, 41,990,400 scalar DOFs, the DOF
+    count of the 724x724 triangle workload).  State: vortex beta = 5 at the centre,
+    projected, plus U(-1e-3, 1e-3) on every coefficient (seed 7613)."""
+    return dict(mesh=periodic_square_quad(n, jitter=0.2, slant=0.3, seed=1601), p=3, beta=5.0, xc=0.5,
+                yc=0.5, perturb=1e-3, seed=7613, cfl=0.3)
+
+
 def cube_tube_p2_64(n: int = 64) -> dict:
     """64^3 periodic cube x 6 Kuhn tets = 1,572,864 tets, p=2, vortex tube."""
     return dict(mesh=periodic_cube_tet(n), p=2, beta=5.0, xc=0.5, yc=0.5, cfl=0.3)

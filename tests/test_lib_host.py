@@ -49,7 +49,16 @@ MESHES = [
     ("open40", lambda: W.open_square_tri(40)),
     ("tet3", lambda: W.periodic_cube_tet(3)),
     ("tet5", lambda: W.periodic_cube_tet(5)),
+    ("quad6p", lambda: W.periodic_square_quad(6, jitter=0.2, slant=0.3, seed=4)),
+    ("quad30v", lambda: W.periodic_square_quad(30, "vertex", jitter=0.2, seed=5)),
+    ("quad9open", lambda: W.open_square_quad(9, "vertex", jitter=0.2, seed=6)),
+    ("hybrid12", lambda: W.hybrid_square(12, 0.3, seed=7)),
+    ("hybrid11open", lambda: W.hybrid_square(11, 0.4, periodic=False, jitter=0.2, seed=8)),
 ]
+
+
+def _ncolors(mi):
+    return 4 if mi.dim == 2 and mi.ev.shape[1] == 4 else mi.dim + 1
 
 
 @pytest.mark.parametrize("name,make", MESHES)
@@ -62,9 +71,9 @@ def test_coloring_and_ordering_bit_exact_vs_oracle(oracle_mod, name, make, seed)
     for a, b in zip(dgc.dgc_get_sides(m.h), om.sides()):
         assert np.array_equal(a, b)
     nc, per = m.color(seed)
-    col_o, _ = om.color(mi.dim + 1, seed)
+    col_o, _ = om.color(_ncolors(mi), seed)
     en, sn, col, off = dgc.dgc_get_ordering(m.h)
-    assert nc == mi.dim + 1
+    assert nc == _ncolors(mi)
     assert np.array_equal(col, col_o)
     en_o, sn_o, off_o = om.reorder(col_o, nc)
     assert np.array_equal(en, en_o) and np.array_equal(sn, sn_o) and np.array_equal(off, off_o)
@@ -98,6 +107,54 @@ def test_projection_matches_oracle(oracle_mod, p):
     c = dgc.dgc_project(m.h, vals)
     c_o = om.project(p, vals)
     np.testing.assert_allclose(c, c_o, atol=1e-13 * np.abs(c_o).max())
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_projection_matches_oracle_quad(oracle_mod, p):
+    mi = W.periodic_square_quad(8, jitter=0.2, slant=0.3, seed=2)
+    m = dgc.Mesh.from_input(mi, p)
+    assert (m.elem, m.nonaffine) == (dgc.DGC_QUAD, 0)
+    assert m.info["np"] == (p + 1) ** 2
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz = dgc.dgc_vol_points(m.h)
+    xyz_o, _, _ = om.eval_points(p)
+    np.testing.assert_allclose(xyz, xyz_o, atol=1e-15)
+    vals = W.vortex_field(xyz[..., 0], xyz[..., 1])
+    c_o = om.project(p, vals)
+    np.testing.assert_allclose(dgc.dgc_project(m.h, vals), c_o, atol=1e-13 * np.abs(c_o).max())
+    np.testing.assert_allclose(dgc.dgc_mesh_info(m.h)["ne"], mi.ne)
+
+
+def test_quad_mesh_statuses(L):
+    """Non-convex or clockwise quadrilaterals are mesh errors; general
+    quadrilaterals and hybrid meshes are colored, and their device calls are
+    refused on the host; an odd closed quadrilateral mesh cannot be 4-colored."""
+    mi = W.periodic_square_quad(6)
+    bad = mi.ev.copy()
+    bad[3] = bad[3, ::-1]
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_mesh_create_elem(dgc.DGC_QUAD, 1, mi.xyz, bad, mi.periodic_len)
+    assert e.value.status == 2
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_mesh_create_elem(dgc.DGC_QUAD, 4, mi.xyz, mi.ev, mi.periodic_len)
+    assert e.value.status == 4
+    for gen in (lambda: W.hybrid_square(8, 0.3, seed=1), lambda: W.periodic_square_quad(8, "vertex", 0.2, seed=1)):
+        g = gen()
+        m = dgc.Mesh.from_input(g, 2)
+        assert m.elem == dgc.DGC_QUAD and m.nonaffine > 0
+        m.color(3)
+        with pytest.raises(dgc.DgcError) as e:
+            dgc.dgc_rhs(m.h, dgc.DGC_FP64, 4096, 8192, 0)
+        assert e.value.status == 4
+        with pytest.raises(dgc.DgcError) as e:
+            dgc.dgc_refine(m.h, np.array([0], np.int32))
+        assert e.value.status == 4
+        m.close()
+    m = dgc.Mesh.from_input(W.periodic_square_quad(5), 1)
+    with pytest.raises(dgc.DgcError) as e:
+        m.color(1, max_swaps=20000)
+    assert e.value.status == 3
+    m.close()
 
 
 @pytest.mark.parametrize("p", [1, 2])
