@@ -404,15 +404,13 @@ Workspace carve(const Mesh& m, dgc_prec prec, char* base) {
 // One SSP-RK3 step.  Per stage: FIRST + COLOR... + LAST (volume integral fused
 // into the first color, stage update into the last) on meshes where every
 // element has one edge of each color, else VOLUME + every color + STAGE.
-// Quadrilateral meshes fuse the volume integral into the first color and run
-// the stage update as its own pass (no fused last color).
 // launch(cls, f) issues the kernels of f() and counts them.
 template <typename Launch>
 void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cfl_, double* dt, const Workspace& w,
                   Launch&& launch) {
   const std::vector<int32_t>& off = m.color_off;
   const int C = m.ncolors;
-  const bool fused = m.fuse && m.perfect && C >= 2 && !m.quad;
+  const bool fused = m.fuse && m.perfect && C >= 2;
   if (prec == DGC_FP64) {
     double* c64 = static_cast<double*>(c);
     launch(DGC_K_CFL, [&] { return cfl(x, c64, cfl_, dt, nullptr); });

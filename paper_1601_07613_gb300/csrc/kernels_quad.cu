@@ -20,8 +20,9 @@
 // the edge points, as Eq. 2 writes it.
 //
 // FP64 kernels evaluate Eq. 2 as written; FP32 kernels in the perturbation form
-// of euler_pert.cuh.  The RK step on quadrilateral meshes fuses the volume
-// integral into the first color and runs the stage update as its own pass.
+// of euler_pert.cuh.  The RK step fuses the volume integral into the first color
+// and the stage update into the last (quad_last64 / quad_last32), one variable
+// at a time.
 #include <cfloat>
 
 #include "dev_util.cuh"
@@ -194,23 +195,6 @@ __device__ __forceinline__ void qload_pert(const float* src, QuadPert<P>& B) {
   }
 }
 
-// FP32 record of an FP64 block (the layout of qload_pert<float>)
-template <int P>
-__device__ __forceinline__ void qrecord_of(const double (&v)[QuadDim<P>::NV], float (&r)[QuadDim<P>::NF]) {
-  using D = QuadDim<P>;
-  const double phi0 = quad_tab<double, P>().phiV[0][0];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const double u = phi0 * v[m * D::NP];
-    r[m] = d2f(u);
-    r[4 + m] = d2f(u - f2d(r[m]));
-#pragma unroll
-    for (int j = 1; j < D::NP; ++j) r[8 + m * (D::NP - 1) + j - 1] = d2f(v[m * D::NP + j]);
-  }
-#pragma unroll
-  for (int i = 4 * (D::NP + 1); i < D::NF; ++i) r[i] = 0.0f;
-}
-
 // ---------------------------------------------------------------------------
 // FP64 Euler flux, Eq. 2 as written
 // ---------------------------------------------------------------------------
@@ -336,6 +320,7 @@ struct QuadParams {
   const void* state;
   void* rhs;
   void* buf;
+  StageArgs sa;
   int sstride;  // floats per element of an FP32 state (record)
 };
 
@@ -393,6 +378,31 @@ struct QuadRank1 {
   __device__ __forceinline__ T operator()(int m, int a, int b) const { return X[m][a] * Y[m][b]; }
 };
 
+// Loads and stores of one variable's NP values at v (16-byte vectors when the
+// row starts on a 16-byte boundary: NP a multiple of 4)
+template <int N, typename T>
+__device__ __forceinline__ void row_load(const T* v, T (&x)[N]) {
+  if constexpr (N % 4 == 0 && sizeof(T) == 4) {
+    qload<N>(v, x);
+  } else if constexpr (N % 2 == 0 && sizeof(T) == 8) {
+    qload<N>(v, x);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = v[i];
+  }
+}
+template <int N, typename T>
+__device__ __forceinline__ void row_store(T* v, const T (&x)[N]) {
+  if constexpr (N % 4 == 0 && sizeof(T) == 4) {
+    qstore<N>(v, x);
+  } else if constexpr (N % 2 == 0 && sizeof(T) == 8) {
+    qstore<N>(v, x);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = x[i];
+  }
+}
+
 template <int P, typename RT, int MODE, typename AT>
 __device__ __forceinline__ void quad_write(const QuadParams& A, int64_t elem, int64_t k, int side,
                                            const QuadRank1<AT, P>& W, const AT* acc) {
@@ -400,13 +410,15 @@ __device__ __forceinline__ void quad_write(const QuadParams& A, int64_t elem, in
   constexpr int NV = D::NV, NP = D::NP, N1 = D::N1;
   RT* r = static_cast<RT*>(A.rhs) + elem * NV;
   if constexpr (MODE == SURF_RMW) {
-    RT v[NV];
-    qload(r, v);
+    // one variable at a time: the row's loads, then its stores
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+    for (int m = 0; m < 4; ++m) {
+      RT v[NP];
+      row_load<NP>(r + m * NP, v);
 #pragma unroll
-      for (int j = 0; j < NP; ++j) v[m * NP + j] += (RT)W(m, j / N1, j % N1);
-    qstore(r, v);
+      for (int j = 0; j < NP; ++j) v[j] += (RT)W(m, j / N1, j % N1);
+      row_store<NP>(r + m * NP, v);
+    }
   } else if constexpr (MODE == SURF_FIRST) {
     RT v[NV];
 #pragma unroll
@@ -426,6 +438,83 @@ __device__ __forceinline__ void quad_write(const QuadParams& A, int64_t elem, in
 #pragma unroll
       for (int j = 0; j < NP; ++j) v[m * NP + j] = (RT)W(m, j / N1, j % N1);
     qstore(static_cast<RT*>(A.buf) + (2 * k + side) * NV, v);
+  }
+}
+
+// Last color, FP64 form: the element's rhs is the stored part plus this edge's
+// rank-one term; uout = a0 u0 + b0 (us + dt L), one variable at a time (the
+// stage input us is re-read: the lane is the only one touching its element).
+template <int P>
+__device__ __forceinline__ void quad_last64(const QuadParams& A, int64_t elem, const QuadRank1<double, P>& W) {
+  using D = QuadDim<P>;
+  constexpr int NP = D::NP, NV = D::NV, N1 = D::N1;
+  const double dt = *A.sa.dt, a0 = A.sa.a0, b0 = A.sa.b0, bdt = b0 * dt;
+  const double* part = static_cast<const double*>(A.rhs) + elem * NV;
+  const double* us = static_cast<const double*>(A.state) + elem * NV;
+  const double* u0 = A.sa.u0 + elem * NV;
+  double* out = A.sa.uout + elem * NV;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    double L[NP], u[NP], z[NP];
+    row_load<NP>(part + m * NP, L);
+    row_load<NP>(us + m * NP, u);
+    if (a0 != 0.0) row_load<NP>(u0 + m * NP, z);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const double Lj = L[j] + W(m, j / N1, j % N1);
+      L[j] = a0 == 0.0 ? fma(bdt, Lj, b0 == 1.0 ? u[j] : b0 * u[j]) : fma(bdt, Lj, fma(a0, z[j], b0 * u[j]));
+    }
+    row_store<NP>(out + m * NP, L);
+  }
+}
+
+// Last color, FP32 increment form of the step (incr_form.cuh), one variable at a
+// time: stages 0 and 1 write the increment and the record of the next stage's
+// state (from the record of u0), stage 2 updates the FP64 state.
+template <int P>
+__device__ __forceinline__ void quad_last32(const QuadParams& A, int64_t elem, const QuadRank1<float, P>& W) {
+  using D = QuadDim<P>;
+  constexpr int NP = D::NP, NV = D::NV, N1 = D::N1, NF = D::NF;
+  const StageArgs& S = A.sa;
+  const F2 dtp = split_f2(*S.dt);
+  const float* part = static_cast<const float*>(A.rhs) + elem * NV;
+  float* dp = S.delta + elem * NV;
+  if (S.stage < 2) {
+    const F2 p0 = split_f2(quad_tab<double, P>().phiV[0][0]);
+    float r[NF];
+    qload<NF>(S.rec0 + elem * S.rec0_stride, r);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float d[NP];
+      row_load<NP>(part + m * NP, d);
+      if (S.stage == 0) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) d[j] = mul_f2(d[j] + W(m, j / N1, j % N1), dtp);
+      } else {
+        float d0[NP];
+        row_load<NP>(dp + m * NP, d0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) d[j] = 0.25f * (d0[j] + mul_f2(d[j] + W(m, j / N1, j % N1), dtp));
+      }
+      pair_add_scaled(r[m], r[4 + m], d[0], p0);
+#pragma unroll
+      for (int j = 1; j < NP; ++j) r[8 + m * (NP - 1) + j - 1] += d[j];
+      row_store<NP>(dp + m * NP, d);
+    }
+    qstore<NF>(S.rec_out + elem * NF, r);
+    return;
+  }
+  // stage 2: delta_2 + dt L; b_2 = 2/3 is applied by the state update
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float d[NP], d0[NP];
+    double z[NP];
+    row_load<NP>(part + m * NP, d);
+    row_load<NP>(dp + m * NP, d0);
+    row_load<NP>(S.u0 + elem * NV + m * NP, z);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) z[j] = fma(2.0 / 3.0, f2d(d0[j] + mul_f2(d[j] + W(m, j / N1, j % N1), dtp)), z[j]);
+    row_store<NP>(S.uout + elem * NV + m * NP, z);
   }
 }
 
@@ -518,7 +607,11 @@ __global__ void __launch_bounds__(256)
       pdl_wait();
       pdl_trigger();
     }
-    if (writer) quad_write<P, RT, MODE>(A, elem, k, side, W, acc);
+    if constexpr (MODE == SURF_LAST) {
+      if (writer) quad_last64<P>(A, elem, W);
+    } else if (writer) {
+      quad_write<P, RT, MODE>(A, elem, k, side, W, acc);
+    }
   } else {
     const QuadTab<float, P>& K = quad_tab<float, P>();
     QuadEdge<float, P> E;
@@ -574,7 +667,11 @@ __global__ void __launch_bounds__(256)
       pdl_wait();
       pdl_trigger();
     }
-    if (writer) quad_write<P, RT, MODE>(A, elem, k, side, W, acc);
+    if constexpr (MODE == SURF_LAST) {
+      if (writer) quad_last32<P>(A, elem, W);
+    } else if (writer) {
+      quad_write<P, RT, MODE>(A, elem, k, side, W, acc);
+    }
   }
 }
 
@@ -583,50 +680,58 @@ __global__ void __launch_bounds__(256)
 // of every element, then FP64 only for the elements within kCflMargin of the
 // minimum.
 // ---------------------------------------------------------------------------
-template <int P, typename T>
-__device__ __forceinline__ T quad_lambda_max(const T (&v)[QuadDim<P>::NV]) {
+// FP32 estimate of max_q (|u| + c) from the FP32 record (mean pair + modes)
+template <int P>
+__device__ __forceinline__ float quad_lambda_rec(const float (&r)[QuadDim<P>::NF]) {
   using D = QuadDim<P>;
   constexpr int NP = D::NP;
-  const QuadTab<T, P>& K = quad_tab<T, P>();
-  T lam = T(0);
+  const QuadTab<float, P>& K = quad_tab<float, P>();
+  float lam = 0.0f;
 #pragma unroll 1
   for (int q = 0; q < D::NQV; ++q) {
-    T U[4];
+    float U[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      T s = T(0);
+      float s = r[4 + m];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * v[m * NP + j];
-      U[m] = s;
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[8 + m * (NP - 1) + j - 1];
+      U[m] = r[m] + s;
     }
-    const T ir = T(1) / U[0], u = U[1] * ir, w = U[2] * ir;
-    const T q2 = u * u + w * w;
-    const T pr = T(0.4) * (U[3] - T(0.5) * U[0] * q2);
-    lam = fmax(lam, sqrt(q2) + sqrt(T(1.4) * pr * ir));
+    const float ir = rcp_fast(U[0]), u = U[1] * ir, w = U[2] * ir;
+    const float q2 = u * u + w * w;
+    const float pr = 0.4f * (U[3] - 0.5f * U[0] * q2);
+    lam = fmaxf(lam, sqrt_fast(q2) + sqrt_fast(1.4f * pr * ir));
   }
   return lam;
 }
 
+// pass 1: the element's record (written when shadow is set) and its FP32 estimate
 template <int P>
 __global__ void __launch_bounds__(128) k_cfl1_quad(const double* c, const double* inr, int64_t ne, float* est,
                                                    unsigned* minbits, float* shadow) {
   using D = QuadDim<P>;
+  constexpr int NP = D::NP;
   pdl_wait();
   pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float best = FLT_MAX;
   if (e < ne) {
-    double v[D::NV];
-    qload(c + e * D::NV, v);
-    if (shadow) {
-      float r[D::NF];
-      qrecord_of<P>(v, r);
-      qstore(shadow + e * D::NF, r);
-    }
-    float f[D::NV];
+    const double phi0 = quad_tab<double, P>().phiV[0][0];
+    float r[D::NF];
 #pragma unroll
-    for (int i = 0; i < D::NV; ++i) f[i] = d2f(v[i]);
-    float d = d2f(inr[e]) / ((2 * P + 1) * quad_lambda_max<P, float>(f));
+    for (int m = 0; m < 4; ++m) {
+      double v[NP];
+      row_load<NP>(c + e * D::NV + m * NP, v);
+      const double u = phi0 * v[0];
+      r[m] = d2f(u);
+      r[4 + m] = d2f(u - f2d(r[m]));
+#pragma unroll
+      for (int j = 1; j < NP; ++j) r[8 + m * (NP - 1) + j - 1] = d2f(v[j]);
+    }
+#pragma unroll
+    for (int i = 4 * (NP + 1); i < D::NF; ++i) r[i] = 0.0f;
+    if (shadow) qstore(shadow + e * D::NF, r);
+    float d = d2f(inr[e]) / ((2 * P + 1) * quad_lambda_rec<P>(r));
     if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;  // non-physical: always re-evaluated
     est[e] = d;
     best = d;
@@ -719,12 +824,17 @@ static int qsurf_mode(const Ctx& x, SurfMode mode, const QuadParams& A) {
     case SURF_FIRST: return qsurf_launch<P, CT, ST, RT, SURF_FIRST>(x, A);
     case SURF_ATOMIC: return qsurf_launch<P, CT, ST, RT, SURF_ATOMIC>(x, A);
     case SURF_BUFFER: return qsurf_launch<P, CT, ST, RT, SURF_BUFFER>(x, A);
-    default: return -1;  // no fused last color on quadrilateral meshes
+    default: return -1;
   }
 }
 
 template <int P>
 static int qsurf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const QuadParams& A) {
+  if (mode == SURF_LAST) {
+    if (ty == TY_D) return qsurf_launch<P, double, double, double, SURF_LAST>(x, A);
+    if (ty == TY_MF && A.sa.kstate == nullptr) return qsurf_launch<P, float, float, float, SURF_LAST>(x, A);
+    return -1;
+  }
   switch (ty) {
     case TY_D: return qsurf_mode<P, double, double, double>(x, mode, A);
     case TY_MD: return qsurf_mode<P, float, double, double>(x, mode, A);
@@ -737,7 +847,6 @@ static int qsurf_p(const Ctx& x, TypeCfg ty, SurfMode mode, const QuadParams& A)
 
 int quad_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                  int sstride, void* rhs, void* buf, const StageArgs* sa) {
-  (void)sa;
   QuadParams A;
   A.begin = begin;
   A.end = end;
@@ -748,6 +857,7 @@ int quad_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t
   A.state = state;
   A.rhs = rhs;
   A.buf = buf;
+  if (sa) A.sa = *sa;
   switch (x.p) {
     case 1: return qsurf_p<1>(x, ty, mode, A);
     case 2: return qsurf_p<2>(x, ty, mode, A);

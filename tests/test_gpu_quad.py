@@ -6,9 +6,13 @@ Tolerances as for triangles: FP64 right-hand side 1e-12 relative L2, FP32-mixed
 and 1e-12 (mixed, whose CFL pass reads the same FP64 state).  Meshes: slanted
 periodic parallelograms (4 colors, every element has each color once) and
 jittered rectangles on the open square (boundary edges, transmissive state).
-Sizes from 6 x 6 (18 edges per color, one partial block) to 64 x 64; the full
+Sizes from 6 x 6 (18 edges per color, one partial block) to 16 x 16; the full
 quadrilateral workload (810 x 810 periodic parallelograms, p = 3) is checked on
-sampled elements and by conservation.
+sampled elements and by conservation.  At h = 1/810 the terms of Eq. 2 (of size
+|F|/h) cancel to a much smaller right-hand side, and two exact FP64 evaluations
+agree only to their rounding of those terms: there the FP64 bound is
+max(1e-12, twice the oracle's disagreement with itself on the mesh translated by
+half a period), computed in the test, as for the triangle workloads.
 """
 
 import numpy as np
@@ -205,10 +209,14 @@ def test_full_size_quad_rhs_sampled(full, oracle_mod):
     sample = np.sort(np.random.default_rng(0).choice(run.om.ne, 3000, replace=False))
     run.load(c)
     ref = run.om.rhs(cfg["p"], c, elems=sample)
+    mi = cfg["mesh"]
+    shifted = oracle_mod.OracleMesh(2, (mi.xyz + 0.5) % 1.0, mi.ev, mi.periodic_len)
+    floor = rel(shifted.rhs(cfg["p"], c, elems=sample), ref)
     e64 = rel(run.rhs(dgc.DGC_FP64)[sample], ref)
     e32 = rel(run.rhs(dgc.DGC_FP32_MIXED)[sample], ref)
-    print(f"quad full size: FP64 rel L2 {e64:.3e}, FP32-mixed {e32:.3e}")
-    assert e64 < 1e-12 and e32 < 1e-5
+    print(f"quad full size: FP64 rel L2 {e64:.3e} (oracle floor {floor:.3e}), FP32-mixed {e32:.3e}")
+    assert e64 < max(1e-12, 2.0 * floor)
+    assert e32 < 1e-5
 
 
 def test_full_size_quad_steps_conserve(full):
