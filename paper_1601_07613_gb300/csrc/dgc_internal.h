@@ -28,6 +28,10 @@ struct RefTables {
   // sqrt(2k+1) P_k(2x-1) (phi_{a(p+1)+b}(r, s) = l_a(r) l_b(s)) at the edge
   // points, [nqf][p+1], and at the ends x = 0 and x = 1, [p+1] each
   std::vector<double> eleg, lend0, lend1;
+  // quadrilaterals: the 1-D factors of the volume rule (the square's (p+1)^2
+  // points are (x_i, x_k)): l_a(x_i) and l_a'(x_i), [p+1][p+1], and weights
+  // summing to 1, [p+1]
+  std::vector<double> vleg, vdleg, vw1;
 };
 
 // Builds the tables (quadrature + orthonormal basis) for triangles (dim 2),

@@ -59,6 +59,10 @@ struct QuadTab {
   T wL[D::NQF][D::N1];  // w_q l_k(t_q), edge weights summing to 1
   T e0[D::N1];          // l_k(0)
   T e1[D::N1];          // l_k(1)
+  // the volume rule's 1-D factors: point (i, k) of the square is (x_i, x_k)
+  T L1[D::N1][D::N1];   // l_a(x_i)
+  T D1[D::N1][D::N1];   // l_a'(x_i)
+  T w1[D::N1];          // 1-D weights, summing to 1
 };
 
 __constant__ QuadTab<double, 1> cQuadD1;
@@ -94,6 +98,13 @@ static void fill_quad(QuadTab<T, P>& K, const RefTables& R) {
   for (int k = 0; k < D::N1; ++k) {
     K.e0[k] = (T)R.lend0[k];
     K.e1[k] = (T)R.lend1[k];
+  }
+  for (int i = 0; i < D::N1; ++i) {
+    K.w1[i] = (T)R.vw1[i];
+    for (int a = 0; a < D::N1; ++a) {
+      K.L1[i][a] = (T)R.vleg[i * D::N1 + a];
+      K.D1[i][a] = (T)R.vdleg[i * D::N1 + a];
+    }
   }
 }
 
@@ -211,43 +222,80 @@ __device__ __forceinline__ void euler2_n(const double* U, double nx, double ny, 
   F[3] = (U[3] + p) * un;
 }
 
-// volume integral sum_q w_q (J^-1 F(U_q)) . grad_ref phi_j, added to acc
-template <int P>
-__device__ __forceinline__ void quad_volume64(const double (&c)[QuadDim<P>::NV], const double* ji,
-                                              double (&acc)[QuadDim<P>::NV]) {
+// Volume integral sum_q w_q (J^-1 F(U_q)) . grad_ref phi_j, added to acc, by sum
+// factorisation over the tensor rule (points (x_i, x_k), weights w_i w_k):
+//   U(i, k) = sum_a l_a(x_i) W_{a,k},  W_{a,k} = sum_b c_{a,b} l_b(x_k);
+//   acc_{a,b} += sum_i [ l_a'(x_i) A_{i,b} + l_a(x_i) B_{i,b} ],
+//   A_{i,b} = sum_k w_i w_k l_b(x_k) F_r(i, k),  B_{i,b} = sum_k w_i w_k l_b'(x_k) F_s(i, k),
+// with F_r, F_s the reference-direction fluxes F . grad r, F . grad s.  The same
+// sums as point by point over the (p+1)^2 points, in (p+1)^3 FMAs per variable
+// and stage instead of (p+1)^4.  c(m, a, b) gives the block.
+template <int P, typename F>
+__device__ __forceinline__ void quad_volume64(F&& c, const double* ji, double (&acc)[QuadDim<P>::NV]) {
   using D = QuadDim<P>;
-  constexpr int NP = D::NP;
+  constexpr int NP = D::NP, N1 = D::N1;
   const QuadTab<double, P>& K = quad_tab<double, P>();
   double J[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) J[i] = __ldg(ji + i);
+  double W[4][N1][N1];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int a = 0; a < N1; ++a)
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < N1; ++b) t += c(m, a, b) * K.L1[k][b];
+        W[m][a][k] = t;
+      }
 #pragma unroll 1
-  for (int q = 0; q < D::NQV; ++q) {
-    double U[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * c[m * NP + j];
-      U[m] = s;
-    }
-    // reference-direction fluxes F . grad r and F . grad s
-    double Fr[4], Fs[4], un, cs;
-    euler2_n(U, J[0], J[1], Fr, un, cs);
-    euler2_n(U, J[2], J[3], Fs, un, cs);
+  for (int i = 0; i < N1; ++i) {
+    double A[4][N1], B[4][N1];
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * Fr[m] + K.vs[q][j] * Fs[m];
+      for (int b = 0; b < N1; ++b) A[m][b] = B[m][b] = 0.0;
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+      double U[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        double t = 0.0;
+#pragma unroll
+        for (int a = 0; a < N1; ++a) t += K.L1[i][a] * W[m][a][k];
+        U[m] = t;
+      }
+      double Fr[4], Fs[4], un, cs;
+      euler2_n(U, J[0], J[1], Fr, un, cs);
+      euler2_n(U, J[2], J[3], Fs, un, cs);
+      const double w = K.w1[i] * K.w1[k];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) {
+          A[m][b] += (w * K.L1[k][b]) * Fr[m];
+          B[m][b] += (w * K.D1[k][b]) * Fs[m];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int a = 0; a < N1; ++a)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) acc[m * NP + a * N1 + b] += K.D1[i][a] * A[m][b] + K.L1[i][a] * B[m][b];
   }
 }
 
-// FP32 volume integral in perturbation form (F(ub) left out: grad phi_0 = 0)
+// FP32 volume integral in perturbation form, sum-factorised as above: the
+// deviation d = u - ub from the modes j >= 1 and lo, F(ub) left out (its
+// integral against grad phi_j vanishes), and grad phi_0 = 0
 template <int P>
 __device__ __forceinline__ void quad_volume32(const QuadPert<P>& B, const PertRef<2>& R, const double* ji,
                                               float (&acc)[QuadDim<P>::NV]) {
   using D = QuadDim<P>;
-  constexpr int NP = D::NP;
+  constexpr int NP = D::NP, N1 = D::N1;
   const QuadTab<float, P>& K = quad_tab<float, P>();
   float J[2][2], th[2];
 #pragma unroll
@@ -256,25 +304,57 @@ __device__ __forceinline__ void quad_volume32(const QuadPert<P>& B, const PertRe
     J[k][1] = d2f(__ldg(ji + 2 * k + 1));
     th[k] = R.u[1] * J[k][0] + R.u[2] * J[k][1];
   }
+  float W[4][N1][N1];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int a = 0; a < N1; ++a)
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        float t = 0.0f;
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+          if (a + b > 0) t += B.cd[m][a * N1 + b - 1] * K.L1[k][b];
+        W[m][a][k] = t;
+      }
 #pragma unroll 1
-  for (int q = 0; q < D::NQV; ++q) {
-    float d[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      float s = B.lo[m];
-#pragma unroll
-      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * B.cd[m][j - 1];
-      d[m] = s;
-    }
-    PertState<2> S;
-    S.init(R, d);
-    float Fr[4], Fs[4];
-    pert_flux<2>(R, S, d, J[0], th[0], Fr);
-    pert_flux<2>(R, S, d, J[1], th[1], Fs);
+  for (int i = 0; i < N1; ++i) {
+    float A[4][N1], Bs[4][N1];
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
-      for (int j = 1; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * Fr[m] + K.vs[q][j] * Fs[m];
+      for (int b = 0; b < N1; ++b) A[m][b] = Bs[m][b] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+      float d[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        float t = B.lo[m];
+#pragma unroll
+        for (int a = 0; a < N1; ++a) t += K.L1[i][a] * W[m][a][k];
+        d[m] = t;
+      }
+      PertState<2> S;
+      S.init(R, d);
+      float Fr[4], Fs[4];
+      pert_flux<2>(R, S, d, J[0], th[0], Fr);
+      pert_flux<2>(R, S, d, J[1], th[1], Fs);
+      const float w = K.w1[i] * K.w1[k];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) {
+          A[m][b] += (w * K.L1[k][b]) * Fr[m];
+          Bs[m][b] += (w * K.D1[k][b]) * Fs[m];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int a = 0; a < N1; ++a)
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+          if (a + b > 0) acc[m * NP + a * N1 + b] += K.D1[i][a] * A[m][b] + K.L1[i][a] * Bs[m][b];
   }
 }
 
@@ -290,7 +370,7 @@ __global__ void __launch_bounds__(128) k_vol_quad(const ST* c, int sstride, cons
     qload(c + e * D::NV, v);
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
-    quad_volume64<P>(v, jinv + 4 * e, acc);
+    quad_volume64<P>([&](int m, int a, int b) { return v[m * D::NP + a * D::N1 + b]; }, jinv + 4 * e, acc);
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
   } else {
@@ -560,8 +640,8 @@ __global__ void __launch_bounds__(256)
       qload(cs, c);
 #pragma unroll
       for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-      quad_volume64<P>(c, A.jinv + 4 * elem, acc);
       trace_coeffs<double, P>(E, [&](int m, int a, int b) { return c[m * NP + a * N1 + b]; }, Tc);
+      quad_volume64<P>([&](int m, int a, int b) { return c[m * NP + a * N1 + b]; }, A.jinv + 4 * elem, acc);
     } else {
       double c[NV];
       qload(cs, c);
@@ -621,12 +701,6 @@ __global__ void __launch_bounds__(256)
     qload_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
     PertRef<2> R;
     R.init(B.hi);
-    float acc[MODE == SURF_FIRST ? NV : 1];
-    if constexpr (MODE == SURF_FIRST) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
-      quad_volume32<P>(B, R, A.jinv + 4 * elem, acc);
-    }
     // own trace minus ub: the modes j >= 1, and lo on the constant (l_0 = 1)
     float Tc[4][N1];
     trace_coeffs<float, P>(
@@ -638,6 +712,12 @@ __global__ void __launch_bounds__(256)
         Tc);
 #pragma unroll
     for (int m = 0; m < 4; ++m) Tc[m][0] += B.lo[m];
+    float acc[MODE == SURF_FIRST ? NV : 1];
+    if constexpr (MODE == SURF_FIRST) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
+      quad_volume32<P>(B, R, A.jinv + 4 * elem, acc);
+    }
     FaceConst<2> F;
     F.init(R, B.hi, {d2f(g0.x), d2f(g0.y)}, side);
     float g[4][N1];

@@ -337,6 +337,19 @@ RefTables make_tables(int dim, int p, bool quad) {
       T.lend0[k] = c * jacobi(k, 0, 0, -1.0);
       T.lend1[k] = c * jacobi(k, 0, 0, 1.0);
     }
+    std::vector<double> xg(p + 1), wg(p + 1);
+    gauss_jacobi(p + 1, 0.0, xg.data(), wg.data());
+    T.vleg.resize((size_t)(p + 1) * (p + 1));
+    T.vdleg.resize((size_t)(p + 1) * (p + 1));
+    T.vw1.resize(p + 1);
+    for (int i = 0; i <= p; ++i) {
+      T.vw1[i] = 0.5 * wg[i];
+      for (int k = 0; k <= p; ++k) {
+        const double c = std::sqrt(2.0 * k + 1.0);
+        T.vleg[(size_t)i * (p + 1) + k] = c * jacobi(k, 0, 0, xg[i]);
+        T.vdleg[(size_t)i * (p + 1) + k] = 2.0 * c * djacobi(k, 0, 0, xg[i]);
+      }
+    }
     return T;
   }
   for (int f = 0; f < T.nfaces; ++f) {
