@@ -186,8 +186,8 @@ def kernel_source_hash() -> str:
 # over the launches of each class) from the launch list of this benchmark's own
 # command, profiles/launch_list_rk_fp32mixed_p3_1048352tri.md, taken with the
 # kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = "9cb08189b89902df"
-TRAFFIC_BYTES = {"last": 1122655086, "first": 364753615, "color": 589439781, "cfl": 495503835}
+TRAFFIC_SOURCES = "688ab6f78f76c4a7"
+TRAFFIC_BYTES = {"last": 1122699349, "first": 364705122, "color": 589416143, "cfl": 495481454}
 
 
 def replica_throughput(torch, ms: float, world: int, units_per_step: float, dev):
@@ -468,7 +468,7 @@ def run_batched(dgc, torch, dev, stream, args):
     return out
 
 
-def run_other_meshes(dgc, torch, dev, stream, args):
+def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     """The other workloads, each an RK step in FP64 and in mixed precision, and
     its right-hand side colored / atomicAdd / two-pass:
     1,572,864 periodic Kuhn tetrahedra at p = 2 (4 face colors; seeded random
@@ -486,6 +486,8 @@ def run_other_meshes(dgc, torch, dev, stream, args):
     for tag, mi, p, refine in (("tet_p2_64cube", tube["mesh"], tube["p"], None),
                                ("nonconforming_p2_256", ref["mesh"], ref["p"], ref["refine"]),
                                ("quad_p3_810", quad["mesh"], quad["p"], None)):
+        if only is not None and not tag.startswith(only):
+            continue
         t0 = time.perf_counter()
         m = dgc.Mesh.from_input(mi, p)
         _, per_color = m.color(1601)
@@ -677,8 +679,20 @@ def main():
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
+    ap.add_argument("--only", choices=["tet", "nonconforming", "quad"],
+                    help="time only that one of the other workloads (its variants entry, printed alone)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.only:
+        import torch
+
+        from paper_1601_07613_gb300 import dgc
+
+        dgc.lib()
+        dev = torch.device("cuda:0")
+        print(json.dumps(run_other_meshes(dgc, torch, dev, torch.cuda.current_stream(), args, only=args.only)),
+              flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
