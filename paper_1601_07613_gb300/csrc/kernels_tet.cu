@@ -542,26 +542,28 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
 
 // CFL reduction in two passes, as for triangles: FP32 estimates of every
 // element, then FP64 only for the elements within kCflMargin of the minimum.
-template <int P, typename T>
-__device__ __forceinline__ T tet_lambda_max(const T (&v)[TetDim<P>::NV]) {
+// Pass 1 builds the element's FP32 record one variable at a time and takes the
+// estimate from it (mean pair + modes).
+template <int P>
+__device__ __forceinline__ float tet_lambda_rec(const float (&r)[TetDim<P>::NF]) {
   using D = TetDim<P>;
   constexpr int NP = D::NP;
-  const TetTab<T, P>& K = tet_tab<T, P>();
-  T lam = T(0);
+  const TetTab<float, P>& K = tet_tab<float, P>();
+  float lam = 0.0f;
 #pragma unroll 2
   for (int q = 0; q < D::NQV; ++q) {
-    T U[5];
+    float U[5];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-      T s = T(0);
+      float s = r[5 + m];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * v[m * NP + j];
-      U[m] = s;
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[10 + m * (NP - 1) + j - 1];
+      U[m] = r[m] + s;
     }
-    const T ir = T(1) / U[0], u = U[1] * ir, w = U[2] * ir, z = U[3] * ir;
-    const T q2 = u * u + w * w + z * z;
-    const T pr = T(0.4) * (U[4] - T(0.5) * U[0] * q2);
-    lam = fmax(lam, sqrt(q2) + sqrt(T(1.4) * pr * ir));
+    const float ir = rcp_fast(U[0]), u = U[1] * ir, w = U[2] * ir, z = U[3] * ir;
+    const float q2 = u * u + w * w + z * z;
+    const float pr = 0.4f * (U[4] - 0.5f * U[0] * q2);
+    lam = fmaxf(lam, sqrt_fast(q2) + sqrt_fast(1.4f * pr * ir));
   }
   return lam;
 }
@@ -570,22 +572,26 @@ template <int P>
 __global__ void __launch_bounds__(128) k_cfl1_tet(const double* c, const double* inr, int64_t ne, float* est,
                                                   unsigned* minbits, float* shadow) {
   using D = TetDim<P>;
+  constexpr int NP = D::NP;
   pdl_wait();
   pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float best = FLT_MAX;
   if (e < ne) {
-    double v[D::NV];
-    tload(c + e * D::NV, v);
-    if (shadow) {
-      float r[D::NF];
-      trecord_of<P>(v, r);
-      tstore(shadow + e * D::NF, r);
-    }
-    float f[D::NV];
+    const double phi0 = tet_tab<double, P>().phiV[0][0];
+    float r[D::NF];
 #pragma unroll
-    for (int i = 0; i < D::NV; ++i) f[i] = d2f(v[i]);
-    float d = d2f(inr[e]) / ((2 * P + 1) * tet_lambda_max<P, float>(f));
+    for (int m = 0; m < 5; ++m) {
+      double v[NP];
+      tload(c + e * D::NV + m * NP, v);
+      tsplit(phi0, v[0], r[m], r[5 + m]);
+#pragma unroll
+      for (int j = 1; j < NP; ++j) r[10 + m * (NP - 1) + j - 1] = d2f(v[j]);
+    }
+#pragma unroll
+    for (int i = 5 * (NP + 1); i < D::NF; ++i) r[i] = 0.0f;
+    if (shadow) tstore(shadow + e * D::NF, r);
+    float d = d2f(inr[e]) / ((2 * P + 1) * tet_lambda_rec<P>(r));
     if (!(d > 0.0f) || !(d < FLT_MAX)) d = 0.0f;
     est[e] = d;
     best = d;
@@ -613,8 +619,7 @@ __global__ void __launch_bounds__(128) k_cfl2_tet(const double* c, const double*
     const int src = __ffs(mask) - 1;
     mask &= mask - 1;
     const long long ec = __shfl_sync(0xffffffffu, (long long)e, src);
-    double v[D::NV];
-    tload(c + ec * D::NV, v);
+    const double* v = c + ec * D::NV;  // the same block for every lane: broadcast loads
     double lam = 0.0;
     for (int q = threadIdx.x & 31; q < D::NQV; q += 32) {
       double U[5];
