@@ -102,6 +102,37 @@ static void upload_p(const RefTables& R, const void* symD, const void* symF) {
   cudaMemcpyToSymbol(symF, &hf, sizeof hf);
 }
 
+// The FP32 volume tables with every entry twice, (v, v): the operand of a packed
+// two-lane FP32 FMA (__ffma2_rn, one instruction for two variables).
+template <int P>
+struct TriPairTab {
+  float2 phiV[TriDim<P>::NQV][TriDim<P>::NP];
+  float2 vr[TriDim<P>::NQV][TriDim<P>::NP];
+  float2 vs[TriDim<P>::NQV][TriDim<P>::NP];
+};
+__constant__ TriPairTab<1> cTriP1;
+__constant__ TriPairTab<2> cTriP2;
+__constant__ TriPairTab<3> cTriP3;
+template <int P>
+__device__ __forceinline__ const TriPairTab<P>& tri_ptab();
+template <> __device__ __forceinline__ const TriPairTab<1>& tri_ptab<1>() { return cTriP1; }
+template <> __device__ __forceinline__ const TriPairTab<2>& tri_ptab<2>() { return cTriP2; }
+template <> __device__ __forceinline__ const TriPairTab<3>& tri_ptab<3>() { return cTriP3; }
+
+template <int P>
+static void upload_pairs(const RefTables& R, const void* sym) {
+  static TriPairTab<P> h;
+  static TriTab<float, P> f;
+  fill_tab(f, R);
+  for (int q = 0; q < TriDim<P>::NQV; ++q)
+    for (int j = 0; j < TriDim<P>::NP; ++j) {
+      h.phiV[q][j] = make_float2(f.phiV[q][j], f.phiV[q][j]);
+      h.vr[q][j] = make_float2(f.vr[q][j], f.vr[q][j]);
+      h.vs[q][j] = make_float2(f.vs[q][j], f.vs[q][j]);
+    }
+  cudaMemcpyToSymbol(sym, &h, sizeof h);
+}
+
 
 
 int tri_record_floats(int p) { return 4 * ((p + 1) * (p + 2) / 2 + 1); }
@@ -302,6 +333,11 @@ __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], c
 
 // FP32 volume integral in perturbation form: sum_q w_q dF(U_q).(J^-T grad phi_j),
 // the constant F(ub) left out (it cancels against the faces); grad phi_0 = 0.
+// With DGC_FFMA2 the evaluation and the projection run on two variables at a
+// time through the packed FP32 FMA (__ffma2_rn): the same roundings per value.
+#ifndef DGC_FFMA2
+#define DGC_FFMA2 1
+#endif
 template <int P>
 __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRef<2>& R,
                                              const double* __restrict__ ji, float (&acc)[TriDim<P>::NV]) {
@@ -312,6 +348,47 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
   const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
   const float nr[2] = {d2f(j0.x), d2f(j0.y)}, ns[2] = {d2f(j1.x), d2f(j1.y)};
   const float thr = R.u[1] * nr[0] + R.u[2] * nr[1], ths = R.u[1] * ns[0] + R.u[2] * ns[1];
+#if DGC_FFMA2
+  // variables in pairs (0, 1), (2, 3): one packed FMA per mode and pair
+  const TriPairTab<P>& K2 = tri_ptab<P>();
+  float2 c01[NP - 1], c23[NP - 1], a01[NP - 1], a23[NP - 1];
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    c01[j - 1] = make_float2(B.cd[0][j - 1], B.cd[1][j - 1]);
+    c23[j - 1] = make_float2(B.cd[2][j - 1], B.cd[3][j - 1]);
+    a01[j - 1] = make_float2(acc[j], acc[NP + j]);
+    a23[j - 1] = make_float2(acc[2 * NP + j], acc[3 * NP + j]);
+  }
+  DGC_UNROLL_Q
+  for (int q = 0; q < D::NQV; ++q) {
+    float2 d01 = make_float2(B.lo[0], B.lo[1]), d23 = make_float2(B.lo[2], B.lo[3]);
+#pragma unroll
+    for (int j = 1; j < NP; ++j) {
+      d01 = __ffma2_rn(K2.phiV[q][j], c01[j - 1], d01);
+      d23 = __ffma2_rn(K2.phiV[q][j], c23[j - 1], d23);
+    }
+    const float d[4] = {d01.x, d01.y, d23.x, d23.y};
+    PertState<2> S;
+    S.init(R, d);
+    float Fr[4], Fs[4];
+    pert_flux<2>(R, S, d, nr, thr, Fr);
+    pert_flux<2>(R, S, d, ns, ths, Fs);
+    const float2 r01 = make_float2(Fr[0], Fr[1]), r23 = make_float2(Fr[2], Fr[3]);
+    const float2 s01 = make_float2(Fs[0], Fs[1]), s23 = make_float2(Fs[2], Fs[3]);
+#pragma unroll
+    for (int j = 1; j < NP; ++j) {
+      a01[j - 1] = __ffma2_rn(K2.vs[q][j], s01, __ffma2_rn(K2.vr[q][j], r01, a01[j - 1]));
+      a23[j - 1] = __ffma2_rn(K2.vs[q][j], s23, __ffma2_rn(K2.vr[q][j], r23, a23[j - 1]));
+    }
+  }
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    acc[j] = a01[j - 1].x;
+    acc[NP + j] = a01[j - 1].y;
+    acc[2 * NP + j] = a23[j - 1].x;
+    acc[3 * NP + j] = a23[j - 1].y;
+  }
+#else
   DGC_UNROLL_Q
   for (int q = 0; q < D::NQV; ++q) {
     float d[4];
@@ -332,6 +409,7 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
 #pragma unroll
       for (int j = 1; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * Fr[m] + K.vs[q][j] * Fs[m];
   }
+#endif
 }
 
 // An element's right-hand side from a [M][NP] register block: mode-major when
@@ -976,6 +1054,9 @@ void tri_upload_tables(int p, const RefTables& R) {
   if (p == 1) upload_ek<1>(R, &cTriK1);
   if (p == 2) upload_ek<2>(R, &cTriK2);
   if (p == 3) upload_ek<3>(R, &cTriK3);
+  if (p == 1) upload_pairs<1>(R, &cTriP1);
+  if (p == 2) upload_pairs<2>(R, &cTriP2);
+  if (p == 3) upload_pairs<3>(R, &cTriP3);
 }
 
 // One lane of the pair that handles edge k (side 0: left element, 1: right).
