@@ -119,11 +119,54 @@ static void upload_quad_p(const RefTables& R, const void* symD, const void* symF
     throw Error{DGC_ERR_CUDA, "cudaMemcpyToSymbol (quadrilateral tables)"};
 }
 
+// The FP32 volume factors with every entry twice, (v, v): operands of the packed
+// two-lane FP32 FMA (__ffma2_rn, one instruction for two variables), and the
+// projection factors with the point weights folded in.
+template <int P>
+struct QuadPairTab {
+  using D = QuadDim<P>;
+  float2 L1[D::N1][D::N1];          // l_a(x_i)
+  float2 D1[D::N1][D::N1];          // l_a'(x_i)
+  float2 WL[D::N1][D::N1][D::N1];   // w_i w_k l_b(x_k)
+  float2 WD[D::N1][D::N1][D::N1];   // w_i w_k l_b'(x_k)
+};
+__constant__ QuadPairTab<1> cQuadP1;
+__constant__ QuadPairTab<2> cQuadP2;
+__constant__ QuadPairTab<3> cQuadP3;
+template <int P>
+__device__ __forceinline__ const QuadPairTab<P>& quad_ptab();
+template <> __device__ __forceinline__ const QuadPairTab<1>& quad_ptab<1>() { return cQuadP1; }
+template <> __device__ __forceinline__ const QuadPairTab<2>& quad_ptab<2>() { return cQuadP2; }
+template <> __device__ __forceinline__ const QuadPairTab<3>& quad_ptab<3>() { return cQuadP3; }
+
+template <int P>
+static void upload_quad_pairs(const RefTables& R, const void* sym) {
+  using D = QuadDim<P>;
+  static QuadTab<float, P> f;
+  static QuadPairTab<P> h;
+  fill_quad(f, R);
+  for (int i = 0; i < D::N1; ++i)
+    for (int a = 0; a < D::N1; ++a) {
+      h.L1[i][a] = make_float2(f.L1[i][a], f.L1[i][a]);
+      h.D1[i][a] = make_float2(f.D1[i][a], f.D1[i][a]);
+      for (int b = 0; b < D::N1; ++b) {
+        const float wl = f.w1[i] * f.w1[a] * f.L1[a][b], wd = f.w1[i] * f.w1[a] * f.D1[a][b];
+        h.WL[i][a][b] = make_float2(wl, wl);
+        h.WD[i][a][b] = make_float2(wd, wd);
+      }
+    }
+  if (cudaMemcpyToSymbol(sym, &h, sizeof h) != cudaSuccess)
+    throw Error{DGC_ERR_CUDA, "cudaMemcpyToSymbol (quadrilateral pair tables)"};
+}
+
 void quad_upload_tables(int p, const RefTables& R) {
   if (!R.quad || R.p != p) return;
   if (p == 1) upload_quad_p<1>(R, &cQuadD1, &cQuadF1);
   if (p == 2) upload_quad_p<2>(R, &cQuadD2, &cQuadF2);
   if (p == 3) upload_quad_p<3>(R, &cQuadD3, &cQuadF3);
+  if (p == 1) upload_quad_pairs<1>(R, &cQuadP1);
+  if (p == 2) upload_quad_pairs<2>(R, &cQuadP2);
+  if (p == 3) upload_quad_pairs<3>(R, &cQuadP3);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,13 +333,14 @@ __device__ __forceinline__ void quad_volume64(F&& c, const double* ji, double (&
 
 // FP32 volume integral in perturbation form, sum-factorised as above: the
 // deviation d = u - ub from the modes j >= 1 and lo, F(ub) left out (its
-// integral against grad phi_j vanishes), and grad phi_0 = 0
+// integral against grad phi_j vanishes), and grad phi_0 = 0.  Variables (0, 1)
+// and (2, 3) go in pairs through the packed FP32 FMA (__ffma2_rn).
 template <int P>
 __device__ __forceinline__ void quad_volume32(const QuadPert<P>& B, const PertRef<2>& R, const double* ji,
                                               float (&acc)[QuadDim<P>::NV]) {
   using D = QuadDim<P>;
   constexpr int NP = D::NP, N1 = D::N1;
-  const QuadTab<float, P>& K = quad_tab<float, P>();
+  const QuadPairTab<P>& K2 = quad_ptab<P>();
   float J[2][2], th[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -304,58 +348,72 @@ __device__ __forceinline__ void quad_volume32(const QuadPert<P>& B, const PertRe
     J[k][1] = d2f(__ldg(ji + 2 * k + 1));
     th[k] = R.u[1] * J[k][0] + R.u[2] * J[k][1];
   }
-  float W[4][N1][N1];
+  float2 W[2][N1][N1];  // [pair][a][k]
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
+  for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int a = 0; a < N1; ++a)
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
-        float t = 0.0f;
+        float2 t = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int b = 0; b < N1; ++b)
-          if (a + b > 0) t += B.cd[m][a * N1 + b - 1] * K.L1[k][b];
-        W[m][a][k] = t;
+          if (a + b > 0)
+            t = __ffma2_rn(K2.L1[k][b], make_float2(B.cd[2 * h][a * N1 + b - 1], B.cd[2 * h + 1][a * N1 + b - 1]), t);
+        W[h][a][k] = t;
       }
+  float2 ac[2][NP];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) ac[h][j] = make_float2(acc[2 * h * NP + j], acc[(2 * h + 1) * NP + j]);
 #pragma unroll 1
   for (int i = 0; i < N1; ++i) {
-    float A[4][N1], Bs[4][N1];
+    float2 A[2][N1], Bs[2][N1];
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int b = 0; b < N1; ++b) A[m][b] = Bs[m][b] = 0.0f;
+      for (int b = 0; b < N1; ++b) A[h][b] = Bs[h][b] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
-      float d[4];
+      float2 t01 = make_float2(B.lo[0], B.lo[1]), t23 = make_float2(B.lo[2], B.lo[3]);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        float t = B.lo[m];
-#pragma unroll
-        for (int a = 0; a < N1; ++a) t += K.L1[i][a] * W[m][a][k];
-        d[m] = t;
+      for (int a = 0; a < N1; ++a) {
+        t01 = __ffma2_rn(K2.L1[i][a], W[0][a][k], t01);
+        t23 = __ffma2_rn(K2.L1[i][a], W[1][a][k], t23);
       }
+      const float d[4] = {t01.x, t01.y, t23.x, t23.y};
       PertState<2> S;
       S.init(R, d);
       float Fr[4], Fs[4];
       pert_flux<2>(R, S, d, J[0], th[0], Fr);
       pert_flux<2>(R, S, d, J[1], th[1], Fs);
-      const float w = K.w1[i] * K.w1[k];
+      const float2 r2[2] = {make_float2(Fr[0], Fr[1]), make_float2(Fr[2], Fr[3])};
+      const float2 s2[2] = {make_float2(Fs[0], Fs[1]), make_float2(Fs[2], Fs[3])};
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int b = 0; b < N1; ++b) {
-          A[m][b] += (w * K.L1[k][b]) * Fr[m];
-          Bs[m][b] += (w * K.D1[k][b]) * Fs[m];
+          A[h][b] = __ffma2_rn(K2.WL[i][k][b], r2[h], A[h][b]);
+          Bs[h][b] = __ffma2_rn(K2.WD[i][k][b], s2[h], Bs[h][b]);
         }
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int a = 0; a < N1; ++a)
 #pragma unroll
         for (int b = 0; b < N1; ++b)
-          if (a + b > 0) acc[m * NP + a * N1 + b] += K.D1[i][a] * A[m][b] + K.L1[i][a] * Bs[m][b];
+          if (a + b > 0)
+            ac[h][a * N1 + b] = __ffma2_rn(K2.D1[i][a], A[h][b], __ffma2_rn(K2.L1[i][a], Bs[h][b], ac[h][a * N1 + b]));
   }
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      acc[2 * h * NP + j] = ac[h][j].x;
+      acc[(2 * h + 1) * NP + j] = ac[h][j].y;
+    }
 }
 
 template <int P, typename CT, typename ST, typename RT>

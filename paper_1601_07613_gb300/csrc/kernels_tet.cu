@@ -76,10 +76,43 @@ static void upload_tet_p(const RefTables& R, const void* symD, const void* symF)
   cudaMemcpyToSymbol(symF, &hf, sizeof hf);
 }
 
+// The FP32 volume tables with every entry twice, (v, v): the operand of a packed
+// two-lane FP32 FMA (__ffma2_rn, one instruction for two variables).
+template <int P>
+struct TetPairTab {
+  float2 phiV[TetDim<P>::NQV][TetDim<P>::NP];
+  float2 vr[TetDim<P>::NQV][TetDim<P>::NP];
+  float2 vs[TetDim<P>::NQV][TetDim<P>::NP];
+  float2 vt[TetDim<P>::NQV][TetDim<P>::NP];
+};
+__constant__ TetPairTab<1> cTetP1;
+__constant__ TetPairTab<2> cTetP2;
+template <int P>
+__device__ __forceinline__ const TetPairTab<P>& tet_ptab();
+template <> __device__ __forceinline__ const TetPairTab<1>& tet_ptab<1>() { return cTetP1; }
+template <> __device__ __forceinline__ const TetPairTab<2>& tet_ptab<2>() { return cTetP2; }
+
+template <int P>
+static void upload_tet_pairs(const RefTables& R, const void* sym) {
+  static TetTab<float, P> f;
+  static TetPairTab<P> h;
+  fill_tet(f, R);
+  for (int q = 0; q < TetDim<P>::NQV; ++q)
+    for (int j = 0; j < TetDim<P>::NP; ++j) {
+      h.phiV[q][j] = make_float2(f.phiV[q][j], f.phiV[q][j]);
+      h.vr[q][j] = make_float2(f.vr[q][j], f.vr[q][j]);
+      h.vs[q][j] = make_float2(f.vs[q][j], f.vs[q][j]);
+      h.vt[q][j] = make_float2(f.vt[q][j], f.vt[q][j]);
+    }
+  cudaMemcpyToSymbol(sym, &h, sizeof h);
+}
+
 void tet_upload_tables(int p, const RefTables& R, DeviceMesh& d) {
   if (R.dim != 3 || R.p != p) return;
   if (p == 1) upload_tet_p<1>(R, &cTetD1, &cTetF1);
   if (p == 2) upload_tet_p<2>(R, &cTetD2, &cTetF2);
+  if (p == 1) upload_tet_pairs<1>(R, &cTetP1);
+  if (p == 2) upload_tet_pairs<2>(R, &cTetP2);
   // orientation tables for the faces, FP64 and FP32 copies, in global memory
   std::vector<double> t = tet_face_orient_tables(R);
   std::vector<float> tf(t.begin(), t.end());
@@ -249,26 +282,52 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
     for (int a = 0; a < 3; ++a) J[k][a] = d2f(__ldg(ji + 3 * k + a));
     th[k] = R.u[1] * J[k][0] + R.u[2] * J[k][1] + R.u[3] * J[k][2];
   }
+  // variables (0, 1) and (2, 3) in pairs on the packed FP32 FMA (__ffma2_rn),
+  // variable 4 alone
+  const TetPairTab<P>& K2 = tet_ptab<P>();
+  float2 c01[NP - 1], c23[NP - 1], a01[NP - 1], a23[NP - 1];
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    c01[j - 1] = make_float2(B.cd[0][j - 1], B.cd[1][j - 1]);
+    c23[j - 1] = make_float2(B.cd[2][j - 1], B.cd[3][j - 1]);
+    a01[j - 1] = make_float2(acc[j], acc[NP + j]);
+    a23[j - 1] = make_float2(acc[2 * NP + j], acc[3 * NP + j]);
+  }
 #pragma unroll 2
   for (int q = 0; q < D::NQV; ++q) {
-    float d[5];
+    float2 d01 = make_float2(B.lo[0], B.lo[1]), d23 = make_float2(B.lo[2], B.lo[3]);
+    float d4 = B.lo[4];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      float s = B.lo[m];
-#pragma unroll
-      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * B.cd[m][j - 1];
-      d[m] = s;
+    for (int j = 1; j < NP; ++j) {
+      d01 = __ffma2_rn(K2.phiV[q][j], c01[j - 1], d01);
+      d23 = __ffma2_rn(K2.phiV[q][j], c23[j - 1], d23);
+      d4 += K.phiV[q][j] * B.cd[4][j - 1];
     }
+    const float d[5] = {d01.x, d01.y, d23.x, d23.y, d4};
     PertState<3> S;
     S.init(R, d);
     float Fr[3][5];
 #pragma unroll
     for (int k = 0; k < 3; ++k) pert_flux<3>(R, S, d, J[k], th[k], Fr[k]);
+    float2 f01[3], f23[3];
 #pragma unroll
-    for (int m = 0; m < 5; ++m)
+    for (int k = 0; k < 3; ++k) {
+      f01[k] = make_float2(Fr[k][0], Fr[k][1]);
+      f23[k] = make_float2(Fr[k][2], Fr[k][3]);
+    }
 #pragma unroll
-      for (int j = 1; j < NP; ++j)
-        acc[m * NP + j] += K.vr[q][j] * Fr[0][m] + K.vs[q][j] * Fr[1][m] + K.vt[q][j] * Fr[2][m];
+    for (int j = 1; j < NP; ++j) {
+      a01[j - 1] = __ffma2_rn(K2.vt[q][j], f01[2], __ffma2_rn(K2.vs[q][j], f01[1], __ffma2_rn(K2.vr[q][j], f01[0], a01[j - 1])));
+      a23[j - 1] = __ffma2_rn(K2.vt[q][j], f23[2], __ffma2_rn(K2.vs[q][j], f23[1], __ffma2_rn(K2.vr[q][j], f23[0], a23[j - 1])));
+      acc[4 * NP + j] += K.vr[q][j] * Fr[0][4] + K.vs[q][j] * Fr[1][4] + K.vt[q][j] * Fr[2][4];
+    }
+  }
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    acc[j] = a01[j - 1].x;
+    acc[NP + j] = a01[j - 1].y;
+    acc[2 * NP + j] = a23[j - 1].x;
+    acc[3 * NP + j] = a23[j - 1].y;
   }
 }
 

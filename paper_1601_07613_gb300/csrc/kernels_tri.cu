@@ -1277,11 +1277,28 @@ template <int P>
 __device__ __forceinline__ float lambda_max_rec(const float (&r)[TriDim<P>::NF]) {
   using D = TriDim<P>;
   constexpr int NP = D::NP;
-  const TriTab<float, P>& K = tri_tab<float, P>();
   float lam = 0.0f;
+#if DGC_FFMA2
+  const TriPairTab<P>& K2 = tri_ptab<P>();
+#else
+  const TriTab<float, P>& K = tri_tab<float, P>();
+#endif
   DGC_UNROLL_Q
   for (int q = 0; q < D::NQV; ++q) {
     float U[4];
+#if DGC_FFMA2
+    // variables in pairs: the record's modes are float4 over the variables
+    float2 s01 = make_float2(r[4], r[5]), s23 = make_float2(r[6], r[7]);
+#pragma unroll
+    for (int j = 1; j < NP; ++j) {
+      s01 = __ffma2_rn(K2.phiV[q][j], make_float2(r[4 * (j + 1)], r[4 * (j + 1) + 1]), s01);
+      s23 = __ffma2_rn(K2.phiV[q][j], make_float2(r[4 * (j + 1) + 2], r[4 * (j + 1) + 3]), s23);
+    }
+    U[0] = r[0] + s01.x;
+    U[1] = r[1] + s01.y;
+    U[2] = r[2] + s23.x;
+    U[3] = r[3] + s23.y;
+#else
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       float s = r[4 + m];
@@ -1289,6 +1306,7 @@ __device__ __forceinline__ float lambda_max_rec(const float (&r)[TriDim<P>::NF])
       for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[4 * (j + 1) + m];
       U[m] = r[m] + s;
     }
+#endif
     const float ir = rcp_fast(U[0]), u = U[1] * ir, w = U[2] * ir;
     const float q2 = u * u + w * w;
     const float pr = 0.4f * (U[3] - 0.5f * U[0] * q2);
