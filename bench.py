@@ -186,8 +186,8 @@ def kernel_source_hash() -> str:
 # over the launches of each class) from the launch list of this benchmark's own
 # command, profiles/launch_list_rk_fp32mixed_p3_1048352tri.md, taken with the
 # kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = "688ab6f78f76c4a7"
-TRAFFIC_BYTES = {"last": 1122699349, "first": 364705122, "color": 589416143, "cfl": 495481454}
+TRAFFIC_SOURCES = "e790ff49ffeaf436"
+TRAFFIC_BYTES = {"last": 1122772699, "first": 364660907, "color": 589470549, "cfl": 495515099}
 
 
 def replica_throughput(torch, ms: float, world: int, units_per_step: float, dev):
