@@ -97,7 +97,8 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, form: str, rec: int = 0) -> float:
+def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, form: str, rec: int = 0,
+                first_est: bool = False) -> float:
     """Algorithmic DRAM bytes of one launch (one call for the two-pass CFL) of a
     kernel class, averaged over the three RK stages; each element is touched once
     per color on a closed conforming mesh.  form: "fp64", or "mixed" / "kahan"
@@ -107,12 +108,17 @@ def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, form: str, rec
     stage 1 also reads rec0 and the increment (3 rec + 12 NV); stage 2 reads the
     record, rhs, increment and the state, writes the state (rec + 24 NV): on
     average (6 rec + 44 NV) / 3.  (The Kahan pair state of a triangle has the FP64
-    state's size.)"""
+    state's size.)  first_est: the mixed triangle step whose first color of stage
+    0 reads the FP64 state and writes the record of u0 and the CFL estimates (the
+    work of CFL pass 1); the CFL class is then pass 2 alone, which reads the
+    estimates."""
     f32 = form != "fp64"
     s_in = rec if f32 else 8 * NV      # state read for traces
     s_rhs = (4 if f32 else 8) * NV     # rhs element block
     edge = 16 + 16 * (2 if dim == 2 else 3)
     if cls == "first":
+        if first_est:
+            s_in = ((8 * NV + rec + 4) + 2 * rec) / 3
         return E * (s_in + 8 * dim * dim + s_rhs) + nedges * edge
     if cls == "color":
         return E * (s_in + 2 * s_rhs) + nedges * edge
@@ -120,6 +126,8 @@ def class_bytes(cls: str, E: int, nedges: int, NV: int, dim: int, form: str, rec
         per = (6 * rec + 44 * NV) / 3 if f32 else 8 * NV * (3 + 2.0 / 3.0)
         return E * per + nedges * edge
     if cls == "cfl":
+        if first_est:
+            return 4.0 * E
         return E * ((rec + 12) if form == "kahan" else (8 * NV + 12 + (rec if f32 else 0)))
     if cls == "volume":
         return E * (s_in + 8 * dim * dim + s_rhs)
@@ -253,7 +261,8 @@ def run_dgc(args, rank, world, local_rank):
     ncolors = info["ncolors"]
     per_color = prep["edges_per_color"]
     kernels = {}
-    kernels_per_call = {"cfl": 2}
+    # the mixed step's first color of stage 0 does CFL pass 1; the CFL class is pass 2
+    kernels_per_call = {"cfl": 1}
     for cls, (tms, nl) in prof.items():
         n = nl // kernels_per_call.get(cls, 1)
         if cls == "first":
@@ -264,7 +273,7 @@ def run_dgc(args, rank, world, local_rank):
             ne_ = sum(per_color[1:-1]) / max(1, ncolors - 2)
         else:
             ne_ = 0
-        b = class_bytes(cls, E, ne_, NV, 2, "mixed", rec=4 * info["M"] * (info["np"] + 1))
+        b = class_bytes(cls, E, ne_, NV, 2, "mixed", rec=4 * info["M"] * (info["np"] + 1), first_est=True)
         avg = tms / n
         kernels[cls] = {"launches": nl, "calls": n, "avg_ms": round(avg, 5), "share": round(tms / (ms_prof * args.steps), 4),
                         "alg_bytes": int(b), "alg_gbs": round(b / (avg * 1e-3) / 1e9, 1),

@@ -448,8 +448,12 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
   const int nf = (int)record_floats(m), kf = kahan ? (int)kahan_floats(m) : 0;
   const float* rec0 = kahan ? ks : w.rec0;
   const int rec0_stride = kahan ? kf : nf;
+  // mixed form on triangles with the fusions: the first color of stage 0 reads
+  // the FP64 state and does pass 1 of the CFL reduction (the record of u0 and
+  // the estimates); pass 2 runs between it and the next color
+  const bool first_est = fused && !kahan && m.dim == 2 && !m.quad;
   if (kahan) launch(DGC_K_CFL, [&] { return tri_cfl_kahan(x, ks, cfl_, dt); });
-  else launch(DGC_K_CFL, [&] { return cfl(x, static_cast<double*>(c), cfl_, dt, w.rec0); });
+  else if (!first_est) launch(DGC_K_CFL, [&] { return cfl(x, static_cast<double*>(c), cfl_, dt, w.rec0); });
   for (int s = 0; s < 3; ++s) {
     const float* in = s == 0 ? rec0 : w.recs;
     const int ss = s == 0 ? rec0_stride : nf;
@@ -464,7 +468,15 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
     sa.delta = w.delta;
     sa.kstate = ks;
     if (fused) {
-      launch(DGC_K_FIRST, [&] { return surf(x, TY_MF, SURF_FIRST, off[0], off[1], in, ss, w.rhs, nullptr, nullptr); });
+      if (s == 0 && first_est) {
+        launch(DGC_K_FIRST, [&] {
+          return tri_first_est(x, off[0], off[1], static_cast<const double*>(c), w.rec0, static_cast<float*>(w.rhs));
+        });
+        launch(DGC_K_CFL, [&] { return tri_cfl_pass2(x, static_cast<const double*>(c), cfl_, dt); });
+      } else {
+        launch(DGC_K_FIRST,
+               [&] { return surf(x, TY_MF, SURF_FIRST, off[0], off[1], in, ss, w.rhs, nullptr, nullptr); });
+      }
       for (int k = 2; k < C; ++k)
         launch(DGC_K_COLOR, [&] { return surf(x, TY_MF, SURF_RMW, off[k - 1], off[k], in, ss, w.rhs, nullptr, nullptr); });
       launch(DGC_K_LAST, [&] { return surf(x, TY_MF, SURF_LAST, off[C - 1], off[C], in, ss, w.rhs, nullptr, &sa); });

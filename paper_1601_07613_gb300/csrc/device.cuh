@@ -142,6 +142,10 @@ int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* r
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
+// stage 0 of the mixed step on perfectly colored meshes: the first color also
+// writes the record of u0 and the CFL estimates (pass 1); pass 2 alone
+int tri_first_est(const Ctx& c, int64_t begin, int64_t end, const double* state, float* rec0, float* rhs);
+int tri_cfl_pass2(const Ctx& c, const double* state, double cfl, double* dt);
 int tri_kahan_floats(int p);
 int tri_cfl_kahan(const Ctx& c, const float* kstate, double cfl, double* dt);
 

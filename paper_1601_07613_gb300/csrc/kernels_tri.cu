@@ -338,9 +338,12 @@ __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], c
 #ifndef DGC_FFMA2
 #define DGC_FFMA2 1
 #endif
-template <int P>
+// LAM: also max_q (|u| + c) of the state at the volume points (the CFL estimate
+// of lambda_max_rec, from the same sums), into *lam.
+template <int P, bool LAM = false>
 __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRef<2>& R,
-                                             const double* __restrict__ ji, float (&acc)[TriDim<P>::NV]) {
+                                             const double* __restrict__ ji, float (&acc)[TriDim<P>::NV],
+                                             float* lam = nullptr) {
   using D = TriDim<P>;
   constexpr int NP = D::NP;
   const TriTab<float, P>& K = tri_tab<float, P>();
@@ -368,6 +371,13 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
       d23 = __ffma2_rn(K2.phiV[q][j], c23[j - 1], d23);
     }
     const float d[4] = {d01.x, d01.y, d23.x, d23.y};
+    if constexpr (LAM) {
+      const float U0 = R.u[0] + d[0], U1 = R.u[1] + d[1], U2 = R.u[2] + d[2], U3 = R.u[3] + d[3];
+      const float ir = rcp_fast(U0), u = U1 * ir, w = U2 * ir;
+      const float q2 = u * u + w * w;
+      const float pr = 0.4f * (U3 - 0.5f * U0 * q2);
+      *lam = fmaxf(*lam, sqrt_fast(q2) + sqrt_fast(1.4f * pr * ir));
+    }
     PertState<2> S;
     S.init(R, d);
     float Fr[4], Fs[4];
@@ -473,6 +483,12 @@ struct SurfParams {
   StageArgs sa;
   int ntab;     // edge tables to stage (3, or 9 on meshes with hanging edges)
   int sstride;  // floats per element of an FP32 state (record or Kahan state)
+  // first color of stage 0 of the mixed step (tri_first_est): the record of u0
+  // it writes, the elements' FP32 CFL estimates, their minimum, the inradii
+  float* rec_first = nullptr;
+  float* est = nullptr;
+  unsigned* estmin = nullptr;
+  const double* inr = nullptr;
 };
 
 // the contribution of one lane's element is in acc; write it as the mode asks
@@ -832,9 +848,14 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
   }
 }
 
+// MODE == SURF_FIRST with STG == 0 (FP64 state, FP32 rhs): the first color of
+// stage 0 of the mixed step, which also writes its element's record of u0 and
+// FP32 CFL estimate (both as pass 1 of the CFL reduction would) into A.rec_first
+// and A.est, and returns the estimate in *best (FLT_MAX for lanes that write
+// nothing).
 template <int P, typename ST, typename RT, int MODE, int STG = -1>
 __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
-                                          const float* se, float* rslot = nullptr) {
+                                          const float* se, float* rslot = nullptr, float* best = nullptr) {
   using D = TriDim<P>;
   using T = ETab32<P>;
   constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV, K1 = P + 1;
@@ -924,7 +945,25 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
     float acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
-    volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
+    if constexpr (STG == 0 && sizeof(ST) == 8) {
+      static_assert(sizeof(RT) == 4, "the stage-0 first color writes the FP32 rhs of the step");
+      float lam = 0.0f;
+      volume_acc32<P, true>(B, R, A.jinv + 4 * elem, acc, &lam);
+      if (writer) {
+        // the record of u0 (mode-major), as the CFL pass 1 writes it
+        float4* r = reinterpret_cast<float4*>(A.rec_first + elem * D::NF);
+        r[0] = make_float4(B.hi[0], B.hi[1], B.hi[2], B.hi[3]);
+        r[1] = make_float4(B.lo[0], B.lo[1], B.lo[2], B.lo[3]);
+#pragma unroll
+        for (int j = 1; j < NP; ++j) r[j + 1] = make_float4(B.cd[0][j - 1], B.cd[1][j - 1], B.cd[2][j - 1], B.cd[3][j - 1]);
+        float dd = d2f(__ldg(A.inr + elem)) / ((2 * P + 1) * lam);
+        if (!(dd > 0.0f) || !(dd < FLT_MAX)) dd = 0.0f;  // non-physical: always re-evaluated
+        A.est[elem] = dd;
+        *best = dd;
+      }
+    } else {
+      volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
+    }
     FaceConst<2> E;
     E.init(R, hi, {d2f(g0.x), d2f(g0.y)}, side);
     const float escale = right ? d2f(g1.y) : -d2f(g1.x);  // the lane's signed edge measure
@@ -1122,7 +1161,13 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
     float* rslot = nullptr;
     if constexpr (MODE == SURF_LAST && STG == 0 && sizeof(ST) == 4)
       rslot = reinterpret_cast<float*>(rslots) + threadIdx.x * rec_slot<P>();
-    surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se, rslot);
+    if constexpr (MODE == SURF_FIRST && STG == 0) {
+      float best = FLT_MAX;
+      surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se, rslot, &best);
+      block_min_to(best, A.estmin);
+    } else {
+      surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se, rslot);
+    }
   } else {
     __shared__ double sphi[9 * D::NQE * D::NP];
     __shared__ double sw[D::NQE];
@@ -1749,6 +1794,52 @@ int tri_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t 
     case 1: return surf_p<1>(x, ty, mode, A);
     case 2: return surf_p<2>(x, ty, mode, A);
     case 3: return surf_p<3>(x, ty, mode, A);
+    default: return -1;
+  }
+}
+
+// Stage 0 of the mixed step on a mesh where every element has one edge of each
+// color: the first color (edges [begin, end)) reads the FP64 state c and, with
+// the volume integral and its edge, writes each element's record of u0 (rec0)
+// and FP32 CFL estimate, the work of pass 1 of the CFL reduction (the estimate
+// comes from the volume integral's own point values).  tri_cfl_pass2 then
+// finishes dt before the next color.
+int tri_first_est(const Ctx& x, int64_t begin, int64_t end, const double* c, float* rec0, float* rhs) {
+  unsigned* mn = reinterpret_cast<unsigned*>(x.d->cfl_est + x.ne);
+  if (cudaMemsetAsync(mn, 0x7F, sizeof(unsigned), x.st) != cudaSuccess) return -1;
+  SurfParams A;
+  A.begin = begin;
+  A.end = end;
+  A.sstride = 0;
+  A.topo = x.d->topo;
+  A.fgeo = x.d->fgeo;
+  A.jinv = x.d->jinv;
+  A.state = c;
+  A.rhs = rhs;
+  A.buf = nullptr;
+  A.ntab = x.d->edge_tables;
+  A.rec_first = rec0;
+  A.est = x.d->cfl_est;
+  A.estmin = mn;
+  A.inr = x.d->inr;
+  switch (x.p) {
+    case 1: return surf_launch<1, float, double, float, SURF_FIRST, 0>(x, A);
+    case 2: return surf_launch<2, float, double, float, SURF_FIRST, 0>(x, A);
+    case 3: return surf_launch<3, float, double, float, SURF_FIRST, 0>(x, A);
+    default: return -1;
+  }
+}
+
+int tri_cfl_pass2(const Ctx& x, const double* s, double cfl, double* dt) {
+  const int bs = 128;
+  const unsigned grid = (unsigned)((x.ne + bs - 1) / bs);
+  auto* bits = reinterpret_cast<unsigned long long*>(dt);
+  const float* est = x.d->cfl_est;
+  const unsigned* mn = reinterpret_cast<const unsigned*>(x.d->cfl_est + x.ne);
+  switch (x.p) {
+    case 1: launch_k(x, k_cfl2_tri<1, false>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits); return 1;
+    case 2: launch_k(x, k_cfl2_tri<2, false>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits); return 1;
+    case 3: launch_k(x, k_cfl2_tri<3, false>, grid, bs, 0, s, x.d->inr, x.ne, cfl, est, mn, bits); return 1;
     default: return -1;
   }
 }
