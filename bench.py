@@ -280,9 +280,18 @@ def run_dgc(args, rank, world, local_rank):
                         "frac_hbm": round(b / (avg * 1e-3) / 1e9 / hbm, 3)}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["calls"])
     step_bytes = sum(kernels[k]["alg_bytes"] * kernels[k]["calls"] for k in kernels) / args.steps
-    traffic = TRAFFIC_BYTES.get(dom) if TRAFFIC_SOURCES == kernel_source_hash() and args.n == 724 else None
+    measured = TRAFFIC_SOURCES == kernel_source_hash() and args.n == 724
+    traffic = TRAFFIC_BYTES.get(dom) if measured else None
+    if measured:
+        # the same kernels by the DRAM bytes ncu measured per launch (launch list in profiles/)
+        for k, kv in kernels.items():
+            if k in TRAFFIC_BYTES:
+                g = TRAFFIC_BYTES[k] / (kv["avg_ms"] * 1e-3) / 1e9
+                kv["dram_gbs"] = round(g, 1)
+                kv["dram_frac_hbm"] = round(g / hbm, 3)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["alg_gbs"], "peak": hbm,
                 "unit": "GB/s", "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
+                "dram_frac": kernels[dom].get("dram_frac_hbm"),
                 "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
                 "profiled_ms_per_step": round(ms_prof, 5),
                 "step_alg_gbs": round(step_bytes / (ms * 1e-3) / 1e9, 1),
