@@ -229,3 +229,24 @@ def test_full_size_quad_steps_conserve(full):
         t0 = (detj[:, None] * c[:, :, 0]).sum(0)
         t1 = (detj[:, None] * got[:, :, 0]).sum(0)
         np.testing.assert_allclose(t1, t0, rtol=rtol, atol=1e-13 * np.abs(t0).max())
+
+
+def test_quad_static_step_equals_regular(torch_dev, oracle_mod):
+    """The allocation-free step (its workspace in the library's static device
+    array) runs the same launches: bit-identical states."""
+    torch, dev = torch_dev
+    mi = _mesh("periodic", 8)
+    out = []
+    for static in (False, True):
+        run = Q(torch_dev, oracle_mod, mi, 2)
+        run.load(run.vortex())
+        d = torch.zeros(1, dtype=torch.float64, device=dev)
+        if static:
+            for _ in range(2):
+                dgc.dgc_rk_step_static(run.m.h, dgc.DGC_FP32_MIXED, run.c, 0.3, d)
+            torch.cuda.synchronize()
+            out.append(dgc.dgc_export_state(run.m.h, run.c))
+        else:
+            out.append(run.rk(dgc.DGC_FP32_MIXED, 0.3, steps=2)[0])
+        run.close()
+    assert np.array_equal(out[0], out[1])
