@@ -232,13 +232,17 @@ const Mesh& checked(const dgc_mesh* mesh) {
   return *reinterpret_cast<const Mesh*>(mesh);
 }
 
-Ctx ready(Mesh& m, void* stream) {
+// The checks every device call on a mesh makes first.
+void require_device_ready(const Mesh& m) {
   require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
   require(!m.nonaffine,
           "the kernels take parallelogram quadrilaterals only; this mesh (general quadrilaterals or hybrid) is "
           "colored only",
           DGC_ERR_UNSUPPORTED);
-  upload(m);
+}
+
+// The kernels' view of an uploaded mesh (d: its device arrays).
+Ctx make_ctx(const Mesh& m, const DeviceMesh* d, void* stream) {
   Ctx x;
   x.dim = m.dim;
   x.quad = m.quad;
@@ -249,7 +253,7 @@ Ctx ready(Mesh& m, void* stream) {
   x.ne = m.ne;
   x.ns = m.ns;
   x.epb = m.edges_per_block;
-  x.d = m.dev;
+  x.d = d;
   x.shadow.M = m.M;
   x.shadow.np = m.np;
   x.shadow.nv = m.M * m.np;
@@ -259,6 +263,12 @@ Ctx ready(Mesh& m, void* stream) {
   x.shadow.phi0 = m.tab.phiV[0];
   x.st = static_cast<cudaStream_t>(stream);
   return x;
+}
+
+Ctx ready(Mesh& m, void* stream) {
+  require_device_ready(m);
+  upload(m);
+  return make_ctx(m, m.dev, stream);
 }
 
 void check_ptr(const void* p, const char* what) {
@@ -1103,7 +1113,7 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     check_ptr(c_dev, "c_dev");
     require(dt_dev != nullptr && reinterpret_cast<uintptr_t>(dt_dev) % 8 == 0, "dt_dev must be an aligned device double");
     require(cfl_ > 0.0, "cfl must be positive");
-    require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
+    require_device_ready(m);
     const int64_t ws = workspace_bytes(m, prec);
     if (ws > kStaticScratchBytes)
       throw Error{DGC_ERR_ARG, "mesh too large for dgc_rk_step_static: needs " + std::to_string(ws) +
@@ -1117,24 +1127,7 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     const Workspace w = carve(m, prec, base);
     DeviceMesh dcopy = *m.dev;  // the same mesh arrays, CFL estimates in the static array
     dcopy.cfl_est = w.est;
-    Ctx x;
-    x.dim = m.dim;
-    x.p = m.p;
-    x.np = m.np;
-    x.M = m.M;
-    x.nfpe = m.nfpe;
-    x.ne = m.ne;
-    x.ns = m.ns;
-    x.epb = m.edges_per_block;
-    x.d = &dcopy;
-    x.st = static_cast<cudaStream_t>(stream);
-    x.shadow.M = m.M;
-    x.shadow.np = m.np;
-    x.shadow.nv = m.M * m.np;
-    x.shadow.rec = (int)record_floats(m);
-    x.shadow.split = true;
-    x.shadow.mode_major = m.dim == 2;
-    x.shadow.phi0 = m.tab.phiV[0];
+    Ctx x = make_ctx(m, &dcopy, stream);
     int64_t n = 0;
     DGC_CUDA(cudaMemsetAsync(dt_dev, 0x7F, sizeof(double), x.st));
     x.pdl = m.pdl;
