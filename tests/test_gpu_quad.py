@@ -250,3 +250,17 @@ def test_quad_static_step_equals_regular(torch_dev, oracle_mod):
             out.append(run.rk(dgc.DGC_FP32_MIXED, 0.3, steps=2)[0])
         run.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_quad_cfl_dt_matches_oracle(torch_dev, oracle_mod, p):
+    torch, dev = torch_dev
+    run = Q(torch_dev, oracle_mod, _mesh("open"), p)
+    c = run.vortex()
+    run.load(c)
+    d = torch.zeros(1, dtype=torch.float64, device=dev)
+    dgc.dgc_cfl_dt(run.m.h, run.c, 0.3, d)
+    torch.cuda.synchronize()
+    ref = run.om.dt(p, c, 0.3)
+    assert abs(float(d.item()) - ref) < 1e-13 * ref
+    run.close()
