@@ -364,6 +364,7 @@ def run_dgc(args, rank, world, local_rank):
         variants.update(run_batched(dgc, torch, dev, stream, args))
         variants.update(run_other_meshes(dgc, torch, dev, stream, args))
         variants.update(run_table7(dgc, torch, dev, stream, args, cfg, c_host))
+        variants["table2_coloring"] = run_table2(dgc)
 
     # ---- end to end through the C ABI with pinned host buffers -----------------------------
     e2e = None
@@ -575,6 +576,25 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
         del c, r
         m.close()
     return out
+
+
+def run_table2(dgc) -> list:
+    """Table 2's kind of statistics on this library (host only): quadrilateral meshes
+    of the rectangle-domain family at growing size (each about 4x the last, as
+    meshes A-E) and hybrid triangle/quadrilateral meshes; edges per color, the
+    greedy pass and conflict resolution with the reordering, in seconds."""
+    rows = []
+    for kind, n in (("quad", 32), ("quad", 64), ("quad", 128), ("quad", 256), ("quad", 512),
+                    ("hybrid", 40), ("hybrid", 160)):
+        mi = (W.open_square_quad(n, "vertex", jitter=0.2, seed=n) if kind == "quad"
+              else W.hybrid_square(n, 0.3, periodic=False, jitter=0.2, seed=n))
+        m = dgc.Mesh.from_input(mi, 1)
+        t0 = time.perf_counter()
+        nc, per = m.color(1601)
+        rows.append({"mesh": kind, "elements": m.info["ne"], "sides": m.info["ns"], "colors": nc,
+                     "per_color": per, "coloring_s": round(time.perf_counter() - t0, 4)})
+        m.close()
+    return rows
 
 
 def run_table7(dgc, torch, dev, stream, args, cfg, c_base):
