@@ -364,7 +364,7 @@ def run_dgc(args, rank, world, local_rank):
         variants.update(run_batched(dgc, torch, dev, stream, args))
         variants.update(run_other_meshes(dgc, torch, dev, stream, args))
         variants.update(run_table7(dgc, torch, dev, stream, args, cfg, c_host))
-        variants["table2_coloring"] = run_table2(dgc)
+        variants["coloring_tables"] = run_coloring_tables(dgc)
 
     # ---- end to end through the C ABI with pinned host buffers -----------------------------
     e2e = None
@@ -578,16 +578,20 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     return out
 
 
-def run_table2(dgc) -> list:
-    """Table 2's kind of statistics on this library (host only): quadrilateral meshes
-    of the rectangle-domain family at growing size (each about 4x the last, as
-    meshes A-E) and hybrid triangle/quadrilateral meshes; edges per color, the
-    greedy pass and conflict resolution with the reordering, in seconds."""
+def run_coloring_tables(dgc) -> list:
+    """Tables 1-3's kind of statistics on this library (host only): triangle,
+    quadrilateral and tetrahedral meshes of growing size (each about 4x the last,
+    as the rectangle meshes A-E; tetrahedra 8x) and hybrid triangle/quadrilateral
+    meshes; edges (faces) per color, the greedy pass and conflict resolution with
+    the reordering, in seconds."""
     rows = []
-    for kind, n in (("quad", 32), ("quad", 64), ("quad", 128), ("quad", 256), ("quad", 512),
-                    ("hybrid", 40), ("hybrid", 160)):
-        mi = (W.open_square_quad(n, "vertex", jitter=0.2, seed=n) if kind == "quad"
-              else W.hybrid_square(n, 0.3, periodic=False, jitter=0.2, seed=n))
+    for kind, n in (("tri", 64), ("tri", 128), ("tri", 256), ("tri", 512),
+                    ("quad", 32), ("quad", 64), ("quad", 128), ("quad", 256), ("quad", 512),
+                    ("hybrid", 40), ("hybrid", 160), ("tet", 8), ("tet", 16), ("tet", 32)):
+        mi = {"tri": lambda: W.open_square_tri(n, jitter=0.2, seed=n),
+              "quad": lambda: W.open_square_quad(n, "vertex", jitter=0.2, seed=n),
+              "hybrid": lambda: W.hybrid_square(n, 0.3, periodic=False, jitter=0.2, seed=n),
+              "tet": lambda: W.periodic_cube_tet(n)}[kind]()
         m = dgc.Mesh.from_input(mi, 1)
         t0 = time.perf_counter()
         nc, per = m.color(1601)
