@@ -25,16 +25,41 @@
  *     C = {1, 2, 3, 4} (Sec. 3.1, Table 2), and Eq. 2 on parallelogram
  *     quadrilaterals.
  *
+ * The same file builds three ways (oracle/__init__.py): FP64 (the tests'
+ * oracle), long double (the extended build: the same steps with a wider
+ * significand, the reference an FP64 evaluation's rounding is measured
+ * against), and FP64 with OpenMP over the elements of a right-hand side (the
+ * CPU baseline; every element's arithmetic is unchanged).
+ *
  * The paper leaves the DG ingredients to its reference [giuliani]; the readings
  * used here (orthonormal Dubiner basis, Gauss rules, local Lax-Friedrichs flux,
  * the CFL rule, SSP-RK3, the RNG and tie-break protocol of the coloring) are
  * stated beside each function.  Parity pins for each function live in tests/.
  */
-#include <math.h>
+#include <float.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Arithmetic type.  The default build computes in FP64; the extended build
+ * (-DORC_REAL="long double": the x87 80-bit format on x86-64, IEEE binary128 on
+ * aarch64) evaluates the same steps with a wider significand, as a reference
+ * for how close an FP64 evaluation of Eq. 2 comes to the exact result of the
+ * same inputs.  <tgmath.h> makes sqrt, fabs, pow, fmax and round follow the
+ * argument type. */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
+
+/* size of the arithmetic type and its significand bits (53 for FP64) */
+int orc_real_bytes(void) { return (int)sizeof(real); }
+int orc_real_mant_dig(void) { return sizeof(real) == sizeof(double) ? DBL_MANT_DIG : LDBL_MANT_DIG; }
 
 #define ORC_MAXP 8
 #define ORC_MAXNP 165 /* (p+1)(p+2)(p+3)/6 at p = 8 */
@@ -53,8 +78,8 @@ static int fail(const char *msg) {
 
 /* Jacobi polynomial P_n^{(a,0)}(x) and its derivative, by the classical
  * three-term recurrence in n (beta = 0). */
-static void jacobi_a0(int n, double a, double x, double *P, double *dP) {
-  double p0 = 1.0, p1, d0 = 0.0, d1;
+static void jacobi_a0(int n, real a, real x, real *P, real *dP) {
+  real p0 = 1.0, p1, d0 = 0.0, d1;
   if (n == 0) {
     *P = 1.0;
     *dP = 0.0;
@@ -63,12 +88,12 @@ static void jacobi_a0(int n, double a, double x, double *P, double *dP) {
   p1 = 0.5 * ((a + 2.0) * x + a);
   d1 = 0.5 * (a + 2.0);
   for (int k = 2; k <= n; ++k) {
-    double c = 2.0 * k + a; /* 2k + a + b with b = 0 */
-    double A = 2.0 * k * (k + a) * (c - 2.0);
-    double B = (c - 1.0) * (c * (c - 2.0) * x + a * a);
-    double C = 2.0 * (k + a - 1.0) * (k - 1.0) * c;
-    double p2 = (B * p1 - C * p0) / A;
-    double d2 = ((c - 1.0) * c * (c - 2.0) * p1 + B * d1 - C * d0) / A;
+    real c = 2.0 * k + a; /* 2k + a + b with b = 0 */
+    real A = 2.0 * k * (k + a) * (c - 2.0);
+    real B = (c - 1.0) * (c * (c - 2.0) * x + a * a);
+    real C = 2.0 * (k + a - 1.0) * (k - 1.0) * c;
+    real p2 = (B * p1 - C * p0) / A;
+    real d2 = ((c - 1.0) * c * (c - 2.0) * p1 + B * d1 - C * d0) / A;
     p0 = p1;
     p1 = p2;
     d0 = d1;
@@ -83,26 +108,31 @@ static void jacobi_a0(int n, double a, double x, double *P, double *dP) {
  * polished by Newton; weights from the classical formula
  *   w_i = 2^(a+1) * G(n+a+1) G(n+1) / (G(n+a+1) n!) / ((1-x_i^2) P_n'(x_i)^2)
  * which for integer a in {0,1,2} reduces to 2^(a+1) / ((1-x^2) P'^2). */
-int orc_gauss_jacobi(int n, double a, double *x, double *w) {
+/* the root search stops when a step is below 1e-17 in FP64 and below the
+ * same multiple of the unit roundoff in a wider type */
+#define ORC_ROOT_TOL \
+  ((real)1e-17 * (sizeof(real) == sizeof(double) ? (real)1 : (real)(LDBL_EPSILON / DBL_EPSILON)))
+
+int orc_gauss_jacobi(int n, real a, real *x, real *w) {
   if (n < 1 || n > 64) return fail("gauss_jacobi: n out of range");
   int found = 0;
   const int grid = 200000;
-  double xa = -1.0, Pa, dPa;
+  real xa = -1.0, Pa, dPa;
   jacobi_a0(n, a, xa, &Pa, &dPa);
   for (int g = 1; g <= grid && found < n; ++g) {
-    double xb = -1.0 + 2.0 * g / grid, Pb, dPb;
+    real xb = -1.0 + 2.0 * g / grid, Pb, dPb;
     jacobi_a0(n, a, xb, &Pb, &dPb);
     if (Pa == 0.0) {
       x[found++] = xa;
     } else if (Pa * Pb < 0.0) {
-      double lo = xa, hi = xb, r = 0.5 * (xa + xb);
+      real lo = xa, hi = xb, r = 0.5 * (xa + xb);
       for (int it = 0; it < 200; ++it) { /* safeguarded Newton */
-        double P, dP;
+        real P, dP;
         jacobi_a0(n, a, r, &P, &dP);
         if ((P < 0.0) == (Pa < 0.0)) lo = r; else hi = r;
-        double rn = r - P / dP;
+        real rn = r - P / dP;
         if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
-        if (fabs(rn - r) < 1e-17) { r = rn; break; }
+        if (fabs(rn - r) < ORC_ROOT_TOL) { r = rn; break; }
         r = rn;
       }
       x[found++] = r;
@@ -112,14 +142,14 @@ int orc_gauss_jacobi(int n, double a, double *x, double *w) {
   }
   if (found != n) return fail("gauss_jacobi: root count mismatch");
   for (int i = 0; i < n; ++i) {
-    double P, dP;
+    real P, dP;
     jacobi_a0(n, a, x[i], &P, &dP);
     w[i] = pow(2.0, a + 1.0) / ((1.0 - x[i] * x[i]) * dP * dP);
   }
   return 0;
 }
 
-int orc_gauss_legendre(int n, double *x, double *w) { return orc_gauss_jacobi(n, 0.0, x, w); }
+int orc_gauss_legendre(int n, real *x, real *w) { return orc_gauss_jacobi(n, 0.0, x, w); }
 
 /* ======================================================================= */
 /* Reference-element rules (collapsed "Duffy" products)                    */
@@ -129,8 +159,8 @@ int orc_gauss_legendre(int n, double *x, double *w) { return orc_gauss_jacobi(n,
  * Gauss-Jacobi(1,0) points in eta; r = (1+xi)(1-eta)/4, s = (1+eta)/2,
  * w = w_xi w_eta / 8.  Exact for total degree 2n-1.  Point index = i*n + k
  * (i over eta, k over xi). */
-int orc_tri_rule(int n, double *r, double *s, double *w) {
-  double xg[64], wg[64], xj[64], wj[64];
+int orc_tri_rule(int n, real *r, real *s, real *w) {
+  real xg[64], wg[64], xj[64], wj[64];
   if (orc_gauss_jacobi(n, 0.0, xg, wg) || orc_gauss_jacobi(n, 1.0, xj, wj)) return -1;
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
@@ -143,8 +173,8 @@ int orc_tri_rule(int n, double *r, double *s, double *w) {
 
 /* Tetrahedron {r,s,t >= 0, r+s+t <= 1}: Gauss-Legendre x Gauss-Jacobi(1,0) x
  * Gauss-Jacobi(2,0), n points each; exact for total degree 2n-1. */
-int orc_tet_rule(int n, double *r, double *s, double *t, double *w) {
-  double xa[64], wa[64], xb[64], wb[64], xc[64], wc[64];
+int orc_tet_rule(int n, real *r, real *s, real *t, real *w) {
+  real xa[64], wa[64], xb[64], wb[64], xc[64], wc[64];
   if (orc_gauss_jacobi(n, 0.0, xa, wa) || orc_gauss_jacobi(n, 1.0, xb, wb) ||
       orc_gauss_jacobi(n, 2.0, xc, wc))
     return -1;
@@ -152,7 +182,7 @@ int orc_tet_rule(int n, double *r, double *s, double *t, double *w) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
       for (int k = 0; k < n; ++k, ++q) {
-        double a = xa[k], b = xb[j], c = xc[i];
+        real a = xa[k], b = xb[j], c = xc[i];
         t[q] = 0.5 * (1.0 + c);
         s[q] = 0.25 * (1.0 + b) * (1.0 - c);
         r[q] = 0.125 * (1.0 + a) * (1.0 - b) * (1.0 - c);
@@ -179,8 +209,8 @@ static int npoly_tet(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
 /* Q_n, dQ/dr, dQ/ds for n = 0..p of the homogeneous Legendre recurrence in
  * the variable (2r - 1 + s) with "scale" (1 - s); used by both simplices. */
-static void hleg(int p, double u, double du_dr, double du_ds, double v, double dv_ds,
-                 double *Q, double *Qr, double *Qs) {
+static void hleg(int p, real u, real du_dr, real du_ds, real v, real dv_ds,
+                 real *Q, real *Qr, real *Qs) {
   /* Q_n = v^n P_n(u / v); recurrence (n+1)Q_{n+1} = (2n+1) u Q_n - n v^2 Q_{n-1} */
   Q[0] = 1.0;
   Qr[0] = 0.0;
@@ -198,17 +228,17 @@ static void hleg(int p, double u, double du_dr, double du_ds, double v, double d
   }
 }
 
-int orc_basis_tri(int p, double r, double s, double *phi, double *dr, double *ds) {
+int orc_basis_tri(int p, real r, real s, real *phi, real *dr, real *ds) {
   if (p < 0 || p > ORC_MAXP) return fail("basis_tri: p out of range");
-  double Q[ORC_MAXP + 1], Qr[ORC_MAXP + 1], Qs[ORC_MAXP + 1];
+  real Q[ORC_MAXP + 1], Qr[ORC_MAXP + 1], Qs[ORC_MAXP + 1];
   hleg(p, 2.0 * r - 1.0 + s, 2.0, 1.0, 1.0 - s, -1.0, Q, Qr, Qs);
   int j = 0;
   for (int d = 0; d <= p; ++d)
     for (int k = d; k >= 0; --k) {
       int l = d - k;
-      double J, dJ;
+      real J, dJ;
       jacobi_a0(l, 2.0 * k + 1.0, 2.0 * s - 1.0, &J, &dJ);
-      double N = sqrt(2.0 * (2 * k + 1) * (k + l + 1));
+      real N = sqrt((real)(2 * (2 * k + 1) * (k + l + 1)));
       phi[j] = N * Q[k] * J;
       if (dr) dr[j] = N * Qr[k] * J;
       if (ds) ds[j] = N * (Qs[k] * J + Q[k] * 2.0 * dJ);
@@ -224,8 +254,8 @@ int orc_basis_tri(int p, double r, double s, double *phi, double *dr, double *ds
  *          in collapsed coordinates; pinned numerically by orthonormality).
  * Ordering: d = 0..p, i = d..0, j = d-i..0, k = d-i-j. */
 /* homogeneous Jacobi H_n = v^n P_n^{(a,0)}(u/v) with partial derivatives */
-static void hjac(int p, double a, double u, double ur, double us, double ut, double v, double vs,
-                 double vt, double *H, double *Hr, double *Hs, double *Ht) {
+static void hjac(int p, real a, real u, real ur, real us, real ut, real v, real vs,
+                 real vt, real *H, real *Hr, real *Hs, real *Ht) {
   H[0] = 1.0;
   Hr[0] = Hs[0] = Ht[0] = 0.0;
   if (p >= 1) {
@@ -236,11 +266,11 @@ static void hjac(int p, double a, double u, double ur, double us, double ut, dou
     Ht[1] = 0.5 * ((a + 2.0) * ut + a * vt);
   }
   for (int n = 2; n <= p; ++n) {
-    double c = 2.0 * n + a;
-    double A = 2.0 * n * (n + a) * (c - 2.0);
-    double B1 = (c - 1.0) * c * (c - 2.0); /* multiplies x P_{n-1} -> u H_{n-1} */
-    double B0 = (c - 1.0) * a * a;         /* multiplies P_{n-1}   -> v H_{n-1} */
-    double C = 2.0 * (n + a - 1.0) * (n - 1.0) * c; /* multiplies P_{n-2} -> v^2 H_{n-2} */
+    real c = 2.0 * n + a;
+    real A = 2.0 * n * (n + a) * (c - 2.0);
+    real B1 = (c - 1.0) * c * (c - 2.0); /* multiplies x P_{n-1} -> u H_{n-1} */
+    real B0 = (c - 1.0) * a * a;         /* multiplies P_{n-1}   -> v H_{n-1} */
+    real C = 2.0 * (n + a - 1.0) * (n - 1.0) * c; /* multiplies P_{n-2} -> v^2 H_{n-2} */
     H[n] = (B1 * u * H[n - 1] + B0 * v * H[n - 1] - C * v * v * H[n - 2]) / A;
     Hr[n] = (B1 * (ur * H[n - 1] + u * Hr[n - 1]) + B0 * v * Hr[n - 1] - C * v * v * Hr[n - 2]) / A;
     Hs[n] = (B1 * (us * H[n - 1] + u * Hs[n - 1]) + B0 * (vs * H[n - 1] + v * Hs[n - 1]) -
@@ -250,24 +280,24 @@ static void hjac(int p, double a, double u, double ur, double us, double ut, dou
   }
 }
 
-int orc_basis_tet(int p, double r, double s, double t, double *phi, double *dr, double *ds,
-                  double *dt) {
+int orc_basis_tet(int p, real r, real s, real t, real *phi, real *dr, real *ds,
+                  real *dt) {
   if (p < 0 || p > ORC_MAXP) return fail("basis_tet: p out of range");
   /* Q_i: homogeneous Legendre in u = 2r - 1 + s + t, v = 1 - s - t */
-  double Q[ORC_MAXP + 1], Qr[ORC_MAXP + 1], Qs[ORC_MAXP + 1], Qt[ORC_MAXP + 1];
+  real Q[ORC_MAXP + 1], Qr[ORC_MAXP + 1], Qs[ORC_MAXP + 1], Qt[ORC_MAXP + 1];
   hjac(p, 0.0, 2.0 * r - 1.0 + s + t, 2.0, 1.0, 1.0, 1.0 - s - t, -1.0, -1.0, Q, Qr, Qs, Qt);
   int n = 0;
   for (int d = 0; d <= p; ++d)
     for (int i = d; i >= 0; --i) {
       /* R_ij: homogeneous Jacobi(2i+1,0) in u = 2s - 1 + t, v = 1 - t */
-      double R[ORC_MAXP + 1], Rr[ORC_MAXP + 1], Rs[ORC_MAXP + 1], Rt[ORC_MAXP + 1];
+      real R[ORC_MAXP + 1], Rr[ORC_MAXP + 1], Rs[ORC_MAXP + 1], Rt[ORC_MAXP + 1];
       hjac(d - i, 2.0 * i + 1.0, 2.0 * s - 1.0 + t, 0.0, 2.0, 1.0, 1.0 - t, 0.0, -1.0, R, Rr, Rs, Rt);
       for (int j = d - i; j >= 0; --j) {
         int k = d - i - j;
-        double J, dJ;
+        real J, dJ;
         jacobi_a0(k, 2.0 * i + 2.0 * j + 2.0, 2.0 * t - 1.0, &J, &dJ);
-        double N = sqrt(2.0 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3));
-        double a = Q[i] * R[j];
+        real N = sqrt((real)(2 * (2 * i + 1) * (i + j + 1) * (2 * i + 2 * j + 2 * k + 3)));
+        real a = Q[i] * R[j];
         phi[n] = N * a * J;
         if (dr) dr[n] = N * (Qr[i] * R[j]) * J;
         if (ds) ds[n] = N * (Qs[i] * R[j] + Q[i] * Rs[j]) * J;
@@ -285,8 +315,8 @@ int orc_basis_tet(int p, double r, double s, double t, double *phi, double *dr, 
  * so mode 0 is the constant.  P_n from Bonnet's recurrence
  * (n+1) P_{n+1}(t) = (2n+1) t P_n(t) - n P_{n-1}(t), derivatives from
  * P'_{n+1} = P'_{n-1} + (2n+1) P_n. */
-static void legendre01(int p, double x, double *l, double *dl) {
-  double t = 2.0 * x - 1.0, P[ORC_MAXP + 2], D[ORC_MAXP + 2];
+static void legendre01(int p, real x, real *l, real *dl) {
+  real t = 2.0 * x - 1.0, P[ORC_MAXP + 2], D[ORC_MAXP + 2];
   P[0] = 1.0;
   D[0] = 0.0;
   P[1] = t;
@@ -296,7 +326,7 @@ static void legendre01(int p, double x, double *l, double *dl) {
     D[n + 1] = D[n - 1] + (2 * n + 1) * P[n];
   }
   for (int n = 0; n <= p; ++n) {
-    double c = sqrt(2.0 * n + 1.0);
+    real c = sqrt((real)(2 * n + 1));
     l[n] = c * P[n];
     if (dl) dl[n] = 2.0 * c * D[n]; /* dt/dx = 2 */
   }
@@ -304,9 +334,9 @@ static void legendre01(int p, double x, double *l, double *dl) {
 
 static int npoly_quad(int p) { return (p + 1) * (p + 1); }
 
-int orc_basis_quad(int p, double r, double s, double *phi, double *dr, double *ds) {
+int orc_basis_quad(int p, real r, real s, real *phi, real *dr, real *ds) {
   if (p < 0 || p > ORC_MAXP) return fail("basis_quad: p out of range");
-  double lr[ORC_MAXP + 2], dlr[ORC_MAXP + 2], ls[ORC_MAXP + 2], dls[ORC_MAXP + 2];
+  real lr[ORC_MAXP + 2], dlr[ORC_MAXP + 2], ls[ORC_MAXP + 2], dls[ORC_MAXP + 2];
   legendre01(p, r, lr, dlr);
   legendre01(p, s, ls, dls);
   for (int a = 0; a <= p; ++a)
@@ -321,8 +351,8 @@ int orc_basis_quad(int p, double r, double s, double *phi, double *dr, double *d
 
 /* Square [0,1]^2: n x n Gauss-Legendre points, point i n + k at
  * (x_i, x_k); weights sum to 1. */
-int orc_quad_rule(int n, double *r, double *s, double *w) {
-  double x[64], wg[64];
+int orc_quad_rule(int n, real *r, real *s, real *w) {
+  real x[64], wg[64];
   if (n < 1 || n > 64) return fail("quad_rule: n out of range");
   if (orc_gauss_legendre(n, x, wg)) return -1;
   for (int i = 0; i < n; ++i)
@@ -356,17 +386,17 @@ typedef struct {
   int quad;
   int64_t nonaffine;
   int64_t nv, ne, ns;
-  double L[3];
+  real L[3];
   int periodic;
-  double *X;      /* ne * nvpe * dim unwrapped vertex coordinates */
+  real *X;      /* ne * nvpe * dim unwrapped vertex coordinates */
   int32_t *ev;    /* ne * nvpe */
   int32_t *sl, *sr;
   int8_t *sql, *sqr;
   int32_t *es;    /* ne * nfpe: side of each local face */
   int32_t *enb;   /* ne * nfpe: neighbour element (-1 on boundary) */
   /* geometry, FP64 */
-  double *detJ;   /* ne */
-  double *Jinv;   /* ne * dim * dim, row k = grad of reference coordinate k */
+  real *detJ;   /* ne */
+  real *Jinv;   /* ne * dim * dim, row k = grad of reference coordinate k */
   /* nonconforming meshes only (orc_refine), NULL otherwise */
   int32_t *es2;   /* ne * nfpe: second side on a split edge of a coarse element, -1 if none */
   int8_t *shalf;  /* per side: half of the right element's edge a hanging side covers, or -1 */
@@ -426,19 +456,19 @@ static void sort3(int32_t *k, int n) {
       }
 }
 
-static double det_and_inv(int dim, const double *J, double *Ji) {
+static real det_and_inv(int dim, const real *J, real *Ji) {
   /* J column-major by reference direction: J[a*dim + k] = d x_a / d r_k */
   if (dim == 2) {
-    double a = J[0], b = J[1], c = J[2], d = J[3]; /* [[a b],[c d]] */
-    double det = a * d - b * c;
+    real a = J[0], b = J[1], c = J[2], d = J[3]; /* [[a b],[c d]] */
+    real det = a * d - b * c;
     Ji[0] = d / det;
     Ji[1] = -b / det;
     Ji[2] = -c / det;
     Ji[3] = a / det;
     return det;
   }
-  double a = J[0], b = J[1], c = J[2], d = J[3], e = J[4], f = J[5], g = J[6], h = J[7], i = J[8];
-  double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+  real a = J[0], b = J[1], c = J[2], d = J[3], e = J[4], f = J[5], g = J[6], h = J[7], i = J[8];
+  real det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
   Ji[0] = (e * i - f * h) / det;
   Ji[1] = (c * h - b * i) / det;
   Ji[2] = (b * f - c * e) / det;
@@ -461,20 +491,20 @@ void orc_mesh_free(void *h);
  * quadrilateral must also turn counterclockwise at every corner. */
 static int elem_geometry(orc_mesh *m, int64_t e) {
   int dim = m->dim;
-  double J[9];
-  const double *X = m->X + e * m->nvpe * dim;
+  real J[9];
+  const real *X = m->X + e * m->nvpe * dim;
   int nf = elem_nfaces(m, e);
   int kv[3] = {1, (m->quad && nf == 4) ? 3 : 2, 3};
   for (int a = 0; a < dim; ++a)
     for (int k = 0; k < dim; ++k) J[a * dim + k] = X[kv[k] * dim + a] - X[a];
-  double det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
+  real det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
   m->detJ[e] = det;
   if (m->quad && nf == 3) m->nonaffine++;
   if (m->quad && nf == 4) {
-    double scale = 0.0, off = 0.0;
+    real scale = 0.0, off = 0.0;
     for (int c = 0; c < 4; ++c) {
-      const double *A = X + c * 2, *B = X + ((c + 1) % 4) * 2, *Cc = X + ((c + 3) % 4) * 2;
-      double cr = (B[0] - A[0]) * (Cc[1] - A[1]) - (B[1] - A[1]) * (Cc[0] - A[0]);
+      const real *A = X + c * 2, *B = X + ((c + 1) % 4) * 2, *Cc = X + ((c + 3) % 4) * 2;
+      real cr = (B[0] - A[0]) * (Cc[1] - A[1]) - (B[1] - A[1]) * (Cc[0] - A[0]);
       if (!(cr > 0.0)) return -1;
       scale = fmax(scale, fabs(B[0] - A[0]) + fabs(B[1] - A[1]));
     }
@@ -484,8 +514,8 @@ static int elem_geometry(orc_mesh *m, int64_t e) {
   return det > 0.0 ? 0 : -1;
 }
 
-static void *mesh_new(int dim, int quad, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
-                      const double *L) {
+static void *mesh_new(int dim, int quad, int64_t nv, const real *xyz, int64_t ne, const int32_t *ev,
+                      const real *L) {
   if (dim != 2 && dim != 3) return fail("mesh: dim must be 2 or 3"), (void *)0;
   if (ne <= 0 || nv <= 0 || ne > (1LL << 30) || nv > (1LL << 30))
     return fail("mesh: element or vertex count out of range"), (void *)0;
@@ -501,9 +531,9 @@ static void *mesh_new(int dim, int quad, int64_t nv, const double *xyz, int64_t 
   int nvpe = m->nvpe, nfpe = m->nfpe;
   m->ev = (int32_t *)malloc(sizeof(int32_t) * ne * nvpe);
   memcpy(m->ev, ev, sizeof(int32_t) * ne * nvpe);
-  m->X = (double *)malloc(sizeof(double) * ne * nvpe * dim);
-  m->detJ = (double *)malloc(sizeof(double) * ne);
-  m->Jinv = (double *)malloc(sizeof(double) * ne * dim * dim);
+  m->X = (real *)malloc(sizeof(real) * ne * nvpe * dim);
+  m->detJ = (real *)malloc(sizeof(real) * ne);
+  m->Jinv = (real *)malloc(sizeof(real) * ne * dim * dim);
   for (int64_t e = 0; e < ne; ++e) {
     for (int k = 0; k < nvpe; ++k) {
       int32_t v = ev[e * nvpe + k];
@@ -516,9 +546,9 @@ static void *mesh_new(int dim, int quad, int64_t nv, const double *xyz, int64_t 
         return fail("mesh: vertex id out of range"), (void *)0;
       }
       for (int a = 0; a < dim; ++a) {
-        double x = xyz[(int64_t)v * dim + a];
+        real x = xyz[(int64_t)v * dim + a];
         if (m->periodic && k > 0) {
-          double x0 = m->X[(e * nvpe) * dim + a];
+          real x0 = m->X[(e * nvpe) * dim + a];
           x += m->L[a] * round((x0 - x) / m->L[a]);
         }
         m->X[(e * nvpe + k) * dim + a] = x;
@@ -597,13 +627,13 @@ static void *mesh_new(int dim, int quad, int64_t nv, const double *xyz, int64_t 
   return m;
 }
 
-void *orc_mesh_new(int dim, int64_t nv, const double *xyz, int64_t ne, const int32_t *ev,
-                   const double *L) {
+void *orc_mesh_new(int dim, int64_t nv, const real *xyz, int64_t ne, const int32_t *ev,
+                   const real *L) {
   return mesh_new(dim, 0, nv, xyz, ne, ev, L);
 }
 
 /* quadrilateral or hybrid mesh: ev is [ne][4], -1 as the fourth id of a triangle */
-void *orc_mesh_new_quad(int64_t nv, const double *xyz, int64_t ne, const int32_t *ev, const double *L) {
+void *orc_mesh_new_quad(int64_t nv, const real *xyz, int64_t ne, const int32_t *ev, const real *L) {
   return mesh_new(2, 1, nv, xyz, ne, ev, L);
 }
 
@@ -639,9 +669,9 @@ void orc_mesh_sides(void *h, int32_t *l, int32_t *r, int8_t *ql, int8_t *qr) {
   memcpy(qr, m->sqr, m->ns);
 }
 
-void orc_mesh_detj(void *h, double *detJ) {
+void orc_mesh_detj(void *h, real *detJ) {
   orc_mesh *m = (orc_mesh *)h;
-  memcpy(detJ, m->detJ, sizeof(double) * m->ne);
+  memcpy(detJ, m->detJ, sizeof(real) * m->ne);
 }
 
 /* ======================================================================= */
@@ -936,28 +966,28 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   m->L[0] = b->L[0];
   m->L[1] = b->L[1];
   m->ev = (int32_t *)malloc(sizeof(int32_t) * ne * 3);
-  m->X = (double *)malloc(sizeof(double) * ne * 6);
-  m->detJ = (double *)malloc(sizeof(double) * ne);
-  m->Jinv = (double *)malloc(sizeof(double) * ne * 4);
+  m->X = (real *)malloc(sizeof(real) * ne * 6);
+  m->detJ = (real *)malloc(sizeof(real) * ne);
+  m->Jinv = (real *)malloc(sizeof(real) * ne * 4);
   int bad = 0;
   for (int64_t e = 0; e < ne0; ++e) {
     const int32_t *v = b->ev + e * 3;
-    const double *P = b->X + e * 6;
+    const real *P = b->X + e * 6;
     int64_t n = first[e];
     if (!flag[e]) {
       memcpy(m->ev + n * 3, v, sizeof(int32_t) * 3);
-      memcpy(m->X + n * 6, P, sizeof(double) * 6);
+      memcpy(m->X + n * 6, P, sizeof(real) * 6);
       continue;
     }
     int32_t mv[3];
-    double Q[3][2];
+    real Q[3][2];
     for (int k = 0; k < 3; ++k) {
       mv[k] = mid[b->es[e * 3 + k]];
       for (int a = 0; a < 2; ++a) Q[k][a] = 0.5 * (P[k * 2 + a] + P[((k + 1) % 3) * 2 + a]);
     }
     /* children as (vertex id, coordinates) */
     int32_t cid[4][3] = {{v[0], mv[0], mv[2]}, {mv[0], v[1], mv[1]}, {mv[2], mv[1], v[2]}, {mv[0], mv[1], mv[2]}};
-    const double *cx[4][3] = {{P, Q[0], Q[2]}, {Q[0], P + 2, Q[1]}, {Q[2], Q[1], P + 4}, {Q[0], Q[1], Q[2]}};
+    const real *cx[4][3] = {{P, Q[0], Q[2]}, {Q[0], P + 2, Q[1]}, {Q[2], Q[1], P + 4}, {Q[0], Q[1], Q[2]}};
     for (int c = 0; c < 4; ++c)
       for (int k = 0; k < 3; ++k) {
         m->ev[(n + c) * 3 + k] = cid[c][k];
@@ -1088,10 +1118,10 @@ int64_t orc_mesh_nelem(void *h) { return ((orc_mesh *)h)->ne; }
 int64_t orc_mesh_nvert(void *h) { return ((orc_mesh *)h)->nv; }
 
 /* element vertex ids and unwrapped coordinates */
-void orc_mesh_elements(void *h, int32_t *ev, double *X) {
+void orc_mesh_elements(void *h, int32_t *ev, real *X) {
   orc_mesh *m = (orc_mesh *)h;
   memcpy(ev, m->ev, sizeof(int32_t) * m->ne * m->nvpe);
-  memcpy(X, m->X, sizeof(double) * m->ne * m->nvpe * m->dim);
+  memcpy(X, m->X, sizeof(real) * m->ne * m->nvpe * m->dim);
 }
 
 /* colors of a refined mesh and the hanging half of each side (-1 conforming) */
@@ -1115,15 +1145,15 @@ int orc_mesh_refined(void *h, int8_t *col, int8_t *half) {
 #define ORC_GAMMA 1.4
 enum { ORC_EULER = 0, ORC_ADVECTION = 1 };
 
-static void euler_flux_n(int dim, const double *U, const double *n, double *Fn, double *lam) {
-  double rho = U[0], E = U[dim + 1];
-  double vel[3] = {0, 0, 0}, q2 = 0.0, un = 0.0;
+static void euler_flux_n(int dim, const real *U, const real *n, real *Fn, real *lam) {
+  real rho = U[0], E = U[dim + 1];
+  real vel[3] = {0, 0, 0}, q2 = 0.0, un = 0.0;
   for (int a = 0; a < dim; ++a) {
     vel[a] = U[1 + a] / rho;
     q2 += vel[a] * vel[a];
     un += vel[a] * n[a];
   }
-  double p = (ORC_GAMMA - 1.0) * (E - 0.5 * rho * q2);
+  real p = (ORC_GAMMA - 1.0) * (E - 0.5 * rho * q2);
   Fn[0] = rho * un;
   for (int a = 0; a < dim; ++a) Fn[1 + a] = U[1 + a] * un + p * n[a];
   Fn[dim + 1] = (E + p) * un;
@@ -1131,39 +1161,39 @@ static void euler_flux_n(int dim, const double *U, const double *n, double *Fn, 
 }
 
 /* physical flux in direction a (for the volume term) */
-static void euler_flux_dir(int dim, const double *U, int a, double *F) {
-  double n[3] = {0, 0, 0}, lam;
+static void euler_flux_dir(int dim, const real *U, int a, real *F) {
+  real n[3] = {0, 0, 0}, lam;
   n[a] = 1.0;
   euler_flux_n(dim, U, n, F, &lam);
 }
 
 typedef struct {
   int kind, dim, M;
-  double adv[3];
+  real adv[3];
 } orc_phys;
 
-static void phys_flux_dir(const orc_phys *ph, const double *U, int a, double *F) {
+static void phys_flux_dir(const orc_phys *ph, const real *U, int a, real *F) {
   if (ph->kind == ORC_EULER) euler_flux_dir(ph->dim, U, a, F);
   else F[0] = ph->adv[a] * U[0];
 }
 
-static void num_flux(const orc_phys *ph, const double *Um, const double *Up, const double *n,
-                     double *Fs) {
+static void num_flux(const orc_phys *ph, const real *Um, const real *Up, const real *n,
+                     real *Fs) {
   if (ph->kind == ORC_EULER) {
-    double Fm[ORC_MAXM], Fp[ORC_MAXM], lm, lp;
+    real Fm[ORC_MAXM], Fp[ORC_MAXM], lm, lp;
     euler_flux_n(ph->dim, Um, n, Fm, &lm);
     euler_flux_n(ph->dim, Up, n, Fp, &lp);
-    double lam = lm > lp ? lm : lp;
+    real lam = lm > lp ? lm : lp;
     for (int k = 0; k < ph->M; ++k) Fs[k] = 0.5 * (Fm[k] + Fp[k]) - 0.5 * lam * (Up[k] - Um[k]);
   } else {
-    double an = 0.0;
+    real an = 0.0;
     for (int a = 0; a < ph->dim; ++a) an += ph->adv[a] * n[a];
     Fs[0] = 0.5 * an * (Um[0] + Up[0]) - 0.5 * fabs(an) * (Up[0] - Um[0]);
   }
 }
 
 /* exported for the flux pins */
-int orc_lf_flux(int dim, const double *Um, const double *Up, const double *n, double *Fs) {
+int orc_lf_flux(int dim, const real *Um, const real *Up, const real *n, real *Fs) {
   orc_phys ph = {ORC_EULER, dim, dim + 2, {0, 0, 0}};
   num_flux(&ph, Um, Up, n, Fs);
   return 0;
@@ -1173,8 +1203,8 @@ int orc_lf_flux(int dim, const double *Um, const double *Up, const double *n, do
 /* Eq. 2, element by element                                                */
 /* ======================================================================= */
 
-static int basis_eval(const orc_mesh *m, int p, const double *x, double *phi, double *d0, double *d1,
-                      double *d2) {
+static int basis_eval(const orc_mesh *m, int p, const real *x, real *phi, real *d0, real *d1,
+                      real *d2) {
   if (m->quad) return orc_basis_quad(p, x[0], x[1], phi, d0, d1);
   if (m->dim == 2) return orc_basis_tri(p, x[0], x[1], phi, d0, d1);
   return orc_basis_tet(p, x[0], x[1], x[2], phi, d0, d1, d2);
@@ -1182,31 +1212,31 @@ static int basis_eval(const orc_mesh *m, int p, const double *x, double *phi, do
 
 /* reference coordinates of physical point x in element e (nearest periodic
  * image of x to the element's centroid) */
-static void ref_coords(const orc_mesh *m, int64_t e, const double *x, double *rs) {
+static void ref_coords(const orc_mesh *m, int64_t e, const real *x, real *rs) {
   int dim = m->dim;
-  const double *X = m->X + e * m->nvpe * dim;
-  double xs[3];
+  const real *X = m->X + e * m->nvpe * dim;
+  real xs[3];
   for (int a = 0; a < dim; ++a) {
-    double cen = 0.0;
+    real cen = 0.0;
     for (int k = 0; k < m->nvpe; ++k) cen += X[k * dim + a];
     cen /= m->nvpe;
     xs[a] = x[a];
     if (m->periodic) xs[a] += m->L[a] * round((cen - x[a]) / m->L[a]);
   }
-  const double *Ji = m->Jinv + e * dim * dim;
+  const real *Ji = m->Jinv + e * dim * dim;
   for (int k = 0; k < dim; ++k) {
-    double v = 0.0;
+    real v = 0.0;
     for (int a = 0; a < dim; ++a) v += Ji[k * dim + a] * (xs[a] - X[a]);
     rs[k] = v;
   }
 }
 
-static void eval_state(const orc_mesh *m, int p, int M, int Np, const double *c, const double *rs,
-                       double *U) {
-  double phi[ORC_MAXNP];
+static void eval_state(const orc_mesh *m, int p, int M, int Np, const real *c, const real *rs,
+                       real *U) {
+  real phi[ORC_MAXNP];
   basis_eval(m, p, rs, phi, NULL, NULL, NULL);
   for (int k = 0; k < M; ++k) {
-    double v = 0.0;
+    real v = 0.0;
     for (int j = 0; j < Np; ++j) v += c[k * Np + j] * phi[j];
     U[k] = v;
   }
@@ -1221,8 +1251,8 @@ static void eval_state(const orc_mesh *m, int p, int M, int Np, const double *c,
  * sum to 1. */
 typedef struct {
   int dim, nv, nf;
-  double *vr, *vs, *vt, *vw;
-  double *fa, *fb, *fw;
+  real *vr, *vs, *vt, *vw;
+  real *fa, *fb, *fw;
 } orc_rules;
 
 static int default_face_n1(int dim, int p) { return dim == 2 ? 2 * p + 1 : p + 2; }
@@ -1244,20 +1274,20 @@ static int rules_make(int dim, int quad, int nf1, int nv1, orc_rules *R) {
   R->dim = dim;
   if (nf1 < 1 || nf1 > 64 || nv1 < 1 || nv1 > 64) return fail("rules: size out of range");
   R->nv = dim == 2 ? nv1 * nv1 : nv1 * nv1 * nv1;
-  R->vr = (double *)malloc(sizeof(double) * R->nv);
-  R->vs = (double *)malloc(sizeof(double) * R->nv);
-  R->vt = (double *)calloc(R->nv, sizeof(double));
-  R->vw = (double *)malloc(sizeof(double) * R->nv);
+  R->vr = (real *)malloc(sizeof(real) * R->nv);
+  R->vs = (real *)malloc(sizeof(real) * R->nv);
+  R->vt = (real *)calloc(R->nv, sizeof(real));
+  R->vw = (real *)malloc(sizeof(real) * R->nv);
   int rc = quad ? orc_quad_rule(nv1, R->vr, R->vs, R->vw)
            : dim == 2 ? orc_tri_rule(nv1, R->vr, R->vs, R->vw)
                       : orc_tet_rule(nv1, R->vr, R->vs, R->vt, R->vw);
   if (rc) return rc;
   R->nf = dim == 2 ? nf1 : nf1 * nf1;
-  R->fa = (double *)malloc(sizeof(double) * R->nf);
-  R->fb = (double *)calloc(R->nf, sizeof(double));
-  R->fw = (double *)malloc(sizeof(double) * R->nf);
+  R->fa = (real *)malloc(sizeof(real) * R->nf);
+  R->fb = (real *)calloc(R->nf, sizeof(real));
+  R->fw = (real *)malloc(sizeof(real) * R->nf);
   if (dim == 2) {
-    double xg[64], wg[64];
+    real xg[64], wg[64];
     if (orc_gauss_legendre(nf1, xg, wg)) return -1;
     for (int i = 0; i < nf1; ++i) {
       R->fa[i] = 0.5 * (1.0 + xg[i]);
@@ -1274,19 +1304,19 @@ static int rules_make(int dim, int quad, int nf1, int nv1, orc_rules *R) {
  * normal (pointing away from the opposite vertex) and its quadrature points. */
 typedef struct {
   int nq;
-  double meas, n[3];
-  double *x; /* nq * 3 */
-  const double *w;
+  real meas, n[3];
+  real *x; /* nq * 3 */
+  const real *w;
 } orc_face;
 
 static void face_geometry(const orc_mesh *m, int64_t e, int q, const orc_rules *R, orc_face *F) {
   int dim = m->dim;
-  const double *X = m->X + e * m->nvpe * dim;
+  const real *X = m->X + e * m->nvpe * dim;
   int fv[3], nf = elem_nfaces(m, e);
   face_verts_e(m, e, q, fv);
-  const double *A = X + fv[0] * dim, *B = X + fv[1] * dim;
-  const double *O = dim == 2 ? X + ((q + 2) % nf) * dim : X + q * dim; /* a vertex off the face */
-  double u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+  const real *A = X + fv[0] * dim, *B = X + fv[1] * dim;
+  const real *O = dim == 2 ? X + ((q + 2) % nf) * dim : X + q * dim; /* a vertex off the face */
+  real u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
   for (int a = 0; a < dim; ++a) u[a] = B[a] - A[a];
   if (dim == 2) {
     F->meas = sqrt(u[0] * u[0] + u[1] * u[1]);
@@ -1294,14 +1324,14 @@ static void face_geometry(const orc_mesh *m, int64_t e, int q, const orc_rules *
     F->n[1] = -u[0] / F->meas;
     F->n[2] = 0.0;
   } else {
-    const double *C = X + fv[2] * dim;
+    const real *C = X + fv[2] * dim;
     for (int a = 0; a < 3; ++a) v[a] = C[a] - A[a];
-    double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-    double nn = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    real cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    real nn = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
     F->meas = 0.5 * nn;
     for (int a = 0; a < 3; ++a) F->n[a] = cr[a] / nn;
   }
-  double side = 0.0;
+  real side = 0.0;
   for (int a = 0; a < dim; ++a) side += F->n[a] * (O[a] - A[a]);
   if (side > 0.0)
     for (int a = 0; a < dim; ++a) F->n[a] = -F->n[a];
@@ -1322,9 +1352,9 @@ static void face_points_of_left(const orc_mesh *m, int64_t e, int32_t s, const o
   int64_t l = m->sl[s];
   if (l == e) return;
   int dim = m->dim, fv[3];
-  const double *X = m->X + l * m->nvpe * dim;
+  const real *X = m->X + l * m->nvpe * dim;
   face_verts_e(m, l, m->sql[s], fv);
-  const double *A = X + fv[0] * dim, *B = X + fv[1] * dim, *C = dim == 3 ? X + fv[2] * dim : A;
+  const real *A = X + fv[0] * dim, *B = X + fv[1] * dim, *C = dim == 3 ? X + fv[2] * dim : A;
   for (int i = 0; i < R->nf; ++i)
     for (int a = 0; a < dim; ++a)
       F->x[i * 3 + a] = A[a] + R->fa[i] * (B[a] - A[a]) + R->fb[i] * (C[a] - A[a]);
@@ -1336,7 +1366,7 @@ static void face_points_of_left(const orc_mesh *m, int64_t e, int32_t s, const o
  * advection with velocity adv.  nq_face1 / nq_vol1 override the 1-D point
  * counts (0 = defaults).  Boundary faces use the transmissive state U+ = U-
  * (reading; the configurations are periodic). */
-int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double *rhs,
+int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
             const int64_t *elems, int64_t nelem, int nq_face1, int nq_vol1) {
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim;
@@ -1353,30 +1383,40 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
     rules_free(&R);
     return -1;
   }
-  orc_face F;
-  F.x = (double *)malloc(sizeof(double) * 3 * R.nf);
   int64_t count = nelem < 0 ? m->ne : nelem;
+  /* elements are independent: the threaded build (-fopenmp) splits the list
+   * across threads, each with its own face scratch; the arithmetic of each
+   * element is the same as in the sequential build */
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+  {
+  orc_face F;
+  F.x = (real *)malloc(sizeof(real) * 3 * R.nf);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
   for (int64_t ii = 0; ii < count; ++ii) {
     int64_t e = nelem < 0 ? ii : elems[ii];
-    const double *ce = c + e * M * Np;
-    double *re = rhs + ii * M * Np;
+    const real *ce = c + e * M * Np;
+    real *re = rhs + ii * M * Np;
     for (int i = 0; i < M * Np; ++i) re[i] = 0.0;
-    const double *Ji = m->Jinv + e * dim * dim;
+    const real *Ji = m->Jinv + e * dim * dim;
     /* volume integral: sum_q w_q F(U_q) . (J^-T grad_ref phi_j) */
     for (int q = 0; q < R.nv; ++q) {
-      double x[3] = {R.vr[q], R.vs[q], R.vt[q]};
-      double phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM];
+      real x[3] = {R.vr[q], R.vs[q], R.vt[q]};
+      real phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM];
       basis_eval(m, p, x, phi, d[0], d[1], d[2]);
       for (int k = 0; k < M; ++k) {
-        double v = 0.0;
+        real v = 0.0;
         for (int j = 0; j < Np; ++j) v += ce[k * Np + j] * phi[j];
         U[k] = v;
       }
       for (int a = 0; a < dim; ++a) {
-        double Fa[ORC_MAXM];
+        real Fa[ORC_MAXM];
         phys_flux_dir(&ph, U, a, Fa);
         for (int j = 0; j < Np; ++j) {
-          double gx = 0.0; /* d phi_j / d x_a */
+          real gx = 0.0; /* d phi_j / d x_a */
           for (int r = 0; r < dim; ++r) gx += Ji[r * dim + a] * d[r][j];
           for (int k = 0; k < M; ++k) re[k * Np + j] += R.vw[q] * Fa[k] * gx;
         }
@@ -1393,18 +1433,18 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
       face_points_of_left(m, e, s, &R, &F);
       int32_t nb = m->sl[s] == e ? m->sr[s] : m->sl[s];
       if (m->shalf && m->shalf[s] >= 0 && m->sr[s] == e) {
-        const double *Xl = m->X + (int64_t)m->sl[s] * 6;
+        const real *Xl = m->X + (int64_t)m->sl[s] * 6;
         int q = m->sql[s];
-        double dx = Xl[((q + 1) % 3) * 2] - Xl[q * 2], dy = Xl[((q + 1) % 3) * 2 + 1] - Xl[q * 2 + 1];
+        real dx = Xl[((q + 1) % 3) * 2] - Xl[q * 2], dy = Xl[((q + 1) % 3) * 2 + 1] - Xl[q * 2 + 1];
         F.meas = sqrt(dx * dx + dy * dy);
       }
-      double scale = F.meas / m->detJ[e];
+      real scale = F.meas / m->detJ[e];
       for (int q = 0; q < F.nq; ++q) {
-        double rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];
+        real rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];
         ref_coords(m, e, F.x + 3 * q, rs);
         eval_state(m, p, M, Np, ce, rs, Um);
         if (nb >= 0) {
-          double rn[3];
+          real rn[3];
           ref_coords(m, nb, F.x + 3 * q, rn);
           eval_state(m, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
         } else {
@@ -1418,8 +1458,21 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
     }
   }
   free(F.x);
+  }
   rules_free(&R);
   return 0;
+}
+
+/* threads the element loop of orc_rhs uses (threaded build only); returns
+ * the count in effect, 1 in the sequential build */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* ======================================================================= */
@@ -1427,7 +1480,7 @@ int orc_rhs(void *h, int p, int kind, const double *adv, const double *c, double
 /* ======================================================================= */
 /* dt = cfl * min_i r_i / ((2p+1) lambda_i); r_i = dim |element| / |boundary|
  * (the inradius), lambda_i = max over the element's volume points of |u|+c. */
-int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
+int orc_dt(void *h, int p, const real *c, real cfl, real *dt_out) {
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim, M = dim + 2, Np = npoly_m(m, p);
   if (m->nonaffine) return fail("dt: quadrilaterals must be parallelograms");
@@ -1437,27 +1490,27 @@ int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
     return -1;
   }
   orc_face F;
-  F.x = (double *)malloc(sizeof(double) * 3 * R.nf);
-  double best = INFINITY;
+  F.x = (real *)malloc(sizeof(real) * 3 * R.nf);
+  real best = INFINITY;
   for (int64_t e = 0; e < m->ne; ++e) {
-    double lam = 0.0;
+    real lam = 0.0;
     for (int q = 0; q < R.nv; ++q) {
-      double x[3] = {R.vr[q], R.vs[q], R.vt[q]}, U[ORC_MAXM];
+      real x[3] = {R.vr[q], R.vs[q], R.vt[q]}, U[ORC_MAXM];
       eval_state(m, p, M, Np, c + e * M * Np, x, U);
-      double rho = U[0], q2 = 0.0;
+      real rho = U[0], q2 = 0.0;
       for (int a = 0; a < dim; ++a) q2 += (U[1 + a] / rho) * (U[1 + a] / rho);
-      double pr = (ORC_GAMMA - 1.0) * (U[dim + 1] - 0.5 * rho * q2);
-      double l = sqrt(q2) + sqrt(ORC_GAMMA * pr / rho);
+      real pr = (ORC_GAMMA - 1.0) * (U[dim + 1] - 0.5 * rho * q2);
+      real l = sqrt(q2) + sqrt(ORC_GAMMA * pr / rho);
       if (l > lam) lam = l;
     }
-    double bnd = 0.0;
+    real bnd = 0.0;
     for (int f = 0; f < m->nfpe; ++f) {
       face_geometry(m, e, f, &R, &F);
       bnd += F.meas;
     }
-    double vol = m->detJ[e] / (m->quad ? 1.0 : dim == 2 ? 2.0 : 6.0);
-    double r = dim * vol / bnd;
-    double v = r / ((2 * p + 1) * lam);
+    real vol = m->detJ[e] / (m->quad ? 1.0 : dim == 2 ? 2.0 : 6.0);
+    real r = dim * vol / bnd;
+    real v = r / ((2 * p + 1) * lam);
     if (v < best) best = v;
   }
   free(F.x);
@@ -1466,29 +1519,40 @@ int orc_dt(void *h, int p, const double *c, double cfl, double *dt_out) {
   return 0;
 }
 
-/* One SSP-RK3 (Shu-Osher) step of the Euler system, in place:
+/* One SSP-RK3 (Shu-Osher) step, in place:
  *   u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));
- *   u  = 1/3 u + 2/3 (u2 + dt L(u2)).
- * dt comes from the state at the start of the step, or is dt_in when > 0. */
-int orc_rk_step(void *h, int p, double *c, double cfl, double dt_in, double *dt_out) {
+ *   u  = 1/3 u + 2/3 (u2 + dt L(u2)),
+ * with L the right-hand side of Eq. 2 for the flux kind (ORC_EULER, or
+ * ORC_ADVECTION with velocity adv and one equation).  dt comes from the
+ * state at the start of the step (Euler only), or is dt_in when > 0. */
+int orc_rk_step_kind(void *h, int p, int kind, const real *adv, real *c, real cfl, real dt_in,
+                     real *dt_out) {
   orc_mesh *m = (orc_mesh *)h;
-  int dim = m->dim, M = dim + 2, Np = npoly_m(m, p);
+  int dim = m->dim, M = kind == ORC_EULER ? dim + 2 : 1, Np = npoly_m(m, p);
   int64_t n = m->ne * M * Np;
-  double dt = dt_in;
-  if (!(dt > 0.0) && orc_dt(h, p, c, cfl, &dt)) return -1;
-  double *u1 = (double *)malloc(sizeof(double) * n), *u2 = (double *)malloc(sizeof(double) * n);
-  double *L = (double *)malloc(sizeof(double) * n);
-  int rc = orc_rhs(h, p, ORC_EULER, NULL, c, L, NULL, -1, 0, 0);
+  real dt = dt_in;
+  if (!(dt > 0.0)) {
+    if (kind != ORC_EULER) return fail("rk_step: the advection form needs dt_in > 0");
+    if (orc_dt(h, p, c, cfl, &dt)) return -1;
+  }
+  real *u1 = (real *)malloc(sizeof(real) * n), *u2 = (real *)malloc(sizeof(real) * n);
+  real *L = (real *)malloc(sizeof(real) * n);
+  int rc = orc_rhs(h, p, kind, adv, c, L, NULL, -1, 0, 0);
   for (int64_t i = 0; i < n && !rc; ++i) u1[i] = c[i] + dt * L[i];
-  if (!rc) rc = orc_rhs(h, p, ORC_EULER, NULL, u1, L, NULL, -1, 0, 0);
+  if (!rc) rc = orc_rhs(h, p, kind, adv, u1, L, NULL, -1, 0, 0);
   for (int64_t i = 0; i < n && !rc; ++i) u2[i] = 0.75 * c[i] + 0.25 * (u1[i] + dt * L[i]);
-  if (!rc) rc = orc_rhs(h, p, ORC_EULER, NULL, u2, L, NULL, -1, 0, 0);
-  for (int64_t i = 0; i < n && !rc; ++i) c[i] = c[i] / 3.0 + 2.0 / 3.0 * (u2[i] + dt * L[i]);
+  if (!rc) rc = orc_rhs(h, p, kind, adv, u2, L, NULL, -1, 0, 0);
+  for (int64_t i = 0; i < n && !rc; ++i) c[i] = c[i] / 3.0 + (real)2 / 3 * (u2[i] + dt * L[i]);
   free(u1);
   free(u2);
   free(L);
   if (dt_out) *dt_out = dt;
   return rc;
+}
+
+/* the Euler system's step */
+int orc_rk_step(void *h, int p, real *c, real cfl, real dt_in, real *dt_out) {
+  return orc_rk_step_kind(h, p, ORC_EULER, NULL, c, cfl, dt_in, dt_out);
 }
 
 /* ======================================================================= */
@@ -1502,8 +1566,8 @@ int orc_num_vol_points(int dim, int p) {
 /* physical coordinates (unwrapped per element) of the volume points of a
  * rule with n1 points per direction (0 = default), [E][Nq][dim]; optional
  * physical weights [E][Nq] and DG solution values U [E][Nq][M] of c. */
-int orc_eval_points(void *h, int p, int M, const double *c, int n1, double *xyz, double *w,
-                    double *U) {
+int orc_eval_points(void *h, int p, int M, const real *c, int n1, real *xyz, real *w,
+                    real *U) {
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim, Np = npoly_m(m, p);
   if (m->nonaffine) return fail("eval_points: quadrilaterals must be parallelograms");
@@ -1515,11 +1579,11 @@ int orc_eval_points(void *h, int p, int M, const double *c, int n1, double *xyz,
   /* the reference axes run from v0 to v1, v2 (simplices) or v1, v3 (quadrilaterals) */
   const int kv[3] = {1, m->quad ? 3 : 2, 3};
   for (int64_t e = 0; e < m->ne; ++e) {
-    const double *X = m->X + e * m->nvpe * dim;
+    const real *X = m->X + e * m->nvpe * dim;
     for (int q = 0; q < R.nv; ++q) {
-      double rs[3] = {R.vr[q], R.vs[q], R.vt[q]};
+      real rs[3] = {R.vr[q], R.vs[q], R.vt[q]};
       for (int a = 0; a < dim; ++a) {
-        double v = X[a];
+        real v = X[a];
         for (int k = 0; k < dim; ++k) v += (X[kv[k] * dim + a] - X[a]) * rs[k];
         if (xyz) xyz[(e * R.nv + q) * dim + a] = v;
       }
@@ -1535,7 +1599,7 @@ int orc_eval_points(void *h, int p, int M, const double *c, int n1, double *xyz,
 /* L2 projection: with a basis orthonormal on the reference element the
  * coefficients are c[e][k][j] = sum_q w_q U_k(x_q) phi_j(x_q) over the
  * default volume rule; vals is [E][Nq][M] at the points of orc_eval_points. */
-int orc_project(void *h, int p, int M, const double *vals, double *c) {
+int orc_project(void *h, int p, int M, const real *vals, real *c) {
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim, Np = npoly_m(m, p);
   orc_rules R;
@@ -1544,10 +1608,10 @@ int orc_project(void *h, int p, int M, const double *vals, double *c) {
     return -1;
   }
   for (int64_t e = 0; e < m->ne; ++e) {
-    double *ce = c + e * M * Np;
+    real *ce = c + e * M * Np;
     for (int i = 0; i < M * Np; ++i) ce[i] = 0.0;
     for (int q = 0; q < R.nv; ++q) {
-      double x[3] = {R.vr[q], R.vs[q], R.vt[q]}, phi[ORC_MAXNP];
+      real x[3] = {R.vr[q], R.vs[q], R.vt[q]}, phi[ORC_MAXNP];
       basis_eval(m, p, x, phi, NULL, NULL, NULL);
       for (int k = 0; k < M; ++k)
         for (int j = 0; j < Np; ++j) ce[k * Np + j] += R.vw[q] * vals[(e * R.nv + q) * M + k] * phi[j];
