@@ -191,9 +191,8 @@ def kernel_source_hash() -> str:
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
-# over the launches of each class) from the launch list of this benchmark's own
-# command, profiles/launch_list_rk_fp32mixed_p3_1048352tri.md, taken with the
-# kernel sources of hash TRAFFIC_SOURCES.
+# over the launches of each class) from an ncu capture of this benchmark's own
+# command, taken with the kernel sources of hash TRAFFIC_SOURCES.
 TRAFFIC_SOURCES = "8dc544a059717f84"
 TRAFFIC_BYTES = {"last": 1122772187, "first": 478180730, "color": 589463979, "cfl": 4220489}
 
@@ -647,27 +646,41 @@ def run_table7(dgc, torch, dev, stream, args, cfg, c_base):
                                 "p": cfg["p"], "dofs": dofs, "rows": rows}}
 
 
-def cpu_baseline(mi, p, c_host, dofs, elements=None):
-    """The CPU oracle as it stands (single-threaded C, FP64), one right-hand side
-    of the same workload (all elements unless a count is given)."""
+def host_cores() -> int:
+    """Host cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(mi, p, c_host, dofs, single_elements: int = 100_000):
+    """The CPU oracle as it stands (FP64 C, element by element as Eq. 2 is
+    written): its threaded build (gcc -O3 -fopenmp, the element loop split over
+    all host cores) on one whole right-hand side of the same workload, and its
+    sequential build on a random sample of single_elements elements."""
     import oracle
 
-    om = oracle.OracleMesh.from_input(mi)
     E = mi.ne
-    if elements is None or elements >= E:
-        t0 = time.perf_counter()
-        om.rhs(p, c_host)
-        t = time.perf_counter() - t0
-        n = E
-    else:
-        sel = np.random.default_rng(0).choice(E, elements, replace=False)
-        t0 = time.perf_counter()
-        om.rhs(p, c_host, elems=sel)
-        t = time.perf_counter() - t0
-        n = elements
     nv = c_host.shape[1] * c_host.shape[2]
-    return {"value": n * nv / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one FP64 right-hand side of {n} of {E} elements, {t:.1f} s, single thread"}
+    cores = host_cores()
+    mt = oracle.OracleMesh.from_input(mi, build="threads")
+    used = oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    mt.rhs(p, c_host)
+    t = time.perf_counter() - t0
+    del mt
+    om = oracle.OracleMesh.from_input(mi)
+    n1 = min(single_elements, E)
+    sel = np.random.default_rng(0).choice(E, n1, replace=False)
+    t1 = time.perf_counter()
+    om.rhs(p, c_host, elems=sel)
+    ts = time.perf_counter() - t1
+    return {"value": E * nv / t, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"one FP64 right-hand side of all {E} elements, {t:.2f} s on {used} threads "
+                      f"(gcc -O3 -fopenmp, no FMA contraction)",
+            "single_thread": {"value": n1 * nv / ts, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} random elements of one right-hand side, {ts:.2f} s, sequential build"}}
 
 
 def run_reference(args):
@@ -685,24 +698,33 @@ def run_reference(args):
     del xyz
     E = mi.ne
     NV = c.shape[1] * c.shape[2]
-    per_step = min(args.ref_elements, E)
+    per_step = min(args.ref_elements, E) if args.ref_elements > 0 else E
+    cores = host_cores()
+    mt = oracle.OracleMesh.from_input(mi, build="threads")
+    used = oracle.set_threads(cores)
+    del om
     rng = np.random.default_rng(0)
+
+    def sample():
+        return None if per_step == E else rng.choice(E, per_step, replace=False)
+
     for _ in range(args.warmup):
-        om.rhs(p, c, elems=rng.choice(E, per_step, replace=False))
+        mt.rhs(p, c, elems=sample())
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        om.rhs(p, c, elems=rng.choice(E, per_step, replace=False))
+        mt.rhs(p, c, elems=sample())
     t = (time.perf_counter() - t0) / args.steps
     value = per_step * NV / t
+    what = "all" if per_step == E else f"{per_step} random"
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload, "elements": E, "p": p,
-                   "step": f"one oracle right-hand side of {per_step} random elements"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": f"{per_step} random elements per step, single-threaded FP64 C oracle"},
+                   "step": f"one oracle right-hand side of {what} elements"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": used,
+                         "sample": f"{what} elements per step, FP64 C oracle, threaded build on {used} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -716,7 +738,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 and comparator timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) timing")
-    ap.add_argument("--ref-elements", type=int, default=40000, help="oracle elements per reference step")
+    ap.add_argument("--ref-elements", type=int, default=0,
+                    help="oracle elements per reference step (0 = the whole mesh)")
     ap.add_argument("--epb", type=int, default=0, help="edges per block of the surface kernels (0 = library default)")
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "

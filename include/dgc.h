@@ -357,16 +357,22 @@ const char* dgc_last_error(void);
  * reserves the whole device for its own pool, or a fixed-footprint solver loop that may
  * not change its allocations once running -- and so cannot produce the workspace
  * dgc_rk_step needs.  The paper has no counterpart; this is an interface addition.
- *   Limits: dgc_workspace_size(prec) plus 4 bytes per element (+256) must fit in 16 MiB
- *   (e.g. up to ~25,000 triangles at p = 3, ~79,000 at p = 1); larger meshes get
- *   DGC_ERR_ARG.  The mesh must already be on the current device from an earlier device
- *   call (uploading allocates), else DGC_ERR_ARG.
+ *   Limits: dgc_workspace_size(mesh, prec) must not exceed 16 MiB (16,777,216 bytes):
+ *   e.g. up to about 24,800 triangles at p = 3 and 73,500 at p = 1 in the FP32-mixed
+ *   form, 26,000 and 85,500 in FP64; larger meshes get DGC_ERR_ARG.  The mesh must already be
+ *   on the current device from an earlier device call (uploading allocates), else
+ *   DGC_ERR_ARG.
+ *   When the 16 MiB is reserved: at the first mesh upload on each device (the first
+ *   device call on a mesh: dgc_import_state, dgc_rhs, dgc_cfl_dt, dgc_rk_step, ...),
+ *   which loads the library's module holding the array; from then on every such GPU
+ *   holds it until the process exits, and this call only reads its cached address.
+ *   (Under the CUDA driver's lazy module loading, each kernel's code is still loaded on
+ *   its first launch; a caller that fixes its footprint makes one step first.)
  *   The array is shared by every call on a device and keeps the last call's contents
  *   (each call writes what it reads first; dt_dev and the CFL minimum are reset per call).
  *   Calls whose work overlaps on the GPU (two streams, or two meshes at once) race on
- *   the array: serialise them.  The first call on each device looks up the array's device
- *   address (a CUDA runtime query); make that first call before any stream capture.
- *   Every GPU that loads the library holds the 16 MiB until the process exits. */
+ *   the array: serialise them.  A context reset (cudaDeviceReset) frees the array with
+ *   every other device buffer of the library: destroy the meshes before one. */
 dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl,
                               double* dt_dev, void* stream);
 

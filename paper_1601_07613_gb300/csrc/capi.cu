@@ -109,6 +109,12 @@ void parallel_for(int64_t n, F&& f) {
 std::mutex g_tab_mu;
 std::set<std::pair<int, int>> g_tab_done;  // (device, dim*16 + p)
 
+// Device address of the allocation-free step's static array on device dev
+// (defined with the step below).  load = true looks it up on first use, which
+// loads the module that holds the array and so reserves its device memory;
+// load = false only returns the address cached by an earlier lookup.
+void* static_scratch(int dev, bool load);
+
 template <typename T>
 T* dalloc(int64_t n) {
   T* p = nullptr;
@@ -219,6 +225,10 @@ void upload(Mesh& m) {
       g_tab_done.insert(key);
     }
   }
+  // reserve the allocation-free step's array on this device now, in a call
+  // that allocates anyway: the lookup loads the module that holds it (under
+  // lazy module loading nothing else would before the first static step)
+  static_scratch(dev, true);
   m.dev = d.release();
   m.dirty = false;
 }
@@ -1077,8 +1087,10 @@ void dgc_destroy(dgc_mesh* mesh) {
 // ---------------------------------------------------------------------------
 // Allocation-free RK step.  Its workspace (stage state, FP32 record, rhs) and
 // the CFL estimates live in one file-scope device array, so the call needs no
-// buffer from the caller and allocates nothing.  Every GPU that loads the
-// library holds the array until the process exits.
+// buffer from the caller and allocates nothing.  The array's device memory is
+// reserved when this file's module is loaded on a device, which the first mesh
+// upload on that device forces (upload() looks the address up); every GPU the
+// library has uploaded a mesh to holds it until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1089,13 +1101,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
-void* static_scratch(int dev) {
+// In host code the array's name is only a host-side stand-in, so its address
+// is looked up once per device (with that device current) and cached.  A
+// context reset (cudaDeviceReset) frees it with every other device buffer the
+// library holds; meshes must be destroyed before one and re-created after.
+void* static_scratch(int dev, bool load) {
   if (dev < 0 || dev >= kMaxDevices) throw Error{DGC_ERR_UNSUPPORTED, "device index out of range"};
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_addr[dev]) {
+    if (!load) throw Error{DGC_ERR_ARG, "the static array is not reserved on this device: upload a mesh first"};
     void* p = nullptr;
     DGC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
     g_static_addr[dev] = p;
@@ -1123,7 +1137,7 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
     // uploading the mesh would allocate: an earlier device call must have done it
     require(m.dev != nullptr && !m.dirty && m.dev->device == dev,
             "mesh not on this device yet: make one device call on it first (e.g. dgc_cfl_dt)");
-    char* base = static_cast<char*>(static_scratch(dev));
+    char* base = static_cast<char*>(static_scratch(dev, false));  // reserved by the upload
     const Workspace w = carve(m, prec, base);
     DeviceMesh dcopy = *m.dev;  // the same mesh arrays, CFL estimates in the static array
     dcopy.cfl_est = w.est;

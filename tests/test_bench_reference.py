@@ -22,3 +22,14 @@ def test_reference_arm_prints_one_json_line():
     assert d["config"]["elements"] == 2 * 24 * 24
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_whole_mesh_on_all_cores():
+    """--ref-elements 0 (the default): every step is one whole right-hand side,
+    timed on the oracle's threaded build with all host cores."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "16", "--steps", "2",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][0])
+    assert d["config"]["step"] == "one oracle right-hand side of all elements"
+    assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))

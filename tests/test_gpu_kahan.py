@@ -13,6 +13,7 @@ import pytest
 
 from paper_1601_07613_gb300 import dgc
 from paper_1601_07613_gb300 import workloads as W
+from _parity import check, rel
 
 pytestmark = pytest.mark.gpu
 KAHAN, MIXED, FP64 = dgc.DGC_FP32_KAHAN, dgc.DGC_FP32_MIXED, dgc.DGC_FP64
@@ -25,10 +26,6 @@ def torch_dev():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     dgc.lib()
     return torch, torch.device("cuda:0")
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 class K:
@@ -97,8 +94,7 @@ def test_kahan_rhs_matches_oracle(torch_dev, oracle_mod, p, kind):
     run = K(torch_dev, mi, p)
     run.load(c)
     ref = om.rhs(p, c)
-    e = rel(run.rhs(KAHAN), ref)
-    assert e < 1e-5, e
+    check(run.rhs(KAHAN), ref, 1e-5)
     run.close()
 
 
@@ -113,8 +109,7 @@ def test_kahan_and_mixed_rk_step_match_oracle(torch_dev, oracle_mod, p, fuse):
         run.load(c)
         got, dt = run.rk(prec, 0.3)
         assert abs(dt - dt_ref) < 1e-12 * dt_ref
-        e = rel(got - c, ref - c)
-        assert e < 1e-5, (prec, e)
+        check(got - c, ref - c, 1e-5, f"prec {prec}")
     run.close()
 
 
@@ -134,9 +129,11 @@ def test_kahan_tracks_fp64_over_many_small_steps(torch_dev, oracle_mod):
     gm, _ = run.rk(MIXED, 0.02, steps=200)
     ek, em = rel(gk - c, ref - c), rel(gm - c, ref - c)
     print(f"200 small steps: du rel L2 Kahan {ek:.2e}, mixed {em:.2e}")
-    assert ek < 1e-5 and em < 1e-5
+    check(gk - c, ref - c, 1e-5)
+    check(gm - c, ref - c, 1e-5)
     # the whole state: both within a few FP32 ulps of the FP64 run (not drifting)
-    assert rel(gk, ref) < 1e-7 and rel(gm, ref) < 1e-7
+    check(gk, ref, 1e-7)
+    check(gm, ref, 1e-7)
     run.close()
 
 

@@ -6,7 +6,9 @@ running -- so they cannot hand dgc_rk_step the workspace it needs.
 dgc_rk_step_static takes that workspace from a fixed 16 MiB array the library
 holds on the device.  This file checks, through the C ABI, that two steps in a
 row give the same state and time step as the regular entry point (within the
-tolerances of the other RK tests), that a mesh not yet on the device and a mesh
+tolerances of the other RK tests), that the static calls leave the device's free
+memory unchanged (the array is reserved by the mesh upload, with the module
+loading left at the CUDA default), that a mesh not yet on the device and a mesh
 too large for the array are refused, and it runs the same way alone in a fresh
 process or after the rest of the suite (the file is collected last).
 """
@@ -16,6 +18,7 @@ import pytest
 
 from paper_1601_07613_gb300 import dgc
 from paper_1601_07613_gb300 import workloads as W
+from _parity import check
 
 pytestmark = pytest.mark.gpu
 
@@ -27,10 +30,6 @@ def torch_dev():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     dgc.lib()
     return torch, torch.device("cuda:0")
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 @pytest.mark.parametrize("prec,tol", [(dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)])
@@ -48,14 +47,22 @@ def test_static_step_matches_regular_step(torch_dev, prec, tol):
     ws = torch.empty(dgc.dgc_workspace_size(mesh.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
     dta = torch.zeros(1, dtype=torch.float64, device=dev)
     dtb = torch.zeros(1, dtype=torch.float64, device=dev)
-    for _ in range(2):  # two calls in a row
+    for step in range(2):  # two calls in a row
         dgc.dgc_rk_step(mesh.h, prec, a, 0.3, dta, ws)
+        torch.cuda.synchronize()
+        # the regular step has launched every kernel the static one uses, so the
+        # driver has loaded their code: the static call itself must not change
+        # the device's free memory (the array was reserved at the mesh upload)
+        free_before = torch.cuda.mem_get_info()[0]
+        torch_before = torch.cuda.memory_allocated()
         dgc.dgc_rk_step_static(mesh.h, prec, b, 0.3, dtb)
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before, f"call {step}: free device memory changed"
+        assert torch.cuda.memory_allocated() == torch_before
         ua = dgc.dgc_export_state(mesh.h, a)
         ub = dgc.dgc_export_state(mesh.h, b)
         assert abs(dtb.item() - dta.item()) <= 1e-13 * dta.item()
-        assert _rel(ub - c0, ua - c0) < tol
+        check(ub - c0, ua - c0, tol, f"call {step}")
     mesh.close()
 
 
