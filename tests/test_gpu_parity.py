@@ -266,6 +266,7 @@ def test_full_size_rhs_sampled(big, big_exact, oracle_mod):
     got64 = run.rhs(dgc.DGC_FP64)[sample]
     got32 = run.rhs(dgc.DGC_FP32_MIXED)[sample]
     e64, eo = fp64_vs_exact(got64, ref, refx, 1e-12, "full size RHS")
+    assert e64 < 1e-12, e64  # the headline configuration meets the literal bound against the exact result
     e32, _ = check(got32, ref, 1e-5, "full size FP32-mixed RHS")
     print(f"full size: FP64 rel L2 vs exact {e64:.3e} (FP64 oracle vs exact {eo:.3e}, GPU vs FP64 oracle "
           f"{rel(got64, ref):.3e}), FP32-mixed {e32:.3e}")
