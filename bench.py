@@ -51,8 +51,29 @@ def peaks():
 
 
 # FP64 peak derived from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM
-# (2 DFMA/clk/SM, the GB300's FP64 rate) x 2.07 GHz.
+# (2 DFMA/clk/SM, the GB300's FP64 rate) x 2.07 GHz; the roofline uses the
+# measured figure (fp64_peak_tflops) and keeps this one beside it.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+def fp64_peak_tflops(torch, dev, n: int = 4096, reps: int = 3) -> float:
+    """Measured FP64 rate of this GPU: a library FP64 GEMM (torch float64 matmul,
+    cuBLAS DGEMM) of n^3, best of reps, CUDA events; 2 n^3 flops."""
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e))
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 class Clocks:
@@ -219,6 +240,8 @@ def run_dgc(args, rank, world, local_rank):
     cfg, mi, mesh, c_host, prep = setup_workload(dgc, torch, dev, args.n)
     if args.epb:
         dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_EDGES_PER_BLOCK, args.epb)
+    if args.tpe:
+        dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_THREADS_PER_EDGE, args.tpe)
     if args.no_pdl:
         dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_PDL, 0)
     info = mesh.info
@@ -234,6 +257,18 @@ def run_dgc(args, rank, world, local_rank):
 
     def step(prec):
         dgc.dgc_rk_step(mesh.h, prec, c, cfg["cfl"], dt, ws)
+
+    # ---- tiles: the library's autotuner (edges per block x threads per edge of the
+    # first, middle and last colors) on a scratch copy of the state, untimed
+    tiles = None
+    if not (args.no_autotune or args.epb or args.tpe):
+        scratch = torch.empty_like(c)
+        dgc.dgc_import_state(mesh.h, c_host, scratch)
+        tiles, tune_ms = dgc.dgc_autotune(mesh.h, mixed, scratch, cfg["cfl"], dt, ws, reps=3)
+        del scratch
+    else:
+        tiles = {k: dgc.dgc_get_tile(mesh.h, kc) for k, kc in (("first", dgc.DGC_K_FIRST),
+                                                                ("color", dgc.DGC_K_COLOR), ("last", dgc.DGC_K_LAST))}
 
     # ---- headline: FP32-mixed RK step -------------------------------------------------
     for _ in range(args.warmup):
@@ -324,10 +359,14 @@ def run_dgc(args, rank, world, local_rank):
         ms_plain = time_steps(torch, lambda: step(mixed), args.steps, stream)
         dgc.dgc_set_option(mesh.h, dgc.DGC_OPT_PDL, 0 if args.no_pdl else 1)
         variants["rk_fp32mixed_plain_launch"] = {"value": 3 * dofs / (ms_plain * 1e-3), "ms_per_step": round(ms_plain, 4)}
+        p64 = fp64_peak_tflops(torch, dev)
         variants["rk_fp64"] = {"value": 3 * dofs / (ms64 * 1e-3), "ms_per_step": round(ms64, 4),
                                "roofline": {"bound": "alu", "achieved": round(fl / (ms64 * 1e-3) / 1e12, 3),
-                                            "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
-                                            "frac": round(fl / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)}}
+                                            "peak": round(p64, 3), "unit": "TFLOP/s",
+                                            "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 (torch)",
+                                            "frac": round(fl / (ms64 * 1e-3) / 1e12 / p64, 3),
+                                            "derived_peak": round(FP64_PEAK_TFLOPS, 3),
+                                            "frac_of_derived": round(fl / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)}}
         # ---- Kahan form: FP32 pair state, compensated update --------------------------
         kst = torch.empty(dgc.dgc_state_bytes(mesh.h, dgc.DGC_FP32_KAHAN) // 4, dtype=torch.float32, device=dev)
         wsk = torch.empty(dgc.dgc_workspace_size(mesh.h, dgc.DGC_FP32_KAHAN) // 8 + 64, dtype=torch.float64,
@@ -384,7 +423,8 @@ def run_dgc(args, rank, world, local_rank):
                    "dofs": dofs, "step": "SSP-RK3 (3 RHS) with FP64 CFL reduction",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "no flush: state 335 MB FP64 + 168 MB FP32 copy per replica exceed the 129 MB L2",
-                   "host_prep": prep},
+                   "host_prep": prep,
+                   "tiles": {k: {"edges_per_block": v[0], "threads_per_edge": v[1]} for k, v in tiles.items()}},
         "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks, "e2e": e2e, "variants": variants,
     }
@@ -473,14 +513,16 @@ def run_batched(dgc, torch, dev, stream, args):
         for prec, tag in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
             ws = torch.empty(dgc.dgc_batch_workspace_size(batch, prec) // 8 + 64, dtype=torch.float64, device=dev)
             dts = torch.zeros(len(meshes), dtype=torch.float64, device=dev)
-            best, tune = dgc.dgc_batch_autotune(batch, prec, cdev, 0.3, dts, ws, reps=3 if tag == "fp32mixed" else 1)
+            tiles_b, tune_ms = dgc.dgc_batch_autotune(batch, prec, cdev, 0.3, dts, ws,
+                                                      reps=3 if tag == "fp32mixed" else 1)
             k = max(3, args.steps) if tag == "fp32mixed" else 3
             ms = time_steps(torch, lambda: dgc.dgc_batch_rk_step(batch, prec, cdev, 0.3, dts, ws), k, stream)
             out[f"batched_{tag}"] = {
                 "value": 3 * dofs / (ms * 1e-3), "ms_per_step": round(ms, 4), "meshes": len(meshes),
                 "elements": sum(m.info["ne"] for m in meshes), "dofs": dofs,
                 "launches_per_step": dgc.dgc_batch_launch_count(batch), "graph": True,
-                "edges_per_block": best, "autotune_ms": {str(e): round(v, 4) for e, v in tune.items()}}
+                "tiles": {k: {"edges_per_block": v[0], "threads_per_edge": v[1]} for k, v in tiles_b.items()},
+                "autotune_best_ms": round(tune_ms, 4)}
             del ws
     finally:
         dgc.dgc_batch_destroy(batch)
@@ -744,10 +786,13 @@ def main():
     ap.add_argument("--ref-elements", type=int, default=0,
                     help="oracle elements per reference step (0 = the whole mesh)")
     ap.add_argument("--epb", type=int, default=0, help="edges per block of the surface kernels (0 = library default)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tiles")
+    ap.add_argument("--tpe", type=int, default=0, help="threads per edge of the FP32 surface kernels (0 = library "
+                    "default: 2)")
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
-    ap.add_argument("--only", choices=["tet", "nonconforming", "quad"],
+    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "batch"],
                     help="time only that one of the other workloads (its variants entry, printed alone)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -758,8 +803,11 @@ def main():
 
         dgc.lib()
         dev = torch.device("cuda:0")
-        print(json.dumps(run_other_meshes(dgc, torch, dev, torch.cuda.current_stream(), args, only=args.only)),
-              flush=True)
+        st = torch.cuda.current_stream()
+        if args.only == "batch":
+            print(json.dumps(run_batched(dgc, torch, dev, st, args)), flush=True)
+        else:
+            print(json.dumps(run_other_meshes(dgc, torch, dev, st, args, only=args.only)), flush=True)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

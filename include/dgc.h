@@ -75,7 +75,12 @@ typedef enum {
                                   (closed conforming meshes only); 0: separate volume
                                   kernel, every color read-modify-writes rhs (Alg. 1) */
   DGC_OPT_EDGES_PER_BLOCK = 1, /* surface-kernel tile: edges per thread block (16..128, x16) */
-  DGC_OPT_THREADS_PER_EDGE = 2, /* 2 (one thread per edge side); reserved for tuning */
+  DGC_OPT_THREADS_PER_EDGE = 2, /* FP32 colored kernels of the RK steps on triangle meshes:
+                                   2 (default: one lane per edge side) or 4 (two lanes per side,
+                                   which split the edge's quadrature points, the volume integral's
+                                   points and the modes of the epilogue); threads per edge x edges
+                                   per block <= 256.  The FP64 kernels, dgc_rhs and the
+                                   comparators use 2.  Results differ by FP32 summation order. */
   DGC_OPT_PROFILE = 3,          /* 1: record a CUDA event pair around every kernel launch, on
                                    the launch stream, for dgc_profile_collect; 0 (default): off */
   DGC_OPT_GRAPH = 4,            /* batches: 1 (default) capture the step in a CUDA graph on the
@@ -331,9 +336,14 @@ dgc_status dgc_last_launch_count(const dgc_mesh* mesh, int64_t* launches);
  *   dgc_batch_workspace_size() bytes, 256-byte aligned.  The first call with a new set of
  *   buffers uploads the meshes and the tile tables synchronously (make it before any
  *   capture); later calls are asynchronous.  Results equal dgc_rk_step on each mesh.
- *   dgc_batch_autotune: runs 1 + reps steps per tile size (16, 32, 64, 128 edges per
- *   block) -- the states advance -- keeps the fastest and returns it, with the measured
- *   ms per step in ms_per_step[4] (may be NULL). */
+ *   dgc_batch_autotune: coordinate search over the tiles of the last, middle and first
+ *   colors' launches (edges per block 16, 32, 64, 128 x threads per edge 2, or 4 in the
+ *   FP32-mixed form; at most 256 threads per block), each candidate timed over 1 + reps
+ *   steps -- the states advance -- keeping the fastest; the batch keeps the chosen tiles
+ *   and they are written to edges_per_block[3] / threads_per_edge[3] (first, middle,
+ *   last color), the best ms per step to *ms_per_step (may be NULL).
+ *   DGC_OPT_EDGES_PER_BLOCK and DGC_OPT_THREADS_PER_EDGE (dgc_batch_set_option) set the
+ *   tile of all three. */
 dgc_status dgc_batch_create(int n, dgc_mesh* const* meshes, dgc_batch** out);
 dgc_status dgc_batch_workspace_size(const dgc_batch* batch, dgc_prec prec, int64_t* bytes);
 dgc_status dgc_batch_set_option(dgc_batch* batch, dgc_option opt, int64_t value);
@@ -342,9 +352,33 @@ dgc_status dgc_batch_rk_step(dgc_batch* batch, dgc_prec prec, double* const* c_d
                              void* stream);
 dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_devs, double cfl,
                               double* dt_devs, void* workspace_dev, int64_t workspace_bytes,
-                              int reps, void* stream, int64_t* best_epb, double* ms_per_step);
+                              int reps, void* stream, int* edges_per_block, int* threads_per_edge,
+                              double* ms_per_step);
 dgc_status dgc_batch_launch_count(const dgc_batch* batch, int64_t* launches);
 void dgc_batch_destroy(dgc_batch* batch);
+
+/* Surface-kernel tile of one kernel class of the triangle RK steps (no paper counterpart:
+ * launch shape only).  kclass: DGC_K_FIRST (first color, with the volume integral),
+ * DGC_K_COLOR (middle colors; also the comparators' and dgc_rhs's colors), DGC_K_LAST
+ * (last color with the stage update).  edges_per_block 16..128 (a multiple of 16),
+ * threads_per_edge 2 or 4 (4: triangle meshes, FP32 forms of dgc_rk_step /
+ * dgc_rk_step_static; two lanes per edge side split the edge's quadrature points, the
+ * volume integral's points and the epilogue's modes), at most 256 threads per block;
+ * else DGC_ERR_ARG (DGC_ERR_UNSUPPORTED for 4 on other element types).  The options
+ * DGC_OPT_EDGES_PER_BLOCK / DGC_OPT_THREADS_PER_EDGE set all three classes. */
+dgc_status dgc_set_tile(dgc_mesh* mesh, int kclass, int edges_per_block, int threads_per_edge);
+dgc_status dgc_get_tile(const dgc_mesh* mesh, int kclass, int* edges_per_block, int* threads_per_edge);
+
+/* Tile autotuner for one mesh's RK step: coordinate search over the last, middle and
+ * first colors' tiles (edges per block 32 / 64 / 128 x threads per edge 2 / 4 where
+ * allowed), each candidate timed over `reps` steps (after one untimed step) with CUDA
+ * events on `stream`, keeping the fastest; the mesh keeps the chosen tiles.  The steps
+ * advance c_dev (pass a scratch copy of the state).  Writes the tiles of FIRST, COLOR,
+ * LAST into edges_per_block[3] / threads_per_edge[3] and the best time per step (ms, may
+ * be NULL).  Arguments as dgc_rk_step. */
+dgc_status dgc_autotune(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl, double* dt_dev,
+                        void* workspace_dev, int64_t workspace_bytes, int reps, void* stream,
+                        int* edges_per_block, int* threads_per_edge, double* ms_per_step);
 
 /* Thread-local message of the last error (empty string if none). */
 const char* dgc_last_error(void);

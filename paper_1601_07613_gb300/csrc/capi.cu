@@ -242,6 +242,15 @@ const Mesh& checked(const dgc_mesh* mesh) {
   return *reinterpret_cast<const Mesh*>(mesh);
 }
 
+// A surface-kernel tile: 16..128 edges per block (a multiple of 16), 2 or 4
+// threads per edge (4: triangle meshes), at most 256 threads per block.
+void check_tile(const Mesh& m, int epb, int tpe) {
+  require(epb >= 16 && epb <= 128 && epb % 16 == 0, "edges per block must be 16..128, a multiple of 16");
+  require(tpe == 2 || tpe == 4, "threads per edge must be 2 or 4");
+  require(tpe == 2 || (m.dim == 2 && !m.quad), "4 threads per edge: triangle meshes only", DGC_ERR_UNSUPPORTED);
+  require(tpe * epb <= 256, "threads per edge x edges per block must not exceed 256");
+}
+
 // The checks every device call on a mesh makes first.
 void require_device_ready(const Mesh& m) {
   require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
@@ -263,6 +272,10 @@ Ctx make_ctx(const Mesh& m, const DeviceMesh* d, void* stream) {
   x.ne = m.ne;
   x.ns = m.ns;
   x.epb = m.edges_per_block;
+  for (int c = 0; c < 3; ++c) {
+    x.tile_epb[c] = m.tile_epb[c];
+    x.tile_tpe[c] = m.tile_tpe[c];
+  }
   x.d = d;
   x.shadow.M = m.M;
   x.shadow.np = m.np;
@@ -976,6 +989,92 @@ dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_, 
   });
 }
 
+namespace {
+int tile_index(int kclass) {
+  require(kclass == DGC_K_FIRST || kclass == DGC_K_COLOR || kclass == DGC_K_LAST,
+          "tile class must be DGC_K_FIRST, DGC_K_COLOR or DGC_K_LAST");
+  return kclass == DGC_K_FIRST ? 0 : kclass == DGC_K_COLOR ? 1 : 2;
+}
+}  // namespace
+
+dgc_status dgc_set_tile(dgc_mesh* mesh, int kclass, int edges_per_block, int threads_per_edge) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    const int i = tile_index(kclass);
+    check_tile(m, edges_per_block, threads_per_edge);
+    m.tile_epb[i] = edges_per_block;
+    m.tile_tpe[i] = threads_per_edge;
+  });
+}
+
+dgc_status dgc_get_tile(const dgc_mesh* mesh, int kclass, int* edges_per_block, int* threads_per_edge) {
+  return guarded([&] {
+    const Mesh& m = checked(mesh);
+    require(edges_per_block != nullptr && threads_per_edge != nullptr, "null output");
+    const int i = tile_index(kclass);
+    *edges_per_block = m.tile_epb[i];
+    *threads_per_edge = m.tile_tpe[i];
+  });
+}
+
+dgc_status dgc_autotune(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_, double* dt_dev,
+                        void* workspace_dev, int64_t workspace_size, int reps, void* stream, int* edges_per_block,
+                        int* threads_per_edge, double* ms_per_step) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(reps > 0 && edges_per_block != nullptr && threads_per_edge != nullptr, "bad argument");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool tri32 = m.dim == 2 && !m.quad && prec != DGC_FP64;
+    cudaEvent_t e0, e1;
+    DGC_CUDA(cudaEventCreate(&e0));
+    DGC_CUDA(cudaEventCreate(&e1));
+    auto time_steps = [&]() {
+      dgc_status s = dgc_rk_step(mesh, prec, c_dev, cfl_, dt_dev, workspace_dev, workspace_size, stream);
+      if (s != DGC_OK) throw Error{s, g_err};
+      DGC_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) {
+        s = dgc_rk_step(mesh, prec, c_dev, cfl_, dt_dev, workspace_dev, workspace_size, stream);
+        if (s != DGC_OK) throw Error{s, g_err};
+      }
+      DGC_CUDA(cudaEventRecord(e1, st));
+      DGC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      DGC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return (double)ms / reps;
+    };
+    // coordinate search, one kernel class at a time (last, middle, first
+    // color): every tile of the candidate set with the other classes fixed
+    double best = time_steps();
+    const int cls[3] = {2, 1, 0};
+    for (int ci : cls) {
+      int be = m.tile_epb[ci], bt = m.tile_tpe[ci];
+      for (int tpe : {2, 4}) {
+        if (tpe == 4 && !tri32) continue;
+        for (int epb : {32, 64, 128}) {
+          if (tpe * epb > 256 || (epb == be && tpe == bt)) continue;
+          m.tile_epb[ci] = epb;
+          m.tile_tpe[ci] = tpe;
+          const double t = time_steps();
+          if (t < best) {
+            best = t;
+            be = epb;
+            bt = tpe;
+          }
+        }
+      }
+      m.tile_epb[ci] = be;
+      m.tile_tpe[ci] = bt;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < 3; ++i) {
+      edges_per_block[i] = m.tile_epb[i];
+      threads_per_edge[i] = m.tile_tpe[i];
+    }
+    if (ms_per_step) *ms_per_step = best;
+  });
+}
+
 dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, double* rhs_dev, void* stream) {
   return guarded([&] {
     Mesh& m = checked(mesh);
@@ -1027,12 +1126,13 @@ dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value) {
         m.fuse = value != 0;
         break;
       case DGC_OPT_EDGES_PER_BLOCK:
-        require(value >= 16 && value <= 128 && value % 16 == 0, "edges per block must be 16..128, a multiple of 16");
+        for (int c = 0; c < 3; ++c) check_tile(m, (int)value, m.tile_tpe[c]);
         m.edges_per_block = (int)value;
+        for (int c = 0; c < 3; ++c) m.tile_epb[c] = (int)value;
         break;
       case DGC_OPT_THREADS_PER_EDGE:
-        require(value == 2, "this build uses two threads per edge");
-        m.threads_per_edge = (int)value;
+        for (int c = 0; c < 3; ++c) check_tile(m, m.tile_epb[c], (int)value);
+        for (int c = 0; c < 3; ++c) m.tile_tpe[c] = (int)value;
         break;
       case DGC_OPT_PROFILE:
         m.profile = value != 0;
@@ -1157,7 +1257,9 @@ extern "C" dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_
 // ---------------------------------------------------------------------------
 struct dgc_batch {
   std::vector<Mesh*> meshes;
-  int epb = 64;
+  int epb = 64;                    // DGC_OPT_EDGES_PER_BLOCK (all classes)
+  int tepb[3] = {64, 64, 64};      // tile of the first, middle, last color: edges per block
+  int ttpe[3] = {2, 2, 2};         // and threads per edge (4: FP32-mixed form only)
   bool use_graph = true;
   int device = -1;
   // device tables, rebuilt when the call's buffers or the tile size change
@@ -1168,7 +1270,7 @@ struct dgc_batch {
   std::vector<double*> key_c;
   double* key_dt = nullptr;
   void* key_ws = nullptr;
-  int key_prec = -1, key_epb = -1;
+  int key_prec = -1, key_epb[3] = {-1, -1, -1}, key_tpe[3] = {-1, -1, -1};
   cudaGraphExec_t exec = nullptr;
   double graph_cfl = 0.0;
   // the step is captured on this library-owned stream (capture is not allowed
@@ -1197,10 +1299,14 @@ int64_t batch_ws_bytes(const dgc_batch& b, dgc_prec prec) {
   return t;
 }
 
+// tile class of color c of C: first, middle, last
+int batch_class(int c, int C) { return c == 1 ? 0 : c == C ? 2 : 1; }
+
 // descriptors and tiles for this call's buffers (host work + one synchronous upload)
 void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* dt_devs, void* ws) {
   const int n = (int)b.meshes.size();
-  bool same = b.dmeshes && b.key_prec == (int)prec && b.key_dt == dt_devs && b.key_ws == ws && b.key_epb == b.epb;
+  bool same = b.dmeshes && b.key_prec == (int)prec && b.key_dt == dt_devs && b.key_ws == ws &&
+              std::equal(b.tepb, b.tepb + 3, b.key_epb) && std::equal(b.ttpe, b.ttpe + 3, b.key_tpe);
   for (int i = 0; same && i < n; ++i) same = b.key_c[i] == c_devs[i];
   if (same) return;
   batch_release(b);
@@ -1235,10 +1341,11 @@ void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* d
   b.ncolors = b.meshes[0]->ncolors;
   b.tile_off[0] = 0;
   for (int c = 1; c <= b.ncolors; ++c) {
+    const int epb = b.tepb[batch_class(c, b.ncolors)];
     for (int i : order) {
       const Mesh& m = *b.meshes[i];
-      for (int64_t s = m.color_off[c - 1]; s < m.color_off[c]; s += b.epb)
-        tiles.push_back({i, m.p, s, std::min<int64_t>(s + b.epb, m.color_off[c])});
+      for (int64_t s = m.color_off[c - 1]; s < m.color_off[c]; s += epb)
+        tiles.push_back({i, m.p, s, std::min<int64_t>(s + epb, m.color_off[c])});
     }
     b.tile_off[c] = (int)tiles.size();
   }
@@ -1255,14 +1362,14 @@ void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* d
   b.key_dt = dt_devs;
   b.key_ws = ws;
   b.key_prec = (int)prec;
-  b.key_epb = b.epb;
+  std::copy(b.tepb, b.tepb + 3, b.key_epb);
+  std::copy(b.ttpe, b.ttpe + 3, b.key_tpe);
 }
 
 // the launches of one step: reset, CFL (2), then per stage the three colors
 int64_t batch_enqueue(dgc_batch& b, dgc_prec prec, double cfl_, cudaStream_t st) {
   const bool mixed = prec == DGC_FP32_MIXED;
   const int n = (int)b.meshes.size(), C = b.ncolors;
-  const int threads = 2 * b.epb;
   int64_t launches = batch_init(st, b.dmeshes, n);
   const BatchTile* et = b.dtiles + b.tile_off[C];
   launches += batch_cfl(st, b.dmeshes, et, b.tile_off[C + 1] - b.tile_off[C], cfl_, mixed);
@@ -1270,8 +1377,9 @@ int64_t batch_enqueue(dgc_batch& b, dgc_prec prec, double cfl_, cudaStream_t st)
   for (int s = 0; s < 3; ++s)
     for (int c = 1; c <= C; ++c) {
       const SurfMode mode = c == 1 ? SURF_FIRST : (c == C ? SURF_LAST : SURF_RMW);
+      const int k = batch_class(c, C), tpe = mixed ? b.ttpe[k] : 2;
       const int r = batch_surf(st, b.dmeshes, b.dtiles + b.tile_off[c - 1], b.tile_off[c] - b.tile_off[c - 1], s,
-                               A0[s], B0[s], mode, mixed, threads);
+                               A0[s], B0[s], mode, mixed, tpe * b.tepb[k], tpe);
       if (r < 0) throw Error{DGC_ERR_UNSUPPORTED, "no batched kernel for this configuration"};
       launches += r;
     }
@@ -1316,7 +1424,17 @@ dgc_status dgc_batch_set_option(dgc_batch* batch, dgc_option opt, int64_t value)
     dgc_batch& b = checked_batch(batch);
     if (opt == DGC_OPT_EDGES_PER_BLOCK) {
       require(value >= 16 && value <= 128 && value % 16 == 0, "edges per block must be 16..128, a multiple of 16");
+      for (int k = 0; k < 3; ++k) require(b.ttpe[k] * value <= 256, "threads per edge x edges per block > 256");
       b.epb = (int)value;
+      for (int k = 0; k < 3; ++k) b.tepb[k] = (int)value;
+      if (b.exec) cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    } else if (opt == DGC_OPT_THREADS_PER_EDGE) {
+      require(value == 2 || value == 4, "threads per edge must be 2 or 4");
+      for (int k = 0; k < 3; ++k) require(value * b.tepb[k] <= 256, "threads per edge x edges per block > 256");
+      for (int k = 0; k < 3; ++k) b.ttpe[k] = (int)value;
+      if (b.exec) cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
     } else if (opt == DGC_OPT_GRAPH) {
       b.use_graph = value != 0;
       if (b.exec) cudaGraphExecDestroy(b.exec);
@@ -1380,19 +1498,15 @@ dgc_status dgc_batch_rk_step(dgc_batch* batch, dgc_prec prec, double* const* c_d
 
 dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_devs, double cfl_, double* dt_devs,
                               void* workspace_dev, int64_t workspace_size, int reps, void* stream,
-                              int64_t* best_epb, double* ms_per_step) {
+                              int* edges_per_block, int* threads_per_edge, double* ms_per_step) {
   return guarded([&] {
     dgc_batch& b = checked_batch(batch);
-    require(reps > 0 && best_epb != nullptr, "bad argument");
-    const int cand[4] = {16, 32, 64, 128};
+    require(reps > 0 && edges_per_block != nullptr && threads_per_edge != nullptr, "bad argument");
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     DGC_CUDA(cudaEventCreate(&e0));
     DGC_CUDA(cudaEventCreate(&e1));
-    double best = 1e300;
-    int besti = 0;
-    for (int k = 0; k < 4; ++k) {
-      b.epb = cand[k];
+    auto time_steps = [&]() {
       if (b.exec) cudaGraphExecDestroy(b.exec);
       b.exec = nullptr;
       dgc_status s = dgc_batch_rk_step(batch, prec, c_devs, cfl_, dt_devs, workspace_dev, workspace_size, stream);
@@ -1406,19 +1520,39 @@ dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_
       DGC_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
       DGC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      const double per = ms / reps;
-      if (ms_per_step) ms_per_step[k] = per;
-      if (per < best) {
-        best = per;
-        besti = k;
+      return (double)ms / reps;
+    };
+    // coordinate search over the last, middle and first colors' tiles: edges
+    // per block 16..128 x threads per edge 2 or 4 (FP32-mixed form)
+    double best = time_steps();
+    for (int k : {2, 1, 0}) {
+      int be = b.tepb[k], bt = b.ttpe[k];
+      for (int tpe : {2, 4}) {
+        if (tpe == 4 && prec != DGC_FP32_MIXED) continue;
+        for (int epb : {16, 32, 64, 128}) {
+          if (tpe * epb > 256 || (epb == be && tpe == bt)) continue;
+          b.tepb[k] = epb;
+          b.ttpe[k] = tpe;
+          const double t = time_steps();
+          if (t < best) {
+            best = t;
+            be = epb;
+            bt = tpe;
+          }
+        }
       }
+      b.tepb[k] = be;
+      b.ttpe[k] = bt;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b.epb = cand[besti];
     if (b.exec) cudaGraphExecDestroy(b.exec);
     b.exec = nullptr;
-    *best_epb = b.epb;
+    for (int k = 0; k < 3; ++k) {
+      edges_per_block[k] = b.tepb[k];
+      threads_per_edge[k] = b.ttpe[k];
+    }
+    if (ms_per_step) *ms_per_step = best;
   });
 }
 

@@ -63,6 +63,11 @@ struct Ctx {
   ShadowLayout shadow;
   int64_t ne = 0, ns = 0;
   int epb = 128;
+  // triangle kernels: edges per block and threads per edge (2: one lane per
+  // edge side; 4: two lanes per side, FP32 right-hand sides of an RK step) of
+  // the first, middle and last colors
+  int tile_epb[3] = {128, 128, 128};
+  int tile_tpe[3] = {2, 2, 2};
   const DeviceMesh* d = nullptr;
   cudaStream_t st = nullptr;
   bool pdl = false;  // launch the surface and CFL kernels with programmatic dependent launch
@@ -134,7 +139,7 @@ void tri_upload_tables(int p, const RefTables& T);
 int batch_init(cudaStream_t st, const BatchMeshDev* d, int n);
 int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, double cfl, bool mixed);
 int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage, double a0,
-               double b0, SurfMode mode, bool mixed, int threads);
+               double b0, SurfMode mode, bool mixed, int threads, int tpe);
 int tri_record_floats(int p);
 // sstride: floats per element of an FP32 state (record or Kahan state); ignored for FP64 states
 // volume kernels cover elements [e0, ne)

@@ -97,8 +97,11 @@ struct Mesh {
   int64_t reached = -1;
   // options
   bool fuse = true;
-  int edges_per_block = 64;
-  int threads_per_edge = 2;
+  int edges_per_block = 64;  // surface-kernel tile of the kernels without a per-class tile
+  // triangle RK steps: tile of the first, middle and last colors' FP32 kernels
+  // (edges per block, threads per edge 2 or 4); dgc_set_tile, dgc_autotune
+  int tile_epb[3] = {64, 64, 64};
+  int tile_tpe[3] = {2, 2, 2};
   bool profile = false;
   bool pdl = true;  // programmatic dependent launch of the RK step's kernels
   void* prof = nullptr;  // event records (capi.cu)

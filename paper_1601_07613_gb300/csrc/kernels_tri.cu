@@ -339,11 +339,12 @@ __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], c
 #define DGC_FFMA2 1
 #endif
 // LAM: also max_q (|u| + c) of the state at the volume points (the CFL estimate
-// of lambda_max_rec, from the same sums), into *lam.
-template <int P, bool LAM = false>
+// of lambda_max_rec, from the same sums), into *lam.  S lanes share an element
+// (S = 2: two lanes per edge side): lane sub takes the points sub, sub + S, ...
+template <int P, bool LAM = false, int S = 1>
 __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRef<2>& R,
                                              const double* __restrict__ ji, float (&acc)[TriDim<P>::NV],
-                                             float* lam = nullptr) {
+                                             float* lam = nullptr, int sub = 0) {
   using D = TriDim<P>;
   constexpr int NP = D::NP;
   const TriTab<float, P>& K = tri_tab<float, P>();
@@ -363,7 +364,7 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
     a23[j - 1] = make_float2(acc[2 * NP + j], acc[3 * NP + j]);
   }
   DGC_UNROLL_Q
-  for (int q = 0; q < D::NQV; ++q) {
+  for (int q = S == 1 ? 0 : sub; q < D::NQV; q += S) {
     float2 d01 = make_float2(B.lo[0], B.lo[1]), d23 = make_float2(B.lo[2], B.lo[3]);
 #pragma unroll
     for (int j = 1; j < NP; ++j) {
@@ -378,11 +379,11 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
       const float pr = 0.4f * (U3 - 0.5f * U0 * q2);
       *lam = fmaxf(*lam, sqrt_fast(q2) + sqrt_fast(1.4f * pr * ir));
     }
-    PertState<2> S;
-    S.init(R, d);
+    PertState<2> PS;
+    PS.init(R, d);
     float Fr[4], Fs[4];
-    pert_flux<2>(R, S, d, nr, thr, Fr);
-    pert_flux<2>(R, S, d, ns, ths, Fs);
+    pert_flux<2>(R, PS, d, nr, thr, Fr);
+    pert_flux<2>(R, PS, d, ns, ths, Fs);
     const float2 r01 = make_float2(Fr[0], Fr[1]), r23 = make_float2(Fr[2], Fr[3]);
     const float2 s01 = make_float2(Fs[0], Fs[1]), s23 = make_float2(Fs[2], Fs[3]);
 #pragma unroll
@@ -400,7 +401,7 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
   }
 #else
   DGC_UNROLL_Q
-  for (int q = 0; q < D::NQV; ++q) {
+  for (int q = S == 1 ? 0 : sub; q < D::NQV; q += S) {
     float d[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -409,11 +410,11 @@ __device__ __forceinline__ void volume_acc32(const PertBlock<P>& B, const PertRe
       for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * B.cd[m][j - 1];
       d[m] = s;
     }
-    PertState<2> S;
-    S.init(R, d);
+    PertState<2> PS;
+    PS.init(R, d);
     float Fr[4], Fs[4];
-    pert_flux<2>(R, S, d, nr, thr, Fr);
-    pert_flux<2>(R, S, d, ns, ths, Fs);
+    pert_flux<2>(R, PS, d, nr, thr, Fr);
+    pert_flux<2>(R, PS, d, ns, ths, Fs);
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -731,13 +732,15 @@ __device__ __forceinline__ void mode_sum(const float4 row, const float (&b)[P + 
 // 0, 1), the FP64 state of the mixed form, in place, u = u0 + (2/3) delta
 // (STG 2), or the Kahan pair state (STG 3).  The modes go in batches of JB
 // whose loads are all issued before the batch's stores, so that a batch costs
-// one memory round trip.  The buffers are distinct arrays.
+// one memory round trip.  The buffers are distinct arrays.  The lane takes the
+// jcnt modes from jbase (all of them with one lane per side; with two lanes per
+// side each takes its share, split at an even mode when stage 2 pairs modes).
 template <int P, int STG>
 __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P + 1][4], const float4* rs,
                                            const float4* __restrict__ part, float4* __restrict__ dp,
                                            const float4* __restrict__ r0, float4* __restrict__ ro,
                                            float4* __restrict__ ks, double* __restrict__ u, double dt,
-                                           double phi0) {
+                                           double phi0, int jbase = 0, int jcnt = TriDim<P>::NP) {
   static_assert(STG >= 0 && STG <= 3, "stage");
   constexpr int NP = TriDim<P>::NP, NF4 = NP + 1;
   // modes per batch: stage 2 of an FP64 state pairs modes (j, j+1) into double2
@@ -745,15 +748,16 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
   constexpr bool PAIRS = NP % 2 == 0, kahan = STG == 3;
   static_assert(STG != 2 || !PAIRS || JB % 2 == 0, "stage 2 pairs modes: even batches");
   const F2 dtp = split_f2(dt);
-  float dk[PAIRS ? 1 : NP][4];  // stage 2, FP64 state, odd NP: every mode's increment
+  float dk[PAIRS ? 1 : NP][4];  // stage 2, FP64 state, odd NP: every mode's increment (jbase = 0)
 #pragma unroll
-  for (int j0 = 0; j0 < NP; j0 += JB) {
+  for (int i0 = 0; i0 < NP; i0 += JB) {
+    if (i0 >= jcnt) break;
     float4 pa[JB], da[JB], ha[JB], la[JB];
-    double2 ua[(JB + 1) / 2][4];  // stage 2, FP64 state: modes (j0 + 2h, j0 + 2h + 1) of variable m
+    double2 ua[(JB + 1) / 2][4];  // stage 2, FP64 state: modes (j + 2h, j + 2h + 1) of variable m
 #pragma unroll
     for (int i = 0; i < JB; ++i) {
-      const int j = j0 + i;
-      if (j >= NP) continue;
+      const int ii = i0 + i, j = jbase + ii;
+      if (ii >= jcnt) continue;
       pa[i] = part[j];
       if (STG >= 1) da[i] = dp[j];
       if (STG == 0 && rs) {
@@ -771,15 +775,15 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
       const double2* a2 = reinterpret_cast<const double2*>(u);
 #pragma unroll
       for (int h = 0; h < JB / 2; ++h)
-        if (j0 + 2 * h < NP)
+        if (i0 + 2 * h < jcnt)
 #pragma unroll
-          for (int m = 0; m < 4; ++m) ua[h][m] = a2[(m * NP + j0 + 2 * h) / 2];
+          for (int m = 0; m < 4; ++m) ua[h][m] = a2[(m * NP + jbase + i0 + 2 * h) / 2];
     }
     float dfirst[4];  // stage 2, FP64 state: the first mode of the current pair
 #pragma unroll
     for (int i = 0; i < JB; ++i) {
-      const int j = j0 + i;
-      if (j >= NP) continue;
+      const int ii = i0 + i, j = jbase + ii;
+      if (ii >= jcnt) continue;
       float a[4];
       mode_sum<P>(lds4(tb + j), b, a);
       const float4 dL = f4_mul_f2(f4_add(pa[i], a), dtp);
@@ -827,25 +831,37 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
           }
         } else {
 #pragma unroll
-          for (int m = 0; m < 4; ++m) dk[j][m] = d[m];
+          for (int m = 0; m < 4; ++m) dk[ii][m] = d[m];
         }
       }
     }
   }
   if constexpr (STG == 2 && !PAIRS) {
     // odd NP (p = 1, 12 values): u = u0 + (2/3) f64(delta) over the [M][NP]
-    // FP64 block, all loads before the stores
-    constexpr int H = 2 * NP;
-    double2* u2 = reinterpret_cast<double2*>(u);
-    double2 a[H];
+    // FP64 block, all loads before the stores; only a lane that holds every
+    // mode (jbase = 0, jcnt = NP) writes it
+    if (jcnt == NP) {
+      constexpr int H = 2 * NP;
+      double2* u2 = reinterpret_cast<double2*>(u);
+      double2 a[H];
 #pragma unroll
-    for (int i = 0; i < H; ++i) a[i] = u2[i];
+      for (int i = 0; i < H; ++i) a[i] = u2[i];
 #pragma unroll
-    for (int i = 0; i < H; ++i) {
-      const int v = 2 * i, m0 = v / NP, j0 = v % NP, m1 = (v + 1) / NP, j1 = (v + 1) % NP;
-      u2[i] = make_double2(fma(2.0 / 3.0, f2d(dk[j0][m0]), a[i].x), fma(2.0 / 3.0, f2d(dk[j1][m1]), a[i].y));
+      for (int i = 0; i < H; ++i) {
+        const int v = 2 * i, m0 = v / NP, j0 = v % NP, m1 = (v + 1) / NP, j1 = (v + 1) % NP;
+        u2[i] = make_double2(fma(2.0 / 3.0, f2d(dk[j0][m0]), a[i].x), fma(2.0 / 3.0, f2d(dk[j1][m1]), a[i].y));
+      }
     }
   }
+}
+
+// Two lanes per edge side (S = 2): the modes each takes in the epilogues.  The
+// first lane takes modes [0, split), the second [split, NP); split is even when
+// NP is (the FP64 state update of stage 2 pairs modes into double2).
+template <int P>
+__host__ __device__ constexpr int mode_split() {
+  constexpr int NP = TriDim<P>::NP;
+  return NP % 2 == 0 ? 2 * ((NP + 2) / 4) : (NP + 1) / 2;
 }
 
 // MODE == SURF_FIRST with STG == 0 (FP64 state, FP32 rhs): the first color of
@@ -853,14 +869,25 @@ __device__ __forceinline__ void last_modes(const float4* tb, const float (&b)[P 
 // FP32 CFL estimate (both as pass 1 of the CFL reduction would) into A.rec_first
 // and A.est, and returns the estimate in *best (FLT_MAX for lanes that write
 // nothing).
-template <int P, typename ST, typename RT, int MODE, int STG = -1>
+// S lanes per edge side (threads per edge 2 S).  S = 2: the two lanes of a
+// side (sub = 0, 1; lanes 2 apart, the sides' lanes adjacent) both load the
+// element's record and form its edge coefficients; lane sub takes the edge
+// points sub, sub + 2, ... and the volume points likewise, their sums are
+// combined across the two lanes, and each lane writes its share of the modes
+// (mode_split).  FP32 right-hand sides of the colored modes only.
+template <int P, typename ST, typename RT, int MODE, int STG = -1, int S = 1>
 __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
-                                          const float* se, float* rslot = nullptr, float* best = nullptr) {
+                                          const float* se, float* rslot = nullptr, float* best = nullptr,
+                                          int sub = 0) {
   using D = TriDim<P>;
   using T = ETab32<P>;
   constexpr int NP = D::NP, NQ = D::NQE, NV = D::NV, K1 = P + 1;
   // the FP32 path writes FP32 right-hand sides only in the colored modes
   static_assert(sizeof(RT) == 8 || MODE == SURF_FIRST || MODE == SURF_RMW || MODE == SURF_LAST, "FP32 rhs modes");
+  static_assert(S == 1 || (S == 2 && sizeof(RT) == 4), "two lanes per side: the FP32 right-hand sides of a step");
+  // the modes this lane writes, [jlo, jlo + jn)
+  constexpr int JS = S == 1 ? NP : mode_split<P>();
+  const int jlo = sub ? JS : 0, jn = sub ? NP - JS : JS;
   const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
   const bool right = side && !bnd;
   const int64_t elem = right ? tp.y : tp.x;
@@ -948,21 +975,29 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
     if constexpr (STG == 0 && sizeof(ST) == 8) {
       static_assert(sizeof(RT) == 4, "the stage-0 first color writes the FP32 rhs of the step");
       float lam = 0.0f;
-      volume_acc32<P, true>(B, R, A.jinv + 4 * elem, acc, &lam);
+      volume_acc32<P, true, S>(B, R, A.jinv + 4 * elem, acc, &lam, sub);
+      if constexpr (S == 2) lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, 2));
       if (writer) {
-        // the record of u0 (mode-major), as the CFL pass 1 writes it
+        // the record of u0 (mode-major), as the CFL pass 1 writes it (mode j at
+        // float4 j + 1, the mean pair at 0 and 1; each lane its share)
         float4* r = reinterpret_cast<float4*>(A.rec_first + elem * D::NF);
-        r[0] = make_float4(B.hi[0], B.hi[1], B.hi[2], B.hi[3]);
-        r[1] = make_float4(B.lo[0], B.lo[1], B.lo[2], B.lo[3]);
+        if (jlo == 0) {
+          r[0] = make_float4(B.hi[0], B.hi[1], B.hi[2], B.hi[3]);
+          r[1] = make_float4(B.lo[0], B.lo[1], B.lo[2], B.lo[3]);
+        }
 #pragma unroll
-        for (int j = 1; j < NP; ++j) r[j + 1] = make_float4(B.cd[0][j - 1], B.cd[1][j - 1], B.cd[2][j - 1], B.cd[3][j - 1]);
-        float dd = d2f(__ldg(A.inr + elem)) / ((2 * P + 1) * lam);
-        if (!(dd > 0.0f) || !(dd < FLT_MAX)) dd = 0.0f;  // non-physical: always re-evaluated
-        A.est[elem] = dd;
-        *best = dd;
+        for (int j = 1; j < NP; ++j)
+          if (S == 1 || (j >= jlo && j < jlo + jn))
+            r[j + 1] = make_float4(B.cd[0][j - 1], B.cd[1][j - 1], B.cd[2][j - 1], B.cd[3][j - 1]);
+        if (sub == 0) {
+          float dd = d2f(__ldg(A.inr + elem)) / ((2 * P + 1) * lam);
+          if (!(dd > 0.0f) || !(dd < FLT_MAX)) dd = 0.0f;  // non-physical: always re-evaluated
+          A.est[elem] = dd;
+          *best = dd;
+        }
       }
     } else {
-      volume_acc32<P>(B, R, A.jinv + 4 * elem, acc);
+      volume_acc32<P, false, S>(B, R, A.jinv + 4 * elem, acc, nullptr, sub);
     }
     FaceConst<2> E;
     E.init(R, hi, {d2f(g0.x), d2f(g0.y)}, side);
@@ -972,8 +1007,12 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
     for (int kk = 0; kk < K1; ++kk)
 #pragma unroll
       for (int m = 0; m < 4; ++m) bk[kk][m] = 0.0f;
+    // (every lane of a pair runs the same number of points: the shuffles of
+    // lf_exchange need all 32 lanes; a lane past the last point repeats it
+    // with weight 0)
     DGC_UNROLL_Q
-    for (int q = 0; q < NQ; ++q) {
+    for (int i = 0; i < (NQ + S - 1) / S; ++i) {
+      const int q0 = S * i + sub, q = q0 < NQ ? q0 : NQ - 1;
       float L[K1], t[4], G[4];
 #pragma unroll
       for (int kk = 0; kk < K1; ++kk) L[kk] = EK.Lq[q][kk];
@@ -985,13 +1024,24 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
         t[m] = v;
       }
       lf_exchange<2>(R, E, t, G);
-      const float s = escale * K.wE[q];
+      const float s = q0 < NQ ? escale * K.wE[q] : 0.0f;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const float g = s * G[m];
 #pragma unroll
         for (int kk = 0; kk < K1; ++kk) bk[kk][m] = fmaf(L[kk], g, bk[kk][m]);
       }
+    }
+    if constexpr (S == 2) {
+      // the two lanes' point sums: edge coefficients and volume integral
+#pragma unroll
+      for (int kk = 0; kk < K1; ++kk)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) bk[kk][m] += __shfl_xor_sync(0xffffffffu, bk[kk][m], 2);
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int j = 1; j < NP; ++j) acc[m * NP + j] += __shfl_xor_sync(0xffffffffu, acc[m * NP + j], 2);
     }
     if (!writer) return;
 #pragma unroll
@@ -1001,8 +1051,17 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[m * NP + j] += a[m];
     }
-    if constexpr (sizeof(RT) == 4) store_rhs<P>(static_cast<float*>(A.rhs) + elem * NV, acc);
-    else surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    if constexpr (S == 2) {
+      // this lane's share of the modes of the mode-major FP32 rhs
+      float4* r = reinterpret_cast<float4*>(static_cast<float*>(A.rhs) + elem * NV);
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        if (j >= jlo && j < jlo + jn) r[j] = make_float4(acc[j], acc[NP + j], acc[2 * NP + j], acc[3 * NP + j]);
+    } else if constexpr (sizeof(RT) == 4) {
+      store_rhs<P>(static_cast<float*>(A.rhs) + elem * NV, acc);
+    } else {
+      surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
   } else {
     // 2. fluxes at every point; then 3. b_k = sum_q w_q G_q L_k(xi_q)
     FaceConst<2> E;
@@ -1014,7 +1073,8 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
 #pragma unroll
       for (int m = 0; m < 4; ++m) bk[kk][m] = 0.0f;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
+    for (int i = 0; i < (NQ + S - 1) / S; ++i) {
+      const int q0 = S * i + sub, q = q0 < NQ ? q0 : NQ - 1;  // as in the first color
       float t[4], G[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
@@ -1024,13 +1084,19 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
         t[m] = v;
       }
       lf_exchange<2>(R, E, t, G);
-      const float s = escale * K.wE[q];
+      const float s = q0 < NQ ? escale * K.wE[q] : 0.0f;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const float g = s * G[m];
 #pragma unroll
         for (int kk = 0; kk < K1; ++kk) bk[kk][m] = fmaf(EK.Lq[q][kk], g, bk[kk][m]);
       }
+    }
+    if constexpr (S == 2) {
+#pragma unroll
+      for (int kk = 0; kk < K1; ++kk)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) bk[kk][m] += __shfl_xor_sync(0xffffffffu, bk[kk][m], 2);
     }
 
     // modes and epilogue, after the predecessor grid has completed
@@ -1039,35 +1105,48 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
     if (!writer) return;
     if constexpr (MODE == SURF_LAST) {
       // (the FP64 state of the mixed form is updated in place: S.u0 == S.uout)
-      const StageArgs& S = A.sa;
+      const StageArgs& SA = A.sa;
       const float4* part = reinterpret_cast<const float4*>(static_cast<const float*>(A.rhs) + elem * NV);
-      float4* dp = reinterpret_cast<float4*>(S.delta + elem * NV);
-      const float4* r0 = reinterpret_cast<const float4*>(S.rec0 + elem * S.rec0_stride);
-      float4* ro = reinterpret_cast<float4*>(S.rec_out + elem * D::NF);
-      float4* ks = S.kstate ? reinterpret_cast<float4*>(S.kstate + elem * S.rec0_stride) : nullptr;
-      double* u = S.uout ? S.uout + elem * NV : nullptr;
-      const double dt = *S.dt, phi0 = tri_tab<double, P>().phiV[0][0];
-      const int stage = STG >= 0 ? STG : (S.stage == 2 && ks ? 3 : S.stage);
+      float4* dp = reinterpret_cast<float4*>(SA.delta + elem * NV);
+      const float4* r0 = reinterpret_cast<const float4*>(SA.rec0 + elem * SA.rec0_stride);
+      float4* ro = reinterpret_cast<float4*>(SA.rec_out + elem * D::NF);
+      float4* ks = SA.kstate ? reinterpret_cast<float4*>(SA.kstate + elem * SA.rec0_stride) : nullptr;
+      double* u = SA.uout ? SA.uout + elem * NV : nullptr;
+      const double dt = *SA.dt, phi0 = tri_tab<double, P>().phiV[0][0];
+      const int stage = STG >= 0 ? STG : (SA.stage == 2 && ks ? 3 : SA.stage);
       const float4* rs = reinterpret_cast<const float4*>(rslot);
-      if (stage == 0) last_modes<P, 0>(tb, bk, rs, part, dp, r0, ro, ks, u, dt, phi0);
-      else if (stage == 1) last_modes<P, 1>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
-      else if (stage == 2) last_modes<P, 2>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
-      else last_modes<P, 3>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
+      if constexpr (S == 1) {
+        if (stage == 0) last_modes<P, 0>(tb, bk, rs, part, dp, r0, ro, ks, u, dt, phi0);
+        else if (stage == 1) last_modes<P, 1>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
+        else if (stage == 2) last_modes<P, 2>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
+        else last_modes<P, 3>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0);
+      } else {
+        // stage 2 of the FP64 state with an odd mode count writes the whole
+        // [M][NP] block at once: the first lane of the side takes every mode
+        const bool whole = stage == 2 && NP % 2 == 1;
+        const int b0 = whole ? (sub ? NP : 0) : jlo, n0 = whole ? (sub ? 0 : NP) : jn;
+        if (stage == 0) last_modes<P, 0>(tb, bk, rs, part, dp, r0, ro, ks, u, dt, phi0, b0, n0);
+        else if (stage == 1) last_modes<P, 1>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0, b0, n0);
+        else if (stage == 2) last_modes<P, 2>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0, b0, n0);
+        else last_modes<P, 3>(tb, bk, nullptr, part, dp, r0, ro, ks, u, dt, phi0, b0, n0);
+      }
     } else if constexpr (sizeof(RT) == 4) {
       // read-modify-write in batches of JB modes, each batch's loads first
+      // (this lane's modes [jlo, jlo + jn))
       constexpr int JB = 5;
-      float4* r = reinterpret_cast<float4*>(static_cast<float*>(A.rhs) + elem * NV);
+      float4* r = reinterpret_cast<float4*>(static_cast<float*>(A.rhs) + elem * NV) + jlo;
 #pragma unroll
-      for (int j0 = 0; j0 < NP; j0 += JB) {
+      for (int j0 = 0; j0 < JS; j0 += JB) {
+        if (j0 >= jn) break;
         float4 o[JB];
 #pragma unroll
         for (int i = 0; i < JB; ++i)
-          if (j0 + i < NP) o[i] = r[j0 + i];
+          if (j0 + i < jn) o[i] = r[j0 + i];
 #pragma unroll
         for (int i = 0; i < JB; ++i) {
-          if (j0 + i >= NP) continue;
+          if (j0 + i >= jn) continue;
           float a[4];
-          mode_sum<P>(lds4(tb + j0 + i), bk, a);
+          mode_sum<P>(lds4(tb + jlo + j0 + i), bk, a);
           r[j0 + i] = f4_add(o[i], a);
         }
       }
@@ -1145,11 +1224,12 @@ constexpr int surf_regs() {
                                                 : 128;
 }
 
-template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1>
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, int S = 1>
 __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MODE, STG>())) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
-  const int side = threadIdx.x & 1;
-  int64_t k = A.begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1);
+  // lanes 2S e .. 2S e + 2S - 1 take edge e: side = bit 0, the lane of the side bit 1 (S = 2)
+  const int side = threadIdx.x & 1, sub = S == 2 ? (threadIdx.x >> 1) & 1 : 0;
+  int64_t k = A.begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> (S == 2 ? 2 : 1));
   const bool valid = k < A.end;
   if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
   const int4 tp = A.topo[k];
@@ -1163,12 +1243,13 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
       rslot = reinterpret_cast<float*>(rslots) + threadIdx.x * rec_slot<P>();
     if constexpr (MODE == SURF_FIRST && STG == 0) {
       float best = FLT_MAX;
-      surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se, rslot, &best);
+      surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, &best, sub);
       block_min_to(best, A.estmin);
     } else {
-      surf_fp32<P, ST, RT, MODE, STG>(A, k, tp, valid, side, se, rslot);
+      surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, nullptr, sub);
     }
   } else {
+    static_assert(S == 1, "FP64 lanes: one per edge side");
     __shared__ double sphi[9 * D::NQE * D::NP];
     __shared__ double sw[D::NQE];
     stage_edge_tables<P, double>(sphi, sw, A.ntab);
@@ -1498,10 +1579,11 @@ template <int MODE, bool MIXED, int STG>
 constexpr int batch_regs() {
   return !MIXED ? 255 : surf_regs<3, float, float, float, MODE, STG>() + DGC_BATCH_EXTRA_REGS;
 }
-template <int MODE, bool MIXED, int STG = -1>
+template <int MODE, bool MIXED, int STG = -1, int S = 1>
 __global__ void __launch_bounds__(256) __maxnreg__((batch_regs<MODE, MIXED, STG>()))
     k_batch_surf(const BatchMeshDev* __restrict__ meshes, const BatchTile* __restrict__ tiles, int nt, int stage,
                  double a0, double b0) {
+  static_assert(S == 1 || MIXED, "two lanes per edge side: the FP32-mixed form");
   using CT = typename std::conditional<MIXED, float, double>::type;
   using RT = CT;
   using ST = CT;
@@ -1557,15 +1639,15 @@ __global__ void __launch_bounds__(256) __maxnreg__((batch_regs<MODE, MIXED, STG>
     A.buf = nullptr;
     A.ntab = 3;
     A.sa.dt = B.dt;
-    int64_t k = T.begin + (threadIdx.x >> 1);
+    int64_t k = T.begin + (threadIdx.x >> (S == 2 ? 2 : 1));
     const bool valid = k < T.end;
     if (!valid) k = T.end - 1;
-    const int side = threadIdx.x & 1;
+    const int side = threadIdx.x & 1, sub = S == 2 ? (threadIdx.x >> 1) & 1 : 0;
     const int4 tp = A.topo[k];
     if constexpr (MIXED) {
-      if (T.p == 1) surf_fp32<1, ST, RT, MODE, STG>(A, k, tp, valid, side, sphi);
-      else if (T.p == 2) surf_fp32<2, ST, RT, MODE, STG>(A, k, tp, valid, side, sphi);
-      else surf_fp32<3, ST, RT, MODE, STG>(A, k, tp, valid, side, sphi);
+      if (T.p == 1) surf_fp32<1, ST, RT, MODE, STG, S>(A, k, tp, valid, side, sphi, nullptr, nullptr, sub);
+      else if (T.p == 2) surf_fp32<2, ST, RT, MODE, STG, S>(A, k, tp, valid, side, sphi, nullptr, nullptr, sub);
+      else surf_fp32<3, ST, RT, MODE, STG, S>(A, k, tp, valid, side, sphi, nullptr, nullptr, sub);
     } else {
       if (T.p == 1) surf_pair<1, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
       else if (T.p == 2) surf_pair<2, CT, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
@@ -1657,27 +1739,36 @@ int batch_cfl(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, in
   return 2;
 }
 
-template <int MODE, bool MIXED, int STG = -1>
+template <int MODE, bool MIXED, int STG = -1, int S = 1>
 static int batch_surf_launch(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage,
                              double a0, double b0, int threads) {
   if (nt <= 0) return 0;
-  const int g = persistent_grid((const void*)k_batch_surf<MODE, MIXED, STG>, threads, nt);
-  launch_k(pdl_ctx(st), k_batch_surf<MODE, MIXED, STG>, (unsigned)g, (unsigned)threads, 0, d, tiles, nt, stage, a0,
-           b0);
+  if (threads > 256) return -1;
+  const int g = persistent_grid((const void*)k_batch_surf<MODE, MIXED, STG, S>, threads, nt);
+  launch_k(pdl_ctx(st), k_batch_surf<MODE, MIXED, STG, S>, (unsigned)g, (unsigned)threads, 0, d, tiles, nt, stage,
+           a0, b0);
   return 1;
 }
 
+template <int MODE, int STG = -1>
+static int batch_mixed(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage, double a0,
+                       double b0, int threads, int tpe) {
+  if (tpe == 4) return batch_surf_launch<MODE, true, STG, 2>(st, d, tiles, nt, stage, a0, b0, threads);
+  return batch_surf_launch<MODE, true, STG, 1>(st, d, tiles, nt, stage, a0, b0, threads);
+}
+
 int batch_surf(cudaStream_t st, const BatchMeshDev* d, const BatchTile* tiles, int nt, int stage, double a0,
-               double b0, SurfMode mode, bool mixed, int threads) {
+               double b0, SurfMode mode, bool mixed, int threads, int tpe) {
   if (mixed) {
-    if (mode == SURF_FIRST) return batch_surf_launch<SURF_FIRST, true>(st, d, tiles, nt, stage, a0, b0, threads);
-    if (mode == SURF_RMW) return batch_surf_launch<SURF_RMW, true>(st, d, tiles, nt, stage, a0, b0, threads);
+    if (mode == SURF_FIRST) return batch_mixed<SURF_FIRST>(st, d, tiles, nt, stage, a0, b0, threads, tpe);
+    if (mode == SURF_RMW) return batch_mixed<SURF_RMW>(st, d, tiles, nt, stage, a0, b0, threads, tpe);
     if (mode == SURF_LAST) {  // the batch runs the mixed form only: stage 2 updates the FP64 state
-      if (stage == 0) return batch_surf_launch<SURF_LAST, true, 0>(st, d, tiles, nt, stage, a0, b0, threads);
-      if (stage == 1) return batch_surf_launch<SURF_LAST, true, 1>(st, d, tiles, nt, stage, a0, b0, threads);
-      return batch_surf_launch<SURF_LAST, true, 2>(st, d, tiles, nt, stage, a0, b0, threads);
+      if (stage == 0) return batch_mixed<SURF_LAST, 0>(st, d, tiles, nt, stage, a0, b0, threads, tpe);
+      if (stage == 1) return batch_mixed<SURF_LAST, 1>(st, d, tiles, nt, stage, a0, b0, threads, tpe);
+      return batch_mixed<SURF_LAST, 2>(st, d, tiles, nt, stage, a0, b0, threads, tpe);
     }
   } else {
+    if (tpe != 2) return -1;
     if (mode == SURF_FIRST) return batch_surf_launch<SURF_FIRST, false>(st, d, tiles, nt, stage, a0, b0, threads);
     if (mode == SURF_RMW) return batch_surf_launch<SURF_RMW, false>(st, d, tiles, nt, stage, a0, b0, threads);
     if (mode == SURF_LAST) return batch_surf_launch<SURF_LAST, false>(st, d, tiles, nt, stage, a0, b0, threads);
@@ -1718,24 +1809,38 @@ int tri_volume(const Ctx& x, TypeCfg ty, const void* s, int sstride, void* r, in
   }
 }
 
-template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1>
-static int surf_launch(const Ctx& x, const SurfParams& A) {
+// the tile class of a surface mode: first, middle, last color (comparators: middle)
+constexpr int tile_class(int mode) { return mode == SURF_FIRST ? 0 : mode == SURF_LAST ? 2 : 1; }
+
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, int S = 1>
+static int surf_launch_s(const Ctx& x, const SurfParams& A) {
   const int64_t n = A.end - A.begin;
   if (n <= 0) return 0;
-  const int threads = 2 * x.epb;
-  const int64_t grid = (2 * n + threads - 1) / threads;
+  const int threads = 2 * S * x.tile_epb[tile_class(MODE)];
+  if (threads > 256) return -1;  // the kernels' launch bound
+  const int64_t grid = (2 * S * n + threads - 1) / threads;
   const size_t smem =
       MODE == SURF_LAST && STG == 0 && sizeof(ST) == 4 ? (size_t)threads * rec_slot<P>() * sizeof(float) : 0;
   if (smem > 32 * 1024) {  // 256-thread blocks: above the default 48 KB with the static tables
     static bool raised = false;
     if (!raised) {
-      cudaFuncSetAttribute(k_surf_tri<P, CT, ST, RT, MODE, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_surf_tri<P, CT, ST, RT, MODE, STG, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            64 * 1024);
       raised = true;
     }
   }
-  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG>, (unsigned)grid, (unsigned)threads, smem, A);
+  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG, S>, (unsigned)grid, (unsigned)threads, smem, A);
   return 1;
+}
+
+// The FP32 colored kernels of an RK step (FP32 rhs) take their class's threads
+// per edge (2 or 4); every other kernel has one lane per edge side.
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1>
+static int surf_launch(const Ctx& x, const SurfParams& A) {
+  if constexpr (sizeof(CT) == 4 && sizeof(RT) == 4) {
+    if (x.tile_tpe[tile_class(MODE)] == 4) return surf_launch_s<P, CT, ST, RT, MODE, STG, 2>(x, A);
+  }
+  return surf_launch_s<P, CT, ST, RT, MODE, STG, 1>(x, A);
 }
 
 template <int P, typename CT, typename ST, typename RT>

@@ -72,12 +72,16 @@ SIGNATURES = {
     "dgc_last_launch_count": (C.c_int, [_P, _I64P]),
     "dgc_last_error": (C.c_char_p, []),
     "dgc_rk_step_static": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P]),
+    "dgc_set_tile": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "dgc_get_tile": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "dgc_autotune": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P, _I64, C.c_int, _P, C.POINTER(C.c_int),
+                               C.POINTER(C.c_int), _DP]),
     "dgc_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
     "dgc_batch_workspace_size": (C.c_int, [_P, C.c_int, _I64P]),
     "dgc_batch_set_option": (C.c_int, [_P, C.c_int, _I64]),
     "dgc_batch_rk_step": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, _P, _P, _I64, _P]),
-    "dgc_batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, _P, _P, _I64, C.c_int, _P, _I64P,
-                                     _DP]),
+    "dgc_batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, _P, _P, _I64, C.c_int, _P,
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
     "dgc_batch_launch_count": (C.c_int, [_P, _I64P]),
     "dgc_batch_destroy": (None, [_P]),
     "dgc_destroy": (None, [_P]),
@@ -353,6 +357,30 @@ def dgc_set_option(mesh, opt: int, value: int):
     _check(lib().dgc_set_option(mesh, opt, value))
 
 
+DGC_K_FIRST, DGC_K_COLOR, DGC_K_LAST = 2, 3, 4
+
+
+def dgc_set_tile(mesh, kclass: int, edges_per_block: int, threads_per_edge: int):
+    _check(lib().dgc_set_tile(mesh, kclass, edges_per_block, threads_per_edge))
+
+
+def dgc_get_tile(mesh, kclass: int):
+    e, t = C.c_int(), C.c_int()
+    _check(lib().dgc_get_tile(mesh, kclass, C.byref(e), C.byref(t)))
+    return e.value, t.value
+
+
+def dgc_autotune(mesh, prec: int, c_dev, cfl: float, dt_dev, workspace_dev, reps: int = 5, workspace_bytes=None,
+                 stream=None):
+    """Returns ({"first"|"color"|"last": (edges per block, threads per edge)}, best ms per step)."""
+    e = (C.c_int * 3)()
+    t = (C.c_int * 3)()
+    ms = C.c_double()
+    _check(lib().dgc_autotune(mesh, prec, _dptr(c_dev), cfl, _dptr(dt_dev), _dptr(workspace_dev),
+                              _nbytes(workspace_dev, workspace_bytes), reps, _stream(stream), e, t, C.byref(ms)))
+    return {k: (e[i], t[i]) for i, k in enumerate(("first", "color", "last"))}, ms.value
+
+
 def dgc_profile_collect(mesh) -> dict:
     ms = (C.c_double * 16)()
     n = (C.c_int64 * 16)()
@@ -403,12 +431,14 @@ def dgc_batch_rk_step(batch, prec: int, c_devs, cfl: float, dt_devs, workspace_d
 
 def dgc_batch_autotune(batch, prec: int, c_devs, cfl: float, dt_devs, workspace_dev, reps: int = 5,
                        workspace_bytes=None, stream=None):
-    best = C.c_int64()
-    ms = (C.c_double * 4)()
+    """Returns ({"first"|"color"|"last": (edges per block, threads per edge)}, best ms per step)."""
+    e = (C.c_int * 3)()
+    t = (C.c_int * 3)()
+    ms = C.c_double()
     _check(lib().dgc_batch_autotune(batch, prec, _ptr_array(c_devs), cfl, _dptr(dt_devs), _dptr(workspace_dev),
-                                    _nbytes(workspace_dev, workspace_bytes), reps, _stream(stream),
-                                    C.byref(best), ms))
-    return best.value, dict(zip((16, 32, 64, 128), list(ms)))
+                                    _nbytes(workspace_dev, workspace_bytes), reps, _stream(stream), e, t,
+                                    C.byref(ms)))
+    return {k: (e[i], t[i]) for i, k in enumerate(("first", "color", "last"))}, ms.value
 
 
 def dgc_batch_launch_count(batch) -> int:

@@ -39,6 +39,44 @@ def _meshes_and_states(seed=0):
     return meshes, states
 
 
+@pytest.mark.parametrize("tpe", [2, 4])
+def test_batch_four_threads_per_edge_equal_single_mesh(torch_dev, tpe):
+    """Batched FP32-mixed step with 2 or 4 threads per edge (all classes, 32
+    edges per block) equals the single-mesh step with the same tiles bit for
+    bit: the same per-edge code."""
+    torch, dev = torch_dev
+    meshes, states = _meshes_and_states()
+    prec = dgc.DGC_FP32_MIXED
+    cb = [torch.empty(m.state_shape(), dtype=torch.float64, device=dev) for m in meshes]
+    cs = [torch.empty_like(x) for x in cb]
+    for m, c, a, b in zip(meshes, states, cb, cs):
+        dgc.dgc_import_state(m.h, c, a)
+        dgc.dgc_import_state(m.h, c, b)
+        dgc.dgc_set_option(m.h, dgc.DGC_OPT_EDGES_PER_BLOCK, 32)
+        dgc.dgc_set_option(m.h, dgc.DGC_OPT_THREADS_PER_EDGE, tpe)
+    batch = dgc.dgc_batch_create(meshes)
+    dgc.dgc_batch_set_option(batch, dgc.DGC_OPT_EDGES_PER_BLOCK, 32)
+    dgc.dgc_batch_set_option(batch, dgc.DGC_OPT_THREADS_PER_EDGE, tpe)
+    ws = torch.empty(dgc.dgc_batch_workspace_size(batch, prec) // 8 + 64, dtype=torch.float64, device=dev)
+    dts = torch.zeros(len(meshes), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        dgc.dgc_batch_rk_step(batch, prec, cb, 0.3, dts, ws)
+    torch.cuda.synchronize()
+    for i, m in enumerate(meshes):
+        wsi = torch.empty(dgc.dgc_workspace_size(m.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
+        d = torch.zeros(1, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            dgc.dgc_rk_step(m.h, prec, cs[i], 0.3, d, wsi)
+        torch.cuda.synchronize()
+        assert dts[i].item() == d.item()
+        assert torch.equal(cb[i], cs[i]), f"mesh {i}"
+    with pytest.raises(dgc.DgcError):  # 4 x 128 threads exceed a block
+        dgc.dgc_batch_set_option(batch, dgc.DGC_OPT_EDGES_PER_BLOCK, 128 if tpe == 4 else 256)
+    dgc.dgc_batch_destroy(batch)
+    for m in meshes:
+        m.close()
+
+
 @pytest.mark.parametrize("prec", [dgc.DGC_FP64, dgc.DGC_FP32_MIXED])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batch_equals_single_mesh_steps(torch_dev, prec, graph):
@@ -81,9 +119,10 @@ def test_batch_autotune_and_refusals(torch_dev):
     need = dgc.dgc_batch_workspace_size(batch, prec)
     ws = torch.empty(need // 8 + 64, dtype=torch.float64, device=dev)
     dts = torch.zeros(len(meshes), dtype=torch.float64, device=dev)
-    best, ms = dgc.dgc_batch_autotune(batch, prec, cb, 0.3, dts, ws, reps=2)
-    assert best in (16, 32, 64, 128) and all(v > 0 for v in ms.values())
-    assert ms[best] == min(ms.values())
+    tiles, ms = dgc.dgc_batch_autotune(batch, prec, cb, 0.3, dts, ws, reps=2)
+    assert ms > 0
+    for e, t in tiles.values():
+        assert e in (16, 32, 64, 128) and t in (2, 4) and e * t <= 256
     with pytest.raises(dgc.DgcError) as e:
         dgc.dgc_batch_rk_step(batch, prec, cb, 0.3, dts, ws, workspace_bytes=need - 1)
     assert e.value.status == 1
@@ -202,6 +241,7 @@ def test_full_size_batch_sampled(torch_dev, oracle_mod, batch64, prec):
     for m, c, a in zip(meshes, states, scratch):
         dgc.dgc_import_state(m.h, c, a)
     best, _ = dgc.dgc_batch_autotune(batch, prec, scratch, 0.3, dts, ws, reps=1)
+    best = ", ".join(f"{k} {e}x{t}" for k, (e, t) in best.items())
     cb = [torch.empty(m.state_shape(), dtype=torch.float64, device=dev) for m in meshes]
     for m, c, a in zip(meshes, states, cb):
         dgc.dgc_import_state(m.h, c, a)
@@ -221,7 +261,7 @@ def test_full_size_batch_sampled(torch_dev, oracle_mod, batch64, prec):
         s0, s1, s2, _ = _rings(om, seeds, 3)
         got = dgc.dgc_export_state(meshes[i].h, cb[i])[s0] - c[s0]
         u3 = _sampled_step(om, p, c, dt, (s0, s1, s2)) - c[s0]
-        what = f"batch mesh {i} ({meshes[i].info['ne']} elements, p = {p}, {best} edges per block)"
+        what = f"batch mesh {i} ({meshes[i].info['ne']} elements, p = {p}, tiles {best})"
         if prec == dgc.DGC_FP64:
             ox = oracle_mod.OracleMesh.from_input(mis[i], build="extended")
             u3x = _sampled_step(ox, p, c, dt, (s0, s1, s2)) - c[s0]
