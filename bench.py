@@ -557,6 +557,8 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
         if refine is not None:
             m.refine(refine)
         prep_s = time.perf_counter() - t0
+        if args.epb:
+            dgc.dgc_set_option(m.h, dgc.DGC_OPT_EDGES_PER_BLOCK, args.epb)
         info = m.info
         if mi.dim == 3:
             # seeded mean state + perturbed modes (projecting the tube at 100M
@@ -609,6 +611,20 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
                 call()
                 t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
                 entry[f"rhs_{kind}_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+            if mi.dim == 2 and not m.elem == dgc.DGC_QUAD:
+                # the colored right-hand side as one cooperative launch (grid barriers between colors)
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_COOPERATIVE, 1)
+                call = lambda: dgc.dgc_rhs(m.h, prec, c, r)
+                call()
+                t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
+                entry[f"rhs_colored_coop_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_COOPERATIVE, 0)
+                # one wave of blocks per color, grid-stride
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_PERSISTENT, 1)
+                call()
+                t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
+                entry[f"rhs_colored_persistent_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_PERSISTENT, 0)
             dgc.dgc_set_option(m.h, dgc.DGC_OPT_FUSE, 0)
             call = lambda: dgc.dgc_rhs(m.h, prec, c, r)
             call()

@@ -85,11 +85,21 @@ typedef enum {
                                    the launch stream, for dgc_profile_collect; 0 (default): off */
   DGC_OPT_GRAPH = 4,            /* batches: 1 (default) capture the step in a CUDA graph on the
                                    first call and replay it; 0: launch the kernels directly */
-  DGC_OPT_PDL = 5               /* meshes: 1 (default) launch the surface and CFL kernels of
+  DGC_OPT_PDL = 5,              /* meshes: 1 (default) launch the surface and CFL kernels of
                                    dgc_rk_step, dgc_rhs and the comparators with programmatic
                                    dependent launch (each kernel's work that does not read its
                                    predecessor's output overlaps the predecessor's end); 0: plain
                                    stream order.  Results are identical. */
+  DGC_OPT_COOPERATIVE = 6,      /* triangle meshes: 1 runs dgc_rhs as one cooperative launch, the
+                                   phases of Algorithm 1 (first color with the volume integral,
+                                   then each further color) separated by grid-wide barriers
+                                   instead of kernel boundaries; 0 (default): one launch per
+                                   phase.  Results are identical. */
+  DGC_OPT_PERSISTENT = 7        /* triangle meshes: 1 launches each color's surface kernel with at
+                                   most one wave of blocks, every warp looping over the color in
+                                   steps of the whole grid (no partly filled last wave); 0
+                                   (default): one block per tile of edges.  Results are
+                                   identical. */
 } dgc_option;
 
 /* Kernel classes reported by dgc_profile_collect. */

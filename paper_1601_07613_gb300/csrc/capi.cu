@@ -272,6 +272,12 @@ Ctx make_ctx(const Mesh& m, const DeviceMesh* d, void* stream) {
   x.ne = m.ne;
   x.ns = m.ns;
   x.epb = m.edges_per_block;
+  x.persistent = m.persistent;
+  if (m.persistent) {
+    int dev = 0;
+    DGC_CUDA(cudaGetDevice(&dev));
+    DGC_CUDA(cudaDeviceGetAttribute(&x.sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   for (int c = 0; c < 3; ++c) {
     x.tile_epb[c] = m.tile_epb[c];
     x.tile_tpe[c] = m.tile_tpe[c];
@@ -383,6 +389,13 @@ int64_t unreached(const Mesh& m) { return m.perfect ? m.ne : m.reached; }
 int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss, void* rhs) {
   int64_t n = 0;
   const std::vector<int32_t>& off = m.color_off;
+  if (m.coop && m.dim == 2 && !m.quad && (ty == TY_D || ty == TY_MD)) {
+    // every phase of Algorithm 1 in one cooperative launch
+    run(m, x, DGC_K_COLOR, n, [&] {
+      return tri_rhs_coop(x, ty, off.data(), m.ncolors, first_fused(m), unreached(m), state, rhs);
+    });
+    return n;
+  }
   if (first_fused(m)) {
     run(m, x, DGC_K_FIRST, n, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], state, ss, rhs, nullptr, nullptr); });
     run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, state, ss, rhs, unreached(m)); });
@@ -1139,6 +1152,16 @@ dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value) {
         break;
       case DGC_OPT_PDL:
         m.pdl = value != 0;
+        break;
+      case DGC_OPT_PERSISTENT:
+        require(value == 0 || (m.dim == 2 && !m.quad), "persistent surface kernels: triangle meshes only",
+                DGC_ERR_UNSUPPORTED);
+        m.persistent = value != 0;
+        break;
+      case DGC_OPT_COOPERATIVE:
+        require(value == 0 || (m.dim == 2 && !m.quad), "cooperative right-hand side: triangle meshes only",
+                DGC_ERR_UNSUPPORTED);
+        m.coop = value != 0;
         break;
       default:
         throw Error{DGC_ERR_ARG, "unknown option"};

@@ -68,6 +68,10 @@ struct Ctx {
   // the first, middle and last colors
   int tile_epb[3] = {128, 128, 128};
   int tile_tpe[3] = {2, 2, 2};
+  // triangle surface kernels: grid-stride over the color with one wave of
+  // blocks (sms = the GPU's multiprocessors) instead of one block per tile
+  bool persistent = false;
+  int sms = 0;
   const DeviceMesh* d = nullptr;
   cudaStream_t st = nullptr;
   bool pdl = false;  // launch the surface and CFL kernels with programmatic dependent launch
@@ -144,6 +148,11 @@ int tri_record_floats(int p);
 // sstride: floats per element of an FP32 state (record or Kahan state); ignored for FP64 states
 // volume kernels cover elements [e0, ne)
 int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs, int64_t e0 = 0);
+// dgc_rhs of a triangle mesh in one cooperative launch (FP64 or FP32-mixed with
+// FP64 state and rhs): off = the color offsets, fused = the first color also
+// stores the volume integral of the elements [0, e_vol0)
+int tri_rhs_coop(const Ctx& x, TypeCfg ty, const int* off, int ncolors, bool fused, int64_t e_vol0,
+                 const void* state, void* rhs);
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);

@@ -104,6 +104,8 @@ struct Mesh {
   int tile_tpe[3] = {2, 2, 2};
   bool profile = false;
   bool pdl = true;  // programmatic dependent launch of the RK step's kernels
+  bool coop = false;  // dgc_rhs of triangle meshes as one cooperative launch
+  bool persistent = false;  // triangle surface kernels: one wave of blocks, grid-stride over the color
   void* prof = nullptr;  // event records (capi.cu)
   // device side
   DeviceMesh* dev = nullptr;

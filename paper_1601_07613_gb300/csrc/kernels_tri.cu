@@ -15,6 +15,8 @@
 //
 // FP64 kernels evaluate Eq. 2 as written.  FP32 kernels evaluate it in the
 // perturbation form of euler_pert.cuh (deviations from the element mean).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cfloat>
 #include <type_traits>
@@ -440,11 +442,9 @@ __device__ __forceinline__ void store_rhs(RT* dst, const AT (&acc)[TriDim<P>::NV
 // Volume kernel (unfused path): one thread per element, rhs = volume integral.
 // ---------------------------------------------------------------------------
 template <int P, typename CT, typename ST, typename RT>
-__global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, int sstride, const double* __restrict__ jinv,
-                                                 RT* __restrict__ rhs, int64_t e0, int64_t ne) {
+__device__ __forceinline__ void vol_elem(const ST* __restrict__ c, int sstride, const double* __restrict__ jinv,
+                                         RT* __restrict__ rhs, int64_t e) {
   using D = TriDim<P>;
-  const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
   RT out[D::NV];
   if constexpr (sizeof(CT) == 8) {
     double v[D::NV], acc[D::NV];
@@ -470,6 +470,14 @@ __global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, int s
   store_block(rhs + e * D::NV, out);
 }
 
+template <int P, typename CT, typename ST, typename RT>
+__global__ void __launch_bounds__(128) k_vol_tri(const ST* __restrict__ c, int sstride, const double* __restrict__ jinv,
+                                                 RT* __restrict__ rhs, int64_t e0, int64_t ne) {
+  const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  vol_elem<P, CT, ST, RT>(c, sstride, jinv, rhs, e);
+}
+
 // ---------------------------------------------------------------------------
 // Surface kernel for one color (or all edges for the comparators).
 // ---------------------------------------------------------------------------
@@ -484,6 +492,7 @@ struct SurfParams {
   StageArgs sa;
   int ntab;     // edge tables to stage (3, or 9 on meshes with hanging edges)
   int sstride;  // floats per element of an FP32 state (record or Kahan state)
+  int persistent = 0;  // grid-stride over the color with at most one wave of blocks
   // first color of stage 0 of the mixed step (tri_first_est): the record of u0
   // it writes, the elements' FP32 CFL estimates, their minimum, the inradii
   float* rec_first = nullptr;
@@ -1228,11 +1237,13 @@ template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, 
 __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MODE, STG>())) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
   // lanes 2S e .. 2S e + 2S - 1 take edge e: side = bit 0, the lane of the side bit 1 (S = 2)
+  constexpr int SH = S == 2 ? 2 : 1;
   const int side = threadIdx.x & 1, sub = S == 2 ? (threadIdx.x >> 1) & 1 : 0;
-  int64_t k = A.begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> (S == 2 ? 2 : 1));
-  const bool valid = k < A.end;
-  if (!valid) k = A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
-  const int4 tp = A.topo[k];
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // A.persistent: the grid is at most one wave and every warp loops over the
+  // color in steps of the whole grid; else one edge per lane group.  The loop
+  // test is on the warp's first edge, so a warp runs (and shuffles) together.
+  const int64_t step = A.persistent ? ((int64_t)gridDim.x * blockDim.x) >> SH : 0;
   if constexpr (sizeof(CT) == 4) {
     __shared__ __align__(16) float se[ETab32<P>::SIZE];
     extern __shared__ float4 rslots[];  // the last color's stage 0: rec_slot<P>() floats per thread
@@ -1241,20 +1252,36 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
     float* rslot = nullptr;
     if constexpr (MODE == SURF_LAST && STG == 0 && sizeof(ST) == 4)
       rslot = reinterpret_cast<float*>(rslots) + threadIdx.x * rec_slot<P>();
-    if constexpr (MODE == SURF_FIRST && STG == 0) {
-      float best = FLT_MAX;
-      surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, &best, sub);
-      block_min_to(best, A.estmin);
-    } else {
-      surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, nullptr, sub);
+    float best = FLT_MAX;
+    for (int64_t k0 = A.begin + (gtid >> SH), kw = A.begin + ((gtid & ~(int64_t)31) >> SH); kw < A.end;
+         k0 += step, kw += step) {
+      const bool valid = k0 < A.end;
+      const int64_t k = valid ? k0 : A.end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
+      const int4 tp = A.topo[k];
+      if constexpr (MODE == SURF_FIRST && STG == 0) {
+        float b = FLT_MAX;
+        surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, &b, sub);
+        best = fminf(best, b);
+      } else {
+        surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, nullptr, sub);
+      }
+      if (!step) break;
     }
+    if constexpr (MODE == SURF_FIRST && STG == 0) block_min_to(best, A.estmin);
   } else {
     static_assert(S == 1, "FP64 lanes: one per edge side");
     __shared__ double sphi[9 * D::NQE * D::NP];
     __shared__ double sw[D::NQE];
     stage_edge_tables<P, double>(sphi, sw, A.ntab);
     __syncthreads();
-    surf_pair<P, double, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+    for (int64_t k0 = A.begin + (gtid >> 1), kw = A.begin + ((gtid & ~(int64_t)31) >> 1); kw < A.end;
+         k0 += step, kw += step) {
+      const bool valid = k0 < A.end;
+      const int64_t k = valid ? k0 : A.end - 1;
+      const int4 tp = A.topo[k];
+      surf_pair<P, double, ST, RT, MODE>(A, k, tp, valid, side, sphi, sw);
+      if (!step) break;
+    }
   }
 }
 
@@ -1818,9 +1845,26 @@ static int surf_launch_s(const Ctx& x, const SurfParams& A) {
   if (n <= 0) return 0;
   const int threads = 2 * S * x.tile_epb[tile_class(MODE)];
   if (threads > 256) return -1;  // the kernels' launch bound
-  const int64_t grid = (2 * S * n + threads - 1) / threads;
+  int64_t grid = (2 * S * n + threads - 1) / threads;
   const size_t smem =
       MODE == SURF_LAST && STG == 0 && sizeof(ST) == 4 ? (size_t)threads * rec_slot<P>() * sizeof(float) : 0;
+  SurfParams B = A;
+  B.persistent = 0;
+  if (x.persistent) {
+    // one wave: resident blocks per SM of this instantiation at this block size
+    static int per = -1, per_threads = -1;
+    if (per_threads != threads) {
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_surf_tri<P, CT, ST, RT, MODE, STG, S>, threads, smem);
+      per = occ > 0 ? occ : 1;
+      per_threads = threads;
+    }
+    const int64_t wave = (int64_t)x.sms * per;
+    if (grid > wave) {
+      grid = wave;
+      B.persistent = 1;
+    }
+  }
   if (smem > 32 * 1024) {  // 256-thread blocks: above the default 48 KB with the static tables
     static bool raised = false;
     if (!raised) {
@@ -1829,7 +1873,7 @@ static int surf_launch_s(const Ctx& x, const SurfParams& A) {
       raised = true;
     }
   }
-  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG, S>, (unsigned)grid, (unsigned)threads, smem, A);
+  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG, S>, (unsigned)grid, (unsigned)threads, smem, B);
   return 1;
 }
 
@@ -1899,6 +1943,117 @@ int tri_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t 
     case 1: return surf_p<1>(x, ty, mode, A);
     case 2: return surf_p<2>(x, ty, mode, A);
     case 3: return surf_p<3>(x, ty, mode, A);
+    default: return -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The whole right-hand side in one cooperative launch (dgc_rhs with
+// DGC_OPT_COOPERATIVE): the phases of Algorithm 1 -- the first color with the
+// volume integral of the elements it reaches and the volume integral of the
+// rest (disjoint elements, one phase), then every further color -- separated
+// by grid-wide barriers instead of kernel boundaries.  The grid is co-resident
+// (cudaLaunchCooperativeKernel refuses one that is not); each warp takes
+// chunks of 16 edges (or 32 elements) in a grid-stride loop, so a color with
+// fewer edges than the GPU holds threads spreads over every SM.  Per element
+// the arithmetic and its order are those of the separate launches.
+// ---------------------------------------------------------------------------
+struct CoopRhs {
+  SurfParams A;
+  int off[kMaxColors + 1];  // color offsets of the edges
+  int ncolors;
+  int fused;      // the first color stores rhs with the volume integral of [0, e_vol0)
+  int64_t e_vol0;  // the volume phase covers [e_vol0, ne)
+  int64_t ne;
+};
+
+template <int P, typename CT, typename ST, typename RT, int MODE>
+__device__ __forceinline__ void coop_edges(const SurfParams& A, int64_t begin, int64_t end, const CT* tab,
+                                           const CT* sw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int side = lane & 1;
+  for (int64_t ch = wid; begin + 16 * ch < end; ch += warps) {  // warp-uniform trip count
+    int64_t k = begin + 16 * ch + (lane >> 1);
+    const bool valid = k < end;
+    if (!valid) k = end - 1;
+    const int4 tp = A.topo[k];
+    if constexpr (sizeof(CT) == 4) surf_fp32<P, ST, RT, MODE>(A, k, tp, valid, side, tab);
+    else surf_pair<P, CT, ST, RT, MODE>(A, k, tp, valid, side, tab, sw);
+  }
+}
+
+template <int P, typename CT, typename ST, typename RT>
+__global__ void __launch_bounds__(128) __maxnreg__((surf_regs<P, CT, ST, RT, SURF_FIRST, -1>()))
+    k_rhs_coop(const CoopRhs C) {
+  using D = TriDim<P>;
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  constexpr int TAB = sizeof(CT) == 4 ? ETab32<P>::SIZE : 9 * D::NQE * D::NP;
+  __shared__ __align__(16) CT tab[TAB];
+  __shared__ CT sw[D::NQE];
+  if constexpr (sizeof(CT) == 4) stage_etab32<P>(reinterpret_cast<float*>(tab), C.A.ntab);
+  else stage_edge_tables<P, double>(reinterpret_cast<double*>(tab), reinterpret_cast<double*>(sw), C.A.ntab);
+  __syncthreads();
+  const SurfParams& A = C.A;
+  // phase 0: the first color (fused) and the volume integral of the others
+  if (C.fused) coop_edges<P, CT, ST, RT, SURF_FIRST>(A, C.off[0], C.off[1], tab, sw);
+  for (int64_t e = C.e_vol0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < C.ne;
+       e += (int64_t)gridDim.x * blockDim.x)
+    vol_elem<P, CT, ST, RT>(static_cast<const ST*>(A.state), A.sstride, A.jinv, static_cast<RT*>(A.rhs), e);
+  for (int c = C.fused ? 2 : 1; c <= C.ncolors; ++c) {
+    __threadfence();
+    grid.sync();
+    coop_edges<P, CT, ST, RT, SURF_RMW>(A, C.off[c - 1], C.off[c], tab, sw);
+  }
+}
+
+template <int P, typename CT, typename ST, typename RT>
+static int rhs_coop_launch(const Ctx& x, const CoopRhs& C) {
+  static int grid = 0;  // co-resident blocks of this kernel (per instantiation; one device model)
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rhs_coop<P, CT, ST, RT>, 128, 0);
+    if (per <= 0) return -1;
+    grid = sms * per;
+  }
+  void* args[] = {const_cast<CoopRhs*>(&C)};
+  if (cudaLaunchCooperativeKernel((const void*)k_rhs_coop<P, CT, ST, RT>, dim3(grid), dim3(128), args, 0, x.st) !=
+      cudaSuccess)
+    return -1;
+  return 1;
+}
+
+int tri_rhs_coop(const Ctx& x, TypeCfg ty, const int* off, int ncolors, bool fused, int64_t e_vol0,
+                 const void* state, void* rhs) {
+  if (ncolors > kMaxColors) return -1;
+  CoopRhs C;
+  C.A.begin = 0;
+  C.A.end = 0;
+  C.A.sstride = 0;
+  C.A.topo = x.d->topo;
+  C.A.fgeo = x.d->fgeo;
+  C.A.jinv = x.d->jinv;
+  C.A.state = state;
+  C.A.rhs = rhs;
+  C.A.buf = nullptr;
+  C.A.ntab = x.d->edge_tables;
+  for (int c = 0; c <= ncolors; ++c) C.off[c] = off[c];
+  C.ncolors = ncolors;
+  C.fused = fused ? 1 : 0;
+  C.e_vol0 = fused ? e_vol0 : 0;
+  C.ne = x.ne;
+  if (ty != TY_D && ty != TY_MD) return -1;
+  switch (x.p) {
+    case 1: return ty == TY_D ? rhs_coop_launch<1, double, double, double>(x, C)
+                              : rhs_coop_launch<1, float, double, double>(x, C);
+    case 2: return ty == TY_D ? rhs_coop_launch<2, double, double, double>(x, C)
+                              : rhs_coop_launch<2, float, double, double>(x, C);
+    case 3: return ty == TY_D ? rhs_coop_launch<3, double, double, double>(x, C)
+                              : rhs_coop_launch<3, float, double, double>(x, C);
     default: return -1;
   }
 }

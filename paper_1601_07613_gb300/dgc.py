@@ -24,6 +24,8 @@ DGC_OPT_THREADS_PER_EDGE = 2
 DGC_OPT_PROFILE = 3
 DGC_OPT_GRAPH = 4
 DGC_OPT_PDL = 5
+DGC_OPT_COOPERATIVE = 6
+DGC_OPT_PERSISTENT = 7
 DGC_TRI, DGC_QUAD, DGC_TET = 0, 1, 2  # dgc_elem
 KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
 
