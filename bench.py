@@ -212,10 +212,13 @@ def kernel_source_hash() -> str:
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
-# over the launches of each class) from an ncu capture of this benchmark's own
-# command, taken with the kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = "8dc544a059717f84"
-TRAFFIC_BYTES = {"last": 1122772187, "first": 478180730, "color": 589463979, "cfl": 4220489}
+# over the launches of each class as one step has them: the first color once
+# with the FP64 state and twice with the record, the last color once per
+# stage) from ncu captures of this benchmark's own command at full size with
+# the tiles 64x2, 64x2, 32x4 (one kernel and two launches per capture), taken
+# with the kernel sources of hash TRAFFIC_SOURCES.
+TRAFFIC_SOURCES = "f41d638e7f35bf61"
+TRAFFIC_BYTES = {"last": 1123974698, "first": 480850560, "color": 592490624, "cfl": 4220928}
 
 
 def replica_throughput(torch, ms: float, world: int, units_per_step: float, dev):
@@ -261,7 +264,11 @@ def run_dgc(args, rank, world, local_rank):
     # ---- tiles: the library's autotuner (edges per block x threads per edge of the
     # first, middle and last colors) on a scratch copy of the state, untimed
     tiles = None
-    if not (args.no_autotune or args.epb or args.tpe):
+    if args.tiles:
+        for kc, t in zip((dgc.DGC_K_FIRST, dgc.DGC_K_COLOR, dgc.DGC_K_LAST), args.tiles.split(",")):
+            e, tp = (int(v) for v in t.split("x"))
+            dgc.dgc_set_tile(mesh.h, kc, e, tp)
+    if not (args.no_autotune or args.epb or args.tpe or args.tiles):
         scratch = torch.empty_like(c)
         dgc.dgc_import_state(mesh.h, c_host, scratch)
         tiles, tune_ms = dgc.dgc_autotune(mesh.h, mixed, scratch, cfg["cfl"], dt, ws, reps=3)
@@ -803,6 +810,8 @@ def main():
                     help="oracle elements per reference step (0 = the whole mesh)")
     ap.add_argument("--epb", type=int, default=0, help="edges per block of the surface kernels (0 = library default)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tiles")
+    ap.add_argument("--tiles", default="", help="tiles of the first, middle and last colors as EPBxTPE,EPBxTPE,"
+                    "EPBxTPE (edges per block x threads per edge), instead of the autotuner's")
     ap.add_argument("--tpe", type=int, default=0, help="threads per edge of the FP32 surface kernels (0 = library "
                     "default: 2)")
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
