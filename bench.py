@@ -520,8 +520,16 @@ def run_batched(dgc, torch, dev, stream, args):
         for prec, tag in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
             ws = torch.empty(dgc.dgc_batch_workspace_size(batch, prec) // 8 + 64, dtype=torch.float64, device=dev)
             dts = torch.zeros(len(meshes), dtype=torch.float64, device=dev)
-            tiles_b, tune_ms = dgc.dgc_batch_autotune(batch, prec, cdev, 0.3, dts, ws,
-                                                      reps=3 if tag == "fp32mixed" else 1)
+            if args.tiles:  # fixed tiles (a profiler's command), else the autotuner's
+                for kc, t in zip((dgc.DGC_K_FIRST, dgc.DGC_K_COLOR, dgc.DGC_K_LAST), args.tiles.split(",")):
+                    e, tp = (int(v) for v in t.split("x"))
+                    dgc.dgc_batch_set_tile(batch, kc, e, tp if tag == "fp32mixed" else 2)
+                tiles_b = {k: (int(t.split("x")[0]), int(t.split("x")[1]) if tag == "fp32mixed" else 2)
+                           for k, t in zip(("first", "color", "last"), args.tiles.split(","))}
+                tune_ms = None
+            else:
+                tiles_b, tune_ms = dgc.dgc_batch_autotune(batch, prec, cdev, 0.3, dts, ws,
+                                                          reps=3 if tag == "fp32mixed" else 1)
             k = max(3, args.steps) if tag == "fp32mixed" else 3
             ms = time_steps(torch, lambda: dgc.dgc_batch_rk_step(batch, prec, cdev, 0.3, dts, ws), k, stream)
             out[f"batched_{tag}"] = {
@@ -529,7 +537,42 @@ def run_batched(dgc, torch, dev, stream, args):
                 "elements": sum(m.info["ne"] for m in meshes), "dofs": dofs,
                 "launches_per_step": dgc.dgc_batch_launch_count(batch), "graph": True,
                 "tiles": {k: {"edges_per_block": v[0], "threads_per_edge": v[1]} for k, v in tiles_b.items()},
-                "autotune_best_ms": round(tune_ms, 4)}
+                "autotune_best_ms": round(tune_ms, 4) if tune_ms is not None else None}
+            hbm, _ = peaks()
+            infos = [m.info for m in meshes]
+            if tag == "fp32mixed":
+                # whole step against the paper-structure model, and per kernel class from
+                # a profiled pass (event pairs around every launch, graph off)
+                pm = sum(i["ne"] * ((2 + 3 * 3) * 4 * i["M"] * i["np"] + 40 + 1.5 * 48) for i in infos)
+                out[f"batched_{tag}"]["paper_structure"] = {
+                    "bytes_per_rhs": int(pm), "gbs": round(pm / (ms / 3 * 1e-3) / 1e9, 1),
+                    "frac": round(pm / (ms / 3 * 1e-3) / 1e9 / hbm, 3)}
+                dgc.dgc_batch_set_option(batch, dgc.DGC_OPT_PROFILE, 1)
+                dgc.dgc_batch_profile_collect(batch)
+                msp = time_steps(torch, lambda: dgc.dgc_batch_rk_step(batch, prec, cdev, 0.3, dts, ws), k, stream)
+                prof = dgc.dgc_batch_profile_collect(batch)
+                dgc.dgc_batch_set_option(batch, dgc.DGC_OPT_PROFILE, 0)
+                kern = {}
+                for cls, (tms, nl) in prof.items():
+                    calls = nl // k if cls == "cfl" else nl
+                    b = 0.0
+                    for i in infos:
+                        nv, rec = i["M"] * i["np"], 4 * i["M"] * (i["np"] + 1)
+                        b += class_bytes(cls, i["ne"], i["ne"] // 2, nv, 2, "mixed", rec=rec)
+                    avg = tms / (k if cls == "cfl" else calls)  # the CFL class: both passes and the reset, per step
+                    kern[cls] = {"launches_per_step": nl // k, "avg_ms": round(avg, 5),
+                                 "share": round(tms / (msp * k), 4), "alg_bytes": int(b),
+                                 "alg_gbs": round(b / (avg * 1e-3) / 1e9, 1),
+                                 "frac_hbm": round(b / (avg * 1e-3) / 1e9 / hbm, 3)}
+                out[f"batched_{tag}"]["profiled_ms_per_step"] = round(msp, 4)
+                out[f"batched_{tag}"]["kernels"] = kern
+            else:
+                fl = 3 * sum(flops_per_rhs(i["ne"], i["M"] * i["np"], i["nqv"], i["nqf"]) for i in infos)
+                p64 = fp64_peak_tflops(torch, dev)
+                out[f"batched_{tag}"]["roofline"] = {
+                    "bound": "alu", "achieved": round(fl / (ms * 1e-3) / 1e12, 3), "peak": round(p64, 3),
+                    "unit": "TFLOP/s", "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 (torch)",
+                    "frac": round(fl / (ms * 1e-3) / 1e12 / p64, 3)}
             del ws
     finally:
         dgc.dgc_batch_destroy(batch)

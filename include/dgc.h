@@ -365,6 +365,16 @@ dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_
                               int reps, void* stream, int* edges_per_block, int* threads_per_edge,
                               double* ms_per_step);
 dgc_status dgc_batch_launch_count(const dgc_batch* batch, int64_t* launches);
+/* A batch's tile of one kernel class (DGC_K_FIRST, DGC_K_COLOR, DGC_K_LAST), as dgc_set_tile
+ * for a mesh; threads per edge 4 applies to the FP32-mixed form (FP64 runs 2). */
+dgc_status dgc_batch_set_tile(dgc_batch* batch, int kclass, int edges_per_block, int threads_per_edge);
+/* With DGC_OPT_PROFILE set on the batch (dgc_batch_set_option), every step runs without its
+ * graph and records a CUDA event pair on the launch stream around each launch (the reset and
+ * the two CFL passes share one pair, class DGC_K_CFL; the colors are DGC_K_FIRST, DGC_K_COLOR,
+ * DGC_K_LAST).  dgc_batch_profile_collect adds each class's milliseconds and event pairs since
+ * the last collect into ms[] / launches[] (DGC_K_NCLASSES entries, zeroed by the caller),
+ * synchronising on the events, and forgets them. */
+dgc_status dgc_batch_profile_collect(dgc_batch* batch, double* ms, int64_t* launches);
 void dgc_batch_destroy(dgc_batch* batch);
 
 /* Surface-kernel tile of one kernel class of the triangle RK steps (no paper counterpart:

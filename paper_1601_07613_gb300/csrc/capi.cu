@@ -1300,6 +1300,12 @@ struct dgc_batch {
   // on the legacy default stream a caller may pass) and launched on the caller's
   cudaStream_t capture_stream = nullptr;
   int64_t launches = 0;
+  // DGC_OPT_PROFILE: an event pair around every launch (the step then runs
+  // without its graph), per kernel class, for dgc_batch_profile_collect
+  bool profile = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pcls;
+  size_t pused = 0;
 };
 
 namespace {
@@ -1389,20 +1395,42 @@ void batch_prepare(dgc_batch& b, dgc_prec prec, double* const* c_devs, double* d
   std::copy(b.ttpe, b.ttpe + 3, b.key_tpe);
 }
 
+// with DGC_OPT_PROFILE, f()'s launches between an event pair of class cls
+template <typename F>
+int batch_run(dgc_batch& b, cudaStream_t st, int cls, F&& f) {
+  if (!b.profile) return f();
+  while (b.pev.size() < b.pused + 2) {
+    cudaEvent_t e;
+    DGC_CUDA(cudaEventCreate(&e));
+    b.pev.push_back(e);
+  }
+  DGC_CUDA(cudaEventRecord(b.pev[b.pused], st));
+  const int r = f();
+  DGC_CUDA(cudaEventRecord(b.pev[b.pused + 1], st));
+  b.pused += 2;
+  b.pcls.push_back(cls);
+  return r;
+}
+
 // the launches of one step: reset, CFL (2), then per stage the three colors
 int64_t batch_enqueue(dgc_batch& b, dgc_prec prec, double cfl_, cudaStream_t st) {
   const bool mixed = prec == DGC_FP32_MIXED;
   const int n = (int)b.meshes.size(), C = b.ncolors;
-  int64_t launches = batch_init(st, b.dmeshes, n);
+  int64_t launches = batch_run(b, st, DGC_K_CFL, [&] { return batch_init(st, b.dmeshes, n); });
   const BatchTile* et = b.dtiles + b.tile_off[C];
-  launches += batch_cfl(st, b.dmeshes, et, b.tile_off[C + 1] - b.tile_off[C], cfl_, mixed);
+  launches += batch_run(b, st, DGC_K_CFL, [&] {
+    return batch_cfl(st, b.dmeshes, et, b.tile_off[C + 1] - b.tile_off[C], cfl_, mixed);
+  });
   const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
   for (int s = 0; s < 3; ++s)
     for (int c = 1; c <= C; ++c) {
       const SurfMode mode = c == 1 ? SURF_FIRST : (c == C ? SURF_LAST : SURF_RMW);
       const int k = batch_class(c, C), tpe = mixed ? b.ttpe[k] : 2;
-      const int r = batch_surf(st, b.dmeshes, b.dtiles + b.tile_off[c - 1], b.tile_off[c] - b.tile_off[c - 1], s,
-                               A0[s], B0[s], mode, mixed, tpe * b.tepb[k], tpe);
+      const int cls = k == 0 ? DGC_K_FIRST : k == 2 ? DGC_K_LAST : DGC_K_COLOR;
+      const int r = batch_run(b, st, cls, [&] {
+        return batch_surf(st, b.dmeshes, b.dtiles + b.tile_off[c - 1], b.tile_off[c] - b.tile_off[c - 1], s, A0[s],
+                          B0[s], mode, mixed, tpe * b.tepb[k], tpe);
+      });
       if (r < 0) throw Error{DGC_ERR_UNSUPPORTED, "no batched kernel for this configuration"};
       launches += r;
     }
@@ -1458,6 +1486,8 @@ dgc_status dgc_batch_set_option(dgc_batch* batch, dgc_option opt, int64_t value)
       for (int k = 0; k < 3; ++k) b.ttpe[k] = (int)value;
       if (b.exec) cudaGraphExecDestroy(b.exec);
       b.exec = nullptr;
+    } else if (opt == DGC_OPT_PROFILE) {
+      b.profile = value != 0;
     } else if (opt == DGC_OPT_GRAPH) {
       b.use_graph = value != 0;
       if (b.exec) cudaGraphExecDestroy(b.exec);
@@ -1486,7 +1516,7 @@ dgc_status dgc_batch_rk_step(dgc_batch* batch, dgc_prec prec, double* const* c_d
     b.device = dev;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     batch_prepare(b, prec, c_devs, dt_devs, workspace_dev);
-    if (!b.use_graph) {
+    if (!b.use_graph || b.profile) {
       b.launches = batch_enqueue(b, prec, cfl_, st);
     } else {
       if (!b.exec || b.graph_cfl != cfl_) {
@@ -1579,6 +1609,37 @@ dgc_status dgc_batch_autotune(dgc_batch* batch, dgc_prec prec, double* const* c_
   });
 }
 
+dgc_status dgc_batch_set_tile(dgc_batch* batch, int kclass, int edges_per_block, int threads_per_edge) {
+  return guarded([&] {
+    dgc_batch& b = checked_batch(batch);
+    const int k = tile_index(kclass);
+    require(edges_per_block >= 16 && edges_per_block <= 128 && edges_per_block % 16 == 0,
+            "edges per block must be 16..128, a multiple of 16");
+    require(threads_per_edge == 2 || threads_per_edge == 4, "threads per edge must be 2 or 4");
+    require(threads_per_edge * edges_per_block <= 256, "threads per edge x edges per block must not exceed 256");
+    b.tepb[k] = edges_per_block;
+    b.ttpe[k] = threads_per_edge;
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    b.exec = nullptr;
+  });
+}
+
+dgc_status dgc_batch_profile_collect(dgc_batch* batch, double* ms, int64_t* launches) {
+  return guarded([&] {
+    dgc_batch& b = checked_batch(batch);
+    require(ms != nullptr && launches != nullptr, "null output");
+    for (size_t i = 0; i < b.pcls.size(); ++i) {
+      DGC_CUDA(cudaEventSynchronize(b.pev[2 * i + 1]));
+      float t = 0.f;
+      DGC_CUDA(cudaEventElapsedTime(&t, b.pev[2 * i], b.pev[2 * i + 1]));
+      ms[b.pcls[i]] += t;
+      launches[b.pcls[i]] += 1;
+    }
+    b.pcls.clear();
+    b.pused = 0;
+  });
+}
+
 dgc_status dgc_batch_launch_count(const dgc_batch* batch, int64_t* launches) {
   return guarded([&] {
     require(batch != nullptr && launches != nullptr, "null argument");
@@ -1589,6 +1650,7 @@ dgc_status dgc_batch_launch_count(const dgc_batch* batch, int64_t* launches) {
 void dgc_batch_destroy(dgc_batch* batch) {
   if (!batch) return;
   batch_release(*batch);
+  for (cudaEvent_t e : batch->pev) cudaEventDestroy(e);
   delete batch;
 }
 

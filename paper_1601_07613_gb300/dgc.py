@@ -85,6 +85,8 @@ SIGNATURES = {
     "dgc_batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_double, _P, _P, _I64, C.c_int, _P,
                                      C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
     "dgc_batch_launch_count": (C.c_int, [_P, _I64P]),
+    "dgc_batch_profile_collect": (C.c_int, [_P, _DP, _I64P]),
+    "dgc_batch_set_tile": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "dgc_batch_destroy": (None, [_P]),
     "dgc_destroy": (None, [_P]),
 }
@@ -447,6 +449,17 @@ def dgc_batch_launch_count(batch) -> int:
     b = C.c_int64()
     _check(lib().dgc_batch_launch_count(batch, C.byref(b)))
     return b.value
+
+
+def dgc_batch_set_tile(batch, kclass: int, edges_per_block: int, threads_per_edge: int):
+    _check(lib().dgc_batch_set_tile(batch, kclass, edges_per_block, threads_per_edge))
+
+
+def dgc_batch_profile_collect(batch) -> dict:
+    ms = (C.c_double * 16)()
+    n = (C.c_int64 * 16)()
+    _check(lib().dgc_batch_profile_collect(batch, ms, n))
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES) if n[i] > 0}
 
 
 def dgc_batch_destroy(batch):

@@ -275,3 +275,33 @@ def test_full_size_batch_sampled(torch_dev, oracle_mod, batch64, prec):
         om = oracle_mod.OracleMesh.from_input(mis[i])
         dt = om.dt(specs[i]["p"], states[i], 0.3)
         assert abs(dts[i].item() - dt) < 1e-13 * dt, i
+
+
+def test_batch_profile_collect(torch_dev):
+    """DGC_OPT_PROFILE on a batch: event pairs per launch (graph off), the same
+    states as the graph replay."""
+    torch, dev = torch_dev
+    meshes, states = _meshes_and_states()
+    prec = dgc.DGC_FP32_MIXED
+    out = []
+    for profile in (0, 1):
+        cb = [torch.empty(m.state_shape(), dtype=torch.float64, device=dev) for m in meshes]
+        for m, c, a in zip(meshes, states, cb):
+            dgc.dgc_import_state(m.h, c, a)
+        batch = dgc.dgc_batch_create(meshes)
+        dgc.dgc_batch_set_option(batch, dgc.DGC_OPT_PROFILE, profile)
+        ws = torch.empty(dgc.dgc_batch_workspace_size(batch, prec) // 8 + 64, dtype=torch.float64, device=dev)
+        dts = torch.zeros(len(meshes), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            dgc.dgc_batch_rk_step(batch, prec, cb, 0.3, dts, ws)
+        torch.cuda.synchronize()
+        if profile:
+            prof = dgc.dgc_batch_profile_collect(batch)
+            assert {k: v[1] for k, v in prof.items()} == {"cfl": 4, "first": 6, "color": 6, "last": 6}
+            assert all(v[0] > 0 for v in prof.values())
+        out.append([x.clone() for x in cb])
+        dgc.dgc_batch_destroy(batch)
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+    for m in meshes:
+        m.close()
