@@ -127,6 +127,7 @@ class _Build:
         L.orc_mesh_nvert.argtypes = [P]
         L.orc_mesh_elements.argtypes = [P, C.POINTER(C.c_int32), dp]
         L.orc_mesh_refined.argtypes = [P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]
+        L.orc_transfer.argtypes = [P, P, C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, dp, dp]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
         self.L = L
@@ -315,10 +316,32 @@ class OracleMesh:
         m.ns = int(B.L.orc_mesh_nsides(h))
         m.nv = int(B.L.orc_mesh_nvert(h))
         m._L = self._L
+        m._parent = self
+        m._flag = flag
         m.colors = np.zeros(m.ns, np.int8)
         m.hanging = np.zeros(m.ns, np.int8)
         B.check(B.L.orc_mesh_refined(h, _i8(m.colors), _i8(m.hanging)))
         return m
+
+    def prolong(self, p: int, c_coarse: np.ndarray) -> np.ndarray:
+        """For a mesh made by refine(): the parent mesh's state [E0][M][Np] projected
+        onto this mesh (each child the L2 projection of its parent's polynomial)."""
+        B = self._b
+        c = B.arr(c_coarse)
+        out = np.zeros((self.ne, c.shape[1], c.shape[2]), self.real)
+        B.check(B.L.orc_transfer(self._parent._h, self._h, self._flag.ctypes.data_as(C.POINTER(C.c_uint8)), p,
+                                 c.shape[1], 0, B.ptr(c), B.ptr(out)))
+        return out
+
+    def restrict(self, p: int, c_fine: np.ndarray) -> np.ndarray:
+        """For a mesh made by refine(): this mesh's state projected onto the parent mesh
+        (each parent the L2 projection of its children's piecewise polynomial)."""
+        B = self._b
+        c = B.arr(c_fine)
+        out = np.zeros((self._parent.ne, c.shape[1], c.shape[2]), self.real)
+        B.check(B.L.orc_transfer(self._parent._h, self._h, self._flag.ctypes.data_as(C.POINTER(C.c_uint8)), p,
+                                 c.shape[1], 1, B.ptr(c), B.ptr(out)))
+        return out
 
     def elements(self):
         """Vertex ids [E][nvpe] and unwrapped coordinates [E][nvpe][dim] (nvpe = 4 for

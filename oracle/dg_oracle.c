@@ -1556,6 +1556,80 @@ int orc_rk_step(void *h, int p, real *c, real cfl, real dt_in, real *dt_out) {
 }
 
 /* ======================================================================= */
+/* State transfer between a mesh and its one-level refinement (Sec. 3.2)   */
+/* ======================================================================= */
+/* coarse: the mesh before refinement, fine: orc_refine(coarse, ., flag), whose
+ * children of coarse element e are fine elements first(e) .. first(e) + 3 (an
+ * unrefined element is one fine element).  States [E][M][Np], each element's
+ * coefficients w.r.t. its own reference-orthonormal basis.
+ *   dir 0, prolongation: a child's coefficients are the L2 projection of its
+ *     parent's polynomial onto the child, d_j = sum_q w_q u(x_q) phi_j(rho_q)
+ *     over the child's volume rule (exact: the integrand has degree 2p);
+ *   dir 1, restriction: a parent's coefficients are the L2 projection of its
+ *     children's piecewise polynomial, c_k = sum_children (detJ_child /
+ *     detJ_parent) sum_q w_q u_child(rho_q) phi_k(r_parent(x_q)), each child
+ *     integrated with its own rule.
+ * Points are mapped through physical space: a child's reference point to its
+ * physical point, then the parent's reference coordinates by inverting the
+ * parent's affine map. */
+int orc_transfer(void *hc, void *hf, const uint8_t *flag, int p, int M, int dir, const real *cin, real *cout) {
+  const orc_mesh *mc = (const orc_mesh *)hc, *mf = (const orc_mesh *)hf;
+  if (mc->dim != 2 || mc->quad || mf->dim != 2) return fail("transfer: triangle meshes only");
+  const int Np = npoly_tri(p);
+  orc_rules R;
+  if (rules_make(2, 0, 1, default_vol_n1(2, p), &R)) {
+    rules_free(&R);
+    return -1;
+  }
+  int64_t n = 0;
+  for (int64_t e = 0; e < mc->ne; ++e) {
+    const int kids = flag[e] ? 4 : 1;
+    if (n + kids > mf->ne) {
+      rules_free(&R);
+      return fail("transfer: the meshes do not match the flags");
+    }
+    if (!flag[e]) {
+      const real *src = cin + (dir == 0 ? e : n) * M * Np;
+      real *dst = cout + (dir == 0 ? n : e) * M * Np;
+      for (int i = 0; i < M * Np; ++i) dst[i] = src[i];
+      n += 1;
+      continue;
+    }
+    const real *ce = dir == 0 ? cin + e * M * Np : NULL;
+    real *pe = dir == 1 ? cout + e * M * Np : NULL;
+    if (pe)
+      for (int i = 0; i < M * Np; ++i) pe[i] = 0.0;
+    for (int c = 0; c < 4; ++c, ++n) {
+      const real *Xc = mf->X + n * 6;
+      real *de = dir == 0 ? cout + n * M * Np : NULL;
+      const real *dc = dir == 1 ? cin + n * M * Np : NULL;
+      if (de)
+        for (int i = 0; i < M * Np; ++i) de[i] = 0.0;
+      const real ratio = mf->detJ[n] / mc->detJ[e];
+      for (int q = 0; q < R.nv; ++q) {
+        real rho[3] = {R.vr[q], R.vs[q], 0.0}, x[3], rs[3], phi[ORC_MAXNP], U[ORC_MAXM];
+        for (int a = 0; a < 2; ++a) x[a] = Xc[a] + (Xc[2 + a] - Xc[a]) * rho[0] + (Xc[4 + a] - Xc[a]) * rho[1];
+        ref_coords(mc, e, x, rs);
+        if (dir == 0) {
+          eval_state(mc, p, M, Np, ce, rs, U);  /* the parent's polynomial at the child's point */
+          basis_eval(mf, p, rho, phi, NULL, NULL, NULL);
+          for (int k = 0; k < M; ++k)
+            for (int j = 0; j < Np; ++j) de[k * Np + j] += R.vw[q] * U[k] * phi[j];
+        } else {
+          eval_state(mf, p, M, Np, dc, rho, U);  /* the child's polynomial at its own point */
+          basis_eval(mc, p, rs, phi, NULL, NULL, NULL);
+          for (int k = 0; k < M; ++k)
+            for (int j = 0; j < Np; ++j) pe[k * Np + j] += ratio * R.vw[q] * U[k] * phi[j];
+        }
+      }
+    }
+  }
+  rules_free(&R);
+  if (n != mf->ne) return fail("transfer: the meshes do not match the flags");
+  return 0;
+}
+
+/* ======================================================================= */
 /* Initial conditions: L2 projection onto the orthonormal basis             */
 /* ======================================================================= */
 int orc_num_vol_points(int dim, int p) {
