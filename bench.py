@@ -682,6 +682,20 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
             entry[f"rhs_colored_unfused_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
             dgc.dgc_set_option(m.h, dgc.DGC_OPT_FUSE, 1)
             del buf
+        if refine is not None:
+            # dynamic adaptivity on the device: the Sec. 3.2 color map of the refined
+            # sides, and the state moved to and from the mesh before refinement
+            _, map_ms = dgc.dgc_refine_colors_device(m.h, info["ns"])
+            ne0 = mi.ne
+            cc = torch.zeros((ne0, info["M"], info["np"]), dtype=torch.float64, device=dev)
+            pro = lambda: dgc.dgc_prolong_state(m.h, cc, c)
+            res = lambda: dgc.dgc_restrict_state(m.h, c, cc)
+            pro()
+            res()
+            entry["adapt"] = {"host_refine_s": round(prep_s, 4), "device_color_map_ms": round(map_ms, 4),
+                              "prolong_ms": round(time_steps(torch, pro, 10, stream), 4),
+                              "restrict_ms": round(time_steps(torch, res, 10, stream), 4)}
+            del cc
         out[tag] = entry
         del c, r
         m.close()

@@ -224,6 +224,29 @@ dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems);
  * not refined.  Host only; states sized for the refined mesh are invalid afterwards. */
 dgc_status dgc_coarsen(dgc_mesh* mesh);
 
+/* Dynamic adaptivity on the device, for a mesh refined by dgc_refine (Sec. 3.2):
+ *   dgc_prolong_state: the state of the mesh before refinement (device, [E0][M][Np] FP64
+ *     in that mesh's internal order, as it was imported before dgc_refine) to the refined
+ *     mesh's state (device, internal order): each child takes the L2 projection of its
+ *     parent's polynomial (exact: the child's space contains it); unrefined elements are
+ *     copied.
+ *   dgc_restrict_state: the refined mesh's state to the state of the mesh before
+ *     refinement (call it before dgc_coarsen; the result is in the internal order the mesh
+ *     has again after dgc_coarsen): each parent takes the L2 projection of its four
+ *     children's piecewise polynomial; unrefined elements are copied.  Restriction after
+ *     prolongation is the identity; both conserve the integral of the solution.
+ *   Triangle meshes, FP64 states, stream-ordered (the first call after a refinement
+ *   uploads the mesh, which allocates).  DGC_ERR_ARG if the mesh is not refined.
+ *   dgc_refine_colors_device: the Sec. 3.2 color map of the refined sides evaluated on the
+ *     device, one thread per side, from the coloring before refinement (a split edge's
+ *     halves take c and c + 3, an interior edge its parallel parent edge's color, other
+ *     edges keep theirs); writes the colors in the refined mesh's original side order to
+ *     the host array colors[Ns] (the same colors dgc_refine assigned on the host) and the
+ *     map kernel's time in ms (may be NULL).  Allocates its scratch, synchronises. */
+dgc_status dgc_prolong_state(dgc_mesh* mesh, const double* c_coarse_dev, double* c_fine_dev, void* stream);
+dgc_status dgc_restrict_state(dgc_mesh* mesh, const double* c_fine_dev, double* c_coarse_dev, void* stream);
+dgc_status dgc_refine_colors_device(dgc_mesh* mesh, int8_t* colors, double* ms, void* stream);
+
 /* Per edge (original order): the half (0: next to the coarse element's local edge's first
  * vertex, 1: the other) of the right element's local edge that a hanging edge covers, or
  * -1 for a conforming or boundary edge. */

@@ -71,8 +71,13 @@ std::vector<std::pair<const Mesh*, Staging>> g_staging;
 
 double* staging_for(const Mesh& m) {
   std::lock_guard<std::mutex> lk(g_stage_mu);
-  for (auto& s : g_staging)
-    if (s.first == &m) return s.second.ptr;
+  for (size_t i = 0; i < g_staging.size(); ++i)
+    if (g_staging[i].first == &m) {
+      if (g_staging[i].second.bytes >= state_bytes(m)) return g_staging[i].second.ptr;
+      cudaFreeHost(g_staging[i].second.ptr);  // the mesh grew (refinement): a larger buffer
+      g_staging.erase(g_staging.begin() + i);
+      break;
+    }
   Staging s;
   s.bytes = state_bytes(m);
   DGC_CUDA(cudaMallocHost(&s.ptr, s.bytes));
@@ -125,6 +130,52 @@ T* dalloc(int64_t n) {
                 std::string("cudaMalloc: ") + cudaGetErrorString(e)};
   }
   return p;
+}
+
+// Refined triangle meshes: the tables of the state transfer to and from the
+// mesh before refinement (internal orders of both), and the child projections
+// P_c[j][k] = sum_q w_q phi_j(rho_q) phi_k(A_c rho_q) of the reference triangle
+// (A_c: child c's reference triangle inside its parent's, children ordered as
+// refine() makes them: [v0, m01, m20], [m01, v1, m12], [m20, m12, v2],
+// [m01, m12, m20]); the volume rule integrates the degree-2p products exactly.
+void upload_transfer(const Mesh& m, DeviceMesh& d) {
+  const Mesh::Base& b = m.base;
+  const int np = m.np;
+  std::vector<int32_t> src(m.ne, -1), kids((size_t)b.ne * 4, -1);
+  std::vector<int8_t> kind(m.ne, 4);
+  for (int64_t e = 0, n = 0; e < b.ne; ++e) {
+    const int32_t ce = b.elem_new_of_old[e];
+    const int k = b.flag[e] ? 4 : 1;
+    for (int c = 0; c < k; ++c, ++n) {
+      const int32_t fe = m.elem_new_of_old[n];
+      src[fe] = ce;
+      kind[fe] = (int8_t)(k == 4 ? c : 4);
+      kids[(size_t)ce * 4 + c] = fe;
+    }
+  }
+  // A_c (rho, sigma) = o + a rho + b sigma in the parent's reference coordinates
+  const double A[4][6] = {{0.0, 0.0, 0.5, 0.0, 0.0, 0.5},
+                          {0.5, 0.0, 0.5, 0.0, 0.0, 0.5},
+                          {0.0, 0.5, 0.5, 0.0, 0.0, 0.5},
+                          {0.5, 0.0, 0.0, 0.5, -0.5, 0.5}};
+  std::vector<double> P((size_t)4 * np * np, 0.0), phi(np), phic(np);
+  for (int c = 0; c < 4; ++c)
+    for (int q = 0; q < m.tab.nqv; ++q) {
+      const double x[2] = {m.tab.vr[q], m.tab.vs[q]};
+      const double y[2] = {A[c][0] + A[c][2] * x[0] + A[c][4] * x[1], A[c][1] + A[c][3] * x[0] + A[c][5] * x[1]};
+      basis_eval(2, m.p, x, phic.data(), nullptr);
+      basis_eval(2, m.p, y, phi.data(), nullptr);
+      for (int j = 0; j < np; ++j)
+        for (int k = 0; k < np; ++k) P[((size_t)c * np + j) * np + k] += m.tab.vw[q] * phic[j] * phi[k];
+    }
+  d.xf_src = dalloc<int32_t>(m.ne);
+  d.xf_kind = dalloc<int8_t>(m.ne);
+  d.xf_kids = dalloc<int32_t>((int64_t)kids.size());
+  d.xf_P = dalloc<double>((int64_t)P.size());
+  DGC_CUDA(cudaMemcpy(d.xf_src, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice));
+  DGC_CUDA(cudaMemcpy(d.xf_kind, kind.data(), kind.size(), cudaMemcpyHostToDevice));
+  DGC_CUDA(cudaMemcpy(d.xf_kids, kids.data(), sizeof(int32_t) * kids.size(), cudaMemcpyHostToDevice));
+  DGC_CUDA(cudaMemcpy(d.xf_P, P.data(), sizeof(double) * P.size(), cudaMemcpyHostToDevice));
 }
 
 // Upload the renumbered mesh: per element inverse Jacobian and inradius, per
@@ -211,6 +262,7 @@ void upload(Mesh& m) {
     DGC_CUDA(cudaMemcpy(d->slots, slots.data(), sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice));
     if (dim == 3) tet_upload_tables(m.p, m.tab, *d);
     if (m.quad) quad_upload_tables(m.p, m.tab);
+    if (m.refined) upload_transfer(m, *d);
   } catch (...) {
     m.dev = d.release();
     device_free(m);
@@ -555,6 +607,10 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->ftab);
   cudaFree(m.dev->ftabd);
   cudaFree(m.dev->cfl_est);
+  cudaFree(m.dev->xf_src);
+  cudaFree(m.dev->xf_kind);
+  cudaFree(m.dev->xf_kids);
+  cudaFree(m.dev->xf_P);
   delete m.dev;
   m.dev = nullptr;
   m.dirty = true;
@@ -999,6 +1055,80 @@ dgc_status dgc_rk_step(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl_, 
     x.pdl = m.pdl;
     rk_step_body(m, x, prec, c_dev, cfl_, dt_dev, w, [&](int cls, auto&& f) { run(m, x, cls, n, f); });
     finish(m, n);
+  });
+}
+
+dgc_status dgc_prolong_state(dgc_mesh* mesh, const double* c_coarse_dev, double* c_fine_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.refined, "mesh is not refined (dgc_refine first)");
+    check_ptr(c_coarse_dev, "c_coarse_dev");
+    check_ptr(c_fine_dev, "c_fine_dev");
+    Ctx x = ready(m, stream);
+    const int r = transfer_state(x.st, true, c_coarse_dev, c_fine_dev, m.dev->xf_src, m.dev->xf_kind, nullptr,
+                                 m.dev->xf_P, m.ne, m.M, m.np);
+    if (r < 0) throw Error{DGC_ERR_UNSUPPORTED, "no transfer kernel for this order"};
+    finish(m, r);
+  });
+}
+
+dgc_status dgc_restrict_state(dgc_mesh* mesh, const double* c_fine_dev, double* c_coarse_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.refined, "mesh is not refined (dgc_refine first)");
+    check_ptr(c_coarse_dev, "c_coarse_dev");
+    check_ptr(c_fine_dev, "c_fine_dev");
+    Ctx x = ready(m, stream);
+    const int r = transfer_state(x.st, false, c_fine_dev, c_coarse_dev, nullptr, nullptr, m.dev->xf_kids,
+                                 m.dev->xf_P, m.base.ne, m.M, m.np);
+    if (r < 0) throw Error{DGC_ERR_UNSUPPORTED, "no transfer kernel for this order"};
+    finish(m, r);
+  });
+}
+
+dgc_status dgc_refine_colors_device(dgc_mesh* mesh, int8_t* colors, double* ms, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.refined, "mesh is not refined (dgc_refine first)");
+    require(colors != nullptr, "null output");
+    const Mesh::Base& b = m.base;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int8_t *bc = nullptr, *rule = nullptr, *out = nullptr;
+    int32_t *bf = nullptr, *src = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release = [&] {
+      cudaFree(bc), cudaFree(rule), cudaFree(out), cudaFree(bf), cudaFree(src);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    };
+    try {
+      bc = dalloc<int8_t>(b.ns);
+      bf = dalloc<int32_t>(b.ne * 3);
+      src = dalloc<int32_t>(m.ns);
+      rule = dalloc<int8_t>(m.ns);
+      out = dalloc<int8_t>(m.ns);
+      DGC_CUDA(cudaMemcpyAsync(bc, b.color.data(), b.ns, cudaMemcpyHostToDevice, st));
+      DGC_CUDA(cudaMemcpyAsync(bf, b.face_of.data(), sizeof(int32_t) * b.ne * 3, cudaMemcpyHostToDevice, st));
+      DGC_CUDA(cudaMemcpyAsync(src, b.color_src.data(), sizeof(int32_t) * m.ns, cudaMemcpyHostToDevice, st));
+      DGC_CUDA(cudaMemcpyAsync(rule, b.color_rule.data(), m.ns, cudaMemcpyHostToDevice, st));
+      DGC_CUDA(cudaEventCreate(&e0));
+      DGC_CUDA(cudaEventCreate(&e1));
+      DGC_CUDA(cudaEventRecord(e0, st));
+      refine_colors(st, bc, bf, src, rule, m.ns, out);
+      DGC_CUDA(cudaEventRecord(e1, st));
+      DGC_CUDA(cudaMemcpyAsync(colors, out, m.ns, cudaMemcpyDeviceToHost, st));
+      DGC_CUDA(cudaStreamSynchronize(st));
+      DGC_CUDA(cudaGetLastError());
+      if (ms) {
+        float t = 0.f;
+        DGC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        *ms = t;
+      }
+    } catch (...) {
+      release();
+      throw;
+    }
+    release();
   });
 }
 

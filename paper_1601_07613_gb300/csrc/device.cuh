@@ -27,6 +27,14 @@ struct DeviceMesh {
   float* cfl_est = nullptr; // [E] FP32 step estimates of the CFL pre-pass, then 1 minimum
   int32_t* perm = nullptr;  // [E] internal element id of each original element (import / export)
   double* xfer = nullptr;   // [E][M*Np] state in original order (import / export; allocated on first use)
+  // refined meshes: state transfer to and from the mesh before refinement
+  // (internal orders): per fine element its coarse element and child 0..3 (4:
+  // copy), per coarse element its children's fine ids (kids[1] = -1: one copy),
+  // and the child projections P [4][Np][Np]
+  int32_t* xf_src = nullptr;
+  int8_t* xf_kind = nullptr;
+  int32_t* xf_kids = nullptr;
+  double* xf_P = nullptr;
 };
 
 // Surface-kernel modes (Algorithm 1 and the comparators of Sec. 1).
@@ -185,6 +193,14 @@ int incr_stage_update(const Ctx& c, const float* rhs, const StageArgs& sa);
 int gather_two_pass(const Ctx& c, bool f32, void* rhs, const void* buf);
 // element blocks of nv doubles between original and internal order:
 // to_internal: dst[perm[e]] = src[e]; else dst[e] = src[perm[e]]
+// refinement on the device (kernels_common.cu): the Sec. 3.2 color map of the
+// refined sides, and the state between a mesh and its refinement (prolong: n =
+// fine elements, src / kind per fine element; restrict: n = coarse elements,
+// kids[4] per coarse element; P [4][NP][NP])
+int refine_colors(cudaStream_t st, const int8_t* base_color, const int32_t* base_face_of, const int32_t* src,
+                  const int8_t* rule, int64_t ns, int8_t* out);
+int transfer_state(cudaStream_t st, bool prolong, const double* in, double* out, const int32_t* src,
+                   const int8_t* kind, const int32_t* kids, const double* P, int64_t n, int M, int NP);
 int permute_blocks(cudaStream_t st, double* dst, const double* src, const int32_t* perm, int nv, int64_t ne,
                    bool to_internal);
 

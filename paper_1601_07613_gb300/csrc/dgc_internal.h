@@ -82,6 +82,13 @@ struct Mesh {
     std::vector<int32_t> ev, sl, sr, face_of;
     std::vector<int8_t> sql, sqr, color;
     std::vector<uint8_t> flag;  // refined elements
+    std::vector<int32_t> elem_new_of_old;  // the coarse mesh's internal element order
+    // per refined side (original order), where the Sec. 3.2 map takes its color
+    // from: rule 0 = base side src keeps its color, 1 / 2 = first / second half of
+    // base side src (c, c + 3), 3 + k = interior edge of refined base element src
+    // parallel to its edge k
+    std::vector<int32_t> color_src;
+    std::vector<int8_t> color_rule;
   } base;
   // geometry, original order
   std::vector<double> detJ, Jinv, inradius;  // Jinv [ne][dim][dim] (row k = grad r_k)

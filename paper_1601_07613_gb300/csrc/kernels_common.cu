@@ -128,4 +128,100 @@ int permute_blocks(cudaStream_t st, double* dst, const double* src, const int32_
   return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Refinement (Sec. 3.2) on the device: the 6-color map of the refined sides
+// from the coarse coloring, and the DG state between the coarse mesh and its
+// refinement.
+// ---------------------------------------------------------------------------
+// One thread per refined side: rule 0 keeps base side src's color c, rules 1
+// and 2 (the half next to the smaller and the larger vertex id) give
+// ((c + 3 m - 4) mod 6) + 1 = c and c + 3, rule 3 + k gives the interior edge of
+// refined base element src the color of its edge k (the parallel one).
+__global__ void k_refine_colors(const int8_t* __restrict__ base_color, const int32_t* __restrict__ base_face_of,
+                                const int32_t* __restrict__ src, const int8_t* __restrict__ rule, int64_t ns,
+                                int8_t* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const int r = rule[s];
+  int c;
+  if (r == 0) c = base_color[src[s]];
+  else if (r <= 2) c = (base_color[src[s]] + 3 * r - 4) % 6 + 1;
+  else c = base_color[base_face_of[(int64_t)src[s] * 3 + (r - 3)]];
+  out[s] = (int8_t)c;
+}
+
+int refine_colors(cudaStream_t st, const int8_t* base_color, const int32_t* base_face_of, const int32_t* src,
+                  const int8_t* rule, int64_t ns, int8_t* out) {
+  if (ns <= 0) return 0;
+  const int bs = 256;
+  k_refine_colors<<<(unsigned)((ns + bs - 1) / bs), bs, 0, st>>>(base_color, base_face_of, src, rule, ns, out);
+  return 1;
+}
+
+// Prolongation, one thread per fine element and variable: a child c of coarse
+// element src takes out_j = sum_k P_c[j][k] in_k (P_c: the L2 projection of the
+// parent's basis onto the child's, [4][NP][NP]); kind 4 copies the element.
+__global__ void k_prolong(const double* __restrict__ cc, double* __restrict__ cf, const int32_t* __restrict__ src,
+                          const int8_t* __restrict__ kind, const double* __restrict__ P, int64_t nef, int M, int NP) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nef * M) return;
+  const int64_t e = i / M;
+  const int m = (int)(i - e * M);
+  const double* in = cc + ((int64_t)src[e] * M + m) * NP;
+  double* out = cf + (e * M + m) * NP;
+  const int c = kind[e];
+  if (c == 4) {
+    for (int j = 0; j < NP; ++j) out[j] = in[j];
+    return;
+  }
+  const double* Pc = P + (int64_t)c * NP * NP;
+  double v[16];
+  for (int k = 0; k < NP; ++k) v[k] = in[k];
+  for (int j = 0; j < NP; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < NP; ++k) s = fma(Pc[j * NP + k], v[k], s);
+    out[j] = s;
+  }
+}
+
+// Restriction, one thread per coarse element and variable: a refined element
+// takes out_k = (1/4) sum_c sum_j P_c[j][k] in^c_j over its children kids[4]
+// (each child a quarter of the parent's area); kids[1] < 0 copies kids[0].
+__global__ void k_restrict(const double* __restrict__ cf, double* __restrict__ cc, const int32_t* __restrict__ kids,
+                           const double* __restrict__ P, int64_t nec, int M, int NP) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nec * M) return;
+  const int64_t e = i / M;
+  const int m = (int)(i - e * M);
+  double* out = cc + (e * M + m) * NP;
+  const int32_t* kd = kids + e * 4;
+  if (kd[1] < 0) {
+    const double* in = cf + ((int64_t)kd[0] * M + m) * NP;
+    for (int j = 0; j < NP; ++j) out[j] = in[j];
+    return;
+  }
+  double acc[16];
+  for (int k = 0; k < NP; ++k) acc[k] = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    const double* in = cf + ((int64_t)kd[c] * M + m) * NP;
+    const double* Pc = P + (int64_t)c * NP * NP;
+    for (int j = 0; j < NP; ++j) {
+      const double v = in[j];
+      for (int k = 0; k < NP; ++k) acc[k] = fma(Pc[j * NP + k], v, acc[k]);
+    }
+  }
+  for (int k = 0; k < NP; ++k) out[k] = 0.25 * acc[k];
+}
+
+int transfer_state(cudaStream_t st, bool prolong, const double* in, double* out, const int32_t* src,
+                   const int8_t* kind, const int32_t* kids, const double* P, int64_t n, int M, int NP) {
+  if (n <= 0) return 0;
+  if (NP > 16) return -1;
+  const int bs = 128;
+  const unsigned grid = (unsigned)((n * M + bs - 1) / bs);
+  if (prolong) k_prolong<<<grid, bs, 0, st>>>(in, out, src, kind, P, n, M, NP);
+  else k_restrict<<<grid, bs, 0, st>>>(in, out, kids, P, n, M, NP);
+  return 1;
+}
+
 }  // namespace dgc

@@ -947,10 +947,13 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
       }
   }
 
-  std::vector<int32_t> sl, sr;
-  std::vector<int8_t> sql, sqr, half, col;
+  std::vector<int32_t> sl, sr, csrc;
+  std::vector<int8_t> sql, sqr, half, col, crule;
   const size_t cap = (size_t)ns0 * 2 + (size_t)(ne - ne0);
   sl.reserve(cap), sr.reserve(cap), sql.reserve(cap), sqr.reserve(cap), half.reserve(cap), col.reserve(cap);
+  csrc.reserve(cap), crule.reserve(cap);
+  int32_t src = 0;
+  int8_t rule = 0;
   auto add = [&](int64_t l, int64_t r, int ql, int qr, int h, int c) {
     sl.push_back((int32_t)l);
     sr.push_back((int32_t)r);
@@ -958,11 +961,15 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
     sqr.push_back((int8_t)qr);
     half.push_back((int8_t)h);
     col.push_back((int8_t)c);
+    csrc.push_back(src);
+    crule.push_back(rule);
   };
   for (int64_t s = 0; s < ns0; ++s) {
     const int32_t l = m.sl[s], r = m.sr[s];
     const int ql = m.sql[s], qr = m.sqr[s], c = m.color[s];
     const bool Rl = flag[l] != 0, Rr = r >= 0 && flag[r] != 0;
+    src = (int32_t)s;
+    rule = 0;
     if (!Rl && !Rr) {
       add(first[l], r >= 0 ? first[r] : -1, ql, r >= 0 ? qr : -1, -1, c);
       continue;
@@ -972,6 +979,7 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
     for (int child = 1; child <= 2; ++child) {
       const int32_t P = child == 1 ? std::min(a, b) : std::max(a, b);  // endpoint the half touches
       const int cc = (c + 3 * child - 4) % 6 + 1;
+      rule = (int8_t)child;
       const int64_t lc = first[l] + (P == a ? ql : (ql + 1) % 3);
       if (r < 0) {
         add(lc, -1, ql, -1, -1, cc);
@@ -988,8 +996,12 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
     const int64_t n = first[e];
     int c[3];
     for (int k = 0; k < 3; ++k) c[k] = m.color[m.face_of[(size_t)e * 3 + k]];
+    src = (int32_t)e;
+    rule = 3 + 1;
     add(n + 0, n + 3, 1, 2, -1, c[1]);  // m01-m20, parallel to parent edge 1
+    rule = 3 + 2;
     add(n + 1, n + 3, 2, 0, -1, c[2]);  // m12-m01, parallel to parent edge 2
+    rule = 3 + 0;
     add(n + 2, n + 3, 0, 1, -1, c[0]);  // m20-m12, parallel to parent edge 0
   }
   const int64_t ns = (int64_t)sl.size();
@@ -1012,6 +1024,9 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   b.ne = m.ne;
   b.ns = m.ns;
   b.flag = flag;
+  b.elem_new_of_old = m.elem_new_of_old;
+  b.color_src.swap(csrc);
+  b.color_rule.swap(crule);
   m.ne = ne;
   m.nv = nv;
   m.ns = ns;

@@ -75,6 +75,9 @@ SIGNATURES = {
     "dgc_last_error": (C.c_char_p, []),
     "dgc_rk_step_static": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P]),
     "dgc_set_tile": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "dgc_prolong_state": (C.c_int, [_P, _P, _P, _P]),
+    "dgc_restrict_state": (C.c_int, [_P, _P, _P, _P]),
+    "dgc_refine_colors_device": (C.c_int, [_P, C.POINTER(C.c_int8), _DP, _P]),
     "dgc_get_tile": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "dgc_autotune": (C.c_int, [_P, C.c_int, _P, C.c_double, _P, _P, _I64, C.c_int, _P, C.POINTER(C.c_int),
                                C.POINTER(C.c_int), _DP]),
@@ -362,6 +365,23 @@ def dgc_set_option(mesh, opt: int, value: int):
 
 
 DGC_K_FIRST, DGC_K_COLOR, DGC_K_LAST = 2, 3, 4
+
+
+def dgc_prolong_state(mesh, c_coarse_dev, c_fine_dev, stream=None):
+    _check(lib().dgc_prolong_state(mesh, _dptr(c_coarse_dev), _dptr(c_fine_dev), _stream(stream)))
+
+
+def dgc_restrict_state(mesh, c_fine_dev, c_coarse_dev, stream=None):
+    _check(lib().dgc_restrict_state(mesh, _dptr(c_fine_dev), _dptr(c_coarse_dev), _stream(stream)))
+
+
+def dgc_refine_colors_device(mesh, ns: int, stream=None):
+    """Returns (colors int8[Ns] in original side order, map kernel ms)."""
+    out = np.zeros(ns, np.int8)
+    ms = C.c_double()
+    _check(lib().dgc_refine_colors_device(mesh, out.ctypes.data_as(C.POINTER(C.c_int8)), C.byref(ms),
+                                          _stream(stream)))
+    return out, ms.value
 
 
 def dgc_set_tile(mesh, kclass: int, edges_per_block: int, threads_per_edge: int):
