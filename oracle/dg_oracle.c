@@ -499,7 +499,6 @@ static int elem_geometry(orc_mesh *m, int64_t e) {
     for (int k = 0; k < dim; ++k) J[a * dim + k] = X[kv[k] * dim + a] - X[a];
   real det = det_and_inv(dim, J, m->Jinv + e * dim * dim);
   m->detJ[e] = det;
-  if (m->quad && nf == 3) m->nonaffine++;
   if (m->quad && nf == 4) {
     real scale = 0.0, off = 0.0;
     for (int c = 0; c < 4; ++c) {
@@ -1210,6 +1209,21 @@ static int basis_eval(const orc_mesh *m, int p, const real *x, real *phi, real *
   return orc_basis_tet(p, x[0], x[1], x[2], phi, d0, d1, d2);
 }
 
+/* Element e's own space on a hybrid triangle/quadrilateral mesh (Sec. 3.1,
+ * Table 2's hybrid mesh; reading: each element carries the space of its kind,
+ * P_p on a triangle and Q_p on a quadrilateral, and the state is stored with
+ * the larger count Np = (p+1)^2 per variable, a triangle using the first
+ * (p+1)(p+2)/2 entries).  On other meshes these are the mesh-wide ones. */
+static int elem_is_quad(const orc_mesh *m, int64_t e) { return m->quad && m->ev[e * 4 + 3] >= 0; }
+static int npoly_e(const orc_mesh *m, int64_t e, int p) {
+  return m->quad && !elem_is_quad(m, e) ? npoly_tri(p) : npoly_m(m, p);
+}
+static int basis_eval_e(const orc_mesh *m, int64_t e, int p, const real *x, real *phi, real *d0, real *d1,
+                        real *d2) {
+  if (m->quad && !elem_is_quad(m, e)) return orc_basis_tri(p, x[0], x[1], phi, d0, d1);
+  return basis_eval(m, p, x, phi, d0, d1, d2);
+}
+
 /* reference coordinates of physical point x in element e (nearest periodic
  * image of x to the element's centroid) */
 static void ref_coords(const orc_mesh *m, int64_t e, const real *x, real *rs) {
@@ -1242,6 +1256,25 @@ static void eval_state(const orc_mesh *m, int p, int M, int Np, const real *c, c
   }
 }
 
+/* the state of element e (block c, stride Np per variable) at reference point rs,
+ * in e's own space */
+static void eval_state_e(const orc_mesh *m, int64_t e, int p, int M, int Np, const real *c, const real *rs,
+                         real *U) {
+  if (!(m->quad && !elem_is_quad(m, e))) {
+    eval_state(m, p, M, Np, c, rs, U);
+    return;
+  }
+  real phi[ORC_MAXNP];
+  const int n = basis_eval_e(m, e, p, rs, phi, NULL, NULL, NULL);
+  for (int k = 0; k < M; ++k) {
+    real v = 0.0;
+    for (int j = 0; j < n; ++j) v += c[k * Np + j] * phi[j];
+    U[k] = v;
+  }
+}
+
+
+
 /* Quadrature rules of one call, computed once.  Default sizes (reading, fixed
  * by the configurations' "7-pt edge / 16-pt area" at p = 3): triangle edges
  * 2p+1 Gauss points, triangle areas (p+1)^2; tetrahedron faces (p+2)^2,
@@ -1253,6 +1286,10 @@ typedef struct {
   int dim, nv, nf;
   real *vr, *vs, *vt, *vw;
   real *fa, *fb, *fw;
+  /* quadrilateral (and hybrid) meshes: the triangle volume rule of the same
+   * size, for the triangles of a hybrid mesh */
+  int tnv;
+  real *tvr, *tvs, *tvw;
 } orc_rules;
 
 static int default_face_n1(int dim, int p) { return dim == 2 ? 2 * p + 1 : p + 2; }
@@ -1266,6 +1303,9 @@ static void rules_free(orc_rules *R) {
   free(R->fa);
   free(R->fb);
   free(R->fw);
+  free(R->tvr);
+  free(R->tvs);
+  free(R->tvw);
   memset(R, 0, sizeof *R);
 }
 
@@ -1282,6 +1322,13 @@ static int rules_make(int dim, int quad, int nf1, int nv1, orc_rules *R) {
            : dim == 2 ? orc_tri_rule(nv1, R->vr, R->vs, R->vw)
                       : orc_tet_rule(nv1, R->vr, R->vs, R->vt, R->vw);
   if (rc) return rc;
+  if (quad) {
+    R->tnv = nv1 * nv1;
+    R->tvr = (real *)malloc(sizeof(real) * R->tnv);
+    R->tvs = (real *)malloc(sizeof(real) * R->tnv);
+    R->tvw = (real *)malloc(sizeof(real) * R->tnv);
+    if (orc_tri_rule(nv1, R->tvr, R->tvs, R->tvw)) return -1;
+  }
   R->nf = dim == 2 ? nf1 : nf1 * nf1;
   R->fa = (real *)malloc(sizeof(real) * R->nf);
   R->fb = (real *)calloc(R->nf, sizeof(real));
@@ -1298,6 +1345,17 @@ static int rules_make(int dim, int quad, int nf1, int nv1, orc_rules *R) {
     for (int i = 0; i < R->nf; ++i) R->fw[i] *= 2.0;
   }
   return 0;
+}
+
+/* element e's volume rule */
+static int vol_rule_e(const orc_rules *R, const orc_mesh *m, int64_t e, const real **vr, const real **vs,
+                      const real **vt, const real **vw) {
+  if (m->quad && !elem_is_quad(m, e)) {
+    *vr = R->tvr, *vs = R->tvs, *vt = R->vt, *vw = R->tvw;
+    return R->tnv;
+  }
+  *vr = R->vr, *vs = R->vs, *vt = R->vt, *vw = R->vw;
+  return R->nv;
 }
 
 /* One face of element e, in physical space: its measure, its outward unit
@@ -1371,7 +1429,7 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim;
   if (p < 0 || p > ORC_MAXP) return fail("rhs: p out of range");
-  if (m->nonaffine) return fail("rhs: quadrilaterals must be parallelograms (hybrid meshes are colored only)");
+  if (m->nonaffine) return fail("rhs: quadrilaterals must be parallelograms");
   int Np = npoly_m(m, p);
   orc_phys ph = {kind, dim, kind == ORC_EULER ? dim + 2 : 1, {0, 0, 0}};
   if (adv)
@@ -1402,23 +1460,26 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
     real *re = rhs + ii * M * Np;
     for (int i = 0; i < M * Np; ++i) re[i] = 0.0;
     const real *Ji = m->Jinv + e * dim * dim;
+    const int Ne = npoly_e(m, e, p); /* the element's own modes (hybrid: fewer on a triangle) */
+    const real *vr, *vs, *vt, *vw;
+    const int nvq = vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
     /* volume integral: sum_q w_q F(U_q) . (J^-T grad_ref phi_j) */
-    for (int q = 0; q < R.nv; ++q) {
-      real x[3] = {R.vr[q], R.vs[q], R.vt[q]};
+    for (int q = 0; q < nvq; ++q) {
+      real x[3] = {vr[q], vs[q], vt[q]};
       real phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM];
-      basis_eval(m, p, x, phi, d[0], d[1], d[2]);
+      basis_eval_e(m, e, p, x, phi, d[0], d[1], d[2]);
       for (int k = 0; k < M; ++k) {
         real v = 0.0;
-        for (int j = 0; j < Np; ++j) v += ce[k * Np + j] * phi[j];
+        for (int j = 0; j < Ne; ++j) v += ce[k * Np + j] * phi[j];
         U[k] = v;
       }
       for (int a = 0; a < dim; ++a) {
         real Fa[ORC_MAXM];
         phys_flux_dir(&ph, U, a, Fa);
-        for (int j = 0; j < Np; ++j) {
+        for (int j = 0; j < Ne; ++j) {
           real gx = 0.0; /* d phi_j / d x_a */
           for (int r = 0; r < dim; ++r) gx += Ji[r * dim + a] * d[r][j];
-          for (int k = 0; k < M; ++k) re[k * Np + j] += R.vw[q] * Fa[k] * gx;
+          for (int k = 0; k < M; ++k) re[k * Np + j] += vw[q] * Fa[k] * gx;
         }
       }
     }
@@ -1442,17 +1503,17 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
       for (int q = 0; q < F.nq; ++q) {
         real rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];
         ref_coords(m, e, F.x + 3 * q, rs);
-        eval_state(m, p, M, Np, ce, rs, Um);
+        eval_state_e(m, e, p, M, Np, ce, rs, Um);
         if (nb >= 0) {
           real rn[3];
           ref_coords(m, nb, F.x + 3 * q, rn);
-          eval_state(m, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
+          eval_state_e(m, nb, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
         } else {
           for (int k = 0; k < M; ++k) Up[k] = Um[k];
         }
         num_flux(&ph, Um, Up, F.n, Fs);
-        basis_eval(m, p, rs, phi, NULL, NULL, NULL);
-        for (int j = 0; j < Np; ++j)
+        basis_eval_e(m, e, p, rs, phi, NULL, NULL, NULL);
+        for (int j = 0; j < Ne; ++j)
           for (int k = 0; k < M; ++k) re[k * Np + j] -= scale * F.w[q] * phi[j] * Fs[k];
       }
     }
@@ -1494,9 +1555,11 @@ int orc_dt(void *h, int p, const real *c, real cfl, real *dt_out) {
   real best = INFINITY;
   for (int64_t e = 0; e < m->ne; ++e) {
     real lam = 0.0;
-    for (int q = 0; q < R.nv; ++q) {
-      real x[3] = {R.vr[q], R.vs[q], R.vt[q]}, U[ORC_MAXM];
-      eval_state(m, p, M, Np, c + e * M * Np, x, U);
+    const real *vr, *vs, *vt, *vw;
+    const int nvq = vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
+    for (int q = 0; q < nvq; ++q) {
+      real x[3] = {vr[q], vs[q], vt[q]}, U[ORC_MAXM];
+      eval_state_e(m, e, p, M, Np, c + e * M * Np, x, U);
       real rho = U[0], q2 = 0.0;
       for (int a = 0; a < dim; ++a) q2 += (U[1 + a] / rho) * (U[1 + a] / rho);
       real pr = (ORC_GAMMA - 1.0) * (U[dim + 1] - 0.5 * rho * q2);
@@ -1504,11 +1567,11 @@ int orc_dt(void *h, int p, const real *c, real cfl, real *dt_out) {
       if (l > lam) lam = l;
     }
     real bnd = 0.0;
-    for (int f = 0; f < m->nfpe; ++f) {
+    for (int f = 0; f < elem_nfaces(m, e); ++f) {
       face_geometry(m, e, f, &R, &F);
       bnd += F.meas;
     }
-    real vol = m->detJ[e] / (m->quad ? 1.0 : dim == 2 ? 2.0 : 6.0);
+    real vol = m->detJ[e] / (elem_is_quad(m, e) ? 1.0 : dim == 2 ? 2.0 : 6.0);
     real r = dim * vol / bnd;
     real v = r / ((2 * p + 1) * lam);
     if (v < best) best = v;
@@ -1650,19 +1713,21 @@ int orc_eval_points(void *h, int p, int M, const real *c, int n1, real *xyz, rea
     rules_free(&R);
     return -1;
   }
-  /* the reference axes run from v0 to v1, v2 (simplices) or v1, v3 (quadrilaterals) */
-  const int kv[3] = {1, m->quad ? 3 : 2, 3};
   for (int64_t e = 0; e < m->ne; ++e) {
+    /* the reference axes run from v0 to v1, v2 (simplices) or v1, v3 (quadrilaterals) */
+    const int kv[3] = {1, elem_is_quad(m, e) ? 3 : 2, 3};
     const real *X = m->X + e * m->nvpe * dim;
+    const real *vr, *vs, *vt, *vw;
+    vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
     for (int q = 0; q < R.nv; ++q) {
-      real rs[3] = {R.vr[q], R.vs[q], R.vt[q]};
+      real rs[3] = {vr[q], vs[q], vt[q]};
       for (int a = 0; a < dim; ++a) {
         real v = X[a];
         for (int k = 0; k < dim; ++k) v += (X[kv[k] * dim + a] - X[a]) * rs[k];
         if (xyz) xyz[(e * R.nv + q) * dim + a] = v;
       }
-      if (w) w[e * R.nv + q] = R.vw[q] * m->detJ[e];
-      if (U) eval_state(m, p, M, Np, c + e * M * Np, rs, U + (e * R.nv + q) * M);
+      if (w) w[e * R.nv + q] = vw[q] * m->detJ[e];
+      if (U) eval_state_e(m, e, p, M, Np, c + e * M * Np, rs, U + (e * R.nv + q) * M);
     }
   }
   int nq = R.nv;
@@ -1684,11 +1749,14 @@ int orc_project(void *h, int p, int M, const real *vals, real *c) {
   for (int64_t e = 0; e < m->ne; ++e) {
     real *ce = c + e * M * Np;
     for (int i = 0; i < M * Np; ++i) ce[i] = 0.0;
+    const real *vr, *vs, *vt, *vw;
+    vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
+    const int Ne = npoly_e(m, e, p);
     for (int q = 0; q < R.nv; ++q) {
-      real x[3] = {R.vr[q], R.vs[q], R.vt[q]}, phi[ORC_MAXNP];
-      basis_eval(m, p, x, phi, NULL, NULL, NULL);
+      real x[3] = {vr[q], vs[q], vt[q]}, phi[ORC_MAXNP];
+      basis_eval_e(m, e, p, x, phi, NULL, NULL, NULL);
       for (int k = 0; k < M; ++k)
-        for (int j = 0; j < Np; ++j) ce[k * Np + j] += R.vw[q] * vals[(e * R.nv + q) * M + k] * phi[j];
+        for (int j = 0; j < Ne; ++j) ce[k * Np + j] += vw[q] * vals[(e * R.nv + q) * M + k] * phi[j];
     }
   }
   rules_free(&R);

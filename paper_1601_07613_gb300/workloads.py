@@ -188,13 +188,15 @@ def open_square_quad(n: int, mode: str = "parallelogram", jitter: float = 0.0, s
 
 
 def hybrid_square(n: int, frac: float = 0.25, periodic: bool = True, jitter: float = 0.0,
-                  seed: int | None = None) -> MeshInput:
-    """The ``n x n`` quadrilateral grid (``mode="vertex"``) with a seeded fraction
-    ``frac`` of its squares split along the diagonal (i,j)-(i+1,j+1) into two CCW
-    triangles, listed with -1 as their fourth vertex.  Elements are numbered
-    square by square, a split square's two triangles in place of the square."""
-    base = (periodic_square_quad(n, "vertex", jitter, seed=seed) if periodic
-            else open_square_quad(n, "vertex", jitter, seed=seed))
+                  seed: int | None = None, mode: str = "vertex", slant: float = 0.0) -> MeshInput:
+    """The ``n x n`` quadrilateral grid (``mode`` as for ``periodic_square_quad``:
+    "vertex" jitters every vertex, "parallelogram" keeps every cell a
+    parallelogram) with a seeded fraction ``frac`` of its cells split along the
+    diagonal (i,j)-(i+1,j+1) into two CCW triangles, listed with -1 as their fourth
+    vertex.  Elements are numbered cell by cell, a split cell's two triangles in
+    place of the cell."""
+    base = (periodic_square_quad(n, mode, jitter, slant, seed=seed) if periodic
+            else open_square_quad(n, mode, jitter, slant, seed=seed))
     rng = np.random.default_rng(None if seed is None else seed + 1)
     split = rng.uniform(size=n * n) < frac
     rows = []
@@ -207,7 +209,7 @@ def hybrid_square(n: int, frac: float = 0.25, periodic: bool = True, jitter: flo
             rows.append((a, b, c, d))
     ev = np.array(rows, dtype=np.int32)
     return MeshInput(2, base.xyz, ev, base.periodic_len, name=f"hybrid_square_{n}x{n}",
-                     meta={"n": n, "frac": frac, "periodic": periodic, "seed": seed})
+                     meta={"n": n, "frac": frac, "periodic": periodic, "seed": seed, "mode": mode})
 
 
 # The six tetrahedra of the Kuhn split of the unit cube: the path 000 -> 111
