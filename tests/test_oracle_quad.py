@@ -106,13 +106,16 @@ def test_quad_coloring_perfect_on_even_periodic_grid(oracle_mod, seed):
 def test_hybrid_coloring_valid(oracle_mod, kind):
     mi = W.hybrid_square(9 if kind == "open" else 10, 0.3, periodic=kind == "periodic", seed=3)
     m = oracle_mod.OracleMesh.from_input(mi)
-    assert m.nonaffine == int((mi.ev[:, 3] < 0).sum())  # triangles: colored only
+    assert m.nonaffine == 0  # unjittered squares and their triangles: every element affine
     col, _ = m.color(4, 5)
     _check_coloring(m, col, mi.ev)
     counts = np.bincount(col)[1:]
     assert counts.min() > 0.8 * counts.mean()  # roughly balanced, as in Table 2
+    # with every vertex jittered the quadrilaterals are general: Eq. 2 is refused there
+    mj = oracle_mod.OracleMesh.from_input(W.hybrid_square(9, 0.3, periodic=kind == "periodic", jitter=0.2, seed=3))
+    assert mj.nonaffine > 0
     with pytest.raises(RuntimeError):
-        m.rhs(1, np.zeros((m.ne, 4, 4)))
+        mj.rhs(1, np.zeros((mj.ne, 4, 4)))
 
 
 def test_odd_closed_quad_mesh_is_not_4_colorable(oracle_mod):
