@@ -132,6 +132,52 @@ T* dalloc(int64_t n) {
   return p;
 }
 
+// Hybrid meshes: each element's kind (internal order) and the tables of
+// kernels_hybrid.cu: per kind (triangle, quadrilateral) the basis and the
+// weighted reference gradients at the (p+1)^2 volume points and the basis at the
+// 2p+1 Gauss points of each local edge (from its first vertex to its second),
+// zero past the kind's modes, then the edge weights (summing to 1).
+void upload_hybrid(const Mesh& m, DeviceMesh& d) {
+  const int p = m.p, NPX = m.np, NQE = 2 * p + 1;
+  const int NQV = m.tab.nqv;
+  const int VOL = NQV * NPX, EDGE = 4 * NQE * NPX;
+  std::vector<double> t((size_t)hyb_table_doubles(p), 0.0);
+  if ((int64_t)t.size() != 2 * (3 * VOL + EDGE) + NQE || m.tab_tri.nqv != NQV)
+    throw Error{DGC_ERR_UNSUPPORTED, "hybrid meshes: p = 1..3"};
+  std::vector<double> xg(NQE), wg(NQE);
+  gauss_jacobi(NQE, 0.0, xg.data(), wg.data());
+  const double refv[2][4][2] = {{{0, 0}, {1, 0}, {0, 1}, {0, 0}}, {{0, 0}, {1, 0}, {1, 1}, {0, 1}}};
+  for (int k = 0; k < 2; ++k) {
+    const RefTables& T = k ? m.tab : m.tab_tri;
+    const int np = T.np, nf = k ? 4 : 3;
+    double* vol = &t[(size_t)k * 3 * VOL];
+    for (int q = 0; q < NQV; ++q)
+      for (int j = 0; j < np; ++j) {
+        vol[q * NPX + j] = T.phiV[(size_t)q * np + j];
+        vol[VOL + q * NPX + j] = T.vw[q] * T.dphiV[(size_t)q * np + j];
+        vol[2 * VOL + q * NPX + j] = T.vw[q] * T.dphiV[((size_t)NQV + q) * np + j];
+      }
+    double* edge = &t[(size_t)6 * VOL + (size_t)k * EDGE];
+    std::vector<double> phi(np);
+    for (int f = 0; f < nf; ++f)
+      for (int q = 0; q < NQE; ++q) {
+        const double tq = 0.5 * (1.0 + xg[q]);
+        const double* A = refv[k][f];
+        const double* B = refv[k][(f + 1) % nf];
+        const double x[2] = {A[0] + tq * (B[0] - A[0]), A[1] + tq * (B[1] - A[1])};
+        basis_eval(2, p, x, phi.data(), nullptr, k == 1);
+        for (int j = 0; j < np; ++j) edge[((size_t)f * NQE + q) * NPX + j] = phi[j];
+      }
+  }
+  for (int q = 0; q < NQE; ++q) t[(size_t)6 * VOL + 2 * EDGE + q] = 0.5 * wg[q];
+  std::vector<int8_t> kind(m.ne);
+  for (int64_t e = 0; e < m.ne; ++e) kind[m.elem_new_of_old[e]] = (int8_t)(m.ev[(size_t)e * 4 + 3] >= 0);
+  d.hyb_kind = dalloc<int8_t>(m.ne);
+  d.hyb_tab = dalloc<double>((int64_t)t.size());
+  DGC_CUDA(cudaMemcpy(d.hyb_kind, kind.data(), kind.size(), cudaMemcpyHostToDevice));
+  DGC_CUDA(cudaMemcpy(d.hyb_tab, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
+}
+
 // Refined triangle meshes: the tables of the state transfer to and from the
 // mesh before refinement (internal orders of both), and the child projections
 // P_c[j][k] = sum_q w_q phi_j(rho_q) phi_k(A_c rho_q) of the reference triangle
@@ -263,6 +309,7 @@ void upload(Mesh& m) {
     if (dim == 3) tet_upload_tables(m.p, m.tab, *d);
     if (m.quad) quad_upload_tables(m.p, m.tab);
     if (m.refined) upload_transfer(m, *d);
+    if (m.hybrid) upload_hybrid(m, *d);
   } catch (...) {
     m.dev = d.release();
     device_free(m);
@@ -317,6 +364,7 @@ Ctx make_ctx(const Mesh& m, const DeviceMesh* d, void* stream) {
   Ctx x;
   x.dim = m.dim;
   x.quad = m.quad;
+  x.hybrid = m.hybrid;
   x.p = m.p;
   x.np = m.np;
   x.M = m.M;
@@ -359,16 +407,22 @@ void check_ptr(const void* p, const char* what) {
 
 // ss: floats per element of an FP32 state (record or Kahan state), 0 for FP64 states
 int vol(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r, int64_t e0 = 0) {
+  if (x.hybrid) return ty == TY_D && e0 == 0 ? hyb_volume(x, static_cast<const double*>(s), static_cast<double*>(r)) : -1;
   if (x.quad) return quad_volume(x, ty, s, ss, r, e0);
   return x.dim == 2 ? tri_volume(x, ty, s, ss, r, e0) : tet_volume(x, ty, s, ss, r, e0);
 }
 int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, int ss, void* r, void* buf,
          const StageArgs* sa) {
+  if (x.hybrid) {
+    if (ty != TY_D || (mode != SURF_RMW && mode != SURF_ATOMIC)) return -1;
+    return hyb_surface(x, mode == SURF_ATOMIC, b, e, static_cast<const double*>(s), static_cast<double*>(r));
+  }
   if (x.quad) return quad_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
   return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, ss, r, buf, sa)
                     : tet_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
 }
 int cfl(const Ctx& x, const double* s, double c, double* dt, float* sh) {
+  if (x.hybrid) return sh ? -1 : hyb_cfl(x, s, c, dt);
   if (x.quad) return quad_cfl(x, s, c, dt, sh);
   return x.dim == 2 ? tri_cfl(x, s, c, dt, sh) : tet_cfl(x, s, c, dt, sh);
 }
@@ -435,7 +489,7 @@ void finish(Mesh& m, int64_t launches) {
 // every element once (closed conforming meshes), or, after the color-1
 // renumbering, the elements [0, reached) it does reach; the rest get a volume
 // kernel of their own.
-bool first_fused(const Mesh& m) { return m.fuse && (m.perfect || m.reached >= 0); }
+bool first_fused(const Mesh& m) { return m.fuse && !m.hybrid && (m.perfect || m.reached >= 0); }
 int64_t unreached(const Mesh& m) { return m.perfect ? m.ne : m.reached; }
 
 int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss, void* rhs) {
@@ -607,6 +661,8 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->ftab);
   cudaFree(m.dev->ftabd);
   cudaFree(m.dev->cfl_est);
+  cudaFree(m.dev->hyb_kind);
+  cudaFree(m.dev->hyb_tab);
   cudaFree(m.dev->xf_src);
   cudaFree(m.dev->xf_kind);
   cudaFree(m.dev->xf_kids);
@@ -803,6 +859,7 @@ static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) { return carve(m, p
 
 static void require_prec(const Mesh& m, dgc_prec prec) {
   require(prec == DGC_FP64 || prec == DGC_FP32_MIXED || prec == DGC_FP32_KAHAN, "unknown precision");
+  require(!m.hybrid || prec == DGC_FP64, "hybrid triangle/quadrilateral meshes run in FP64", DGC_ERR_UNSUPPORTED);
   require(prec != DGC_FP32_KAHAN || (m.dim == 2 && !m.quad), "the Kahan form is implemented for triangle meshes",
           DGC_ERR_UNSUPPORTED);
 }

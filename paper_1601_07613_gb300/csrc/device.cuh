@@ -31,6 +31,10 @@ struct DeviceMesh {
   // (internal orders): per fine element its coarse element and child 0..3 (4:
   // copy), per coarse element its children's fine ids (kids[1] = -1: one copy),
   // and the child projections P [4][Np][Np]
+  // hybrid triangle/quadrilateral meshes: per element its kind (0 triangle, 1
+  // quadrilateral), and the tables of kernels_hybrid.cu
+  int8_t* hyb_kind = nullptr;
+  double* hyb_tab = nullptr;
   int32_t* xf_src = nullptr;
   int8_t* xf_kind = nullptr;
   int32_t* xf_kids = nullptr;
@@ -80,6 +84,7 @@ struct Ctx {
   // blocks (sms = the GPU's multiprocessors) instead of one block per tile
   bool persistent = false;
   int sms = 0;
+  bool hybrid = false;  // hybrid triangle/quadrilateral mesh: kernels_hybrid.cu (FP64)
   const DeviceMesh* d = nullptr;
   cudaStream_t st = nullptr;
   bool pdl = false;  // launch the surface and CFL kernels with programmatic dependent launch
@@ -156,6 +161,13 @@ int tri_record_floats(int p);
 // sstride: floats per element of an FP32 state (record or Kahan state); ignored for FP64 states
 // volume kernels cover elements [e0, ne)
 int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* rhs, int64_t e0 = 0);
+// hybrid triangle/quadrilateral meshes, FP64 (kernels_hybrid.cu): the volume
+// integral of every element (plain store), one color's edges (read-modify-write,
+// or atomics), the CFL step into *dt; the table size in doubles
+int hyb_volume(const Ctx& x, const double* state, double* rhs);
+int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs);
+int hyb_cfl(const Ctx& x, const double* state, double cfl, double* dt);
+int hyb_table_doubles(int p);
 // dgc_rhs of a triangle mesh in one cooperative launch (FP64 or FP32-mixed with
 // FP64 state and rhs): off = the color offsets, fused = the first color also
 // stores the volume integral of the elements [0, e_vol0)

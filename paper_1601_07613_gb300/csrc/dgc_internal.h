@@ -62,6 +62,10 @@ struct Mesh {
   // are not parallelograms, triangles of hybrid meshes): colored only
   bool quad = false;
   int64_t nonaffine = 0;
+  // hybrid triangle/quadrilateral mesh (quad with some triangles): each element
+  // carries the space of its kind, P_p (tab_tri) or Q_p (tab); states keep
+  // (p+1)^2 coefficients per variable, a triangle using the first (p+1)(p+2)/2
+  bool hybrid = false;
   int64_t nv = 0, ne = 0, ns = 0;
   bool periodic = false;
   double L[3] = {0, 0, 0};
@@ -94,6 +98,7 @@ struct Mesh {
   std::vector<double> detJ, Jinv, inradius;  // Jinv [ne][dim][dim] (row k = grad r_k)
   std::vector<double> snormal, smeas;        // [ns][dim] outward normal of the left element, |face|
   RefTables tab;
+  RefTables tab_tri;  // hybrid meshes: the triangles' tables (same point counts as tab)
   // coloring and ordering
   int ncolors = 0;
   bool perfect = false;  // every element has exactly one face of each color

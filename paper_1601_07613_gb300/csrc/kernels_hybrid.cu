@@ -1,0 +1,258 @@
+// FP64 kernels for hybrid triangle/quadrilateral meshes (Sec. 3.1: Table 2's
+// hybrid mesh is colored with C = {1, 2, 3, 4}; Eq. 2 with each element in the
+// space of its kind: P_p on a triangle, Q_p on a parallelogram).
+//
+// The state keeps NPX = (p+1)^2 coefficients per variable for every element; a
+// triangle uses the first (p+1)(p+2)/2 and its other entries of the right-hand
+// side are written as zero.  The kernels are table driven: per kind, the basis
+// and the weighted reference gradients at the (p+1)^2 volume points, and the
+// basis at the 2p+1 points of each local edge, zero past the kind's modes, all
+// in shared memory.  A color runs as Algorithm 1 states it: one lane per edge
+// side, each evaluating its own element's trace and normal flux, the two lanes
+// exchanging them with shuffles, each projecting onto its own element's modes
+// and adding into its right-hand side (read-modify-write: the coloring makes
+// the two elements of an edge the only writers of their blocks in the color).
+#include "dev_util.cuh"
+#include "device.cuh"
+
+namespace dgc {
+
+// table layout (doubles): [kind][NQV][NPX] basis, [kind][NQV][NPX] w d/dr,
+// [kind][NQV][NPX] w d/ds, [kind][4 faces][NQE][NPX] edge basis, [NQE] weights
+template <int P>
+struct HybDim {
+  static constexpr int NPX = (P + 1) * (P + 1), NPT = (P + 1) * (P + 2) / 2, NQV = (P + 1) * (P + 1),
+                       NQE = 2 * P + 1, NV = 4 * NPX;
+  static constexpr int VOL = NQV * NPX, EDGE = 4 * NQE * NPX;
+  static constexpr int SIZE = 2 * (3 * VOL + EDGE) + NQE;
+  __host__ __device__ static constexpr int vol(int kind) { return kind * 3 * VOL; }
+  __host__ __device__ static constexpr int edge(int kind) { return 6 * VOL + kind * EDGE; }
+  __host__ __device__ static constexpr int wts() { return 6 * VOL + 2 * EDGE; }
+};
+
+template <int P>
+__device__ __forceinline__ void hyb_stage(double* s, const double* __restrict__ tab) {
+  for (int i = threadIdx.x; i < HybDim<P>::SIZE; i += blockDim.x) s[i] = tab[i];
+}
+
+// Euler flux components (gamma = 1.4)
+__device__ __forceinline__ void hyb_flux(const double* U, double* F, double* G) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir;
+  const double p = 0.4 * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+  F[0] = U[1];
+  F[1] = U[1] * u + p;
+  F[2] = U[2] * u;
+  F[3] = (U[3] + p) * u;
+  G[0] = U[2];
+  G[1] = U[1] * v;
+  G[2] = U[2] * v + p;
+  G[3] = (U[3] + p) * v;
+}
+
+// volume integral of element e (kind k): rhs = sum_q w_q F(U_q).(J^-T grad phi_j)
+template <int P>
+__global__ void __launch_bounds__(128) k_hyb_vol(const double* __restrict__ c, const double* __restrict__ jinv,
+                                                 const int8_t* __restrict__ kind, const double* __restrict__ tab,
+                                                 double* __restrict__ rhs, int64_t ne) {
+  using D = HybDim<P>;
+  __shared__ double s[D::SIZE];
+  hyb_stage<P>(s, tab);
+  __syncthreads();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int k = kind[e];
+  const int np = k ? D::NPX : D::NPT;
+  const double* phi = s + D::vol(k);
+  const double* gr = phi + D::VOL;
+  const double* gs = gr + D::VOL;
+  const double* ce = c + e * D::NV;
+  const double j00 = jinv[4 * e], j01 = jinv[4 * e + 1], j10 = jinv[4 * e + 2], j11 = jinv[4 * e + 3];
+  double acc[D::NV];
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
+  for (int q = 0; q < D::NQV; ++q) {
+    double U[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < np; ++j) {
+      const double b = phi[q * D::NPX + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) U[m] += b * ce[m * D::NPX + j];
+    }
+    double F[4], G[4];
+    hyb_flux(U, F, G);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const double fr = j00 * F[m] + j01 * G[m], fs = j10 * F[m] + j11 * G[m];
+#pragma unroll
+      for (int j = 0; j < D::NPX; ++j) acc[m * D::NPX + j] += gr[q * D::NPX + j] * fr + gs[q * D::NPX + j] * fs;
+    }
+  }
+  double* re = rhs + e * D::NV;
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) re[i] = acc[i];  // zero past a triangle's modes (zero tables)
+}
+
+// one color's edges [begin, end): two lanes per edge (side 0: left element, 1:
+// right); the right element runs along the edge backwards.  ATOMIC: add with
+// atomics instead (all edges in one launch; comparator).
+template <int P, bool ATOMIC>
+__global__ void __launch_bounds__(128) k_hyb_surf(const double* __restrict__ c, const int4* __restrict__ topo,
+                                                  const double2* __restrict__ fgeo, const int8_t* __restrict__ kind,
+                                                  const double* __restrict__ tab, double* __restrict__ rhs,
+                                                  int64_t begin, int64_t end) {
+  using D = HybDim<P>;
+  constexpr int NQ = D::NQE;
+  __shared__ double s[D::SIZE];
+  hyb_stage<P>(s, tab);
+  __syncthreads();
+  const int side = threadIdx.x & 1;
+  int64_t k = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1);
+  const bool valid = k < end;
+  if (!valid) k = end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
+  const int4 tp = topo[k];
+  const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
+  const bool right = side && !bnd;
+  const int64_t elem = right ? tp.y : tp.x;
+  const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
+  const bool writer = valid && !(side && bnd);
+  const int kd = kind[elem];
+  const int np = kd ? D::NPX : D::NPT;
+  const double2 g0 = fgeo[2 * k], g1 = fgeo[2 * k + 1];
+  const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
+  const double* ph = s + D::edge(kd) + le * NQ * D::NPX;
+  const double* w = s + D::wts();
+  const double* ce = c + elem * D::NV;
+  double acc[D::NV];
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
+  for (int q = 0; q < NQ; ++q) {
+    const int qq = right ? NQ - 1 - q : q;
+    double U[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < np; ++j) {
+      const double b = ph[qq * D::NPX + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) U[m] += b * ce[m * D::NPX + j];
+    }
+    // own normal flux and wave speed, exchanged with the partner lane
+    const double ir = 1.0 / U[0];
+    const double u = U[1] * ir, v = U[2] * ir;
+    const double p = 0.4 * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+    const double un = u * nx + v * ny;
+    const double Fo[4] = {U[0] * un, U[1] * un + p * nx, U[2] * un + p * ny, (U[3] + p) * un};
+    const double wo = fabs(un) + sqrt(1.4 * p * ir);
+    double V[4], Fp[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+      Fp[m] = __shfl_xor_sync(0xffffffffu, Fo[m], 1);
+    }
+    const double lam = fmax(wo, __shfl_xor_sync(0xffffffffu, wo, 1));
+    const double g = scale * w[q];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const double a = side ? V[m] : U[m], b = side ? U[m] : V[m];
+      const double Fs = 0.5 * (Fo[m] + Fp[m]) - (0.5 * lam) * (b - a);  // commutative: both lanes' bits agree
+      const double gm = g * Fs;
+#pragma unroll
+      for (int j = 0; j < D::NPX; ++j) acc[m * D::NPX + j] += ph[qq * D::NPX + j] * gm;
+    }
+  }
+  if (!writer) return;
+  double* re = rhs + elem * D::NV;
+  if constexpr (ATOMIC) {
+    for (int i = 0; i < D::NV; ++i)
+      if ((i % D::NPX) < np) atomicAdd(re + i, acc[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) re[i] += acc[i];
+  }
+}
+
+// CFL: dt = cfl min_e r_e / ((2p+1) max_q (|u| + c)), one thread per element,
+// FP64, folded into *dt by a 64-bit atomicMin on the bits (positive doubles
+// order as their bit patterns); *dt must hold a large value beforehand
+template <int P>
+__global__ void __launch_bounds__(128) k_hyb_cfl(const double* __restrict__ c, const double* __restrict__ inr,
+                                                 const int8_t* __restrict__ kind, const double* __restrict__ tab,
+                                                 int64_t ne, double cfl, unsigned long long* dtbits) {
+  using D = HybDim<P>;
+  __shared__ double s[D::SIZE];
+  hyb_stage<P>(s, tab);
+  __syncthreads();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int k = kind[e];
+  const int np = k ? D::NPX : D::NPT;
+  const double* phi = s + D::vol(k);
+  const double* ce = c + e * D::NV;
+  double lam = 0.0;
+  for (int q = 0; q < D::NQV; ++q) {
+    double U[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < np; ++j) {
+      const double b = phi[q * D::NPX + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) U[m] += b * ce[m * D::NPX + j];
+    }
+    const double ir = 1.0 / U[0], u = U[1] * ir, v = U[2] * ir;
+    const double q2 = u * u + v * v;
+    const double pr = 0.4 * (U[3] - 0.5 * U[0] * q2);
+    lam = fmax(lam, sqrt(q2) + sqrt(1.4 * pr * ir));
+  }
+  const double d = cfl * (inr[e] / ((2 * P + 1) * lam));
+  if (d > 0.0) atomicMin(dtbits, (unsigned long long)__double_as_longlong(d));
+}
+
+template <int P>
+static int hyb_p(const Ctx& x, int what, const double* state, double* rhs, int64_t b, int64_t e, double cfl,
+                 double* dt) {
+  const int bs = 128;
+  const DeviceMesh* d = x.d;
+  if (what == 0) {
+    if (x.ne <= 0) return 0;
+    k_hyb_vol<P><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(state, d->jinv, d->hyb_kind, d->hyb_tab, rhs,
+                                                                    x.ne);
+    return 1;
+  }
+  if (what == 1 || what == 2) {
+    const int64_t n = e - b;
+    if (n <= 0) return 0;
+    const unsigned grid = (unsigned)((2 * n + bs - 1) / bs);
+    if (what == 1)
+      k_hyb_surf<P, false><<<grid, bs, 0, x.st>>>(state, d->topo, d->fgeo, d->hyb_kind, d->hyb_tab, rhs, b, e);
+    else
+      k_hyb_surf<P, true><<<grid, bs, 0, x.st>>>(state, d->topo, d->fgeo, d->hyb_kind, d->hyb_tab, rhs, b, e);
+    return 1;
+  }
+  if (cudaMemsetAsync(dt, 0x7F, sizeof(double), x.st) != cudaSuccess) return -1;
+  k_hyb_cfl<P><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(state, d->inr, d->hyb_kind, d->hyb_tab, x.ne, cfl,
+                                                                  reinterpret_cast<unsigned long long*>(dt));
+  return 1;
+}
+
+static int hyb(const Ctx& x, int what, const double* state, double* rhs, int64_t b, int64_t e, double cfl,
+               double* dt) {
+  switch (x.p) {
+    case 1: return hyb_p<1>(x, what, state, rhs, b, e, cfl, dt);
+    case 2: return hyb_p<2>(x, what, state, rhs, b, e, cfl, dt);
+    case 3: return hyb_p<3>(x, what, state, rhs, b, e, cfl, dt);
+    default: return -1;
+  }
+}
+
+int hyb_volume(const Ctx& x, const double* state, double* rhs) { return hyb(x, 0, state, rhs, 0, 0, 0.0, nullptr); }
+int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs) {
+  return hyb(x, atomic ? 2 : 1, state, rhs, begin, end, 0.0, nullptr);
+}
+int hyb_cfl(const Ctx& x, const double* state, double cfl, double* dt) {
+  return hyb(x, 3, state, nullptr, 0, 0, cfl, dt);
+}
+int hyb_table_doubles(int p) {
+  switch (p) {
+    case 1: return HybDim<1>::SIZE;
+    case 2: return HybDim<2>::SIZE;
+    case 3: return HybDim<3>::SIZE;
+    default: return -1;
+  }
+}
+
+}  // namespace dgc

@@ -473,7 +473,7 @@ static void elem_face_vertices(const Mesh& m, int64_t e, int q, int* fv) {
 // A quadrilateral maps the square's corners (0,0), (1,0), (1,1), (0,1) to
 // v0..v3 through v0, v1 and v3 (affine: exact for parallelograms); it must turn
 // counterclockwise at every corner, and one that is not a parallelogram is
-// counted in m.nonaffine (colored only).
+// counted in m.nonaffine (colored only).  A triangle of a hybrid mesh is affine.
 static void element_jacobian(Mesh& m, int64_t e) {
   const int dim = m.dim;
   const double* X = &m.X[(size_t)e * m.nvpe * dim];
@@ -495,8 +495,6 @@ static void element_jacobian(Mesh& m, int64_t e) {
       }
       for (int k = 0; k < 2; ++k) off = std::max(off, std::fabs(X[k] + X[4 + k] - X[2 + k] - X[6 + k]));
       if (off > 1e-12 * scale) m.nonaffine++;
-    } else if (m.quad) {
-      m.nonaffine++;  // a triangle of a hybrid mesh
     }
     det = a * d - b * c;
     Ji[0] = d / det;
@@ -652,6 +650,8 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
   side_geometry(*m);
   m->tab = make_tables(dim, p, quad);
   m->np = m->tab.np;
+  for (int64_t e = 0; quad && e < m->ne && !m->hybrid; ++e) m->hybrid = elem_faces(*m, e) == 3;
+  if (m->hybrid) m->tab_tri = make_tables(2, p, false);
   return m.release();
 }
 
@@ -807,7 +807,9 @@ ColorStats color_faces(Mesh& m, uint64_t seed, int64_t max_swaps) {
   }
   m.color.swap(col);
   m.ncolors = nc;
-  m.perfect = true;
+  // every element has one face of each color, except a hybrid mesh's triangles
+  // (three faces, four colors)
+  m.perfect = !m.hybrid;
   m.dirty = true;
   return st;
 }
@@ -1127,10 +1129,16 @@ void coarsen(Mesh& m) {
 // ---------------------------------------------------------------------------
 // Volume points and L2 projection (initial states)
 // ---------------------------------------------------------------------------
+// an element's reference tables: a triangle of a hybrid mesh has its own
+static const RefTables& elem_tab(const Mesh& m, int64_t e) {
+  return m.hybrid && elem_faces(m, e) == 3 ? m.tab_tri : m.tab;
+}
+
 void vol_points(const Mesh& m, double* xyz) {
-  const RefTables& T = m.tab;
-  const int kv[3] = {1, m.quad ? 3 : 2, 3};  // the vertices at the reference axes' ends
   for (int64_t e = 0; e < m.ne; ++e) {
+    const RefTables& T = elem_tab(m, e);
+    const bool q4 = m.quad && elem_faces(m, e) == 4;
+    const int kv[3] = {1, q4 ? 3 : 2, 3};  // the vertices at the reference axes' ends
     const double* X = &m.X[(size_t)e * m.nvpe * m.dim];
     for (int q = 0; q < T.nqv; ++q) {
       double rs[3] = {T.vr[q], T.vs[q], T.vt[q]};
@@ -1144,15 +1152,15 @@ void vol_points(const Mesh& m, double* xyz) {
 }
 
 void project(const Mesh& m, const double* vals, double* c) {
-  const RefTables& T = m.tab;
-  const int M = m.M, np = T.np;
+  const int M = m.M, np = m.np;  // the state's stride (hybrid: the quadrilaterals' count)
   for (int64_t e = 0; e < m.ne; ++e) {
+    const RefTables& T = elem_tab(m, e);
     double* ce = c + (size_t)e * M * np;
     std::fill(ce, ce + M * np, 0.0);
     for (int q = 0; q < T.nqv; ++q)
       for (int k = 0; k < M; ++k) {
         double v = T.vw[q] * vals[((size_t)e * T.nqv + q) * M + k];
-        for (int j = 0; j < np; ++j) ce[k * np + j] += v * T.phiV[(size_t)q * np + j];
+        for (int j = 0; j < T.np; ++j) ce[k * np + j] += v * T.phiV[(size_t)q * T.np + j];
       }
   }
 }

@@ -127,8 +127,10 @@ def test_projection_matches_oracle_quad(oracle_mod, p):
 
 def test_quad_mesh_statuses(L):
     """Non-convex or clockwise quadrilaterals are mesh errors; general
-    quadrilaterals and hybrid meshes are colored, and their device calls are
-    refused on the host; an odd closed quadrilateral mesh cannot be 4-colored."""
+    quadrilaterals (also in a hybrid mesh) are colored, and their device calls
+    are refused on the host; a hybrid mesh of parallelograms and triangles takes
+    device calls in FP64 only; an odd closed quadrilateral mesh cannot be
+    4-colored."""
     mi = W.periodic_square_quad(6)
     bad = mi.ev.copy()
     bad[3] = bad[3, ::-1]
@@ -138,7 +140,15 @@ def test_quad_mesh_statuses(L):
     with pytest.raises(dgc.DgcError) as e:
         dgc.dgc_mesh_create_elem(dgc.DGC_QUAD, 4, mi.xyz, mi.ev, mi.periodic_len)
     assert e.value.status == 4
-    for gen in (lambda: W.hybrid_square(8, 0.3, seed=1), lambda: W.periodic_square_quad(8, "vertex", 0.2, seed=1)):
+    h = dgc.Mesh.from_input(W.hybrid_square(8, 0.3, seed=1), 2)  # unjittered squares and triangles: affine
+    assert h.elem == dgc.DGC_QUAD and h.nonaffine == 0
+    h.color(3)
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rhs(h.h, dgc.DGC_FP32_MIXED, 4096, 8192, 0)
+    assert e.value.status == 4
+    h.close()
+    for gen in (lambda: W.hybrid_square(8, 0.3, jitter=0.2, seed=1),
+                lambda: W.periodic_square_quad(8, "vertex", 0.2, seed=1)):
         g = gen()
         m = dgc.Mesh.from_input(g, 2)
         assert m.elem == dgc.DGC_QUAD and m.nonaffine > 0
