@@ -595,10 +595,12 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     tube = W.cube_tube_p2_64()
     ref = W.refined_square_vortex_p2_256()
     quad = W.quad_square_vortex_p3_810()
+    hyb = W.hybrid_square_vortex_p3_512()
     hbm, _ = peaks()
     for tag, mi, p, refine in (("tet_p2_64cube", tube["mesh"], tube["p"], None),
                                ("nonconforming_p2_256", ref["mesh"], ref["p"], ref["refine"]),
-                               ("quad_p3_810", quad["mesh"], quad["p"], None)):
+                               ("quad_p3_810", quad["mesh"], quad["p"], None),
+                               ("hybrid_p3_512", hyb["mesh"], hyb["p"], None)):
         if only is not None and not tag.startswith(only):
             continue
         t0 = time.perf_counter()
@@ -624,7 +626,10 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
         dt = torch.zeros(1, dtype=torch.float64, device=dev)
         entry = {"elements": info["ne"], "faces": info["ns"], "p": p, "dofs": dofs, "colors": info["ncolors"],
                  "host_mesh_color_s": round(prep_s, 2)}
+        hybrid = tag.startswith("hybrid")  # FP64 only (the FP32 forms refuse hybrid meshes)
         for prec, name in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
+            if hybrid and prec != dgc.DGC_FP64:
+                continue
             ws = torch.empty(dgc.dgc_workspace_size(m.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
             dgc.dgc_import_state(m.h, c_host, c)
             fn = lambda: dgc.dgc_rk_step(m.h, prec, c, 0.3, dt, ws)
@@ -655,9 +660,11 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
             nbuf = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
             buf = torch.empty(nbuf // 8, dtype=torch.float64, device=dev)
             dgc.dgc_import_state(m.h, c_host, c)
-            for kind, call in (("colored", lambda: dgc.dgc_rhs(m.h, prec, c, r)),
-                               ("atomic", lambda: dgc.dgc_rhs_atomic(m.h, prec, c, r)),
-                               ("two_pass", lambda: dgc.dgc_rhs_two_pass(m.h, prec, c, r, buf))):
+            forms = [("colored", lambda: dgc.dgc_rhs(m.h, prec, c, r)),
+                     ("atomic", lambda: dgc.dgc_rhs_atomic(m.h, prec, c, r))]
+            if not hybrid:
+                forms.append(("two_pass", lambda: dgc.dgc_rhs_two_pass(m.h, prec, c, r, buf)))
+            for kind, call in forms:
                 call()
                 t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
                 entry[f"rhs_{kind}_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
@@ -874,7 +881,7 @@ def main():
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
-    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "batch"],
+    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "batch"],
                     help="time only that one of the other workloads (its variants entry, printed alone)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

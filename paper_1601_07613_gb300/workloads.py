@@ -410,6 +410,14 @@ def refined_square_vortex_p2_256(n: int = 256, radius: float = 0.2) -> dict:
                 xc=0.5, yc=0.5, cfl=0.3, steps=200)
 
 
+def hybrid_square_vortex_p3_512(n: int = 512, frac: float = 0.3) -> dict:
+    """Hybrid workload (Table 2's hybrid mesh at benchmark scale): the periodic
+    n x n parallelogram grid with a fraction ``frac`` of its cells split into two
+    triangles (about 340,000 elements at n = 512), p = 3, vortex strength 5."""
+    mi = hybrid_square(n, frac, periodic=True, jitter=0.2, slant=0.3, seed=8, mode="parallelogram")
+    return dict(mesh=mi, p=3, beta=5.0, cfl=0.3)
+
+
 def batched_square_meshes(count: int = 64, seed: int = 5, e_min: float = 1e3,
                           e_max: float = 2e5) -> list[dict]:
     """Independent periodic square meshes of uneven size and order.
