@@ -381,10 +381,11 @@ typedef struct {
   int dim, nvpe, nfpe;
   /* quadrilateral meshes: nvpe = nfpe = 4; a triangle of a hybrid mesh lists
    * -1 as its fourth vertex and has faces 0..2 only.  nonaffine counts the
-   * elements Eq. 2 is not evaluated on here (quadrilaterals that are not
-   * parallelograms, triangles of hybrid meshes). */
+   * quadrilaterals that are not parallelograms (bil[e] = 1): their map is
+   * bilinear and their mass matrix is not diagonal. */
   int quad;
   int64_t nonaffine;
+  int8_t *bil;    /* ne, quadrilateral meshes: 1 for a bilinear (non-parallelogram) element */
   int64_t nv, ne, ns;
   real L[3];
   int periodic;
@@ -508,7 +509,10 @@ static int elem_geometry(orc_mesh *m, int64_t e) {
       scale = fmax(scale, fabs(B[0] - A[0]) + fabs(B[1] - A[1]));
     }
     for (int a = 0; a < 2; ++a) off = fmax(off, fabs(X[a] + X[4 + a] - X[2 + a] - X[6 + a]));
-    if (off > 1e-12 * scale) m->nonaffine++;
+    if (off > 1e-12 * scale) {
+      m->nonaffine++;
+      m->bil[e] = 1;
+    }
   }
   return det > 0.0 ? 0 : -1;
 }
@@ -533,6 +537,7 @@ static void *mesh_new(int dim, int quad, int64_t nv, const real *xyz, int64_t ne
   m->X = (real *)malloc(sizeof(real) * ne * nvpe * dim);
   m->detJ = (real *)malloc(sizeof(real) * ne);
   m->Jinv = (real *)malloc(sizeof(real) * ne * dim * dim);
+  m->bil = (int8_t *)calloc(ne, 1);
   for (int64_t e = 0; e < ne; ++e) {
     for (int k = 0; k < nvpe; ++k) {
       int32_t v = ev[e * nvpe + k];
@@ -652,6 +657,7 @@ void orc_mesh_free(void *h) {
   free(m->enb);
   free(m->detJ);
   free(m->Jinv);
+  free(m->bil);
   free(m->es2);
   free(m->shalf);
   free(m->col);
@@ -1224,8 +1230,46 @@ static int basis_eval_e(const orc_mesh *m, int64_t e, int p, const real *x, real
   return basis_eval(m, p, x, phi, d0, d1, d2);
 }
 
+/* A quadrilateral that is not a parallelogram (reading: Sec. 1 and Table 2
+ * include general quadrilaterals; [giuliani] is not available): the bilinear
+ * map of the square's corners (0,0), (1,0), (1,1), (0,1) to v0..v3,
+ *   x(r, s) = v0 (1-r)(1-s) + v1 r (1-s) + v2 r s + v3 (1-r) s,
+ * with its Jacobian J[a*2 + k] = d x_a / d r_k (straight edges; the map is
+ * linear along each edge). */
+static int elem_is_bil(const orc_mesh *m, int64_t e) { return m->bil && m->bil[e]; }
+static void bil_map(const real *X, real r, real s, real *x, real *J) {
+  const real w[4] = {(1 - r) * (1 - s), r * (1 - s), r * s, (1 - r) * s};
+  const real wr[4] = {-(1 - s), 1 - s, s, -s}, ws[4] = {-(1 - r), -r, r, 1 - r};
+  for (int a = 0; a < 2; ++a) {
+    real v = 0.0, vr = 0.0, vs = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      v += w[k] * X[k * 2 + a];
+      vr += wr[k] * X[k * 2 + a];
+      vs += ws[k] * X[k * 2 + a];
+    }
+    if (x) x[a] = v;
+    if (J) {
+      J[a * 2] = vr;
+      J[a * 2 + 1] = vs;
+    }
+  }
+}
+/* detJ and J^-1 (row k = gradient of r_k) of the bilinear map at (r, s) */
+static real bil_jinv(const real *X, real r, real s, real *Ji) {
+  real J[4];
+  bil_map(X, r, s, NULL, J);
+  const real det = J[0] * J[3] - J[1] * J[2];
+  Ji[0] = J[3] / det;
+  Ji[1] = -J[1] / det;
+  Ji[2] = -J[2] / det;
+  Ji[3] = J[0] / det;
+  return det;
+}
+
 /* reference coordinates of physical point x in element e (nearest periodic
- * image of x to the element's centroid) */
+ * image of x to the element's centroid); a bilinear element's by Newton's
+ * method from the affine guess (ten steps: quadratic convergence from a guess
+ * within the element) */
 static void ref_coords(const orc_mesh *m, int64_t e, const real *x, real *rs) {
   int dim = m->dim;
   const real *X = m->X + e * m->nvpe * dim;
@@ -1242,6 +1286,65 @@ static void ref_coords(const orc_mesh *m, int64_t e, const real *x, real *rs) {
     real v = 0.0;
     for (int a = 0; a < dim; ++a) v += Ji[k * dim + a] * (xs[a] - X[a]);
     rs[k] = v;
+  }
+  if (elem_is_bil(m, e))
+    for (int it = 0; it < 10; ++it) {
+      real y[2], Jb[4];
+      bil_map(X, rs[0], rs[1], y, NULL);
+      bil_jinv(X, rs[0], rs[1], Jb);
+      const real d0 = y[0] - xs[0], d1 = y[1] - xs[1];
+      rs[0] -= Jb[0] * d0 + Jb[1] * d1;
+      rs[1] -= Jb[2] * d0 + Jb[3] * d1;
+    }
+}
+
+/* solve A x = b in place for nrhs right-hand sides (b[i * ldb + k], row i),
+ * Gaussian elimination with partial pivoting; A (n x n, row-major) is destroyed */
+static int dense_solve(int n, real *A, real *b, int nrhs, int ldb) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (fabs(A[i * n + c]) > fabs(A[piv * n + c])) piv = i;
+    if (!(fabs(A[piv * n + c]) > 0.0)) return -1;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) {
+        real t = A[c * n + j];
+        A[c * n + j] = A[piv * n + j];
+        A[piv * n + j] = t;
+      }
+      for (int k = 0; k < nrhs; ++k) {
+        real t = b[c * ldb + k];
+        b[c * ldb + k] = b[piv * ldb + k];
+        b[piv * ldb + k] = t;
+      }
+    }
+    for (int i = c + 1; i < n; ++i) {
+      const real f = A[i * n + c] / A[c * n + c];
+      for (int j = c; j < n; ++j) A[i * n + j] -= f * A[c * n + j];
+      for (int k = 0; k < nrhs; ++k) b[i * ldb + k] -= f * b[c * ldb + k];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c)
+    for (int k = 0; k < nrhs; ++k) {
+      real v = b[c * ldb + k];
+      for (int j = c + 1; j < n; ++j) v -= A[c * n + j] * b[j * ldb + k];
+      b[c * ldb + k] = v / A[c * n + c];
+    }
+  return 0;
+}
+
+/* a bilinear element's mass matrix M_ij = sum_q w_q detJ(x_q) phi_i phi_j over
+ * the volume rule (exact: degree 2p+1 in each direction), into A[n x n] */
+static void bil_mass(const orc_mesh *m, int64_t e, int p, int n, const real *vr, const real *vs, const real *vw,
+                     int nvq, real *A) {
+  const real *X = m->X + e * 8;
+  for (int i = 0; i < n * n; ++i) A[i] = 0.0;
+  for (int q = 0; q < nvq; ++q) {
+    real Ji[4], x[3] = {vr[q], vs[q], 0.0}, phi[ORC_MAXNP];
+    const real det = bil_jinv(X, vr[q], vs[q], Ji);
+    basis_eval_e(m, e, p, x, phi, NULL, NULL, NULL);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[i * n + j] += vw[q] * det * phi[i] * phi[j];
   }
 }
 
@@ -1429,7 +1532,6 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim;
   if (p < 0 || p > ORC_MAXP) return fail("rhs: p out of range");
-  if (m->nonaffine) return fail("rhs: quadrilaterals must be parallelograms");
   int Np = npoly_m(m, p);
   orc_phys ph = {kind, dim, kind == ORC_EULER ? dim + 2 : 1, {0, 0, 0}};
   if (adv)
@@ -1463,10 +1565,18 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
     const int Ne = npoly_e(m, e, p); /* the element's own modes (hybrid: fewer on a triangle) */
     const real *vr, *vs, *vt, *vw;
     const int nvq = vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
-    /* volume integral: sum_q w_q F(U_q) . (J^-T grad_ref phi_j) */
+    /* volume integral: sum_q w_q F(U_q) . (J^-T grad_ref phi_j); a bilinear
+     * element weighs each point by its own detJ and J^-1 (and its mass matrix
+     * is applied at the end), the others have the constant ones folded into
+     * the mass matrix detJ I */
+    const int bil = elem_is_bil(m, e);
     for (int q = 0; q < nvq; ++q) {
       real x[3] = {vr[q], vs[q], vt[q]};
-      real phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM];
+      real phi[ORC_MAXNP], d[3][ORC_MAXNP], U[ORC_MAXM], Jq[4], wq = vw[q];
+      if (bil) {
+        wq *= bil_jinv(m->X + e * 8, vr[q], vs[q], Jq);
+        Ji = Jq;
+      }
       basis_eval_e(m, e, p, x, phi, d[0], d[1], d[2]);
       for (int k = 0; k < M; ++k) {
         real v = 0.0;
@@ -1479,7 +1589,7 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
         for (int j = 0; j < Ne; ++j) {
           real gx = 0.0; /* d phi_j / d x_a */
           for (int r = 0; r < dim; ++r) gx += Ji[r * dim + a] * d[r][j];
-          for (int k = 0; k < M; ++k) re[k * Np + j] += vw[q] * Fa[k] * gx;
+          for (int k = 0; k < M; ++k) re[k * Np + j] += wq * Fa[k] * gx;
         }
       }
     }
@@ -1499,7 +1609,7 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
         real dx = Xl[((q + 1) % 3) * 2] - Xl[q * 2], dy = Xl[((q + 1) % 3) * 2 + 1] - Xl[q * 2 + 1];
         F.meas = sqrt(dx * dx + dy * dy);
       }
-      real scale = F.meas / m->detJ[e];
+      real scale = elem_is_bil(m, e) ? F.meas : F.meas / m->detJ[e];
       for (int q = 0; q < F.nq; ++q) {
         real rs[3], Um[ORC_MAXM], Up[ORC_MAXM], Fs[ORC_MAXM], phi[ORC_MAXNP];
         ref_coords(m, e, F.x + 3 * q, rs);
@@ -1516,6 +1626,18 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
         for (int j = 0; j < Ne; ++j)
           for (int k = 0; k < M; ++k) re[k * Np + j] -= scale * F.w[q] * phi[j] * Fs[k];
       }
+    }
+    if (bil) {
+      /* dc/dt = M^-1 (volume - surface) with the element's own mass matrix */
+      real *A = (real *)malloc(sizeof(real) * Ne * Ne), *b = (real *)malloc(sizeof(real) * Ne * M);
+      bil_mass(m, e, p, Ne, vr, vs, vw, nvq, A);
+      for (int j = 0; j < Ne; ++j)
+        for (int k = 0; k < M; ++k) b[j * M + k] = re[k * Np + j];
+      dense_solve(Ne, A, b, M, M);
+      for (int j = 0; j < Ne; ++j)
+        for (int k = 0; k < M; ++k) re[k * Np + j] = b[j * M + k];
+      free(A);
+      free(b);
     }
   }
   free(F.x);
@@ -1544,7 +1666,6 @@ int orc_set_threads(int n) {
 int orc_dt(void *h, int p, const real *c, real cfl, real *dt_out) {
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim, M = dim + 2, Np = npoly_m(m, p);
-  if (m->nonaffine) return fail("dt: quadrilaterals must be parallelograms");
   orc_rules R;
   if (rules_make(dim, m->quad, 1, default_vol_n1(dim, p), &R)) {
     rules_free(&R);
@@ -1572,6 +1693,13 @@ int orc_dt(void *h, int p, const real *c, real cfl, real *dt_out) {
       bnd += F.meas;
     }
     real vol = m->detJ[e] / (elem_is_quad(m, e) ? 1.0 : dim == 2 ? 2.0 : 6.0);
+    if (elem_is_bil(m, e)) { /* the area, the integral of the bilinear map's detJ */
+      vol = 0.0;
+      for (int q = 0; q < nvq; ++q) {
+        real Jq[4];
+        vol += vw[q] * bil_jinv(m->X + e * 8, vr[q], vs[q], Jq);
+      }
+    }
     real r = dim * vol / bnd;
     real v = r / ((2 * p + 1) * lam);
     if (v < best) best = v;
@@ -1707,7 +1835,6 @@ int orc_eval_points(void *h, int p, int M, const real *c, int n1, real *xyz, rea
                     real *U) {
   orc_mesh *m = (orc_mesh *)h;
   int dim = m->dim, Np = npoly_m(m, p);
-  if (m->nonaffine) return fail("eval_points: quadrilaterals must be parallelograms");
   orc_rules R;
   if (rules_make(dim, m->quad, 1, n1 > 0 ? n1 : default_vol_n1(dim, p), &R)) {
     rules_free(&R);
@@ -1720,13 +1847,20 @@ int orc_eval_points(void *h, int p, int M, const real *c, int n1, real *xyz, rea
     const real *vr, *vs, *vt, *vw;
     vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
     for (int q = 0; q < R.nv; ++q) {
-      real rs[3] = {vr[q], vs[q], vt[q]};
+      real rs[3] = {vr[q], vs[q], vt[q]}, det = m->detJ[e];
       for (int a = 0; a < dim; ++a) {
         real v = X[a];
         for (int k = 0; k < dim; ++k) v += (X[kv[k] * dim + a] - X[a]) * rs[k];
         if (xyz) xyz[(e * R.nv + q) * dim + a] = v;
       }
-      if (w) w[e * R.nv + q] = vw[q] * m->detJ[e];
+      if (elem_is_bil(m, e)) {
+        real y[2], Jq[4];
+        bil_map(X, rs[0], rs[1], y, NULL);
+        det = bil_jinv(X, rs[0], rs[1], Jq);
+        if (xyz)
+          for (int a = 0; a < 2; ++a) xyz[(e * R.nv + q) * dim + a] = y[a];
+      }
+      if (w) w[e * R.nv + q] = vw[q] * det;
       if (U) eval_state_e(m, e, p, M, Np, c + e * M * Np, rs, U + (e * R.nv + q) * M);
     }
   }
@@ -1751,12 +1885,27 @@ int orc_project(void *h, int p, int M, const real *vals, real *c) {
     for (int i = 0; i < M * Np; ++i) ce[i] = 0.0;
     const real *vr, *vs, *vt, *vw;
     vol_rule_e(&R, m, e, &vr, &vs, &vt, &vw);
-    const int Ne = npoly_e(m, e, p);
+    const int Ne = npoly_e(m, e, p), bil = elem_is_bil(m, e);
     for (int q = 0; q < R.nv; ++q) {
-      real x[3] = {vr[q], vs[q], vt[q]}, phi[ORC_MAXNP];
+      real x[3] = {vr[q], vs[q], vt[q]}, phi[ORC_MAXNP], wq = vw[q];
+      if (bil) {
+        real Jq[4];
+        wq *= bil_jinv(m->X + e * 8, vr[q], vs[q], Jq);
+      }
       basis_eval_e(m, e, p, x, phi, NULL, NULL, NULL);
       for (int k = 0; k < M; ++k)
-        for (int j = 0; j < Ne; ++j) ce[k * Np + j] += vw[q] * vals[(e * R.nv + q) * M + k] * phi[j];
+        for (int j = 0; j < Ne; ++j) ce[k * Np + j] += wq * vals[(e * R.nv + q) * M + k] * phi[j];
+    }
+    if (bil) { /* the L2 projection of a bilinear element: M c = sum w detJ u phi */
+      real *A = (real *)malloc(sizeof(real) * Ne * Ne), *b = (real *)malloc(sizeof(real) * Ne * M);
+      bil_mass(m, e, p, Ne, vr, vs, vw, R.nv, A);
+      for (int j = 0; j < Ne; ++j)
+        for (int k = 0; k < M; ++k) b[j * M + k] = ce[k * Np + j];
+      dense_solve(Ne, A, b, M, M);
+      for (int j = 0; j < Ne; ++j)
+        for (int k = 0; k < M; ++k) ce[k * Np + j] = b[j * M + k];
+      free(A);
+      free(b);
     }
   }
   rules_free(&R);
