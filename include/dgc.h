@@ -4,7 +4,8 @@
  * The library evaluates the right-hand side of the modal discontinuous Galerkin
  * discretisation of the Euler equations (Eq. 2 of Giuliani & Krivodonova, "Edge
  * coloring in unstructured CFD codes") on unstructured triangle and tetrahedral
- * meshes, and on parallelogram quadrilateral meshes (dgc_mesh_create_elem).  The
+ * meshes, and on quadrilateral and hybrid triangle/quadrilateral meshes
+ * (dgc_mesh_create_elem).  The
  * surface integral is evaluated color by color (Algorithm 1): the
  * edges (faces) are colored so that no element has two edges of one color
  * (Sec. 3.1), so all edges of one color scatter their flux projection into both
@@ -139,22 +140,29 @@ typedef enum { DGC_TRI = 0, DGC_QUAD = 1, DGC_TET = 2 } dgc_elem;
  * covers; Sec. 3.1 and Table 2 color them with C = {1, 2, 3, 4}).  ev is ne*4 int32,
  * counterclockwise (every corner must turn left); local edge q is (v_q, v_{q+1 mod 4}).
  * A row whose fourth id is -1 is a triangle: a hybrid triangle/quadrilateral mesh,
- * also colored with 4 colors (Table 2's hybrid mesh).  The DG kernels take meshes
- * whose elements are all parallelograms (v2 = v1 + v3 - v0 to 1e-12 of the element
- * size): the reference square [0,1]^2 with corners (0,0), (1,0), (1,1), (0,1) at
- * v0..v3 maps affinely, and the basis is the tensor-product Legendre space Q_p,
- * phi_{a(p+1)+b}(r, s) = l_a(r) l_b(s), l_k(x) = sqrt(2k+1) P_k(2x-1) (Np = (p+1)^2,
- * orthonormal on the square; p = 1..3).  Other quadrilateral and hybrid meshes can be
- * colored, reordered and inspected; device calls on them return DGC_ERR_UNSUPPORTED.
- * A closed quadrilateral mesh with an odd number of elements has no 4-coloring (each
+ * also colored with 4 colors (Table 2's hybrid mesh).  The reference square [0,1]^2
+ * with corners (0,0), (1,0), (1,1), (0,1) at v0..v3 carries the tensor-product
+ * Legendre space Q_p, phi_{a(p+1)+b}(r, s) = l_a(r) l_b(s), l_k(x) = sqrt(2k+1)
+ * P_k(2x-1) (Np = (p+1)^2, orthonormal on the square; p = 1..3).  A mesh whose
+ * elements are all parallelograms (v2 = v1 + v3 - v0 to 1e-12 of the element size)
+ * maps them affinely and runs in every precision.  A hybrid mesh, or a mesh with
+ * general (non-parallelogram) quadrilaterals, runs in FP64 only (other precisions:
+ * DGC_ERR_UNSUPPORTED) through table-driven kernels: its states hold (p+1)^2
+ * coefficients per variable for every element, a triangle using the first
+ * (p+1)(p+2)/2 (its P_p basis as on triangle meshes; the rest are zero on output);
+ * a general quadrilateral maps the square bilinearly, its coefficients refer to the
+ * same Q_p basis, its mass matrix int phi_i phi_j detJ is no longer detJ I, and the
+ * right-hand side is that of Eq. 2 with this mass matrix inverted.  Such meshes
+ * cannot be refined (dgc_refine: DGC_ERR_UNSUPPORTED) and take no two-pass
+ * comparator.  A closed quadrilateral mesh with an odd number of elements has no 4-coloring (each
  * color would be a perfect matching of the elements); dgc_color_edges then returns
  * DGC_ERR_COLORING_LIMIT.  Errors as dgc_mesh_create, plus DGC_ERR_MESH for a
  * quadrilateral that is not convex and counterclockwise. */
 dgc_status dgc_mesh_create_elem(dgc_elem type, int p, int64_t nv, const double* xyz, int64_t ne,
                                 const int32_t* ev, const double* periodic_len, dgc_mesh** out);
 
-/* The mesh's element type (dgc_elem) and the number of its elements the DG kernels do
- * not take (quadrilaterals that are not parallelograms, triangles of hybrid meshes).
+/* The mesh's element type (dgc_elem) and the number of its elements that are general
+ * (non-parallelogram) quadrilaterals, which only the FP64 table-driven kernels take.
  * Either output may be NULL. */
 dgc_status dgc_mesh_element(const dgc_mesh* mesh, int32_t* type, int64_t* nonaffine);
 

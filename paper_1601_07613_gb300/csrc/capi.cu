@@ -171,11 +171,40 @@ void upload_hybrid(const Mesh& m, DeviceMesh& d) {
   }
   for (int q = 0; q < NQE; ++q) t[(size_t)6 * VOL + 2 * EDGE + q] = 0.5 * wg[q];
   std::vector<int8_t> kind(m.ne);
-  for (int64_t e = 0; e < m.ne; ++e) kind[m.elem_new_of_old[e]] = (int8_t)(m.ev[(size_t)e * 4 + 3] >= 0);
+  std::vector<int32_t> slot(m.ne, -1), belem;
+  std::vector<double> G, Mi;
+  int64_t nb = 0;
+  for (int64_t e = 0; e < m.ne; ++e) {
+    const int32_t n = m.elem_new_of_old[e];
+    const bool bil = !m.bil.empty() && m.bil[e];
+    kind[n] = bil ? 2 : (int8_t)(m.ev[(size_t)e * 4 + 3] >= 0);
+    if (!bil) continue;
+    slot[n] = (int32_t)nb++;
+    belem.push_back(n);
+    const double* X = &m.X[(size_t)e * 8];
+    for (int q = 0; q < NQV; ++q) {  // detJ J^-1 (rows: gradients of r and s) at the point
+      double J[4];
+      bilinear_map(X, m.tab.vr[q], m.tab.vs[q], nullptr, J);
+      G.insert(G.end(), {J[3], -J[1], -J[2], J[0]});
+    }
+    const std::vector<double> inv = bilinear_mass_inverse(m, e);
+    Mi.insert(Mi.end(), inv.begin(), inv.end());
+  }
   d.hyb_kind = dalloc<int8_t>(m.ne);
   d.hyb_tab = dalloc<double>((int64_t)t.size());
   DGC_CUDA(cudaMemcpy(d.hyb_kind, kind.data(), kind.size(), cudaMemcpyHostToDevice));
   DGC_CUDA(cudaMemcpy(d.hyb_tab, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
+  d.nbil = nb;
+  if (nb > 0) {
+    d.bil_slot = dalloc<int32_t>(m.ne);
+    d.bil_elem = dalloc<int32_t>(nb);
+    DGC_CUDA(cudaMemcpy(d.bil_elem, belem.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
+    d.bil_G = dalloc<double>((int64_t)G.size());
+    d.bil_Minv = dalloc<double>((int64_t)Mi.size());
+    DGC_CUDA(cudaMemcpy(d.bil_slot, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice));
+    DGC_CUDA(cudaMemcpy(d.bil_G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice));
+    DGC_CUDA(cudaMemcpy(d.bil_Minv, Mi.data(), sizeof(double) * Mi.size(), cudaMemcpyHostToDevice));
+  }
 }
 
 // Refined triangle meshes: the tables of the state transfer to and from the
@@ -271,7 +300,10 @@ void upload(Mesh& m) {
     }
     topo[k] = make_int4(en[l], r >= 0 ? en[r] : -1, ql | (qr << 4) | (orient << 8), 0);
     double meas = m.smeas[old];
-    double sl = meas / m.detJ[l], sr = r >= 0 ? meas / m.detJ[r] : 0.0;
+    // |f| / detJ per side (a bilinear element's detJ varies: its mass matrix is
+    // applied after the colors instead, so its factor is |f|)
+    auto fdet = [&](int32_t e) { return m.bil.empty() || !m.bil[e] ? m.detJ[e] : 1.0; };
+    double sl = meas / fdet(l), sr = r >= 0 ? meas / fdet(r) : 0.0;
     const double* n = &m.snormal[(size_t)old * dim];
     if (dim == 2) {
       fgeo[2 * k] = make_double2(n[0], n[1]);
@@ -353,10 +385,7 @@ void check_tile(const Mesh& m, int epb, int tpe) {
 // The checks every device call on a mesh makes first.
 void require_device_ready(const Mesh& m) {
   require(m.ncolors > 0 && !m.side_old_of_new.empty(), "mesh is not colored (call dgc_color_edges first)");
-  require(!m.nonaffine,
-          "the kernels take parallelogram quadrilaterals only; this mesh (general quadrilaterals or hybrid) is "
-          "colored only",
-          DGC_ERR_UNSUPPORTED);
+  require(!m.nonaffine || m.hybrid, "general quadrilaterals need the table-driven kernels", DGC_ERR_UNSUPPORTED);
 }
 
 // The kernels' view of an uploaded mesh (d: its device arrays).
@@ -420,6 +449,11 @@ int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const vo
   if (x.quad) return quad_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
   return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, ss, r, buf, sa)
                     : tet_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
+}
+// general quadrilaterals of a hybrid mesh: their mass matrices, after the colors
+int mass(const Ctx& x, TypeCfg ty, void* r) {
+  if (!x.hybrid) return 0;
+  return ty == TY_D ? hyb_mass(x, static_cast<double*>(r)) : -1;
 }
 int cfl(const Ctx& x, const double* s, double c, double* dt, float* sh) {
   if (x.hybrid) return sh ? -1 : hyb_cfl(x, s, c, dt);
@@ -511,6 +545,7 @@ int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss,
     run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, state, ss, rhs); });
     for (int c = 1; c <= m.ncolors; ++c)
       run(m, x, DGC_K_COLOR, n, [&] { return surf(x, ty, SURF_RMW, off[c - 1], off[c], state, ss, rhs, nullptr, nullptr); });
+    run(m, x, DGC_K_VOLUME, n, [&] { return mass(x, ty, rhs); });
   }
   return n;
 }
@@ -589,6 +624,7 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
         launch(DGC_K_VOLUME, [&] { return vol(x, TY_D, us, 0, w.rhs, k0 == 2 ? unreached(m) : 0); });
         for (int k = k0; k <= C; ++k)
           launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
+        launch(DGC_K_VOLUME, [&] { return mass(x, TY_D, w.rhs); });
         launch(DGC_K_STAGE, [&] { return stage_update(x, false, us, w.rhs, sa); });
       }
     }
@@ -663,6 +699,10 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->cfl_est);
   cudaFree(m.dev->hyb_kind);
   cudaFree(m.dev->hyb_tab);
+  cudaFree(m.dev->bil_slot);
+  cudaFree(m.dev->bil_elem);
+  cudaFree(m.dev->bil_G);
+  cudaFree(m.dev->bil_Minv);
   cudaFree(m.dev->xf_src);
   cudaFree(m.dev->xf_kind);
   cudaFree(m.dev->xf_kids);
@@ -1287,6 +1327,7 @@ dgc_status dgc_rhs_atomic(dgc_mesh* mesh, dgc_prec prec, const double* c_dev, do
     int64_t n = 0;
     run(m, x, DGC_K_VOLUME, n, [&] { return vol(x, ty, c_dev, 0, rhs_dev); });
     run(m, x, DGC_K_ATOMIC, n, [&] { return surf(x, ty, SURF_ATOMIC, 0, m.ns, c_dev, 0, rhs_dev, nullptr, nullptr); });
+    run(m, x, DGC_K_VOLUME, n, [&] { return mass(x, ty, rhs_dev); });
     finish(m, n);
   });
 }

@@ -33,8 +33,15 @@ struct DeviceMesh {
   // and the child projections P [4][Np][Np]
   // hybrid triangle/quadrilateral meshes: per element its kind (0 triangle, 1
   // quadrilateral), and the tables of kernels_hybrid.cu
-  int8_t* hyb_kind = nullptr;
+  int8_t* hyb_kind = nullptr;  // 2: a general (bilinear) quadrilateral
   double* hyb_tab = nullptr;
+  // general quadrilaterals: per element its slot (-1: none), and per slot
+  // detJ J^-1 at the volume points [NQV][4] and the inverse mass matrix [Np][Np]
+  int32_t* bil_slot = nullptr;
+  int32_t* bil_elem = nullptr;
+  double* bil_G = nullptr;
+  double* bil_Minv = nullptr;
+  int64_t nbil = 0;
   int32_t* xf_src = nullptr;
   int8_t* xf_kind = nullptr;
   int32_t* xf_kids = nullptr;
@@ -167,6 +174,8 @@ int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* r
 int hyb_volume(const Ctx& x, const double* state, double* rhs);
 int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs);
 int hyb_cfl(const Ctx& x, const double* state, double cfl, double* dt);
+// general quadrilaterals: rhs <- M^-1 rhs on every bilinear element
+int hyb_mass(const Ctx& x, double* rhs);
 int hyb_table_doubles(int p);
 // dgc_rhs of a triangle mesh in one cooperative launch (FP64 or FP32-mixed with
 // FP64 state and rhs): off = the color offsets, fused = the first color also

@@ -66,6 +66,10 @@ struct Mesh {
   // carries the space of its kind, P_p (tab_tri) or Q_p (tab); states keep
   // (p+1)^2 coefficients per variable, a triangle using the first (p+1)(p+2)/2
   bool hybrid = false;
+  // general quadrilaterals (not parallelograms) map the square bilinearly: per
+  // element 1 for such an element (original order); they also run on the
+  // table-driven kernels (hybrid = true), with their own mass matrices
+  std::vector<uint8_t> bil;
   int64_t nv = 0, ne = 0, ns = 0;
   bool periodic = false;
   double L[3] = {0, 0, 0};
@@ -142,6 +146,10 @@ void reorder(Mesh& m, bool renumber, bool reorder_left);
 void refine(Mesh& m, const std::vector<uint8_t>& flag);
 void coarsen(Mesh& m);
 void vol_points(const Mesh& m, double* xyz);
+// general quadrilaterals: the bilinear map (point x and Jacobian J[a*2+k] at
+// (r, s) of the square) and the inverse mass matrix of element e (np x np)
+void bilinear_map(const double* X, double r, double s, double* x, double* J);
+std::vector<double> bilinear_mass_inverse(const Mesh& m, int64_t e);
 void project(const Mesh& m, const double* vals, double* c);
 
 // Device side (capi.cu).

@@ -12,6 +12,14 @@
 // exchanging them with shuffles, each projecting onto its own element's modes
 // and adding into its right-hand side (read-modify-write: the coloring makes
 // the two elements of an edge the only writers of their blocks in the color).
+//
+// A general (bilinear) quadrilateral (kind 2) takes the square's tables too; its
+// volume integral weights each point's flux by detJ J^-1 at that point, its
+// faces' scales are the bare face lengths, and after the last color its
+// right-hand side is multiplied by the inverse of its own mass matrix
+// M_ij = int phi_i phi_j detJ (k_hyb_mass), where an affine element's mass
+// matrix is detJ times the identity and is divided out by the face and volume
+// scales instead.
 #include "dev_util.cuh"
 #include "device.cuh"
 
@@ -51,10 +59,13 @@ __device__ __forceinline__ void hyb_flux(const double* U, double* F, double* G) 
 }
 
 // volume integral of element e (kind k): rhs = sum_q w_q F(U_q).(J^-T grad phi_j)
+// (kind 2: detJ J^-1 at each point, from bil_G[slot])
 template <int P>
 __global__ void __launch_bounds__(128) k_hyb_vol(const double* __restrict__ c, const double* __restrict__ jinv,
                                                  const int8_t* __restrict__ kind, const double* __restrict__ tab,
-                                                 double* __restrict__ rhs, int64_t ne) {
+                                                 const int32_t* __restrict__ bil_slot,
+                                                 const double* __restrict__ bil_G, double* __restrict__ rhs,
+                                                 int64_t ne) {
   using D = HybDim<P>;
   __shared__ double s[D::SIZE];
   hyb_stage<P>(s, tab);
@@ -63,11 +74,12 @@ __global__ void __launch_bounds__(128) k_hyb_vol(const double* __restrict__ c, c
   if (e >= ne) return;
   const int k = kind[e];
   const int np = k ? D::NPX : D::NPT;
-  const double* phi = s + D::vol(k);
+  const double* phi = s + D::vol(k ? 1 : 0);
   const double* gr = phi + D::VOL;
   const double* gs = gr + D::VOL;
   const double* ce = c + e * D::NV;
-  const double j00 = jinv[4 * e], j01 = jinv[4 * e + 1], j10 = jinv[4 * e + 2], j11 = jinv[4 * e + 3];
+  double j00 = jinv[4 * e], j01 = jinv[4 * e + 1], j10 = jinv[4 * e + 2], j11 = jinv[4 * e + 3];
+  const double* Gq = k == 2 ? bil_G + (int64_t)bil_slot[e] * (4 * D::NQV) : nullptr;
   double acc[D::NV];
 #pragma unroll
   for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
@@ -80,6 +92,7 @@ __global__ void __launch_bounds__(128) k_hyb_vol(const double* __restrict__ c, c
     }
     double F[4], G[4];
     hyb_flux(U, F, G);
+    if (Gq) j00 = Gq[4 * q], j01 = Gq[4 * q + 1], j10 = Gq[4 * q + 2], j11 = Gq[4 * q + 3];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const double fr = j00 * F[m] + j01 * G[m], fs = j10 * F[m] + j11 * G[m];
@@ -115,7 +128,7 @@ __global__ void __launch_bounds__(128) k_hyb_surf(const double* __restrict__ c, 
   const int64_t elem = right ? tp.y : tp.x;
   const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
   const bool writer = valid && !(side && bnd);
-  const int kd = kind[elem];
+  const int kd = kind[elem] ? 1 : 0;  // a general quadrilateral takes the square's tables
   const int np = kd ? D::NPX : D::NPT;
   const double2 g0 = fgeo[2 * k], g1 = fgeo[2 * k + 1];
   const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(128) k_hyb_cfl(const double* __restrict__ c, c
   __syncthreads();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
-  const int k = kind[e];
+  const int k = kind[e] ? 1 : 0;
   const int np = k ? D::NPX : D::NPT;
   const double* phi = s + D::vol(k);
   const double* ce = c + e * D::NV;
@@ -202,6 +215,31 @@ __global__ void __launch_bounds__(128) k_hyb_cfl(const double* __restrict__ c, c
   if (d > 0.0) atomicMin(dtbits, (unsigned long long)__double_as_longlong(d));
 }
 
+// general quadrilaterals: rhs_e <- M_e^-1 rhs_e per variable, one thread per
+// such element (bil_elem: the element of each slot; Minv row-major [NPX][NPX])
+template <int P>
+__global__ void __launch_bounds__(128) k_hyb_mass(const int32_t* __restrict__ bil_elem,
+                                                  const double* __restrict__ Minv, double* __restrict__ rhs,
+                                                  int64_t nb) {
+  using D = HybDim<P>;
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double* re = rhs + (int64_t)bil_elem[b] * D::NV;
+  const double* A = Minv + b * (D::NPX * D::NPX);
+  double r[D::NV], o[D::NV];
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) r[i] = re[i], o[i] = 0.0;
+  for (int i = 0; i < D::NPX; ++i)
+#pragma unroll
+    for (int j = 0; j < D::NPX; ++j) {
+      const double a = A[i * D::NPX + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) o[m * D::NPX + i] += a * r[m * D::NPX + j];
+    }
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) re[i] = o[i];
+}
+
 template <int P>
 static int hyb_p(const Ctx& x, int what, const double* state, double* rhs, int64_t b, int64_t e, double cfl,
                  double* dt) {
@@ -209,8 +247,13 @@ static int hyb_p(const Ctx& x, int what, const double* state, double* rhs, int64
   const DeviceMesh* d = x.d;
   if (what == 0) {
     if (x.ne <= 0) return 0;
-    k_hyb_vol<P><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(state, d->jinv, d->hyb_kind, d->hyb_tab, rhs,
-                                                                    x.ne);
+    k_hyb_vol<P><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(state, d->jinv, d->hyb_kind, d->hyb_tab,
+                                                                    d->bil_slot, d->bil_G, rhs, x.ne);
+    return 1;
+  }
+  if (what == 4) {
+    if (d->nbil <= 0) return 0;
+    k_hyb_mass<P><<<(unsigned)((d->nbil + bs - 1) / bs), bs, 0, x.st>>>(d->bil_elem, d->bil_Minv, rhs, d->nbil);
     return 1;
   }
   if (what == 1 || what == 2) {
@@ -246,6 +289,7 @@ int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const dou
 int hyb_cfl(const Ctx& x, const double* state, double cfl, double* dt) {
   return hyb(x, 3, state, nullptr, 0, 0, cfl, dt);
 }
+int hyb_mass(const Ctx& x, double* rhs) { return hyb(x, 4, nullptr, rhs, 0, 0, 0.0, nullptr); }
 int hyb_table_doubles(int p) {
   switch (p) {
     case 1: return HybDim<1>::SIZE;

@@ -473,7 +473,9 @@ static void elem_face_vertices(const Mesh& m, int64_t e, int q, int* fv) {
 // A quadrilateral maps the square's corners (0,0), (1,0), (1,1), (0,1) to
 // v0..v3 through v0, v1 and v3 (affine: exact for parallelograms); it must turn
 // counterclockwise at every corner, and one that is not a parallelogram is
-// counted in m.nonaffine (colored only).  A triangle of a hybrid mesh is affine.
+// counted in m.nonaffine and marked in m.bil (its map is bilinear; detJ and
+// J^-1 here are those of the corner v0 only, used for nothing but the sign
+// check).  A triangle of a hybrid mesh is affine.
 static void element_jacobian(Mesh& m, int64_t e) {
   const int dim = m.dim;
   const double* X = &m.X[(size_t)e * m.nvpe * dim];
@@ -494,7 +496,11 @@ static void element_jacobian(Mesh& m, int64_t e) {
         scale = std::max(scale, std::fabs(B[0] - A[0]) + std::fabs(B[1] - A[1]));
       }
       for (int k = 0; k < 2; ++k) off = std::max(off, std::fabs(X[k] + X[4 + k] - X[2 + k] - X[6 + k]));
-      if (off > 1e-12 * scale) m.nonaffine++;
+      if (off > 1e-12 * scale) {
+        m.nonaffine++;
+        if (m.bil.size() != (size_t)m.ne) m.bil.assign(m.ne, 0);
+        m.bil[e] = 1;
+      }
     }
     det = a * d - b * c;
     Ji[0] = d / det;
@@ -570,6 +576,12 @@ static void side_geometry(Mesh& m) {
     for (int q = 0; q < elem_faces(m, e); ++q) bnd += face_normal(m, e, q, n);
     const bool q4 = m.quad && elem_faces(m, e) == 4;
     double vol = m.detJ[e] / (q4 ? 1.0 : dim == 2 ? 2.0 : 6.0);
+    if (q4 && !m.bil.empty() && m.bil[e]) {  // a general quadrilateral: its area (shoelace)
+      const double* X = &m.X[(size_t)e * 8];
+      double a = 0.0;
+      for (int k = 0; k < 4; ++k) a += X[2 * k] * X[2 * ((k + 1) % 4) + 1] - X[2 * ((k + 1) % 4)] * X[2 * k + 1];
+      vol = 0.5 * a;
+    }
     m.inradius[e] = dim * vol / bnd;
   }
 }
@@ -651,6 +663,7 @@ Mesh* build_mesh(int dim, int p, int64_t nv, const double* xyz, int64_t ne, cons
   m->tab = make_tables(dim, p, quad);
   m->np = m->tab.np;
   for (int64_t e = 0; quad && e < m->ne && !m->hybrid; ++e) m->hybrid = elem_faces(*m, e) == 3;
+  if (quad && m->nonaffine > 0) m->hybrid = true;  // general quadrilaterals: the table-driven kernels
   if (m->hybrid) m->tab_tri = make_tables(2, p, false);
   return m.release();
 }
@@ -1134,12 +1147,66 @@ static const RefTables& elem_tab(const Mesh& m, int64_t e) {
   return m.hybrid && elem_faces(m, e) == 3 ? m.tab_tri : m.tab;
 }
 
+// a general quadrilateral's bilinear map of the square's corners to v0..v3 at
+// (r, s), its point x and Jacobian J[a * 2 + k] = d x_a / d r_k
+void bilinear_map(const double* X, double r, double s, double* x, double* J) {
+  const double w[4] = {(1 - r) * (1 - s), r * (1 - s), r * s, (1 - r) * s};
+  const double wr[4] = {-(1 - s), 1 - s, s, -s}, ws[4] = {-(1 - r), -r, r, 1 - r};
+  for (int a = 0; a < 2; ++a) {
+    double v = 0.0, vr = 0.0, vs = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      v += w[k] * X[k * 2 + a];
+      vr += wr[k] * X[k * 2 + a];
+      vs += ws[k] * X[k * 2 + a];
+    }
+    if (x) x[a] = v;
+    if (J) J[a * 2] = vr, J[a * 2 + 1] = vs;
+  }
+}
+
+// the inverse of a general quadrilateral's mass matrix M_ij = sum_q w_q detJ_q
+// phi_i phi_j over the volume rule (row-major, np x np), by Gauss-Jordan
+// elimination with partial pivoting (M is symmetric positive definite)
+std::vector<double> bilinear_mass_inverse(const Mesh& m, int64_t e) {
+  const RefTables& T = m.tab;
+  const int n = T.np;
+  std::vector<double> A((size_t)n * n, 0.0), I((size_t)n * n, 0.0);
+  const double* X = &m.X[(size_t)e * 8];
+  for (int q = 0; q < T.nqv; ++q) {
+    double J[4];
+    bilinear_map(X, T.vr[q], T.vs[q], nullptr, J);
+    const double det = J[0] * J[3] - J[1] * J[2];
+    const double* ph = &T.phiV[(size_t)q * n];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[(size_t)i * n + j] += T.vw[q] * det * ph[i] * ph[j];
+  }
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = i;
+    for (int j = 0; j < n; ++j) {
+      std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
+      std::swap(I[(size_t)c * n + j], I[(size_t)piv * n + j]);
+    }
+    const double d = A[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) A[(size_t)c * n + j] /= d, I[(size_t)c * n + j] /= d;
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = A[(size_t)i * n + c];
+      for (int j = 0; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)c * n + j], I[(size_t)i * n + j] -= f * I[(size_t)c * n + j];
+    }
+  }
+  return I;
+}
+
 void vol_points(const Mesh& m, double* xyz) {
   for (int64_t e = 0; e < m.ne; ++e) {
     const RefTables& T = elem_tab(m, e);
     const bool q4 = m.quad && elem_faces(m, e) == 4;
     const int kv[3] = {1, q4 ? 3 : 2, 3};  // the vertices at the reference axes' ends
     const double* X = &m.X[(size_t)e * m.nvpe * m.dim];
+    const bool bil = !m.bil.empty() && m.bil[e];
     for (int q = 0; q < T.nqv; ++q) {
       double rs[3] = {T.vr[q], T.vs[q], T.vt[q]};
       for (int a = 0; a < m.dim; ++a) {
@@ -1147,6 +1214,7 @@ void vol_points(const Mesh& m, double* xyz) {
         for (int k = 0; k < m.dim; ++k) v += (X[kv[k] * m.dim + a] - X[a]) * rs[k];
         xyz[((size_t)e * T.nqv + q) * m.dim + a] = v;
       }
+      if (bil) bilinear_map(X, rs[0], rs[1], &xyz[((size_t)e * T.nqv + q) * 2], nullptr);
     }
   }
 }
@@ -1155,13 +1223,31 @@ void project(const Mesh& m, const double* vals, double* c) {
   const int M = m.M, np = m.np;  // the state's stride (hybrid: the quadrilaterals' count)
   for (int64_t e = 0; e < m.ne; ++e) {
     const RefTables& T = elem_tab(m, e);
+    const bool bil = !m.bil.empty() && m.bil[e];
     double* ce = c + (size_t)e * M * np;
     std::fill(ce, ce + M * np, 0.0);
-    for (int q = 0; q < T.nqv; ++q)
+    for (int q = 0; q < T.nqv; ++q) {
+      double wq = T.vw[q];
+      if (bil) {
+        double J[4];
+        bilinear_map(&m.X[(size_t)e * 8], T.vr[q], T.vs[q], nullptr, J);
+        wq *= J[0] * J[3] - J[1] * J[2];
+      }
       for (int k = 0; k < M; ++k) {
-        double v = T.vw[q] * vals[((size_t)e * T.nqv + q) * M + k];
+        double v = wq * vals[((size_t)e * T.nqv + q) * M + k];
         for (int j = 0; j < T.np; ++j) ce[k * np + j] += v * T.phiV[(size_t)q * T.np + j];
       }
+    }
+    if (bil) {  // the L2 projection on a general quadrilateral: c = M^-1 (sum w detJ u phi)
+      const std::vector<double> Mi = bilinear_mass_inverse(m, e);
+      std::vector<double> b(ce, ce + M * np);
+      for (int k = 0; k < M; ++k)
+        for (int i = 0; i < np; ++i) {
+          double v = 0.0;
+          for (int j = 0; j < np; ++j) v += Mi[(size_t)i * np + j] * b[k * np + j];
+          ce[k * np + i] = v;
+        }
+    }
   }
 }
 

@@ -125,12 +125,31 @@ def test_projection_matches_oracle_quad(oracle_mod, p):
     np.testing.assert_allclose(dgc.dgc_mesh_info(m.h)["ne"], mi.ne)
 
 
+@pytest.mark.parametrize("p", [1, 3])
+@pytest.mark.parametrize("kind", ["quad", "hybrid"])
+def test_projection_matches_oracle_bilinear(oracle_mod, p, kind):
+    """General quadrilaterals: the volume points under the bilinear map and the
+    L2 projection through each element's own mass matrix, as the oracle's."""
+    mi = (W.periodic_square_quad(8, "vertex", 0.2, seed=3) if kind == "quad"
+          else W.hybrid_square(8, 0.3, jitter=0.2, seed=3))
+    m = dgc.Mesh.from_input(mi, p)
+    assert m.elem == dgc.DGC_QUAD and m.nonaffine > 0
+    om = oracle_mod.OracleMesh.from_input(mi)
+    xyz = dgc.dgc_vol_points(m.h)
+    xyz_o, _, _ = om.eval_points(p)
+    np.testing.assert_allclose(xyz, xyz_o, atol=1e-15)
+    vals = W.vortex_field(xyz[..., 0], xyz[..., 1])
+    c_o = om.project(p, vals)
+    np.testing.assert_allclose(dgc.dgc_project(m.h, vals), c_o, atol=1e-12 * np.abs(c_o).max())
+    m.close()
+
+
 def test_quad_mesh_statuses(L):
-    """Non-convex or clockwise quadrilaterals are mesh errors; general
-    quadrilaterals (also in a hybrid mesh) are colored, and their device calls
-    are refused on the host; a hybrid mesh of parallelograms and triangles takes
-    device calls in FP64 only; an odd closed quadrilateral mesh cannot be
-    4-colored."""
+    """Non-convex or clockwise quadrilaterals are mesh errors; a hybrid mesh
+    (of parallelograms and triangles, or with general quadrilaterals) and a mesh
+    of general quadrilaterals take device calls in FP64 only, the others refused
+    on the host, and cannot be refined; an odd closed quadrilateral mesh cannot
+    be 4-colored."""
     mi = W.periodic_square_quad(6)
     bad = mi.ev.copy()
     bad[3] = bad[3, ::-1]
@@ -153,9 +172,10 @@ def test_quad_mesh_statuses(L):
         m = dgc.Mesh.from_input(g, 2)
         assert m.elem == dgc.DGC_QUAD and m.nonaffine > 0
         m.color(3)
-        with pytest.raises(dgc.DgcError) as e:
-            dgc.dgc_rhs(m.h, dgc.DGC_FP64, 4096, 8192, 0)
-        assert e.value.status == 4
+        for prec in (dgc.DGC_FP32_MIXED, dgc.DGC_FP32_KAHAN):
+            with pytest.raises(dgc.DgcError) as e:
+                dgc.dgc_rhs(m.h, prec, 4096, 8192, 0)
+            assert e.value.status == 4
         with pytest.raises(dgc.DgcError) as e:
             dgc.dgc_refine(m.h, np.array([0], np.int32))
         assert e.value.status == 4
