@@ -588,7 +588,10 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     state),
     the 256 x 256 x 2 periodic triangle mesh refined once within radius 0.2 of the
     centre (180,512 elements, hanging edges, 6 colors) at p = 2, and
-    656,100 periodic parallelograms (810 x 810, 4 edge colors) at p = 3.
+    656,100 periodic parallelograms (810 x 810, 4 edge colors) at p = 3, the
+    hybrid 512 x 512 grid with 30 % of its cells split into triangles at p = 3,
+    and 262,144 general (bilinear) quadrilaterals (512 x 512, every vertex
+    jittered) at p = 3, the last two in FP64 only.
     On the tetrahedra and the parallelograms the mixed step also gets a per-kernel
     breakdown from a profiled pass against the HBM roofline."""
     out = {}
@@ -596,11 +599,13 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     ref = W.refined_square_vortex_p2_256()
     quad = W.quad_square_vortex_p3_810()
     hyb = W.hybrid_square_vortex_p3_512()
+    bil = W.bilinear_square_vortex_p3_512()
     hbm, _ = peaks()
     for tag, mi, p, refine in (("tet_p2_64cube", tube["mesh"], tube["p"], None),
                                ("nonconforming_p2_256", ref["mesh"], ref["p"], ref["refine"]),
                                ("quad_p3_810", quad["mesh"], quad["p"], None),
-                               ("hybrid_p3_512", hyb["mesh"], hyb["p"], None)):
+                               ("hybrid_p3_512", hyb["mesh"], hyb["p"], None),
+                               ("bilinear_p3_512", bil["mesh"], bil["p"], None)):
         if only is not None and not tag.startswith(only):
             continue
         t0 = time.perf_counter()
@@ -626,7 +631,8 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
         dt = torch.zeros(1, dtype=torch.float64, device=dev)
         entry = {"elements": info["ne"], "faces": info["ns"], "p": p, "dofs": dofs, "colors": info["ncolors"],
                  "host_mesh_color_s": round(prep_s, 2)}
-        hybrid = tag.startswith("hybrid")  # FP64 only (the FP32 forms refuse hybrid meshes)
+        # FP64 only (the FP32 forms refuse hybrid meshes and general quadrilaterals)
+        hybrid = tag.startswith(("hybrid", "bilinear"))
         for prec, name in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
             if hybrid and prec != dgc.DGC_FP64:
                 continue
@@ -881,7 +887,7 @@ def main():
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
-    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "batch"],
+    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "bilinear", "batch"],
                     help="time only that one of the other workloads (its variants entry, printed alone)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -418,6 +418,14 @@ def hybrid_square_vortex_p3_512(n: int = 512, frac: float = 0.3) -> dict:
     return dict(mesh=mi, p=3, beta=5.0, cfl=0.3)
 
 
+def bilinear_square_vortex_p3_512(n: int = 512) -> dict:
+    """General-quadrilateral workload: the periodic n x n grid with every vertex
+    jittered by U(-0.2 h, 0.2 h) (bilinear elements, 262,144 at n = 512), p = 3,
+    vortex strength 5."""
+    mi = periodic_square_quad(n, "vertex", 0.2, seed=9)
+    return dict(mesh=mi, p=3, beta=5.0, cfl=0.3)
+
+
 def batched_square_meshes(count: int = 64, seed: int = 5, e_min: float = 1e3,
                           e_max: float = 2e5) -> list[dict]:
     """Independent periodic square meshes of uneven size and order.
