@@ -130,6 +130,13 @@ class _Build:
         L.orc_transfer.argtypes = [P, P, C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, dp, dp]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
+        i8 = C.POINTER(C.c_int8)
+        L.orc_set_bc.argtypes = [P, i8, i8, C.c_int, dp, dp, i8]
+        L.orc_boundary_state.argtypes = [P, C.c_int32, dp, dp, dp, dp]
+        L.orc_set_time.argtypes = [P, R]
+        L.orc_get_time.argtypes = [P, dp]
+        L.orc_set_limiter.argtypes = [P, C.c_int]
+        L.orc_limit.argtypes = [P, C.c_int, dp]
         self.L = L
 
     def arr(self, a):
@@ -434,6 +441,50 @@ class OracleMesh:
         B.check(B.L.orc_rk_step_kind(self._h, p, kind, B.ptr(a) if a is not None else None, B.ptr(u), cfl, dt,
                                      B.ptr(out)))
         return u, float(out[0])
+
+    # boundary conditions, time and limiter (triangle meshes; dg_oracle.c
+    # orc_set_bc, orc_limit)
+    BC_TRANSMISSIVE, BC_WALL, BC_STATE, BC_SHOCK = 0, 1, 2, 3
+
+    def set_bc(self, kind, sidx=None, states=None, shock=None, shock_states=None):
+        """kind[s] per side (boundary sides only matter), sidx[s] the state of a
+        BC_STATE side, states [n][4], shock (a, b, c): the state shock_states[0]
+        where x < a + b y + c t, else shock_states[1]."""
+        B = self._b
+        kind = np.ascontiguousarray(kind, dtype=np.int8)
+        assert kind.shape == (self.ns,)
+        sidx = None if sidx is None else np.ascontiguousarray(sidx, dtype=np.int8)
+        st = B.arr(np.zeros((0, 4)) if states is None else np.asarray(states).reshape(-1, 4))
+        sh = None if shock is None else B.arr(shock)
+        ss = None if shock_states is None else np.ascontiguousarray(shock_states, dtype=np.int8)
+        B.check(B.L.orc_set_bc(self._h, _i8(kind), _i8(sidx) if sidx is not None else None, st.shape[0],
+                               B.ptr(st) if st.size else None, B.ptr(sh) if sh is not None else None,
+                               _i8(ss) if ss is not None else None))
+
+    def boundary_state(self, s: int, Um, n, x):
+        B = self._b
+        Um, n, x = B.arr(Um), B.arr(n), B.arr(x)
+        out = np.zeros(4, self.real)
+        B.check(B.L.orc_boundary_state(self._h, int(s), B.ptr(Um), B.ptr(n), B.ptr(x), B.ptr(out)))
+        return out
+
+    def set_time(self, t: float):
+        self._b.check(self._b.L.orc_set_time(self._h, t))
+
+    def time(self) -> float:
+        out = np.zeros(1, self.real)
+        self._b.check(self._b.L.orc_get_time(self._h, self._b.ptr(out)))
+        return float(out[0])
+
+    def set_limiter(self, on: bool):
+        self._b.check(self._b.L.orc_set_limiter(self._h, int(bool(on))))
+
+    def limit(self, p: int, c: np.ndarray) -> np.ndarray:
+        """The limited copy of state c (the limiter alone, as after an RK stage)."""
+        B = self._b
+        u = np.array(c, dtype=self.real, copy=True, order="C")
+        B.check(B.L.orc_limit(self._h, p, B.ptr(u)))
+        return u
 
     def eval_points(self, p: int, c=None, n1: int = 0, M: int | None = None):
         """Volume points (unwrapped), physical weights and, if c is given, U there."""

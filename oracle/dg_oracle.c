@@ -23,7 +23,11 @@
  *     left-ascending order of the remaining colors of Sec. 5 (Tables 5, 6);
  *   - quadrilateral and hybrid triangle/quadrilateral meshes, colored with
  *     C = {1, 2, 3, 4} (Sec. 3.1, Table 2), and Eq. 2 on parallelogram
- *     quadrilaterals.
+ *     quadrilaterals;
+ *   - the boundary conditions and the limiter of the double Mach reflection
+ *     run of Sec. 5 (Table 7): slip walls, prescribed states, a moving planar
+ *     shock, and a Barth-Jespersen limiter after every RK stage (readings: the
+ *     paper takes both from [giuliani]).
  *
  * The same file builds three ways (oracle/__init__.py): FP64 (the tests'
  * oracle), long double (the extended build: the same steps with a wider
@@ -64,6 +68,7 @@ int orc_real_mant_dig(void) { return sizeof(real) == sizeof(double) ? DBL_MANT_D
 #define ORC_MAXP 8
 #define ORC_MAXNP 165 /* (p+1)(p+2)(p+3)/6 at p = 8 */
 #define ORC_MAXM 5
+#define ORC_MAXBCS 8
 
 static char orc_err[256];
 const char *orc_last_error(void) { return orc_err; }
@@ -402,6 +407,15 @@ typedef struct {
   int32_t *es2;   /* ne * nfpe: second side on a split edge of a coarse element, -1 if none */
   int8_t *shalf;  /* per side: half of the right element's edge a hanging side covers, or -1 */
   int8_t *col;    /* per side: color from the map of Sec. 3.2 */
+  /* boundary conditions and limiter (orc_set_bc, orc_set_limiter); all zero by
+   * default: every boundary face transmissive, no limiter */
+  int8_t *bck;    /* per side: ORC_BC_* kind of a boundary side (r = -1) */
+  int8_t *bcs;    /* per side: state index of an ORC_BC_STATE side */
+  real bcst[ORC_MAXBCS][ORC_MAXM];
+  real shock[3];  /* ORC_BC_SHOCK: state shock_st[0] where x < shock[0] + shock[1] y + shock[2] t */
+  int8_t shock_st[2];
+  real time;      /* the time the boundary states are taken at */
+  int limit;      /* 1: the limiter after every RK stage */
 } orc_mesh;
 
 static void face_verts(int dim, int q, int *fv) {
@@ -661,6 +675,8 @@ void orc_mesh_free(void *h) {
   free(m->es2);
   free(m->shalf);
   free(m->col);
+  free(m->bck);
+  free(m->bcs);
   free(m);
 }
 
@@ -1197,6 +1213,97 @@ static void num_flux(const orc_phys *ph, const real *Um, const real *Up, const r
   }
 }
 
+/* Boundary kinds and the state U+ outside a boundary face at the physical
+ * point x (readings: Sec. 5 runs the double Mach reflection of [giuliani],
+ * whose boundaries are slip walls, inflow states and the moving incident
+ * shock; the paper states none of them):
+ *   transmissive: U+ = U-;
+ *   wall (slip): U+ = U- with its normal momentum reversed, m+ = m- - 2 (m-.n) n
+ *     (so the Lax-Friedrichs flux carries no mass and no energy through it);
+ *   state: U+ = the face's prescribed state;
+ *   shock: a planar shock whose trace moves along x: U+ = the state behind it
+ *     where x < a + b y + c t, else the state ahead of it. */
+enum { ORC_BC_TRANSMISSIVE = 0, ORC_BC_WALL = 1, ORC_BC_STATE = 2, ORC_BC_SHOCK = 3 };
+
+static void bc_state(const orc_mesh *m, int32_t s, int M, const real *Um, const real *n, const real *x,
+                     real *Up) {
+  const int kind = m->bck ? m->bck[s] : ORC_BC_TRANSMISSIVE;
+  if (kind == ORC_BC_WALL) {
+    real mn = 0.0;
+    for (int a = 0; a < m->dim; ++a) mn += Um[1 + a] * n[a];
+    Up[0] = Um[0];
+    for (int a = 0; a < m->dim; ++a) Up[1 + a] = Um[1 + a] - 2.0 * mn * n[a];
+    Up[M - 1] = Um[M - 1];
+  } else if (kind == ORC_BC_STATE) {
+    for (int k = 0; k < M; ++k) Up[k] = m->bcst[m->bcs[s]][k];
+  } else if (kind == ORC_BC_SHOCK) {
+    const real xs = m->shock[0] + m->shock[1] * x[1] + m->shock[2] * m->time;
+    const real *S = m->bcst[m->shock_st[x[0] < xs ? 0 : 1]];
+    for (int k = 0; k < M; ++k) Up[k] = S[k];
+  } else {
+    for (int k = 0; k < M; ++k) Up[k] = Um[k];
+  }
+}
+
+/* exported for the boundary pins: U+ of boundary side s at point x, with the
+ * side's outward unit normal n (that of its element) */
+int orc_boundary_state(void *h, int32_t s, const real *Um, const real *n, const real *x, real *Up) {
+  const orc_mesh *m = (const orc_mesh *)h;
+  if (s < 0 || s >= m->ns || m->sr[s] >= 0) return fail("boundary_state: not a boundary side");
+  bc_state(m, s, m->dim + 2, Um, n, x, Up);
+  return 0;
+}
+
+/* Boundary conditions of a triangle mesh: kind[s] (ORC_BC_*) for every side s
+ * with r = -1 (entries of interior sides are ignored), sidx[s] the state of an
+ * ORC_BC_STATE side, states [nstates][4], shock = (a, b, c) and shock_st = (the
+ * states behind and ahead) of ORC_BC_SHOCK sides (either may be NULL when no
+ * side is of that kind). */
+int orc_set_bc(void *h, const int8_t *kind, const int8_t *sidx, int nstates, const real *states,
+               const real *shock, const int8_t *shock_st) {
+  orc_mesh *m = (orc_mesh *)h;
+  if (m->dim != 2 || m->quad) return fail("set_bc: triangle meshes only");
+  if (nstates < 0 || nstates > ORC_MAXBCS) return fail("set_bc: state count out of range");
+  for (int64_t s = 0; s < m->ns; ++s) {
+    if (m->sr[s] >= 0) continue;
+    if (kind[s] < 0 || kind[s] > ORC_BC_SHOCK) return fail("set_bc: unknown boundary kind");
+    if (kind[s] == ORC_BC_STATE && (!sidx || sidx[s] < 0 || sidx[s] >= nstates))
+      return fail("set_bc: state index out of range");
+    if (kind[s] == ORC_BC_SHOCK && (!shock || !shock_st || shock_st[0] < 0 || shock_st[0] >= nstates ||
+                                    shock_st[1] < 0 || shock_st[1] >= nstates))
+      return fail("set_bc: shock states out of range");
+  }
+  if (!m->bck) {
+    m->bck = (int8_t *)calloc((size_t)(m->ns > 0 ? m->ns : 1), 1);
+    m->bcs = (int8_t *)calloc((size_t)(m->ns > 0 ? m->ns : 1), 1);
+  }
+  for (int64_t s = 0; s < m->ns; ++s) {
+    m->bck[s] = m->sr[s] >= 0 ? 0 : kind[s];
+    m->bcs[s] = m->sr[s] >= 0 || !sidx ? 0 : sidx[s];
+  }
+  for (int i = 0; i < nstates; ++i)
+    for (int k = 0; k < 4; ++k) m->bcst[i][k] = states[i * 4 + k];
+  for (int a = 0; a < 3; ++a) m->shock[a] = shock ? shock[a] : 0.0;
+  m->shock_st[0] = shock_st ? shock_st[0] : 0;
+  m->shock_st[1] = shock_st ? shock_st[1] : 0;
+  return 0;
+}
+
+int orc_set_time(void *h, real t) {
+  ((orc_mesh *)h)->time = t;
+  return 0;
+}
+int orc_get_time(void *h, real *t) {
+  *t = ((orc_mesh *)h)->time;
+  return 0;
+}
+int orc_set_limiter(void *h, int on) {
+  orc_mesh *m = (orc_mesh *)h;
+  if (on && (m->dim != 2 || m->quad)) return fail("set_limiter: triangle meshes only");
+  m->limit = on != 0;
+  return 0;
+}
+
 /* exported for the flux pins */
 int orc_lf_flux(int dim, const real *Um, const real *Up, const real *n, real *Fs) {
   orc_phys ph = {ORC_EULER, dim, dim + 2, {0, 0, 0}};
@@ -1525,8 +1632,8 @@ static void face_points_of_left(const orc_mesh *m, int64_t e, int32_t s, const o
  * nelem < 0; then rhs is [E][M][Np], else [nelem][M][Np] in list order).
  * c is [E][M][Np] in original element order.  kind 0 = Euler, 1 = linear
  * advection with velocity adv.  nq_face1 / nq_vol1 override the 1-D point
- * counts (0 = defaults).  Boundary faces use the transmissive state U+ = U-
- * (reading; the configurations are periodic). */
+ * counts (0 = defaults).  Boundary faces take U+ from bc_state: the
+ * transmissive state U+ = U- unless orc_set_bc gave the face another kind. */
 int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
             const int64_t *elems, int64_t nelem, int nq_face1, int nq_vol1) {
   orc_mesh *m = (orc_mesh *)h;
@@ -1534,6 +1641,7 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
   if (p < 0 || p > ORC_MAXP) return fail("rhs: p out of range");
   int Np = npoly_m(m, p);
   orc_phys ph = {kind, dim, kind == ORC_EULER ? dim + 2 : 1, {0, 0, 0}};
+  if (m->bck && kind != ORC_EULER) return fail("rhs: boundary conditions are for the Euler system");
   if (adv)
     for (int a = 0; a < dim; ++a) ph.adv[a] = adv[a];
   int M = ph.M;
@@ -1619,7 +1727,7 @@ int orc_rhs(void *h, int p, int kind, const real *adv, const real *c, real *rhs,
           ref_coords(m, nb, F.x + 3 * q, rn);
           eval_state_e(m, nb, p, M, Np, c + (int64_t)nb * M * Np, rn, Up);
         } else {
-          for (int k = 0; k < M; ++k) Up[k] = Um[k];
+          bc_state(m, s, M, Um, F.n, F.x + 3 * q, Up);
         }
         num_flux(&ph, Um, Up, F.n, Fs);
         basis_eval_e(m, e, p, rs, phi, NULL, NULL, NULL);
@@ -1656,6 +1764,71 @@ int orc_set_threads(int n) {
   (void)n;
   return 1;
 #endif
+}
+
+/* ======================================================================= */
+/* Limiter (reading: the paper's solver takes its limiter from [giuliani])  */
+/* ======================================================================= */
+/* The Barth-Jespersen limiter on the conserved variables, one variable at a
+ * time.  On element e with mean u_e (its mode-0 coefficient times phi_0):
+ * u_min, u_max = the least and greatest of u_e and the means of the elements
+ * across its faces (both halves of a split face); d_i = u(x_i) - u_e =
+ * sum_{j>=1} c_j phi_j(x_i) at the element's vertices and volume points; then
+ *   alpha = min(1, min over d_i > 0 of (u_max - u_e) / d_i,
+ *                  min over d_i < 0 of (u_min - u_e) / d_i)
+ * and every mode j >= 1 is multiplied by alpha.  The means never change, so the
+ * result does not depend on the order the elements are visited in; at p = 1 the
+ * limited polynomial lies within [u_min, u_max] on the whole element (a linear
+ * function takes its extremes at the vertices). */
+int orc_limit(void *h, int p, real *c) {
+  orc_mesh *m = (orc_mesh *)h;
+  if (m->dim != 2 || m->quad) return fail("limit: triangle meshes only");
+  if (p < 1 || p > ORC_MAXP) return fail("limit: p out of range");
+  const int M = 4, Np = npoly_tri(p);
+  orc_rules R;
+  if (rules_make(2, 0, 1, default_vol_n1(2, p), &R)) {
+    rules_free(&R);
+    return -1;
+  }
+  const int npt = 3 + R.nv;
+  real *phi = (real *)malloc(sizeof(real) * npt * Np), *mean = (real *)malloc(sizeof(real) * m->ne * M);
+  for (int i = 0; i < npt; ++i) {
+    real x[3] = {i == 1 ? 1.0 : 0.0, i == 2 ? 1.0 : 0.0, 0.0};
+    if (i >= 3) x[0] = R.vr[i - 3], x[1] = R.vs[i - 3];
+    basis_eval(m, p, x, phi + i * Np, NULL, NULL, NULL);
+  }
+  const real phi0 = phi[0];
+  for (int64_t e = 0; e < m->ne; ++e)
+    for (int k = 0; k < M; ++k) mean[e * M + k] = c[(e * M + k) * Np] * phi0;
+  for (int64_t e = 0; e < m->ne; ++e) {
+    for (int k = 0; k < M; ++k) {
+      const real ue = mean[e * M + k];
+      real lo = ue, hi = ue;
+      for (int sub = 0; sub < 2 * m->nfpe; ++sub) {
+        const int f = sub % m->nfpe;
+        const int32_t s = sub < m->nfpe ? m->es[e * m->nfpe + f] : (m->es2 ? m->es2[e * m->nfpe + f] : -1);
+        if (s < 0) continue;
+        const int32_t nb = m->sl[s] == e ? m->sr[s] : m->sl[s];
+        if (nb < 0) continue;
+        const real v = mean[(int64_t)nb * M + k];
+        if (v < lo) lo = v;
+        if (v > hi) hi = v;
+      }
+      real *ce = c + (e * M + k) * Np;
+      real alpha = 1.0;
+      for (int i = 0; i < npt; ++i) {
+        real d = 0.0;
+        for (int j = 1; j < Np; ++j) d += ce[j] * phi[i * Np + j];
+        if (d > 0.0 && (hi - ue) / d < alpha) alpha = (hi - ue) / d;
+        if (d < 0.0 && (lo - ue) / d < alpha) alpha = (lo - ue) / d;
+      }
+      for (int j = 1; j < Np; ++j) ce[j] *= alpha;
+    }
+  }
+  free(phi);
+  free(mean);
+  rules_free(&R);
+  return 0;
 }
 
 /* ======================================================================= */
@@ -1715,7 +1888,10 @@ int orc_dt(void *h, int p, const real *c, real cfl, real *dt_out) {
  *   u  = 1/3 u + 2/3 (u2 + dt L(u2)),
  * with L the right-hand side of Eq. 2 for the flux kind (ORC_EULER, or
  * ORC_ADVECTION with velocity adv and one equation).  dt comes from the
- * state at the start of the step (Euler only), or is dt_in when > 0. */
+ * state at the start of the step (Euler only), or is dt_in when > 0.  The
+ * stages take their boundary states at t, t + dt and t + dt/2 (t the mesh's
+ * time, advanced by dt), and with the limiter on (orc_set_limiter) each stage's
+ * result is limited (orc_limit) before the next stage reads it. */
 int orc_rk_step_kind(void *h, int p, int kind, const real *adv, real *c, real cfl, real dt_in,
                      real *dt_out) {
   orc_mesh *m = (orc_mesh *)h;
@@ -1728,12 +1904,22 @@ int orc_rk_step_kind(void *h, int p, int kind, const real *adv, real *c, real cf
   }
   real *u1 = (real *)malloc(sizeof(real) * n), *u2 = (real *)malloc(sizeof(real) * n);
   real *L = (real *)malloc(sizeof(real) * n);
+  /* stage times t, t + dt, t + dt/2 (for time-dependent boundary states); the
+   * limiter, when on, after every stage */
+  const real t0 = m->time;
+  const int lim = m->limit && kind == ORC_EULER;
   int rc = orc_rhs(h, p, kind, adv, c, L, NULL, -1, 0, 0);
   for (int64_t i = 0; i < n && !rc; ++i) u1[i] = c[i] + dt * L[i];
+  if (!rc && lim) rc = orc_limit(h, p, u1);
+  m->time = t0 + dt;
   if (!rc) rc = orc_rhs(h, p, kind, adv, u1, L, NULL, -1, 0, 0);
   for (int64_t i = 0; i < n && !rc; ++i) u2[i] = 0.75 * c[i] + 0.25 * (u1[i] + dt * L[i]);
+  if (!rc && lim) rc = orc_limit(h, p, u2);
+  m->time = t0 + 0.5 * dt;
   if (!rc) rc = orc_rhs(h, p, kind, adv, u2, L, NULL, -1, 0, 0);
   for (int64_t i = 0; i < n && !rc; ++i) c[i] = c[i] / 3.0 + (real)2 / 3 * (u2[i] + dt * L[i]);
+  if (!rc && lim) rc = orc_limit(h, p, c);
+  m->time = t0 + dt;
   free(u1);
   free(u2);
   free(L);

@@ -121,6 +121,33 @@ def open_square_tri(n: int, jitter: float = 0.0, seed: int | None = None) -> Mes
     return MeshInput(2, xyz, ev, None, name=f"open_square_tri_{n}x{n}", meta={"n": n})
 
 
+def open_rect_tri(nx: int, ny: int, lx: float, ly: float, jitter: float = 0.0,
+                  seed: int | None = None) -> MeshInput:
+    """Non-periodic ``nx x ny`` rectangle [0, lx] x [0, ly] of cells split into
+    two triangles each as in ``open_square_tri``; only interior vertices are
+    jittered (by ``U(-jitter h, jitter h)`` per axis, h the cell size along that
+    axis), so the four sides stay straight."""
+    hx, hy = lx / nx, ly / ny
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    xyz = np.stack([ii.ravel() * hx, jj.ravel() * hy], axis=1).astype(np.float64)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        d = rng.uniform(-jitter, jitter, size=xyz.shape) * np.array([hx, hy])
+        interior = (ii.ravel() > 0) & (ii.ravel() < nx) & (jj.ravel() > 0) & (jj.ravel() < ny)
+        xyz[interior] += d[interior]
+    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    i, j = ci.ravel(), cj.ravel()
+
+    def vid(i, j):
+        return j * (nx + 1) + i
+
+    a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+    ev = np.empty((2 * nx * ny, 3), dtype=np.int32)
+    ev[0::2] = np.stack([a, b, c], axis=1)
+    ev[1::2] = np.stack([a, c, d], axis=1)
+    return MeshInput(2, xyz, ev, None, name=f"open_rect_tri_{nx}x{ny}", meta={"nx": nx, "ny": ny})
+
+
 def _quad_grid(n: int, periodic: bool, mode: str, jitter: float, slant: float, seed):
     nn = n if periodic else n + 1
     h = 1.0 / n
@@ -424,6 +451,71 @@ def bilinear_square_vortex_p3_512(n: int = 512) -> dict:
     vortex strength 5."""
     mi = periodic_square_quad(n, "vertex", 0.2, seed=9)
     return dict(mesh=mi, p=3, beta=5.0, cfl=0.3)
+
+
+# ---------------------------------------------------------------------------
+# Double Mach reflection (Sec. 5 times Table 7 on it: mesh D, 627,326 triangles,
+# p = 1, 1000 steps; the setup is [giuliani]'s and not in the paper; this is the
+# standard one of Woodward and Colella): a Mach 10 shock in air (gamma = 1.4)
+# at 60 degrees to a reflecting wall y = 0, x >= 1/6, on [0, 4] x [0, 1].
+# ---------------------------------------------------------------------------
+BC_TRANSMISSIVE, BC_WALL, BC_STATE, BC_SHOCK = 0, 1, 2, 3
+DMR_SHOCK = (1.0 / 6.0, 1.0 / np.sqrt(3.0), 20.0 / np.sqrt(3.0))  # x_s = a + b y + c t
+
+
+def _conserved(rho, u, v, p, gamma=1.4):
+    return np.array([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def double_mach_states() -> np.ndarray:
+    """[2][4] conserved states: 0 behind the shock (rho 8, p 116.5, speed 8.25
+    at -30 degrees), 1 ahead of it (rho 1.4, p 1, at rest)."""
+    return np.stack([_conserved(8.0, 8.25 * np.cos(np.pi / 6), -8.25 * np.sin(np.pi / 6), 116.5),
+                     _conserved(1.4, 0.0, 0.0, 1.0)])
+
+
+def double_mach_field(x: np.ndarray, y: np.ndarray, t: float = 0.0) -> np.ndarray:
+    """The shock's two states on either side of x_s(y, t): [..., 4]."""
+    S = double_mach_states()
+    a, b, c = DMR_SHOCK
+    behind = x < a + b * y + c * t
+    return np.where(behind[..., None], S[0], S[1])
+
+
+def double_mach_boundary(mi: MeshInput, left: np.ndarray, right: np.ndarray, qleft: np.ndarray):
+    """Boundary kind and state index per side (sides as both the library and the
+    oracle list them: left/right element, local face of the left), from each
+    boundary face's midpoint: the bottom up to x = 1/6 and the left side take
+    the state behind the shock, the bottom beyond it is a slip wall, the top
+    follows the moving shock (states 0 behind, 1 ahead), the right side is
+    transmissive."""
+    kind = np.zeros(left.size, np.int8)
+    sidx = np.zeros(left.size, np.int8)
+    b = np.nonzero(right < 0)[0]
+    v0 = mi.ev[left[b], qleft[b]]
+    v1 = mi.ev[left[b], (qleft[b] + 1) % 3]
+    mid = 0.5 * (mi.xyz[v0] + mi.xyz[v1])
+    lx = mi.xyz[:, 0].max()
+    ly = mi.xyz[:, 1].max()
+    tol = 1e-9
+    k = np.full(b.size, BC_TRANSMISSIVE, np.int8)
+    bottom, top = mid[:, 1] < tol, mid[:, 1] > ly - tol
+    leftb, rightb = mid[:, 0] < tol, mid[:, 0] > lx - tol
+    k[bottom & (mid[:, 0] < DMR_SHOCK[0])] = BC_STATE
+    k[bottom & (mid[:, 0] >= DMR_SHOCK[0])] = BC_WALL
+    k[top] = BC_SHOCK
+    k[leftb & ~bottom & ~top] = BC_STATE
+    k[rightb & ~bottom & ~top] = BC_TRANSMISSIVE
+    kind[b] = k
+    return kind, sidx
+
+
+def double_mach_p1(ny: int = 280) -> dict:
+    """The double Mach workload: [0, 4] x [0, 1] as 4 ny x ny cells of two
+    jittered triangles (627,200 at ny = 280, mesh D's size), p = 1, the shock
+    states of ``double_mach_states`` at t = 0, CFL 0.3, the limiter on."""
+    mi = open_rect_tri(4 * ny, ny, 4.0, 1.0, jitter=0.2, seed=482)
+    return dict(mesh=mi, p=1, cfl=0.3, states=double_mach_states(), shock=DMR_SHOCK, shock_states=(0, 1))
 
 
 def batched_square_meshes(count: int = 64, seed: int = 5, e_min: float = 1e3,
