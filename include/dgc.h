@@ -96,12 +96,65 @@ typedef enum {
                                    then each further color) separated by grid-wide barriers
                                    instead of kernel boundaries; 0 (default): one launch per
                                    phase.  Results are identical. */
-  DGC_OPT_PERSISTENT = 7        /* triangle meshes: 1 launches each color's surface kernel with at
+  DGC_OPT_PERSISTENT = 7,       /* triangle meshes: 1 launches each color's surface kernel with at
                                    most one wave of blocks, every warp looping over the color in
                                    steps of the whole grid (no partly filled last wave); 0
                                    (default): one block per tile of edges.  Results are
                                    identical. */
+  DGC_OPT_LIMITER = 8           /* conforming triangle meshes, FP64: 1 applies the limiter of
+                                   dgc_limit after every stage of dgc_rk_step (and of
+                                   dgc_rk_step_static); 0 (default): no limiter.  The FP32 forms
+                                   refuse a mesh with the limiter on (DGC_ERR_UNSUPPORTED). */
 } dgc_option;
+
+/* Boundary kinds of dgc_set_boundary. */
+typedef enum {
+  DGC_BC_TRANSMISSIVE = 0,  /* U+ = U- (the default of every boundary face) */
+  DGC_BC_WALL = 1,          /* slip wall: U+ = U- with the normal momentum reversed */
+  DGC_BC_STATE = 2,         /* U+ = a prescribed state */
+  DGC_BC_SHOCK = 3          /* a moving planar shock: the state behind it where x < a + b y + c t */
+} dgc_bc;
+
+/* Boundary conditions of a conforming triangle mesh (Sec. 5 runs the double Mach
+ * reflection problem of its reference [giuliani] for Table 7; the paper states
+ * neither its boundary conditions nor its limiter, and this library's are
+ * readings: a slip wall, prescribed inflow states and the moving incident shock
+ * on the top boundary, the standard setup of that problem).  kind[s] and
+ * state_idx[s] are given per side in the original side order of dgc_get_sides;
+ * entries of interior sides are ignored.  At a boundary face the numerical flux
+ * takes U- from the element and U+ from its kind: DGC_BC_TRANSMISSIVE U+ = U-;
+ * DGC_BC_WALL U+ = (rho, m - 2 (m.n) n, E) with n the element's outward unit
+ * normal (no mass or energy crosses the face); DGC_BC_STATE U+ =
+ * states[state_idx[s]]; DGC_BC_SHOCK U+ = states[shock_states[0]] where
+ * x < shock[0] + shock[1] y + shock[2] t at the face's quadrature point x,
+ * else states[shock_states[1]], with t the mesh's time (dgc_set_time; each
+ * stage of dgc_rk_step takes t, t + dt, t + dt/2 and the step advances it by
+ * dt, on the device).  states: nstates (<= 8) conserved states of 4 doubles;
+ * shock and shock_states may be NULL when no face is DGC_BC_SHOCK.  Host
+ * arrays, copied.  The kernels that honour boundary conditions are the FP64
+ * ones (dgc_rhs, dgc_rk_step, dgc_rk_step_static, the comparators); the FP32
+ * forms, cooperative dgc_rhs and batches refuse a mesh with boundary
+ * conditions other than transmissive, and so do dgc_refine and quadrilateral,
+ * hybrid and tetrahedral meshes (DGC_ERR_UNSUPPORTED).  DGC_ERR_ARG on a bad
+ * kind, state index or count. */
+dgc_status dgc_set_boundary(dgc_mesh* mesh, const int8_t* kind, const int8_t* state_idx, int nstates,
+                            const double* states, const double* shock, const int8_t* shock_states);
+
+/* The mesh's time, which time-dependent boundary states (DGC_BC_SHOCK) are taken
+ * at.  dgc_set_time sets it (0 at creation); dgc_get_time reads the device copy
+ * back (synchronising with the device; the host value before the first upload). */
+dgc_status dgc_set_time(dgc_mesh* mesh, double t);
+dgc_status dgc_get_time(dgc_mesh* mesh, double* t);
+
+/* The limiter, once, in place on an FP64 state c_dev of a conforming triangle mesh
+ * (reading: the paper takes its limiter from [giuliani]; this is the
+ * Barth-Jespersen limiter on the conserved variables): per element and variable,
+ * with u_e the element's mean and u_min, u_max the least and greatest of u_e and
+ * its face neighbours' means, every mode j >= 1 is multiplied by the largest
+ * alpha in [0, 1] that keeps u_e + alpha (u(x_i) - u_e) within [u_min, u_max] at
+ * the element's vertices and volume quadrature points.  Means are unchanged.
+ * DGC_OPT_LIMITER applies it after every RK stage.  prec must be DGC_FP64. */
+dgc_status dgc_limit(dgc_mesh* mesh, dgc_prec prec, double* c_dev, void* stream);
 
 /* Kernel classes reported by dgc_profile_collect. */
 typedef enum {

@@ -1,6 +1,7 @@
 // C ABI of the library (include/dgc.h): argument checks, device upload of the
 // renumbered mesh, and the launch sequences of Algorithm 1 and SSP-RK3.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -275,6 +276,7 @@ void upload(Mesh& m) {
   std::vector<double2> fgeo((size_t)m.ns * gstride);
   const int slot_w = m.refined ? 2 * nfpe : nfpe;
   std::vector<int32_t> slots((size_t)m.ne * slot_w, -1);
+  std::vector<double4> bgeo;  // boundary conditions: per boundary face its first vertex and edge vector
   for (int64_t k = 0; k < m.ns; ++k) {
     int64_t old = m.side_old_of_new[k];
     int32_t l = m.sl[old], r = m.sr[old];
@@ -298,7 +300,15 @@ void upload(Mesh& m) {
         if (kFacePerms[o][0] == perm[0] && kFacePerms[o][1] == perm[1] && kFacePerms[o][2] == perm[2]) orient = o;
       if (orient < 0) throw Error{DGC_ERR_MESH, "face vertices of the two sides do not match"};
     }
-    topo[k] = make_int4(en[l], r >= 0 ? en[r] : -1, ql | (qr << 4) | (orient << 8), 0);
+    int bw = 0;  // boundary conditions: kind | state << 4 | boundary face << 8
+    if (m.has_bc && r < 0) {
+      bw = m.bc_kind[old] | (m.bc_sidx[old] << 4) | ((int)bgeo.size() << 8);
+      const double* X = &m.X[(size_t)l * 6];
+      const double* A = X + 2 * ql;
+      const double* B = X + 2 * ((ql + 1) % 3);
+      bgeo.push_back(make_double4(A[0], A[1], B[0] - A[0], B[1] - A[1]));
+    }
+    topo[k] = make_int4(en[l], r >= 0 ? en[r] : -1, ql | (qr << 4) | (orient << 8), bw);
     double meas = m.smeas[old];
     // |f| / detJ per side (a bilinear element's detJ varies: its mass matrix is
     // applied after the colors instead, so its factor is |f|)
@@ -342,6 +352,37 @@ void upload(Mesh& m) {
     if (m.quad) quad_upload_tables(m.p, m.tab);
     if (m.refined) upload_transfer(m, *d);
     if (m.hybrid) upload_hybrid(m, *d);
+    if (m.has_bc) {
+      std::vector<double> blk(kBcDoubles, 0.0);
+      std::copy(m.bc_states.begin(), m.bc_states.end(), blk.begin() + kBcStates);
+      for (int a = 0; a < 3; ++a) blk[kBcShock + a] = m.shock[a];
+      blk[kBcShock + 3] = m.shock_st[0];
+      blk[kBcShock + 4] = m.shock_st[1];
+      d->bc = dalloc<double>(kBcDoubles);
+      DGC_CUDA(cudaMemcpy(d->bc, blk.data(), sizeof(double) * blk.size(), cudaMemcpyHostToDevice));
+      d->bgeo = dalloc<double4>(std::max<int64_t>(1, (int64_t)bgeo.size()));
+      if (!bgeo.empty())
+        DGC_CUDA(cudaMemcpy(d->bgeo, bgeo.data(), sizeof(double4) * bgeo.size(), cudaMemcpyHostToDevice));
+    }
+    if (dim == 2 && !m.quad) {
+      // the mesh's time (boundary states) and the limiter's face neighbours
+      d->time = dalloc<double>(1);
+      DGC_CUDA(cudaMemcpy(d->time, &m.time, sizeof(double), cudaMemcpyHostToDevice));
+      if (!m.refined && m.want_enb) {
+        std::vector<int4> enb(m.ne);
+        for (int64_t e = 0; e < m.ne; ++e) {
+          int nb[3];
+          for (int f = 0; f < 3; ++f) {
+            const int32_t sd = m.face_of[(size_t)e * 3 + f];
+            const int32_t o = sd < 0 ? -1 : (m.sl[sd] == e ? m.sr[sd] : m.sl[sd]);
+            nb[f] = o < 0 ? -1 : en[o];
+          }
+          enb[en[e]] = make_int4(nb[0], nb[1], nb[2], 0);
+        }
+        d->enb = dalloc<int4>(m.ne);
+        DGC_CUDA(cudaMemcpy(d->enb, enb.data(), sizeof(int4) * enb.size(), cudaMemcpyHostToDevice));
+      }
+    }
   } catch (...) {
     m.dev = d.release();
     device_free(m);
@@ -530,6 +571,7 @@ int64_t launch_rhs(Mesh& m, const Ctx& x, TypeCfg ty, const void* state, int ss,
   int64_t n = 0;
   const std::vector<int32_t>& off = m.color_off;
   if (m.coop && m.dim == 2 && !m.quad && (ty == TY_D || ty == TY_MD)) {
+    require(!m.has_bc, "the cooperative right-hand side keeps transmissive boundaries", DGC_ERR_UNSUPPORTED);
     // every phase of Algorithm 1 in one cooperative launch
     run(m, x, DGC_K_COLOR, n, [&] {
       return tri_rhs_coop(x, ty, off.data(), m.ncolors, first_fused(m), unreached(m), state, rhs);
@@ -602,7 +644,12 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
     double* c64 = static_cast<double*>(c);
     launch(DGC_K_CFL, [&] { return cfl(x, c64, cfl_, dt, nullptr); });
     const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double TF[3] = {0.0, 1.0, 0.5};  // the stages' times, in units of dt from the step's start
     for (int s = 0; s < 3; ++s) {
+      Ctx xs_ = x;
+      xs_.tfrac = TF[s];
+      xs_.dtp = dt;
+      const Ctx& x = xs_;
       double* us = s == 0 ? c64 : w.u1;
       StageArgs sa;
       sa.u0 = c64;
@@ -627,7 +674,9 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
         launch(DGC_K_VOLUME, [&] { return mass(x, TY_D, w.rhs); });
         launch(DGC_K_STAGE, [&] { return stage_update(x, false, us, w.rhs, sa); });
       }
+      if (m.limit) launch(DGC_K_STAGE, [&] { return tri_limit(x, sa.uout); });
     }
+    if (m.has_bc) launch(DGC_K_STAGE, [&] { return time_advance(x, dt); });
     return;
   }
   // FP32 forms, increment form of the step (incr_form.cuh)
@@ -703,6 +752,14 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->bil_elem);
   cudaFree(m.dev->bil_G);
   cudaFree(m.dev->bil_Minv);
+  if (m.dev->time) {  // keep the time the steps advanced to
+    double t = m.time;
+    if (cudaMemcpy(&t, m.dev->time, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) m.time = t;
+  }
+  cudaFree(m.dev->bc);
+  cudaFree(m.dev->bgeo);
+  cudaFree(m.dev->time);
+  cudaFree(m.dev->enb);
   cudaFree(m.dev->xf_src);
   cudaFree(m.dev->xf_kind);
   cudaFree(m.dev->xf_kids);
@@ -839,6 +896,7 @@ dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems) {
     require(m.dim == 2 && !m.quad, "nonconforming refinement is implemented for triangle meshes",
             DGC_ERR_UNSUPPORTED);
     require(!m.refined, "the mesh is already refined (one level is supported)", DGC_ERR_UNSUPPORTED);
+    require(!m.has_bc && !m.limit, "refinement keeps transmissive boundaries and no limiter", DGC_ERR_UNSUPPORTED);
     require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
             "refine a mesh colored by dgc_color_edges with 3 colors");
     require(n >= 0 && (n == 0 || elems != nullptr), "bad element list");
@@ -901,6 +959,9 @@ static void require_prec(const Mesh& m, dgc_prec prec) {
   require(prec == DGC_FP64 || prec == DGC_FP32_MIXED || prec == DGC_FP32_KAHAN, "unknown precision");
   require(!m.hybrid || prec == DGC_FP64, "hybrid triangle/quadrilateral meshes run in FP64", DGC_ERR_UNSUPPORTED);
   require(prec != DGC_FP32_KAHAN || (m.dim == 2 && !m.quad), "the Kahan form is implemented for triangle meshes",
+          DGC_ERR_UNSUPPORTED);
+  require(prec == DGC_FP64 || (!m.has_bc && !m.limit),
+          "boundary conditions and the limiter run in FP64 (the FP32 forms keep transmissive boundaries)",
           DGC_ERR_UNSUPPORTED);
 }
 
@@ -1114,6 +1175,87 @@ dgc_status dgc_rhs(dgc_mesh* mesh, dgc_prec prec, const void* c_dev, double* rhs
     x.pdl = m.pdl;
     if (prec == DGC_FP32_KAHAN) finish(m, launch_rhs(m, x, TY_KD, c_dev, (int)kahan_floats(m), rhs_dev));
     else finish(m, launch_rhs(m, x, prec == DGC_FP64 ? TY_D : TY_MD, c_dev, 0, rhs_dev));
+  });
+}
+
+dgc_status dgc_set_boundary(dgc_mesh* mesh, const int8_t* kind, const int8_t* state_idx, int nstates,
+                            const double* states, const double* shock, const int8_t* shock_states) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(m.dim == 2 && !m.quad, "boundary conditions: triangle meshes only", DGC_ERR_UNSUPPORTED);
+    require(!m.refined, "boundary conditions: conforming meshes only", DGC_ERR_UNSUPPORTED);
+    require(kind != nullptr, "null kind array");
+    require(nstates >= 0 && nstates <= kBcMaxStates, "state count must be 0..8");
+    require(nstates == 0 || states != nullptr, "null states");
+    bool any = false, shock_used = false;
+    for (int64_t s = 0; s < m.ns; ++s) {
+      if (m.sr[s] >= 0) continue;
+      const int k = kind[s];
+      require(k >= DGC_BC_TRANSMISSIVE && k <= DGC_BC_SHOCK, "unknown boundary kind");
+      if (k == DGC_BC_STATE)
+        require(state_idx != nullptr && state_idx[s] >= 0 && state_idx[s] < nstates, "state index out of range");
+      shock_used |= k == DGC_BC_SHOCK;
+      any |= k != DGC_BC_TRANSMISSIVE;
+    }
+    if (shock_used)
+      require(shock != nullptr && shock_states != nullptr && shock_states[0] >= 0 && shock_states[0] < nstates &&
+                  shock_states[1] >= 0 && shock_states[1] < nstates,
+              "shock faces need the shock and its two states");
+    for (int i = 0; i < 4 * nstates; ++i) require(std::isfinite(states[i]), "states must be finite");
+    m.bc_kind.assign(m.ns, 0);
+    m.bc_sidx.assign(m.ns, 0);
+    for (int64_t s = 0; s < m.ns; ++s)
+      if (m.sr[s] < 0) {
+        m.bc_kind[s] = kind[s];
+        m.bc_sidx[s] = kind[s] == DGC_BC_STATE ? state_idx[s] : 0;
+      }
+    m.bc_states.assign(states, states + 4 * nstates);
+    for (int a = 0; a < 3; ++a) m.shock[a] = shock_used ? shock[a] : 0.0;
+    m.shock_st[0] = shock_used ? shock_states[0] : 0;
+    m.shock_st[1] = shock_used ? shock_states[1] : 0;
+    if (m.dev) {  // keep the device's time across the re-upload
+      double t = m.time;
+      if (m.dev->time) DGC_CUDA(cudaMemcpy(&t, m.dev->time, sizeof(double), cudaMemcpyDeviceToHost));
+      m.time = t;
+    }
+    m.has_bc = any;
+    m.dirty = true;
+  });
+}
+
+dgc_status dgc_set_time(dgc_mesh* mesh, double t) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(std::isfinite(t), "time must be finite");
+    m.time = t;
+    if (m.dev && m.dev->time) DGC_CUDA(cudaMemcpy(m.dev->time, &t, sizeof(double), cudaMemcpyHostToDevice));
+  });
+}
+
+dgc_status dgc_get_time(dgc_mesh* mesh, double* t) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(t != nullptr, "null output");
+    if (m.dev && m.dev->time) DGC_CUDA(cudaMemcpy(&m.time, m.dev->time, sizeof(double), cudaMemcpyDeviceToHost));
+    *t = m.time;
+  });
+}
+
+dgc_status dgc_limit(dgc_mesh* mesh, dgc_prec prec, double* c_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = checked(mesh);
+    require(prec == DGC_FP64, "the limiter runs on FP64 states", DGC_ERR_UNSUPPORTED);
+    require(m.dim == 2 && !m.quad && !m.refined, "the limiter: conforming triangle meshes only",
+            DGC_ERR_UNSUPPORTED);
+    check_ptr(c_dev, "c_dev");
+    if (!m.want_enb) {
+      m.want_enb = true;
+      if (m.dev) device_free(m);  // the next upload adds the face neighbours
+    }
+    Ctx x = ready(m, stream);
+    int64_t n = 0;
+    run(m, x, DGC_K_STAGE, n, [&] { return tri_limit(x, c_dev); });
+    finish(m, n);
   });
 }
 
@@ -1385,6 +1527,15 @@ dgc_status dgc_set_option(dgc_mesh* mesh, dgc_option opt, int64_t value) {
         require(value == 0 || (m.dim == 2 && !m.quad), "persistent surface kernels: triangle meshes only",
                 DGC_ERR_UNSUPPORTED);
         m.persistent = value != 0;
+        break;
+      case DGC_OPT_LIMITER:
+        require(value == 0 || (m.dim == 2 && !m.quad && !m.refined),
+                "the limiter: conforming triangle meshes only", DGC_ERR_UNSUPPORTED);
+        m.limit = value != 0;
+        if (m.limit && !m.want_enb) {
+          m.want_enb = true;
+          if (m.dev) device_free(m);  // the next upload adds the face neighbours
+        }
         break;
       case DGC_OPT_COOPERATIVE:
         require(value == 0 || (m.dim == 2 && !m.quad), "cooperative right-hand side: triangle meshes only",
@@ -1682,6 +1833,8 @@ dgc_status dgc_batch_create(int n, dgc_mesh* const* meshes, dgc_batch** out) {
     for (int i = 0; i < n; ++i) {
       Mesh& m = checked(meshes[i]);
       require(m.dim == 2 && !m.quad, "batches hold triangle meshes");
+      require(!m.has_bc && !m.limit, "batched meshes keep transmissive boundaries and no limiter",
+              DGC_ERR_UNSUPPORTED);
       require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
               "batched meshes must be colored with 3 colors, every element with one edge of each color");
       b->meshes.push_back(&m);

@@ -42,11 +42,24 @@ struct DeviceMesh {
   double* bil_G = nullptr;
   double* bil_Minv = nullptr;
   int64_t nbil = 0;
+  // boundary conditions (dgc_set_boundary; null: every boundary transmissive):
+  // the boundary block (kBc*), per boundary face (the index in topo.w >> 8) the
+  // left element's first vertex of the face and the edge vector (x0, y0, dx,
+  // dy), the time the boundary states are taken at (advanced by each RK step)
+  double* bc = nullptr;
+  double4* bgeo = nullptr;
+  double* time = nullptr;
+  // the limiter: per element its face neighbours (-1 on a boundary), internal ids
+  int4* enb = nullptr;
   int32_t* xf_src = nullptr;
   int8_t* xf_kind = nullptr;
   int32_t* xf_kids = nullptr;
   double* xf_P = nullptr;
 };
+
+// The boundary block: up to kBcMaxStates prescribed states [4] from kBcStates,
+// then the shock's a, b, c and its states behind and ahead (as doubles).
+constexpr int kBcMaxStates = 8, kBcStates = 0, kBcShock = 4 * kBcMaxStates, kBcDoubles = kBcShock + 8;
 
 // Surface-kernel modes (Algorithm 1 and the comparators of Sec. 1).
 enum SurfMode {
@@ -95,6 +108,10 @@ struct Ctx {
   const DeviceMesh* d = nullptr;
   cudaStream_t st = nullptr;
   bool pdl = false;  // launch the surface and CFL kernels with programmatic dependent launch
+  // the time boundary states are taken at: the mesh's time + tfrac * (*dtp)
+  // (the RK stages: 0, 1, 1/2 of the step's dt; dtp null: the mesh's time)
+  double tfrac = 0.0;
+  const double* dtp = nullptr;
 };
 
 // A kernel launch on x.st with smem bytes of dynamic shared memory; with x.pdl,
@@ -185,6 +202,10 @@ int tri_rhs_coop(const Ctx& x, TypeCfg ty, const int* off, int ncolors, bool fus
 int tri_surface(const Ctx& c, TypeCfg ty, SurfMode mode, int64_t begin, int64_t end, const void* state,
                 int sstride, void* rhs, void* buf, const StageArgs* sa);
 int tri_cfl(const Ctx& c, const double* state, double cfl, double* dt, float* shadow);
+// the limiter on an FP64 triangle state, in place (kernels_tri.cu k_limit_tri)
+int tri_limit(const Ctx& x, double* c);
+// the mesh's device time += *dt (meshes with boundary conditions)
+int time_advance(const Ctx& x, const double* dt);
 // stage 0 of the mixed step on perfectly colored meshes: the first color also
 // writes the record of u0 and the CFL estimates (pass 1); pass 2 alone
 int tri_first_est(const Ctx& c, int64_t begin, int64_t end, const double* state, float* rec0, float* rhs);

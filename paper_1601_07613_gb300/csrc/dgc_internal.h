@@ -20,6 +20,7 @@ struct RefTables {
   std::vector<double> phiV;            // [nqv][np]
   std::vector<double> dphiV;           // [dim][nqv][np]
   std::vector<double> fw;              // [nqf] face weights
+  std::vector<double> ft;              // 2D: [nqf] edge points' parameters in [0, 1] from the edge's first vertex
   std::vector<double> phiF;            // [nfaces][nqf][np], face points in face parameters
   // triangles: phi_j on half h of local edge f, at edge parameter (h + t_q) / 2,
   // [nfaces][2][nqf][np] (the coarse side of a hanging edge, Sec. 3.2)
@@ -32,6 +33,8 @@ struct RefTables {
   // points are (x_i, x_k)): l_a(x_i) and l_a'(x_i), [p+1][p+1], and weights
   // summing to 1, [p+1]
   std::vector<double> vleg, vdleg, vw1;
+  // triangles: phi_j at the vertices (0,0), (1,0), (0,1), [3][np] (the limiter)
+  std::vector<double> phiX;
 };
 
 // Builds the tables (quadrature + orthonormal basis) for triangles (dim 2),
@@ -122,6 +125,20 @@ struct Mesh {
   bool pdl = true;  // programmatic dependent launch of the RK step's kernels
   bool coop = false;  // dgc_rhs of triangle meshes as one cooperative launch
   bool persistent = false;  // triangle surface kernels: one wave of blocks, grid-stride over the color
+  // boundary conditions (dgc_set_boundary; triangle meshes, FP64): per side in
+  // original order its kind (DGC_BC_*) and state index, the states [n][4], the
+  // moving shock x_s = shock[0] + shock[1] y + shock[2] t between the states
+  // shock_st[0] (behind) and shock_st[1] (ahead); has_bc: any kind but
+  // transmissive; time: the time the boundary states are taken at (the device
+  // copy advances with the RK steps and is read back by dgc_get_time)
+  std::vector<int8_t> bc_kind, bc_sidx;
+  std::vector<double> bc_states;
+  double shock[3] = {0.0, 0.0, 0.0};
+  int shock_st[2] = {0, 0};
+  bool has_bc = false;
+  double time = 0.0;
+  bool limit = false;  // the limiter after every RK stage (DGC_OPT_LIMITER)
+  bool want_enb = false;  // the device keeps the limiter's face neighbours (set by its first use)
   void* prof = nullptr;  // event records (capi.cu)
   // device side
   DeviceMesh* dev = nullptr;

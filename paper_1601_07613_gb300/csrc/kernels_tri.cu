@@ -58,6 +58,8 @@ struct TriTab {
   // local edge f as [3 + 2 f + h] (the coarse side of a hanging edge)
   T phiE[9][TriDim<P>::NQE][TriDim<P>::NP];
   T wE[TriDim<P>::NQE];                      // edge weights, sum 1
+  T tE[TriDim<P>::NQE];                      // edge points' parameters in [0, 1] from the edge's first vertex
+  T phiX[3][TriDim<P>::NP];                  // phi_j at the vertices (0,0), (1,0), (0,1)
 };
 
 __constant__ TriTab<double, 1> cTriD1;
@@ -92,6 +94,9 @@ static void fill_tab(TriTab<T, P>& K, const RefTables& R) {
     for (int q = 0; q < D::NQE; ++q)
       for (int j = 0; j < D::NP; ++j) K.phiE[3 + t][q][j] = (T)R.phiH[(t * D::NQE + q) * D::NP + j];
   for (int q = 0; q < D::NQE; ++q) K.wE[q] = (T)R.fw[q];
+  for (int q = 0; q < D::NQE; ++q) K.tE[q] = (T)R.ft[q];
+  for (int v = 0; v < 3; ++v)
+    for (int j = 0; j < D::NP; ++j) K.phiX[v][j] = (T)R.phiX[v * D::NP + j];
 }
 
 template <int P>
@@ -499,6 +504,15 @@ struct SurfParams {
   float* est = nullptr;
   unsigned* estmin = nullptr;
   const double* inr = nullptr;
+  // boundary conditions (FP64 lanes; null: every boundary transmissive): the
+  // mesh's boundary block (kBc*), per boundary face its first vertex and edge
+  // vector, and the time t0 + tfrac * dt (dt on the device, or none) the
+  // boundary states are taken at
+  const double* bc = nullptr;
+  const double4* bgeo = nullptr;
+  const double* t0 = nullptr;
+  const double* dtp = nullptr;
+  double tfrac = 0.0;
 };
 
 // the contribution of one lane's element is in acc; write it as the mode asks
@@ -1286,6 +1300,33 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
 }
 
 
+// The state outside a boundary face at its edge point q, taken by the second
+// lane of the face's pair in place of its own trace (dgc_set_boundary; tp.w =
+// kind | state << 4 | boundary face << 8): a slip wall reverses the normal
+// momentum, a state face takes its prescribed state, a shock face the state
+// behind the moving shock where x < a + b y + c t, else the state ahead;
+// transmissive faces keep U (U+ = U-).
+__device__ __forceinline__ void bc_outside(const SurfParams& A, int w, double tq, double nx, double ny, double* U) {
+  const int kind = w & 15;
+  if (kind == DGC_BC_WALL) {
+    const double mn = U[1] * nx + U[2] * ny;
+    U[1] -= 2.0 * mn * nx;
+    U[2] -= 2.0 * mn * ny;
+  } else if (kind == DGC_BC_STATE || kind == DGC_BC_SHOCK) {
+    int s = (w >> 4) & 15;
+    if (kind == DGC_BC_SHOCK) {
+      const double4 g = A.bgeo[w >> 8];
+      const double x = g.x + tq * g.z, y = g.y + tq * g.w;
+      const double t = *A.t0 + (A.dtp ? A.tfrac * *A.dtp : 0.0);
+      const double* sh = A.bc + kBcShock;
+      s = x < sh[0] + sh[1] * y + sh[2] * t ? (int)sh[3] : (int)sh[4];
+    }
+    const double* S = A.bc + kBcStates + 4 * s;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) U[m] = S[m];
+  }
+}
+
 template <int P, typename CT, typename ST, typename RT, int MODE>
 __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
                                           const CT* sphi, const CT* sw) {
@@ -1327,6 +1368,8 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
         for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
         U[m] = s;
       }
+      // a boundary face's second lane holds the state outside it
+      if (bnd && side && A.bc) bc_outside(A, tp.w, tri_tab<double, P>().tE[q], nx, ny, U);
       // own side's normal flux and wave speed, then the partner's
       double Fo[4], Fp[4], wo;
       lf_side(U, nx, ny, Fo, wo);
@@ -1939,6 +1982,11 @@ int tri_surface(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t begin, int64_t 
   A.buf = buf;
   A.ntab = x.d->edge_tables;
   if (sa) A.sa = *sa;
+  A.bc = x.d->bc;
+  A.bgeo = x.d->bgeo;
+  A.t0 = x.d->time;
+  A.dtp = x.dtp;
+  A.tfrac = x.tfrac;
   switch (x.p) {
     case 1: return surf_p<1>(x, ty, mode, A);
     case 2: return surf_p<2>(x, ty, mode, A);
@@ -2126,6 +2174,79 @@ int tri_cfl(const Ctx& x, const double* s, double cfl, double* dt, float* shadow
       return 2;
     default: return -1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Limiter (after each RK stage of a limited step, or dgc_limit): the
+// Barth-Jespersen limiter on the conserved variables, one thread per element,
+// FP64.  Per variable: the element's mean u_e (mode 0 times phi_0) and the
+// least and greatest of it and its face neighbours' means bound the deviations
+// d_i = sum_{j>=1} c_j phi_j(x_i) at the element's vertices and volume points;
+// alpha = min(1, (u_max - u_e) / d_i for d_i > 0, (u_min - u_e) / d_i for
+// d_i < 0), and the modes j >= 1 are multiplied by alpha.  A thread writes
+// only its element's modes j >= 1 and reads only its neighbours' mode 0, so
+// the elements are independent and the state is limited in place.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_limit_tri(double* c, const int4* __restrict__ enb, int64_t ne) {
+  using D = TriDim<P>;
+  constexpr int NP = D::NP, NV = D::NV;
+  const TriTab<double, P>& K = tri_tab<double, P>();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double v[NV];
+  load_plain(c + e * NV, v);
+  const int4 nb = enb[e];
+  const int nbs[3] = {nb.x, nb.y, nb.z};
+  const double phi0 = K.phiX[0][0];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const double ue = v[m * NP] * phi0;
+    double lo = ue, hi = ue;
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      if (nbs[f] >= 0) {
+        const double u = c[(int64_t)nbs[f] * NV + m * NP] * phi0;
+        lo = fmin(lo, u);
+        hi = fmax(hi, u);
+      }
+    double alpha = 1.0;
+    for (int i = 0; i < 3 + D::NQV; ++i) {
+      const double* ph = i < 3 ? K.phiX[i] : K.phiV[i - 3];
+      double d = 0.0;
+#pragma unroll
+      for (int j = 1; j < NP; ++j) d += v[m * NP + j] * ph[j];
+      if (d > 0.0) alpha = fmin(alpha, (hi - ue) / d);
+      if (d < 0.0) alpha = fmin(alpha, (lo - ue) / d);
+    }
+#pragma unroll
+    for (int j = 1; j < NP; ++j) v[m * NP + j] *= alpha;
+  }
+  double* dst = c + e * NV;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (i % NP) dst[i] = v[i];
+}
+
+int tri_limit(const Ctx& x, double* c) {
+  if (x.ne <= 0) return 0;
+  if (!x.d->enb) return -1;
+  const unsigned grid = (unsigned)((x.ne + 127) / 128);
+  switch (x.p) {
+    case 1: k_limit_tri<1><<<grid, 128, 0, x.st>>>(c, x.d->enb, x.ne); return 1;
+    case 2: k_limit_tri<2><<<grid, 128, 0, x.st>>>(c, x.d->enb, x.ne); return 1;
+    case 3: k_limit_tri<3><<<grid, 128, 0, x.st>>>(c, x.d->enb, x.ne); return 1;
+    default: return -1;
+  }
+}
+
+// the mesh's time advanced by the step's dt, on the device (one thread)
+__global__ void k_time_advance(double* t, const double* dt) { *t += *dt; }
+
+int time_advance(const Ctx& x, const double* dt) {
+  if (!x.d->time) return 0;
+  k_time_advance<<<1, 1, 0, x.st>>>(x.d->time, dt);
+  return 1;
 }
 
 }  // namespace dgc

@@ -297,6 +297,7 @@ RefTables make_tables(int dim, int p, bool quad) {
       fa.push_back(0.5 * (1.0 + x[i]));
       fb.push_back(0.0);
       T.fw.push_back(0.5 * w[i]);
+      T.ft.push_back(fa.back());
     }
   } else {
     tet_rule(p + 2, T.vr, T.vs, T.vt, T.vw);
@@ -368,6 +369,12 @@ RefTables make_tables(int dim, int p, bool quad) {
     }
   }
   if (dim == 2) {
+    T.phiX.resize((size_t)3 * T.np);
+    for (int v = 0; v < 3; ++v) {
+      double x[3] = {kTriV[v][0], kTriV[v][1], 0.0};
+      basis_eval(dim, p, x, phi.data(), nullptr);
+      for (int j = 0; j < T.np; ++j) T.phiX[(size_t)v * T.np + j] = phi[j];
+    }
     T.phiH.resize((size_t)3 * 2 * T.nqf * T.np);
     for (int f = 0; f < 3; ++f)
       for (int h = 0; h < 2; ++h)

@@ -26,6 +26,8 @@ DGC_OPT_GRAPH = 4
 DGC_OPT_PDL = 5
 DGC_OPT_COOPERATIVE = 6
 DGC_OPT_PERSISTENT = 7
+DGC_OPT_LIMITER = 8
+DGC_BC_TRANSMISSIVE, DGC_BC_WALL, DGC_BC_STATE, DGC_BC_SHOCK = 0, 1, 2, 3  # dgc_bc
 DGC_TRI, DGC_QUAD, DGC_TET = 0, 1, 2  # dgc_elem
 KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
 
@@ -90,6 +92,11 @@ SIGNATURES = {
     "dgc_batch_launch_count": (C.c_int, [_P, _I64P]),
     "dgc_batch_profile_collect": (C.c_int, [_P, _DP, _I64P]),
     "dgc_batch_set_tile": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "dgc_set_boundary": (C.c_int, [_P, C.POINTER(C.c_int8), C.POINTER(C.c_int8), C.c_int, _DP, _DP,
+                                   C.POINTER(C.c_int8)]),
+    "dgc_set_time": (C.c_int, [_P, C.c_double]),
+    "dgc_get_time": (C.c_int, [_P, _DP]),
+    "dgc_limit": (C.c_int, [_P, C.c_int, _P, _P]),
     "dgc_batch_destroy": (None, [_P]),
     "dgc_destroy": (None, [_P]),
 }
@@ -326,6 +333,34 @@ def dgc_export_state_prec(mesh, prec: int, c_dev, out=None, stream=None):
 
 def dgc_rhs(mesh, prec: int, c_dev, rhs_dev, stream=None):
     _check(lib().dgc_rhs(mesh, prec, _dptr(c_dev), _dptr(rhs_dev), _stream(stream)))
+
+
+def dgc_set_boundary(mesh, kind, state_idx=None, states=None, shock=None, shock_states=None):
+    """kind[s], state_idx[s] per side in dgc_get_sides order; states [n][4]."""
+    k = np.ascontiguousarray(kind, dtype=np.int8)
+    si = None if state_idx is None else np.ascontiguousarray(state_idx, dtype=np.int8)
+    st = np.ascontiguousarray(np.zeros((0, 4)) if states is None else np.asarray(states, dtype=np.float64).reshape(-1, 4))
+    sh = None if shock is None else np.ascontiguousarray(shock, dtype=np.float64)
+    ss = None if shock_states is None else np.ascontiguousarray(shock_states, dtype=np.int8)
+    i8 = C.POINTER(C.c_int8)
+    _check(lib().dgc_set_boundary(mesh, k.ctypes.data_as(i8), si.ctypes.data_as(i8) if si is not None else None,
+                                  st.shape[0], st.ctypes.data_as(_DP) if st.size else None,
+                                  sh.ctypes.data_as(_DP) if sh is not None else None,
+                                  ss.ctypes.data_as(i8) if ss is not None else None))
+
+
+def dgc_set_time(mesh, t: float):
+    _check(lib().dgc_set_time(mesh, float(t)))
+
+
+def dgc_get_time(mesh) -> float:
+    t = C.c_double(0.0)
+    _check(lib().dgc_get_time(mesh, C.byref(t)))
+    return t.value
+
+
+def dgc_limit(mesh, prec: int, c_dev, stream=None):
+    _check(lib().dgc_limit(mesh, prec, _dptr(c_dev), _stream(stream)))
 
 
 def dgc_cfl_dt(mesh, c_dev, cfl: float, dt_dev, stream=None):

@@ -294,3 +294,43 @@ def test_buffer_sizes_are_checked_before_device_work(L):
         dgc.dgc_rhs_two_pass(m.h, dgc.DGC_FP64, 4096, 8192, 1 << 20, buffer_bytes=nb - 8, stream=0)
     assert e.value.status == 1 and "buffer" in str(e.value)
     m.close()
+
+
+def test_boundary_arguments_are_checked_on_the_host(L):
+    """dgc_set_boundary validates kinds, state indices and the shock before any
+    device work; quadrilateral meshes refuse it; the time round-trips on the
+    host before the first upload."""
+    mi = W.open_rect_tri(8, 2, 4.0, 1.0)
+    m = dgc.Mesh.from_input(mi, 1)
+    m.color(1)
+    l, r, ql, qr = dgc.dgc_get_sides(m.h)
+    kind, sidx = W.double_mach_boundary(mi, l, r, ql)
+    S = W.double_mach_states()
+    dgc.dgc_set_boundary(m.h, kind, sidx, S, W.DMR_SHOCK, (0, 1))
+    bad = kind.copy()
+    bad[np.nonzero(r < 0)[0][0]] = 7
+    for args in ((bad, sidx, S, W.DMR_SHOCK, (0, 1)),       # unknown kind
+                 (kind, sidx + 5, S, W.DMR_SHOCK, (0, 1)),  # state index out of range (state faces)
+                 (kind, sidx, S, None, None),               # shock faces without the shock
+                 (kind, sidx, S, W.DMR_SHOCK, (0, 2))):     # shock state out of range
+        with pytest.raises(dgc.DgcError) as e:
+            dgc.dgc_set_boundary(m.h, *args)
+        assert e.value.status == 1
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_set_boundary(m.h, kind, sidx, np.zeros((9, 4)), W.DMR_SHOCK, (0, 1))
+    assert e.value.status == 1
+    dgc.dgc_set_time(m.h, 0.125)
+    assert dgc.dgc_get_time(m.h) == 0.125
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rhs(m.h, dgc.DGC_FP32_MIXED, 4096, 8192, 0)
+    assert e.value.status == 4
+    m.close()
+    q = dgc.Mesh.from_input(W.open_square_quad(4), 1)
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_set_boundary(q.h, np.zeros(q.info["ns"], np.int8))
+    assert e.value.status == 4
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_set_option(q.h, dgc.DGC_OPT_LIMITER, 1)
+    assert e.value.status == 4
+    q.close()
+
