@@ -412,6 +412,7 @@ def run_dgc(args, rank, world, local_rank):
         variants.update(run_batched(dgc, torch, dev, stream, args))
         variants.update(run_other_meshes(dgc, torch, dev, stream, args))
         variants.update(run_table7(dgc, torch, dev, stream, args, cfg, c_host))
+        variants.update(run_double_mach(dgc, torch, dev, stream, args))
         variants["coloring_tables"] = run_coloring_tables(dgc)
 
     # ---- end to end through the C ABI with pinned host buffers -----------------------------
@@ -784,6 +785,93 @@ def run_table7(dgc, torch, dev, stream, args, cfg, c_base):
                                 "p": cfg["p"], "dofs": dofs, "rows": rows}}
 
 
+def run_double_mach(dgc, torch, dev, stream, args):
+    """The double Mach reflection run Table 7 times (Sec. 5; its setup is
+    [giuliani]'s, not the paper's: the standard Mach 10 problem on [0, 4] x
+    [0, 1]): 1120 x 280 cells of two jittered triangles (627,200 elements, mesh
+    D's size), p = 1, FP64, slip wall / inflow / moving-shock / outflow
+    boundaries and the limiter after every RK stage.  Times the limited RK step
+    (CUDA events over the paper's 1000 steps from the initial state), checks the
+    means stay physical, and repeats Table 7's ablation on this mesh with its
+    element list in a seeded random order (naive greedy 5 colors or the
+    modified coloring's 3, with and without the color-1 renumbering and the
+    left-ascending edge order; 200 steps each; pct = speed-up over the first row)."""
+    cfg = W.double_mach_p1()
+    p = cfg["p"]
+
+    def build(mi):
+        m = dgc.Mesh.from_input(mi, p)
+        l, r, ql, _ = dgc.dgc_get_sides(m.h)
+        kind, sidx = W.double_mach_boundary(mi, l, r, ql)
+        dgc.dgc_set_boundary(m.h, kind, sidx, cfg["states"], cfg["shock"], cfg["shock_states"])
+        dgc.dgc_set_option(m.h, dgc.DGC_OPT_LIMITER, 1)
+        xyz = dgc.dgc_vol_points(m.h)
+        return m, dgc.dgc_project(m.h, W.double_mach_field(xyz[..., 0], xyz[..., 1]))
+
+    out = {}
+    t0 = time.perf_counter()
+    m, c_host = build(cfg["mesh"])
+    m.color(1601)
+    prep = time.perf_counter() - t0
+    info = m.info
+    dofs = info["ne"] * info["M"] * info["np"]
+    c = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    ws = torch.empty(dgc.dgc_workspace_size(m.h, dgc.DGC_FP64) // 8 + 64, dtype=torch.float64, device=dev)
+    dgc.dgc_import_state(m.h, c_host, c)
+    dgc.dgc_limit(m.h, dgc.DGC_FP64, c)
+    dgc.dgc_set_time(m.h, 0.0)
+    fn = lambda: dgc.dgc_rk_step(m.h, dgc.DGC_FP64, c, cfg["cfl"], dt, ws)
+    ms = time_steps(torch, fn, 1000, stream)
+    t_end = dgc.dgc_get_time(m.h)
+    U = dgc.dgc_export_state(m.h, c)[:, :, 0] * np.sqrt(2.0)  # element means (phi_0 = sqrt 2)
+    # per kernel class from a profiled pass (event pairs around every launch)
+    dgc.dgc_set_option(m.h, dgc.DGC_OPT_PROFILE, 1)
+    dgc.dgc_profile_collect(m.h)
+    msp = time_steps(torch, fn, 50, stream)
+    prof = dgc.dgc_profile_collect(m.h)
+    dgc.dgc_set_option(m.h, dgc.DGC_OPT_PROFILE, 0)
+    kern = {cls: {"launches": nl, "ms_per_step": round(tms / 50, 4), "share": round(tms / (msp * 50), 3)}
+            for cls, (tms, nl) in prof.items()}
+    pr = 0.4 * (U[:, 3] - 0.5 * (U[:, 1] ** 2 + U[:, 2] ** 2) / U[:, 0])
+    out["run"] = {"elements": info["ne"], "p": p, "dofs": dofs, "colors": info["ncolors"], "steps": 1000,
+                  "ms_per_step": round(ms, 4), "s_1000_steps": round(ms, 3),
+                  "value": 3 * dofs / (ms * 1e-3), "unit": "DOF-RHS updates/s",
+                  "launches_per_step": dgc.dgc_last_launch_count(m.h), "t_end": t_end,
+                  "min_density": float(U[:, 0].min()), "min_pressure": float(pr.min()),
+                  "finite": bool(np.isfinite(U).all()), "host_prep_s": round(prep, 2),
+                  "profiled_ms_per_step": round(msp, 4), "kernels": kern}
+    m.close()
+    # Table 7 on this mesh, its elements in a seeded random order
+    mi = cfg["mesh"]
+    perm = np.random.default_rng(1601).permutation(mi.ne)
+    mp = W.MeshInput(2, mi.xyz, np.ascontiguousarray(mi.ev[perm]), None, name=mi.name + "_shuffled")
+    m, c_host = build(mp)
+    rows = []
+    for colors, renumber, reorder in ((5, False, False), (3, False, False), (5, True, False), (3, True, False),
+                                      (5, True, True), (3, True, True)):
+        if colors == 5:
+            nc, _ = dgc.dgc_color_edges_naive(m.h, renumber, reorder)
+        else:
+            nc, _ = dgc.dgc_color_edges(m.h, 1601, 0)
+            dgc.dgc_reorder(m.h, renumber, reorder)
+        ws = torch.empty(dgc.dgc_workspace_size(m.h, dgc.DGC_FP64) // 8 + 64, dtype=torch.float64, device=dev)
+        dgc.dgc_import_state(m.h, c_host, c)
+        dgc.dgc_set_time(m.h, 0.0)
+        fn = lambda: dgc.dgc_rk_step(m.h, dgc.DGC_FP64, c, cfg["cfl"], dt, ws)
+        fn()
+        t_rk = time_steps(torch, fn, 200, stream)
+        rows.append({"colors": int(nc), "renumber": renumber, "reorder": reorder, "ms_per_step": round(t_rk, 4),
+                     "launches_per_step": dgc.dgc_last_launch_count(m.h)})
+        del ws
+    for row in rows:
+        row["pct"] = round(100.0 * (rows[0]["ms_per_step"] - row["ms_per_step"]) / rows[0]["ms_per_step"], 1)
+    m.close()
+    out["table7"] = {"mesh": "the same mesh, element list in seeded random order", "steps_per_row": 200,
+                     "rows": rows}
+    return {"double_mach_p1_627200": out}
+
+
 def host_cores() -> int:
     """Host cores this process may run on (nproc)."""
     try:
@@ -887,7 +975,7 @@ def main():
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
-    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "bilinear", "batch"],
+    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "bilinear", "batch", "double_mach"],
                     help="time only that one of the other workloads (its variants entry, printed alone)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -901,6 +989,8 @@ def main():
         st = torch.cuda.current_stream()
         if args.only == "batch":
             print(json.dumps(run_batched(dgc, torch, dev, st, args)), flush=True)
+        elif args.only == "double_mach":
+            print(json.dumps(run_double_mach(dgc, torch, dev, st, args)), flush=True)
         else:
             print(json.dumps(run_other_meshes(dgc, torch, dev, st, args, only=args.only)), flush=True)
         return

@@ -167,6 +167,7 @@ typedef enum {
   DGC_K_ATOMIC = 6,   /* all edges with atomicAdd (comparator) */
   DGC_K_BUFFER = 7,   /* all edges into the per-edge buffer (comparator) */
   DGC_K_GATHER = 8,   /* per-element gather of the buffer (comparator) */
+  DGC_K_LIMIT = 9,    /* the limiter after an RK stage (and the step's time advance) */
   DGC_K_NCLASSES = 16
 } dgc_kernel_class;
 

@@ -674,9 +674,9 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
         launch(DGC_K_VOLUME, [&] { return mass(x, TY_D, w.rhs); });
         launch(DGC_K_STAGE, [&] { return stage_update(x, false, us, w.rhs, sa); });
       }
-      if (m.limit) launch(DGC_K_STAGE, [&] { return tri_limit(x, sa.uout); });
+      if (m.limit) launch(DGC_K_LIMIT, [&] { return tri_limit(x, sa.uout); });
     }
-    if (m.has_bc) launch(DGC_K_STAGE, [&] { return time_advance(x, dt); });
+    if (m.has_bc) launch(DGC_K_LIMIT, [&] { return time_advance(x, dt); });
     return;
   }
   // FP32 forms, increment form of the step (incr_form.cuh)
@@ -1254,7 +1254,7 @@ dgc_status dgc_limit(dgc_mesh* mesh, dgc_prec prec, double* c_dev, void* stream)
     }
     Ctx x = ready(m, stream);
     int64_t n = 0;
-    run(m, x, DGC_K_STAGE, n, [&] { return tri_limit(x, c_dev); });
+    run(m, x, DGC_K_LIMIT, n, [&] { return tri_limit(x, c_dev); });
     finish(m, n);
   });
 }

@@ -2210,15 +2210,21 @@ __global__ void __launch_bounds__(128) k_limit_tri(double* c, const int4* __rest
         lo = fmin(lo, u);
         hi = fmax(hi, u);
       }
-    double alpha = 1.0;
+    // the least ratio over the points is the one at the largest deviation of
+    // each sign (a correctly rounded quotient is monotone in its divisor, so
+    // this is the same number as the least of the per-point quotients)
+    double dmax = 0.0, dmin = 0.0;
     for (int i = 0; i < 3 + D::NQV; ++i) {
       const double* ph = i < 3 ? K.phiX[i] : K.phiV[i - 3];
       double d = 0.0;
 #pragma unroll
       for (int j = 1; j < NP; ++j) d += v[m * NP + j] * ph[j];
-      if (d > 0.0) alpha = fmin(alpha, (hi - ue) / d);
-      if (d < 0.0) alpha = fmin(alpha, (lo - ue) / d);
+      dmax = fmax(dmax, d);
+      dmin = fmin(dmin, d);
     }
+    double alpha = 1.0;
+    if (dmax > 0.0) alpha = fmin(alpha, (hi - ue) / dmax);
+    if (dmin < 0.0) alpha = fmin(alpha, (lo - ue) / dmin);
 #pragma unroll
     for (int j = 1; j < NP; ++j) v[m * NP + j] *= alpha;
   }

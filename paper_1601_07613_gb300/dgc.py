@@ -29,7 +29,7 @@ DGC_OPT_PERSISTENT = 7
 DGC_OPT_LIMITER = 8
 DGC_BC_TRANSMISSIVE, DGC_BC_WALL, DGC_BC_STATE, DGC_BC_SHOCK = 0, 1, 2, 3  # dgc_bc
 DGC_TRI, DGC_QUAD, DGC_TET = 0, 1, 2  # dgc_elem
-KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather"]
+KERNEL_CLASSES = ["cfl", "volume", "first", "color", "last", "stage", "atomic", "buffer", "gather", "limit"]
 
 STATUS = {0: "DGC_OK", 1: "DGC_ERR_ARG", 2: "DGC_ERR_MESH", 3: "DGC_ERR_COLORING_LIMIT",
           4: "DGC_ERR_UNSUPPORTED", 5: "DGC_ERR_CUDA", 6: "DGC_ERR_OOM", 7: "DGC_ERR_NONFINITE"}
