@@ -276,7 +276,7 @@ void upload(Mesh& m) {
   std::vector<double2> fgeo((size_t)m.ns * gstride);
   const int slot_w = m.refined ? 2 * nfpe : nfpe;
   std::vector<int32_t> slots((size_t)m.ne * slot_w, -1);
-  std::vector<double4> bgeo;  // boundary conditions: per boundary face its first vertex and edge vector
+  std::vector<BndGeo> bgeo;  // boundary conditions: per boundary face its first vertex and edge vector
   for (int64_t k = 0; k < m.ns; ++k) {
     int64_t old = m.side_old_of_new[k];
     int32_t l = m.sl[old], r = m.sr[old];
@@ -306,7 +306,7 @@ void upload(Mesh& m) {
       const double* X = &m.X[(size_t)l * 6];
       const double* A = X + 2 * ql;
       const double* B = X + 2 * ((ql + 1) % 3);
-      bgeo.push_back(make_double4(A[0], A[1], B[0] - A[0], B[1] - A[1]));
+      bgeo.push_back(BndGeo{A[0], A[1], B[0] - A[0], B[1] - A[1]});
     }
     topo[k] = make_int4(en[l], r >= 0 ? en[r] : -1, ql | (qr << 4) | (orient << 8), bw);
     double meas = m.smeas[old];
@@ -360,9 +360,9 @@ void upload(Mesh& m) {
       blk[kBcShock + 4] = m.shock_st[1];
       d->bc = dalloc<double>(kBcDoubles);
       DGC_CUDA(cudaMemcpy(d->bc, blk.data(), sizeof(double) * blk.size(), cudaMemcpyHostToDevice));
-      d->bgeo = dalloc<double4>(std::max<int64_t>(1, (int64_t)bgeo.size()));
+      d->bgeo = dalloc<BndGeo>(std::max<int64_t>(1, (int64_t)bgeo.size()));
       if (!bgeo.empty())
-        DGC_CUDA(cudaMemcpy(d->bgeo, bgeo.data(), sizeof(double4) * bgeo.size(), cudaMemcpyHostToDevice));
+        DGC_CUDA(cudaMemcpy(d->bgeo, bgeo.data(), sizeof(BndGeo) * bgeo.size(), cudaMemcpyHostToDevice));
     }
     if (dim == 2 && !m.quad) {
       // the mesh's time (boundary states) and the limiter's face neighbours

@@ -9,6 +9,11 @@
 
 namespace dgc {
 
+// A boundary face's left-element first vertex and edge vector (the shock's points).
+struct BndGeo {
+  double x0, y0, dx, dy;
+};
+
 // Device copies of one mesh, in the internal (renumbered) order.
 struct DeviceMesh {
   int device = -1;
@@ -47,7 +52,7 @@ struct DeviceMesh {
   // left element's first vertex of the face and the edge vector (x0, y0, dx,
   // dy), the time the boundary states are taken at (advanced by each RK step)
   double* bc = nullptr;
-  double4* bgeo = nullptr;
+  BndGeo* bgeo = nullptr;
   double* time = nullptr;
   // the limiter: per element its face neighbours (-1 on a boundary), internal ids
   int4* enb = nullptr;

@@ -509,7 +509,7 @@ struct SurfParams {
   // vector, and the time t0 + tfrac * dt (dt on the device, or none) the
   // boundary states are taken at
   const double* bc = nullptr;
-  const double4* bgeo = nullptr;
+  const BndGeo* bgeo = nullptr;
   const double* t0 = nullptr;
   const double* dtp = nullptr;
   double tfrac = 0.0;
@@ -1315,8 +1315,8 @@ __device__ __forceinline__ void bc_outside(const SurfParams& A, int w, double tq
   } else if (kind == DGC_BC_STATE || kind == DGC_BC_SHOCK) {
     int s = (w >> 4) & 15;
     if (kind == DGC_BC_SHOCK) {
-      const double4 g = A.bgeo[w >> 8];
-      const double x = g.x + tq * g.z, y = g.y + tq * g.w;
+      const BndGeo g = A.bgeo[w >> 8];
+      const double x = g.x0 + tq * g.dx, y = g.y0 + tq * g.dy;
       const double t = *A.t0 + (A.dtp ? A.tfrac * *A.dtp : 0.0);
       const double* sh = A.bc + kBcShock;
       s = x < sh[0] + sh[1] * y + sh[2] * t ? (int)sh[3] : (int)sh[4];
