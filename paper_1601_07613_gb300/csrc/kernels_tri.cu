@@ -142,6 +142,46 @@ static void upload_pairs(const RefTables& R, const void* sym) {
 
 
 
+// The FP64 lanes' tables as FP32 pairs (hi, lo) = (fl32(x), fl32(x - hi)): the
+// volume tables and the edge tables (staged into shared memory per block).
+template <int P>
+struct TriDfTab {
+  float2 phiV[TriDim<P>::NQV][TriDim<P>::NP];
+  float2 vr[TriDim<P>::NQV][TriDim<P>::NP];
+  float2 vs[TriDim<P>::NQV][TriDim<P>::NP];
+  float2 phiE[9][TriDim<P>::NQE][TriDim<P>::NP];
+};
+__constant__ TriDfTab<1> cTriDF1;
+__constant__ TriDfTab<2> cTriDF2;
+__constant__ TriDfTab<3> cTriDF3;
+template <int P>
+__device__ __forceinline__ const TriDfTab<P>& tri_dftab();
+template <> __device__ __forceinline__ const TriDfTab<1>& tri_dftab<1>() { return cTriDF1; }
+template <> __device__ __forceinline__ const TriDfTab<2>& tri_dftab<2>() { return cTriDF2; }
+template <> __device__ __forceinline__ const TriDfTab<3>& tri_dftab<3>() { return cTriDF3; }
+
+static float2 host_df(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+template <int P>
+static void upload_df(const RefTables& R, const void* sym) {
+  static TriDfTab<P> h;
+  static TriTab<double, P> d;
+  fill_tab(d, R);
+  for (int q = 0; q < TriDim<P>::NQV; ++q)
+    for (int j = 0; j < TriDim<P>::NP; ++j) {
+      h.phiV[q][j] = host_df(d.phiV[q][j]);
+      h.vr[q][j] = host_df(d.vr[q][j]);
+      h.vs[q][j] = host_df(d.vs[q][j]);
+    }
+  for (int t = 0; t < 9; ++t)
+    for (int q = 0; q < TriDim<P>::NQE; ++q)
+      for (int j = 0; j < TriDim<P>::NP; ++j) h.phiE[t][q][j] = host_df(d.phiE[t][q][j]);
+  cudaMemcpyToSymbol(sym, &h, sizeof h);
+}
+
 int tri_record_floats(int p) { return 4 * ((p + 1) * (p + 2) / 2 + 1); }
 
 // ---------------------------------------------------------------------------
@@ -308,12 +348,83 @@ __device__ __forceinline__ void lf_side(const double* U, double nx, double ny, d
 }
 
 
+// ---------------------------------------------------------------------------
+// FP64 lanes: the basis contractions in FP32 pairs.  On this GPU the FP64 pipe
+// runs at 1/64 of the FP32 rate, and the contractions (the traces
+// sum_j phi_j c_j and the projections sum_q w_q phi_j F_q) took 60 % of the
+// FP64 kernels' time (measured by leaving them out).  A value x is carried as
+// a pair hi + lo, hi = fl32(x), lo = fl32(x - hi) (2^-48 of x), and s += t b
+// runs on the FP32 pipe as the error-free product of the high parts (the FMA
+// returns a product's rounding error exactly, Dekker's product) plus the two
+// cross terms, added into s by Knuth's two-sum (TAOCP vol. 2, 4.2.2): 12 FP32
+// operations in place of one FP64 FMA.  Fluxes, wave speeds, geometry and the
+// stage update stay FP64.  The values projected are the deviations of the
+// fluxes from the flux of the element's mean ub: F(u) - F(ub) in the volume,
+// F* - F(ub).n on the faces.  For every element the two omitted parts cancel
+// (the rules integrate grad phi_j and phi_j exactly, so sum_q w_q grad phi_j .
+// F(ub) over the element equals the sum over its faces of sum_q w_q phi_j
+// F(ub).n), so the pair arithmetic only carries deviations and its rounding
+// stays below the FP64 rounding of the fluxes themselves.
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_split(double x) {
+  const float h = d2f(x);
+  return DF{h, d2f(x - f2d(h))};
+}
+__device__ __forceinline__ double df_join(DF a) { return f2d(a.h) + f2d(a.l); }
+// a b for two pairs, as a pair (Dekker's product of the high parts plus the
+// cross terms; the lo * lo term is below the pairs' precision)
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float h = __fadd_rn(p, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+// s += t b (t a table value as (hi, lo)); the intrinsics keep the compiler from
+// contracting the error-free steps into FMAs
+__device__ __forceinline__ void df_fma(DF& s, float2 t, DF b) {
+  const float p = __fmul_rn(t.x, b.h);
+  float e = __fmaf_rn(t.x, b.h, -p);
+  e = __fmaf_rn(t.x, b.l, e);
+  e = __fmaf_rn(t.y, b.h, e);
+  const float u = __fadd_rn(s.h, p);
+  const float bp = __fsub_rn(u, s.h);
+  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(u, bp)), __fsub_rn(p, bp));
+  s.h = u;
+  s.l = __fadd_rn(s.l, __fadd_rn(err, e));
+}
+
+// An FP64 element block split for the pair contractions: the mean ub = phi_0 c_0
+// (FP64) and the modes j >= 1 as pairs.
 template <int P>
-__device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], const double* __restrict__ ji,
-                                             double (&acc)[TriDim<P>::NV]) {
+struct DfBlock {
+  double ub[4];
+  DF cd[4][TriDim<P>::NP - 1];
+  __device__ __forceinline__ void init(const double (&c)[TriDim<P>::NV]) {
+    constexpr int NP = TriDim<P>::NP;
+    const double phi0 = tri_tab<double, P>().phiV[0][0];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      ub[m] = phi0 * c[m * NP];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) cd[m][j - 1] = df_split(c[m * NP + j]);
+    }
+  }
+};
+
+// Volume integral sum_q w_q (F(U_q) - F(ub)).(J^-T grad phi_j), j >= 1 (grad
+// phi_0 = 0), into the pair accumulators acc[m][j]; Fb, Gb = the x and y fluxes
+// of ub.
+template <int P>
+__device__ __forceinline__ void volume_df(const DfBlock<P>& B, const double (&Fb)[4], const double (&Gb)[4],
+                                          const double* __restrict__ ji, DF (&acc)[4][TriDim<P>::NP]) {
   using D = TriDim<P>;
   constexpr int NP = D::NP;
-  const TriTab<double, P>& K = tri_tab<double, P>();
+  const TriDfTab<P>& T = tri_dftab<P>();
   const double2 j0 = __ldg(reinterpret_cast<const double2*>(ji));
   const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
   DGC_UNROLL_Q
@@ -321,21 +432,45 @@ __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], c
     double U[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      double s = 0.0;
+      DF d{0.0f, 0.0f};
 #pragma unroll
-      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * c[m * NP + j];
-      U[m] = s;
+      for (int j = 1; j < NP; ++j) df_fma(d, T.phiV[q][j], B.cd[m][j - 1]);
+      U[m] = B.ub[m] + df_join(d);
     }
     double F[4], G[4];
     euler_xy(U, F, G);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const double fr = j0.x * F[m] + j0.y * G[m];
-      const double fs = j1.x * F[m] + j1.y * G[m];
+      const double dF = F[m] - Fb[m], dG = G[m] - Gb[m];
+      const DF fr = df_split(j0.x * dF + j0.y * dG), fs = df_split(j1.x * dF + j1.y * dG);
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * fr + K.vs[q][j] * fs;
+      for (int j = 1; j < NP; ++j) {
+        df_fma(acc[m][j], T.vr[q][j], fr);
+        df_fma(acc[m][j], T.vs[q][j], fs);
+      }
     }
   }
+}
+
+// The volume integral of an FP64 block, added into acc (the unfused kernel).
+template <int P>
+__device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], const double* __restrict__ ji,
+                                             double (&acc)[TriDim<P>::NV]) {
+  constexpr int NP = TriDim<P>::NP;
+  DfBlock<P> B;
+  B.init(c);
+  double Fb[4], Gb[4];
+  euler_xy(B.ub, Fb, Gb);
+  DF a[4][NP];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) a[m][j] = DF{0.0f, 0.0f};
+  volume_df<P>(B, Fb, Gb, ji, a);
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int j = 1; j < NP; ++j) acc[m * NP + j] += df_join(a[m][j]);
 }
 
 // FP32 volume integral in perturbation form: sum_q w_q dF(U_q).(J^-T grad phi_j),
@@ -591,8 +726,15 @@ template <int P, typename CT>
 __device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw, int ntab = 3) {
   using D = TriDim<P>;
   const TriTab<CT, P>& K = tri_tab<CT, P>();
-  const CT* src = &K.phiE[0][0][0];
-  for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) sphi[i] = src[i];
+  if constexpr (sizeof(CT) == 8) {
+    // the FP64 lanes read the edge tables as FP32 pairs (one 8-byte pair per entry)
+    const float2* src = &tri_dftab<P>().phiE[0][0][0];
+    float2* dst = reinterpret_cast<float2*>(sphi);
+    for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) dst[i] = src[i];
+  } else {
+    const CT* src = &K.phiE[0][0][0];
+    for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) sphi[i] = src[i];
+  }
   if (threadIdx.x < D::NQE) sw[threadIdx.x] = K.wE[threadIdx.x];
 }
 
@@ -1198,6 +1340,9 @@ void tri_upload_tables(int p, const RefTables& R) {
   if (p == 1) upload_pairs<1>(R, &cTriP1);
   if (p == 2) upload_pairs<2>(R, &cTriP2);
   if (p == 3) upload_pairs<3>(R, &cTriP3);
+  if (p == 1) upload_df<1>(R, &cTriDF1);
+  if (p == 2) upload_df<2>(R, &cTriDF2);
+  if (p == 3) upload_df<3>(R, &cTriDF3);
 }
 
 // One lane of the pair that handles edge k (side 0: left element, 1: right).
@@ -1215,7 +1360,8 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 // and 2 (batches of four modes, three operand arrays) at 96; the first color
 // (volume integral) and the kernels reading an FP64 state (right-hand side
 // calls and comparators), which keep the element block in registers, at 128.
-// FP64 kernels are not capped.
+// FP64 kernels at 168 (the pair contractions' registers; 2 % faster than 255
+// and 8 % faster than 128 at p = 3).
 #ifndef DGC_REGS_P3_FIRST
 #define DGC_REGS_P3_FIRST 128
 #endif
@@ -1234,9 +1380,12 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 #ifndef DGC_REGS_P2
 #define DGC_REGS_P2 80
 #endif
+#ifndef DGC_REGS_FP64
+#define DGC_REGS_FP64 168
+#endif
 template <int P, typename CT, typename ST, typename RT, int MODE, int STG>
 constexpr int surf_regs() {
-  return sizeof(CT) == 8                        ? 255
+  return sizeof(CT) == 8                        ? DGC_REGS_FP64
          : P == 3 && (sizeof(ST) == 8 || sizeof(RT) == 8 || MODE == SURF_FIRST) ? DGC_REGS_P3_FIRST
          : P == 3 && MODE == SURF_LAST && STG >= 1 ? DGC_REGS_P3_LAST12
          : P == 3 && MODE == SURF_LAST          ? DGC_REGS_P3_LAST
@@ -1338,7 +1487,6 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
   const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
   const bool writer = valid && !(side && bnd);
   const double2 g0 = A.fgeo[2 * k], g1 = A.fgeo[2 * k + 1];
-  const CT* ph = sphi + le * NQ * NP;
   // (in SURF_LAST the state may alias the stage output, but each element's
   // block is read and written by its own lane only)
 
@@ -1348,25 +1496,37 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
     pdl_trigger();
   }
   {
-    // ---------------- FP64: Eq. 2 as written ----------------
-    double c[NV], acc[NV];
-    load_block(static_cast<const double*>(A.state) + elem * NV, c);
+    // ---------------- FP64: Eq. 2, contractions in FP32 pairs ----------------
+    DfBlock<P> B;
+    {
+      double c[NV];
+      load_block(static_cast<const double*>(A.state) + elem * NV, c);
+      B.init(c);
+    }
+    double Fb[4], Gb[4];  // the x and y fluxes of the element's mean
+    euler_xy(B.ub, Fb, Gb);
+    DF acc2[4][NP];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    if constexpr (MODE == SURF_FIRST) volume_acc64<P>(c, A.jinv + 4 * elem, acc);
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc2[m][j] = DF{0.0f, 0.0f};
+    if constexpr (MODE == SURF_FIRST) volume_df<P>(B, Fb, Gb, A.jinv + 4 * elem, acc2);
     const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
+    double Fbn[4];  // F(ub).n, subtracted from the face flux (the volume integral omits F(ub))
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Fbn[m] = Fb[m] * nx + Gb[m] * ny;
+    const float2* ph = reinterpret_cast<const float2*>(sphi) + le * NQ * NP;
+    const DF sdf = df_split(scale);
     DGC_UNROLL_Q
     for (int q = 0; q < NQ; ++q) {
       const int qq = right ? NQ - 1 - q : q;  // the right element runs along the edge backwards
-      double phi[NP], U[4], V[4], a[4], b[4], Fs[4];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) phi[j] = ph[qq * NP + j];
+      double U[4], V[4], a[4], b[4], Fs[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        double s = 0.0;
+        DF t{0.0f, 0.0f};
 #pragma unroll
-        for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
-        U[m] = s;
+        for (int j = 1; j < NP; ++j) df_fma(t, ph[qq * NP + j], B.cd[m][j - 1]);
+        U[m] = B.ub[m] + df_join(t);
       }
       // a boundary face's second lane holds the state outside it
       if (bnd && side && A.bc) bc_outside(A, tp.w, tri_tab<double, P>().tE[q], nx, ny, U);
@@ -1387,19 +1547,26 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
         b[m] = side ? U[m] : V[m];
         Fs[m] = 0.5 * (Fo[m] + Fp[m]) - (0.5 * lam) * (b[m] - a[m]);
       }
-      const double s = scale * sw[q];
+      const DF sq = df_mul(sdf, df_split(sw[q]));
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const double g = s * Fs[m];
+        const DF g = df_mul(sq, df_split(Fs[m] - Fbn[m]));
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+        for (int j = 0; j < NP; ++j) df_fma(acc2[m][j], ph[qq * NP + j], g);
       }
     }
+    double acc[NV];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc[m * NP + j] = df_join(acc2[m][j]);
     if constexpr (MODE != SURF_FIRST) {
       pdl_wait();
       pdl_trigger();
     }
     if constexpr (MODE == SURF_LAST) {
+      double c[NV];  // the stage input block again (cached), for the update
+      load_block(static_cast<const double*>(A.state) + elem * NV, c);
       if (writer) fp64_last<P>(A, elem, acc, c);
     } else if (writer) {
       surf_write<P, RT, MODE>(A, elem, k, side, acc);
@@ -2033,7 +2200,7 @@ __device__ __forceinline__ void coop_edges(const SurfParams& A, int64_t begin, i
 }
 
 template <int P, typename CT, typename ST, typename RT>
-__global__ void __launch_bounds__(128) __maxnreg__((surf_regs<P, CT, ST, RT, SURF_FIRST, -1>()))
+__global__ void __launch_bounds__(128) __maxnreg__((sizeof(CT) == 8 ? 255 : surf_regs<P, CT, ST, RT, SURF_FIRST, -1>()))
     k_rhs_coop(const CoopRhs C) {
   using D = TriDim<P>;
   namespace cg = cooperative_groups;
