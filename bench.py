@@ -217,8 +217,23 @@ def kernel_source_hash() -> str:
 # stage) from ncu captures of this benchmark's own command at full size with
 # the tiles 64x2, 64x2, 32x4 (one kernel and two launches per capture), taken
 # with the kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = "f41d638e7f35bf61"
-TRAFFIC_BYTES = {"last": 1123974698, "first": 480850560, "color": 592490624, "cfl": 4220928}
+TRAFFIC_SOURCES = "6313644ba56c8009"
+TRAFFIC_BYTES = {"last": 1123977557, "first": 480874026, "color": 592413952, "cfl": 4221056}
+
+
+def fp64_roofline(flops: float, ms: float, p64: float) -> dict:
+    """The FP64 form against the FP64 pipe.  flops = Eq. 2's floating-point
+    operations as a term-by-term FP64 evaluation does them; on triangle meshes
+    the basis contractions among them run as FP32 pairs on the FP32 pipe, so the
+    effective rate can exceed the FP64 pipe's peak: reported as such (frac = null)."""
+    eff = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": None, "peak": round(p64, 3), "unit": "TFLOP/s",
+            "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 (torch)", "frac": None,
+            "effective_fp64_equivalent": round(eff, 3), "effective_vs_fp64_peak": round(eff / p64, 3),
+            "derived_peak": round(FP64_PEAK_TFLOPS, 3),
+            "note": "Eq. 2's FP64 flop count over the step time; the basis contractions run as FP32 pairs on the "
+                    "FP32 pipe (fluxes, geometry and the stage update on the FP64 pipe), so no fraction of the "
+                    "FP64 peak is claimed"}
 
 
 def replica_throughput(torch, ms: float, world: int, units_per_step: float, dev):
@@ -368,12 +383,7 @@ def run_dgc(args, rank, world, local_rank):
         variants["rk_fp32mixed_plain_launch"] = {"value": 3 * dofs / (ms_plain * 1e-3), "ms_per_step": round(ms_plain, 4)}
         p64 = fp64_peak_tflops(torch, dev)
         variants["rk_fp64"] = {"value": 3 * dofs / (ms64 * 1e-3), "ms_per_step": round(ms64, 4),
-                               "roofline": {"bound": "alu", "achieved": round(fl / (ms64 * 1e-3) / 1e12, 3),
-                                            "peak": round(p64, 3), "unit": "TFLOP/s",
-                                            "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 (torch)",
-                                            "frac": round(fl / (ms64 * 1e-3) / 1e12 / p64, 3),
-                                            "derived_peak": round(FP64_PEAK_TFLOPS, 3),
-                                            "frac_of_derived": round(fl / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)}}
+                               "roofline": fp64_roofline(fl, ms64, p64)}
         # ---- Kahan form: FP32 pair state, compensated update --------------------------
         kst = torch.empty(dgc.dgc_state_bytes(mesh.h, dgc.DGC_FP32_KAHAN) // 4, dtype=torch.float32, device=dev)
         wsk = torch.empty(dgc.dgc_workspace_size(mesh.h, dgc.DGC_FP32_KAHAN) // 8 + 64, dtype=torch.float64,
@@ -570,10 +580,7 @@ def run_batched(dgc, torch, dev, stream, args):
             else:
                 fl = 3 * sum(flops_per_rhs(i["ne"], i["M"] * i["np"], i["nqv"], i["nqf"]) for i in infos)
                 p64 = fp64_peak_tflops(torch, dev)
-                out[f"batched_{tag}"]["roofline"] = {
-                    "bound": "alu", "achieved": round(fl / (ms * 1e-3) / 1e12, 3), "peak": round(p64, 3),
-                    "unit": "TFLOP/s", "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 (torch)",
-                    "frac": round(fl / (ms * 1e-3) / 1e12 / p64, 3)}
+                out[f"batched_{tag}"]["roofline"] = fp64_roofline(fl, ms, p64)
             del ws
     finally:
         dgc.dgc_batch_destroy(batch)
