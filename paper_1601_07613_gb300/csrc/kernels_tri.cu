@@ -366,6 +366,16 @@ __device__ __forceinline__ void lf_side(const double* U, double nx, double ny, d
 // F(ub).n), so the pair arithmetic only carries deviations and its rounding
 // stays below the FP64 rounding of the fluxes themselves.
 // ---------------------------------------------------------------------------
+#ifndef DGC_DF_MIN_P
+#define DGC_DF_MIN_P 2
+#endif
+// the FP64 lanes of order P use the pair contractions (at p = 1, with three
+// modes, the splits and joins cost more than the FP64 contractions they replace)
+template <int P>
+__host__ __device__ constexpr bool df_lanes() {
+  return P >= DGC_DF_MIN_P;
+}
+
 struct DF {
   float h, l;
 };
@@ -457,6 +467,33 @@ template <int P>
 __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], const double* __restrict__ ji,
                                              double (&acc)[TriDim<P>::NV]) {
   constexpr int NP = TriDim<P>::NP;
+  if constexpr (!df_lanes<P>()) {  // Eq. 2 as written, FP64 throughout
+    using D = TriDim<P>;
+    const TriTab<double, P>& K = tri_tab<double, P>();
+    const double2 j0 = __ldg(reinterpret_cast<const double2*>(ji));
+    const double2 j1 = __ldg(reinterpret_cast<const double2*>(ji) + 1);
+    DGC_UNROLL_Q
+    for (int q = 0; q < D::NQV; ++q) {
+      double U[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * c[m * NP + j];
+        U[m] = s;
+      }
+      double F[4], G[4];
+      euler_xy(U, F, G);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double fr = j0.x * F[m] + j0.y * G[m];
+        const double fs = j1.x * F[m] + j1.y * G[m];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[m * NP + j] += K.vr[q][j] * fr + K.vs[q][j] * fs;
+      }
+    }
+    return;
+  }
   DfBlock<P> B;
   B.init(c);
   double Fb[4], Gb[4];
@@ -726,7 +763,7 @@ template <int P, typename CT>
 __device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw, int ntab = 3) {
   using D = TriDim<P>;
   const TriTab<CT, P>& K = tri_tab<CT, P>();
-  if constexpr (sizeof(CT) == 8) {
+  if constexpr (sizeof(CT) == 8 && df_lanes<P>()) {
     // the FP64 lanes read the edge tables as FP32 pairs (one 8-byte pair per entry)
     const float2* src = &tri_dftab<P>().phiE[0][0][0];
     float2* dst = reinterpret_cast<float2*>(sphi);
@@ -1385,7 +1422,7 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 #endif
 template <int P, typename CT, typename ST, typename RT, int MODE, int STG>
 constexpr int surf_regs() {
-  return sizeof(CT) == 8                        ? DGC_REGS_FP64
+  return sizeof(CT) == 8                        ? (df_lanes<P>() ? DGC_REGS_FP64 : 255)
          : P == 3 && (sizeof(ST) == 8 || sizeof(RT) == 8 || MODE == SURF_FIRST) ? DGC_REGS_P3_FIRST
          : P == 3 && MODE == SURF_LAST && STG >= 1 ? DGC_REGS_P3_LAST12
          : P == 3 && MODE == SURF_LAST          ? DGC_REGS_P3_LAST
@@ -1495,7 +1532,65 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
     pdl_wait();
     pdl_trigger();
   }
-  {
+  if constexpr (!df_lanes<P>()) {
+    // ---------------- FP64: Eq. 2 as written ----------------
+    double c[NV], acc[NV];
+    load_block(static_cast<const double*>(A.state) + elem * NV, c);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    if constexpr (MODE == SURF_FIRST) volume_acc64<P>(c, A.jinv + 4 * elem, acc);
+    const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
+    const CT* ph = sphi + le * NQ * NP;
+    DGC_UNROLL_Q
+    for (int q = 0; q < NQ; ++q) {
+      const int qq = right ? NQ - 1 - q : q;  // the right element runs along the edge backwards
+      double phi[NP], U[4], V[4], a[4], b[4], Fs[4];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) phi[j] = ph[qq * NP + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
+        U[m] = s;
+      }
+      // a boundary face's second lane holds the state outside it
+      if (bnd && side && A.bc) bc_outside(A, tp.w, tri_tab<double, P>().tE[q], nx, ny, U);
+      // own side's normal flux and wave speed, then the partner's
+      double Fo[4], Fp[4], wo;
+      lf_side(U, nx, ny, Fo, wo);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        V[m] = __shfl_xor_sync(0xffffffffu, U[m], 1);
+        Fp[m] = __shfl_xor_sync(0xffffffffu, Fo[m], 1);
+      }
+      const double lam = fmax(wo, __shfl_xor_sync(0xffffffffu, wo, 1));
+      // F* = (F(a).n + F(b).n)/2 - lam (b - a)/2 with a = left, b = right: the
+      // sums are commutative, so both lanes get the same bits (conservation)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        a[m] = side ? V[m] : U[m];
+        b[m] = side ? U[m] : V[m];
+        Fs[m] = 0.5 * (Fo[m] + Fp[m]) - (0.5 * lam) * (b[m] - a[m]);
+      }
+      const double s = scale * sw[q];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double g = s * Fs[m];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+      }
+    }
+    if constexpr (MODE != SURF_FIRST) {
+      pdl_wait();
+      pdl_trigger();
+    }
+    if constexpr (MODE == SURF_LAST) {
+      if (writer) fp64_last<P>(A, elem, acc, c);
+    } else if (writer) {
+      surf_write<P, RT, MODE>(A, elem, k, side, acc);
+    }
+  } else {
     // ---------------- FP64: Eq. 2, contractions in FP32 pairs ----------------
     DfBlock<P> B;
     {
