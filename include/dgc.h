@@ -64,14 +64,14 @@ typedef enum {
  *     summation; no FP64 arithmetic but the CFL reduction.  Triangles.  Its device layout
  *     (dgc_state_bytes) is written and read by dgc_import_state_prec / _export_.
  * DGC_FP64 keeps the state, geometry, fluxes, wave speeds, the CFL reduction and the
- * stage update in FP64.  On triangle meshes of order p >= 2 its basis contractions (the traces
- * sum_j phi_j c_j and the projections onto the modes) run as FP32 pairs (hi + lo,
- * 2^-48 relative per value) on the FP32 pipe, on the deviations of the fluxes from the
- * flux of the element's mean (F(u) - F(ub) and F* - F(ub).n, whose omitted parts
+ * stage update in FP64.  On triangle meshes of order p >= 2 and on tetrahedral meshes its
+ * basis contractions (the traces sum_j phi_j c_j and the projections onto the modes) run
+ * as FP32 pairs (hi + lo, 2^-48 relative per value) on the FP32 pipe, on the deviations of
+ * the fluxes from the flux of the element's mean (F(u) - F(ub) and F* - F(ub).n, whose omitted parts
  * cancel exactly between each element's volume and faces); on the benchmark workloads
  * the right-hand side is within 3e-13 of the exact one (relative L2), closer than a
- * plain FP64 evaluation of Eq. 2.  Triangle meshes of order 1 and quadrilateral, hybrid and
- * tetrahedral meshes evaluate Eq. 2 as written in FP64. */
+ * plain FP64 evaluation of Eq. 2.  Triangle meshes of order 1 and quadrilateral and hybrid
+ * meshes evaluate Eq. 2 as written in FP64. */
 typedef enum {
   DGC_FP64 = 0,        /* FP64 state, fluxes and stage update (contractions: see above) */
   DGC_FP32_MIXED = 1,  /* FP32 flux with an FP64 state */

@@ -745,6 +745,8 @@ void device_free(Mesh& m) {
   cudaFree(m.dev->xfer);
   cudaFree(m.dev->ftab);
   cudaFree(m.dev->ftabd);
+  cudaFree(m.dev->ftabdf);
+  cudaFree(m.dev->vtabdf);
   cudaFree(m.dev->cfl_est);
   cudaFree(m.dev->hyb_kind);
   cudaFree(m.dev->hyb_tab);

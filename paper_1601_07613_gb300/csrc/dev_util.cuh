@@ -108,6 +108,45 @@ __device__ __forceinline__ double f2d(float f) {
   return f2d_any(f);
 }
 
+// FP32 pairs (the FP64 lanes' basis contractions): a value x as hi + lo, hi =
+// fl32(x), lo = fl32(x - hi), 2^-48 of x.  s += t b runs on the FP32 pipe as
+// the error-free product of the high parts (the FMA returns a product's
+// rounding error exactly: Dekker's product) plus the two cross terms, added
+// into s by Knuth's two-sum (TAOCP vol. 2, 4.2.2): 12 FP32 operations for one
+// FP64 FMA.  The intrinsics keep the compiler from contracting the error-free
+// steps into FMAs.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_split(double x) {
+  const float h = d2f(x);
+  return DF{h, d2f(x - f2d(h))};
+}
+__device__ __forceinline__ double df_join(DF a) { return f2d(a.h) + f2d(a.l); }
+// a b for two pairs, as a pair (Dekker's product of the high parts plus the
+// cross terms; the lo * lo term is below the pairs' precision)
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float h = __fadd_rn(p, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+// s += t b (t a table value as (hi, lo)); the intrinsics keep the compiler from
+// contracting the error-free steps into FMAs
+__device__ __forceinline__ void df_fma(DF& s, float2 t, DF b) {
+  const float p = __fmul_rn(t.x, b.h);
+  float e = __fmaf_rn(t.x, b.h, -p);
+  e = __fmaf_rn(t.x, b.l, e);
+  e = __fmaf_rn(t.y, b.h, e);
+  const float u = __fadd_rn(s.h, p);
+  const float bp = __fsub_rn(u, s.h);
+  const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(u, bp)), __fsub_rn(p, bp));
+  s.h = u;
+  s.l = __fadd_rn(s.l, __fadd_rn(err, e));
+}
+
 template <typename T>
 __device__ __forceinline__ T to(double x);
 template <>

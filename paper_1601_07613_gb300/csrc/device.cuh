@@ -29,6 +29,8 @@ struct DeviceMesh {
   int edge_tables = 3;      // triangle edge tables the surface kernels stage (3, or 9 when refined)
   float* ftab = nullptr;    // 3D face tables (float copy)
   double* ftabd = nullptr;  // 3D face tables
+  float2* ftabdf = nullptr; // 3D face tables as FP32 pairs (hi, lo): the FP64 kernels
+  float2* vtabdf = nullptr; // 3D volume tables as FP32 pairs [4][NQV][NP]: the FP64 kernels
   float* cfl_est = nullptr; // [E] FP32 step estimates of the CFL pre-pass, then 1 minimum
   int32_t* perm = nullptr;  // [E] internal element id of each original element (import / export)
   double* xfer = nullptr;   // [E][M*Np] state in original order (import / export; allocated on first use)

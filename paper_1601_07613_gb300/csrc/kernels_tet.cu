@@ -121,6 +121,25 @@ void tet_upload_tables(int p, const RefTables& R, DeviceMesh& d) {
     throw Error{DGC_ERR_OOM, "cudaMalloc (face tables)"};
   cudaMemcpy(d.ftabd, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d.ftab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice);
+  // the FP64 kernels' tables as FP32 pairs (hi, lo): the face tables, and the
+  // volume tables [4][NQV][NP] (phi_j, w dphi_j/dr, w dphi_j/ds, w dphi_j/dt)
+  auto pair = [](double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+  };
+  std::vector<float2> tp(t.size()), vp((size_t)4 * R.nqv * R.np);
+  for (size_t i = 0; i < t.size(); ++i) tp[i] = pair(t[i]);
+  for (int q = 0; q < R.nqv; ++q)
+    for (int j = 0; j < R.np; ++j) {
+      vp[(size_t)q * R.np + j] = pair(R.phiV[(size_t)q * R.np + j]);
+      for (int a = 0; a < 3; ++a)
+        vp[((size_t)(a + 1) * R.nqv + q) * R.np + j] = pair(R.vw[q] * R.dphiV[((size_t)a * R.nqv + q) * R.np + j]);
+    }
+  if (cudaMalloc(&d.ftabdf, sizeof(float2) * tp.size()) != cudaSuccess ||
+      cudaMalloc(&d.vtabdf, sizeof(float2) * vp.size()) != cudaSuccess)
+    throw Error{DGC_ERR_OOM, "cudaMalloc (pair tables)"};
+  cudaMemcpy(d.ftabdf, tp.data(), sizeof(float2) * tp.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(d.vtabdf, vp.data(), sizeof(float2) * vp.size(), cudaMemcpyHostToDevice);
 }
 
 // ---------------------------------------------------------------------------
@@ -237,34 +256,81 @@ __device__ __forceinline__ void euler3_n(const double* U, double nx, double ny, 
 }
 
 
+// The FP64 form with the basis contractions as FP32 pairs (dev_util.cuh), as
+// on triangles: the element's mean ub = phi_0 c_0 in FP64, its modes j >= 1 as
+// pairs; the volume integral projects F(U) . grad r_k - F(ub) . grad r_k, and
+// the faces F* - F(ub).n (the omitted parts cancel exactly for each element),
+// so the pairs carry only deviations.  The pair volume tables [4][NQV][NP] sit
+// in shared memory (vt).
 template <int P>
-__device__ __forceinline__ void tet_volume64(const double (&c)[TetDim<P>::NV], const double* ji,
-                                             double (&acc)[TetDim<P>::NV]) {
+struct TetDfBlock {
+  double ub[5];
+  DF cd[5][TetDim<P>::NP - 1];
+  __device__ __forceinline__ void init(const double (&c)[TetDim<P>::NV]) {
+    constexpr int NP = TetDim<P>::NP;
+    const double phi0 = tet_tab<double, P>().phiV[0][0];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      ub[m] = phi0 * c[m * NP];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) cd[m][j - 1] = df_split(c[m * NP + j]);
+    }
+  }
+};
+
+// the Euler flux of U in direction n (any length), given 1/rho and p
+__device__ __forceinline__ void euler3_dir(const double* U, double ir, double p, const double* n, double* F) {
+  const double un = (U[1] * n[0] + U[2] * n[1] + U[3] * n[2]) * ir;
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + p * n[0];
+  F[2] = U[2] * un + p * n[1];
+  F[3] = U[3] * un + p * n[2];
+  F[4] = (U[4] + p) * un;
+}
+
+template <int P>
+__device__ __forceinline__ void tet_volume_df(const TetDfBlock<P>& B, const double* ji, const float2* vt,
+                                              DF (&acc)[5][TetDim<P>::NP]) {
   using D = TetDim<P>;
-  constexpr int NP = D::NP;
-  const TetTab<double, P>& K = tet_tab<double, P>();
+  constexpr int NP = D::NP, NQV = D::NQV;
   double J[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) J[i] = __ldg(ji + i);
-#pragma unroll 2
-  for (int q = 0; q < D::NQV; ++q) {
+  double Fb[3][5];  // F(ub) . grad r_k
+  {
+    const double ir = 1.0 / B.ub[0];
+    const double p = 0.4 * (B.ub[4] - 0.5 * (B.ub[1] * B.ub[1] + B.ub[2] * B.ub[2] + B.ub[3] * B.ub[3]) * ir);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) euler3_dir(B.ub, ir, p, J + 3 * k, Fb[k]);
+  }
+#pragma unroll 1
+  for (int q = 0; q < NQV; ++q) {
     double U[5];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-      double s = 0.0;
+      DF d{0.0f, 0.0f};
 #pragma unroll
-      for (int j = 0; j < NP; ++j) s += K.phiV[q][j] * c[m * NP + j];
-      U[m] = s;
+      for (int j = 1; j < NP; ++j) df_fma(d, vt[q * NP + j], B.cd[m][j - 1]);
+      U[m] = B.ub[m] + df_join(d);
     }
-    // reference-direction fluxes F . grad r_k
-    double Fr[3][5], un, cs;
+    const double ir = 1.0 / U[0];
+    const double p = 0.4 * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir);
+    DF g[3][5];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) euler3_n(U, J[3 * k], J[3 * k + 1], J[3 * k + 2], Fr[k], un, cs);
+    for (int k = 0; k < 3; ++k) {
+      double F[5];
+      euler3_dir(U, ir, p, J + 3 * k, F);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) g[k][m] = df_split(F[m] - Fb[k][m]);
+    }
 #pragma unroll
     for (int m = 0; m < 5; ++m)
 #pragma unroll
-      for (int j = 0; j < NP; ++j)
-        acc[m * NP + j] += K.vr[q][j] * Fr[0][m] + K.vs[q][j] * Fr[1][m] + K.vt[q][j] * Fr[2][m];
+      for (int j = 1; j < NP; ++j) {
+        df_fma(acc[m][j], vt[(NQV + q) * NP + j], g[0][m]);
+        df_fma(acc[m][j], vt[(2 * NQV + q) * NP + j], g[1][m]);
+        df_fma(acc[m][j], vt[(3 * NQV + q) * NP + j], g[2][m]);
+      }
   }
 }
 
@@ -333,19 +399,34 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
 
 template <int P, typename CT, typename ST, typename RT>
 __global__ void __launch_bounds__(128) k_vol_tet(const ST* c, int sstride, const double* jinv, RT* rhs, int64_t e0,
-                                                 int64_t ne) {
+                                                 int64_t ne, const float2* vtab) {
   using D = TetDim<P>;
+  constexpr int NP = D::NP;
+  extern __shared__ float2 vt_s[];  // FP64: the pair volume tables [4][NQV][NP]
+  if constexpr (sizeof(CT) == 8) {
+    for (int i = threadIdx.x; i < 4 * D::NQV * NP; i += blockDim.x) vt_s[i] = vtab[i];
+    __syncthreads();
+  }
   const int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   RT out[D::NV];
   if constexpr (sizeof(CT) == 8) {
-    double v[D::NV], acc[D::NV];
-    tload(c + e * D::NV, v);
+    TetDfBlock<P> B;
+    {
+      double v[D::NV];
+      tload(c + e * D::NV, v);
+      B.init(v);
+    }
+    DF acc[5][NP];
 #pragma unroll
-    for (int i = 0; i < D::NV; ++i) acc[i] = 0.0;
-    tet_volume64<P>(v, jinv + 9 * e, acc);
+    for (int m = 0; m < 5; ++m)
 #pragma unroll
-    for (int i = 0; i < D::NV; ++i) out[i] = (RT)acc[i];
+      for (int j = 0; j < NP; ++j) acc[m][j] = DF{0.0f, 0.0f};
+    tet_volume_df<P>(B, jinv + 9 * e, vt_s, acc);
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) out[m * NP + j] = j ? (RT)df_join(acc[m][j]) : (RT)0.0;
   } else {
     const int64_t stride = sizeof(ST) == 8 ? D::NV : sstride;
     TetPert<P> B;
@@ -367,7 +448,8 @@ struct TetParams {
   const int4* topo;
   const double2* fgeo;
   const double* jinv;
-  const void* ftab;  // [4][6][NQF][NP] of CT
+  const void* ftab;  // [4][6][NQF][NP] of CT (FP64 kernels: FP32 pairs)
+  const float2* vtab = nullptr;  // FP64 first color: the pair volume tables [4][NQV][NP]
   const void* state;
   void* rhs;
   void* buf;
@@ -459,11 +541,15 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
   using D = TetDim<P>;
   constexpr int NP = D::NP, NQ = D::NQF, NV = D::NV;
   extern __shared__ unsigned char smem_raw[];
-  CT* sphi = reinterpret_cast<CT*>(smem_raw);  // [4][6][NQ][NP]
+  CT* sphi = reinterpret_cast<CT*>(smem_raw);  // [4][6][NQ][NP] (FP64: FP32 pairs of the same size)
   {
     const CT* src = static_cast<const CT*>(A.ftab);
     for (int i = threadIdx.x; i < 24 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
   }
+  // the FP64 first color: the pair volume tables after the face tables
+  float2* vt = reinterpret_cast<float2*>(smem_raw + sizeof(CT) * 24 * NQ * NP);
+  if constexpr (sizeof(CT) == 8 && MODE == SURF_FIRST)
+    for (int i = threadIdx.x; i < 4 * D::NQV * NP; i += blockDim.x) vt[i] = A.vtab[i];
   __syncthreads();
   // programmatic launch (dev_util.cuh): the first color reads its predecessor's
   // record and overwrites the rhs it read, so it waits at once; the other
@@ -489,24 +575,39 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
   const CT* ph = sphi + (lf * 6 + orient) * NQ * NP;
 
   if constexpr (sizeof(CT) == 8) {
+    // FP64 flux and update, the basis contractions as FP32 pairs on the flux
+    // deviations (tet_volume_df)
     const TetTab<double, P>& K = tet_tab<double, P>();
-    double c[NV], acc[NV];
-    tload(static_cast<const double*>(A.state) + elem * NV, c);
+    const float2* ph2 = reinterpret_cast<const float2*>(ph);
+    TetDfBlock<P> B;
+    {
+      double c[NV];
+      tload(static_cast<const double*>(A.state) + elem * NV, c);
+      B.init(c);
+    }
+    DF acc2[5][NP];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    if constexpr (MODE == SURF_FIRST) tet_volume64<P>(c, A.jinv + 9 * elem, acc);
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc2[m][j] = DF{0.0f, 0.0f};
+    if constexpr (MODE == SURF_FIRST) tet_volume_df<P>(B, A.jinv + 9 * elem, vt, acc2);
     const double scale = right ? g2.y : -g2.x;
+    const double nn[3] = {g0.x, g0.y, g1.x};
+    double Fbn[5];  // F(ub).n, subtracted from the face flux (the volume integral omits F(ub))
+    {
+      const double ir = 1.0 / B.ub[0];
+      const double p = 0.4 * (B.ub[4] - 0.5 * (B.ub[1] * B.ub[1] + B.ub[2] * B.ub[2] + B.ub[3] * B.ub[3]) * ir);
+      euler3_dir(B.ub, ir, p, nn, Fbn);
+    }
 #pragma unroll 2
     for (int q = 0; q < NQ; ++q) {
-      double phi[NP], U[5], V[5], a[5], b[5], Fs[5];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) phi[j] = ph[q * NP + j];
+      double U[5], V[5], a[5], b[5], Fs[5];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        double s = 0.0;
+        DF t{0.0f, 0.0f};
 #pragma unroll
-        for (int j = 0; j < NP; ++j) s += phi[j] * c[m * NP + j];
-        U[m] = s;
+        for (int j = 1; j < NP; ++j) df_fma(t, ph2[q * NP + j], B.cd[m][j - 1]);
+        U[m] = B.ub[m] + df_join(t);
       }
       // each lane evaluates its own side (one division, one square root) and
       // exchanges the normal flux and wave speed with its partner; the sums
@@ -526,19 +627,26 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
         b[m] = side ? U[m] : V[m];
         Fs[m] = 0.5 * (Fo[m] + Fp[m]) - (0.5 * lam) * (b[m] - a[m]);
       }
-      const double s = scale * K.wF[q];
+      const double sq = scale * K.wF[q];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        const double g = s * Fs[m];
+        const DF g = df_split(sq * (Fs[m] - Fbn[m]));
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+        for (int j = 0; j < NP; ++j) df_fma(acc2[m][j], ph2[q * NP + j], g);
       }
     }
+    double acc[NV];
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc[m * NP + j] = df_join(acc2[m][j]);
     if constexpr (MODE != SURF_FIRST) {
       pdl_wait();
       pdl_trigger();
     }
     if constexpr (MODE == SURF_LAST) {
+      double c[NV];  // the stage input block again (cached), for the update
+      tload(static_cast<const double*>(A.state) + elem * NV, c);
       if (writer) tet_fp64_last<P>(A, elem, acc, c);
     } else if (writer) {
       tet_write<P, RT, MODE>(A, elem, k, side, acc);
@@ -708,8 +816,12 @@ static int tvol_p(const Ctx& x, const void* s, int ss, void* r, int64_t e0) {
   const int bs = 128;
   const int64_t n = x.ne - e0;
   if (n <= 0) return 0;
-  k_vol_tet<P, CT, ST, RT><<<(unsigned)((n + bs - 1) / bs), bs, 0, x.st>>>(
-      static_cast<const ST*>(s), ss, x.d->jinv, static_cast<RT*>(r), e0, x.ne);
+  using D = TetDim<P>;
+  const size_t smem = sizeof(CT) == 8 ? sizeof(float2) * 4 * D::NQV * D::NP : 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_vol_tet<P, CT, ST, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+  k_vol_tet<P, CT, ST, RT><<<(unsigned)((n + bs - 1) / bs), bs, smem, x.st>>>(
+      static_cast<const ST*>(s), ss, x.d->jinv, static_cast<RT*>(r), e0, x.ne, x.d->vtabdf);
   return 1;
 }
 
@@ -730,8 +842,10 @@ static int tsurf_launch(const Ctx& x, TetParams A) {
   const int64_t n = A.end - A.begin;
   if (n <= 0) return 0;
   using D = TetDim<P>;
-  A.ftab = sizeof(CT) == 8 ? (const void*)x.d->ftabd : (const void*)x.d->ftab;
-  const size_t smem = sizeof(CT) * 24 * D::NQF * D::NP;
+  A.ftab = sizeof(CT) == 8 ? (const void*)x.d->ftabdf : (const void*)x.d->ftab;
+  A.vtab = x.d->vtabdf;
+  const size_t smem = sizeof(CT) * 24 * D::NQF * D::NP +
+                      (sizeof(CT) == 8 && MODE == SURF_FIRST ? sizeof(float2) * 4 * D::NQV * D::NP : 0);
   auto kern = k_surf_tet<P, CT, ST, RT, MODE>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = 2 * x.epb;
