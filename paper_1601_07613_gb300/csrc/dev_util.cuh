@@ -147,6 +147,25 @@ __device__ __forceinline__ void df_fma(DF& s, float2 t, DF b) {
   s.l = __fadd_rn(s.l, __fadd_rn(err, e));
 }
 
+// Two variables at once (sharing one table value) on the packed FP32 pipe
+// (__fmul2_rn, __ffma2_rn, __fadd2_rn): s_k += t b_k for k = 0, 1, with the
+// table value t = (hi, hi, lo, lo) and s, b as (hi pair, lo pair); the same
+// steps as df_fma, each subtraction an FMA with -1 (one rounding, as a
+// subtraction).
+__device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float4 t, float2 bh, float2 bl) {
+  const float2 th = make_float2(t.x, t.y), tl = make_float2(t.z, t.w), m1 = make_float2(-1.0f, -1.0f);
+  const float2 p = __fmul2_rn(th, bh);
+  float2 e = __ffma2_rn(th, bh, __fmul2_rn(p, m1));
+  e = __ffma2_rn(th, bl, e);
+  e = __ffma2_rn(tl, bh, e);
+  const float2 u = __fadd2_rn(sh, p);
+  const float2 bp = __ffma2_rn(sh, m1, u);   // u - sh
+  const float2 ap = __ffma2_rn(bp, m1, u);   // u - bp
+  const float2 err = __fadd2_rn(__ffma2_rn(ap, m1, sh), __ffma2_rn(bp, m1, p));
+  sh = u;
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
+}
+
 template <typename T>
 __device__ __forceinline__ T to(double x);
 template <>

@@ -143,12 +143,14 @@ static void upload_pairs(const RefTables& R, const void* sym) {
 
 
 // The FP64 lanes' tables as FP32 pairs (hi, lo) = (fl32(x), fl32(x - hi)): the
-// volume tables and the edge tables (staged into shared memory per block).
+// volume tables as (hi, hi, lo, lo), the operand of a packed update of two
+// variables (df_fma2), and the edge tables as (hi, lo) (staged into shared
+// memory per block as (hi, hi, lo, lo)).
 template <int P>
 struct TriDfTab {
-  float2 phiV[TriDim<P>::NQV][TriDim<P>::NP];
-  float2 vr[TriDim<P>::NQV][TriDim<P>::NP];
-  float2 vs[TriDim<P>::NQV][TriDim<P>::NP];
+  float4 phiV[TriDim<P>::NQV][TriDim<P>::NP];
+  float4 vr[TriDim<P>::NQV][TriDim<P>::NP];
+  float4 vs[TriDim<P>::NQV][TriDim<P>::NP];
   float2 phiE[9][TriDim<P>::NQE][TriDim<P>::NP];
 };
 __constant__ TriDfTab<1> cTriDF1;
@@ -164,6 +166,10 @@ static float2 host_df(double x) {
   const float h = (float)x;
   return make_float2(h, (float)(x - (double)h));
 }
+static float4 host_df4(double x) {
+  const float2 v = host_df(x);
+  return make_float4(v.x, v.x, v.y, v.y);
+}
 
 template <int P>
 static void upload_df(const RefTables& R, const void* sym) {
@@ -172,9 +178,9 @@ static void upload_df(const RefTables& R, const void* sym) {
   fill_tab(d, R);
   for (int q = 0; q < TriDim<P>::NQV; ++q)
     for (int j = 0; j < TriDim<P>::NP; ++j) {
-      h.phiV[q][j] = host_df(d.phiV[q][j]);
-      h.vr[q][j] = host_df(d.vr[q][j]);
-      h.vs[q][j] = host_df(d.vs[q][j]);
+      h.phiV[q][j] = host_df4(d.phiV[q][j]);
+      h.vr[q][j] = host_df4(d.vr[q][j]);
+      h.vs[q][j] = host_df4(d.vs[q][j]);
     }
   for (int t = 0; t < 9; ++t)
     for (int q = 0; q < TriDim<P>::NQE; ++q)
@@ -369,6 +375,9 @@ __device__ __forceinline__ void lf_side(const double* U, double nx, double ny, d
 #ifndef DGC_DF_MIN_P
 #define DGC_DF_MIN_P 2
 #endif
+// doubles per entry of the FP64 lanes' shared-memory edge tables (pair lanes:
+// one (hi, hi, lo, lo) float4)
+constexpr int kFp64TabWords = 2;
 // the FP64 lanes of order P use the pair contractions (at p = 1, with three
 // modes, the splits and joins cost more than the FP64 contractions they replace)
 template <int P>
@@ -377,29 +386,57 @@ __host__ __device__ constexpr bool df_lanes() {
 }
 
 // An FP64 element block split for the pair contractions: the mean ub = phi_0 c_0
-// (FP64) and the modes j >= 1 as pairs.
+// (FP64) and the modes j >= 1 as pairs, two variables per float2 (k: the
+// variables 2k and 2k + 1).
 template <int P>
 struct DfBlock {
   double ub[4];
-  DF cd[4][TriDim<P>::NP - 1];
+  float2 ch[2][TriDim<P>::NP - 1], cl[2][TriDim<P>::NP - 1];
   __device__ __forceinline__ void init(const double (&c)[TriDim<P>::NV]) {
     constexpr int NP = TriDim<P>::NP;
     const double phi0 = tri_tab<double, P>().phiV[0][0];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      ub[m] = phi0 * c[m * NP];
+    for (int m = 0; m < 4; ++m) ub[m] = phi0 * c[m * NP];
 #pragma unroll
-      for (int j = 1; j < NP; ++j) cd[m][j - 1] = df_split(c[m * NP + j]);
-    }
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int j = 1; j < NP; ++j) {
+        const DF a = df_split(c[2 * k * NP + j]), b = df_split(c[(2 * k + 1) * NP + j]);
+        ch[k][j - 1] = make_float2(a.h, b.h);
+        cl[k][j - 1] = make_float2(a.l, b.l);
+      }
   }
 };
 
+// Pair accumulators of an element's modes, two variables per float2.
+template <int P>
+struct DfAcc {
+  float2 h[2][TriDim<P>::NP], l[2][TriDim<P>::NP];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int j = 0; j < TriDim<P>::NP; ++j) h[k][j] = l[k][j] = make_float2(0.0f, 0.0f);
+  }
+  // the value of variable m, mode j, in FP64
+  __device__ __forceinline__ double get(int m, int j) const {
+    const float2 a = h[m >> 1][j], b = l[m >> 1][j];
+    return (m & 1) ? df_join(DF{a.y, b.y}) : df_join(DF{a.x, b.x});
+  }
+};
+
+// split two FP64 values into a (hi pair, lo pair)
+__device__ __forceinline__ void df_split2(double x0, double x1, float2& h, float2& l) {
+  const DF a = df_split(x0), b = df_split(x1);
+  h = make_float2(a.h, b.h);
+  l = make_float2(a.l, b.l);
+}
+
 // Volume integral sum_q w_q (F(U_q) - F(ub)).(J^-T grad phi_j), j >= 1 (grad
-// phi_0 = 0), into the pair accumulators acc[m][j]; Fb, Gb = the x and y fluxes
-// of ub.
+// phi_0 = 0), into the pair accumulators; Fb, Gb = the x and y fluxes of ub.
 template <int P>
 __device__ __forceinline__ void volume_df(const DfBlock<P>& B, const double (&Fb)[4], const double (&Gb)[4],
-                                          const double* __restrict__ ji, DF (&acc)[4][TriDim<P>::NP]) {
+                                          const double* __restrict__ ji, DfAcc<P>& acc) {
   using D = TriDim<P>;
   constexpr int NP = D::NP;
   const TriDfTab<P>& T = tri_dftab<P>();
@@ -409,22 +446,26 @@ __device__ __forceinline__ void volume_df(const DfBlock<P>& B, const double (&Fb
   for (int q = 0; q < D::NQV; ++q) {
     double U[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      DF d{0.0f, 0.0f};
+    for (int k = 0; k < 2; ++k) {
+      float2 dh = make_float2(0.0f, 0.0f), dl = dh;
 #pragma unroll
-      for (int j = 1; j < NP; ++j) df_fma(d, T.phiV[q][j], B.cd[m][j - 1]);
-      U[m] = B.ub[m] + df_join(d);
+      for (int j = 1; j < NP; ++j) df_fma2(dh, dl, T.phiV[q][j], B.ch[k][j - 1], B.cl[k][j - 1]);
+      U[2 * k] = B.ub[2 * k] + df_join(DF{dh.x, dl.x});
+      U[2 * k + 1] = B.ub[2 * k + 1] + df_join(DF{dh.y, dl.y});
     }
     double F[4], G[4];
     euler_xy(U, F, G);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const double dF = F[m] - Fb[m], dG = G[m] - Gb[m];
-      const DF fr = df_split(j0.x * dF + j0.y * dG), fs = df_split(j1.x * dF + j1.y * dG);
+    for (int k = 0; k < 2; ++k) {
+      const double dF0 = F[2 * k] - Fb[2 * k], dG0 = G[2 * k] - Gb[2 * k];
+      const double dF1 = F[2 * k + 1] - Fb[2 * k + 1], dG1 = G[2 * k + 1] - Gb[2 * k + 1];
+      float2 frh, frl, fsh, fsl;
+      df_split2(j0.x * dF0 + j0.y * dG0, j0.x * dF1 + j0.y * dG1, frh, frl);
+      df_split2(j1.x * dF0 + j1.y * dG0, j1.x * dF1 + j1.y * dG1, fsh, fsl);
 #pragma unroll
       for (int j = 1; j < NP; ++j) {
-        df_fma(acc[m][j], T.vr[q][j], fr);
-        df_fma(acc[m][j], T.vs[q][j], fs);
+        df_fma2(acc.h[k][j], acc.l[k][j], T.vr[q][j], frh, frl);
+        df_fma2(acc.h[k][j], acc.l[k][j], T.vs[q][j], fsh, fsl);
       }
     }
   }
@@ -466,16 +507,13 @@ __device__ __forceinline__ void volume_acc64(const double (&c)[TriDim<P>::NV], c
   B.init(c);
   double Fb[4], Gb[4];
   euler_xy(B.ub, Fb, Gb);
-  DF a[4][NP];
-#pragma unroll
-  for (int m = 0; m < 4; ++m)
-#pragma unroll
-    for (int j = 0; j < NP; ++j) a[m][j] = DF{0.0f, 0.0f};
+  DfAcc<P> a;
+  a.zero();
   volume_df<P>(B, Fb, Gb, ji, a);
 #pragma unroll
   for (int m = 0; m < 4; ++m)
 #pragma unroll
-    for (int j = 1; j < NP; ++j) acc[m * NP + j] += df_join(a[m][j]);
+    for (int j = 1; j < NP; ++j) acc[m * NP + j] += a.get(m, j);
 }
 
 // FP32 volume integral in perturbation form: sum_q w_q dF(U_q).(J^-T grad phi_j),
@@ -732,10 +770,14 @@ __device__ __forceinline__ void stage_edge_tables(CT* sphi, CT* sw, int ntab = 3
   using D = TriDim<P>;
   const TriTab<CT, P>& K = tri_tab<CT, P>();
   if constexpr (sizeof(CT) == 8 && df_lanes<P>()) {
-    // the FP64 lanes read the edge tables as FP32 pairs (one 8-byte pair per entry)
+    // the FP64 lanes read the edge tables as FP32 pairs (hi, hi, lo, lo): 16 bytes
+    // per entry, so their buffers hold two doubles per entry (kFp64TabWords)
     const float2* src = &tri_dftab<P>().phiE[0][0][0];
-    float2* dst = reinterpret_cast<float2*>(sphi);
-    for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) dst[i] = src[i];
+    float4* dst = reinterpret_cast<float4*>(sphi);
+    for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) {
+      const float2 v = src[i];
+      dst[i] = make_float4(v.x, v.x, v.y, v.y);
+    }
   } else {
     const CT* src = &K.phiE[0][0][0];
     for (int i = threadIdx.x; i < ntab * D::NQE * D::NP; i += blockDim.x) sphi[i] = src[i];
@@ -1365,8 +1407,9 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 // and 2 (batches of four modes, three operand arrays) at 96; the first color
 // (volume integral) and the kernels reading an FP64 state (right-hand side
 // calls and comparators), which keep the element block in registers, at 128.
-// FP64 kernels at 168 (the pair contractions' registers; 2 % faster than 255
-// and 8 % faster than 128 at p = 3).
+// FP64 pair lanes at 168 at p = 2 and uncapped at p = 3 (measured, packed pair
+// updates: p = 2 RK step 12.06 ms at 168 against 12.89 at 255; p = 3 21.08 ms
+// at 255 against 21.27 at 200 and 21.65 at 168).
 #ifndef DGC_REGS_P3_FIRST
 #define DGC_REGS_P3_FIRST 128
 #endif
@@ -1388,9 +1431,12 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
 #ifndef DGC_REGS_FP64
 #define DGC_REGS_FP64 168
 #endif
+#ifndef DGC_REGS_FP64_P3
+#define DGC_REGS_FP64_P3 255
+#endif
 template <int P, typename CT, typename ST, typename RT, int MODE, int STG>
 constexpr int surf_regs() {
-  return sizeof(CT) == 8                        ? (df_lanes<P>() ? DGC_REGS_FP64 : 255)
+  return sizeof(CT) == 8                        ? (df_lanes<P>() ? (P == 3 ? DGC_REGS_FP64_P3 : DGC_REGS_FP64) : 255)
          : P == 3 && (sizeof(ST) == 8 || sizeof(RT) == 8 || MODE == SURF_FIRST) ? DGC_REGS_P3_FIRST
          : P == 3 && MODE == SURF_LAST && STG >= 1 ? DGC_REGS_P3_LAST12
          : P == 3 && MODE == SURF_LAST          ? DGC_REGS_P3_LAST
@@ -1438,7 +1484,7 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
     if constexpr (MODE == SURF_FIRST && STG == 0) block_min_to(best, A.estmin);
   } else {
     static_assert(S == 1, "FP64 lanes: one per edge side");
-    __shared__ double sphi[9 * D::NQE * D::NP];
+    __shared__ __align__(16) double sphi[kFp64TabWords * 9 * D::NQE * D::NP];
     __shared__ double sw[D::NQE];
     stage_edge_tables<P, double>(sphi, sw, A.ntab);
     __syncthreads();
@@ -1568,28 +1614,26 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
     }
     double Fb[4], Gb[4];  // the x and y fluxes of the element's mean
     euler_xy(B.ub, Fb, Gb);
-    DF acc2[4][NP];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc2[m][j] = DF{0.0f, 0.0f};
+    DfAcc<P> acc2;
+    acc2.zero();
     if constexpr (MODE == SURF_FIRST) volume_df<P>(B, Fb, Gb, A.jinv + 4 * elem, acc2);
     const double nx = g0.x, ny = g0.y, scale = right ? g1.y : -g1.x;
     double Fbn[4];  // F(ub).n, subtracted from the face flux (the volume integral omits F(ub))
 #pragma unroll
     for (int m = 0; m < 4; ++m) Fbn[m] = Fb[m] * nx + Gb[m] * ny;
-    const float2* ph = reinterpret_cast<const float2*>(sphi) + le * NQ * NP;
+    const float4* ph = reinterpret_cast<const float4*>(sphi) + le * NQ * NP;
     const DF sdf = df_split(scale);
     DGC_UNROLL_Q
     for (int q = 0; q < NQ; ++q) {
       const int qq = right ? NQ - 1 - q : q;  // the right element runs along the edge backwards
       double U[4], V[4], a[4], b[4], Fs[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        DF t{0.0f, 0.0f};
+      for (int k = 0; k < 2; ++k) {
+        float2 th = make_float2(0.0f, 0.0f), tl = th;
 #pragma unroll
-        for (int j = 1; j < NP; ++j) df_fma(t, ph[qq * NP + j], B.cd[m][j - 1]);
-        U[m] = B.ub[m] + df_join(t);
+        for (int j = 1; j < NP; ++j) df_fma2(th, tl, ph[qq * NP + j], B.ch[k][j - 1], B.cl[k][j - 1]);
+        U[2 * k] = B.ub[2 * k] + df_join(DF{th.x, tl.x});
+        U[2 * k + 1] = B.ub[2 * k + 1] + df_join(DF{th.y, tl.y});
       }
       // a boundary face's second lane holds the state outside it
       if (bnd && side && A.bc) bc_outside(A, tp.w, tri_tab<double, P>().tE[q], nx, ny, U);
@@ -1612,17 +1656,19 @@ __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 t
       }
       const DF sq = df_mul(sdf, df_split(sw[q]));
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const DF g = df_mul(sq, df_split(Fs[m] - Fbn[m]));
+      for (int k = 0; k < 2; ++k) {
+        const DF g0 = df_mul(sq, df_split(Fs[2 * k] - Fbn[2 * k]));
+        const DF g1 = df_mul(sq, df_split(Fs[2 * k + 1] - Fbn[2 * k + 1]));
+        const float2 gh = make_float2(g0.h, g1.h), gl = make_float2(g0.l, g1.l);
 #pragma unroll
-        for (int j = 0; j < NP; ++j) df_fma(acc2[m][j], ph[qq * NP + j], g);
+        for (int j = 0; j < NP; ++j) df_fma2(acc2.h[k][j], acc2.l[k][j], ph[qq * NP + j], gh, gl);
       }
     }
     double acc[NV];
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc[m * NP + j] = df_join(acc2[m][j]);
+      for (int j = 0; j < NP; ++j) acc[m * NP + j] = acc2.get(m, j);
     if constexpr (MODE != SURF_FIRST) {
       pdl_wait();
       pdl_trigger();
@@ -1889,7 +1935,7 @@ __global__ void __launch_bounds__(256) __maxnreg__((batch_regs<MODE, MIXED, STG>
   using ST = CT;
   // edge tables of the current order: FP32 in the mode-outer layout, FP64 as
   // [table][point][mode]
-  constexpr int TAB = MIXED ? 2 * 3 * ETab32<3>::BLK : 3 * TriDim<3>::NQE * TriDim<3>::NP;
+  constexpr int TAB = MIXED ? 2 * 3 * ETab32<3>::BLK : kFp64TabWords * 3 * TriDim<3>::NQE * TriDim<3>::NP;
   __shared__ __align__(16) CT sphi[TAB];
   __shared__ CT sw[TriDim<3>::NQE];
   int curp = 0;
@@ -2268,7 +2314,7 @@ __global__ void __launch_bounds__(128) __maxnreg__((sizeof(CT) == 8 ? 255 : surf
   using D = TriDim<P>;
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  constexpr int TAB = sizeof(CT) == 4 ? ETab32<P>::SIZE : 9 * D::NQE * D::NP;
+  constexpr int TAB = sizeof(CT) == 4 ? ETab32<P>::SIZE : kFp64TabWords * 9 * D::NQE * D::NP;
   __shared__ __align__(16) CT tab[TAB];
   __shared__ CT sw[D::NQE];
   if constexpr (sizeof(CT) == 4) stage_etab32<P>(reinterpret_cast<float*>(tab), C.A.ntab);
