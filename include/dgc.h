@@ -140,12 +140,13 @@ typedef enum {
  * stage of dgc_rk_step takes t, t + dt, t + dt/2 and the step advances it by
  * dt, on the device).  states: nstates (<= 8) conserved states of 4 doubles;
  * shock and shock_states may be NULL when no face is DGC_BC_SHOCK.  Host
- * arrays, copied.  The kernels that honour boundary conditions are the FP64
- * ones (dgc_rhs, dgc_rk_step, dgc_rk_step_static, the comparators); the FP32
- * forms, cooperative dgc_rhs and batches refuse a mesh with boundary
- * conditions other than transmissive, and so do dgc_refine and quadrilateral,
- * hybrid and tetrahedral meshes (DGC_ERR_UNSUPPORTED).  DGC_ERR_ARG on a bad
- * kind, state index or count. */
+ * arrays, copied.  Every precision form honours them in dgc_rhs, dgc_rk_step,
+ * dgc_rk_step_static and the comparators (the FP32 forms evaluate U+ in FP64
+ * and take it as a deviation from the element's reference state, like U-);
+ * cooperative dgc_rhs and batches refuse a mesh with boundary conditions other
+ * than transmissive, and so do dgc_refine and quadrilateral, hybrid and
+ * tetrahedral meshes (DGC_ERR_UNSUPPORTED).  DGC_ERR_ARG on a bad kind, state
+ * index or count. */
 dgc_status dgc_set_boundary(dgc_mesh* mesh, const int8_t* kind, const int8_t* state_idx, int nstates,
                             const double* states, const double* shock, const int8_t* shock_states);
 

@@ -648,7 +648,7 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
     for (int s = 0; s < 3; ++s) {
       Ctx xs_ = x;
       xs_.tfrac = TF[s];
-      xs_.dtp = dt;
+      xs_.dtp = s == 0 ? nullptr : dt;  // stage 0 runs at the step's start, before dt is known
       const Ctx& x = xs_;
       double* us = s == 0 ? c64 : w.u1;
       StageArgs sa;
@@ -691,7 +691,12 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
   const bool first_est = fused && !kahan && m.dim == 2 && !m.quad;
   if (kahan) launch(DGC_K_CFL, [&] { return tri_cfl_kahan(x, ks, cfl_, dt); });
   else if (!first_est) launch(DGC_K_CFL, [&] { return cfl(x, static_cast<double*>(c), cfl_, dt, w.rec0); });
+  const double TF[3] = {0.0, 1.0, 0.5};  // the stages' times, in units of dt from the step's start
   for (int s = 0; s < 3; ++s) {
+    Ctx xs_ = x;
+    xs_.tfrac = TF[s];
+    xs_.dtp = s == 0 ? nullptr : dt;  // stage 0 runs at the step's start, before dt is known
+    const Ctx& x = xs_;
     const float* in = s == 0 ? rec0 : w.recs;
     const int ss = s == 0 ? rec0_stride : nf;
     StageArgs sa;
@@ -729,6 +734,7 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
       launch(DGC_K_STAGE, [&] { return incr_stage_update(x, static_cast<const float*>(w.rhs), sa); });
     }
   }
+  if (m.has_bc) launch(DGC_K_LIMIT, [&] { return time_advance(x, dt); });
 }
 
 }  // namespace
@@ -962,9 +968,7 @@ static void require_prec(const Mesh& m, dgc_prec prec) {
   require(!m.hybrid || prec == DGC_FP64, "hybrid triangle/quadrilateral meshes run in FP64", DGC_ERR_UNSUPPORTED);
   require(prec != DGC_FP32_KAHAN || (m.dim == 2 && !m.quad), "the Kahan form is implemented for triangle meshes",
           DGC_ERR_UNSUPPORTED);
-  require(prec == DGC_FP64 || (!m.has_bc && !m.limit),
-          "boundary conditions and the limiter run in FP64 (the FP32 forms keep transmissive boundaries)",
-          DGC_ERR_UNSUPPORTED);
+  require(prec == DGC_FP64 || !m.limit, "the limiter runs in FP64", DGC_ERR_UNSUPPORTED);
 }
 
 // bytes of one device state of the given precision form

@@ -693,6 +693,87 @@ struct SurfParams {
   double tfrac = 0.0;
 };
 
+// The state outside a boundary face at its edge point q, taken by the second
+// lane of the face's pair in place of its own trace (dgc_set_boundary; tp.w =
+// kind | state << 4 | boundary face << 8): a slip wall reverses the normal
+// momentum, a state face takes its prescribed state, a shock face the state
+// behind the moving shock where x < a + b y + c t, else the state ahead;
+// transmissive faces keep U (U+ = U-).
+__device__ __forceinline__ void bc_outside(const SurfParams& A, int w, double tq, double nx, double ny, double* U) {
+  const int kind = w & 15;
+  if (kind == DGC_BC_WALL) {
+    const double mn = U[1] * nx + U[2] * ny;
+    U[1] -= 2.0 * mn * nx;
+    U[2] -= 2.0 * mn * ny;
+  } else if (kind == DGC_BC_STATE || kind == DGC_BC_SHOCK) {
+    int s = (w >> 4) & 15;
+    if (kind == DGC_BC_SHOCK) {
+      const BndGeo g = A.bgeo[w >> 8];
+      const double x = g.x0 + tq * g.dx, y = g.y0 + tq * g.dy;
+      const double t = *A.t0 + (A.dtp ? A.tfrac * *A.dtp : 0.0);
+      const double* sh = A.bc + kBcShock;
+      s = x < sh[0] + sh[1] * y + sh[2] * t ? (int)sh[3] : (int)sh[4];
+    }
+    const double* S = A.bc + kBcStates + 4 * s;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) U[m] = S[m];
+  }
+}
+
+// The same for the FP32 lanes, on the edge coefficients ak of the trace's
+// deviation t(xi) = sum_k L_k(xi) ak[k] (L_0 = 1) from the element's reference
+// ub, before the point loop: the outside state relative to the same reference
+// is affine in t for a wall (the momentum of ub + t reflected) and constant for
+// a prescribed state (S - ub), so both map the coefficients.  A shock face's
+// state is piecewise constant along the edge and replaces the trace whole: the
+// function returns true, and the coefficient registers, no longer needed, carry
+// the line f(tq) = al + be tq (negative where the point lies behind the shock)
+// as the bits of two doubles in ak[0] (no register held across the point loop
+// for it); bc_shock32 then sets each point's deviation.
+template <int K1>
+__device__ __forceinline__ bool bc_modal32(const SurfParams& A, int w, float nx, float ny, const float* ub,
+                                           float (&ak)[K1][4]) {
+  const int kind = w & 15;
+  if (kind == DGC_BC_WALL) {
+#pragma unroll
+    for (int kk = 0; kk < K1; ++kk) {
+      const float mn = kk == 0 ? (ub[1] + ak[0][1]) * nx + (ub[2] + ak[0][2]) * ny : ak[kk][1] * nx + ak[kk][2] * ny;
+      ak[kk][1] -= 2.0f * mn * nx;
+      ak[kk][2] -= 2.0f * mn * ny;
+    }
+  } else if (kind == DGC_BC_STATE) {
+    const double* S = A.bc + kBcStates + 4 * ((w >> 4) & 15);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      ak[0][m] = d2f(S[m] - (double)ub[m]);
+#pragma unroll
+      for (int kk = 1; kk < K1; ++kk) ak[kk][m] = 0.0f;
+    }
+  } else if (kind == DGC_BC_SHOCK) {
+    const BndGeo g = A.bgeo[w >> 8];
+    const double t = *A.t0 + (A.dtp ? A.tfrac * *A.dtp : 0.0);
+    const double* sh = A.bc + kBcShock;
+    const double al = g.x0 - sh[0] - sh[1] * g.y0 - sh[2] * t, be = g.dx - sh[1] * g.dy;
+    ak[0][0] = __int_as_float(__double2hiint(al)), ak[0][1] = __int_as_float(__double2loint(al));
+    ak[0][2] = __int_as_float(__double2hiint(be)), ak[0][3] = __int_as_float(__double2loint(be));
+    return true;
+  }
+  return false;
+}
+
+// a shock face's deviation at the edge point tq: the state behind the shock
+// where al + be tq < 0, else the state ahead, minus the reference (a0: the
+// line's bits, as bc_modal32 left them)
+__device__ __forceinline__ void bc_shock32(const SurfParams& A, const float (&a0)[4], double tq, const float* ub,
+                                           float* t) {
+  const double al = __hiloint2double(__float_as_int(a0[0]), __float_as_int(a0[1]));
+  const double be = __hiloint2double(__float_as_int(a0[2]), __float_as_int(a0[3]));
+  const double* sh = A.bc + kBcShock;
+  const double* S = A.bc + kBcStates + 4 * (int)(fma(be, tq, al) < 0.0 ? sh[3] : sh[4]);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) t[m] = d2f(S[m] - (double)ub[m]);
+}
+
 // the contribution of one lane's element is in acc; write it as the mode asks
 template <int P, typename RT, int MODE, typename AT>
 __device__ __forceinline__ void surf_write(const SurfParams& A, int64_t elem, int64_t k, int side,
@@ -1087,7 +1168,7 @@ __host__ __device__ constexpr int mode_split() {
 // points sub, sub + 2, ... and the volume points likewise, their sums are
 // combined across the two lanes, and each lane writes its share of the modes
 // (mode_split).  FP32 right-hand sides of the colored modes only.
-template <int P, typename ST, typename RT, int MODE, int STG = -1, int S = 1>
+template <int P, typename ST, typename RT, int MODE, int STG = -1, int S = 1, bool BC = false>
 __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
                                           const float* se, float* rslot = nullptr, float* best = nullptr,
                                           int sub = 0) {
@@ -1177,6 +1258,9 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
 #pragma unroll
       for (int m = 0; m < 4; ++m) ak[kk][m] = fmaf(tr[kk], c[m], ak[kk][m]);
   }
+  // the second lane of a boundary face: the outside state (the face normal is g0)
+  bool shk = false;
+  if constexpr (BC) shk = bnd && side && bc_modal32<K1>(A, tp.w, d2f(g0.x), d2f(g0.y), R.u, ak);
 
   if constexpr (MODE == SURF_FIRST) {
     // First color: the volume integral, then the edge's points one at a time
@@ -1235,6 +1319,7 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
         for (int kk = 1; kk < K1; ++kk) v = fmaf(L[kk], ak[kk][m], v);
         t[m] = v;
       }
+      if (BC && shk) bc_shock32(A, ak[0], tri_tab<double, P>().tE[q], R.u, t);
       lf_exchange<2>(R, E, t, G);
       const float s = q0 < NQ ? escale * K.wE[q] : 0.0f;
 #pragma unroll
@@ -1295,6 +1380,7 @@ __device__ __forceinline__ void surf_fp32(const SurfParams& A, int64_t k, int4 t
         for (int kk = 1; kk < K1; ++kk) v = fmaf(EK.Lq[q][kk], ak[kk][m], v);
         t[m] = v;
       }
+      if (BC && shk) bc_shock32(A, ak[0], tri_tab<double, P>().tE[q], R.u, t);
       lf_exchange<2>(R, E, t, G);
       const float s = q0 < NQ ? escale * K.wE[q] : 0.0f;
 #pragma unroll
@@ -1447,7 +1533,10 @@ constexpr int surf_regs() {
                                                 : 128;
 }
 
-template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, int S = 1>
+// BC: the FP32 lanes honour boundary conditions (A.bc set; the FP64 lanes test
+// A.bc at run time).  Meshes without take BC = false, whose point loops carry
+// no boundary code.
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, int S = 1, bool BC = false>
 __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MODE, STG>())) k_surf_tri(const SurfParams A) {
   using D = TriDim<P>;
   // lanes 2S e .. 2S e + 2S - 1 take edge e: side = bit 0, the lane of the side bit 1 (S = 2)
@@ -1474,10 +1563,10 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
       const int4 tp = A.topo[k];
       if constexpr (MODE == SURF_FIRST && STG == 0) {
         float b = FLT_MAX;
-        surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, &b, sub);
+        surf_fp32<P, ST, RT, MODE, STG, S, BC>(A, k, tp, valid, side, se, rslot, &b, sub);
         best = fminf(best, b);
       } else {
-        surf_fp32<P, ST, RT, MODE, STG, S>(A, k, tp, valid, side, se, rslot, nullptr, sub);
+        surf_fp32<P, ST, RT, MODE, STG, S, BC>(A, k, tp, valid, side, se, rslot, nullptr, sub);
       }
       if (!step) break;
     }
@@ -1499,33 +1588,6 @@ __global__ void __launch_bounds__(256) __maxnreg__((surf_regs<P, CT, ST, RT, MOD
   }
 }
 
-
-// The state outside a boundary face at its edge point q, taken by the second
-// lane of the face's pair in place of its own trace (dgc_set_boundary; tp.w =
-// kind | state << 4 | boundary face << 8): a slip wall reverses the normal
-// momentum, a state face takes its prescribed state, a shock face the state
-// behind the moving shock where x < a + b y + c t, else the state ahead;
-// transmissive faces keep U (U+ = U-).
-__device__ __forceinline__ void bc_outside(const SurfParams& A, int w, double tq, double nx, double ny, double* U) {
-  const int kind = w & 15;
-  if (kind == DGC_BC_WALL) {
-    const double mn = U[1] * nx + U[2] * ny;
-    U[1] -= 2.0 * mn * nx;
-    U[2] -= 2.0 * mn * ny;
-  } else if (kind == DGC_BC_STATE || kind == DGC_BC_SHOCK) {
-    int s = (w >> 4) & 15;
-    if (kind == DGC_BC_SHOCK) {
-      const BndGeo g = A.bgeo[w >> 8];
-      const double x = g.x0 + tq * g.dx, y = g.y0 + tq * g.dy;
-      const double t = *A.t0 + (A.dtp ? A.tfrac * *A.dtp : 0.0);
-      const double* sh = A.bc + kBcShock;
-      s = x < sh[0] + sh[1] * y + sh[2] * t ? (int)sh[3] : (int)sh[4];
-    }
-    const double* S = A.bc + kBcStates + 4 * s;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) U[m] = S[m];
-  }
-}
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
 __device__ __forceinline__ void surf_pair(const SurfParams& A, int64_t k, int4 tp, bool valid, int side,
@@ -2158,7 +2220,7 @@ int tri_volume(const Ctx& x, TypeCfg ty, const void* s, int sstride, void* r, in
 // the tile class of a surface mode: first, middle, last color (comparators: middle)
 constexpr int tile_class(int mode) { return mode == SURF_FIRST ? 0 : mode == SURF_LAST ? 2 : 1; }
 
-template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, int S = 1>
+template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1, int S = 1, bool BC = false>
 static int surf_launch_s(const Ctx& x, const SurfParams& A) {
   const int64_t n = A.end - A.begin;
   if (n <= 0) return 0;
@@ -2174,7 +2236,7 @@ static int surf_launch_s(const Ctx& x, const SurfParams& A) {
     static int per = -1, per_threads = -1;
     if (per_threads != threads) {
       int occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_surf_tri<P, CT, ST, RT, MODE, STG, S>, threads, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_surf_tri<P, CT, ST, RT, MODE, STG, S, BC>, threads, smem);
       per = occ > 0 ? occ : 1;
       per_threads = threads;
     }
@@ -2187,12 +2249,12 @@ static int surf_launch_s(const Ctx& x, const SurfParams& A) {
   if (smem > 32 * 1024) {  // 256-thread blocks: above the default 48 KB with the static tables
     static bool raised = false;
     if (!raised) {
-      cudaFuncSetAttribute(k_surf_tri<P, CT, ST, RT, MODE, STG, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_surf_tri<P, CT, ST, RT, MODE, STG, S, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            64 * 1024);
       raised = true;
     }
   }
-  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG, S>, (unsigned)grid, (unsigned)threads, smem, B);
+  launch_k(x, k_surf_tri<P, CT, ST, RT, MODE, STG, S, BC>, (unsigned)grid, (unsigned)threads, smem, B);
   return 1;
 }
 
@@ -2200,6 +2262,9 @@ static int surf_launch_s(const Ctx& x, const SurfParams& A) {
 // per edge (2 or 4); every other kernel has one lane per edge side.
 template <int P, typename CT, typename ST, typename RT, int MODE, int STG = -1>
 static int surf_launch(const Ctx& x, const SurfParams& A) {
+  // boundary conditions on the FP32 lanes: their instantiation, one lane per side
+  if constexpr (sizeof(CT) == 4)
+    if (A.bc) return surf_launch_s<P, CT, ST, RT, MODE, STG, 1, true>(x, A);
   if constexpr (sizeof(CT) == 4 && sizeof(RT) == 4) {
     if (x.tile_tpe[tile_class(MODE)] == 4) return surf_launch_s<P, CT, ST, RT, MODE, STG, 2>(x, A);
   }
@@ -2406,6 +2471,11 @@ int tri_first_est(const Ctx& x, int64_t begin, int64_t end, const double* c, flo
   A.est = x.d->cfl_est;
   A.estmin = mn;
   A.inr = x.d->inr;
+  A.bc = x.d->bc;
+  A.bgeo = x.d->bgeo;
+  A.t0 = x.d->time;
+  A.dtp = x.dtp;
+  A.tfrac = x.tfrac;
   switch (x.p) {
     case 1: return surf_launch<1, float, double, float, SURF_FIRST, 0>(x, A);
     case 2: return surf_launch<2, float, double, float, SURF_FIRST, 0>(x, A);

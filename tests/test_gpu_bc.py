@@ -3,12 +3,14 @@
 states, the moving incident shock and a limiter after every RK stage; readings
 of [giuliani], dg_oracle.c bc_state / orc_limit) against the oracle, FP64.
 
-Tolerances: right-hand side 1e-12 relative L2 (colored, atomic, two-pass);
+Tolerances: FP64 right-hand side 1e-12 relative L2 (colored, atomic, two-pass),
+FP32-mixed 1e-5; the FP32 forms' RK step (boundary conditions, no limiter)
+1e-5;
 the limiter alone 1e-13; one limited RK step's state change 1e-11; ten
 limited steps of the double Mach setup 1e-10 (per-element max as in
 tests/_parity.py); dt and the advanced time 1e-13.  The allocation-free step
-is bit-identical to the regular one.  The FP32 forms, batches, refinement and
-the cooperative right-hand side refuse boundary conditions.
+is bit-identical to the regular one.  Batches, refinement and the cooperative
+right-hand side refuse boundary conditions, and the FP32 forms the limiter.
 """
 
 import numpy as np
@@ -35,7 +37,7 @@ class Run:
     """A double Mach-type mesh with its boundary conditions on the device and
     in the oracle."""
 
-    def __init__(self, torch_dev, oracle_mod, mi, p, limiter=False, seed=1601):
+    def __init__(self, torch_dev, oracle_mod, mi, p, limiter=False, seed=1601, states=None):
         self.torch, self.dev = torch_dev
         self.p = p
         self.m = dgc.Mesh.from_input(mi, p)
@@ -46,7 +48,7 @@ class Run:
         assert np.array_equal(l, lo) and np.array_equal(r, ro) and np.array_equal(ql, qlo)
         kind, sidx = W.double_mach_boundary(mi, l, r, ql)
         self.kind = kind
-        S = W.double_mach_states()
+        S = W.double_mach_states() if states is None else states
         dgc.dgc_set_boundary(self.m.h, kind, sidx, S, W.DMR_SHOCK, (0, 1))
         self.om.set_bc(kind, sidx, S, W.DMR_SHOCK, (0, 1))
         if limiter:
@@ -64,19 +66,19 @@ class Run:
         xyz, _, _ = self.om.eval_points(self.p)
         return self.om.limit(self.p, self.om.project(self.p, W.double_mach_field(xyz[..., 0], xyz[..., 1])))
 
-    def rhs(self, c, kind="colored"):
+    def rhs(self, c, kind="colored", prec=FP64):
         T = self.torch
         dgc.dgc_import_state(self.m.h, c, self.c)
         self.r.fill_(float("nan"))
         if kind == "colored":
-            dgc.dgc_rhs(self.m.h, FP64, self.c, self.r)
+            dgc.dgc_rhs(self.m.h, prec, self.c, self.r)
         elif kind == "atomic":
-            dgc.dgc_rhs_atomic(self.m.h, FP64, self.c, self.r)
+            dgc.dgc_rhs_atomic(self.m.h, prec, self.c, self.r)
         else:
             info = self.m.info
             nb = dgc.dgc_two_pass_buffer_bytes(info["ns"], info["np"], info["M"], 8)
             buf = T.empty(nb // 8, dtype=T.float64, device=self.dev)
-            dgc.dgc_rhs_two_pass(self.m.h, FP64, self.c, self.r, buf)
+            dgc.dgc_rhs_two_pass(self.m.h, prec, self.c, self.r, buf)
         T.cuda.synchronize()
         return dgc.dgc_export_state(self.m.h, self.r)
 
@@ -103,6 +105,16 @@ def _mesh(nx=32, ny=8, seed=21):
     return W.open_rect_tri(nx, ny, 4.0, 1.0, jitter=0.2, seed=seed)
 
 
+def _conserved(rho, u, v, pr):
+    return [rho, rho * u, rho * v, pr / 0.4 + 0.5 * rho * (u * u + v * v)]
+
+
+# Prescribed states near the smooth field below, for the unlimited RK steps:
+# the double Mach states (density 8 behind a Mach 10 shock) against that field
+# make a discontinuity that an unlimited step turns non-physical.
+MILD_STATES = np.array([_conserved(1.6, 1.1, -0.6, 2.1), _conserved(1.4, 0.9, -0.8, 1.9)])
+
+
 def _smooth(run, seed):
     """A positive smooth state with large velocities at every boundary."""
     xyz, _, _ = run.om.eval_points(run.p)
@@ -125,6 +137,57 @@ def test_boundary_rhs_matches_oracle(torch_dev, oracle_mod, p):
     ref = run.om.rhs(p, c)
     for kind in ("colored", "atomic", "two_pass"):
         check(run.rhs(c, kind), ref, 1e-12, f"boundary rhs {kind} p = {p}")
+    run.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_boundary_rhs_fp32_matches_oracle(torch_dev, oracle_mod, p):
+    """The FP32-mixed right-hand side with the same boundaries: the second lane
+    of a boundary face evaluates the outside state as a deviation from the
+    element's reference (walls mirror it, state and shock faces replace it)."""
+    run = Run(torch_dev, oracle_mod, _mesh(), p)
+    run.set_time(0.05)
+    c = _smooth(run, 20 + p)
+    ref = run.om.rhs(p, c)
+    for kind in ("colored", "atomic", "two_pass"):
+        check(run.rhs(c, kind, dgc.DGC_FP32_MIXED), ref, 1e-5, f"boundary rhs FP32 {kind} p = {p}")
+    run.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("fuse", [True, False])
+def test_boundary_rk_step_fp32_matches_oracle(torch_dev, oracle_mod, p, fuse):
+    """The FP32 forms' RK step with boundaries (no limiter): the state change
+    against the oracle's, and the mesh's time advanced by dt.  Walls, the
+    transmissive outflow and a moving shock between two prescribed states
+    near the smooth field (the stage times t, t + dt, t + dt / 2 move the
+    shock's foot along the bottom)."""
+    run = Run(torch_dev, oracle_mod, _mesh(seed=25), p, states=MILD_STATES)
+    dgc.dgc_set_option(run.m.h, dgc.DGC_OPT_FUSE, int(fuse))
+    c = _smooth(run, 30 + p)
+    T = run.torch
+    for prec in (dgc.DGC_FP32_MIXED, dgc.DGC_FP32_KAHAN):
+        run.set_time(0.05)
+        ref, dt_ref = run.om.rk_step(p, c, 0.3)
+        assert np.isfinite(ref).all()
+        d = T.zeros(1, dtype=T.float64, device=run.dev)
+        ws = T.empty(dgc.dgc_workspace_size(run.m.h, prec) // 8 + 64, dtype=T.float64, device=run.dev)
+        if prec == dgc.DGC_FP32_KAHAN:
+            k = T.empty(dgc.dgc_state_bytes(run.m.h, prec) // 4, dtype=T.float32, device=run.dev)
+            dgc.dgc_import_state_prec(run.m.h, prec, c, k)
+            dgc.dgc_rk_step(run.m.h, prec, k, 0.3, d, ws)
+            T.cuda.synchronize()
+            got = dgc.dgc_export_state_prec(run.m.h, prec, k)
+        else:
+            dgc.dgc_import_state(run.m.h, c, run.c)
+            dgc.dgc_rk_step(run.m.h, prec, run.c, 0.3, d, ws)
+            T.cuda.synchronize()
+            got = dgc.dgc_export_state(run.m.h, run.c)
+        dt = float(d.item())
+        assert abs(dt - dt_ref) < 1e-12 * dt_ref
+        check(got - c, ref - c, 1e-5, f"FP32 RK step with boundaries, prec {prec}, p = {p}")
+        t = dgc.dgc_get_time(run.m.h)
+        assert abs(t - run.om.time()) < 1e-13 * t
     run.close()
 
 

@@ -299,7 +299,7 @@ def test_buffer_sizes_are_checked_before_device_work(L):
 def test_boundary_arguments_are_checked_on_the_host(L):
     """dgc_set_boundary validates kinds, state indices and the shock before any
     device work; quadrilateral meshes refuse it; the time round-trips on the
-    host before the first upload."""
+    host before the first upload; the FP32 forms refuse the limiter."""
     mi = W.open_rect_tri(8, 2, 4.0, 1.0)
     m = dgc.Mesh.from_input(mi, 1)
     m.color(1)
@@ -321,6 +321,7 @@ def test_boundary_arguments_are_checked_on_the_host(L):
     assert e.value.status == 1
     dgc.dgc_set_time(m.h, 0.125)
     assert dgc.dgc_get_time(m.h) == 0.125
+    dgc.dgc_set_option(m.h, dgc.DGC_OPT_LIMITER, 1)  # the limiter runs in FP64 only
     with pytest.raises(dgc.DgcError) as e:
         dgc.dgc_rhs(m.h, dgc.DGC_FP32_MIXED, 4096, 8192, 0)
     assert e.value.status == 4
