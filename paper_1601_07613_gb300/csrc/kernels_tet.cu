@@ -7,7 +7,9 @@
 // evaluates its basis through one of six orientation tables (the face's
 // vertex permutation is stored per face).  FP64 kernels evaluate Eq. 2 as
 // written, FP32 kernels in the perturbation form of euler_pert.cuh.
+#include <algorithm>
 #include <cfloat>
+#include <cmath>
 
 #include "dev_util.cuh"
 #include "device.cuh"
@@ -21,6 +23,7 @@ struct TetDim {
   static constexpr int NP = (P + 1) * (P + 2) * (P + 3) / 6;
   static constexpr int NQV = (P + 2) * (P + 2) * (P + 2);
   static constexpr int NQF = (P + 2) * (P + 2);
+  static constexpr int KF = (P + 1) * (P + 2) / 2;  // polynomials of degree P on a face
   static constexpr int M = 5;
   static constexpr int NV = M * NP;
   // FP32 record: hi[M], lo[M], modes j >= 1 as [M][NP-1], padded to 4 floats
@@ -107,17 +110,98 @@ static void upload_tet_pairs(const RefTables& R, const void* sym) {
   cudaMemcpyToSymbol(sym, &h, sizeof h);
 }
 
+// Face-modal traces of the FP32 lanes.  The traces of the element's basis on a
+// face span the polynomials of degree p on that face.  psi_k (k < KF) is a
+// basis of that space orthonormal under the face rule (Gram-Schmidt on the
+// traces through local face 0 at the face points); the trace of phi_j seen
+// through local face f and orientation o is then sum_k T[f][o][k][j] psi_k, with
+// T = sum_q w_q psi_k(q) phi_j(q), exactly at the face points (the rule
+// integrates degree 2p exactly).  So a lane evaluates its trace from KF face
+// coefficients a_k = sum_j T[k][j] c_j, projects its flux onto the psi_k, and
+// maps the KF projections back to its modes with T's transpose.
+template <int P>
+struct TetFaceTab {
+  float psi[TetDim<P>::NQF][TetDim<P>::KF];
+  float2 psi2[TetDim<P>::NQF][TetDim<P>::KF];  // (psi, psi) for the packed FMA
+};
+__constant__ TetFaceTab<1> cTetM1;
+__constant__ TetFaceTab<2> cTetM2;
+template <int P>
+__device__ __forceinline__ const TetFaceTab<P>& tet_mtab();
+template <> __device__ __forceinline__ const TetFaceTab<1>& tet_mtab<1>() { return cTetM1; }
+template <> __device__ __forceinline__ const TetFaceTab<2>& tet_mtab<2>() { return cTetM2; }
+
+// psi [NQF][KF] and T [4][6][KF][NP] from the orientation tables t [4][6][NQF][NP]
+static void tet_face_modal(const std::vector<double>& t, const RefTables& R, std::vector<double>& psi,
+                           std::vector<double>& T) {
+  const int nq = R.nqf, np = R.np, kf = (R.p + 1) * (R.p + 2) / 2;
+  auto dot = [&](const double* f, const double* g) {
+    double v = 0.0;
+    for (int q = 0; q < nq; ++q) v += R.fw[q] * f[q] * g[q];
+    return v;
+  };
+  std::vector<double> basis;  // [k][q]
+  std::vector<double> v(nq);
+  for (int j = 0; j < np && (int)(basis.size() / nq) < kf; ++j) {
+    for (int q = 0; q < nq; ++q) v[q] = t[(size_t)q * np + j];
+    const double n0 = std::sqrt(dot(v.data(), v.data()));
+    for (int pass = 0; pass < 2; ++pass)
+      for (size_t k = 0; k < basis.size() / nq; ++k) {
+        const double c = dot(v.data(), basis.data() + k * nq);
+        for (int q = 0; q < nq; ++q) v[q] -= c * basis[k * nq + q];
+      }
+    const double n1 = std::sqrt(dot(v.data(), v.data()));
+    if (n1 > 1e-8 * n0)
+      for (int q = 0; q < nq; ++q) basis.push_back(v[q] / n1);
+  }
+  if ((int)(basis.size() / nq) != kf) throw Error{DGC_ERR_UNSUPPORTED, "face-modal basis: wrong rank (internal)"};
+  psi.assign((size_t)nq * kf, 0.0);
+  for (int q = 0; q < nq; ++q)
+    for (int k = 0; k < kf; ++k) psi[(size_t)q * kf + k] = basis[(size_t)k * nq + q];
+  T.assign((size_t)24 * kf * np, 0.0);
+  for (int fo = 0; fo < 24; ++fo)
+    for (int j = 0; j < np; ++j) {
+      const double* ph = t.data() + (size_t)fo * nq * np;
+      for (int q = 0; q < nq; ++q) v[q] = ph[(size_t)q * np + j];
+      double err = 0.0, mx = 0.0;
+      for (int k = 0; k < kf; ++k) T[((size_t)fo * kf + k) * np + j] = dot(basis.data() + (size_t)k * nq, v.data());
+      for (int q = 0; q < nq; ++q) {
+        double r = v[q];
+        for (int k = 0; k < kf; ++k) r -= T[((size_t)fo * kf + k) * np + j] * psi[(size_t)q * kf + k];
+        err = std::max(err, std::fabs(r));
+        mx = std::max(mx, std::fabs(v[q]));
+      }
+      if (err > 1e-11 * (1.0 + mx)) throw Error{DGC_ERR_UNSUPPORTED, "face-modal traces: not exact at the face points (internal)"};
+    }
+}
+
+template <int P>
+static void upload_tet_modal(const std::vector<double>& psi, const void* sym) {
+  static TetFaceTab<P> h;
+  for (int q = 0; q < TetDim<P>::NQF; ++q)
+    for (int k = 0; k < TetDim<P>::KF; ++k) {
+      const float v = (float)psi[(size_t)q * TetDim<P>::KF + k];
+      h.psi[q][k] = v;
+      h.psi2[q][k] = make_float2(v, v);
+    }
+  cudaMemcpyToSymbol(sym, &h, sizeof h);
+}
+
 void tet_upload_tables(int p, const RefTables& R, DeviceMesh& d) {
   if (R.dim != 3 || R.p != p) return;
   if (p == 1) upload_tet_p<1>(R, &cTetD1, &cTetF1);
   if (p == 2) upload_tet_p<2>(R, &cTetD2, &cTetF2);
   if (p == 1) upload_tet_pairs<1>(R, &cTetP1);
   if (p == 2) upload_tet_pairs<2>(R, &cTetP2);
-  // orientation tables for the faces, FP64 and FP32 copies, in global memory
-  std::vector<double> t = tet_face_orient_tables(R);
-  std::vector<float> tf(t.begin(), t.end());
+  // orientation tables for the faces (FP64) and the FP32 lanes' face-modal
+  // tables T [4][6][KF][NP], in global memory
+  std::vector<double> t = tet_face_orient_tables(R), psi, T;
+  tet_face_modal(t, R, psi, T);
+  if (p == 1) upload_tet_modal<1>(psi, &cTetM1);
+  if (p == 2) upload_tet_modal<2>(psi, &cTetM2);
+  std::vector<float> tf(T.begin(), T.end());
   if (cudaMalloc(&d.ftabd, sizeof(double) * t.size()) != cudaSuccess ||
-      cudaMalloc(&d.ftab, sizeof(float) * t.size()) != cudaSuccess)
+      cudaMalloc(&d.ftab, sizeof(float) * tf.size()) != cudaSuccess)
     throw Error{DGC_ERR_OOM, "cudaMalloc (face tables)"};
   cudaMemcpy(d.ftabd, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d.ftab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice);
@@ -448,7 +532,7 @@ struct TetParams {
   const int4* topo;
   const double2* fgeo;
   const double* jinv;
-  const void* ftab;  // [4][6][NQF][NP] of CT (FP64 kernels: FP32 pairs)
+  const void* ftab;  // FP64: [4][6][NQF][NP] as FP32 pairs; FP32: the face-modal T [4][6][KF][NP]
   const float2* vtab = nullptr;  // FP64 first color: the pair volume tables [4][NQV][NP]
   const void* state;
   void* rhs;
@@ -483,6 +567,37 @@ __device__ __forceinline__ void tet_write(const TetParams& A, int64_t elem, int6
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = (RT)acc[i];
     tstore(static_cast<RT*>(A.buf) + (2 * k + side) * NV, out);
+  }
+}
+
+// One variable's NP values of a lane's contribution, written as the mode asks
+// (the FP32 lanes but the last color's)
+template <int P, typename RT, int MODE>
+__device__ __forceinline__ void tet_write_var(const TetParams& A, int64_t elem, int64_t k, int side, int m,
+                                              const float (&cm)[TetDim<P>::NP]) {
+  constexpr int NP = TetDim<P>::NP, NV = TetDim<P>::NV;
+  static_assert(NP % 2 == 0, "one variable's block: 8-byte (float) or 16-byte (double) vectors");
+  if constexpr (MODE == SURF_FIRST) {
+    RT out[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) out[j] = (RT)cm[j];
+    tstore(static_cast<RT*>(A.rhs) + elem * NV + m * NP, out);
+  } else if constexpr (MODE == SURF_RMW) {
+    RT* r = static_cast<RT*>(A.rhs) + elem * NV + m * NP;
+    RT old[NP];
+    tload(r, old);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) old[j] += (RT)cm[j];
+    tstore(r, old);
+  } else if constexpr (MODE == SURF_ATOMIC) {
+    RT* r = static_cast<RT*>(A.rhs) + elem * NV + m * NP;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) atomicAdd(r + j, (RT)cm[j]);
+  } else if constexpr (MODE == SURF_BUFFER) {
+    RT out[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) out[j] = (RT)cm[j];
+    tstore(static_cast<RT*>(A.buf) + (2 * k + side) * NV + m * NP, out);
   }
 }
 
@@ -531,20 +646,33 @@ __device__ __forceinline__ void tet_fp64_last(const TetParams& A, int64_t elem, 
 #ifndef DGC_TET_REGS
 #define DGC_TET_REGS 168
 #endif
+#ifndef DGC_TET_QUNROLL
+#define DGC_TET_QUNROLL 2
+#endif
+#define DGC_TET_PRAGMA(x) _Pragma(#x)
+#define DGC_TET_PRAGMA2(x) DGC_TET_PRAGMA(x)
+#define DGC_TET_UNROLL_Q DGC_TET_PRAGMA2(unroll DGC_TET_QUNROLL)
+#ifndef DGC_TET_REGS_COLOR
+#define DGC_TET_REGS_COLOR 128
+#endif
 #ifndef DGC_TET_MINB
 #define DGC_TET_MINB 1
 #endif
 
 template <int P, typename CT, typename ST, typename RT, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
-    __maxnreg__((sizeof(CT) == 4 ? DGC_TET_REGS : 255)) k_surf_tet(const TetParams A) {
+    __maxnreg__((sizeof(CT) == 4 ? (MODE == SURF_FIRST || MODE == SURF_LAST ? DGC_TET_REGS : DGC_TET_REGS_COLOR) : 255))
+        k_surf_tet(const TetParams A) {
   using D = TetDim<P>;
   constexpr int NP = D::NP, NQ = D::NQF, NV = D::NV;
   extern __shared__ unsigned char smem_raw[];
-  CT* sphi = reinterpret_cast<CT*>(smem_raw);  // [4][6][NQ][NP] (FP64: FP32 pairs of the same size)
+  // FP64: the orientation tables [4][6][NQ][NP] as FP32 pairs; FP32: the
+  // face-modal tables T [4][6][KF][NP]
+  constexpr int NTAB = sizeof(CT) == 8 ? 24 * NQ * NP : 24 * D::KF * NP;
+  CT* sphi = reinterpret_cast<CT*>(smem_raw);
   {
     const CT* src = static_cast<const CT*>(A.ftab);
-    for (int i = threadIdx.x; i < 24 * NQ * NP; i += blockDim.x) sphi[i] = src[i];
+    for (int i = threadIdx.x; i < NTAB; i += blockDim.x) sphi[i] = src[i];
   }
   // the FP64 first color: the pair volume tables after the face tables
   float2* vt = reinterpret_cast<float2*>(smem_raw + sizeof(CT) * 24 * NQ * NP);
@@ -572,9 +700,9 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
   const int orient = right ? ((tp.z >> 8) & 7) : 0;
   const bool writer = valid && !(side && bnd);
   const double2 g0 = A.fgeo[3 * k], g1 = A.fgeo[3 * k + 1], g2 = A.fgeo[3 * k + 2];
-  const CT* ph = sphi + (lf * 6 + orient) * NQ * NP;
 
   if constexpr (sizeof(CT) == 8) {
+    const CT* ph = sphi + (lf * 6 + orient) * NQ * NP;
     // FP64 flux and update, the basis contractions as FP32 pairs on the flux
     // deviations (tet_volume_df)
     const TetTab<double, P>& K = tet_tab<double, P>();
@@ -652,57 +780,155 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
       tet_write<P, RT, MODE>(A, elem, k, side, acc);
     }
   } else {
+    // FP32 lanes, face-modal (tet_face_modal): the element block is turned into
+    // the volume integral (first color) and the trace's KF face coefficients,
+    // and not held through the point loop; variables (0, 1) and (2, 3) in pairs
+    // on the packed FP32 FMA, variable 4 alone
+    constexpr int KF = D::KF;
     const TetTab<float, P>& K = tet_tab<float, P>();
+    const TetFaceTab<P>& FM = tet_mtab<P>();
+    const float* Tl = reinterpret_cast<const float*>(sphi) + (lf * 6 + orient) * KF * NP;  // T [KF][NP]
+    float* vsm = reinterpret_cast<float*>(sphi) + NTAB;  // first color: [NV][blockDim.x]
     const int64_t stride = sizeof(ST) == 8 ? NV : A.sstride;
-    TetPert<P> B;
-    tload_pert<P>(static_cast<const ST*>(A.state) + elem * stride, B);
-    PertRef<3> R;
-    R.init(B.hi);
+    const ST* src = static_cast<const ST*>(A.state) + elem * stride;
     float acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0f;
-    if constexpr (MODE == SURF_FIRST) tet_volume32<P>(B, R, A.jinv + 9 * elem, acc);
-    // each lane evaluates its own side's flux and the pair exchanges one value
-    // per variable (euler_pert.cuh, lf_exchange)
-    FaceConst<3> E;
-    E.init(R, B.hi, {d2f(g0.x), d2f(g0.y), d2f(g1.x)}, side);
-    const float scale = right ? d2f(g2.y) : -d2f(g2.x);
-#pragma unroll 2
-    for (int q = 0; q < NQ; ++q) {
-      float phi[NP], ds[5], G[5];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) phi[j] = ph[q * NP + j];
+    float hi[5], lo[5];
+    float2 a01[KF], a23[KF];
+    float a4[KF];
+    PertRef<3> R;
+    {
+      TetPert<P> B;
+      tload_pert<P>(src, B);
+      R.init(B.hi);
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        float s = 0.0f;
-#pragma unroll
-        for (int j = 1; j < NP; ++j) s += phi[j] * B.cd[m][j - 1];
-        ds[m] = B.lo[m] + s;  // own trace - ub
+        hi[m] = B.hi[m];
+        lo[m] = B.lo[m];
       }
+      if constexpr (MODE == SURF_FIRST) {
+        // the volume integral waits in shared memory (one value per thread and
+        // row: conflict-free) while the point loop runs
+        tet_volume32<P>(B, R, A.jinv + 9 * elem, acc);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) vsm[i * blockDim.x + threadIdx.x] = acc[i];
+      }
+      // the trace deviation's face coefficients a_k = sum_{j >= 1} T[k][j] c_j
+#pragma unroll
+      for (int kk = 0; kk < KF; ++kk) {
+        a01[kk] = make_float2(0.0f, 0.0f);
+        a23[kk] = make_float2(0.0f, 0.0f);
+        a4[kk] = 0.0f;
+      }
+#pragma unroll
+      for (int j = 1; j < NP; ++j) {
+        const float2 c01 = make_float2(B.cd[0][j - 1], B.cd[1][j - 1]);
+        const float2 c23 = make_float2(B.cd[2][j - 1], B.cd[3][j - 1]);
+#pragma unroll
+        for (int kk = 0; kk < KF; ++kk) {
+          const float t = Tl[kk * NP + j];
+          const float2 t2 = make_float2(t, t);
+          a01[kk] = __ffma2_rn(t2, c01, a01[kk]);
+          a23[kk] = __ffma2_rn(t2, c23, a23[kk]);
+          a4[kk] = fmaf(t, B.cd[4][j - 1], a4[kk]);
+        }
+      }
+    }
+    // each lane evaluates its own side's flux and the pair exchanges one value
+    // per variable (euler_pert.cuh, lf_exchange); the lane projects onto psi_k
+    FaceConst<3> E;
+    E.init(R, hi, {d2f(g0.x), d2f(g0.y), d2f(g1.x)}, side);
+    const float scale = right ? d2f(g2.y) : -d2f(g2.x);
+    float2 b01[KF], b23[KF];
+    float b4[KF];
+#pragma unroll
+    for (int kk = 0; kk < KF; ++kk) {
+      b01[kk] = make_float2(0.0f, 0.0f);
+      b23[kk] = make_float2(0.0f, 0.0f);
+      b4[kk] = 0.0f;
+    }
+    DGC_TET_UNROLL_Q
+    for (int q = 0; q < NQ; ++q) {
+      float2 d01 = make_float2(lo[0], lo[1]), d23 = make_float2(lo[2], lo[3]);
+      float d4 = lo[4];
+#pragma unroll
+      for (int kk = 0; kk < KF; ++kk) {
+        d01 = __ffma2_rn(FM.psi2[q][kk], a01[kk], d01);
+        d23 = __ffma2_rn(FM.psi2[q][kk], a23[kk], d23);
+        d4 = fmaf(FM.psi[q][kk], a4[kk], d4);
+      }
+      const float ds[5] = {d01.x, d01.y, d23.x, d23.y, d4};  // own trace - ub
+      float G[5];
       lf_exchange<3>(R, E, ds, G);
       const float s = scale * K.wF[q];
+      const float2 g01 = make_float2(s * G[0], s * G[1]), g23 = make_float2(s * G[2], s * G[3]);
+      const float g4 = s * G[4];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const float g = s * G[m];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc[m * NP + j] += phi[j] * g;
+      for (int kk = 0; kk < KF; ++kk) {
+        b01[kk] = __ffma2_rn(FM.psi2[q][kk], g01, b01[kk]);
+        b23[kk] = __ffma2_rn(FM.psi2[q][kk], g23, b23[kk]);
+        b4[kk] = fmaf(FM.psi[q][kk], g4, b4[kk]);
       }
+    }
+    // the face's contribution to the lane's modes, sum_k T[k][j] b_k: into acc
+    // for the last color; the other modes take it one variable at a time in
+    // their write (the whole block is never live beside b)
+    auto bvar = [&](int kk, int m) {
+      return m == 0 ? b01[kk].x : m == 1 ? b01[kk].y : m == 2 ? b23[kk].x : m == 3 ? b23[kk].y : b4[kk];
+    };
+    if constexpr (MODE == SURF_LAST) {
+#pragma unroll
+      for (int m = 0; m < 5; ++m)
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+#pragma unroll
+          for (int kk = 0; kk < KF; ++kk) acc[m * NP + j] = fmaf(Tl[kk * NP + j], bvar(kk, m), acc[m * NP + j]);
     }
     if constexpr (MODE != SURF_FIRST) {
       pdl_wait();
       pdl_trigger();
     }
     if constexpr (MODE == SURF_LAST) {
-      // the element's right-hand side is complete: SSP-RK3 stage in increment form
+      // the element's right-hand side is complete: SSP-RK3 stage in increment
+      // form (stage 0 writes the record of u0, the block read above: read again)
       if (writer) {
         float L[NV];
         ldv<NV>(static_cast<const float*>(A.rhs) + elem * NV, L);
 #pragma unroll
         for (int i = 0; i < NV; ++i) L[i] += acc[i];
+        TetPert<P> B;
+        if (A.sa.stage == 0) tload_pert<P>(src, B);
         incr_last<5, NP>(A.sa, elem, L, B, tet_tab<double, P>().phiV[0][0]);
       }
     } else if (writer) {
-      tet_write<P, RT, MODE>(A, elem, k, side, acc);
+      if constexpr (MODE == SURF_RMW && sizeof(RT) == 4) {
+        // FP32 rhs: the whole block's loads in flight at once, then each
+        // variable's contributions added (the block and b fit beside each other)
+        float* r = static_cast<float*>(A.rhs) + elem * NV;
+        float old[NV];
+        tload(r, old);
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+#pragma unroll
+          for (int j = 0; j < NP; ++j)
+#pragma unroll
+            for (int kk = 0; kk < KF; ++kk) old[m * NP + j] = fmaf(Tl[kk * NP + j], bvar(kk, m), old[m * NP + j]);
+        tstore(r, old);
+        return;
+      }
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        float cm[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          float v = MODE == SURF_FIRST ? vsm[(m * NP + j) * blockDim.x + threadIdx.x] : 0.0f;
+#pragma unroll
+          for (int kk = 0; kk < KF; ++kk) v = fmaf(Tl[kk * NP + j], bvar(kk, m), v);
+          cm[j] = v;
+        }
+        tet_write_var<P, RT, MODE>(A, elem, k, side, m, cm);
+      }
     }
   }
 }
@@ -844,11 +1070,14 @@ static int tsurf_launch(const Ctx& x, TetParams A) {
   using D = TetDim<P>;
   A.ftab = sizeof(CT) == 8 ? (const void*)x.d->ftabdf : (const void*)x.d->ftab;
   A.vtab = x.d->vtabdf;
-  const size_t smem = sizeof(CT) * 24 * D::NQF * D::NP +
-                      (sizeof(CT) == 8 && MODE == SURF_FIRST ? sizeof(float2) * 4 * D::NQV * D::NP : 0);
+  const int threads = 2 * x.epb;
+  // the face tables; the FP64 first color's pair volume tables, the FP32 first
+  // color's volume integrals (NV floats per thread)
+  const size_t smem = (sizeof(CT) == 8 ? sizeof(CT) * 24 * D::NQF * D::NP : sizeof(float) * 24 * D::KF * D::NP) +
+                      (sizeof(CT) == 8 && MODE == SURF_FIRST ? sizeof(float2) * 4 * D::NQV * D::NP : 0) +
+                      (sizeof(CT) == 4 && MODE == SURF_FIRST ? sizeof(float) * D::NV * threads : 0);
   auto kern = k_surf_tet<P, CT, ST, RT, MODE>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int threads = 2 * x.epb;
   launch_k(x, kern, (unsigned)((2 * n + threads - 1) / threads), (unsigned)threads, smem, A);
   return 1;
 }
