@@ -283,20 +283,30 @@ dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, in
  *     then three interior edges per refined element.  A half whose other neighbour stays
  *     coarse is a hanging edge: left = the fine child, right = the coarse element, whose
  *     basis is evaluated on that half of its edge (dgc_get_hanging).
+ * A refined mesh can be refined again (Sec. 3.2 says the map extends to several levels and
+ * gives no rule; reading): an element of level L carries colors 1..K, K = 3 * 2^L, and its
+ * split edges' halves take c and c + K (the palette doubles again, colors 1..12 at level 2);
+ * the listed elements must have no coarser neighbour (adjacent elements differ by at most one
+ * level); an element that is the coarse side of hanging halves may be listed: each half then
+ * joins the fine neighbour and the child holding it, with its color, and the interior edge
+ * parallel to that edge takes the halves' color modulo K.  At most two levels (12 colors).
  * The mesh is then reordered as by dgc_color_edges (Sec. 5; elements no color-1 edge reaches
- * are numbered last, in original order).  Errors: DGC_ERR_UNSUPPORTED (tetrahedra, a mesh
- * already refined), DGC_ERR_ARG (not colored with 3 colors, id out of range).  Host only;
- * states sized for the old mesh are invalid afterwards. */
+ * are numbered last, in original order).  Errors: DGC_ERR_UNSUPPORTED (tetrahedra, a third
+ * level), DGC_ERR_ARG (not colored with 3 colors nor refined before, id out of range, an
+ * element finer than a neighbour).  Host only; states sized for the old mesh are invalid
+ * afterwards. */
 dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems);
 
-/* Undoes dgc_refine (Sec. 3.2): the four children of every refined element merge back into
- * their parent, and each parent edge takes the color of the child edge parallel to it.  That
- * recovers the coloring before refinement; the call checks it (DGC_ERR_MESH otherwise) and
- * restores the mesh, its 3-coloring and the Sec. 5 ordering.  DGC_ERR_ARG if the mesh is
- * not refined.  Host only; states sized for the refined mesh are invalid afterwards. */
+/* Undoes the last dgc_refine (Sec. 3.2): the four children of every element it refined merge
+ * back into their parent, and each parent edge takes the color of the child edge parallel to
+ * it.  That recovers the coloring before that refinement; the call checks it (DGC_ERR_MESH
+ * otherwise) and restores the mesh, its coloring and the Sec. 5 ordering (a mesh refined
+ * twice comes back to its first refinement, which a second call undoes).  DGC_ERR_ARG if the
+ * mesh is not refined.  Host only; states sized for the refined mesh are invalid afterwards. */
 dgc_status dgc_coarsen(dgc_mesh* mesh);
 
-/* Dynamic adaptivity on the device, for a mesh refined by dgc_refine (Sec. 3.2):
+/* Dynamic adaptivity on the device, for a mesh refined by dgc_refine (Sec. 3.2), between the
+ * mesh and its last refinement:
  *   dgc_prolong_state: the state of the mesh before refinement (device, [E0][M][Np] FP64
  *     in that mesh's internal order, as it was imported before dgc_refine) to the refined
  *     mesh's state (device, internal order): each child takes the L2 projection of its
@@ -311,8 +321,9 @@ dgc_status dgc_coarsen(dgc_mesh* mesh);
  *   uploads the mesh, which allocates).  DGC_ERR_ARG if the mesh is not refined.
  *   dgc_refine_colors_device: the Sec. 3.2 color map of the refined sides evaluated on the
  *     device, one thread per side, from the coloring before refinement (a split edge's
- *     halves take c and c + 3, an interior edge its parallel parent edge's color, other
- *     edges keep theirs); writes the colors in the refined mesh's original side order to
+ *     halves take c and c + K, K = 3 * 2^L at the level L of its elements, an interior edge
+ *     its parallel parent edge's color, other edges keep theirs); writes the colors in the
+ *     refined mesh's original side order to
  *     the host array colors[Ns] (the same colors dgc_refine assigned on the host) and the
  *     map kernel's time in ms (may be NULL).  Allocates its scratch, synchronises. */
 dgc_status dgc_prolong_state(dgc_mesh* mesh, const double* c_coarse_dev, double* c_fine_dev, void* stream);

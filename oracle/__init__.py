@@ -127,6 +127,8 @@ class _Build:
         L.orc_mesh_nvert.argtypes = [P]
         L.orc_mesh_elements.argtypes = [P, C.POINTER(C.c_int32), dp]
         L.orc_mesh_refined.argtypes = [P, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]
+        L.orc_mesh_levels.restype = None
+        L.orc_mesh_levels.argtypes = [P, C.POINTER(C.c_int8)]
         L.orc_transfer.argtypes = [P, P, C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, dp, dp]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
@@ -303,9 +305,11 @@ class OracleMesh:
         return cls(mi.dim, mi.xyz, mi.ev, mi.periodic_len, build=build)
 
     def refine(self, col: np.ndarray, elems) -> "OracleMesh":
-        """One level of refinement of the listed elements with the 6-color map of
-        Sec. 3.2 (dg_oracle.c, orc_refine); col holds this mesh's colors 1..3.
-        The new mesh carries .colors and .hanging (per side)."""
+        """One level of refinement of the listed elements with the color map of
+        Sec. 3.2 (dg_oracle.c, orc_refine); col holds this mesh's colors (1..3 on
+        a conforming mesh; a refined mesh's .colors for a further level).  The
+        new mesh carries .colors and .hanging (per side) and .levels (per
+        element)."""
         B = self._b
         col = np.ascontiguousarray(col, dtype=np.int8)
         flag = np.zeros(self.ne, np.uint8)
@@ -328,6 +332,8 @@ class OracleMesh:
         m.colors = np.zeros(m.ns, np.int8)
         m.hanging = np.zeros(m.ns, np.int8)
         B.check(B.L.orc_mesh_refined(h, _i8(m.colors), _i8(m.hanging)))
+        m.levels = np.zeros(m.ne, np.int8)
+        B.L.orc_mesh_levels(h, _i8(m.levels))
         return m
 
     def prolong(self, p: int, c_coarse: np.ndarray) -> np.ndarray:

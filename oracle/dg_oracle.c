@@ -407,6 +407,7 @@ typedef struct {
   int32_t *es2;   /* ne * nfpe: second side on a split edge of a coarse element, -1 if none */
   int8_t *shalf;  /* per side: half of the right element's edge a hanging side covers, or -1 */
   int8_t *col;    /* per side: color from the map of Sec. 3.2 */
+  int8_t *lev;    /* per element: refinement level (NULL: every element level 0) */
   /* boundary conditions and limiter (orc_set_bc, orc_set_limiter); all zero by
    * default: every boundary face transmissive, no limiter */
   int8_t *bck;    /* per side: ORC_BC_* kind of a boundary side (r = -1) */
@@ -675,6 +676,7 @@ void orc_mesh_free(void *h) {
   free(m->es2);
   free(m->shalf);
   free(m->col);
+  free(m->lev);
   free(m->bck);
   free(m->bcs);
   free(m);
@@ -925,8 +927,9 @@ int orc_reorder(void *h, int nc, const int8_t *col, int32_t *elem_new_of_old,
 /* ======================================================================= */
 /* Nonconforming refinement and its 6-color map (Sec. 3.2)                  */
 /* ======================================================================= */
-/* One level of isotropic refinement of the flagged triangles of a conforming
- * triangle mesh whose edges carry colors 1..3.  A flagged triangle (v0, v1, v2)
+/* One level of isotropic refinement of the flagged triangles of a triangle
+ * mesh whose edges carry a valid coloring: a conforming mesh colored 1..3, or
+ * a mesh this function refined before.  A flagged triangle (v0, v1, v2)
  * is split through the midpoints m_k of its edges k = (v_k, v_k+1) into the
  * corner triangles (v0, m0, m2), (m0, v1, m1), (m2, m1, v2) and the middle
  * triangle (m0, m1, m2), numbered in place of the parent in that order.  The
@@ -938,6 +941,16 @@ int orc_reorder(void *h, int nc, const int8_t *col, int32_t *elem_new_of_old,
  * triangle takes the color of the parent edge it is parallel to (the edge
  * joining the midpoints of parent edges a and b is parallel to the third one);
  * the other edges keep their colors.
+ * Further levels (the paper says the map extends to several levels and gives no
+ * rule; reading): elements of level L carry colors 1..K, K = 3 * 2^L, the map
+ * doubles the palette again, halves c and c + K, so a level-L+1 child's edges
+ * are distinct modulo K as its parent's are, and the mesh uses 3 * 2^Lmax
+ * colors.  The elements refined must have no coarser neighbour (adjacent
+ * elements differ by at most one level, as the paper assumes); an element that
+ * is the coarse side of hanging halves may be refined: its split edge keeps its
+ * midpoint vertex, each half becomes a conforming side with its color, and the
+ * parent color of that edge, for the parallel interior edge, is the smaller of
+ * its halves' colors (c against c + K).
  * Readings:
  *  - half m = 1 is the one touching the endpoint of the parent edge with the
  *    smaller vertex id.  The paper counts the halves counterclockwise per
@@ -963,10 +976,35 @@ static int find_edge(const orc_mesh *m, int64_t e, int32_t x, int32_t y) {
   return -1;
 }
 
+/* the midpoint vertex of local edge k of base element e: a new one (mid[] of
+ * its side), or, on an edge already split into two hanging halves (e their
+ * coarse element), the vertex the halves share */
+static int32_t edge_midpoint(const orc_mesh *b, const int32_t *mid, int64_t e, int k) {
+  const int32_t s = b->es[e * 3 + k];
+  if (!b->es2 || b->es2[e * 3 + k] < 0) return mid[s];
+  const int32_t A = b->ev[e * 3 + k], B = b->ev[e * 3 + (k + 1) % 3];
+  const int32_t l = b->sl[s];
+  const int32_t x = b->ev[l * 3 + b->sql[s]], y = b->ev[l * 3 + (b->sql[s] + 1) % 3];
+  return (x != A && x != B) ? x : y;
+}
+
+/* the color of parent edge k of base element e: its side's color, or the
+ * smaller of its two halves' colors on a split edge */
+static int parent_color(const orc_mesh *b, const int8_t *col, int64_t e, int k) {
+  int c = col[b->es[e * 3 + k]];
+  if (b->es2 && b->es2[e * 3 + k] >= 0 && col[b->es2[e * 3 + k]] < c) c = col[b->es2[e * 3 + k]];
+  return c;
+}
+
 void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   const orc_mesh *b = (const orc_mesh *)h;
   if (b->dim != 2 || b->quad) return fail("refine: triangles only"), (void *)0;
   int64_t ne0 = b->ne, ns0 = b->ns, ne = 0, nv = b->nv, nref = 0;
+  /* adjacent elements differ by at most one level: no flagged element may be
+   * the fine side of a hanging side */
+  if (b->shalf)
+    for (int64_t s = 0; s < ns0; ++s)
+      if (b->shalf[s] >= 0 && flag[b->sl[s]]) return fail("refine: an element finer than its neighbour"), (void *)0;
   int64_t *first = (int64_t *)malloc(sizeof(int64_t) * ne0);
   for (int64_t e = 0; e < ne0; ++e) {
     first[e] = ne;
@@ -976,7 +1014,8 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   int32_t *mid = (int32_t *)malloc(sizeof(int32_t) * ns0);
   for (int64_t s = 0; s < ns0; ++s) {
     int32_t l = b->sl[s], r = b->sr[s];
-    mid[s] = (flag[l] || (r >= 0 && flag[r])) ? (int32_t)nv++ : -1;
+    int hang = b->shalf && b->shalf[s] >= 0;
+    mid[s] = (!hang && (flag[l] || (r >= 0 && flag[r]))) ? (int32_t)nv++ : -1;
   }
   orc_mesh *m = (orc_mesh *)calloc(1, sizeof *m);
   m->dim = 2;
@@ -990,31 +1029,36 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   m->X = (real *)malloc(sizeof(real) * ne * 6);
   m->detJ = (real *)malloc(sizeof(real) * ne);
   m->Jinv = (real *)malloc(sizeof(real) * ne * 4);
+  m->lev = (int8_t *)malloc(ne);
   int bad = 0;
   for (int64_t e = 0; e < ne0; ++e) {
     const int32_t *v = b->ev + e * 3;
     const real *P = b->X + e * 6;
+    const int le = b->lev ? b->lev[e] : 0;
     int64_t n = first[e];
     if (!flag[e]) {
       memcpy(m->ev + n * 3, v, sizeof(int32_t) * 3);
       memcpy(m->X + n * 6, P, sizeof(real) * 6);
+      m->lev[n] = (int8_t)le;
       continue;
     }
     int32_t mv[3];
     real Q[3][2];
     for (int k = 0; k < 3; ++k) {
-      mv[k] = mid[b->es[e * 3 + k]];
+      mv[k] = edge_midpoint(b, mid, e, k);
       for (int a = 0; a < 2; ++a) Q[k][a] = 0.5 * (P[k * 2 + a] + P[((k + 1) % 3) * 2 + a]);
     }
     /* children as (vertex id, coordinates) */
     int32_t cid[4][3] = {{v[0], mv[0], mv[2]}, {mv[0], v[1], mv[1]}, {mv[2], mv[1], v[2]}, {mv[0], mv[1], mv[2]}};
     const real *cx[4][3] = {{P, Q[0], Q[2]}, {Q[0], P + 2, Q[1]}, {Q[2], Q[1], P + 4}, {Q[0], Q[1], Q[2]}};
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 4; ++c) {
+      m->lev[n + c] = (int8_t)(le + 1);
       for (int k = 0; k < 3; ++k) {
         m->ev[(n + c) * 3 + k] = cid[c][k];
         m->X[((n + c) * 3 + k) * 2 + 0] = cx[c][k][0];
         m->X[((n + c) * 3 + k) * 2 + 1] = cx[c][k][1];
       }
+    }
   }
   int64_t cap = 2 * ns0 + 3 * nref, ns = 0;
   m->sl = (int32_t *)malloc(sizeof(int32_t) * cap);
@@ -1036,15 +1080,38 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   for (int64_t s = 0; s < ns0; ++s) {
     int32_t l = b->sl[s], r = b->sr[s];
     int c = col[s];
+    if (b->shalf && b->shalf[s] >= 0) {
+      /* a hanging half (l fine, r coarse): it stays hanging, or, when the
+       * coarse element is refined, joins l and the child of r that holds it */
+      if (!flag[r]) {
+        ADD_SIDE(first[l], first[r], b->sql[s], b->sqr[s], b->shalf[s], c);
+        continue;
+      }
+      int32_t x = b->ev[l * 3 + b->sql[s]], y = b->ev[l * 3 + (b->sql[s] + 1) % 3];
+      int64_t fr = -1;
+      int qr = -1;
+      for (int k = 0; k < 4; ++k)
+        if ((qr = find_edge(m, first[r] + k, x, y)) >= 0) {
+          fr = first[r] + k;
+          break;
+        }
+      if (fr < 0) bad = 1;
+      ADD_SIDE(first[l], fr, b->sql[s], qr, -1, c);
+      continue;
+    }
     int Rl = flag[l] != 0, Rr = r >= 0 && flag[r] != 0;
     if (!Rl && !Rr) {
       ADD_SIDE(first[l], r >= 0 ? first[r] : -1, b->sql[s], r >= 0 ? b->sqr[s] : -1, -1, c);
       continue;
     }
+    /* the palette of the side's level (a conforming side joins two elements of one level) */
+    const int lv = b->lev ? b->lev[l] : 0;
+    if (r >= 0 && b->lev && b->lev[r] != lv) bad = 1;
+    const int K = 3 << lv;
     int32_t va = b->ev[l * 3 + b->sql[s]], vb = b->ev[l * 3 + (b->sql[s] + 1) % 3];
     for (int half = 1; half <= 2; ++half) {
       int32_t Pv = (half == 1) == (va < vb) ? va : vb; /* endpoint this half touches */
-      int cm = (c + 3 * half - 4) % 6 + 1;
+      int cm = c + (half - 1) * K; /* ((c + 3m - 4) mod 6) + 1 at level 0 */
       /* the fine element(s) holding the half (Pv, mid) and their local edge */
       int64_t fl = -1, fr = -1;
       int ql = -1, qr = -1;
@@ -1075,10 +1142,15 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
   for (int64_t e = 0; e < ne0; ++e) {
     if (!flag[e]) continue;
     int64_t n = first[e];
-    for (int k = 0; k < 3; ++k) { /* the interior edge of corner child k */
+    int32_t mv[3];
+    for (int t = 0; t < 3; ++t) mv[t] = edge_midpoint(b, mid, e, t);
+    for (int k = 0; k < 3; ++k) { /* the interior edge of corner child k: both ends are midpoints */
       int q = -1, qm = -1, ea = -1, eb = -1;
-      for (int t = 0; t < 3 && q < 0; ++t)
-        if (m->ev[(n + k) * 3 + t] >= b->nv && m->ev[(n + k) * 3 + (t + 1) % 3] >= b->nv) q = t;
+      for (int t = 0; t < 3 && q < 0; ++t) {
+        int32_t x = m->ev[(n + k) * 3 + t], y = m->ev[(n + k) * 3 + (t + 1) % 3];
+        int xm = x == mv[0] || x == mv[1] || x == mv[2], ym = y == mv[0] || y == mv[1] || y == mv[2];
+        if (xm && ym) q = t;
+      }
       if (q < 0) {
         bad = 1;
         continue;
@@ -1086,8 +1158,7 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
       int32_t x = m->ev[(n + k) * 3 + q], y = m->ev[(n + k) * 3 + (q + 1) % 3];
       qm = find_edge(m, n + 3, x, y);
       for (int t = 0; t < 3; ++t) {
-        int32_t mt = mid[b->es[e * 3 + t]];
-        if (mt == x || mt == y) {
+        if (mv[t] == x || mv[t] == y) {
           if (ea < 0) ea = t;
           else eb = t;
         }
@@ -1096,7 +1167,7 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
         bad = 1;
         continue;
       }
-      ADD_SIDE(n + k, n + 3, q, qm, -1, col[b->es[e * 3 + (3 - ea - eb)]]);
+      ADD_SIDE(n + k, n + 3, q, qm, -1, parent_color(b, col, e, 3 - ea - eb));
     }
   }
 #undef ADD_SIDE
@@ -1133,6 +1204,12 @@ void *orc_refine(void *h, const int8_t *col, const uint8_t *flag) {
     return fail("refine: inconsistent refined mesh"), (void *)0;
   }
   return m;
+}
+
+/* refinement level of each element (0 on a mesh orc_refine did not make) */
+void orc_mesh_levels(void *h, int8_t *lev) {
+  orc_mesh *m = (orc_mesh *)h;
+  for (int64_t e = 0; e < m->ne; ++e) lev[e] = m->lev ? m->lev[e] : 0;
 }
 
 int64_t orc_mesh_nelem(void *h) { return ((orc_mesh *)h)->ne; }

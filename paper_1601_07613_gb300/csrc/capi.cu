@@ -903,10 +903,9 @@ dgc_status dgc_refine(dgc_mesh* mesh, int64_t n, const int32_t* elems) {
     Mesh& m = checked(mesh);
     require(m.dim == 2 && !m.quad, "nonconforming refinement is implemented for triangle meshes",
             DGC_ERR_UNSUPPORTED);
-    require(!m.refined, "the mesh is already refined (one level is supported)", DGC_ERR_UNSUPPORTED);
     require(!m.has_bc && !m.limit, "refinement keeps transmissive boundaries and no limiter", DGC_ERR_UNSUPPORTED);
-    require(m.ncolors == 3 && m.perfect && !m.side_old_of_new.empty(),
-            "refine a mesh colored by dgc_color_edges with 3 colors");
+    require(!m.side_old_of_new.empty() && (m.refined || (m.ncolors == 3 && m.perfect)),
+            "refine a mesh colored by dgc_color_edges with 3 colors, or one refined before");
     require(n >= 0 && (n == 0 || elems != nullptr), "bad element list");
     std::vector<uint8_t> flag(m.ne, 0);
     for (int64_t i = 0; i < n; ++i) {

@@ -85,22 +85,28 @@ struct Mesh {
   // nonconforming meshes (Sec. 3.2): half (0 or 1) of the right element's local
   // edge that side s covers, -1 for a conforming side; empty when conforming
   std::vector<int8_t> shalf;
+  // refinement level of each element (original order; empty: every element 0)
+  std::vector<int8_t> level;
   bool refined = false;
-  // the mesh before dgc_refine, kept for coarsening
+  // the mesh before the last dgc_refine, kept for coarsening (a mesh refined
+  // again keeps the earlier ones in base_stack)
   struct Base {
     int64_t nv = 0, ne = 0, ns = 0;
     std::vector<double> X;
     std::vector<int32_t> ev, sl, sr, face_of;
-    std::vector<int8_t> sql, sqr, color;
+    std::vector<int8_t> sql, sqr, color, shalf, level;
     std::vector<uint8_t> flag;  // refined elements
     std::vector<int32_t> elem_new_of_old;  // the coarse mesh's internal element order
+    int ncolors = 0;
     // per refined side (original order), where the Sec. 3.2 map takes its color
-    // from: rule 0 = base side src keeps its color, 1 / 2 = first / second half of
-    // base side src (c, c + 3), 3 + k = interior edge of refined base element src
-    // parallel to its edge k
+    // from: rule & 15 = 0: base side src keeps its color, 1 / 2: first / second
+    // half of base side src (c, c + K), 3 + k: interior edge of refined base
+    // element src parallel to its edge k; rule >> 4 = the level L of the base
+    // elements, K = 3 * 2^L
     std::vector<int32_t> color_src;
     std::vector<int8_t> color_rule;
   } base;
+  std::vector<Base> base_stack;
   // geometry, original order
   std::vector<double> detJ, Jinv, inradius;  // Jinv [ne][dim][dim] (row k = grad r_k)
   std::vector<double> snormal, smeas;        // [ns][dim] outward normal of the left element, |face|

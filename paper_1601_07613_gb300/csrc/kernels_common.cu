@@ -133,20 +133,22 @@ int permute_blocks(cudaStream_t st, double* dst, const double* src, const int32_
 // from the coarse coloring, and the DG state between the coarse mesh and its
 // refinement.
 // ---------------------------------------------------------------------------
-// One thread per refined side: rule 0 keeps base side src's color c, rules 1
-// and 2 (the half next to the smaller and the larger vertex id) give
-// ((c + 3 m - 4) mod 6) + 1 = c and c + 3, rule 3 + k gives the interior edge of
-// refined base element src the color of its edge k (the parallel one).
+// One thread per refined side: rule & 15 = 0 keeps base side src's color c,
+// 1 and 2 (the half next to the smaller and the larger vertex id) give c and
+// c + K (at level 0, K = 3: ((c + 3 m - 4) mod 6) + 1), 3 + k gives the interior
+// edge of refined base element src the color of its edge k (the parallel one;
+// a split edge's half taken modulo K); K = 3 * 2^(rule >> 4), the palette of the
+// base elements' level.
 __global__ void k_refine_colors(const int8_t* __restrict__ base_color, const int32_t* __restrict__ base_face_of,
                                 const int32_t* __restrict__ src, const int8_t* __restrict__ rule, int64_t ns,
                                 int8_t* __restrict__ out) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
-  const int r = rule[s];
+  const int r = rule[s] & 15, K = 3 << (rule[s] >> 4);
   int c;
   if (r == 0) c = base_color[src[s]];
-  else if (r <= 2) c = (base_color[src[s]] + 3 * r - 4) % 6 + 1;
-  else c = base_color[base_face_of[(int64_t)src[s] * 3 + (r - 3)]];
+  else if (r <= 2) c = base_color[src[s]] + (r - 1) * K;
+  else c = (base_color[base_face_of[(int64_t)src[s] * 3 + (r - 3)]] - 1) % K + 1;
   out[s] = (int8_t)c;
 }
 

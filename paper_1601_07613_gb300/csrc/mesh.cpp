@@ -906,12 +906,12 @@ void reorder(Mesh& m, bool renumber, bool reorder_left) {
 
 // ---------------------------------------------------------------------------
 // Nonconforming refinement and its 6-color map (Sec. 3.2).  One level of
-// quadrisection of the flagged triangles of a conforming mesh colored with
-// three colors.  Triangle (v0, v1, v2) with edge midpoints m01, m12, m20 is
-// replaced, in place, by the children [v0, m01, m20], [m01, v1, m12],
-// [m20, m12, v2] and [m01, m12, m20].  Corner child k holds the halves of the
-// parent's local edges that meet at v_k, on its own local edges of the same
-// index.  Edge colors:
+// quadrisection of the flagged triangles of a mesh colored by the map: a
+// conforming mesh colored with three colors, or a mesh refined before.
+// Triangle (v0, v1, v2) with edge midpoints m01, m12, m20 is replaced, in
+// place, by the children [v0, m01, m20], [m01, v1, m12], [m20, m12, v2] and
+// [m01, m12, m20].  Corner child k holds the halves of the parent's local edges
+// that meet at v_k, on its own local edges of the same index.  Edge colors:
 //  - the half of a parent edge of color c next to the edge's endpoint with the
 //    smaller vertex id is the first child (m = 1), the other the second
 //    (m = 2); child m gets ((c + 3m - 4) mod 6) + 1, i.e. c or c + 3.  (Reading:
@@ -920,6 +920,15 @@ void reorder(Mesh& m, bool renumber, bool reorder_left) {
 //    count is fixed once, by the global vertex order, for both sides.)
 //  - an interior edge takes the color of the parent edge it is parallel to;
 //  - edges of unrefined neighbours keep their colors.
+// Further levels (reading: the paper says the map extends and gives no rule):
+// an element of level L has colors 1..K, K = 3 * 2^L, and its split edges'
+// halves take c and c + K, the palette doubling again, so a child's three
+// edges stay distinct modulo K.  A flagged element may not be finer than a
+// neighbour (adjacent elements differ by at most one level); a flagged element
+// that is the coarse side of hanging halves keeps that edge's midpoint vertex,
+// each half joins the fine neighbour and the child that now holds it (its color
+// kept), and the parallel interior edge takes the parent color, the half's
+// color taken modulo K.
 // Side order: the base sides in order (one side, or its two halves, first
 // child first), then three interior sides per refined element, in element
 // order.  A half whose other neighbour is not refined is a hanging side: the
@@ -929,6 +938,17 @@ void reorder(Mesh& m, bool renumber, bool reorder_left) {
 // ---------------------------------------------------------------------------
 void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   const int64_t ne0 = m.ne, ns0 = m.ns;
+  auto lev = [&](int64_t e) { return m.level.empty() ? 0 : (int)m.level[e]; };
+  auto hanging = [&](int64_t s) { return !m.shalf.empty() && m.shalf[s] >= 0; };
+  for (int64_t s = 0; s < ns0; ++s)
+    if (hanging(s) && flag[m.sl[s]])
+      throw Error{DGC_ERR_ARG, "refinement: an element finer than its neighbour (refine the coarser one first)"};
+  int maxlev = 0;
+  for (int64_t e = 0; e < ne0; ++e) {
+    if (flag[e] && 3 << (lev(e) + 1) > kMaxColors)
+      throw Error{DGC_ERR_UNSUPPORTED, "refinement: at most two levels (12 colors)"};
+    maxlev = std::max(maxlev, lev(e) + (flag[e] ? 1 : 0));
+  }
   std::vector<int64_t> first(ne0);
   int64_t ne = 0;
   for (int64_t e = 0; e < ne0; ++e) {
@@ -939,11 +959,22 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   std::vector<int32_t> mid(ns0, -1);  // midpoint vertex of each split base edge
   int64_t nv = m.nv;
   for (int64_t s = 0; s < ns0; ++s)
-    if (flag[m.sl[s]] || (m.sr[s] >= 0 && flag[m.sr[s]])) mid[s] = (int32_t)nv++;
+    if (!hanging(s) && (flag[m.sl[s]] || (m.sr[s] >= 0 && flag[m.sr[s]]))) mid[s] = (int32_t)nv++;
   if (nv > (1LL << 30)) throw Error{DGC_ERR_ARG, "refined mesh too large"};
+  // the midpoint vertex of local edge k of element e: a new one, or on an edge
+  // already split (e the coarse side of its hanging halves) the vertex the
+  // halves share, the end of the fine element's edge that is not e's
+  auto midpoint = [&](int64_t e, int k) -> int32_t {
+    const int32_t s = m.face_of[(size_t)e * 3 + k];
+    if (!hanging(s)) return mid[s];
+    const int32_t A = m.ev[(size_t)e * 3 + k], B = m.ev[(size_t)e * 3 + (k + 1) % 3];
+    const int32_t f = m.sl[s], x = m.ev[(size_t)f * 3 + m.sql[s]], y = m.ev[(size_t)f * 3 + (m.sql[s] + 1) % 3];
+    return x != A && x != B ? x : y;
+  };
 
   std::vector<double> X((size_t)ne * 6);
   std::vector<int32_t> ev((size_t)ne * 3);
+  std::vector<int8_t> level((size_t)ne);
   for (int64_t e = 0; e < ne0; ++e) {
     const double* P = &m.X[(size_t)e * 6];
     const int32_t* v = &m.ev[(size_t)e * 3];
@@ -951,6 +982,7 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
     if (!flag[e]) {
       std::copy_n(P, 6, &X[(size_t)n * 6]);
       std::copy_n(v, 3, &ev[(size_t)n * 3]);
+      level[n] = (int8_t)lev(e);
       continue;
     }
     double Q[3][2];
@@ -958,15 +990,17 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
     for (int k = 0; k < 3; ++k) {
       const int k1 = (k + 1) % 3;
       for (int a = 0; a < 2; ++a) Q[k][a] = 0.5 * (P[k * 2 + a] + P[k1 * 2 + a]);
-      mv[k] = mid[m.face_of[(size_t)e * 3 + k]];
+      mv[k] = midpoint(e, k);
     }
     const int32_t cv[4][3] = {{v[0], mv[0], mv[2]}, {mv[0], v[1], mv[1]}, {mv[2], mv[1], v[2]}, {mv[0], mv[1], mv[2]}};
     const double* cx[4][3] = {{P, Q[0], Q[2]}, {Q[0], P + 2, Q[1]}, {Q[2], Q[1], P + 4}, {Q[0], Q[1], Q[2]}};
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 4; ++c) {
+      level[n + c] = (int8_t)(lev(e) + 1);
       for (int k = 0; k < 3; ++k) {
         ev[(size_t)(n + c) * 3 + k] = cv[c][k];
         for (int a = 0; a < 2; ++a) X[((size_t)(n + c) * 3 + k) * 2 + a] = cx[c][k][a];
       }
+    }
   }
 
   std::vector<int32_t> sl, sr, csrc;
@@ -989,19 +1023,29 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   for (int64_t s = 0; s < ns0; ++s) {
     const int32_t l = m.sl[s], r = m.sr[s];
     const int ql = m.sql[s], qr = m.sqr[s], c = m.color[s];
-    const bool Rl = flag[l] != 0, Rr = r >= 0 && flag[r] != 0;
     src = (int32_t)s;
     rule = 0;
+    if (hanging(s)) {
+      // l fine, r coarse: the half stays hanging, or joins l and the corner
+      // child of r that holds it (half 0 lies at v_qr: child qr; half 1 at
+      // v_qr+1: child qr + 1), on that child's local edge qr
+      if (!flag[r]) add(first[l], first[r], ql, qr, m.shalf[s], c);
+      else add(first[l], first[r] + (m.shalf[s] == 0 ? qr : (qr + 1) % 3), ql, qr, -1, c);
+      continue;
+    }
+    const bool Rl = flag[l] != 0, Rr = r >= 0 && flag[r] != 0;
     if (!Rl && !Rr) {
       add(first[l], r >= 0 ? first[r] : -1, ql, r >= 0 ? qr : -1, -1, c);
       continue;
     }
+    // the palette of the side's level (both elements of a conforming side have it)
+    const int L = lev(l), K = 3 << L;
     // l runs along the edge from a to b, r (if any) from b to a
     const int32_t a = m.ev[(size_t)l * 3 + ql], b = m.ev[(size_t)l * 3 + (ql + 1) % 3];
     for (int child = 1; child <= 2; ++child) {
       const int32_t P = child == 1 ? std::min(a, b) : std::max(a, b);  // endpoint the half touches
-      const int cc = (c + 3 * child - 4) % 6 + 1;
-      rule = (int8_t)child;
+      const int cc = c + (child - 1) * K;  // ((c + 3m - 4) mod 6) + 1 at level 0
+      rule = (int8_t)(child | L << 4);
       const int64_t lc = first[l] + (P == a ? ql : (ql + 1) % 3);
       if (r < 0) {
         add(lc, -1, ql, -1, -1, cc);
@@ -1016,14 +1060,15 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   for (int64_t e = 0; e < ne0; ++e) {
     if (!flag[e]) continue;
     const int64_t n = first[e];
-    int c[3];
-    for (int k = 0; k < 3; ++k) c[k] = m.color[m.face_of[(size_t)e * 3 + k]];
+    const int L = lev(e), K = 3 << L;
+    int c[3];  // the parent colors (a split edge's half, taken modulo K)
+    for (int k = 0; k < 3; ++k) c[k] = (m.color[m.face_of[(size_t)e * 3 + k]] - 1) % K + 1;
     src = (int32_t)e;
-    rule = 3 + 1;
+    rule = (int8_t)((3 + 1) | L << 4);
     add(n + 0, n + 3, 1, 2, -1, c[1]);  // m01-m20, parallel to parent edge 1
-    rule = 3 + 2;
+    rule = (int8_t)((3 + 2) | L << 4);
     add(n + 1, n + 3, 2, 0, -1, c[2]);  // m12-m01, parallel to parent edge 2
-    rule = 3 + 0;
+    rule = (int8_t)((3 + 0) | L << 4);
     add(n + 2, n + 3, 0, 1, -1, c[0]);  // m20-m12, parallel to parent edge 0
   }
   const int64_t ns = (int64_t)sl.size();
@@ -1041,10 +1086,13 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   for (int32_t f : face_of)
     if (f < 0) throw Error{DGC_ERR_MESH, "refinement: element edge without a side"};
 
+  if (m.refined) m.base_stack.push_back(std::move(m.base));
+  m.base = Mesh::Base();
   Mesh::Base& b = m.base;
   b.nv = m.nv;
   b.ne = m.ne;
   b.ns = m.ns;
+  b.ncolors = m.ncolors;
   b.flag = flag;
   b.elem_new_of_old = m.elem_new_of_old;
   b.color_src.swap(csrc);
@@ -1061,20 +1109,23 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   m.shalf.swap(half);
   m.color.swap(col);
   m.face_of.swap(face_of);
+  m.level.swap(level);
   b.X.swap(X);
   b.ev.swap(ev);
   b.sl.swap(sl);
   b.sr.swap(sr);
   b.sql.swap(sql);
   b.sqr.swap(sqr);
+  b.shalf.swap(half);
   b.color.swap(col);
   b.face_of.swap(face_of);
+  b.level.swap(level);
   m.detJ.assign(ne, 0.0);
   m.Jinv.assign((size_t)ne * 4, 0.0);
   for (int64_t e = 0; e < ne; ++e) element_jacobian(m, e);
   side_geometry(m);
   m.refined = true;
-  m.ncolors = 6;
+  m.ncolors = 3 << std::max(1, maxlev);  // 6 even when nothing was refined
   m.perfect = false;
   reorder(m, true, true);
   m.dirty = true;
@@ -1084,11 +1135,13 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
 // into the parent, and a parent edge takes the color of the child edge parallel
 // to it -- the middle child's edge (k + 1) mod 3 is parallel to parent edge k.
 // A parent edge whose neighbour stayed coarse is also read off its halves
-// (colors c and c + 3: the parent's is the one <= 3).  The colors so derived
-// from the refined mesh alone are checked against the coloring before
-// refinement, and the mesh before refinement is restored.
+// (colors c and c + K, K = 3 * 2^L at the parents' level L: the parent's is the
+// one <= K).  The colors so derived from the refined mesh alone are checked
+// against the coloring before refinement, and the mesh before the last
+// refinement is restored (with its own refinement, if it had one).
 void coarsen(Mesh& m) {
   const Mesh::Base& b = m.base;
+  auto bhang = [&](int64_t s) { return !b.shalf.empty() && b.shalf[s] >= 0; };
   const int64_t ne0 = b.ne, ns0 = b.ns;
   std::vector<int64_t> first(ne0);
   for (int64_t e = 0, n = 0; e < ne0; ++e) {
@@ -1103,15 +1156,15 @@ void coarsen(Mesh& m) {
   int64_t pos = 0;  // refined sides: the base sides in order (one, or two halves), then interior sides
   for (int64_t s = 0; s < ns0; ++s) {
     const int32_t l = b.sl[s], r = b.sr[s];
-    const bool split = b.flag[l] || (r >= 0 && b.flag[r]);
+    const bool split = !bhang(s) && (b.flag[l] || (r >= 0 && b.flag[r]));
     if (!split) {
       set(s, m.color[pos++]);
       continue;
     }
-    const int c1 = m.color[pos], c2 = m.color[pos + 1];
+    const int c1 = m.color[pos], c2 = m.color[pos + 1], K = 3 << (b.level.empty() ? 0 : b.level[l]);
     pos += 2;
-    if (std::min(c1, c2) < 1 || std::min(c1, c2) > 3 || std::max(c1, c2) != std::min(c1, c2) + 3)
-      throw Error{DGC_ERR_MESH, "coarsening: the halves of a split edge are not colored c and c + 3"};
+    if (std::min(c1, c2) < 1 || std::min(c1, c2) > K || std::max(c1, c2) != std::min(c1, c2) + K)
+      throw Error{DGC_ERR_MESH, "coarsening: the halves of a split edge are not colored c and c + K"};
     set(s, std::min(c1, c2));
     for (int32_t x : {l, r}) {
       if (x < 0 || !b.flag[x]) continue;
@@ -1133,15 +1186,21 @@ void coarsen(Mesh& m) {
   m.sqr = b.sqr;
   m.face_of = b.face_of;
   m.color.swap(col);
-  m.shalf.clear();
-  m.base = Mesh::Base();
+  m.shalf = b.shalf;
+  m.level = b.level;
+  m.ncolors = b.ncolors;
+  m.perfect = b.shalf.empty();
+  m.refined = !m.base_stack.empty();
+  if (m.refined) {
+    m.base = std::move(m.base_stack.back());
+    m.base_stack.pop_back();
+  } else {
+    m.base = Mesh::Base();
+  }
   m.detJ.assign(m.ne, 0.0);
   m.Jinv.assign((size_t)m.ne * 4, 0.0);
   for (int64_t e = 0; e < m.ne; ++e) element_jacobian(m, e);
   side_geometry(m);
-  m.refined = false;
-  m.ncolors = 3;
-  m.perfect = true;
   reorder(m, true, true);
   m.dirty = true;
 }

@@ -19,6 +19,7 @@ import pytest
 
 from paper_1601_07613_gb300 import dgc
 from paper_1601_07613_gb300 import workloads as W
+from _amr import second_level
 from _parity import check, fp64_vs_exact
 
 pytestmark = pytest.mark.gpu
@@ -151,6 +152,65 @@ def test_refine_step_coarsen_cycle(torch_dev, oracle_mod, prec, tol):
     dgc.dgc_rk_step(m.h, prec, cc, 0.3, d, ws)
     torch.cuda.synchronize()
     assert torch.isfinite(cc).all()
+    m.close()
+
+
+def test_two_level_color_map_and_cycle(torch_dev, oracle_mod):
+    """A second level on the device: its color map (the palette doubled again,
+    12 colors) bit for bit against the host's and the oracle's; then the coarse
+    vortex state prolonged through both levels, three FP64 steps on the
+    two-level mesh, restricted and coarsened back through both levels, against
+    the oracle (its extended build for the FP64 comparison)."""
+    torch, dev = torch_dev
+    mi, elems = _mesh("periodic")
+    p, steps = 2, 3
+    om = oracle_mod.OracleMesh.from_input(mi)
+    col, _ = om.color(3, 1601)
+    f1 = om.refine(col, elems)
+    e2 = second_level(f1, (0.45, 0.55), 0.18, 0.36)
+    f2 = f1.refine(f1.colors, e2)
+    xyz, _, _ = om.eval_points(p)
+    c0 = om.project(p, W.vortex_field(xyz[..., 0], xyz[..., 1], beta=5.0))
+
+    def cycle(g1, g2):
+        u = g2.prolong(p, g1.prolong(p, c0))
+        for _ in range(steps):
+            u, _ = g2.rk_step(p, u, 0.3)
+        return g1.restrict(p, g2.restrict(p, u))
+
+    ref = cycle(f1, f2)
+    ox = oracle_mod.OracleMesh.from_input(mi, build="extended")
+    x1 = ox.refine(col, elems)
+    refx = cycle(x1, x1.refine(x1.colors, e2))
+    m = dgc.Mesh.from_input(mi, p)
+    m.color(1601)
+    cc = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    dgc.dgc_import_state(m.h, c0, cc)
+    m.refine(elems)
+    c1 = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    dgc.dgc_prolong_state(m.h, cc, c1)
+    m.refine(e2)
+    got, _ = dgc.dgc_refine_colors_device(m.h, m.info["ns"])
+    assert np.array_equal(got, _host_colors(m)) and np.array_equal(got, f2.colors)
+    assert set(np.unique(got)) == set(range(1, 13))
+    c2 = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    dgc.dgc_prolong_state(m.h, c1, c2)
+    ws = torch.empty(dgc.dgc_workspace_size(m.h, dgc.DGC_FP64) // 8 + 64, dtype=torch.float64, device=dev)
+    d = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(steps):
+        dgc.dgc_rk_step(m.h, dgc.DGC_FP64, c2, 0.3, d, ws)
+    dgc.dgc_restrict_state(m.h, c2, c1)
+    m.coarsen()
+    dgc.dgc_restrict_state(m.h, c1, cc)
+    m.coarsen()
+    torch.cuda.synchronize()
+    out = dgc.dgc_export_state(m.h, cc)
+    e, _ = fp64_vs_exact(out - c0, ref - c0, refx - c0, 1e-11, "two-level cycle FP64")
+    print(f"two levels: refine, refine, {steps} steps, coarsen, coarsen: du rel L2 {e:.2e}")
+    dj = om.detj()
+    np.testing.assert_allclose((dj[:, None] * out[:, :, 0]).sum(0), (dj[:, None] * c0[:, :, 0]).sum(0),
+                               rtol=1e-12, atol=1e-13 * np.abs(c0[:, :, 0]).max())
+    assert m.info["ncolors"] == 3 and m.info["ne"] == om.ne
     m.close()
 
 

@@ -21,6 +21,7 @@ import pytest
 
 from paper_1601_07613_gb300 import dgc
 from paper_1601_07613_gb300 import workloads as W
+from _amr import second_level
 from _parity import check, fp64_vs_exact, rel
 
 pytestmark = pytest.mark.gpu
@@ -38,7 +39,7 @@ def torch_dev():
 class Refined:
     """A refined mesh on the device and its oracle twin."""
 
-    def __init__(self, torch_dev, oracle_mod, mi, p, elems, seed=1601, epb=None):
+    def __init__(self, torch_dev, oracle_mod, mi, p, elems, seed=1601, epb=None, second=None):
         self.torch, self.dev = torch_dev
         self.p = p
         self.m = dgc.Mesh.from_input(mi, p)
@@ -47,7 +48,13 @@ class Refined:
         col, _ = om.color(3, seed)
         self.m.refine(elems)
         self.om = om.refine(col, elems)
-        assert self.m.info["ne"] == self.om.ne and self.m.info["ncolors"] == 6
+        if second is not None:
+            # a second level: the elements second(oracle mesh) picks, refined again
+            e2 = second(self.om)
+            self.m.refine(e2)
+            self.om = self.om.refine(self.om.colors, e2)
+        assert self.m.info["ne"] == self.om.ne
+        assert self.m.info["ncolors"] == (6 if second is None else 12)
         if epb:
             dgc.dgc_set_option(self.m.h, dgc.DGC_OPT_EDGES_PER_BLOCK, epb)
         T = self.torch
@@ -168,6 +175,47 @@ def test_refined_rk_step_matches_oracle(torch_dev, oracle_mod, p):
         got, dt = run.rk(prec, 0.3)
         assert abs(dt - dt_ref) < 1e-13 * dt_ref
         check(got - c, ref - c, tol)
+        run.close()
+
+
+def _second(rm):
+    return second_level(rm, (0.45, 0.55), 0.18, 0.36)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("kind", ["periodic", "open"])
+def test_two_level_rhs_matches_oracle(torch_dev, oracle_mod, p, kind):
+    """A second level (12 colors; level-2 elements beside level-1 ones, and
+    level-0 elements beside level-1 ones that were refined from their hanging
+    side): the right-hand side in both precisions, and the comparators."""
+    mi, elems = _case(kind)
+    run = Refined(torch_dev, oracle_mod, mi, p, elems, second=_second)
+    lev = run.om.levels
+    L, _, _, _ = run.om.sides()
+    hang = run.om.hanging >= 0
+    assert (lev == 2).sum() > 100 and (hang & (lev[L] == 2)).sum() > 20 and (hang & (lev[L] == 1)).sum() > 20
+    c = W.random_state(run.om.ne, 4, run.m.info["np"], seed=p)
+    run.load(c)
+    ref = run.om.rhs(p, c)
+    check(run.rhs(dgc.DGC_FP64), ref, 1e-12, "two levels FP64")
+    check(run.rhs(dgc.DGC_FP32_MIXED), ref, 1e-5, "two levels FP32-mixed")
+    if p == 2:
+        check(run.rhs(dgc.DGC_FP64, "atomic"), ref, 1e-12, "two levels atomic")
+        check(run.rhs(dgc.DGC_FP64, "two_pass"), ref, 1e-12, "two levels two-pass")
+    run.close()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_two_level_rk_step_matches_oracle(torch_dev, oracle_mod, p):
+    mi, elems = _case("periodic")
+    for prec, tol in ((dgc.DGC_FP64, 1e-11), (dgc.DGC_FP32_MIXED, 1e-5)):
+        run = Refined(torch_dev, oracle_mod, mi, p, elems, second=_second)
+        c = run.vortex()
+        ref, dt_ref = run.om.rk_step(p, c, 0.3)
+        run.load(c)
+        got, dt = run.rk(prec, 0.3)
+        assert abs(dt - dt_ref) < 1e-13 * dt_ref
+        check(got - c, ref - c, tol, f"two levels RK step prec {prec}")
         run.close()
 
 

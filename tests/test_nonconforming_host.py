@@ -15,6 +15,10 @@ Pins of the oracle's right-hand side on meshes with hanging edges:
   points of a split edge would break it;
 * refining every element gives a conforming mesh: the result equals the one of
   the same mesh built directly from its element list.
+A second level (the map with its palette doubled again, 12 colors): validity,
+the 2:1 refusal, the same right-hand-side pins on a two-level mesh, refining
+every element twice, and the library's second level and its coarsening stack
+against the oracle, bit for bit.
 """
 
 import json
@@ -25,6 +29,7 @@ import pytest
 
 from paper_1601_07613_gb300 import dgc
 from paper_1601_07613_gb300 import workloads as W
+from _amr import second_level
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
 
@@ -191,8 +196,15 @@ def test_refine_errors():
     assert e.value.status == 1
     m.refine([0, 0, 5])  # duplicates are one element
     assert m.info["ne"] == 72 + 6
-    with pytest.raises(dgc.DgcError) as e:  # one level only
-        m.refine([1])
+    l, r, _, _ = dgc.dgc_get_sides(m.h)
+    hang = dgc.dgc_get_hanging(m.h) >= 0
+    with pytest.raises(dgc.DgcError) as e:  # finer than its neighbour: 2:1 balance
+        m.refine([int(l[hang][0])])
+    assert e.value.status == 1
+    m.refine([3])  # the middle child of element 0 (only siblings around it): level 2
+    assert m.info["ncolors"] == 12
+    with pytest.raises(dgc.DgcError) as e:  # a third level would need 24 colors
+        m.refine([6])  # the middle grandchild
     assert e.value.status == 4
     t = dgc.Mesh.from_input(W.periodic_cube_tet(3), 1)
     t.color(1)
@@ -324,4 +336,148 @@ def test_library_coarsening_restores_mesh_and_coloring(frac):
     assert e.value.status == 1
     m.refine(flag)  # and refine again
     assert m.info["ncolors"] == 6
+    m.close()
+
+
+# ---------------------------------------------------------------------------
+# a second level of refinement
+# ---------------------------------------------------------------------------
+def _two_level(oracle_mod, mi, seed=7, frac=None, center=(0.45, 0.55), r1=0.3, r2=0.18):
+    om, col = _colored(oracle_mod, mi, seed)
+    e1 = W.elements_near(mi, center, r1)
+    rm = om.refine(col, e1)
+    e2 = second_level(rm, center, r2, r1 + 0.06)
+    return om, col, e1, rm, e2, rm.refine(rm.colors, e2)
+
+
+@pytest.mark.parametrize("kind", ["periodic", "open"])
+def test_second_level_coloring_is_valid(oracle_mod, kind):
+    mi = (W.periodic_square_tri(16, jitter=0.2, seed=61) if kind == "periodic"
+          else W.open_square_tri(16, jitter=0.2, seed=61))
+    om, col, e1, rm, e2, r2 = _two_level(oracle_mod, mi)
+    assert len(e2) > 10 and (rm.levels[e2] == 0).any() and (rm.levels[e2] == 1).any()
+    assert set(np.unique(r2.colors)) == set(range(1, 13))
+    assert set(np.unique(r2.levels)) == {0, 1, 2}
+    for cs in _edge_colors_per_element(r2.sides(), r2.colors, r2.ne):
+        assert len(cs) == len(set(cs)), cs
+    L, R, _, _ = r2.sides()
+    hang = r2.hanging >= 0
+    # every hanging edge joins elements one level apart; conforming edges equal levels
+    assert (r2.levels[L[hang]] == r2.levels[R[hang]] + 1).all()
+    conf = ~hang & (R >= 0)
+    assert (r2.levels[L[conf]] == r2.levels[R[conf]]).all()
+    # a level-L element's colors lie in 1..3 * 2^L (split edges of coarse ones aside)
+    nsides = np.bincount(np.concatenate([L, R[R >= 0]]), minlength=r2.ne)
+    for s in range(r2.ns):
+        e = L[s]
+        if nsides[e] == 3:
+            assert r2.colors[s] <= 3 << r2.levels[e]
+
+
+def test_second_level_refuses_a_finer_element(oracle_mod):
+    mi = W.periodic_square_tri(10, jitter=0.2, seed=62)
+    om, col = _colored(oracle_mod, mi, 3)
+    rm = om.refine(col, W.elements_near(mi, (0.5, 0.5), 0.25))
+    l, _, _, _ = rm.sides()
+    fine = l[rm.hanging >= 0][0]
+    with pytest.raises(ValueError):
+        rm.refine(rm.colors, [fine])
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_second_level_freestream_and_conservation(oracle_mod, p):
+    mi = W.periodic_square_tri(12, jitter=0.2, seed=63)
+    *_, r2 = _two_level(oracle_mod, mi)
+    rhs = r2.rhs(p, _const(r2.ne, oracle_mod.npoly(2, p)))
+    h = 1.0 / 48  # finest elements
+    assert np.abs(rhs).max() * (0.5 * h * h) / (3.4 * h * 3.0) < 1e-13
+    c = W.random_state(r2.ne, 4, oracle_mod.npoly(2, p), seed=p, amp=2e-2)
+    rhs = r2.rhs(p, c)
+    detj = r2.detj()
+    total = (detj[:, None] * rhs[:, :, 0]).sum(axis=0)
+    scale = (detj[:, None] * np.abs(rhs[:, :, 0])).sum(axis=0)
+    assert np.all(np.abs(total) < 1e-13 * scale)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_second_level_linear_advection_closed_form(oracle_mod, p):
+    mi = W.open_square_tri(10, jitter=0.2, seed=64)
+    *_, r2 = _two_level(oracle_mod, mi)
+    assert ((r2.hanging >= 0) & (r2.levels[r2.sides()[0]] == 2)).sum() > 5
+    a = np.array([0.7, -1.3])
+    coef = np.random.default_rng(p).uniform(-1, 1, size=(p + 1) * (p + 2) // 2)
+    xyz, _, _ = r2.eval_points(p, M=1)
+    u, _, _ = _poly2(p, coef, xyz[..., 0], xyz[..., 1])
+    c = r2.project(p, u[..., None])
+    rhs = r2.rhs(p, c, kind=oracle_mod.ADVECTION, adv=a)
+    xyz2, _, U = r2.eval_points(p, c=rhs, n1=p + 3)
+    _, gx, gy = _poly2(p, coef, xyz2[..., 0], xyz2[..., 1])
+    np.testing.assert_allclose(U[..., 0], -(a[0] * gx + a[1] * gy), atol=1e-9)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_second_level_linear_advection_brute_force(oracle_mod, p):
+    mi = W.periodic_square_tri(8, jitter=0.2, seed=65)
+    *_, r2 = _two_level(oracle_mod, mi)
+    c = np.random.default_rng(p).uniform(-1, 1, size=(r2.ne, 1, oracle_mod.npoly(2, p)))
+    a = np.array([0.4, 0.9])
+    r0 = r2.rhs(p, c, kind=oracle_mod.ADVECTION, adv=a)
+    r1 = r2.rhs(p, c, kind=oracle_mod.ADVECTION, adv=a, nq_face1=30, nq_vol1=30)
+    np.testing.assert_allclose(r0, r1, atol=1e-12 * np.abs(r1).max())
+
+
+def test_all_refined_twice_equals_conforming_mesh(oracle_mod):
+    mi = W.open_square_tri(4, jitter=0.2, seed=66)
+    om, col = _colored(oracle_mod, mi, 3)
+    rm = om.refine(col, np.arange(om.ne))
+    r2 = rm.refine(rm.colors, np.arange(rm.ne))
+    assert (r2.hanging < 0).all() and set(np.unique(r2.levels)) == {2}
+    ev, X = r2.elements()
+    xyz = np.zeros((r2.nv, 2))
+    xyz[ev.ravel()] = X.reshape(-1, 2)
+    plain = oracle_mod.OracleMesh(2, xyz, ev)
+    assert plain.ns == r2.ns
+    c = W.random_state(r2.ne, 4, 10, seed=4, amp=2e-2)
+    r0 = r2.rhs(3, c)
+    r1 = plain.rhs(3, c)
+    assert np.linalg.norm(r0 - r1) <= 1e-14 * np.linalg.norm(r1)
+
+
+@pytest.mark.parametrize("kind", ["periodic", "open"])
+def test_library_second_level_matches_oracle_and_coarsens_back(oracle_mod, kind):
+    mi = (W.periodic_square_tri(16, jitter=0.2, seed=67) if kind == "periodic"
+          else W.open_square_tri(16, jitter=0.2, seed=67))
+    om, col, e1, rm, e2, r2 = _two_level(oracle_mod, mi, seed=31)
+    m = dgc.Mesh.from_input(mi, 2)
+    m.color(31)
+    states = [(dgc.dgc_get_sides(m.h), dgc.dgc_get_ordering(m.h), dgc.dgc_get_elements(m.h), dict(m.info))]
+    m.refine(e1)
+    states.append((dgc.dgc_get_sides(m.h), dgc.dgc_get_ordering(m.h), dgc.dgc_get_elements(m.h), dict(m.info)))
+    m.refine(e2)
+    for a, b in zip(dgc.dgc_get_sides(m.h), r2.sides()):
+        np.testing.assert_array_equal(a, b)
+    ev, X = dgc.dgc_get_elements(m.h)
+    evo, Xo = r2.elements()
+    np.testing.assert_array_equal(ev, evo)
+    np.testing.assert_array_equal(X, Xo)
+    np.testing.assert_array_equal(dgc.dgc_get_hanging(m.h), r2.hanging)
+    en, sn, colL, off = dgc.dgc_get_ordering(m.h)
+    np.testing.assert_array_equal(colL, r2.colors)
+    en_o, sn_o, off_o = r2.reorder(r2.colors, 12)
+    np.testing.assert_array_equal(en, en_o)
+    np.testing.assert_array_equal(sn, sn_o)
+    np.testing.assert_array_equal(off, off_o)
+    assert m.info["ncolors"] == 12 and m.info["perfect"] == 0
+    for want in reversed(states):  # coarsening undoes one level at a time
+        m.coarsen()
+        got = (dgc.dgc_get_sides(m.h), dgc.dgc_get_ordering(m.h), dgc.dgc_get_elements(m.h))
+        for a, b in zip(want[:3], got):
+            for x, y in zip(a, b):
+                np.testing.assert_array_equal(x, y)
+        assert m.info == want[3]
+    with pytest.raises(dgc.DgcError):
+        m.coarsen()
+    m.refine(e1)  # and both levels come back the same
+    m.refine(e2)
+    np.testing.assert_array_equal(dgc.dgc_get_ordering(m.h)[2], r2.colors)
     m.close()
