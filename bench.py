@@ -421,6 +421,7 @@ def run_dgc(args, rank, world, local_rank):
         del buf, r
         variants.update(run_batched(dgc, torch, dev, stream, args))
         variants.update(run_other_meshes(dgc, torch, dev, stream, args))
+        variants["nonconforming_two_level_p2_256"] = run_two_level(dgc, torch, dev, stream, args)
         variants.update(run_table7(dgc, torch, dev, stream, args, cfg, c_host))
         variants.update(run_double_mach(dgc, torch, dev, stream, args))
         variants["coloring_tables"] = run_coloring_tables(dgc)
@@ -723,6 +724,53 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     return out
 
 
+def run_two_level(dgc, torch, dev, stream, args) -> dict:
+    """The nonconforming workload refined a second time (the palette doubled
+    again, 12 colors): the 256 x 256 x 2 mesh refined within radius 0.2 of the
+    vortex centre, then its children within 0.1 and the coarse elements beside
+    hanging halves right of the centre within 0.23 refined again; p = 2.  The
+    mixed and FP64 RK steps, the colored right-hand side, and the device color
+    map of the second level."""
+    ref = W.refined_square_vortex_p2_256()
+    mi, p = ref["mesh"], ref["p"]
+    t0 = time.perf_counter()
+    m = dgc.Mesh.from_input(mi, p)
+    m.color(1601)
+    m.refine(ref["refine"])
+    l, r, _, _ = dgc.dgc_get_sides(m.h)
+    _, xyz = dgc.dgc_get_elements(m.h)
+    e2 = W.second_level_elements(ref["refine"], mi.ne, l, r, dgc.dgc_get_hanging(m.h), xyz, (0.5, 0.5), 0.1, 0.23)
+    m.refine(e2)
+    prep_s = time.perf_counter() - t0
+    info = m.info
+    xyzv = dgc.dgc_vol_points(m.h)
+    c_host = dgc.dgc_project(m.h, W.vortex_field(xyzv[..., 0], xyzv[..., 1], beta=ref["beta"]))
+    dofs = info["ne"] * info["M"] * info["np"]
+    _, map_ms = dgc.dgc_refine_colors_device(m.h, info["ns"])
+    off = dgc.dgc_get_ordering(m.h)[3]
+    entry = {"elements": info["ne"], "sides": info["ns"], "colors": info["ncolors"], "p": p,
+             "second_level_parents": int(len(e2)), "per_color": np.diff(off).tolist(),
+             "host_refine_s": round(prep_s, 3), "device_color_map_ms": round(map_ms, 4)}
+    c = torch.empty(m.state_shape(), dtype=torch.float64, device=dev)
+    rr = torch.empty_like(c)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    for prec, name in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
+        ws = torch.empty(dgc.dgc_workspace_size(m.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
+        dgc.dgc_import_state(m.h, c_host, c)
+        fn = lambda: dgc.dgc_rk_step(m.h, prec, c, ref["cfl"], dt, ws)
+        fn()
+        ms = time_steps(torch, fn, max(3, args.steps // (1 if prec == dgc.DGC_FP32_MIXED else 5)), stream)
+        entry[f"rk_{name}"] = {"value": 3 * dofs / (ms * 1e-3), "ms_per_step": round(ms, 4),
+                               "launches_per_step": dgc.dgc_last_launch_count(m.h)}
+        call = lambda: dgc.dgc_rhs(m.h, prec, c, rr)
+        call()
+        t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
+        entry[f"rhs_colored_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
+        del ws
+    m.close()
+    return entry
+
+
 def run_coloring_tables(dgc) -> list:
     """Tables 1-3's kind of statistics on this library (host only): triangle,
     quadrilateral and tetrahedral meshes of growing size (each about 4x the last,
@@ -982,7 +1030,8 @@ def main():
     ap.add_argument("--no-pdl", action="store_true", help="launch the headline step's kernels in plain stream order")
     ap.add_argument("--n", type=int, default=724, help="grid size n (n x n squares, 2 n^2 triangles); "
                     "724 is the benchmark workload, smaller n is for profiler captures")
-    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "bilinear", "batch", "double_mach"],
+    ap.add_argument("--only", choices=["tet", "nonconforming", "quad", "hybrid", "bilinear", "batch", "double_mach",
+                                       "two_level"],
                     help="time only that one of the other workloads (its variants entry, printed alone)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -998,6 +1047,8 @@ def main():
             print(json.dumps(run_batched(dgc, torch, dev, st, args)), flush=True)
         elif args.only == "double_mach":
             print(json.dumps(run_double_mach(dgc, torch, dev, st, args)), flush=True)
+        elif args.only == "two_level":
+            print(json.dumps({"nonconforming_two_level_p2_256": run_two_level(dgc, torch, dev, st, args)}), flush=True)
         else:
             print(json.dumps(run_other_meshes(dgc, torch, dev, st, args, only=args.only)), flush=True)
         return

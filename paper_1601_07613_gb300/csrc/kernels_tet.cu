@@ -915,19 +915,19 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
 #pragma unroll
             for (int kk = 0; kk < KF; ++kk) old[m * NP + j] = fmaf(Tl[kk * NP + j], bvar(kk, m), old[m * NP + j]);
         tstore(r, old);
-        return;
-      }
+      } else {
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        float cm[NP];
+        for (int m = 0; m < 5; ++m) {
+          float cm[NP];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          float v = MODE == SURF_FIRST ? vsm[(m * NP + j) * blockDim.x + threadIdx.x] : 0.0f;
+          for (int j = 0; j < NP; ++j) {
+            float v = MODE == SURF_FIRST ? vsm[(m * NP + j) * blockDim.x + threadIdx.x] : 0.0f;
 #pragma unroll
-          for (int kk = 0; kk < KF; ++kk) v = fmaf(Tl[kk * NP + j], bvar(kk, m), v);
-          cm[j] = v;
+            for (int kk = 0; kk < KF; ++kk) v = fmaf(Tl[kk * NP + j], bvar(kk, m), v);
+            cm[j] = v;
+          }
+          tet_write_var<P, RT, MODE>(A, elem, k, side, m, cm);
         }
-        tet_write_var<P, RT, MODE>(A, elem, k, side, m, cm);
       }
     }
   }

@@ -437,6 +437,31 @@ def refined_square_vortex_p2_256(n: int = 256, radius: float = 0.2) -> dict:
                 xc=0.5, yc=0.5, cfl=0.3, steps=200)
 
 
+def second_level_elements(refined, ne0: int, left, right, hanging, xyz, center, radius: float,
+                          coarse_radius: float) -> np.ndarray:
+    """The elements to refine a second time after one refinement of the elements
+    ``refined`` of an ``ne0``-element mesh (ids in the refined mesh's expanded
+    order, as the library numbers them): children (level 1) with no coarser
+    neighbour -- the fine side of no hanging edge, so adjacent elements still
+    differ by at most one level -- whose centroid lies within ``radius`` of
+    ``center``, and coarse elements beside hanging halves within
+    ``coarse_radius`` and right of ``center``.  left, right, hanging: the refined
+    mesh's sides (dgc_get_sides, dgc_get_hanging); xyz: its elements' vertex
+    coordinates [E][3][2] (dgc_get_elements)."""
+    flag = np.zeros(ne0, bool)
+    flag[np.asarray(refined, dtype=np.int64)] = True
+    level = np.repeat(flag.astype(np.int8), np.where(flag, 4, 1))
+    hang = np.asarray(hanging) >= 0
+    fine = np.zeros(level.size, bool)
+    fine[np.asarray(left)[hang]] = True
+    coarse = np.zeros(level.size, bool)
+    coarse[np.asarray(right)[hang]] = True
+    d = np.asarray(xyz).mean(axis=1) - np.asarray(center, dtype=np.float64)
+    d2 = (d * d).sum(axis=1)
+    sel = ((level == 1) & ~fine & (d2 < radius * radius)) | (coarse & (d2 < coarse_radius ** 2) & (d[:, 0] > 0))
+    return np.nonzero(sel)[0].astype(np.int32)
+
+
 def hybrid_square_vortex_p3_512(n: int = 512, frac: float = 0.3) -> dict:
     """Hybrid workload (Table 2's hybrid mesh at benchmark scale): the periodic
     n x n parallelogram grid with a fraction ``frac`` of its cells split into two
