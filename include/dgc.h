@@ -532,7 +532,8 @@ const char* dgc_last_error(void);
  *   (each call writes what it reads first; dt_dev and the CFL minimum are reset per call).
  *   Calls whose work overlaps on the GPU (two streams, or two meshes at once) race on
  *   the array: serialise them.  A context reset (cudaDeviceReset) frees the array with
- *   every other device buffer of the library: destroy the meshes before one. */
+ *   every other device buffer of the library: destroy the meshes before one; the next mesh
+ *   upload on the new context looks the array up again. */
 dgc_status dgc_rk_step_static(dgc_mesh* mesh, dgc_prec prec, void* c_dev, double cfl,
                               double* dt_dev, void* stream);
 

@@ -1609,17 +1609,20 @@ std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
 
 // In host code the array's name is only a host-side stand-in, so its address
-// is looked up once per device (with that device current) and cached.  A
-// context reset (cudaDeviceReset) frees it with every other device buffer the
-// library holds; meshes must be destroyed before one and re-created after.
+// is looked up with the device current.  Every mesh upload (load) looks it up
+// again, which loads the module on a new context, and caches it; the step only
+// reads the cache.  A context reset (cudaDeviceReset) frees the array with
+// every other device buffer the library holds: meshes must be destroyed before
+// one and re-created (uploaded again, refreshing the address) after.
 void* static_scratch(int dev, bool load) {
   if (dev < 0 || dev >= kMaxDevices) throw Error{DGC_ERR_UNSUPPORTED, "device index out of range"};
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[dev]) {
-    if (!load) throw Error{DGC_ERR_ARG, "the static array is not reserved on this device: upload a mesh first"};
+  if (load) {
     void* p = nullptr;
     DGC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
     g_static_addr[dev] = p;
+  } else if (!g_static_addr[dev]) {
+    throw Error{DGC_ERR_ARG, "the static array is not reserved on this device: upload a mesh first"};
   }
   return g_static_addr[dev];
 }
