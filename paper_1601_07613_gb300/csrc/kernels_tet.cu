@@ -44,15 +44,25 @@ struct TetTab {
   T wF[TetDim<P>::NQF];                 // face weights, sum 1
 };
 
-__constant__ TetTab<double, 1> cTetD1;
-__constant__ TetTab<double, 2> cTetD2;
+// the FP64 tables the kernels read: the basis at the volume points (the CFL
+// pass, phi_0) and the face weights (the FP64 volume integrals take their
+// tables as FP32 pairs in shared memory)
+template <int P>
+struct TetTabD {
+  double phiV[TetDim<P>::NQV][TetDim<P>::NP];
+  double wF[TetDim<P>::NQF];
+};
+__constant__ TetTabD<1> cTetD1;
+__constant__ TetTabD<2> cTetD2;
 __constant__ TetTab<float, 1> cTetF1;
 __constant__ TetTab<float, 2> cTetF2;
 
 template <typename T, int P>
 __device__ __forceinline__ const TetTab<T, P>& tet_tab();
-template <> __device__ __forceinline__ const TetTab<double, 1>& tet_tab<double, 1>() { return cTetD1; }
-template <> __device__ __forceinline__ const TetTab<double, 2>& tet_tab<double, 2>() { return cTetD2; }
+template <int P>
+__device__ __forceinline__ const TetTabD<P>& tet_tabd();
+template <> __device__ __forceinline__ const TetTabD<1>& tet_tabd<1>() { return cTetD1; }
+template <> __device__ __forceinline__ const TetTabD<2>& tet_tabd<2>() { return cTetD2; }
 template <> __device__ __forceinline__ const TetTab<float, 1>& tet_tab<float, 1>() { return cTetF1; }
 template <> __device__ __forceinline__ const TetTab<float, 2>& tet_tab<float, 2>() { return cTetF2; }
 
@@ -71,9 +81,11 @@ static void fill_tet(TetTab<T, P>& K, const RefTables& R) {
 
 template <int P>
 static void upload_tet_p(const RefTables& R, const void* symD, const void* symF) {
-  static TetTab<double, P> hd;
+  static TetTabD<P> hd;
   static TetTab<float, P> hf;
-  fill_tet(hd, R);
+  for (int q = 0; q < TetDim<P>::NQV; ++q)
+    for (int j = 0; j < TetDim<P>::NP; ++j) hd.phiV[q][j] = R.phiV[q * TetDim<P>::NP + j];
+  for (int q = 0; q < TetDim<P>::NQF; ++q) hd.wF[q] = R.fw[q];
   fill_tet(hf, R);
   cudaMemcpyToSymbol(symD, &hd, sizeof hd);
   cudaMemcpyToSymbol(symF, &hf, sizeof hf);
@@ -94,6 +106,41 @@ template <int P>
 __device__ __forceinline__ const TetPairTab<P>& tet_ptab();
 template <> __device__ __forceinline__ const TetPairTab<1>& tet_ptab<1>() { return cTetP1; }
 template <> __device__ __forceinline__ const TetPairTab<2>& tet_ptab<2>() { return cTetP2; }
+
+// Variable 4 of the volume integral on the packed FMA too: its modes in pairs
+// (1, 2), (3, 4), ...; the tables hold (t_j, t_j+1) (0 past the last mode).
+template <int P>
+struct TetModePairTab {
+  static constexpr int NH = TetDim<P>::NP / 2;  // pairs of the modes 1..NP-1
+  float2 phiV[TetDim<P>::NQV][NH];
+  float2 vr[TetDim<P>::NQV][NH];
+  float2 vs[TetDim<P>::NQV][NH];
+  float2 vt[TetDim<P>::NQV][NH];
+};
+__constant__ TetModePairTab<1> cTetQ1;
+__constant__ TetModePairTab<2> cTetQ2;
+template <int P>
+__device__ __forceinline__ const TetModePairTab<P>& tet_qtab();
+template <> __device__ __forceinline__ const TetModePairTab<1>& tet_qtab<1>() { return cTetQ1; }
+template <> __device__ __forceinline__ const TetModePairTab<2>& tet_qtab<2>() { return cTetQ2; }
+
+template <int P>
+static void upload_tet_mode_pairs(const RefTables& R, const void* sym) {
+  using D = TetDim<P>;
+  static TetTab<float, P> f;
+  static TetModePairTab<P> h;
+  fill_tet(f, R);
+  auto at = [](const float (&t)[D::NQV][D::NP], int q, int j) { return j < D::NP ? t[q][j] : 0.0f; };
+  for (int q = 0; q < D::NQV; ++q)
+    for (int k = 0; k < TetModePairTab<P>::NH; ++k) {
+      const int j = 1 + 2 * k;
+      h.phiV[q][k] = make_float2(at(f.phiV, q, j), at(f.phiV, q, j + 1));
+      h.vr[q][k] = make_float2(at(f.vr, q, j), at(f.vr, q, j + 1));
+      h.vs[q][k] = make_float2(at(f.vs, q, j), at(f.vs, q, j + 1));
+      h.vt[q][k] = make_float2(at(f.vt, q, j), at(f.vt, q, j + 1));
+    }
+  cudaMemcpyToSymbol(sym, &h, sizeof h);
+}
 
 template <int P>
 static void upload_tet_pairs(const RefTables& R, const void* sym) {
@@ -193,6 +240,8 @@ void tet_upload_tables(int p, const RefTables& R, DeviceMesh& d) {
   if (p == 2) upload_tet_p<2>(R, &cTetD2, &cTetF2);
   if (p == 1) upload_tet_pairs<1>(R, &cTetP1);
   if (p == 2) upload_tet_pairs<2>(R, &cTetP2);
+  if (p == 1) upload_tet_mode_pairs<1>(R, &cTetQ1);
+  if (p == 2) upload_tet_mode_pairs<2>(R, &cTetQ2);
   // orientation tables for the faces (FP64) and the FP32 lanes' face-modal
   // tables T [4][6][KF][NP], in global memory
   std::vector<double> t = tet_face_orient_tables(R), psi, T;
@@ -282,7 +331,7 @@ __device__ __forceinline__ void tsplit(double phi0, double c0, float& hi, float&
 template <int P>
 __device__ __forceinline__ void tload_pert(const double* src, TetPert<P>& B) {
   using D = TetDim<P>;
-  const double phi0 = tet_tab<double, P>().phiV[0][0];
+  const double phi0 = tet_tabd<P>().phiV[0][0];
   double v[D::NV];
   tload(src, v);
 #pragma unroll
@@ -310,7 +359,7 @@ __device__ __forceinline__ void tload_pert(const float* src, TetPert<P>& B) {
 template <int P>
 __device__ __forceinline__ void trecord_of(const double (&v)[TetDim<P>::NV], float (&r)[TetDim<P>::NF]) {
   using D = TetDim<P>;
-  const double phi0 = tet_tab<double, P>().phiV[0][0];
+  const double phi0 = tet_tabd<P>().phiV[0][0];
 #pragma unroll
   for (int m = 0; m < 5; ++m) {
     tsplit(phi0, v[m * D::NP], r[m], r[5 + m]);
@@ -352,7 +401,7 @@ struct TetDfBlock {
   DF cd[5][TetDim<P>::NP - 1];
   __device__ __forceinline__ void init(const double (&c)[TetDim<P>::NV]) {
     constexpr int NP = TetDim<P>::NP;
-    const double phi0 = tet_tab<double, P>().phiV[0][0];
+    const double phi0 = tet_tabd<P>().phiV[0][0];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
       ub[m] = phi0 * c[m * NP];
@@ -433,9 +482,11 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
     th[k] = R.u[1] * J[k][0] + R.u[2] * J[k][1] + R.u[3] * J[k][2];
   }
   // variables (0, 1) and (2, 3) in pairs on the packed FP32 FMA (__ffma2_rn),
-  // variable 4 alone
+  // variable 4 with its modes in pairs (1, 2), (3, 4), ...
   const TetPairTab<P>& K2 = tet_ptab<P>();
-  float2 c01[NP - 1], c23[NP - 1], a01[NP - 1], a23[NP - 1];
+  const TetModePairTab<P>& K4 = tet_qtab<P>();
+  constexpr int NH = TetModePairTab<P>::NH;
+  float2 c01[NP - 1], c23[NP - 1], a01[NP - 1], a23[NP - 1], c4[NH], a4[NH];
 #pragma unroll
   for (int j = 1; j < NP; ++j) {
     c01[j - 1] = make_float2(B.cd[0][j - 1], B.cd[1][j - 1]);
@@ -443,17 +494,24 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
     a01[j - 1] = make_float2(acc[j], acc[NP + j]);
     a23[j - 1] = make_float2(acc[2 * NP + j], acc[3 * NP + j]);
   }
+#pragma unroll
+  for (int k = 0; k < NH; ++k) {
+    const int j = 1 + 2 * k;
+    c4[k] = make_float2(B.cd[4][j - 1], j + 1 < NP ? B.cd[4][j] : 0.0f);
+    a4[k] = make_float2(acc[4 * NP + j], j + 1 < NP ? acc[4 * NP + j + 1] : 0.0f);
+  }
 #pragma unroll 2
   for (int q = 0; q < D::NQV; ++q) {
     float2 d01 = make_float2(B.lo[0], B.lo[1]), d23 = make_float2(B.lo[2], B.lo[3]);
-    float d4 = B.lo[4];
+    float2 d4p = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int j = 1; j < NP; ++j) {
       d01 = __ffma2_rn(K2.phiV[q][j], c01[j - 1], d01);
       d23 = __ffma2_rn(K2.phiV[q][j], c23[j - 1], d23);
-      d4 += K.phiV[q][j] * B.cd[4][j - 1];
     }
-    const float d[5] = {d01.x, d01.y, d23.x, d23.y, d4};
+#pragma unroll
+    for (int k = 0; k < NH; ++k) d4p = __ffma2_rn(K4.phiV[q][k], c4[k], d4p);
+    const float d[5] = {d01.x, d01.y, d23.x, d23.y, B.lo[4] + (d4p.x + d4p.y)};
     PertState<3> S;
     S.init(R, d);
     float Fr[3][5];
@@ -469,8 +527,12 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
     for (int j = 1; j < NP; ++j) {
       a01[j - 1] = __ffma2_rn(K2.vt[q][j], f01[2], __ffma2_rn(K2.vs[q][j], f01[1], __ffma2_rn(K2.vr[q][j], f01[0], a01[j - 1])));
       a23[j - 1] = __ffma2_rn(K2.vt[q][j], f23[2], __ffma2_rn(K2.vs[q][j], f23[1], __ffma2_rn(K2.vr[q][j], f23[0], a23[j - 1])));
-      acc[4 * NP + j] += K.vr[q][j] * Fr[0][4] + K.vs[q][j] * Fr[1][4] + K.vt[q][j] * Fr[2][4];
     }
+    const float2 g0 = make_float2(Fr[0][4], Fr[0][4]), g1 = make_float2(Fr[1][4], Fr[1][4]),
+                 g2 = make_float2(Fr[2][4], Fr[2][4]);
+#pragma unroll
+    for (int k = 0; k < NH; ++k)
+      a4[k] = __ffma2_rn(K4.vt[q][k], g2, __ffma2_rn(K4.vs[q][k], g1, __ffma2_rn(K4.vr[q][k], g0, a4[k])));
   }
 #pragma unroll
   for (int j = 1; j < NP; ++j) {
@@ -478,6 +540,12 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
     acc[NP + j] = a01[j - 1].y;
     acc[2 * NP + j] = a23[j - 1].x;
     acc[3 * NP + j] = a23[j - 1].y;
+  }
+#pragma unroll
+  for (int k = 0; k < NH; ++k) {
+    const int j = 1 + 2 * k;
+    acc[4 * NP + j] = a4[k].x;
+    if (j + 1 < NP) acc[4 * NP + j + 1] = a4[k].y;
   }
 }
 
@@ -705,7 +773,7 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
     const CT* ph = sphi + (lf * 6 + orient) * NQ * NP;
     // FP64 flux and update, the basis contractions as FP32 pairs on the flux
     // deviations (tet_volume_df)
-    const TetTab<double, P>& K = tet_tab<double, P>();
+    const TetTabD<P>& K = tet_tabd<P>();
     const float2* ph2 = reinterpret_cast<const float2*>(ph);
     TetDfBlock<P> B;
     {
@@ -899,7 +967,7 @@ __global__ void __launch_bounds__(256, (sizeof(CT) == 4 ? DGC_TET_MINB : 1))
         for (int i = 0; i < NV; ++i) L[i] += acc[i];
         TetPert<P> B;
         if (A.sa.stage == 0) tload_pert<P>(src, B);
-        incr_last<5, NP>(A.sa, elem, L, B, tet_tab<double, P>().phiV[0][0]);
+        incr_last<5, NP>(A.sa, elem, L, B, tet_tabd<P>().phiV[0][0]);
       }
     } else if (writer) {
       if constexpr (MODE == SURF_RMW && sizeof(RT) == 4) {
@@ -971,7 +1039,7 @@ __global__ void __launch_bounds__(128) k_cfl1_tet(const double* c, const double*
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float best = FLT_MAX;
   if (e < ne) {
-    const double phi0 = tet_tab<double, P>().phiV[0][0];
+    const double phi0 = tet_tabd<P>().phiV[0][0];
     float r[D::NF];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
@@ -1007,7 +1075,7 @@ __global__ void __launch_bounds__(128) k_cfl2_tet(const double* c, const double*
   const bool cand = e < ne && est[e] <= __uint_as_float(*minbits) * (1.0f + kCflMargin);
   unsigned mask = __ballot_sync(0xffffffffu, cand);
   double best = DBL_MAX;
-  const TetTab<double, P>& K = tet_tab<double, P>();
+  const TetTabD<P>& K = tet_tabd<P>();
   while (mask) {
     const int src = __ffs(mask) - 1;
     mask &= mask - 1;
