@@ -1009,26 +1009,18 @@ template <int P>
 __device__ __forceinline__ float tet_lambda_rec(const float (&r)[TetDim<P>::NF]) {
   using D = TetDim<P>;
   constexpr int NP = D::NP;
-  // variables (0, 1) and (2, 3) in pairs on the packed FMA, variable 4 with
-  // its modes in pairs, as in the volume integral
-  const TetPairTab<P>& K2 = tet_ptab<P>();
-  const TetModePairTab<P>& K4 = tet_qtab<P>();
-  constexpr int NH = TetModePairTab<P>::NH, NM = NP - 1;
+  const TetTab<float, P>& K = tet_tab<float, P>();
   float lam = 0.0f;
 #pragma unroll 2
   for (int q = 0; q < D::NQV; ++q) {
-    float2 s01 = make_float2(r[5], r[6]), s23 = make_float2(r[7], r[8]), s4 = make_float2(0.0f, 0.0f);
+    float U[5];
 #pragma unroll
-    for (int j = 1; j < NP; ++j) {
-      s01 = __ffma2_rn(K2.phiV[q][j], make_float2(r[10 + j - 1], r[10 + NM + j - 1]), s01);
-      s23 = __ffma2_rn(K2.phiV[q][j], make_float2(r[10 + 2 * NM + j - 1], r[10 + 3 * NM + j - 1]), s23);
-    }
+    for (int m = 0; m < 5; ++m) {
+      float s = r[5 + m];
 #pragma unroll
-    for (int k = 0; k < NH; ++k) {
-      const int j = 1 + 2 * k;
-      s4 = __ffma2_rn(K4.phiV[q][k], make_float2(r[10 + 4 * NM + j - 1], j + 1 < NP ? r[10 + 4 * NM + j] : 0.0f), s4);
+      for (int j = 1; j < NP; ++j) s += K.phiV[q][j] * r[10 + m * (NP - 1) + j - 1];
+      U[m] = r[m] + s;
     }
-    const float U[5] = {r[0] + s01.x, r[1] + s01.y, r[2] + s23.x, r[3] + s23.y, r[4] + (r[9] + (s4.x + s4.y))};
     const float ir = rcp_fast(U[0]), u = U[1] * ir, w = U[2] * ir, z = U[3] * ir;
     const float q2 = u * u + w * w + z * z;
     const float pr = 0.4f * (U[4] - 0.5f * U[0] * q2);
