@@ -217,8 +217,8 @@ def kernel_source_hash() -> str:
 # stage) from ncu captures of this benchmark's own command at full size with
 # the tiles 64x2, 64x2, 32x4 (one kernel and two launches per capture), taken
 # with the kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = "67e61dd5d5033dc3"
-TRAFFIC_BYTES = {"last": 1123999146, "first": 480886698, "color": 592280192, "cfl": 4221056}
+TRAFFIC_SOURCES = "ce0631bb07d066b6"
+TRAFFIC_BYTES = {"last": 1123927936, "first": 480811562, "color": 592662272, "cfl": 4220672}
 
 
 def fp64_roofline(flops: float, ms: float, p64: float) -> dict:
