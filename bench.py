@@ -600,7 +600,7 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
     656,100 periodic parallelograms (810 x 810, 4 edge colors) at p = 3, the
     hybrid 512 x 512 grid with 30 % of its cells split into triangles at p = 3,
     and 262,144 general (bilinear) quadrilaterals (512 x 512, every vertex
-    jittered) at p = 3, the last two in FP64 only.
+    jittered) at p = 3, the last two through the table-driven kernels.
     On the tetrahedra and the parallelograms the mixed step also gets a per-kernel
     breakdown from a profiled pass against the HBM roofline."""
     out = {}
@@ -640,11 +640,9 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
         dt = torch.zeros(1, dtype=torch.float64, device=dev)
         entry = {"elements": info["ne"], "faces": info["ns"], "p": p, "dofs": dofs, "colors": info["ncolors"],
                  "host_mesh_color_s": round(prep_s, 2)}
-        # FP64 only (the FP32 forms refuse hybrid meshes and general quadrilaterals)
+        # (hybrid meshes and general quadrilaterals: the table-driven kernels, FP64 and FP32-mixed)
         hybrid = tag.startswith(("hybrid", "bilinear"))
         for prec, name in ((dgc.DGC_FP32_MIXED, "fp32mixed"), (dgc.DGC_FP64, "fp64")):
-            if hybrid and prec != dgc.DGC_FP64:
-                continue
             ws = torch.empty(dgc.dgc_workspace_size(m.h, prec) // 8 + 64, dtype=torch.float64, device=dev)
             dgc.dgc_import_state(m.h, c_host, c)
             fn = lambda: dgc.dgc_rk_step(m.h, prec, c, 0.3, dt, ws)
@@ -653,7 +651,7 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
             ms = time_steps(torch, fn, k, stream)
             entry[f"rk_{name}"] = {"value": 3 * dofs / (ms * 1e-3), "ms_per_step": round(ms, 4),
                                    "launches_per_step": dgc.dgc_last_launch_count(m.h)}
-            if prec == dgc.DGC_FP32_MIXED and refine is None:
+            if prec == dgc.DGC_FP32_MIXED and refine is None and not hybrid:
                 dgc.dgc_set_option(m.h, dgc.DGC_OPT_PROFILE, 1)
                 dgc.dgc_profile_collect(m.h)
                 msp = time_steps(torch, fn, k, stream)

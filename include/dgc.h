@@ -210,8 +210,11 @@ typedef enum { DGC_TRI = 0, DGC_QUAD = 1, DGC_TET = 2 } dgc_elem;
  * P_k(2x-1) (Np = (p+1)^2, orthonormal on the square; p = 1..3).  A mesh whose
  * elements are all parallelograms (v2 = v1 + v3 - v0 to 1e-12 of the element size)
  * maps them affinely and runs in every precision.  A hybrid mesh, or a mesh with
- * general (non-parallelogram) quadrilaterals, runs in FP64 only (other precisions:
- * DGC_ERR_UNSUPPORTED) through table-driven kernels: its states hold (p+1)^2
+ * general (non-parallelogram) quadrilaterals, runs in DGC_FP64 and DGC_FP32_MIXED
+ * (DGC_FP32_KAHAN: DGC_ERR_UNSUPPORTED) through table-driven kernels (the mixed form:
+ * FP32 fluxes and projections of the deviations from each element's mean, an FP64
+ * state, right-hand side and stage update; its RK step takes the FP64 step's
+ * workspace): its states hold (p+1)^2
  * coefficients per variable for every element, a triangle using the first
  * (p+1)(p+2)/2 (its P_p basis as on triangle meshes; the rest are zero on output);
  * a general quadrilateral maps the square bilinearly, its coefficients refer to the

@@ -477,15 +477,19 @@ void check_ptr(const void* p, const char* what) {
 
 // ss: floats per element of an FP32 state (record or Kahan state), 0 for FP64 states
 int vol(const Ctx& x, TypeCfg ty, const void* s, int ss, void* r, int64_t e0 = 0) {
-  if (x.hybrid) return ty == TY_D && e0 == 0 ? hyb_volume(x, static_cast<const double*>(s), static_cast<double*>(r)) : -1;
+  if (x.hybrid)
+    return (ty == TY_D || ty == TY_MD) && e0 == 0
+               ? hyb_volume(x, static_cast<const double*>(s), static_cast<double*>(r), ty == TY_MD)
+               : -1;
   if (x.quad) return quad_volume(x, ty, s, ss, r, e0);
   return x.dim == 2 ? tri_volume(x, ty, s, ss, r, e0) : tet_volume(x, ty, s, ss, r, e0);
 }
 int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const void* s, int ss, void* r, void* buf,
          const StageArgs* sa) {
   if (x.hybrid) {
-    if (ty != TY_D || (mode != SURF_RMW && mode != SURF_ATOMIC)) return -1;
-    return hyb_surface(x, mode == SURF_ATOMIC, b, e, static_cast<const double*>(s), static_cast<double*>(r));
+    if ((ty != TY_D && ty != TY_MD) || (mode != SURF_RMW && mode != SURF_ATOMIC)) return -1;
+    return hyb_surface(x, mode == SURF_ATOMIC, b, e, static_cast<const double*>(s), static_cast<double*>(r),
+                       ty == TY_MD);
   }
   if (x.quad) return quad_surface(x, ty, mode, b, e, s, ss, r, buf, sa);
   return x.dim == 2 ? tri_surface(x, ty, mode, b, e, s, ss, r, buf, sa)
@@ -494,7 +498,7 @@ int surf(const Ctx& x, TypeCfg ty, SurfMode mode, int64_t b, int64_t e, const vo
 // general quadrilaterals of a hybrid mesh: their mass matrices, after the colors
 int mass(const Ctx& x, TypeCfg ty, void* r) {
   if (!x.hybrid) return 0;
-  return ty == TY_D ? hyb_mass(x, static_cast<double*>(r)) : -1;
+  return ty == TY_D || ty == TY_MD ? hyb_mass(x, static_cast<double*>(r)) : -1;
 }
 int cfl(const Ctx& x, const double* s, double c, double* dt, float* sh) {
   if (x.hybrid) return sh ? -1 : hyb_cfl(x, s, c, dt);
@@ -616,7 +620,7 @@ Workspace carve(const Mesh& m, dgc_prec prec, char* base) {
     o += align256(b);
     return p;
   };
-  if (prec == DGC_FP64) {
+  if (prec == DGC_FP64 || m.hybrid) {  // hybrid meshes take the FP64 step in both forms
     w.u1 = reinterpret_cast<double*>(take(S));
     w.rhs = take(S);
   } else {
@@ -640,7 +644,9 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
   const std::vector<int32_t>& off = m.color_off;
   const int C = m.ncolors;
   const bool fused = m.fuse && m.perfect && C >= 2;
-  if (prec == DGC_FP64) {
+  if (prec == DGC_FP64 || m.hybrid) {
+    // (hybrid meshes in the FP32-mixed form: this FP64 step with FP32 fluxes and projections)
+    const TypeCfg ty = prec == DGC_FP64 ? TY_D : TY_MD;
     double* c64 = static_cast<double*>(c);
     launch(DGC_K_CFL, [&] { return cfl(x, c64, cfl_, dt, nullptr); });
     const double A0[3] = {0.0, 0.75, 1.0 / 3.0}, B0[3] = {1.0, 0.25, 2.0 / 3.0};
@@ -658,20 +664,20 @@ void rk_step_body(const Mesh& m, const Ctx& x, dgc_prec prec, void* c, double cf
       sa.a0 = A0[s];
       sa.b0 = B0[s];
       if (fused) {
-        launch(DGC_K_FIRST, [&] { return surf(x, TY_D, SURF_FIRST, off[0], off[1], us, 0, w.rhs, nullptr, nullptr); });
+        launch(DGC_K_FIRST, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], us, 0, w.rhs, nullptr, nullptr); });
         for (int k = 2; k < C; ++k)
-          launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
-        launch(DGC_K_LAST, [&] { return surf(x, TY_D, SURF_LAST, off[C - 1], off[C], us, 0, w.rhs, nullptr, &sa); });
+          launch(DGC_K_COLOR, [&] { return surf(x, ty, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
+        launch(DGC_K_LAST, [&] { return surf(x, ty, SURF_LAST, off[C - 1], off[C], us, 0, w.rhs, nullptr, &sa); });
       } else {
         int k0 = 1;
         if (first_fused(m)) {
-          launch(DGC_K_FIRST, [&] { return surf(x, TY_D, SURF_FIRST, off[0], off[1], us, 0, w.rhs, nullptr, nullptr); });
+          launch(DGC_K_FIRST, [&] { return surf(x, ty, SURF_FIRST, off[0], off[1], us, 0, w.rhs, nullptr, nullptr); });
           k0 = 2;
         }
-        launch(DGC_K_VOLUME, [&] { return vol(x, TY_D, us, 0, w.rhs, k0 == 2 ? unreached(m) : 0); });
+        launch(DGC_K_VOLUME, [&] { return vol(x, ty, us, 0, w.rhs, k0 == 2 ? unreached(m) : 0); });
         for (int k = k0; k <= C; ++k)
-          launch(DGC_K_COLOR, [&] { return surf(x, TY_D, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
-        launch(DGC_K_VOLUME, [&] { return mass(x, TY_D, w.rhs); });
+          launch(DGC_K_COLOR, [&] { return surf(x, ty, SURF_RMW, off[k - 1], off[k], us, 0, w.rhs, nullptr, nullptr); });
+        launch(DGC_K_VOLUME, [&] { return mass(x, ty, w.rhs); });
         launch(DGC_K_STAGE, [&] { return stage_update(x, false, us, w.rhs, sa); });
       }
       if (m.limit) launch(DGC_K_LIMIT, [&] { return tri_limit(x, sa.uout); });
@@ -964,7 +970,8 @@ static int64_t workspace_bytes(const Mesh& m, dgc_prec prec) { return carve(m, p
 
 static void require_prec(const Mesh& m, dgc_prec prec) {
   require(prec == DGC_FP64 || prec == DGC_FP32_MIXED || prec == DGC_FP32_KAHAN, "unknown precision");
-  require(!m.hybrid || prec == DGC_FP64, "hybrid triangle/quadrilateral meshes run in FP64", DGC_ERR_UNSUPPORTED);
+  require(!m.hybrid || prec != DGC_FP32_KAHAN, "hybrid triangle/quadrilateral meshes run in FP64 and FP32-mixed",
+          DGC_ERR_UNSUPPORTED);
   require(prec != DGC_FP32_KAHAN || (m.dim == 2 && !m.quad), "the Kahan form is implemented for triangle meshes",
           DGC_ERR_UNSUPPORTED);
   require(prec == DGC_FP64 || !m.limit, "the limiter runs in FP64", DGC_ERR_UNSUPPORTED);

@@ -195,8 +195,10 @@ int tri_volume(const Ctx& c, TypeCfg ty, const void* state, int sstride, void* r
 // hybrid triangle/quadrilateral meshes, FP64 (kernels_hybrid.cu): the volume
 // integral of every element (plain store), one color's edges (read-modify-write,
 // or atomics), the CFL step into *dt; the table size in doubles
-int hyb_volume(const Ctx& x, const double* state, double* rhs);
-int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs);
+// fp32: the FP32-mixed kernels (FP32 flux and projection, FP64 state and rhs)
+int hyb_volume(const Ctx& x, const double* state, double* rhs, bool fp32 = false);
+int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs,
+                bool fp32 = false);
 int hyb_cfl(const Ctx& x, const double* state, double cfl, double* dt);
 // general quadrilaterals: rhs <- M^-1 rhs on every bilinear element
 int hyb_mass(const Ctx& x, double* rhs);

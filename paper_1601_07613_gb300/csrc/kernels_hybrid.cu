@@ -22,6 +22,7 @@
 // scales instead.
 #include "dev_util.cuh"
 #include "device.cuh"
+#include "euler_pert.cuh"
 
 namespace dgc {
 
@@ -181,6 +182,155 @@ __global__ void __launch_bounds__(128) k_hyb_surf(const double* __restrict__ c, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32-mixed form (flux, quadrature and projection in FP32; FP64 state and
+// right-hand side), in the perturbation form the triangle kernels use
+// (euler_pert.cuh): each element's reference ub = phi_0 c_0 (FP64, kept as an
+// FP32 pair hi + lo), its modes j >= 1 in FP32, and the flux deviations
+// F(ub + d) - F(ub) projected in the volume and F* - F(ub).n on the faces.  The
+// omitted parts cancel for each element: the volume rule integrates
+// grad phi_j against detJ J^-1 exactly (J^-1 constant, or detJ J^-1 linear in
+// the reference coordinates on a bilinear element) and the edge rule phi_j on
+// each straight edge.  The tables are the FP64 ones, converted while staged.
+// ---------------------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ void hyb_stage32(float* s, const double* __restrict__ tab) {
+  for (int i = threadIdx.x; i < HybDim<P>::SIZE; i += blockDim.x) s[i] = d2f(tab[i]);
+}
+
+// the element's block in perturbation form: hi + lo = phi_0 c_0, cd = modes j >= 1
+template <int P>
+struct HybPert {
+  float hi[4], lo[4], cd[4][HybDim<P>::NPX - 1];
+  __device__ __forceinline__ void load(const double* __restrict__ ce, double phi0, int np) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const double u = phi0 * ce[m * HybDim<P>::NPX];
+      hi[m] = d2f(u);
+      lo[m] = d2f(u - f2d(hi[m]));
+#pragma unroll
+      for (int j = 1; j < HybDim<P>::NPX; ++j) cd[m][j - 1] = j < np ? d2f(ce[m * HybDim<P>::NPX + j]) : 0.0f;
+    }
+  }
+  // the deviation of the trace at a point from the reference: lo + sum_j b_j c_j
+  __device__ __forceinline__ void dev(const float* b, float (&d)[4]) const {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float v = lo[m];
+#pragma unroll
+      for (int j = 1; j < HybDim<P>::NPX; ++j) v = fmaf(b[j], cd[m][j - 1], v);
+      d[m] = v;
+    }
+  }
+};
+
+template <int P>
+__global__ void __launch_bounds__(128) k_hyb_vol32(const double* __restrict__ c, const double* __restrict__ jinv,
+                                                   const int8_t* __restrict__ kind, const double* __restrict__ tab,
+                                                   const int32_t* __restrict__ bil_slot,
+                                                   const double* __restrict__ bil_G, double* __restrict__ rhs,
+                                                   int64_t ne) {
+  using D = HybDim<P>;
+  __shared__ float s[D::SIZE];
+  hyb_stage32<P>(s, tab);
+  __syncthreads();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int k = kind[e];
+  const int np = k ? D::NPX : D::NPT;
+  const float* phi = s + D::vol(k ? 1 : 0);
+  const float* gr = phi + D::VOL;
+  const float* gs = gr + D::VOL;
+  HybPert<P> B;
+  B.load(c + e * D::NV, tab[D::vol(k ? 1 : 0)], np);  // phi_0 (constant) from the FP64 table
+  PertRef<2> R;
+  R.init(B.hi);
+  float nr[2] = {d2f(jinv[4 * e]), d2f(jinv[4 * e + 1])}, ns[2] = {d2f(jinv[4 * e + 2]), d2f(jinv[4 * e + 3])};
+  const double* Gq = k == 2 ? bil_G + (int64_t)bil_slot[e] * (4 * D::NQV) : nullptr;
+  float acc[D::NV];
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) acc[i] = 0.0f;
+  for (int q = 0; q < D::NQV; ++q) {
+    float d[4];
+    B.dev(phi + q * D::NPX, d);
+    if (Gq) nr[0] = d2f(Gq[4 * q]), nr[1] = d2f(Gq[4 * q + 1]), ns[0] = d2f(Gq[4 * q + 2]), ns[1] = d2f(Gq[4 * q + 3]);
+    PertState<2> S;
+    S.init(R, d);
+    float Fr[4], Fs[4];
+    pert_flux<2>(R, S, d, nr, R.u[1] * nr[0] + R.u[2] * nr[1], Fr);
+    pert_flux<2>(R, S, d, ns, R.u[1] * ns[0] + R.u[2] * ns[1], Fs);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 1; j < D::NPX; ++j)
+        acc[m * D::NPX + j] = fmaf(gr[q * D::NPX + j], Fr[m], fmaf(gs[q * D::NPX + j], Fs[m], acc[m * D::NPX + j]));
+  }
+  double* re = rhs + e * D::NV;
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) re[i] = (double)acc[i];  // zero past a triangle's modes (zero tables)
+}
+
+template <int P, bool ATOMIC>
+__global__ void __launch_bounds__(128) k_hyb_surf32(const double* __restrict__ c, const int4* __restrict__ topo,
+                                                    const double2* __restrict__ fgeo, const int8_t* __restrict__ kind,
+                                                    const double* __restrict__ tab, double* __restrict__ rhs,
+                                                    int64_t begin, int64_t end) {
+  using D = HybDim<P>;
+  constexpr int NQ = D::NQE;
+  __shared__ float s[D::SIZE];
+  hyb_stage32<P>(s, tab);
+  __syncthreads();
+  const int side = threadIdx.x & 1;
+  int64_t k = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1);
+  const bool valid = k < end;
+  if (!valid) k = end - 1;  // idle lanes shadow the last edge so both lanes of a pair shuffle
+  const int4 tp = topo[k];
+  const bool bnd = tp.y < 0;  // boundary: both lanes read the left element (U+ = U-)
+  const bool right = side && !bnd;
+  const int64_t elem = right ? tp.y : tp.x;
+  const int le = right ? ((tp.z >> 4) & 15) : (tp.z & 15);
+  const bool writer = valid && !(side && bnd);
+  const int kd = kind[elem] ? 1 : 0;  // a general quadrilateral takes the square's tables
+  const int np = kd ? D::NPX : D::NPT;
+  const double2 g0 = fgeo[2 * k], g1 = fgeo[2 * k + 1];
+  const float scale = right ? d2f(g1.y) : -d2f(g1.x);
+  const float* ph = s + D::edge(kd) + le * NQ * D::NPX;
+  const float* w = s + D::wts();
+  HybPert<P> B;
+  B.load(c + elem * D::NV, tab[D::vol(kd)], np);
+  PertRef<2> R;
+  R.init(B.hi);
+  // each lane evaluates its own side's flux and the pair exchanges one value per
+  // variable (euler_pert.cuh, lf_exchange); all 32 lanes run it
+  FaceConst<2> E;
+  E.init(R, B.hi, {d2f(g0.x), d2f(g0.y)}, side);
+  float acc[D::NV];
+#pragma unroll
+  for (int i = 0; i < D::NV; ++i) acc[i] = 0.0f;
+  for (int q = 0; q < NQ; ++q) {
+    const int qq = right ? NQ - 1 - q : q;
+    float t[4], G[4];
+    B.dev(ph + qq * D::NPX, t);
+    lf_exchange<2>(R, E, t, G);
+    const float g = scale * w[q];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float gm = g * G[m];
+#pragma unroll
+      for (int j = 0; j < D::NPX; ++j) acc[m * D::NPX + j] = fmaf(ph[qq * D::NPX + j], gm, acc[m * D::NPX + j]);
+    }
+  }
+  if (!writer) return;
+  double* re = rhs + elem * D::NV;
+  if constexpr (ATOMIC) {
+    for (int i = 0; i < D::NV; ++i)
+      if ((i % D::NPX) < np) atomicAdd(re + i, (double)acc[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < D::NV; ++i) re[i] += (double)acc[i];
+  }
+}
+
 // CFL: dt = cfl min_e r_e / ((2p+1) max_q (|u| + c)), one thread per element,
 // FP64, folded into *dt by a 64-bit atomicMin on the bits (positive doubles
 // order as their bit patterns); *dt must hold a large value beforehand
@@ -242,13 +392,16 @@ __global__ void __launch_bounds__(128) k_hyb_mass(const int32_t* __restrict__ bi
 
 template <int P>
 static int hyb_p(const Ctx& x, int what, const double* state, double* rhs, int64_t b, int64_t e, double cfl,
-                 double* dt) {
+                 double* dt, bool fp32 = false) {
   const int bs = 128;
   const DeviceMesh* d = x.d;
   if (what == 0) {
     if (x.ne <= 0) return 0;
-    k_hyb_vol<P><<<(unsigned)((x.ne + bs - 1) / bs), bs, 0, x.st>>>(state, d->jinv, d->hyb_kind, d->hyb_tab,
-                                                                    d->bil_slot, d->bil_G, rhs, x.ne);
+    const unsigned grid = (unsigned)((x.ne + bs - 1) / bs);
+    if (fp32)
+      k_hyb_vol32<P><<<grid, bs, 0, x.st>>>(state, d->jinv, d->hyb_kind, d->hyb_tab, d->bil_slot, d->bil_G, rhs, x.ne);
+    else
+      k_hyb_vol<P><<<grid, bs, 0, x.st>>>(state, d->jinv, d->hyb_kind, d->hyb_tab, d->bil_slot, d->bil_G, rhs, x.ne);
     return 1;
   }
   if (what == 4) {
@@ -260,7 +413,11 @@ static int hyb_p(const Ctx& x, int what, const double* state, double* rhs, int64
     const int64_t n = e - b;
     if (n <= 0) return 0;
     const unsigned grid = (unsigned)((2 * n + bs - 1) / bs);
-    if (what == 1)
+    if (fp32 && what == 1)
+      k_hyb_surf32<P, false><<<grid, bs, 0, x.st>>>(state, d->topo, d->fgeo, d->hyb_kind, d->hyb_tab, rhs, b, e);
+    else if (fp32)
+      k_hyb_surf32<P, true><<<grid, bs, 0, x.st>>>(state, d->topo, d->fgeo, d->hyb_kind, d->hyb_tab, rhs, b, e);
+    else if (what == 1)
       k_hyb_surf<P, false><<<grid, bs, 0, x.st>>>(state, d->topo, d->fgeo, d->hyb_kind, d->hyb_tab, rhs, b, e);
     else
       k_hyb_surf<P, true><<<grid, bs, 0, x.st>>>(state, d->topo, d->fgeo, d->hyb_kind, d->hyb_tab, rhs, b, e);
@@ -273,18 +430,20 @@ static int hyb_p(const Ctx& x, int what, const double* state, double* rhs, int64
 }
 
 static int hyb(const Ctx& x, int what, const double* state, double* rhs, int64_t b, int64_t e, double cfl,
-               double* dt) {
+               double* dt, bool fp32 = false) {
   switch (x.p) {
-    case 1: return hyb_p<1>(x, what, state, rhs, b, e, cfl, dt);
-    case 2: return hyb_p<2>(x, what, state, rhs, b, e, cfl, dt);
-    case 3: return hyb_p<3>(x, what, state, rhs, b, e, cfl, dt);
+    case 1: return hyb_p<1>(x, what, state, rhs, b, e, cfl, dt, fp32);
+    case 2: return hyb_p<2>(x, what, state, rhs, b, e, cfl, dt, fp32);
+    case 3: return hyb_p<3>(x, what, state, rhs, b, e, cfl, dt, fp32);
     default: return -1;
   }
 }
 
-int hyb_volume(const Ctx& x, const double* state, double* rhs) { return hyb(x, 0, state, rhs, 0, 0, 0.0, nullptr); }
-int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs) {
-  return hyb(x, atomic ? 2 : 1, state, rhs, begin, end, 0.0, nullptr);
+int hyb_volume(const Ctx& x, const double* state, double* rhs, bool fp32) {
+  return hyb(x, 0, state, rhs, 0, 0, 0.0, nullptr, fp32);
+}
+int hyb_surface(const Ctx& x, bool atomic, int64_t begin, int64_t end, const double* state, double* rhs, bool fp32) {
+  return hyb(x, atomic ? 2 : 1, state, rhs, begin, end, 0.0, nullptr, fp32);
 }
 int hyb_cfl(const Ctx& x, const double* state, double cfl, double* dt) {
   return hyb(x, 3, state, nullptr, 0, 0, cfl, dt);

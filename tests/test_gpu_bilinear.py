@@ -5,8 +5,10 @@ M = int phi_i phi_j detJ applied after the colors).  FP64, the plain
 Algorithm 1 sequence, against the oracle: right-hand side within 1e-12
 relative L2 (colored and atomic), one RK step's state change within 1e-11, dt
 within 1e-13 (per-element max as in tests/_parity.py); the allocation-free step
-bit-identical to the regular one; freestream; a 160 x 160 mesh of jittered
-quadrilaterals sampled against the extended oracle."""
+bit-identical to the regular one; the FP32-mixed form (FP32 fluxes and
+projections in perturbation form, FP64 state) within 1e-5; freestream; a
+160 x 160 mesh of jittered quadrilaterals sampled against the extended
+oracle."""
 
 import numpy as np
 import pytest
@@ -52,26 +54,26 @@ class B:
         self.c = T.empty(self.m.state_shape(), dtype=T.float64, device=self.dev)
         self.r = T.empty_like(self.c)
 
-    def rhs(self, c, kind="colored"):
+    def rhs(self, c, kind="colored", prec=dgc.DGC_FP64):
         dgc.dgc_import_state(self.m.h, c, self.c)
         self.r.fill_(float("nan"))
         if kind == "colored":
-            dgc.dgc_rhs(self.m.h, dgc.DGC_FP64, self.c, self.r)
+            dgc.dgc_rhs(self.m.h, prec, self.c, self.r)
         else:
-            dgc.dgc_rhs_atomic(self.m.h, dgc.DGC_FP64, self.c, self.r)
+            dgc.dgc_rhs_atomic(self.m.h, prec, self.c, self.r)
         self.torch.cuda.synchronize()
         return dgc.dgc_export_state(self.m.h, self.r)
 
-    def rk(self, c, cfl, steps=1, static=False):
+    def rk(self, c, cfl, steps=1, static=False, prec=dgc.DGC_FP64):
         T = self.torch
         dgc.dgc_import_state(self.m.h, c, self.c)
-        ws = T.empty(dgc.dgc_workspace_size(self.m.h, dgc.DGC_FP64) // 8 + 64, dtype=T.float64, device=self.dev)
+        ws = T.empty(dgc.dgc_workspace_size(self.m.h, prec) // 8 + 64, dtype=T.float64, device=self.dev)
         d = T.zeros(1, dtype=T.float64, device=self.dev)
         for _ in range(steps):
             if static:
-                dgc.dgc_rk_step_static(self.m.h, dgc.DGC_FP64, self.c, cfl, d)
+                dgc.dgc_rk_step_static(self.m.h, prec, self.c, cfl, d)
             else:
-                dgc.dgc_rk_step(self.m.h, dgc.DGC_FP64, self.c, cfl, d, ws)
+                dgc.dgc_rk_step(self.m.h, prec, self.c, cfl, d, ws)
         T.cuda.synchronize()
         return dgc.dgc_export_state(self.m.h, self.c), float(d.item())
 
@@ -94,6 +96,8 @@ def test_bilinear_rhs_matches_oracle(torch_dev, oracle_mod, kind, p):
     ref = oracle_mod.OracleMesh.from_input(mi).rhs(p, c)
     check(run.rhs(c), ref, 1e-12, f"bilinear {kind} p = {p}")
     check(run.rhs(c, "atomic"), ref, 1e-12, f"bilinear atomic {kind} p = {p}")
+    check(run.rhs(c, prec=dgc.DGC_FP32_MIXED), ref, 1e-5, f"bilinear FP32-mixed {kind} p = {p}")
+    check(run.rhs(c, "atomic", dgc.DGC_FP32_MIXED), ref, 1e-5, f"bilinear FP32-mixed atomic {kind} p = {p}")
     run.close()
 
 
@@ -109,6 +113,11 @@ def test_bilinear_rk_step_matches_oracle(torch_dev, oracle_mod, kind, p):
     assert abs(dt - dt_ref) < 1e-13 * dt_ref
     check(got - c, ref - c, 1e-11, f"bilinear {kind} RK step p = {p}")
     got_s, dt_s = run.rk(c, 0.3, static=True)
+    assert np.array_equal(got_s, got) and dt_s == dt
+    got, dt = run.rk(c, 0.3, prec=dgc.DGC_FP32_MIXED)
+    assert abs(dt - dt_ref) < 1e-13 * dt_ref
+    check(got - c, ref - c, 1e-5, f"bilinear FP32-mixed {kind} RK step p = {p}")
+    got_s, dt_s = run.rk(c, 0.3, static=True, prec=dgc.DGC_FP32_MIXED)
     assert np.array_equal(got_s, got) and dt_s == dt
     run.close()
 
@@ -126,6 +135,8 @@ def test_bilinear_freestream(torch_dev, oracle_mod):
     r = run.rhs(c)
     h = 0.1
     assert np.abs(r).max() * (0.5 * h * h) / (3.4 * h * 3.0) < 1e-12
+    r32 = run.rhs(c, prec=dgc.DGC_FP32_MIXED)
+    assert np.abs(r32).max() * (0.5 * h * h) / (3.4 * h * 3.0) < 1e-6
     run.close()
 
 

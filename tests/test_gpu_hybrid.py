@@ -4,8 +4,9 @@ with (p+1)^2 coefficients per variable, a triangle using the first
 (p+1)(p+2)/2).  FP64, the plain Algorithm 1 sequence (volume integral, then
 each color), against the oracle: right-hand side within 1e-12 relative L2, one
 RK step's state change within 1e-11 (per-element max as in tests/_parity.py),
-dt within 1e-13; the atomic comparator too; freestream; a 200 x 200 mesh
-sampled against the extended oracle."""
+dt within 1e-13; the atomic comparator too; the FP32-mixed form (FP32 fluxes
+and projections in perturbation form, FP64 state) within 1e-5; freestream; a
+200 x 200 mesh sampled against the extended oracle."""
 
 import numpy as np
 import pytest
@@ -50,23 +51,23 @@ class H:
         self.c = T.empty(self.m.state_shape(), dtype=T.float64, device=self.dev)
         self.r = T.empty_like(self.c)
 
-    def rhs(self, c, kind="colored"):
+    def rhs(self, c, kind="colored", prec=dgc.DGC_FP64):
         dgc.dgc_import_state(self.m.h, c, self.c)
         self.r.fill_(float("nan"))
         if kind == "colored":
-            dgc.dgc_rhs(self.m.h, dgc.DGC_FP64, self.c, self.r)
+            dgc.dgc_rhs(self.m.h, prec, self.c, self.r)
         else:
-            dgc.dgc_rhs_atomic(self.m.h, dgc.DGC_FP64, self.c, self.r)
+            dgc.dgc_rhs_atomic(self.m.h, prec, self.c, self.r)
         self.torch.cuda.synchronize()
         return dgc.dgc_export_state(self.m.h, self.r)
 
-    def rk(self, c, cfl, steps=1):
+    def rk(self, c, cfl, steps=1, prec=dgc.DGC_FP64):
         T = self.torch
         dgc.dgc_import_state(self.m.h, c, self.c)
-        ws = T.empty(dgc.dgc_workspace_size(self.m.h, dgc.DGC_FP64) // 8 + 64, dtype=T.float64, device=self.dev)
+        ws = T.empty(dgc.dgc_workspace_size(self.m.h, prec) // 8 + 64, dtype=T.float64, device=self.dev)
         d = T.zeros(1, dtype=T.float64, device=self.dev)
         for _ in range(steps):
-            dgc.dgc_rk_step(self.m.h, dgc.DGC_FP64, self.c, cfl, d, ws)
+            dgc.dgc_rk_step(self.m.h, prec, self.c, cfl, d, ws)
         T.cuda.synchronize()
         return dgc.dgc_export_state(self.m.h, self.c), float(d.item())
 
@@ -86,6 +87,10 @@ def test_hybrid_rhs_matches_oracle(torch_dev, oracle_mod, kind, p):
     tri = mi.ev[:, 3] < 0
     assert np.all(got[tri][:, :, (p + 1) * (p + 2) // 2:] == 0.0)
     check(run.rhs(c, "atomic"), ref, 1e-12, f"hybrid atomic {kind} p = {p}")
+    got = run.rhs(c, prec=dgc.DGC_FP32_MIXED)
+    check(got, ref, 1e-5, f"hybrid FP32-mixed {kind} p = {p}")
+    assert np.all(got[tri][:, :, (p + 1) * (p + 2) // 2:] == 0.0)
+    check(run.rhs(c, "atomic", dgc.DGC_FP32_MIXED), ref, 1e-5, f"hybrid FP32-mixed atomic {kind} p = {p}")
     run.close()
 
 
@@ -100,6 +105,9 @@ def test_hybrid_rk_step_matches_oracle(torch_dev, oracle_mod, p):
     got, dt = run.rk(c, 0.3)
     assert abs(dt - dt_ref) < 1e-13 * dt_ref
     check(got - c, ref - c, 1e-11, f"hybrid RK step p = {p}")
+    got, dt = run.rk(c, 0.3, prec=dgc.DGC_FP32_MIXED)
+    assert abs(dt - dt_ref) < 1e-13 * dt_ref
+    check(got - c, ref - c, 1e-5, f"hybrid FP32-mixed RK step p = {p}")
     run.close()
 
 
@@ -115,10 +123,11 @@ def test_hybrid_freestream_and_refusals(torch_dev, oracle_mod):
     r = run.rhs(c)
     h = 0.1
     assert np.abs(r).max() * (0.5 * h * h) / (3.4 * h * 3.0) < 1e-13
-    for prec in (dgc.DGC_FP32_MIXED, dgc.DGC_FP32_KAHAN):
-        with pytest.raises(dgc.DgcError) as e:
-            dgc.dgc_rhs(run.m.h, prec, run.c, run.r)
-        assert e.value.status == 4
+    r32 = run.rhs(c, prec=dgc.DGC_FP32_MIXED)  # the perturbation form: the flux of the mean cancels exactly
+    assert np.abs(r32).max() * (0.5 * h * h) / (3.4 * h * 3.0) < 1e-6
+    with pytest.raises(dgc.DgcError) as e:
+        dgc.dgc_rhs(run.m.h, dgc.DGC_FP32_KAHAN, run.c, run.r)
+    assert e.value.status == 4
     buf = torch.empty(1 << 20, dtype=torch.float64, device=dev)
     with pytest.raises(dgc.DgcError):
         dgc.dgc_rhs_two_pass(run.m.h, dgc.DGC_FP64, run.c, run.r, buf)

@@ -162,8 +162,8 @@ def test_quad_mesh_statuses(L):
     h = dgc.Mesh.from_input(W.hybrid_square(8, 0.3, seed=1), 2)  # unjittered squares and triangles: affine
     assert h.elem == dgc.DGC_QUAD and h.nonaffine == 0
     h.color(3)
-    with pytest.raises(dgc.DgcError) as e:
-        dgc.dgc_rhs(h.h, dgc.DGC_FP32_MIXED, 4096, 8192, 0)
+    with pytest.raises(dgc.DgcError) as e:  # hybrid meshes: FP64 and FP32-mixed, no Kahan form
+        dgc.dgc_rhs(h.h, dgc.DGC_FP32_KAHAN, 4096, 8192, 0)
     assert e.value.status == 4
     h.close()
     for gen in (lambda: W.hybrid_square(8, 0.3, jitter=0.2, seed=1),
@@ -172,10 +172,9 @@ def test_quad_mesh_statuses(L):
         m = dgc.Mesh.from_input(g, 2)
         assert m.elem == dgc.DGC_QUAD and m.nonaffine > 0
         m.color(3)
-        for prec in (dgc.DGC_FP32_MIXED, dgc.DGC_FP32_KAHAN):
-            with pytest.raises(dgc.DgcError) as e:
-                dgc.dgc_rhs(m.h, prec, 4096, 8192, 0)
-            assert e.value.status == 4
+        with pytest.raises(dgc.DgcError) as e:
+            dgc.dgc_rhs(m.h, dgc.DGC_FP32_KAHAN, 4096, 8192, 0)
+        assert e.value.status == 4
         with pytest.raises(dgc.DgcError) as e:
             dgc.dgc_refine(m.h, np.array([0], np.int32))
         assert e.value.status == 4
