@@ -217,8 +217,8 @@ def kernel_source_hash() -> str:
 # stage) from ncu captures of this benchmark's own command at full size with
 # the tiles 64x2, 64x2, 32x4 (one kernel and two launches per capture), taken
 # with the kernel sources of hash TRAFFIC_SOURCES.
-TRAFFIC_SOURCES = "ce0631bb07d066b6"
-TRAFFIC_BYTES = {"last": 1123927936, "first": 480811562, "color": 592662272, "cfl": 4220672}
+TRAFFIC_SOURCES = "4a0049ffaf80ecb9"
+TRAFFIC_BYTES = {"last": 1123873706, "first": 480706858, "color": 592563712, "cfl": 4220672}
 
 
 def fp64_roofline(flops: float, ms: float, p64: float) -> dict:
