@@ -272,7 +272,8 @@ dgc_status dgc_get_sides(const dgc_mesh* mesh, int32_t* left, int32_t* right, in
 
 /* Nonconforming refinement and its 6-color edge map (Sec. 3.2).  Splits each listed
  * triangle (original element ids; duplicates ignored; n = 0 refines nothing) into four by
- * its edge midpoints, one level, on a mesh colored by dgc_color_edges with 3 colors.
+ * its edge midpoints, one level per call, on a mesh colored by dgc_color_edges with 3
+ * colors or refined before (see below for a second level).
  *   Elements: every refined element is replaced in place by its children [v0, m01, m20],
  *     [m01, v1, m12], [m20, m12, v2], [m01, m12, m20] (new midpoint vertices numbered after
  *     the existing ones, one per split edge in edge order); the original element order of
