@@ -176,9 +176,15 @@ __global__ void __launch_bounds__(128) k_hyb_surf(const double* __restrict__ c, 
   if constexpr (ATOMIC) {
     for (int i = 0; i < D::NV; ++i)
       if ((i % D::NPX) < np) atomicAdd(re + i, acc[i]);
-  } else {
+  } else if (kd) {
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) re[i] += acc[i];
+  } else {
+    // a triangle: its own modes only (the rest stay as the volume kernel wrote them, zero)
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < D::NPT; ++j) re[m * D::NPX + j] += acc[m * D::NPX + j];
   }
 }
 
@@ -325,9 +331,15 @@ __global__ void __launch_bounds__(128) k_hyb_surf32(const double* __restrict__ c
   if constexpr (ATOMIC) {
     for (int i = 0; i < D::NV; ++i)
       if ((i % D::NPX) < np) atomicAdd(re + i, (double)acc[i]);
-  } else {
+  } else if (kd) {
 #pragma unroll
     for (int i = 0; i < D::NV; ++i) re[i] += (double)acc[i];
+  } else {
+    // a triangle: its own modes only (the rest stay as the volume kernel wrote them, zero)
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < D::NPT; ++j) re[m * D::NPX + j] += (double)acc[m * D::NPX + j];
   }
 }
 
