@@ -481,3 +481,26 @@ def test_library_second_level_matches_oracle_and_coarsens_back(oracle_mod, kind)
     m.refine(e2)
     np.testing.assert_array_equal(dgc.dgc_get_ordering(m.h)[2], r2.colors)
     m.close()
+
+
+def test_second_level_selection_helpers_agree(oracle_mod):
+    """The bench's second-level selection (workloads.second_level_elements, from
+    the library's sides, hanging flags and elements) picks the same elements as
+    the tests' (from the oracle's levels), and the library refines them."""
+    ref = W.refined_square_vortex_p2_256(n=48, radius=0.2)
+    mi = ref["mesh"]
+    om, col = _colored(oracle_mod, mi, 1601)
+    rm = om.refine(col, ref["refine"])
+    m = dgc.Mesh.from_input(mi, 2)
+    m.color(1601)
+    m.refine(ref["refine"])
+    l, r, _, _ = dgc.dgc_get_sides(m.h)
+    _, xyz = dgc.dgc_get_elements(m.h)
+    got = W.second_level_elements(ref["refine"], mi.ne, l, r, dgc.dgc_get_hanging(m.h), xyz, (0.5, 0.5), 0.1, 0.23)
+    want = second_level(rm, (0.5, 0.5), 0.1, 0.23)
+    np.testing.assert_array_equal(got, want)
+    assert len(got) > 10
+    m.refine(got)
+    assert m.info["ncolors"] == 12
+    np.testing.assert_array_equal(dgc.dgc_get_ordering(m.h)[2], rm.refine(rm.colors, want).colors)
+    m.close()
