@@ -473,7 +473,6 @@ __device__ __forceinline__ void tet_volume32(const TetPert<P>& B, const PertRef<
                                              float (&acc)[TetDim<P>::NV]) {
   using D = TetDim<P>;
   constexpr int NP = D::NP;
-  const TetTab<float, P>& K = tet_tab<float, P>();
   float J[3][3], th[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
