@@ -694,7 +694,8 @@ def run_other_meshes(dgc, torch, dev, stream, args, only=None):
                 call()
                 t_ = time_steps(torch, call, max(3, args.steps // 5), stream)
                 entry[f"rhs_colored_persistent_{name}"] = {"value": dofs / (t_ * 1e-3), "ms_per_rhs": round(t_, 4)}
-                dgc.dgc_set_option(m.h, dgc.DGC_OPT_PERSISTENT, 0)
+                # back to the library's default: persistent on refined meshes, else off
+                dgc.dgc_set_option(m.h, dgc.DGC_OPT_PERSISTENT, int(refine is not None))
             dgc.dgc_set_option(m.h, dgc.DGC_OPT_FUSE, 0)
             call = lambda: dgc.dgc_rhs(m.h, prec, c, r)
             call()

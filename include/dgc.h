@@ -107,9 +107,10 @@ typedef enum {
                                    phase.  Results are identical. */
   DGC_OPT_PERSISTENT = 7,       /* triangle meshes: 1 launches each color's surface kernel with at
                                    most one wave of blocks, every warp looping over the color in
-                                   steps of the whole grid (no partly filled last wave); 0
-                                   (default): one block per tile of edges.  Results are
-                                   identical. */
+                                   steps of the whole grid (no partly filled last wave); 0: one
+                                   block per tile of edges.  Default 0; dgc_refine sets 1 (the
+                                   refined region's colors fill less than a wave) and dgc_coarsen
+                                   back to a conforming mesh 0.  Results are identical. */
   DGC_OPT_LIMITER = 8           /* conforming triangle meshes, FP64: 1 applies the limiter of
                                    dgc_limit after every stage of dgc_rk_step (and of
                                    dgc_rk_step_static); 0 (default): no limiter.  The FP32 forms

@@ -1127,6 +1127,9 @@ void refine(Mesh& m, const std::vector<uint8_t>& flag) {
   m.refined = true;
   m.ncolors = 3 << std::max(1, maxlev);  // 6 even when nothing was refined
   m.perfect = false;
+  // the refined region's colors fill less than one wave of blocks: one wave per
+  // color, grid-stride (DGC_OPT_PERSISTENT; results identical)
+  m.persistent = true;
   reorder(m, true, true);
   m.dirty = true;
 }
@@ -1191,6 +1194,7 @@ void coarsen(Mesh& m) {
   m.ncolors = b.ncolors;
   m.perfect = b.shalf.empty();
   m.refined = !m.base_stack.empty();
+  m.persistent = m.refined;  // a conforming mesh again: one block per tile
   if (m.refined) {
     m.base = std::move(m.base_stack.back());
     m.base_stack.pop_back();
